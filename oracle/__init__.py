@@ -1,0 +1,135 @@
+"""FP64 CPU oracle of the split-operator Dirac scheme.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The product library never
+imports, links or executes anything here, and nothing here imports the product.
+
+``dirac_oracle.c`` holds the scheme itself (sweeps of Eqs. sol_dis_1-3, the
+phase of Eq. sol_dis_4 at A = 0, the face flux and the observables).  This
+module compiles it with gcc (``-ffp-contract=off``) and wraps it with ctypes.
+``klein.py`` holds the Klein-step transmission: the closed form of Eq. trans_co
+and a transfer integration of the stationary Dirac equation.
+
+State arrays are complex128 of shape (nz, ny, nx, 4), C-contiguous (ny = 1 for
+the 2-D x-z plane).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dirac_oracle.c")
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+I64_3 = ctypes.c_int64 * 3
+D3 = ctypes.c_double * 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle to oracle/_build/liboracle.so (gcc, OpenMP, no FP contraction)."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        lib.oracle_sweep.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_int]
+        lib.oracle_phase.argtypes = [P, I64_3, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, ctypes.c_int]
+        lib.oracle_step.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
+        lib.oracle_observables.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, D3, ctypes.c_int64, P]
+        for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _as_state(psi: np.ndarray) -> np.ndarray:
+    psi = np.asarray(psi)
+    if psi.ndim == 3:  # (nz, nx, 4): 2-D x-z plane
+        psi = psi[:, None, :, :]
+    if psi.ndim != 4 or psi.shape[-1] != 4:
+        raise ValueError("state must have shape (nz, ny, nx, 4) or (nz, nx, 4)")
+    return np.ascontiguousarray(psi, dtype=np.complex128).copy()
+
+
+def _dims(psi: np.ndarray):
+    nz, ny, nx, _ = psi.shape
+    return I64_3(nx, ny, nz)
+
+
+def _potential(V, psi):
+    if V is None:
+        return None, 0
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    nz, ny, nx, _ = psi.shape
+    if V.size == nx and V.ndim == 1:
+        return V, 1
+    if V.size == nx * ny * nz:
+        return V.reshape(-1), 2
+    raise ValueError("potential must have nx entries (one per x column) or one per cell")
+
+
+def sweep(psi, axis: int, periodic: bool = False) -> np.ndarray:
+    """One directional sub-step (Eq. sol_dis_1/2/3 for axis 0/1/2); returns a new array."""
+    out = _as_state(psi)
+    if _load().oracle_sweep(out.ctypes.data, _dims(out), int(axis), int(bool(periodic))) != 0:
+        raise MemoryError("oracle_sweep")
+    return out
+
+
+def phase(psi, m: float, c: float, dt: float, V=None) -> np.ndarray:
+    """Mass and scalar-potential step (Eq. sol_dis_4 at A = 0); returns a new array."""
+    out = _as_state(psi)
+    Varr, layout = _potential(V, out)
+    _load().oracle_phase(out.ctypes.data, _dims(out), float(m), float(c), float(dt),
+                         None if Varr is None else Varr.ctypes.data, layout)
+    return out
+
+
+def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
+         periodic: bool = False, flux_face: int = -1, flux_cum: float = 0.0):
+    """nsteps first-order split steps (Eqs. split1-4 discretised as sol_dis_1-4), dt = dx/c.
+
+    Returns (psi_out, flux_cum): the cumulative probability carried across the x face
+    `flux_face` (between cells flux_face-1 and flux_face), added to the given start value.
+    """
+    out = _as_state(psi)
+    Varr, layout = _potential(V, out)
+    fc = ctypes.c_double(flux_cum)
+    rc = _load().oracle_step(out.ctypes.data, _dims(out), int(ndim), int(bool(periodic)), float(m), float(c),
+                             float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
+                             int(flux_face), ctypes.addressof(fc))
+    if rc != 0:
+        raise MemoryError("oracle_step")
+    return out, fc.value
+
+
+def observables(psi, ndim: int, dx: float, x_min=(0.0, 0.0, 0.0), flux_face: int = -1) -> dict:
+    """norm, norm right of the flux face and centroid, summed in index order."""
+    arr = _as_state(psi)
+    out = (ctypes.c_double * 5)()
+    _load().oracle_observables(arr.ctypes.data, _dims(arr), int(ndim), float(dx), D3(*x_min),
+                               int(flux_face), ctypes.addressof(out))
+    return {"norm": out[0], "norm_right": out[1], "centroid": (out[2], out[3], out[4])}
+
+
+def density(psi) -> np.ndarray:
+    """rho = sum_c |psi_c|^2 per cell, shape (nz, ny, nx)."""
+    arr = _as_state(psi)
+    return (arr.real ** 2 + arr.imag ** 2).sum(axis=-1)

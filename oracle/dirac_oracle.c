@@ -1,0 +1,214 @@
+/*
+ * FP64 CPU oracle for the split-operator / method-of-characteristics Dirac
+ * scheme (Fillion-Gourdeau, Lorin, Bandrauk, "Numerical solution of the
+ * time-dependent Dirac equation in coordinate space without fermion-doubling").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow statement of what the
+ * scheme computes.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg load it; the product library never does.  It shares no code,
+ * header or table with the CUDA path.
+ *
+ * Grid and storage.  P0 finite volumes of edge a = dx (Sec. 2.3, Eq. discr_psi);
+ * cell (i,j,k) has centre x_min + (i+1/2)dx.  The state is stored point-major as
+ * psi[((k*ny + j)*nx + i)*4 + c] complex (re, im interleaved), c = 0..3 for the
+ * four spinor components.  "2-D" is the x-z plane (ny = 1, the y sweep omitted,
+ * Sec. 2.4 last paragraph).
+ *
+ * Boundary.  ZERO: cells outside the N cells are zero at every sub-step (the
+ * Dirichlet condition psi|dOmega = 0 of Sec. 5).  PERIODIC: indices wrap (the
+ * setting of the Fourier argument of Sec. 3).
+ *
+ * Arithmetic order (shared convention, written out on each side independently):
+ *   - each sweep forms 1/2 {(I + alpha) psi(i-1) + (I - alpha) psi(i+1)} with the
+ *     two bracketed rows added first and the sum then multiplied by 1/2;
+ *   - the phase multiplies by p = (cos t, -sin t) with t = m*c*c*dt + V*dt for
+ *     components 1,2 and t = V*dt - m*c*c*dt for components 3,4, the complex
+ *     product taken as re = fma(z.re, p.re, -(z.im*p.im)),
+ *     im = fma(z.re, p.im, z.im*p.re).
+ * Compiled with -ffp-contract=off so that no other contraction happens.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct { double re, im; } cplx;
+
+static inline cplx c_add(cplx a, cplx b) { cplx r = {a.re + b.re, a.im + b.im}; return r; }
+static inline cplx c_sub(cplx a, cplx b) { cplx r = {a.re - b.re, a.im - b.im}; return r; }
+/* a + i*b and a - i*b, with i*b = (-b.im, b.re) */
+static inline cplx c_add_ib(cplx a, cplx b) { cplx r = {a.re - b.im, a.im + b.re}; return r; }
+static inline cplx c_sub_ib(cplx a, cplx b) { cplx r = {a.re + b.im, a.im - b.re}; return r; }
+static inline cplx c_half(cplx a) { cplx r = {0.5 * a.re, 0.5 * a.im}; return r; }
+static inline cplx c_mul(cplx z, cplx p) {
+    cplx r;
+    r.re = fma(z.re, p.re, -(z.im * p.im));
+    r.im = fma(z.re, p.im, z.im * p.re);
+    return r;
+}
+static inline double c_abs2(cplx a) { return a.re * a.re + a.im * a.im; }
+
+/* Returns a pointer to the 4 components of cell (i,j,k), or NULL for a ghost
+ * cell outside the grid under the ZERO boundary. */
+static const cplx *cell(const cplx *psi, const int64_t n[3], int periodic,
+                        int64_t i, int64_t j, int64_t k) {
+    if (periodic) {
+        i = ((i % n[0]) + n[0]) % n[0];
+        j = ((j % n[1]) + n[1]) % n[1];
+        k = ((k % n[2]) + n[2]) % n[2];
+    } else if (i < 0 || i >= n[0] || j < 0 || j >= n[1] || k < 0 || k >= n[2]) {
+        return NULL;
+    }
+    return psi + ((k * n[1] + j) * n[0] + i) * 4;
+}
+
+static const cplx ZERO4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+
+/* One directional sub-step, Eqs. sol_dis_1 (axis 0), sol_dis_2 (axis 1),
+ * sol_dis_3 (axis 2): out(i) = 1/2 {(I + alpha_d) L + (I - alpha_d) R} with
+ * L = psi(i - e_d), R = psi(i + e_d).  Dirac representation (Eq. dirac_mat):
+ *   alpha_x psi = ( psi4,   psi3,   psi2,   psi1)
+ *   alpha_y psi = (-i psi4, i psi3, -i psi2, i psi1)
+ *   alpha_z psi = ( psi3,  -psi4,   psi1,  -psi2)
+ * Components are 0-based below (psi1 -> [0]). */
+static void sweep_cell(cplx *o, const cplx *L, const cplx *R, int axis) {
+    if (axis == 0) {
+        o[0] = c_half(c_add(c_add(L[0], L[3]), c_sub(R[0], R[3])));
+        o[1] = c_half(c_add(c_add(L[1], L[2]), c_sub(R[1], R[2])));
+        o[2] = c_half(c_add(c_add(L[1], L[2]), c_sub(R[2], R[1])));
+        o[3] = c_half(c_add(c_add(L[0], L[3]), c_sub(R[3], R[0])));
+    } else if (axis == 1) {
+        o[0] = c_half(c_add(c_sub_ib(L[0], L[3]), c_add_ib(R[0], R[3])));
+        o[1] = c_half(c_add(c_add_ib(L[1], L[2]), c_sub_ib(R[1], R[2])));
+        o[2] = c_half(c_add(c_sub_ib(L[2], L[1]), c_add_ib(R[2], R[1])));
+        o[3] = c_half(c_add(c_add_ib(L[3], L[0]), c_sub_ib(R[3], R[0])));
+    } else {
+        o[0] = c_half(c_add(c_add(L[0], L[2]), c_sub(R[0], R[2])));
+        o[1] = c_half(c_add(c_sub(L[1], L[3]), c_add(R[1], R[3])));
+        o[2] = c_half(c_add(c_add(L[0], L[2]), c_sub(R[2], R[0])));
+        o[3] = c_half(c_add(c_sub(L[3], L[1]), c_add(R[1], R[3])));
+    }
+}
+
+/* Sweep along `axis` (0 = x, 1 = y, 2 = z) of the whole grid, in place. */
+int oracle_sweep(double *psi_d, const int64_t n[3], int axis, int periodic) {
+    cplx *psi = (cplx *)psi_d;
+    int64_t total = n[0] * n[1] * n[2];
+    cplx *out = (cplx *)malloc((size_t)total * 4 * sizeof(cplx));
+    if (!out) return -1;
+    int64_t d[3] = {0, 0, 0};
+    d[axis] = 1;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i) {
+                const cplx *L = cell(psi, n, periodic, i - d[0], j - d[1], k - d[2]);
+                const cplx *R = cell(psi, n, periodic, i + d[0], j + d[1], k + d[2]);
+                sweep_cell(out + ((k * n[1] + j) * n[0] + i) * 4, L ? L : ZERO4, R ? R : ZERO4, axis);
+            }
+    memcpy(psi, out, (size_t)total * 4 * sizeof(cplx));
+    free(out);
+    return 0;
+}
+
+/* Potential energy at cell (i,j,k): layout 0 = none (V = 0), 1 = one value per
+ * x column (nx entries), 2 = one value per cell. */
+static double potential(const double *V, int layout, const int64_t n[3], int64_t i, int64_t j, int64_t k) {
+    if (layout == 1) return V[i];
+    if (layout == 2) return V[(k * n[1] + j) * n[0] + i];
+    return 0.0;
+}
+
+/* Mass and scalar-potential step, Eq. sol_dis_4 with A = 0:
+ * psi <- exp(-i beta m c^2 dt - i V dt) psi, i.e. components 1,2 multiplied by
+ * exp(-i (m c^2 dt + V dt)) and components 3,4 by exp(-i (V dt - m c^2 dt)).
+ * (The U matrix of Sec. 2.3 at A = 0 is diag(e^{-i mu}, e^{-i mu}, e^{i mu}, e^{i mu}).) */
+int oracle_phase(double *psi_d, const int64_t n[3], double m, double c, double dt,
+                 const double *V, int layout) {
+    cplx *psi = (cplx *)psi_d;
+    double mu = m * c * c * dt;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i) {
+                double vdt = potential(V, layout, n, i, j, k) * dt;
+                double t_up = mu + vdt;
+                double t_dn = vdt - mu;
+                cplx p_up = {cos(t_up), -sin(t_up)};
+                cplx p_dn = {cos(t_dn), -sin(t_dn)};
+                cplx *q = psi + ((k * n[1] + j) * n[0] + i) * 4;
+                q[0] = c_mul(q[0], p_up);
+                q[1] = c_mul(q[1], p_up);
+                q[2] = c_mul(q[2], p_dn);
+                q[3] = c_mul(q[3], p_dn);
+            }
+    return 0;
+}
+
+/* Probability carried across the face between cells face-1 and face during one
+ * x sweep (Sec. 2.2 and App. A): the +c characteristics (psi1+psi4, psi2+psi3)/sqrt2
+ * of cell face-1 move right, the -c characteristics (psi1-psi4, psi2-psi3)/sqrt2 of
+ * cell face move left.  With c dt = dx a whole cell's characteristic content moves
+ * one cell, so the probability is the density times the cell volume dx^d, summed
+ * over all (j,k) in index order. */
+static double face_flux(const cplx *psi, const int64_t n[3], int periodic, int64_t face, double vol) {
+    double f = 0.0;
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j) {
+            const cplx *a = cell(psi, n, periodic, face - 1, j, k);
+            const cplx *b = cell(psi, n, periodic, face, j, k);
+            a = a ? a : ZERO4;
+            b = b ? b : ZERO4;
+            double right = 0.5 * (c_abs2(c_add(a[0], a[3])) + c_abs2(c_add(a[1], a[2])));
+            double left = 0.5 * (c_abs2(c_sub(b[0], b[3])) + c_abs2(c_sub(b[1], b[2])));
+            f += right - left;
+        }
+    return f * vol;
+}
+
+/* nsteps steps of the first-order splitting, Eqs. split1-split4 in the discrete
+ * form sol_dis_1-sol_dis_4: x sweep, y sweep (3-D only), z sweep, phase.  dt = dx/c
+ * (c dt = a, K = 1, Sec. 2.3).  If flux_face >= 0 the probability crossing that x
+ * face in each x sweep is added to *flux_cum. */
+int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double m, double c,
+                double dx, const double *V, int layout, int64_t nsteps, int64_t flux_face,
+                double *flux_cum) {
+    double dt = dx / c;
+    double vol = (ndim == 3) ? dx * dx * dx : dx * dx;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
+        if (oracle_sweep(psi, n, 0, periodic)) return -1;
+        if (ndim == 3 && oracle_sweep(psi, n, 1, periodic)) return -1;
+        if (oracle_sweep(psi, n, 2, periodic)) return -1;
+        oracle_phase(psi, n, m, c, dt, V, layout);
+    }
+    return 0;
+}
+
+/* Observables, summed in index order:
+ *   out[0] = norm        = sum rho dx^d,  rho = sum_c |psi_c|^2
+ *   out[1] = norm_right  = sum over cells with i >= flux_face of rho dx^d (0 if flux_face < 0)
+ *   out[2..4] = centroid = sum x rho / sum rho, x = x_min + (i+1/2) dx per axis */
+int oracle_observables(const double *psi_d, const int64_t n[3], int ndim, double dx,
+                       const double x_min[3], int64_t flux_face, double out[5]) {
+    const cplx *psi = (const cplx *)psi_d;
+    double vol = (ndim == 3) ? dx * dx * dx : dx * dx;
+    double s = 0.0, sr = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i) {
+                const cplx *q = psi + ((k * n[1] + j) * n[0] + i) * 4;
+                double rho = c_abs2(q[0]) + c_abs2(q[1]) + c_abs2(q[2]) + c_abs2(q[3]);
+                s += rho;
+                if (flux_face >= 0 && i >= flux_face) sr += rho;
+                sx += (x_min[0] + (i + 0.5) * dx) * rho;
+                sy += (x_min[1] + (j + 0.5) * dx) * rho;
+                sz += (x_min[2] + (k + 0.5) * dx) * rho;
+            }
+    out[0] = s * vol;
+    out[1] = sr * vol;
+    out[2] = s > 0 ? sx / s : 0.0;
+    out[3] = s > 0 ? sy / s : 0.0;
+    out[4] = s > 0 ? sz / s : 0.0;
+    return 0;
+}

@@ -1,0 +1,187 @@
+"""Seeded synthetic inputs for the Dirac stepper: initial spinors, potentials and
+run-parameter draws.
+
+This module holds none of the scheme's arithmetic (no sweep, no phase, no
+observable); it only builds the inputs that both the CUDA path and the CPU
+oracle consume.  It imports numpy only.
+
+Units are atomic units (Sec. 5): m = 1, c = 137.0359895, hbar = |e| = 1.
+The cell edge defaults to dx = 10/8192 a.u. (the paper's 2-D mesh spacing), so
+that dt = dx/c = 8.9e-6 a.u. satisfies the time-step bound of Sec. 2.5.
+State arrays are complex128 of shape (nz, ny, nx, 4) (ny = 1 for the x-z plane).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+C_AU = 137.0359895
+M_E = 1.0
+DX_DEFAULT = 10.0 / 8192.0
+SEED = 20111107
+
+
+def cell_centres(n: int, dx: float, x_min: float) -> np.ndarray:
+    """x_min + (i + 1/2) dx, i = 0..n-1 (Sec. 2.3)."""
+    return x_min + (np.arange(n) + 0.5) * dx
+
+
+def normalise(psi: np.ndarray, dx: float, ndim: int) -> np.ndarray:
+    """Scale so that sum |psi|^2 dx^ndim = 1."""
+    rho = (psi.real ** 2 + psi.imag ** 2).sum()
+    return psi / np.sqrt(rho * dx ** ndim)
+
+
+def spinor_C(k0: float, m: float = M_E, c: float = C_AU) -> float:
+    """C = c k0 / (mc^2 + sqrt(m^2 c^4 + c^2 k0^2)) of the travelling packet (Sec. 5.1.4)."""
+    return c * k0 / (m * c * c + np.sqrt(m * m * c ** 4 + c * c * k0 * k0))
+
+
+def gaussian_packet(nx: int, nz: int, dx: float, x_min: float, z_min: float, x0: float, z0: float,
+                    width: float, k0: float, m: float = M_E, c: float = C_AU, ny: int = 1,
+                    y_min: float = 0.0, y0: float = 0.0) -> np.ndarray:
+    """N [1, 0, 0, C] e^{i k0 x} exp(-|r - r0|^2 / (4 width^2)) (Sec. 5.1.4 and 5.2.2), normalised.
+
+    With ny > 1 the Gaussian also extends along y (3-D)."""
+    x = cell_centres(nx, dx, x_min)
+    z = cell_centres(nz, dx, z_min)
+    gx = np.exp(-((x - x0) ** 2) / (4 * width ** 2)) * np.exp(1j * k0 * x)
+    gz = np.exp(-((z - z0) ** 2) / (4 * width ** 2))
+    if ny > 1:
+        y = cell_centres(ny, dx, y_min)
+        gy = np.exp(-((y - y0) ** 2) / (4 * width ** 2))
+    else:
+        gy = np.ones(1)
+    g = gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    spin = np.array([1.0, 0.0, 0.0, spinor_C(k0, m, c)], dtype=np.complex128)
+    psi = g[..., None] * spin
+    return normalise(psi.astype(np.complex128), dx, 3 if ny > 1 else 2)
+
+
+def positive_energy_packet_2d(nx: int, nz: int, dx: float, width: float, k0: float,
+                              m: float = M_E, c: float = C_AU) -> np.ndarray:
+    """Gaussian centred in the box, projected per Fourier mode of the periodic box onto the
+    positive-energy eigenspace of the free Hamiltonian c(alpha_x p_x + alpha_z p_z) + beta mc^2
+    (projector (1 + H(p)/E(p))/2), then normalised.  The box is [-nx dx/2, nx dx/2) x [-nz dx/2, nz dx/2)."""
+    psi = gaussian_packet(nx, nz, dx, -nx * dx / 2, -nz * dx / 2, 0.0, 0.0, width, k0, m, c)[:, 0]
+    px = 2 * np.pi * np.fft.fftfreq(nx, d=dx)
+    pz = 2 * np.pi * np.fft.fftfreq(nz, d=dx)
+    PX, PZ = np.meshgrid(px, pz)  # (nz, nx)
+    ax, az, beta = _dirac_alpha_x(), _dirac_alpha_z(), _dirac_beta()
+    H = c * (PX[..., None, None] * ax + PZ[..., None, None] * az) + m * c * c * beta
+    E = np.sqrt((c * PX) ** 2 + (c * PZ) ** 2 + (m * c * c) ** 2)
+    P = 0.5 * (np.eye(4) + H / E[..., None, None])
+    hat = np.fft.fft2(psi, axes=(0, 1))
+    hat = np.einsum("zxab,zxb->zxa", P, hat)
+    out = np.fft.ifft2(hat, axes=(0, 1))[:, None]
+    return normalise(out, dx, 2)
+
+
+def _dirac_beta():
+    return np.diag([1.0, 1.0, -1.0, -1.0]).astype(np.complex128)
+
+
+def _dirac_alpha_x():
+    a = np.zeros((4, 4), np.complex128)
+    a[0, 3] = a[1, 2] = a[2, 1] = a[3, 0] = 1.0
+    return a
+
+
+def _dirac_alpha_z():
+    a = np.zeros((4, 4), np.complex128)
+    a[0, 2] = 1.0
+    a[1, 3] = -1.0
+    a[2, 0] = 1.0
+    a[3, 1] = -1.0
+    return a
+
+
+def tanh_step(nx: int, dx: float, x_min: float, x_s: float, V0: float, L: float) -> np.ndarray:
+    """V(x) = V0/2 [1 + tanh((x - x_s)/L)] at the x cell centres (Sec. 5.2.1), one value per column."""
+    x = cell_centres(nx, dx, x_min)
+    return 0.5 * V0 * (1.0 + np.tanh((x - x_s) / L))
+
+
+def soft_coulomb_3d(n: int, dx: float, Z: float, a: float) -> np.ndarray:
+    """V = -Z / sqrt(r^2 + a^2) on an n^3 grid centred on the box centre, shape (n, n, n) [z][y][x]."""
+    x = cell_centres(n, dx, -n * dx / 2)
+    r2 = x[None, None, :] ** 2 + x[None, :, None] ** 2 + x[:, None, None] ** 2
+    return -Z / np.sqrt(r2 + a * a)
+
+
+def random_state(nz: int, ny: int, nx: int, seed: int) -> np.ndarray:
+    """Complex Gaussian noise, unit-normalised with dx = 1 (for parity on unstructured inputs)."""
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal((nz, ny, nx, 4)) + 1j * rng.standard_normal((nz, ny, nx, 4))
+    return psi / np.sqrt((np.abs(psi) ** 2).sum())
+
+
+@dataclasses.dataclass
+class KleinRun:
+    """One 2-D Klein-step scattering run on a square grid of `side` cells."""
+    side: int
+    V0: float       # step height, a.u.
+    p0: float       # packet momentum along x, a.u.
+    width: float    # Gaussian width Delta, a.u.
+    nsteps: int
+    dx: float = DX_DEFAULT
+    L: float = 4 * DX_DEFAULT
+    face: int = -1  # flux face index (the step is centred on it)
+
+    def geometry(self):
+        """(x_min, z_min, x_s, x0): the step sits on face `face` (x = 0), the packet 4 widths left of it."""
+        face = self.face if self.face >= 0 else (5 * self.side) // 8
+        x_min = -face * self.dx
+        z_min = -(self.side // 2) * self.dx
+        return x_min, z_min, 0.0, -4.0 * self.width, face
+
+    def state(self, m: float = M_E, c: float = C_AU) -> np.ndarray:
+        x_min, z_min, x_s, x0, _ = self.geometry()
+        return gaussian_packet(self.side, self.side, self.dx, x_min, z_min, x0, 0.0, self.width, self.p0, m, c)
+
+    def potential(self) -> np.ndarray:
+        x_min, _, x_s, _, _ = self.geometry()
+        return tanh_step(self.side, self.dx, x_min, x_s, self.V0, self.L)
+
+
+def klein_config_2d(seed: int = SEED, side: int = 2048, nsteps: int = 4000, m: float = M_E, c: float = C_AU) -> KleinRun:
+    """2-D Klein step, FP64 workload: 2048^2 cells, V0 = 2.5 mc^2, L = 4 dx, width 100 dx,
+    p0 ~ U[0.2, 1.0] mc drawn from numpy PCG64(seed), 4000 steps, step face at 5/8 of the x extent."""
+    rng = np.random.default_rng(seed)
+    p0 = rng.uniform(0.2, 1.0) * m * c
+    dx = DX_DEFAULT
+    return KleinRun(side=side, V0=2.5 * m * c * c, p0=p0, width=100 * dx, nsteps=nsteps, dx=dx, L=4 * dx)
+
+
+ALLOWED_SIDES = (256, 384, 512, 768, 1024)
+
+
+def klein_ensemble(nruns: int = 512, seed: int = SEED + 1, m: float = M_E, c: float = C_AU):
+    """Batched ensemble draws: side U{256..1024}, V0 ~ U[0.5, 3.0] mc^2, p0 ~ U[0.2, 1.0] mc,
+    width ~ U[40, 150] dx.  A drawn side smaller than 8 width + 16 cells is raised to the smallest
+    allowed side that holds the packet (1024 at most); the step face sits 8 widths + 8 cells from
+    the left edge, the packet 4 widths left of it; the step count is the time for the packet
+    centre to travel 8 widths at the group velocity p0 c^2 / E plus 200, clamped to [2000, 6000].
+    Returns (runs, log) where log lists every deviation from the drawn values."""
+    rng = np.random.default_rng(seed)
+    dx = DX_DEFAULT
+    runs, log = [], []
+    for r in range(nruns):
+        side = int(rng.choice(ALLOWED_SIDES))
+        V0 = rng.uniform(0.5, 3.0) * m * c * c
+        p0 = rng.uniform(0.2, 1.0) * m * c
+        w_cells = rng.uniform(40, 150)
+        need = 8 * w_cells + 16
+        if side < need:
+            bigger = [s for s in ALLOWED_SIDES if s >= need]
+            new = bigger[0] if bigger else ALLOWED_SIDES[-1]
+            log.append((r, "side", side, new))
+            side = new
+        E = np.sqrt(p0 * p0 * c * c + m * m * c ** 4)
+        vg_over_c = p0 * c / E
+        nsteps = int(np.clip(np.ceil(8 * w_cells / vg_over_c) + 200, 2000, 6000))
+        face = min(int(np.ceil(8 * w_cells)) + 8, side - 8)
+        runs.append(KleinRun(side=side, V0=V0, p0=p0, width=w_cells * dx, nsteps=nsteps, dx=dx, L=4 * dx,
+                             face=face))
+    return runs, log

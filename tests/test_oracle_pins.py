@@ -1,0 +1,298 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: explicit
+matrices built from the Pauli matrices, Fourier-space closed forms evaluated
+with numpy's FFT, the continuum free evolution, the 1-D dispersion closed form,
+the Klein closed form and an independent ODE, and exact conservation laws.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import klein
+from paper_1107_4650_gb300 import workloads as W
+from tests import dirac_algebra as A
+
+C = W.C_AU
+M = 1.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()[:2]
+            vals[k] = float(v)
+    return vals
+
+
+def _vec(psi):
+    return np.asarray(psi).reshape(-1)
+
+
+# ---------------------------------------------------------------- sweeps, brute force
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("shape,axis", [((5, 1, 4), 0), ((5, 1, 4), 2), ((3, 4, 2), 0), ((3, 4, 2), 1),
+                                        ((3, 4, 2), 2), ((4, 3, 3), 1)])
+def test_sweep_equals_explicit_matrix(oracle_mod, shape, axis, periodic):
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=11 + axis)
+    got = oracle.sweep(psi, axis, periodic)
+    want = A.sweep_matrix(shape, axis, periodic) @ _vec(psi)
+    assert np.max(np.abs(_vec(got) - want)) < 1e-15
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("ndim,shape,layout", [(2, (6, 1, 5), "x"), (2, (6, 1, 5), "full"), (3, (3, 4, 3), "full"),
+                                               (3, (4, 3, 2), "x")])
+def test_step_equals_matrix_product(oracle_mod, ndim, shape, layout, periodic):
+    """One full step = D S_z (S_y) S_x, with D from the Dirac-matrix exponential identity."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(3)
+    dx = W.DX_DEFAULT
+    dt = dx / C
+    psi = W.random_state(nz, ny, nx, seed=5)
+    if layout == "x":
+        V = rng.uniform(-3e4, 3e4, nx)
+        Vcell = np.tile(V, ny * nz)
+    else:
+        V = rng.uniform(-3e4, 3e4, nx * ny * nz)
+        Vcell = V
+    got, _ = oracle.step(psi, ndim, M, C, dx, 1, V=V, periodic=periodic)
+    Mx = A.sweep_matrix(shape, 0, periodic)
+    Mz = A.sweep_matrix(shape, 2, periodic)
+    step = Mz @ (A.sweep_matrix(shape, 1, periodic) @ Mx if ndim == 3 else Mx)
+    D = A.phase_matrix(shape, M, C, dt, Vcell)
+    want = D @ step @ _vec(psi)
+    assert np.max(np.abs(_vec(got) - want)) < 5e-15
+
+
+def test_phase_is_paper_U_matrix_at_zero_field(oracle_mod):
+    """At A = 0 the U matrix of Sec. 2.3 is diag(c - i s, c - i s, c + i s, c + i s) with argument m c^2 dt."""
+    dt = W.DX_DEFAULT / C
+    mu = M * C * C * dt
+    psi = W.random_state(1, 1, 1, seed=9)
+    got = oracle.phase(psi, M, C, dt)
+    U = np.diag([np.cos(mu) - 1j * np.sin(mu)] * 2 + [np.cos(mu) + 1j * np.sin(mu)] * 2)
+    assert np.max(np.abs(_vec(got) - U @ _vec(psi))) < 1e-16
+
+
+# ---------------------------------------------------------------- Fourier statements
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_periodic_sweep_is_exact_exponential_in_fourier_space(oracle_mod, axis):
+    """Eq. sol_dis: the DFT of one sweep is e^{-i alpha_d 2 pi k / N_d}, exactly."""
+    nx, nz = 16, 12
+    psi = W.random_state(nz, 1, nx, seed=21)
+    out = oracle.sweep(psi, axis, periodic=True)
+    hat_in = np.fft.fft2(psi[:, 0], axes=(0, 1))
+    hat_out = np.fft.fft2(out[:, 0], axes=(0, 1))
+    KX, KZ = np.meshgrid(np.arange(nx), np.arange(nz))
+    th = 2 * np.pi * (KX / nx if axis == 0 else KZ / nz)
+    U = np.cos(th)[..., None, None] * A.I4 - 1j * np.sin(th)[..., None, None] * A.ALPHA[axis]
+    want = np.einsum("zxab,zxb->zxa", U, hat_in)
+    assert A.rel_l2(hat_out, want) < 1e-14
+
+
+def test_config1_dft_exact_discrete_evolution(oracle_mod):
+    """Free 256^2 positive-energy packet, width 20 dx, p0 = 0.5 mc, 200 periodic steps: the oracle equals
+    the mode-by-mode product of one-step amplification matrices (Sec. 3.2) to round-off."""
+    n, dx = 256, W.DX_DEFAULT
+    psi0 = W.positive_energy_packet_2d(n, n, dx, 20 * dx, 0.5 * M * C)
+    got, _ = oracle.step(psi0, 2, M, C, dx, 200, periodic=True)
+    want = A.dft_exact_evolution_2d(psi0, 200, M * C * C * dx / C)
+    assert A.rel_l2(got, want) < 1e-12
+
+
+def test_first_order_convergence_to_continuum(oracle_mod):
+    """Lie splitting is first order (Sec. 2.1): at fixed physical time, halving dx (and so dt) halves
+    the error against the exact free evolution e^{-i(c alpha.p + beta mc^2) t} (App. B)."""
+    box = 64 * 4 * W.DX_DEFAULT
+    errs = []
+    for n in (64, 128, 256):
+        dx = box / n
+        nsteps = n // 2
+        t = nsteps * dx / C
+        psi0 = W.positive_energy_packet_2d(n, n, dx, box / 10, 0.5 * M * C)
+        got, _ = oracle.step(psi0, 2, M, C, dx, nsteps, periodic=True)
+        want = A.continuum_evolution_2d(psi0, dx, t, M, C)
+        errs.append(A.rel_l2(got, want))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.7 < r1 < 2.3 and 1.7 < r2 < 2.3, errs
+
+
+# ---------------------------------------------------------------- dispersion: no doubling
+
+def _amplification_from_oracle(nx, nz, kx, kz, mu_dx):
+    """4x4 one-step matrix of mode (kx, kz) read off the oracle by stepping plane waves."""
+    dx = mu_dx
+    x = np.arange(nx)
+    z = np.arange(nz)
+    wave = np.exp(2j * np.pi * (kz * z[:, None] / nz + kx * x[None, :] / nx))
+    U = np.zeros((4, 4), np.complex128)
+    for col in range(4):
+        psi = np.zeros((nz, 1, nx, 4), np.complex128)
+        psi[:, 0, :, col] = wave
+        out, _ = oracle.step(psi, 2, M, C, dx, 1, periodic=True)
+        U[:, col] = out[0, 0, 0, :] / wave[0, 0]
+    return U
+
+
+def test_no_fermion_doubling_1d_dispersion(oracle_mod):
+    """Plane waves along x (nz = 1, periodic: the z sweep is the identity).  The eigenphases of the
+    one-step matrix obey cos(E dt) = cos(mu) cos(k dx) exactly (Sec. 3.1 with the mass phase), so E(k)
+    rises monotonically from k = 0 to the zone edge with a single minimum at k = 0.  A central
+    difference instead gives E ~ sin(k dx)/dx, which returns to its k = 0 value at the zone edge."""
+    nx = 64
+    dx = W.DX_DEFAULT
+    dt = dx / C
+    mu = M * C * C * dt
+    Es = []
+    for k in range(0, nx // 2 + 1):
+        U = _amplification_from_oracle(nx, 1, k, 0, dx)
+        lam = np.linalg.eigvals(U)
+        assert np.allclose(np.abs(lam), 1.0, atol=1e-14)
+        cosE = np.cos(mu) * np.cos(2 * np.pi * k / nx)
+        assert np.allclose(np.sort(lam.real), np.sort([cosE] * 4), atol=1e-14)
+        Es.append(np.max(np.abs(np.angle(lam))) / dt)
+    Es = np.array(Es)
+    assert np.all(np.diff(Es) > 0)
+    assert np.argmin(Es) == 0
+    kk = 2 * np.pi * np.arange(0, nx // 2 + 1) / (nx * dx)
+    naive = np.sqrt((C * np.sin(kk * dx) / dx) ** 2 + (M * C * C) ** 2)
+    assert abs(naive[-1] - naive[0]) < 1e-6 * naive[0]  # the doubler at the zone edge
+    assert Es[-1] > 10 * Es[0]
+
+
+def test_trace_identity_2d(oracle_mod):
+    """1/4 Re tr U(k) = cos(mu) cos(th_x) cos(th_z) for the 2-D one-step matrix (split product of Sec. 3.2)."""
+    nx, nz = 8, 6
+    dx = W.DX_DEFAULT
+    mu = M * C * C * dx / C
+    for kx, kz in [(0, 0), (1, 2), (3, 1), (4, 3), (7, 5)]:
+        U = _amplification_from_oracle(nx, nz, kx, kz, dx)
+        want = np.cos(mu) * np.cos(2 * np.pi * kx / nx) * np.cos(2 * np.pi * kz / nz)
+        assert abs(np.trace(U).real / 4 - want) < 1e-14
+
+
+# ---------------------------------------------------------------- conservation and flux
+
+@pytest.mark.parametrize("ndim,shape", [(2, (24, 1, 20)), (3, (10, 8, 6))])
+def test_unitarity_periodic(oracle_mod, ndim, shape):
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=2)
+    V = np.random.default_rng(4).uniform(-5e4, 5e4, nx * ny * nz)
+    n0 = oracle.observables(psi, ndim, 1.0)["norm"]
+    out, _ = oracle.step(psi, ndim, M, C, W.DX_DEFAULT, 50, V=V, periodic=True)
+    n1 = oracle.observables(out, ndim, 1.0)["norm"]
+    assert abs(n1 - n0) / n0 < 50 * 4e-16
+
+
+def test_zero_boundary_norm_loss_equals_outflow(oracle_mod):
+    """ZERO boundary: a state touching the edge loses exactly the characteristic density that leaves."""
+    nx, nz = 12, 10
+    psi = W.random_state(nz, 1, nx, seed=8)
+    n0 = oracle.observables(psi, 2, 1.0)["norm"]
+    # outflow of the x sweep: right movers at i = nx-1, left movers at i = 0
+    q = psi[:, 0]
+    out_x = 0.5 * (np.abs(q[:, -1, 0] + q[:, -1, 3]) ** 2 + np.abs(q[:, -1, 1] + q[:, -1, 2]) ** 2).sum() \
+        + 0.5 * (np.abs(q[:, 0, 0] - q[:, 0, 3]) ** 2 + np.abs(q[:, 0, 1] - q[:, 0, 2]) ** 2).sum()
+    mid = oracle.sweep(psi, 0, periodic=False)
+    assert abs(oracle.observables(mid, 2, 1.0)["norm"] - (n0 - out_x)) < 1e-14
+    r = mid[:, 0]
+    # z sweep characteristics: (psi1+psi3, psi2-psi4) move +z, (psi1-psi3, psi2+psi4) move -z
+    out_z = 0.5 * (np.abs(r[-1, :, 0] + r[-1, :, 2]) ** 2 + np.abs(r[-1, :, 1] - r[-1, :, 3]) ** 2).sum() \
+        + 0.5 * (np.abs(r[0, :, 0] - r[0, :, 2]) ** 2 + np.abs(r[0, :, 1] + r[0, :, 3]) ** 2).sum()
+    end = oracle.sweep(mid, 2, periodic=False)
+    assert abs(oracle.observables(end, 2, 1.0)["norm"] - (n0 - out_x - out_z)) < 1e-14
+
+
+def test_flux_identity_klein(oracle_mod):
+    """Sum_{i >= face} rho(n) - Sum_{i >= face} rho(0) = cumulative face flux, exactly, while nothing
+    reaches the domain edge (the z sweep and the phase move no probability across an x face)."""
+    run = W.KleinRun(side=320, V0=2.5 * C * C, p0=0.7 * C, width=8 * W.DX_DEFAULT, nsteps=80,
+                     face=180)
+    psi0 = run.state()
+    V = run.potential()
+    x_min, z_min, _, _, face = run.geometry()
+    dx = run.dx
+    o0 = oracle.observables(psi0, 2, dx, (x_min, 0.0, z_min), face)
+    out, F = oracle.step(psi0, 2, M, C, dx, run.nsteps, V=V, flux_face=face)
+    o1 = oracle.observables(out, 2, dx, (x_min, 0.0, z_min), face)
+    assert F > 1e-3
+    assert abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
+    assert abs(o1["norm"] - o0["norm"]) < 1e-12  # nothing has reached the boundary yet
+
+
+def test_observables_invariants(oracle_mod):
+    """Normalised state has norm 1; a packet symmetric about its centre has that centroid; a state
+    entirely right of the face has norm_right = norm."""
+    n, dx = 64, W.DX_DEFAULT
+    x_min, z_min = -32 * dx, -32 * dx
+    psi = W.gaussian_packet(n, n, dx, x_min, z_min, 3 * dx, -5 * dx, 3 * dx, 0.0)
+    o = oracle.observables(psi, 2, dx, (x_min, 0.0, z_min), flux_face=0)
+    assert abs(o["norm"] - 1.0) < 1e-13
+    assert abs(o["centroid"][0] - 3 * dx) < 1e-9 * dx and abs(o["centroid"][2] + 5 * dx) < 1e-9 * dx
+    assert o["norm_right"] == o["norm"]
+
+
+# ---------------------------------------------------------------- Klein closed form
+
+def test_klein_worked_example_matches_printed_values():
+    g = _read_golden("klein_worked_examples.txt")
+    V0 = g["V0_2d_mc2_multiple"] * M * C * C + g["V0_2d_offset"]
+    T = klein.transmission_closed_form(g["k0_2d"], V0, g["L_2d"])
+    unit = 10.0 ** -int(g["digits_2d"])
+    assert abs(T - g["T_2d_analytic"]) <= 0.5 * unit
+    # R = 1 - T = 0.737906 is printed as 0.7380: within one unit of the last printed digit
+    assert abs((1 - T) - g["R_2d_analytic"]) <= 1.0 * unit
+    # 1-D: null transmission below the printed threshold
+    assert klein.transmission_closed_form(g["k0_1d"], g["V0_1d_null_below"], g["L_1d"]) == 0.0
+
+
+@pytest.mark.parametrize("p_over_mc,V0_over_mc2", [(0.2, 2.5), (0.5, 2.5), (1.0, 2.5), (0.6, 3.0), (0.9, 2.6)])
+def test_klein_closed_form_against_ode(p_over_mc, V0_over_mc2):
+    """Eq. trans_co against RK4 integration of the stationary Dirac equation across the tanh step;
+    T + R = 1 from current conservation."""
+    k0, V0, L = p_over_mc * C, V0_over_mc2 * C * C, 4 * W.DX_DEFAULT
+    T_cf = klein.transmission_closed_form(k0, V0, L)
+    T, R = klein.transmission_ode(k0, V0, L, nstep=8000)
+    assert abs(T_cf - T) < 1e-9
+    assert abs(T + R - 1.0) < 1e-9
+
+
+def test_klein_sharp_step_limit():
+    k0, V0 = 100.0, 2 * C * C + 1e4
+    T_sharp = klein.transmission_sharp_step(k0, V0)
+    T_cf_small_L = klein.transmission_closed_form(k0, V0, 1e-8)
+    T_ode, _ = klein.transmission_ode(k0, V0, 1e-8, half_width=1e-6, nstep=2000)
+    assert abs(T_sharp - T_cf_small_L) < 1e-6
+    assert abs(T_sharp - T_ode) < 1e-6
+
+
+def test_oracle_klein_run_converges_to_closed_form():
+    """A z-uniform Klein run (nz = 1, periodic: the 1-D reduction of Sec. 2.4), T = cumulative face
+    flux / initial norm, converges to the packet-averaged Eq. trans_co as the mesh is refined at fixed
+    physical step width, packet and time (Sec. 5.2.1 reports < 0.5% at its finest mesh)."""
+    dx0 = W.DX_DEFAULT
+    p0, width, L, V0 = 0.5 * C, 100 * dx0, 4 * dx0, 2.5 * C * C
+    T_cf = klein.packet_averaged_transmission(p0, width, V0, L)
+    E = np.sqrt(p0 ** 2 * C ** 2 + C ** 4)
+    errs = []
+    for f in (1, 2):
+        dx = dx0 / f
+        nx, face = 4096 * f, 1280 * f
+        x_min = -face * dx
+        psi = W.gaussian_packet(nx, 1, dx, x_min, 0.0, -4 * width, 0.0, width, p0)
+        V = W.tanh_step(nx, dx, x_min, 0.0, V0, L)
+        nsteps = int(f * (8 * 100 / (p0 * C / E) + 200))
+        out, F = oracle.step(psi, 2, M, C, dx, nsteps, V=V, periodic=True, flux_face=face)
+        errs.append(abs(F / oracle.observables(psi, 2, dx)["norm"] - T_cf) / T_cf)
+    assert errs[1] < 0.01 and errs[0] / errs[1] > 3.0, errs
