@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the split-operator Dirac stepper on one GB300.
+
+Workload (one bench step): the 2-D Klein-step scattering run, FP64 state, 2048 x 2048 cells of
+dx = 10/8192 a.u., tanh step V0 = 2.5 m c^2, L = 4 dx on the face at 5/8 of the x extent, Gaussian
+[1,0,0,C] packet of width 100 dx with p0 drawn from U[0.2, 1.0] m c (numpy PCG64, seed 20111107),
+4000 time steps with the transmitted flux accumulated every step.  The metric is 4-spinor
+grid-point-steps per second (cells x time steps / s).
+
+  value      device-resident inputs: each bench step re-seeds the state from a device copy and
+             runs dirac_step(4000); timed with CUDA events on the grid's stream.
+  e2e        the same through the C ABI with host buffers: pinned host state -> device, potential
+             from host, 4000 steps, observables (norm, flux) read back to the host.
+  roofline   the step kernel: algorithmic bytes per launch (128 B per FP64 point-step: the state
+             read and written once) / its mean launch time; FP64 arithmetic (56 flops per 2-D
+             point-step) against the FP64 rate.
+  cpu_baseline  the FP64 CPU oracle on this host's cores, on a bounded sample of the same run.
+
+With --gpus N > 1 (torchrun), every rank runs an independent replica (the path is one grid and is
+not sharded); value = all ranks' point-steps / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_BYTES_PER_POINT_STEP = 128  # 2-D, x-only table: 64 B read + 64 B written
+FP32_BYTES_PER_POINT_STEP = 64
+FLOPS_PER_POINT_STEP_2D = 56    # 32 adds (two sweeps) + 4 complex products of 6 flops
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel on this workload
+# (profiles/step_kernel_fp64_klein2048.md); None until captured for the kernel as it stands.
+MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": None, "fp32": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=2048)
+    ap.add_argument("--nsteps", type=int, default=4000, help="time steps per bench step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(run, seconds: float):
+    """The FP64 CPU oracle, as it stands, on this host's cores: chunks of 25 steps of the same Klein run on a
+    1024^2 crop until `seconds` of wall time; returns (point-steps/s, threads, description)."""
+    ncores = os.cpu_count() or 1
+    os.environ["OMP_NUM_THREADS"] = str(ncores)
+    import oracle
+    from paper_1107_4650_gb300 import workloads as W
+    oracle.build()
+    side = 1024
+    crop = W.KleinRun(side=side, V0=run.V0, p0=run.p0, width=run.width / 2, nsteps=run.nsteps, dx=run.dx, L=run.L)
+    psi = crop.state()
+    V = crop.potential()
+    _, _, _, _, face = crop.geometry()
+    done = 0
+    F = 0.0
+    t0 = time.perf_counter()
+    while True:
+        psi, F = oracle.step(psi, 2, 1.0, W.C_AU, crop.dx, 25, V=V, flux_face=face, flux_cum=F)
+        done += 25
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    rate = side * side * done / dt
+    desc = ("FP64 CPU oracle, %d OpenMP threads, %dx%d crop of the Klein run (width 50 dx), %d time steps in %.1f s"
+            % (ncores, side, side, done, dt))
+    return rate, ncores, desc
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1107_4650_gb300 import workloads as W
+    run = W.klein_config_2d(side=args.side, nsteps=args.nsteps)
+    per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(run, 1.0)
+    vals = []
+    cores, desc = None, ""
+    for _ in range(args.steps):
+        v, cores, desc = cpu_baseline(run, per)
+        vals.append(v)
+    value = float(np.mean(vals))
+    ms = args.side * args.side * args.nsteps / value * 1e3
+    line = {"impl": "reference", "metric": "4-spinor grid-point-steps/s", "value": value, "unit": "point-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2-D Klein step FP64 %dx%d, %d time steps per bench step (CPU oracle on a "
+                                   "bounded 1024^2 crop, rate per point-step)" % (args.side, args.side, args.nsteps)},
+            "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+    import paper_1107_4650_gb300 as D
+    from paper_1107_4650_gb300 import build as B
+    from paper_1107_4650_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if world > 1:
+        dist.barrier()
+    D.load_library()
+
+    run = W.klein_config_2d(side=args.side, nsteps=args.nsteps)
+    x_min, z_min, _, _, face = run.geometry()
+    psi0 = run.state()
+    V = run.potential()
+    ncell = args.side * args.side
+    stream = torch.cuda.Stream()
+
+    def make_grid(precision):
+        cfg = D.make_config((args.side, 1, args.side), x_min=(x_min, 0.0, z_min), flux_face=face,
+                            stream=stream.cuda_stream, device=local, precision=precision)
+        h = D.dirac_create_grid(cfg)
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        return h
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed_device_run(h, dev_state, steps, warmup):
+        """(total ms, ms inside dirac_step only, step-kernel launches in the timed region)."""
+        for _ in range(warmup):
+            D.dirac_set_state(h, dev_state)
+            D.dirac_step(h, args.nsteps)
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        l0 = D.dirac_get_info(h)["kernel_launches"]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_all0.record(stream)
+        for i in range(steps):
+            D.dirac_set_state(h, dev_state)
+            ev[i][0].record(stream)
+            D.dirac_step(h, args.nsteps)
+            ev[i][1].record(stream)
+        e_all1.record(stream)
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        total = e_all0.elapsed_time(e_all1)
+        inner = sum(a.elapsed_time(b) for a, b in ev)
+        launches = D.dirac_get_info(h)["kernel_launches"] - l0
+        return total, inner, launches
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------------------------------------------------------- FP64, device-resident
+    h = make_grid(D.DIRAC_FP64)
+    dev_state = torch.from_numpy(psi0.view(np.float64)).to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    D.dirac_set_state(h, dev_state)
+    D.dirac_autotune(h)
+    info = D.dirac_get_info(h)
+    with ClockSampler(local) as clk:
+        total_ms, inner_ms, launches = timed_device_run(h, dev_state, args.steps, args.warmup)
+    clocks = clk.summary()
+    obs = D.dirac_observables(h)
+    n0 = float(np.sum(np.abs(psi0) ** 2) * run.dx ** 2)
+    total_ms = max_over_ranks(total_ms)
+    point_steps = ncell * args.nsteps * args.steps * world
+    value = point_steps / (total_ms / 1e3)
+    step_launches = args.steps * (args.nsteps // info["steps_per_launch"] + args.nsteps % info["steps_per_launch"])
+    mean_launch_s = inner_ms / 1e3 / max(1, step_launches)
+    k_launch = info["steps_per_launch"]
+    alg_bytes = FP64_BYTES_PER_POINT_STEP * ncell * k_launch
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved_gbs = alg_bytes / mean_launch_s / 1e9
+    fp64_tflops = FLOPS_PER_POINT_STEP_2D * ncell * k_launch / mean_launch_s / 1e12
+    FP64_NOMINAL_TFLOPS = 1.25
+    traffic = MEASURED_TRAFFIC_PER_LAUNCH["fp64"]
+    roofline = {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": fp64_tflops / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+                "peak_source": "nominal FP64 rate of the recipe (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "kernel": "dirac::sweep_kernel<double,%d,%d,0>" % (k_launch, info["points_per_lane"]),
+                "mean_launch_ms": mean_launch_s * 1e3,
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                        "peak_source": hbm_src, "algorithmic_bytes_per_launch": alg_bytes}}
+
+    # ---------------------------------------------------------------- e2e through host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_state = torch.from_numpy(psi0.view(np.float64)).pin_memory()
+        def e2e_step():
+            D.dirac_set_state(h, host_state)
+            D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+            D.dirac_step(h, args.nsteps)
+            return D.dirac_observables(h)
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = e2e_step()
+        stream.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": point_steps / e2e_s, "unit": "point-steps/s",
+               "h2d_bytes_per_step": int(psi0.nbytes + V.nbytes), "d2h_bytes_per_step": 6 * 8,
+               "result": {"T": r["flux_cum"] / n0, "norm": r["norm"]}}
+    D.dirac_destroy(h)
+
+    # ---------------------------------------------------------------- FP32 storage variant
+    variants = {}
+    if not args.no_fp32:
+        h32 = make_grid(D.DIRAC_FP32)
+        dev32 = torch.from_numpy(psi0.astype(np.complex64).view(np.float32)).to(f"cuda:{local}")
+        torch.cuda.synchronize()
+        D.dirac_set_state(h32, dev32)
+        D.dirac_autotune(h32)
+        i32 = D.dirac_get_info(h32)
+        t32, in32, _ = timed_device_run(h32, dev32, args.steps, 1)
+        o32 = D.dirac_observables(h32)
+        t32 = max_over_ranks(t32)
+        k32 = i32["steps_per_launch"]
+        launches32 = args.steps * (args.nsteps // k32 + args.nsteps % k32)
+        mean32 = in32 / 1e3 / max(1, launches32)
+        v32 = point_steps / (t32 / 1e3)
+        eff = FP32_BYTES_PER_POINT_STEP * v32 / world / 1e9
+        variants["fp32"] = {"value": v32, "unit": "point-steps/s", "ms_per_step": t32 / args.steps,
+                            "steps_per_launch": k32, "points_per_lane": i32["points_per_lane"],
+                            "effective_hbm_frac": eff / hbm_peak,
+                            "step_kernel_algorithmic_gbs": FP32_BYTES_PER_POINT_STEP * ncell * k32 / mean32 / 1e9,
+                            "T": o32["flux_cum"] / n0, "T_fp64": obs["flux_cum"] / n0}
+        D.dirac_destroy(h32)
+
+    # ---------------------------------------------------------------- CPU baseline (rank 0)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, desc = cpu_baseline(run, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "point-steps/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": "4-spinor grid-point-steps/s", "value": value, "unit": "point-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "2-D Klein step, FP64, %dx%d cells, %d time steps per bench step, V0=2.5 mc^2, "
+                                       "L=4 dx, width 100 dx, p0=%.4f mc, flux face %d"
+                                       % (args.side, args.side, args.nsteps, run.p0 / W.C_AU, face),
+                           "point_steps_per_bench_step": ncell * args.nsteps,
+                           "l2": "inputs larger than L2: two 268 MB state buffers ping-pong",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "steps_per_launch": k_launch, "points_per_lane": info["points_per_lane"]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks, "variants": variants,
+                "physics": {"T_flux": obs["flux_cum"] / n0, "norm_end": obs["norm"], "norm_start": n0}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

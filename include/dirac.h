@@ -1,0 +1,152 @@
+/*
+ * dirac.h - C ABI of libdirac, a GB300 (sm_103a) implementation of the
+ * split-operator / method-of-characteristics scheme for the time-dependent
+ * Dirac equation of Fillion-Gourdeau, Lorin and Bandrauk (arXiv:1107.4650).
+ *
+ * One time step (first-order splitting, Sec. 2.1, Eqs. split1-split4, in the
+ * discrete form of Sec. 2.3, Eqs. sol_dis_1-sol_dis_4, with c dt = dx, K = 1):
+ *   x sweep   psi <- 1/2 {(I + alpha_x) psi(i-1) + (I - alpha_x) psi(i+1)}
+ *   y sweep   (3-D only, Eq. sol_dis_2)
+ *   z sweep   (Eq. sol_dis_3)
+ *   phase     psi <- exp(-i beta m c^2 dt - i V dt) psi   (Eq. sol_dis_4, A = 0)
+ * "2-D" is the x-z plane (Sec. 2.4).  Units are the caller's (atomic units in
+ * the paper: m = 1, c = 137.0359895).
+ *
+ * Conventions for every call:
+ *   - every call returns a dirac_status; nothing is thrown and nothing exits;
+ *   - on an error the message is kept in the grid (dirac_last_error) when a
+ *     grid exists, otherwise in a thread-local buffer (dirac_last_error(NULL));
+ *   - host buffers passed in are copied before the call returns; device buffers
+ *     passed in are read or written on the grid's stream;
+ *   - a grid is used by one host thread at a time;
+ *   - the state is stored point-major, psi[z][y][x][c][re,im], c = 0..3 the four
+ *     spinor components in the Dirac representation (Eq. dirac_mat): 64 bytes a
+ *     cell in FP64 storage, 32 bytes in FP32 storage.
+ */
+#ifndef DIRAC_H
+#define DIRAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dirac_grid dirac_grid; /* opaque, library-owned */
+
+typedef enum {
+    DIRAC_OK = 0,
+    DIRAC_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, bad enum) */
+    DIRAC_ERR_OOM = 2,       /* device or host allocation failed */
+    DIRAC_ERR_CUDA = 3,      /* a CUDA runtime call failed; see dirac_last_error */
+    DIRAC_ERR_NONFINITE = 4, /* the state holds NaN or Inf (reported by dirac_observables) */
+    DIRAC_ERR_TIMEOUT = 5,   /* a bounded device wait ran out */
+    DIRAC_ERR_STATE = 6      /* call not valid in the grid's current state */
+} dirac_status;
+
+enum { DIRAC_FP64 = 0, DIRAC_FP32 = 1 };              /* storage precision */
+enum { DIRAC_BC_ZERO = 0, DIRAC_BC_PERIODIC = 1 };    /* boundary */
+enum { DIRAC_V_NONE = 0, DIRAC_V_X_ONLY = 1, DIRAC_V_FULL = 2 }; /* potential layout */
+
+typedef struct {
+    int ndim;             /* 2 (x-z plane, n[1] must be 1) or 3 */
+    int64_t n[3];         /* cells along x, y, z */
+    double dx;            /* cell edge a; the time step is dt = dx / c (c dt = a, Sec. 2.3) */
+    double c;             /* speed of light */
+    double m;             /* particle mass */
+    double x_min[3];      /* lower corner: cell (i,j,k) has centre x_min + (i+1/2) dx (Sec. 2.3) */
+    int precision;        /* DIRAC_FP64 or DIRAC_FP32 storage of the state */
+    int boundary;         /* DIRAC_BC_ZERO: cells outside the grid are zero at every sub-step
+                             (Dirichlet condition of Sec. 5); DIRAC_BC_PERIODIC: wrap */
+    int64_t flux_face;    /* x face index i_s in [1, nx-1] whose crossing probability is accumulated
+                             every step (between cells i_s-1 and i_s), or -1 for none */
+    void *stream;         /* cudaStream_t the grid's work is enqueued on (NULL = legacy stream) */
+    int device;           /* CUDA device ordinal */
+    int steps_per_launch; /* steps fused in one 2-D kernel launch (temporal block depth): 1 or 2 for FP64,
+                             1, 2 or 4 for FP32; 0 = library choice (3-D always runs 1) */
+    int use_graphs;       /* 1: replay dirac_step's steady-state launches from a captured CUDA graph */
+    int points_per_lane;  /* x cells per lane of the step kernel: 1, 2 or 4 (K = 2 needs 2 in FP64);
+                             0 = library choice */
+} dirac_config;
+
+/* Fills cfg with defaults: ndim 2, n = {256,1,256}, dx = 10/8192, c = 137.0359895, m = 1,
+ * x_min centred, FP64, zero boundary, no flux face, legacy stream, device 0, library k, graphs on. */
+void dirac_default_config(dirac_config *cfg);
+
+/* Creates a grid: validates cfg, allocates two state buffers (ping-pong), the phase table and
+ * scratch on cfg->device, zero state, V = 0.  Errors: DIRAC_ERR_ARG for an invalid config,
+ * DIRAC_ERR_OOM when allocation fails (nothing is leaked), DIRAC_ERR_CUDA otherwise.
+ * The grid owns all its device memory; free it with dirac_destroy. */
+dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out);
+
+/* Releases every resource of the grid (waits for its stream first).  NULL is accepted. */
+dirac_status dirac_destroy(dirac_grid *g);
+
+/* Static scalar potential energy V (so that V~ = V dt in Eq. field_dis2), host pointer, copied.
+ * layout DIRAC_V_NONE (V ignored, V = 0), DIRAC_V_X_ONLY (count = nx values, V depends on x only)
+ * or DIRAC_V_FULL (count = nx*ny*nz values in [z][y][x] order).  The phase coefficients
+ * exp(-i (+-m c^2 dt + V dt)) (Eq. sol_dis_4 at A = 0) are formed in FP64 on the host and copied to
+ * the device.  Errors: DIRAC_ERR_ARG on a bad layout/count/null V. */
+dirac_status dirac_set_potential(dirac_grid *g, const double *V, int layout, int64_t count);
+
+/* Copies a state in (layout above, storage precision of the grid; complex128 or complex64 per
+ * component).  on_device != 0: psi is a device pointer on the grid's device, read on the grid's
+ * stream.  Resets the step counter and the cumulative flux to 0. */
+dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device);
+
+/* Copies the current state out (same layout).  Host copies are complete when the call returns;
+ * device copies are ordered on the grid's stream. */
+dirac_status dirac_get_state(dirac_grid *g, void *psi, int on_device);
+
+/* Device pointer of the current state buffer (valid until the next dirac_step / dirac_destroy). */
+dirac_status dirac_state_ptr(dirac_grid *g, void **dev_ptr);
+
+/* Advances nsteps >= 0 time steps (asynchronous on the grid's stream): x sweep, (y sweep), z sweep,
+ * phase per step, fused into kernels that each run steps_per_launch steps. */
+dirac_status dirac_step(dirac_grid *g, int64_t nsteps);
+
+typedef struct {
+    double norm;        /* sum rho dx^d, rho = sum_c |psi_c|^2 */
+    double norm_right;  /* the same over cells with i >= flux_face (0 without a face) */
+    double flux_cum;    /* probability carried across flux_face since the last set_state */
+    double centroid[3]; /* sum x rho / sum rho per axis */
+    int64_t step;       /* steps taken since the last set_state */
+} dirac_obs;
+
+/* Reductions of the current state (Sec. 5.2.1: R and T are integrals of |psi|^2), accumulated in
+ * FP64, deterministic.  density (nullable) receives rho per cell in FP64, [z][y][x], on the device
+ * when density_on_device != 0, else on the host.  Synchronises the grid's stream.
+ * Returns DIRAC_ERR_NONFINITE (obs still filled) when the norm is NaN or Inf. */
+dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, int density_on_device);
+
+/* Checkpoint support: sets the step counter and cumulative flux (after dirac_set_state). */
+dirac_status dirac_set_counters(dirac_grid *g, int64_t step, double flux_cum);
+
+typedef struct {
+    int steps_per_launch;   /* temporal block depth k in use */
+    int points_per_lane;    /* x cells per lane in the step kernel */
+    int64_t launch_warps;   /* warps in one step launch */
+    int64_t strip_width;    /* x cells written by one warp */
+    int64_t segment_rows;   /* rows written by one warp */
+    int graphs;             /* 1 when dirac_step replays a CUDA graph */
+    int64_t kernel_launches;/* kernels enqueued by this grid so far (all kinds) */
+    size_t device_bytes;    /* device memory owned by the grid */
+} dirac_info;
+
+dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info);
+
+/* Chooses steps_per_launch and points_per_lane by timing candidate launches on this grid (the state
+ * is saved and restored around the trial).  Synchronises.  The choice holds until destroy. */
+dirac_status dirac_autotune(dirac_grid *g);
+
+/* Last error message for g (or of this thread when g == NULL). Never NULL. */
+const char *dirac_last_error(const dirac_grid *g);
+
+/* Library version string. */
+const char *dirac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIRAC_H */

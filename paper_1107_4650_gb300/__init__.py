@@ -1,1 +1,215 @@
-"""GB300-native split-operator Dirac stepper (placeholder; binding added with the library)."""
+"""GB300 (sm_103a) split-operator Dirac stepper: Python binding of libdirac.
+
+Thin ctypes binding of the C ABI in include/dirac.h, with the same function names.  It only
+marshals arguments: numpy arrays are passed as host pointers, torch CUDA tensors as device
+pointers, and every step of the scheme runs in libdirac's CUDA kernels.  There is no CPU
+fallback: when libdirac.so is missing or fails to load, every call raises.
+
+Build the library with ``python -m paper_1107_4650_gb300.build`` (or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdirac.so")
+
+DIRAC_OK, DIRAC_ERR_ARG, DIRAC_ERR_OOM, DIRAC_ERR_CUDA, DIRAC_ERR_NONFINITE, DIRAC_ERR_TIMEOUT, DIRAC_ERR_STATE = range(7)
+DIRAC_FP64, DIRAC_FP32 = 0, 1
+DIRAC_BC_ZERO, DIRAC_BC_PERIODIC = 0, 1
+DIRAC_V_NONE, DIRAC_V_X_ONLY, DIRAC_V_FULL = 0, 1, 2
+
+STATUS_NAMES = {0: "DIRAC_OK", 1: "DIRAC_ERR_ARG", 2: "DIRAC_ERR_OOM", 3: "DIRAC_ERR_CUDA",
+                4: "DIRAC_ERR_NONFINITE", 5: "DIRAC_ERR_TIMEOUT", 6: "DIRAC_ERR_STATE"}
+
+
+class DiracError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class dirac_config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double),
+                ("c", ctypes.c_double), ("m", ctypes.c_double), ("x_min", ctypes.c_double * 3),
+                ("precision", ctypes.c_int), ("boundary", ctypes.c_int), ("flux_face", ctypes.c_int64),
+                ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("points_per_lane", ctypes.c_int)]
+
+
+class dirac_obs(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_double), ("norm_right", ctypes.c_double), ("flux_cum", ctypes.c_double),
+                ("centroid", ctypes.c_double * 3), ("step", ctypes.c_int64)]
+
+
+class dirac_info(ctypes.Structure):
+    _fields_ = [("steps_per_launch", ctypes.c_int), ("points_per_lane", ctypes.c_int),
+                ("launch_warps", ctypes.c_int64), ("strip_width", ctypes.c_int64),
+                ("segment_rows", ctypes.c_int64), ("graphs", ctypes.c_int),
+                ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libdirac.so; raises RuntimeError if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdirac.so not found at %s: build it first (paper_1107_4650_gb300.build)" % path)
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "dirac_default_config": (None, [ctypes.POINTER(dirac_config)]),
+        "dirac_create_grid": (I, [ctypes.POINTER(dirac_config), ctypes.POINTER(P)]),
+        "dirac_destroy": (I, [P]),
+        "dirac_set_potential": (I, [P, P, I, I64]),
+        "dirac_set_state": (I, [P, P, I]),
+        "dirac_get_state": (I, [P, P, I]),
+        "dirac_state_ptr": (I, [P, ctypes.POINTER(P)]),
+        "dirac_step": (I, [P, I64]),
+        "dirac_observables": (I, [P, ctypes.POINTER(dirac_obs), P, I]),
+        "dirac_set_counters": (I, [P, I64, D]),
+        "dirac_get_info": (I, [P, ctypes.POINTER(dirac_info)]),
+        "dirac_autotune": (I, [P]),
+        "dirac_last_error": (ctypes.c_char_p, [P]),
+        "dirac_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, handle=None):
+    if st != DIRAC_OK:
+        msg = load_library().dirac_last_error(handle)
+        raise DiracError(st, msg.decode() if msg else "")
+
+
+def _ptr(buf, want_elem_bytes: int):
+    """(pointer, on_device) for a numpy array or a torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return buf.ctypes.data, 0
+    if hasattr(buf, "data_ptr") and hasattr(buf, "is_cuda"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr(), 1 if buf.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def dirac_version() -> str:
+    return load_library().dirac_version().decode()
+
+
+def dirac_default_config() -> dirac_config:
+    cfg = dirac_config()
+    load_library().dirac_default_config(ctypes.byref(cfg))
+    return cfg
+
+
+def dirac_create_grid(cfg: dirac_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().dirac_create_grid(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def dirac_destroy(h) -> None:
+    _check(load_library().dirac_destroy(h))
+
+
+def dirac_set_potential(h, V, layout: int) -> None:
+    if layout == DIRAC_V_NONE:
+        _check(load_library().dirac_set_potential(h, None, layout, 0), h)
+        return
+    V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
+    _check(load_library().dirac_set_potential(h, V.ctypes.data, layout, V.size), h)
+
+
+def dirac_set_state(h, psi) -> None:
+    p, dev = _ptr(psi, 8)
+    _check(load_library().dirac_set_state(h, p, dev), h)
+
+
+def dirac_get_state(h, out) -> None:
+    p, dev = _ptr(out, 8)
+    _check(load_library().dirac_get_state(h, p, dev), h)
+
+
+def dirac_state_ptr(h) -> int:
+    p = ctypes.c_void_p()
+    _check(load_library().dirac_state_ptr(h, ctypes.byref(p)), h)
+    return p.value
+
+
+def dirac_step(h, nsteps: int) -> None:
+    _check(load_library().dirac_step(h, int(nsteps)), h)
+
+
+def dirac_observables(h, density=None) -> dict:
+    obs = dirac_obs()
+    if density is None:
+        st = load_library().dirac_observables(h, ctypes.byref(obs), None, 0)
+    else:
+        p, dev = _ptr(density, 8)
+        st = load_library().dirac_observables(h, ctypes.byref(obs), p, dev)
+    _check(st, h)
+    return {"norm": obs.norm, "norm_right": obs.norm_right, "flux_cum": obs.flux_cum,
+            "centroid": tuple(obs.centroid), "step": obs.step}
+
+
+def dirac_set_counters(h, step: int, flux_cum: float) -> None:
+    _check(load_library().dirac_set_counters(h, int(step), float(flux_cum)), h)
+
+
+def dirac_get_info(h) -> dict:
+    info = dirac_info()
+    _check(load_library().dirac_get_info(h, ctypes.byref(info)), h)
+    return {f: getattr(info, f) for f, _ in dirac_info._fields_}
+
+
+def dirac_autotune(h) -> None:
+    _check(load_library().dirac_autotune(h), h)
+
+
+def dirac_last_error(h=None) -> str:
+    return load_library().dirac_last_error(h).decode()
+
+
+def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRAC_FP64,
+                boundary: int = DIRAC_BC_ZERO, x_min=None, flux_face: int = -1, stream=None,
+                device: int = 0, steps_per_launch: int = 0, use_graphs: bool = True,
+                c: float | None = None, m: float | None = None, points_per_lane: int = 0) -> dirac_config:
+    """dirac_default_config() with the given fields replaced (n = (nx, ny, nz))."""
+    cfg = dirac_default_config()
+    cfg.ndim = ndim
+    for d in range(3):
+        cfg.n[d] = int(n[d])
+    if dx is not None:
+        cfg.dx = dx
+    if c is not None:
+        cfg.c = c
+    if m is not None:
+        cfg.m = m
+    if x_min is None:
+        x_min = tuple(-0.5 * n[d] * cfg.dx for d in range(3))
+    for d in range(3):
+        cfg.x_min[d] = x_min[d]
+    cfg.precision = precision
+    cfg.boundary = boundary
+    cfg.flux_face = flux_face
+    cfg.stream = stream
+    cfg.device = device
+    cfg.steps_per_launch = steps_per_launch
+    cfg.use_graphs = 1 if use_graphs else 0
+    cfg.points_per_lane = points_per_lane
+    return cfg

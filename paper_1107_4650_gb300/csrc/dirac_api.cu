@@ -1,0 +1,712 @@
+// Host runtime behind the C ABI of include/dirac.h: grid handles, phase tables, launch planning,
+// CUDA-graph replay of the step loop, observables and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dirac.h"
+#include "dirac_internal.cuh"
+
+using namespace dirac;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+constexpr int kGraphBlocks = 32;   // step launches captured in one graph (even: parity returns)
+constexpr int kObsBlocksMax = 1216;
+
+struct Plan {
+    int K = 1, P = 2, wpb = 4;
+    int64_t strip_w = 0, nstrips = 0, nsegs = 0, seg_h = 0;
+    int z_threads = 128;
+    int64_t z_nsegs = 1, z_seg_h = 0;
+};
+
+}  // namespace
+
+struct dirac_grid {
+    dirac_config cfg{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int fp32 = 0;
+    size_t elem = 8;
+    int64_t ncells = 0;
+    void *psi[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *table = nullptr;
+    size_t table_cap = 0;  // bytes
+    int table_full = 0;
+    double *flux_part = nullptr;
+    size_t flux_part_cap = 0;  // doubles
+    double *flux_dev = nullptr;
+    unsigned *ticket = nullptr;
+    double *obs_partial = nullptr;
+    double *obs_out = nullptr;
+    double *host_obs = nullptr;  // pinned [8]
+    double *density_tmp = nullptr;
+    int obs_blocks = 0;
+    int64_t step = 0;
+    double dt = 0;
+    int sm_count = 0;
+    Plan plan;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t launches = 0;
+    size_t device_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+dirac_status fail(dirac_grid *g, dirac_status st, const std::string &msg) {
+    if (g)
+        g->err = msg;
+    else
+        g_thread_err = msg;
+    return st;
+}
+
+dirac_status cuda_fail(dirac_grid *g, cudaError_t e, const char *where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(g, e == cudaErrorMemoryAllocation ? DIRAC_ERR_OOM : DIRAC_ERR_CUDA, msg);
+}
+
+#define CK(g, expr)                                            \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail((g), e_, #expr); \
+    } while (0)
+
+int ndim_of(const dirac_grid *g) { return g->cfg.ndim; }
+double scale_of(const dirac_grid *g) { return ndim_of(g) == 3 ? 0.125 : 0.25; }
+double cell_volume(const dirac_grid *g) {
+    const double dx = g->cfg.dx;
+    return ndim_of(g) == 3 ? dx * dx * dx : dx * dx;
+}
+
+// FP32 representation of (cos t, -sin t): among the float neighbours of the rounded values, the pair
+// whose squared modulus is closest to 1 (keeps the FP32 phase step unitary to ~1e-9 instead of ~1e-7).
+void round_unitary(double c, double s, float &cf, float &sf) {
+    const float c0 = (float)c, s0 = (float)s;
+    const float cs[3] = {nextafterf(c0, -2.f), c0, nextafterf(c0, 2.f)};
+    const float ss[3] = {nextafterf(s0, -2.f), s0, nextafterf(s0, 2.f)};
+    double best = 1e300;
+    cf = c0;
+    sf = s0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const double dc = cs[i], ds = ss[j];
+            const double err = std::fabs(dc * dc + ds * ds - 1.0);
+            const double dist = std::fabs(dc - c) + std::fabs(ds - s);
+            const double key = err + 1e-3 * dist;
+            if (key < best) {
+                best = key;
+                cf = cs[i];
+                sf = ss[j];
+            }
+        }
+}
+
+// Phase coefficients of Eq. sol_dis_4 at A = 0 for potential energy v, pre-scaled by 2^-d:
+// components 1,2: exp(-i (m c^2 dt + v dt)), components 3,4: exp(-i (v dt - m c^2 dt)).
+void phase_coeffs(double mu, double v, double dt, double scale, double out[4]) {
+    const double vdt = v * dt;
+    const double t_up = mu + vdt;
+    const double t_dn = vdt - mu;
+    out[0] = std::cos(t_up) * scale;
+    out[1] = -std::sin(t_up) * scale;
+    out[2] = std::cos(t_dn) * scale;
+    out[3] = -std::sin(t_dn) * scale;
+}
+
+dirac_status ensure_table(dirac_grid *g, size_t bytes) {
+    if (bytes <= g->table_cap) return DIRAC_OK;
+    if (g->table) {
+        cudaFree(g->table);
+        g->device_bytes -= g->table_cap;
+        g->table = nullptr;
+        g->table_cap = 0;
+    }
+    CK(g, cudaMalloc(&g->table, bytes));
+    g->table_cap = bytes;
+    g->device_bytes += bytes;
+    for (auto &x : g->graph)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    return DIRAC_OK;
+}
+
+dirac_status upload_table(dirac_grid *g, const double *V, int layout, int64_t count) {
+    const double mu = g->cfg.m * g->cfg.c * g->cfg.c * g->dt;
+    const double scale = scale_of(g);
+    const int64_t nentries = (layout == DIRAC_V_FULL) ? g->ncells : g->cfg.n[0];
+    (void)count;
+    const size_t bytes = (size_t)nentries * 4 * g->elem;
+    dirac_status st = ensure_table(g, bytes);
+    if (st != DIRAC_OK) return st;
+    if (g->fp32) {
+        std::vector<float> h((size_t)nentries * 4);
+#pragma omp parallel for schedule(static)
+        for (int64_t e = 0; e < nentries; ++e) {
+            const double v = (layout == DIRAC_V_NONE) ? 0.0 : V[e];
+            double p[4];
+            phase_coeffs(mu, v, g->dt, 1.0, p);
+            float cu, su, cd, sd;
+            round_unitary(p[0], p[1], cu, su);
+            round_unitary(p[2], p[3], cd, sd);
+            h[e * 4 + 0] = cu * (float)scale;
+            h[e * 4 + 1] = su * (float)scale;
+            h[e * 4 + 2] = cd * (float)scale;
+            h[e * 4 + 3] = sd * (float)scale;
+        }
+        CK(g, cudaMemcpyAsync(g->table, h.data(), bytes, cudaMemcpyHostToDevice, g->stream));
+        CK(g, cudaStreamSynchronize(g->stream));
+    } else {
+        std::vector<double> h((size_t)nentries * 4);
+#pragma omp parallel for schedule(static)
+        for (int64_t e = 0; e < nentries; ++e) {
+            const double v = (layout == DIRAC_V_NONE) ? 0.0 : V[e];
+            phase_coeffs(mu, v, g->dt, scale, &h[e * 4]);
+        }
+        CK(g, cudaMemcpyAsync(g->table, h.data(), bytes, cudaMemcpyHostToDevice, g->stream));
+        CK(g, cudaStreamSynchronize(g->stream));
+    }
+    g->table_full = (layout == DIRAC_V_FULL);
+    return DIRAC_OK;
+}
+
+// Launch geometry for (K, P, warps per block): strips of 32P - 2K owned cells, segments sized so the
+// launch holds about `target` warps per SM.
+void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
+    Plan &p = g->plan;
+    p.K = K;
+    p.P = P;
+    p.wpb = wpb;
+    const int64_t nx = g->cfg.n[0];
+    const int64_t nr = (ndim_of(g) == 3) ? g->cfg.n[1] : g->cfg.n[2];
+    const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
+    p.strip_w = 32 * P - 2 * K;
+    p.nstrips = (nx + p.strip_w - 1) / p.strip_w;
+    const int64_t want = (int64_t)g->sm_count * target_warps_per_sm;
+    int64_t nsegs = std::max<int64_t>(1, want / std::max<int64_t>(1, p.nstrips * planes));
+    // keep segments at least 8K rows so halo rows stay a small fraction
+    const int64_t min_rows = std::max<int64_t>(8 * K, 16);
+    nsegs = std::min<int64_t>(nsegs, std::max<int64_t>(1, nr / min_rows));
+    p.seg_h = (nr + nsegs - 1) / nsegs;
+    p.nsegs = (nr + p.seg_h - 1) / p.seg_h;
+    // 3-D z pass: one thread per column, segments until ~target warps per SM
+    if (ndim_of(g) == 3) {
+        const int64_t ncol = g->cfg.n[0] * g->cfg.n[1];
+        const int64_t nz = g->cfg.n[2];
+        int64_t zs = std::max<int64_t>(1, want * 32 / std::max<int64_t>(1, ncol));
+        zs = std::min<int64_t>(zs, std::max<int64_t>(1, nz / 32));
+        p.z_seg_h = (nz + zs - 1) / zs;
+        p.z_nsegs = (nz + p.z_seg_h - 1) / p.z_seg_h;
+    }
+    for (auto &x : g->graph)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+}
+
+dirac_status ensure_flux_part(dirac_grid *g) {
+    const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
+    const size_t need = (size_t)8 * planes * std::max<int64_t>(g->plan.nsegs, 1);
+    if (need <= g->flux_part_cap) return DIRAC_OK;
+    if (g->flux_part) {
+        cudaFree(g->flux_part);
+        g->device_bytes -= g->flux_part_cap * sizeof(double);
+    }
+    g->flux_part = nullptr;
+    CK(g, cudaMalloc(&g->flux_part, need * sizeof(double)));
+    g->flux_part_cap = need;
+    g->device_bytes += need * sizeof(double);
+    return DIRAC_OK;
+}
+
+// One block of work: K steps (2-D) or one step (3-D), from psi[parity] to psi[parity ^ 1] (2-D) or back
+// to psi[parity] (3-D).  Enqueued on s.  K_override > 0 runs that many steps with P from the plan.
+dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s) {
+    const Plan &p = g->plan;
+    const bool flux = g->cfg.flux_face >= 0;
+    const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
+    SweepArgs a{};
+    a.in = g->psi[parity];
+    a.out = g->psi[parity ^ 1];
+    a.table = g->table;
+    a.nx = g->cfg.n[0];
+    a.nr = (ndim_of(g) == 3) ? g->cfg.n[1] : g->cfg.n[2];
+    a.nplanes = planes;
+    a.strip_w = 32 * p.P - 2 * K;
+    a.nstrips = (a.nx + a.strip_w - 1) / a.strip_w;
+    a.nsegs = p.nsegs;
+    a.seg_h = p.seg_h;
+    a.flux_face = flux ? g->cfg.flux_face : -1;
+    a.flux_part = g->flux_part;
+    a.flux_cum = g->flux_dev;
+    a.ticket = g->ticket;
+    a.vol = cell_volume(g);
+    a.periodic = g->cfg.boundary == DIRAC_BC_PERIODIC;
+    a.full_table = g->table_full;
+    const int mode = (ndim_of(g) == 3) ? 1 : 0;
+    cudaError_t e = g->fp32 ? launch_sweep_f32(a, mode, K, p.P, p.wpb, s) : launch_sweep_f64(a, mode, K, p.P, p.wpb, s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "sweep kernel launch");
+    g->launches++;
+    if (ndim_of(g) == 3) {
+        ZArgs z{};
+        z.in = g->psi[parity ^ 1];
+        z.out = g->psi[parity];
+        z.table = g->table;
+        z.nx = g->cfg.n[0];
+        z.ny = g->cfg.n[1];
+        z.nz = g->cfg.n[2];
+        z.nsegs = p.z_nsegs;
+        z.seg_h = p.z_seg_h;
+        z.periodic = a.periodic;
+        z.full_table = g->table_full;
+        e = g->fp32 ? launch_zphase_f32(z, p.z_threads, s) : launch_zphase_f64(z, p.z_threads, s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "z-phase kernel launch");
+        g->launches++;
+    }
+    return DIRAC_OK;
+}
+
+int block_flips(const dirac_grid *g) { return ndim_of(g) == 3 ? 0 : 1; }
+
+dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
+    if (g->graph[parity]) {
+        *out = g->graph[parity];
+        return DIRAC_OK;
+    }
+    CK(g, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
+    int par = parity;
+    const int64_t l0 = g->launches;
+    dirac_status st = DIRAC_OK;
+    for (int b = 0; b < kGraphBlocks && st == DIRAC_OK; ++b) {
+        st = enqueue_block(g, par, g->plan.K, g->cap_stream);
+        par ^= block_flips(g);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+    g->launches = l0;  // captured, not launched
+    if (st != DIRAC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
+    g->graph[parity] = exec;
+    *out = exec;
+    return DIRAC_OK;
+}
+
+int64_t launches_per_block(const dirac_grid *g) { return 1 + (ndim_of(g) == 3 ? 1 : 0); }
+
+dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
+    const int K = (ndim_of(g) == 3) ? 1 : g->plan.K;
+    int64_t blocks = nsteps / K;
+    int64_t rem = nsteps % K;
+    if (g->cfg.use_graphs && blocks >= kGraphBlocks) {
+        while (blocks >= kGraphBlocks) {
+            cudaGraphExec_t ex = nullptr;
+            dirac_status st = get_graph(g, g->cur, &ex);
+            if (st != DIRAC_OK) return st;
+            CK(g, cudaGraphLaunch(ex, g->stream));
+            g->launches += kGraphBlocks * launches_per_block(g);
+            blocks -= kGraphBlocks;
+            // kGraphBlocks is even: parity unchanged
+        }
+    }
+    for (int64_t b = 0; b < blocks; ++b) {
+        dirac_status st = enqueue_block(g, g->cur, K, g->stream);
+        if (st != DIRAC_OK) return st;
+        g->cur ^= block_flips(g);
+    }
+    for (int64_t r = 0; r < rem; ++r) {
+        dirac_status st = enqueue_block(g, g->cur, 1, g->stream);
+        if (st != DIRAC_OK) return st;
+        g->cur ^= block_flips(g);
+    }
+    g->step += nsteps;
+    return DIRAC_OK;
+}
+
+void release(dirac_grid *g) {
+    if (!g) return;
+    if (g->stream || g->cap_stream) cudaStreamSynchronize(g->stream);
+    for (auto &x : g->graph)
+        if (x) cudaGraphExecDestroy(x);
+    for (auto &p : g->psi)
+        if (p) cudaFree(p);
+    if (g->table) cudaFree(g->table);
+    if (g->flux_part) cudaFree(g->flux_part);
+    if (g->flux_dev) cudaFree(g->flux_dev);
+    if (g->ticket) cudaFree(g->ticket);
+    if (g->obs_partial) cudaFree(g->obs_partial);
+    if (g->obs_out) cudaFree(g->obs_out);
+    if (g->density_tmp) cudaFree(g->density_tmp);
+    if (g->host_obs) cudaFreeHost(g->host_obs);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    delete g;
+}
+
+void default_plan(dirac_grid *g) {
+    const int k = g->cfg.steps_per_launch, pp = g->cfg.points_per_lane;
+    if (ndim_of(g) == 3) {
+        make_plan(g, 1, pp > 0 ? pp : 2, 4, 16);
+        return;
+    }
+    int K = g->fp32 ? 4 : 1, P = g->fp32 ? 4 : 2;
+    if (k > 0) K = k;
+    if (pp > 0) P = pp;
+    if (!sweep_supported(g->fp32, 0, K, P)) P = sweep_supported(g->fp32, 0, K, 4) ? 4 : 2;
+    make_plan(g, K, P, 4, g->fp32 ? 12 : 8);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dirac_version(void) { return "dirac-gb300 0.1 (sm_103a)"; }
+
+void dirac_default_config(dirac_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->ndim = 2;
+    cfg->n[0] = 256;
+    cfg->n[1] = 1;
+    cfg->n[2] = 256;
+    cfg->dx = 10.0 / 8192.0;
+    cfg->c = 137.0359895;
+    cfg->m = 1.0;
+    cfg->x_min[0] = -128 * cfg->dx;
+    cfg->x_min[1] = 0.0;
+    cfg->x_min[2] = -128 * cfg->dx;
+    cfg->precision = DIRAC_FP64;
+    cfg->boundary = DIRAC_BC_ZERO;
+    cfg->flux_face = -1;
+    cfg->stream = nullptr;
+    cfg->device = 0;
+    cfg->steps_per_launch = 0;
+    cfg->use_graphs = 1;
+    cfg->points_per_lane = 0;
+}
+
+const char *dirac_last_error(const dirac_grid *g) { return g ? g->err.c_str() : g_thread_err.c_str(); }
+
+dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
+    if (!cfg || !out) return fail(nullptr, DIRAC_ERR_ARG, "dirac_create_grid: null argument");
+    *out = nullptr;
+    if (cfg->ndim != 2 && cfg->ndim != 3) return fail(nullptr, DIRAC_ERR_ARG, "ndim must be 2 or 3");
+    for (int d = 0; d < 3; ++d)
+        if (cfg->n[d] < 1) return fail(nullptr, DIRAC_ERR_ARG, "grid sizes must be >= 1");
+    if (cfg->ndim == 2 && cfg->n[1] != 1) return fail(nullptr, DIRAC_ERR_ARG, "2-D grids (x-z plane) need n[1] == 1");
+    if (!(cfg->dx > 0) || !(cfg->c > 0) || !std::isfinite(cfg->dx) || !std::isfinite(cfg->c) || !std::isfinite(cfg->m))
+        return fail(nullptr, DIRAC_ERR_ARG, "dx and c must be finite and > 0, m finite");
+    if (cfg->precision != DIRAC_FP64 && cfg->precision != DIRAC_FP32)
+        return fail(nullptr, DIRAC_ERR_ARG, "precision must be DIRAC_FP64 or DIRAC_FP32");
+    if (cfg->boundary != DIRAC_BC_ZERO && cfg->boundary != DIRAC_BC_PERIODIC)
+        return fail(nullptr, DIRAC_ERR_ARG, "boundary must be DIRAC_BC_ZERO or DIRAC_BC_PERIODIC");
+    if (cfg->flux_face != -1 && (cfg->flux_face < 1 || cfg->flux_face > cfg->n[0] - 1))
+        return fail(nullptr, DIRAC_ERR_ARG, "flux_face must be -1 or in [1, nx-1]");
+    const double ncells_d = (double)cfg->n[0] * (double)cfg->n[1] * (double)cfg->n[2];
+    if (ncells_d > 4.0e10) return fail(nullptr, DIRAC_ERR_ARG, "grid too large");
+    if (cfg->steps_per_launch != 0 &&
+        !(sweep_supported(cfg->precision == DIRAC_FP32, 0, cfg->steps_per_launch, 2) ||
+          sweep_supported(cfg->precision == DIRAC_FP32, 0, cfg->steps_per_launch, 4)))
+        return fail(nullptr, DIRAC_ERR_ARG, "steps_per_launch must be 0, 1, 2 (FP64) or 0, 1, 2, 4 (FP32)");
+    if (cfg->points_per_lane != 0 && cfg->points_per_lane != 1 && cfg->points_per_lane != 2 &&
+        cfg->points_per_lane != 4)
+        return fail(nullptr, DIRAC_ERR_ARG, "points_per_lane must be 0, 1, 2 or 4");
+    if (cfg->ndim == 2 && cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
+        !sweep_supported(cfg->precision == DIRAC_FP32, 0, cfg->steps_per_launch, cfg->points_per_lane))
+        return fail(nullptr, DIRAC_ERR_ARG, "unsupported (steps_per_launch, points_per_lane) pair");
+    if (std::getenv("DIRAC_INJECT_OOM")) return fail(nullptr, DIRAC_ERR_OOM, "allocation failure injected (DIRAC_INJECT_OOM)");
+
+    dirac_grid *g = new (std::nothrow) dirac_grid();
+    if (!g) return fail(nullptr, DIRAC_ERR_OOM, "host allocation failed");
+    g->cfg = *cfg;
+    g->stream = static_cast<cudaStream_t>(cfg->stream);
+    g->fp32 = cfg->precision == DIRAC_FP32;
+    g->elem = g->fp32 ? 4 : 8;
+    g->ncells = cfg->n[0] * cfg->n[1] * cfg->n[2];
+    g->dt = cfg->dx / cfg->c;
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        release(g);
+        return fail(nullptr, DIRAC_ERR_CUDA, msg);
+    }
+    cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
+    if (g->sm_count <= 0) g->sm_count = 152;
+    const size_t state_bytes = (size_t)g->ncells * 8 * g->elem;
+    struct {
+        void **p;
+        size_t bytes;
+    } allocs[] = {{&g->psi[0], state_bytes}, {&g->psi[1], state_bytes}, {(void **)&g->flux_dev, 8 * sizeof(double)},
+                  {(void **)&g->ticket, 16},
+                  {(void **)&g->obs_partial, (size_t)kObsBlocksMax * 5 * sizeof(double)},
+                  {(void **)&g->obs_out, 8 * sizeof(double)}};
+    for (auto &al : allocs) {
+        e = cudaMalloc(al.p, al.bytes);
+        if (e != cudaSuccess) {
+            std::string msg = std::string("cudaMalloc(") + std::to_string(al.bytes) + " bytes): " + cudaGetErrorString(e);
+            cudaGetLastError();
+            release(g);
+            return fail(nullptr, e == cudaErrorMemoryAllocation ? DIRAC_ERR_OOM : DIRAC_ERR_CUDA, msg);
+        }
+        g->device_bytes += al.bytes;
+    }
+    e = cudaMallocHost(&g->host_obs, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("setup: ") + cudaGetErrorString(e);
+        release(g);
+        return fail(nullptr, DIRAC_ERR_CUDA, msg);
+    }
+    g->obs_blocks = (int)std::min<int64_t>(kObsBlocksMax, std::max<int64_t>(1, (g->ncells + 255) / 256));
+    default_plan(g);
+    dirac_status st = ensure_flux_part(g);
+    if (st == DIRAC_OK) st = upload_table(g, nullptr, DIRAC_V_NONE, 0);
+    if (st == DIRAC_OK) {
+        e = cudaMemsetAsync(g->psi[0], 0, state_bytes, g->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->flux_dev, 0, 8 * sizeof(double), g->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->ticket, 0, 16, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) st = cuda_fail(g, e, "initial clear");
+    }
+    if (st != DIRAC_OK) {
+        std::string msg = g->err;
+        release(g);
+        return fail(nullptr, st, msg);
+    }
+    *out = g;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_destroy(dirac_grid *g) {
+    if (!g) return DIRAC_OK;
+    cudaSetDevice(g->cfg.device);
+    release(g);
+    return DIRAC_OK;
+}
+
+dirac_status dirac_set_potential(dirac_grid *g, const double *V, int layout, int64_t count) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    CK(g, cudaSetDevice(g->cfg.device));
+    if (layout == DIRAC_V_NONE) return upload_table(g, nullptr, layout, 0);
+    if (!V) return fail(g, DIRAC_ERR_ARG, "dirac_set_potential: null V");
+    if (layout == DIRAC_V_X_ONLY) {
+        if (count != g->cfg.n[0]) return fail(g, DIRAC_ERR_ARG, "DIRAC_V_X_ONLY needs count == nx");
+    } else if (layout == DIRAC_V_FULL) {
+        if (count != g->ncells) return fail(g, DIRAC_ERR_ARG, "DIRAC_V_FULL needs count == nx*ny*nz");
+    } else {
+        return fail(g, DIRAC_ERR_ARG, "unknown potential layout");
+    }
+    for (int64_t i = 0; i < count; ++i)
+        if (!std::isfinite(V[i])) return fail(g, DIRAC_ERR_ARG, "potential holds a non-finite value");
+    return upload_table(g, V, layout, count);
+}
+
+dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (!psi) return fail(g, DIRAC_ERR_ARG, "dirac_set_state: null psi");
+    CK(g, cudaSetDevice(g->cfg.device));
+    const size_t bytes = (size_t)g->ncells * 8 * g->elem;
+    CK(g, cudaMemcpyAsync(g->psi[g->cur], psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          g->stream));
+    CK(g, cudaMemsetAsync(g->flux_dev, 0, sizeof(double), g->stream));
+    if (!on_device) CK(g, cudaStreamSynchronize(g->stream));
+    g->step = 0;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_state(dirac_grid *g, void *psi, int on_device) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (!psi) return fail(g, DIRAC_ERR_ARG, "dirac_get_state: null psi");
+    CK(g, cudaSetDevice(g->cfg.device));
+    const size_t bytes = (size_t)g->ncells * 8 * g->elem;
+    CK(g, cudaMemcpyAsync(psi, g->psi[g->cur], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          g->stream));
+    if (!on_device) CK(g, cudaStreamSynchronize(g->stream));
+    return DIRAC_OK;
+}
+
+dirac_status dirac_state_ptr(dirac_grid *g, void **dev_ptr) {
+    if (!g || !dev_ptr) return fail(g, DIRAC_ERR_ARG, "null argument");
+    *dev_ptr = g->psi[g->cur];
+    return DIRAC_OK;
+}
+
+dirac_status dirac_step(dirac_grid *g, int64_t nsteps) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (nsteps < 0) return fail(g, DIRAC_ERR_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return DIRAC_OK;
+    CK(g, cudaSetDevice(g->cfg.device));
+    return run_steps(g, nsteps);
+}
+
+dirac_status dirac_set_counters(dirac_grid *g, int64_t step, double flux_cum) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (step < 0 || !std::isfinite(flux_cum)) return fail(g, DIRAC_ERR_ARG, "bad counters");
+    CK(g, cudaSetDevice(g->cfg.device));
+    g->host_obs[7] = flux_cum;
+    CK(g, cudaMemcpyAsync(g->flux_dev, &g->host_obs[7], sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    CK(g, cudaStreamSynchronize(g->stream));
+    g->step = step;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, int density_on_device) {
+    if (!g || !obs) return fail(g, DIRAC_ERR_ARG, "null argument");
+    CK(g, cudaSetDevice(g->cfg.device));
+    double *dens = nullptr;
+    if (density) {
+        if (density_on_device) {
+            dens = density;
+        } else {
+            if (!g->density_tmp) {
+                CK(g, cudaMalloc(&g->density_tmp, (size_t)g->ncells * sizeof(double)));
+                g->device_bytes += (size_t)g->ncells * sizeof(double);
+            }
+            dens = g->density_tmp;
+        }
+    }
+    ObsArgs a{};
+    a.psi = g->psi[g->cur];
+    a.nx = g->cfg.n[0];
+    a.ny = g->cfg.n[1];
+    a.nz = g->cfg.n[2];
+    a.dx = g->cfg.dx;
+    a.x0 = g->cfg.x_min[0] + 0.5 * g->cfg.dx;
+    a.y0 = g->cfg.x_min[1] + 0.5 * g->cfg.dx;
+    a.z0 = g->cfg.x_min[2] + 0.5 * g->cfg.dx;
+    a.face = g->cfg.flux_face;
+    a.density = dens;
+    a.partial = g->obs_partial;
+    a.out = g->obs_out;
+    cudaError_t e = launch_observables(a, g->fp32, g->obs_blocks, g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "observables launch");
+    g->launches += 2;
+    CK(g, cudaMemcpyAsync(g->host_obs, g->obs_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(g, cudaMemcpyAsync(&g->host_obs[5], g->flux_dev, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    if (density && !density_on_device)
+        CK(g, cudaMemcpyAsync(density, dens, (size_t)g->ncells * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(g, cudaStreamSynchronize(g->stream));
+    const double vol = cell_volume(g);
+    const double *h = g->host_obs;
+    obs->norm = h[0] * vol;
+    obs->norm_right = h[1] * vol;
+    obs->flux_cum = h[5];
+    obs->centroid[0] = h[0] > 0 ? h[2] / h[0] : 0.0;
+    obs->centroid[1] = h[0] > 0 ? h[3] / h[0] : 0.0;
+    obs->centroid[2] = h[0] > 0 ? h[4] / h[0] : 0.0;
+    obs->step = g->step;
+    if (!std::isfinite(obs->norm)) return fail(g, DIRAC_ERR_NONFINITE, "state holds NaN or Inf");
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
+    if (!g || !info) return fail(nullptr, DIRAC_ERR_ARG, "null argument");
+    const Plan &p = g->plan;
+    info->steps_per_launch = (g->cfg.ndim == 3) ? 1 : p.K;
+    info->points_per_lane = p.P;
+    const int64_t planes = (g->cfg.ndim == 3) ? g->cfg.n[2] : 1;
+    info->launch_warps = p.nstrips * p.nsegs * planes;
+    info->strip_width = p.strip_w;
+    info->segment_rows = p.seg_h;
+    info->graphs = g->cfg.use_graphs;
+    info->kernel_launches = g->launches;
+    info->device_bytes = g->device_bytes;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_autotune(dirac_grid *g) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    CK(g, cudaSetDevice(g->cfg.device));
+    struct Cand {
+        int K, P, wpb, wsm;
+    };
+    std::vector<Cand> cands;
+    if (g->cfg.ndim == 3) {
+        for (int P : {1, 2, 4})
+            for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm});
+    } else if (g->fp32) {
+        const int KP[][2] = {{1, 4}, {2, 4}, {4, 2}, {4, 4}};
+        for (auto &kp : KP)
+            for (int wsm : {4, 8, 12, 16}) cands.push_back({kp[0], kp[1], 4, wsm});
+    } else {
+        const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
+        for (auto &kp : KP)
+            for (int wsm : {2, 4, 8, 16}) cands.push_back({kp[0], kp[1], 4, wsm});
+    }
+    // save state and counters
+    const size_t bytes = (size_t)g->ncells * 8 * g->elem;
+    void *backup = nullptr;
+    CK(g, cudaMalloc(&backup, bytes));
+    cudaMemcpyAsync(backup, g->psi[g->cur], bytes, cudaMemcpyDeviceToDevice, g->stream);
+    double flux_saved = 0;
+    cudaMemcpyAsync(&g->host_obs[6], g->flux_dev, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+    cudaStreamSynchronize(g->stream);
+    flux_saved = g->host_obs[6];
+    const int64_t step_saved = g->step, launches_saved = g->launches;
+    const int cur_saved = g->cur;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Cand best = {g->plan.K, g->plan.P, g->plan.wpb, 0};
+    double best_t = 1e300;
+    const int use_graphs = g->cfg.use_graphs;
+    g->cfg.use_graphs = 0;
+    dirac_status st = DIRAC_OK;
+    for (const Cand &c : cands) {
+        make_plan(g, c.K, c.P, c.wpb, c.wsm);
+        st = ensure_flux_part(g);
+        if (st != DIRAC_OK) break;
+        const int64_t nsteps = std::max<int64_t>(8, 8 * (int64_t)c.K);
+        st = run_steps(g, nsteps);  // warm-up
+        if (st != DIRAC_OK) break;
+        cudaEventRecord(e0, g->stream);
+        st = run_steps(g, 3 * nsteps);
+        if (st != DIRAC_OK) break;
+        cudaEventRecord(e1, g->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per_step = ms / (3.0 * nsteps);
+        if (per_step < best_t) {
+            best_t = per_step;
+            best = c;
+        }
+    }
+    g->cfg.use_graphs = use_graphs;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == DIRAC_OK) {
+        make_plan(g, best.K, best.P, best.wpb, best.wsm ? best.wsm : 8);
+        st = ensure_flux_part(g);
+    }
+    g->cur = cur_saved;
+    cudaMemcpyAsync(g->psi[g->cur], backup, bytes, cudaMemcpyDeviceToDevice, g->stream);
+    g->host_obs[6] = flux_saved;
+    cudaMemcpyAsync(g->flux_dev, &g->host_obs[6], sizeof(double), cudaMemcpyHostToDevice, g->stream);
+    cudaStreamSynchronize(g->stream);
+    cudaFree(backup);
+    g->step = step_saved;
+    g->launches = launches_saved;
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Internal declarations shared by the translation units of libdirac.
+// Not part of the public ABI (that is include/dirac.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dirac {
+
+// Arguments of the fused sweep kernels (step_kernels.cuh).
+//
+// The kernel treats the data as `nplanes` independent planes of `nr` rows of `nx` cells.
+//   mode 0 (2-D step):   plane = the x-z grid, rows run along z; one launch runs K full steps
+//                        (x sweep, z sweep, phase), the sweeps' 1/2 factors folded into the
+//                        phase table as 1/4.
+//   mode 1 (3-D, x-y):   planes = z slices, rows run along y; x sweep then y sweep, no phase,
+//                        output left at 4x the swept state (exact scaling, no rounding).
+// Each warp owns an x strip of `strip_w` cells and a segment of `seg_h` rows of one plane.
+struct SweepArgs {
+    const void *in;
+    void *out;
+    const void *table;     // mode 0: 4 values (pu.re, pu.im, pd.re, pd.im) per x column (full_table
+                           //         = 0) or per cell (full_table = 1), element type = storage type
+    int64_t nx, nr, nplanes;
+    int64_t strip_w, nstrips, nsegs, seg_h;
+    int64_t flux_face;     // x face index or -1
+    double *flux_part;     // [K][nplanes*nsegs] per-step face-flux partial sums (unscaled)
+    double *flux_cum;      // cumulative flux; the last block of a launch adds vol * (sum of each step)
+    unsigned *ticket;      // block-completion counter, 0 between launches (the last block resets it)
+    double vol;            // cell volume dx^d
+    int periodic;
+    int full_table;
+};
+
+// Arguments of the 3-D z-sweep + phase kernel: the input is 4x the x-y swept state, the table is
+// pre-scaled by 1/8 so the output is the true state after a full step.
+struct ZArgs {
+    const void *in;
+    void *out;
+    const void *table;     // per x column (full_table = 0) or per cell (full_table = 1)
+    int64_t nx, ny, nz;
+    int64_t nsegs, seg_h;
+    int periodic;
+    int full_table;
+};
+
+// Launchers: return cudaErrorInvalidValue for an unsupported (K, P) pair.
+cudaError_t launch_sweep_f64(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
+cudaError_t launch_sweep_f32(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
+cudaError_t launch_zphase_f64(const ZArgs &a, int threads, cudaStream_t s);
+cudaError_t launch_zphase_f32(const ZArgs &a, int threads, cudaStream_t s);
+
+// Observables: per-block FP64 partial sums of (rho, rho right of face, x rho, y rho, z rho) over the
+// grid, then one block folds the partials in a fixed order into out[5].  rho per cell is written to
+// density when non-null.
+struct ObsArgs {
+    const void *psi;
+    int64_t nx, ny, nz;
+    double dx, x0, y0, z0;  // x0 = x_min + dx/2 etc. (first cell centre)
+    int64_t face;
+    double *density;
+    double *partial;        // [nblocks][5]
+    double *out;            // [5]
+};
+cudaError_t launch_observables(const ObsArgs &a, int fp32, int nblocks, cudaStream_t s);
+
+// Instantiated (K, P) pairs of the sweep kernels.
+bool sweep_supported(int fp32, int mode, int K, int P);
+
+}  // namespace dirac

@@ -1,0 +1,397 @@
+// Fused sweep kernels of the split-operator Dirac scheme (Sec. 2.3, Eqs. sol_dis_1-sol_dis_4).
+//
+// Design (one warp = one independent strip, no shared memory, no block barrier):
+//   * a warp owns `strip_w` consecutive x cells of one plane and a segment of rows; it loads
+//     32*P cells per row (lane l holds cells xa + 32 j + l, j < P), i.e. K halo cells on each side;
+//   * it streams the rows of its segment (plus K halo rows at each end) through K pipelined
+//     levels held in registers: level s turns the step-(s-1) state of row q into the step-s state
+//     of row q-1, so one pass over HBM advances K steps (temporal blocking);
+//   * the x sweep needs cells x-1 and x+1: the characteristic sums u = a+b of the left neighbour
+//     and w = a-b of the right neighbour come from warp shuffles;
+//   * the second sweep (z in 2-D, y in the 3-D x-y pass) needs rows q-1 and q+1: each level keeps
+//     the "+" characteristic sums of the two previous rows in registers;
+//   * the ghost-zero boundary is imposed on every level's output (cells outside the grid are 0
+//     at every sub-step); a zero row stays zero through the x sweep, so one mask per level is
+//     exact.
+// Arithmetic order is fixed (explicit round-to-nearest intrinsics, no contraction):
+//   sweep:  u = a + b, w = a - b;  a' = u(-) + w(+), b' = u(-) - w(+)   (1/2 factors deferred)
+//   phase:  re = fma(z.re, p.re, -(z.im p.im)),  im = fma(z.re, p.im, z.im p.re)
+// with p carrying the deferred 1/4 (exact power-of-two scaling).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dirac_internal.cuh"
+
+namespace dirac {
+
+template <typename T> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+
+template <typename T> struct Cx { T re, im; };
+
+template <typename T> __device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) {
+    return {Ar<T>::add(a.re, b.re), Ar<T>::add(a.im, b.im)};
+}
+template <typename T> __device__ __forceinline__ Cx<T> csub(Cx<T> a, Cx<T> b) {
+    return {Ar<T>::sub(a.re, b.re), Ar<T>::sub(a.im, b.im)};
+}
+// a + i b and a - i b
+template <typename T> __device__ __forceinline__ Cx<T> cadd_ib(Cx<T> a, Cx<T> b) {
+    return {Ar<T>::sub(a.re, b.im), Ar<T>::add(a.im, b.re)};
+}
+template <typename T> __device__ __forceinline__ Cx<T> csub_ib(Cx<T> a, Cx<T> b) {
+    return {Ar<T>::add(a.re, b.im), Ar<T>::sub(a.im, b.re)};
+}
+// i z and -i z (exact)
+template <typename T> __device__ __forceinline__ Cx<T> cmul_i(Cx<T> a) { return {-a.im, a.re}; }
+template <typename T> __device__ __forceinline__ Cx<T> cmul_mi(Cx<T> a) { return {a.im, -a.re}; }
+template <typename T> __device__ __forceinline__ Cx<T> cmulp(Cx<T> z, Cx<T> p) {
+    return {Ar<T>::fma(z.re, p.re, -Ar<T>::mul(z.im, p.im)), Ar<T>::fma(z.re, p.im, Ar<T>::mul(z.im, p.re))};
+}
+template <typename T> __device__ __forceinline__ double abs2d(Cx<T> a) {
+    double r = (double)a.re, i = (double)a.im;
+    return __dadd_rn(__dmul_rn(r, r), __dmul_rn(i, i));
+}
+
+template <typename T> __device__ __forceinline__ Cx<T> shfl_c(Cx<T> v, int src) {
+    return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+
+// ---- point load/store: 4 complex components, 64 B (FP64) or 32 B (FP32)
+__device__ __forceinline__ void load_pt(const double *p, Cx<double> s[4]) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double2 v = q[c];
+        s[c] = {v.x, v.y};
+    }
+}
+__device__ __forceinline__ void load_pt(const float *p, Cx<float> s[4]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    float4 a = q[0], b = q[1];
+    s[0] = {a.x, a.y};
+    s[1] = {a.z, a.w};
+    s[2] = {b.x, b.y};
+    s[3] = {b.z, b.w};
+}
+__device__ __forceinline__ void store_pt(double *p, const Cx<double> s[4]) {
+    double2 *q = reinterpret_cast<double2 *>(p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = make_double2(s[c].re, s[c].im);
+}
+__device__ __forceinline__ void store_pt(float *p, const Cx<float> s[4]) {
+    float4 *q = reinterpret_cast<float4 *>(p);
+    q[0] = make_float4(s[0].re, s[0].im, s[1].re, s[1].im);
+    q[1] = make_float4(s[2].re, s[2].im, s[3].re, s[3].im);
+}
+__device__ __forceinline__ void load_tab(const double *p, Cx<double> &pu, Cx<double> &pd) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = q[0], b = q[1];
+    pu = {a.x, a.y};
+    pd = {b.x, b.y};
+}
+__device__ __forceinline__ void load_tab(const float *p, Cx<float> &pu, Cx<float> &pd) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    pu = {a.x, a.y};
+    pd = {a.z, a.w};
+}
+
+__device__ __forceinline__ int64_t pmod(int64_t a, int64_t n) {
+    int64_t r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+template <typename T, int K, int P, int MODE>
+__device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane);
+template <int K>
+__device__ __forceinline__ void finish_flux(const SweepArgs &a);
+
+// MODE 0: 2-D step (x sweep, z sweep, phase), K steps per launch.
+// MODE 1: 3-D x-y pass (x sweep, y sweep), K must be 1.
+template <typename T, int K, int P, int MODE>
+__global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t per_plane = a.nstrips * a.nsegs;
+    // Warps past the end skip the work but still reach the block-completion ticket below.
+    if (wid < per_plane * a.nplanes) sweep_warp<T, K, P, MODE>(a, wid, lane);
+    if (a.flux_face >= 0) finish_flux<K>(a);
+}
+
+// Last-block fold of the per-warp flux partials: every block takes a ticket after its partials are
+// visible; the block that takes the last ticket sums them in a fixed order (step by step, parts in
+// index order), adds vol * sum to the cumulative flux and resets the ticket.  No block waits.
+template <int K>
+__device__ __forceinline__ void finish_flux(const SweepArgs &a) {
+    __shared__ unsigned s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(a.ticket, 1u);
+        s_last = (t == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const int64_t nparts = a.nsegs * a.nplanes;
+        double F = __ldcg(a.flux_cum);
+        for (int s = 0; s < K; ++s) {
+            double f = 0.0;
+            for (int64_t q = 0; q < nparts; ++q) f = __dadd_rn(f, __ldcg(a.flux_part + s * nparts + q));
+            F = __dadd_rn(F, __dmul_rn(f, a.vol));
+        }
+        *a.flux_cum = F;
+        __threadfence();
+        *a.ticket = 0u;
+    }
+}
+
+template <typename T, int K, int P, int MODE>
+__device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane) {
+    const int64_t per_plane = a.nstrips * a.nsegs;
+    const int64_t plane = wid / per_plane;
+    const int64_t rem = wid - plane * per_plane;
+    const int64_t seg = rem / a.nstrips;
+    const int64_t strip = rem - seg * a.nstrips;
+    const int64_t nx = a.nx, nr = a.nr;
+    const bool per = a.periodic != 0;
+    const int64_t x_own0 = strip * a.strip_w;
+    const int64_t x_own1 = min(x_own0 + a.strip_w, nx);
+    const int64_t xa = x_own0 - K;
+    const int64_t r_begin = seg * a.seg_h;
+    const int64_t r_end = min(r_begin + a.seg_h, nr);
+    const T *in = static_cast<const T *>(a.in) + plane * nr * nx * 8;
+    T *out = static_cast<T *>(a.out) + plane * nr * nx * 8;
+
+    int64_t xl[P];
+    bool xin[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int64_t x = xa + 32 * j + lane;
+        xin[j] = (x >= 0 && x < nx);
+        xl[j] = per ? pmod(x, nx) : min(max(x, (int64_t)0), nx - 1);
+    }
+    // phase coefficients per x column (mode 0, x-only table)
+    Cx<T> pu[P], pd[P];
+    if (MODE == 0 && !a.full_table) {
+#pragma unroll
+        for (int j = 0; j < P; ++j) load_tab(static_cast<const T *>(a.table) + xl[j] * 4, pu[j], pd[j]);
+    }
+    // flux: the lane/point holding x == face (owned by this strip) sums
+    // 1/2(|u14|^2+|u23|^2)(face-1) - 1/2(|w14|^2+|w23|^2)(face) per row.
+    int fj = -1;
+    if (a.flux_face >= x_own0 && a.flux_face < x_own1) {
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            if (xa + 32 * j + lane == a.flux_face) fj = j;
+    }
+    double facc[K];
+#pragma unroll
+    for (int s = 0; s < K; ++s) facc[s] = 0.0;
+
+    // "+" characteristic sums of the two previous rows per level: rows q-2 (A) and q-1 (B)
+    Cx<T> UA[K][P][2], UB[K][P][2];
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                UA[s][j][h] = {T(0), T(0)};
+                UB[s][j][h] = {T(0), T(0)};
+            }
+
+    const int src_prev = (lane + 31) & 31, src_next = (lane + 1) & 31;
+
+    for (int64_t r = r_begin - K; r < r_end + K; ++r) {
+        Cx<T> st[P][4];
+        const bool row_ok = per || (r >= 0 && r < nr);
+        const int64_t rl = per ? pmod(r, nr) : r;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if (row_ok && (per || xin[j])) {
+                load_pt(in + (rl * nx + xl[j]) * 8, st[j]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) st[j][c] = {T(0), T(0)};
+            }
+        }
+#pragma unroll
+        for (int lev = 0; lev < K; ++lev) {
+            const int64_t q = r - lev;  // row of the level-lev state in st
+            Cx<T> u14[P], u23[P], w14[P], w23[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                u14[j] = cadd(st[j][0], st[j][3]);
+                w14[j] = csub(st[j][0], st[j][3]);
+                u23[j] = cadd(st[j][1], st[j][2]);
+                w23[j] = csub(st[j][1], st[j][2]);
+            }
+            Cx<T> pu14[P], pu23[P], nw14[P], nw23[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                pu14[j] = shfl_c(u14[j], src_prev);
+                pu23[j] = shfl_c(u23[j], src_prev);
+                nw14[j] = shfl_c(w14[j], src_next);
+                nw23[j] = shfl_c(w23[j], src_next);
+            }
+            Cx<T> lu14[P], lu23[P], rw14[P], rw23[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const int jp = j > 0 ? j - 1 : 0;
+                const int jn = j < P - 1 ? j + 1 : P - 1;
+                lu14[j] = (lane == 0) ? pu14[jp] : pu14[j];
+                lu23[j] = (lane == 0) ? pu23[jp] : pu23[j];
+                rw14[j] = (lane == 31) ? nw14[jn] : nw14[j];
+                rw23[j] = (lane == 31) ? nw23[jn] : nw23[j];
+            }
+            if (fj >= 0 && q >= r_begin && q < r_end) {
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    if (j == fj) {
+                        const double right = __dmul_rn(0.5, __dadd_rn(abs2d(lu14[j]), abs2d(lu23[j])));
+                        const double left = __dmul_rn(0.5, __dadd_rn(abs2d(w14[j]), abs2d(w23[j])));
+                        facc[lev] = __dadd_rn(facc[lev], __dsub_rn(right, left));
+                    }
+                }
+            }
+            const bool out_row_ok = per || (q - 1 >= 0 && q - 1 < nr);
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                // x sweep (Eq. sol_dis_1), x2
+                const Cx<T> b0 = cadd(lu14[j], rw14[j]);
+                const Cx<T> b3 = csub(lu14[j], rw14[j]);
+                const Cx<T> b1 = cadd(lu23[j], rw23[j]);
+                const Cx<T> b2 = csub(lu23[j], rw23[j]);
+                Cx<T> o[4];
+                if (MODE == 0) {
+                    // z sweep (Eq. sol_dis_3): +z movers (b1+b3, b2-b4), -z movers (b1-b3, b2+b4)
+                    const Cx<T> U13 = cadd(b0, b2), U24 = csub(b1, b3);
+                    const Cx<T> W13 = csub(b0, b2), W24 = cadd(b1, b3);
+                    o[0] = cadd(UA[lev][j][0], W13);
+                    o[2] = csub(UA[lev][j][0], W13);
+                    o[1] = cadd(UA[lev][j][1], W24);
+                    o[3] = csub(W24, UA[lev][j][1]);
+                    UA[lev][j][0] = UB[lev][j][0];
+                    UA[lev][j][1] = UB[lev][j][1];
+                    UB[lev][j][0] = U13;
+                    UB[lev][j][1] = U24;
+                    // phase (Eq. sol_dis_4, A = 0) with the deferred 1/4
+                    Cx<T> qu, qd;
+                    if (a.full_table) {
+                        const int64_t rr = per ? pmod(q - 1, nr) : min(max(q - 1, (int64_t)0), nr - 1);
+                        load_tab(static_cast<const T *>(a.table) + (plane * nr * nx + rr * nx + xl[j]) * 4, qu, qd);
+                    } else {
+                        qu = pu[j];
+                        qd = pd[j];
+                    }
+                    o[0] = cmulp(o[0], qu);
+                    o[1] = cmulp(o[1], qu);
+                    o[2] = cmulp(o[2], qd);
+                    o[3] = cmulp(o[3], qd);
+                } else {
+                    // y sweep (Eq. sol_dis_2): +y movers (b1 - i b4, b2 + i b3), -y movers (b1 + i b4, b2 - i b3)
+                    const Cx<T> U14 = csub_ib(b0, b3), U23 = cadd_ib(b1, b2);
+                    const Cx<T> W14 = cadd_ib(b0, b3), W23 = csub_ib(b1, b2);
+                    o[0] = cadd(UA[lev][j][0], W14);
+                    o[3] = cmul_i(csub(UA[lev][j][0], W14));
+                    o[1] = cadd(UA[lev][j][1], W23);
+                    o[2] = cmul_mi(csub(UA[lev][j][1], W23));
+                    UA[lev][j][0] = UB[lev][j][0];
+                    UA[lev][j][1] = UB[lev][j][1];
+                    UB[lev][j][0] = U14;
+                    UB[lev][j][1] = U23;
+                }
+                const bool keep = per || (out_row_ok && xin[j]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) st[j][c] = keep ? o[c] : Cx<T>{T(0), T(0)};
+            }
+        }
+        const int64_t ro = r - K;
+        if (ro >= r_begin && ro < r_end) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const int64_t x = xa + 32 * j + lane;
+                if (x >= x_own0 && x < x_own1) store_pt(out + (ro * nx + x) * 8, st[j]);
+            }
+        }
+    }
+    if (a.flux_face >= x_own0 && a.flux_face < x_own1) {
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            double v = facc[s];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) a.flux_part[(int64_t)s * a.nsegs * a.nplanes + plane * a.nsegs + seg] = v;
+        }
+    }
+}
+
+// 3-D z sweep + phase: one thread per (x, y) column and z segment; the input is 4x the x-y swept
+// state, the table carries 1/8, so the output is the state after the full step.
+template <typename T>
+__global__ void __launch_bounds__(128) zphase_kernel(const ZArgs a) {
+    const int64_t ncol = a.nx * a.ny;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= ncol * a.nsegs) return;
+    const int64_t seg = tid / ncol;
+    const int64_t col = tid - seg * ncol;
+    const int64_t x = col % a.nx;
+    const int64_t nz = a.nz;
+    const bool per = a.periodic != 0;
+    const int64_t z_begin = seg * a.seg_h;
+    const int64_t z_end = min(z_begin + a.seg_h, nz);
+    const T *in = static_cast<const T *>(a.in);
+    T *out = static_cast<T *>(a.out);
+    const T *tab = static_cast<const T *>(a.table);
+    Cx<T> pu, pd;
+    if (!a.full_table) load_tab(tab + x * 4, pu, pd);
+    Cx<T> UA[2] = {{T(0), T(0)}, {T(0), T(0)}}, UB[2] = {{T(0), T(0)}, {T(0), T(0)}};
+    for (int64_t z = z_begin - 1; z <= z_end; ++z) {
+        Cx<T> s[4];
+        const bool ok = per || (z >= 0 && z < nz);
+        if (ok) {
+            const int64_t zl = per ? pmod(z, nz) : z;
+            load_pt(in + (zl * ncol + col) * 8, s);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s[c] = {T(0), T(0)};
+        }
+        const Cx<T> U13 = cadd(s[0], s[2]), U24 = csub(s[1], s[3]);
+        const Cx<T> W13 = csub(s[0], s[2]), W24 = cadd(s[1], s[3]);
+        const int64_t zo = z - 1;
+        if (zo >= z_begin && zo < z_end) {
+            Cx<T> o[4];
+            o[0] = cadd(UA[0], W13);
+            o[2] = csub(UA[0], W13);
+            o[1] = cadd(UA[1], W24);
+            o[3] = csub(W24, UA[1]);
+            Cx<T> qu = pu, qd = pd;
+            if (a.full_table) load_tab(tab + (zo * ncol + col) * 4, qu, qd);
+            o[0] = cmulp(o[0], qu);
+            o[1] = cmulp(o[1], qu);
+            o[2] = cmulp(o[2], qd);
+            o[3] = cmulp(o[3], qd);
+            store_pt(out + (zo * ncol + col) * 8, o);
+        }
+        UA[0] = UB[0];
+        UA[1] = UB[1];
+        UB[0] = U13;
+        UB[1] = U24;
+    }
+}
+
+}  // namespace dirac

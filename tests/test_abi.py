@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads and exports every symbol the header declares; the ctypes
+structures match the C layout; argument errors are reported without touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dirac.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1107_4650_gb300 import build as B
+    B.build()
+    import paper_1107_4650_gb300 as D
+    return D.load_library()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(dirac_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for want in ("dirac_create_grid", "dirac_set_potential", "dirac_step", "dirac_observables",
+                 "dirac_set_state", "dirac_get_state", "dirac_destroy"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layout_matches_c(tmp_path):
+    import paper_1107_4650_gb300 as D
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dirac.h"\nint main(void){'
+                   'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(dirac_config), sizeof(dirac_obs), sizeof(dirac_info),'
+                   'offsetof(dirac_config, stream), offsetof(dirac_config, points_per_lane), offsetof(dirac_info, device_bytes));'
+                   'return 0;}\n')
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [ctypes.sizeof(D.dirac_config), ctypes.sizeof(D.dirac_obs), ctypes.sizeof(D.dirac_info),
+                    D.dirac_config.stream.offset, D.dirac_config.points_per_lane.offset,
+                    D.dirac_info.device_bytes.offset]
+
+
+def test_version_and_defaults(lib):
+    import paper_1107_4650_gb300 as D
+    assert "sm_103a" in D.dirac_version()
+    cfg = D.dirac_default_config()
+    assert cfg.ndim == 2 and cfg.n[1] == 1 and abs(cfg.c - 137.0359895) < 1e-12 and cfg.flux_face == -1
+
+
+@pytest.mark.parametrize("field,value", [("ndim", 4), ("precision", 7), ("boundary", 5), ("flux_face", 0),
+                                         ("steps_per_launch", 3), ("points_per_lane", 3), ("dx", -1.0)])
+def test_invalid_config_is_rejected_before_any_cuda_call(lib, field, value):
+    import paper_1107_4650_gb300 as D
+    cfg = D.make_config((64, 1, 64))
+    setattr(cfg, field, value)
+    with pytest.raises(D.DiracError) as e:
+        D.dirac_create_grid(cfg)
+    assert e.value.status == D.DIRAC_ERR_ARG
+    assert D.dirac_last_error(None)
+
+
+def test_2d_grid_needs_ny_1(lib):
+    import paper_1107_4650_gb300 as D
+    cfg = D.make_config((64, 2, 64))
+    with pytest.raises(D.DiracError) as e:
+        D.dirac_create_grid(cfg)
+    assert e.value.status == D.DIRAC_ERR_ARG
+
+
+def test_injected_allocation_failure(lib, monkeypatch):
+    import paper_1107_4650_gb300 as D
+    monkeypatch.setenv("DIRAC_INJECT_OOM", "1")
+    with pytest.raises(D.DiracError) as e:
+        D.dirac_create_grid(D.make_config((64, 1, 64)))
+    assert e.value.status == D.DIRAC_ERR_OOM
+
+
+def test_null_handles_are_errors_not_crashes(lib):
+    import paper_1107_4650_gb300 as D
+    assert lib.dirac_step(None, 1) == D.DIRAC_ERR_ARG
+    assert lib.dirac_destroy(None) == D.DIRAC_OK
+    assert lib.dirac_set_state(None, None, 0) == D.DIRAC_ERR_ARG

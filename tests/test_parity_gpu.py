@@ -1,0 +1,286 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+FP64: the kernels follow the same operation order as the oracle (the 1/2 factors of the sweeps
+are carried as an exact power-of-two scale folded into the phase coefficients), so the state is
+compared bit for bit; the flux and the observables are FP64 sums in a different association and
+are compared to 1e-12 relative.  FP32 storage is compared with a tolerance derived from its
+rounding (unit roundoff 6e-8 per operation, about 50 operations a step)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4650_gb300 import workloads as W
+from tests.dirac_algebra import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+C = W.C_AU
+DX = W.DX_DEFAULT
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1107_4650_gb300 import build as B
+    B.build()
+    oracle.build()
+    import paper_1107_4650_gb300 as D
+    D.load_library()
+    return D
+
+
+def run_gpu(D, psi, ndim, nsteps, V=None, periodic=False, fp32=False, K=0, P=0, flux_face=-1, graphs=True,
+            x_min=None, dx=DX, m=1.0):
+    nz, ny, nx, _ = psi.shape
+    cfg = D.make_config((nx, ny, nz), ndim=ndim, dx=dx, m=m, precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO, flux_face=flux_face,
+                        steps_per_launch=K, points_per_lane=P, use_graphs=graphs, x_min=x_min)
+    h = D.dirac_create_grid(cfg)
+    try:
+        if V is not None:
+            D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY if V.size == nx else D.DIRAC_V_FULL)
+        dt = np.complex64 if fp32 else np.complex128
+        D.dirac_set_state(h, np.ascontiguousarray(psi.astype(dt)))
+        D.dirac_step(h, nsteps)
+        out = np.empty(psi.shape, dtype=dt)
+        D.dirac_get_state(h, out)
+        obs = D.dirac_observables(h)
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    return out, obs, info
+
+
+def _bits_equal(a, b):
+    return np.array_equal(a.view(np.float64), b.view(np.float64))
+
+
+# ------------------------------------------------------------------ 2-D FP64, bit-exact
+
+@pytest.mark.parametrize("shape", [(70, 45), (130, 33), (5, 7), (64, 64)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("K,P", [(1, 1), (1, 2), (1, 4), (2, 2)])
+def test_2d_fp64_bit_exact_random(D, shape, periodic, K, P):
+    nx, nz = shape
+    psi = W.random_state(nz, 1, nx, seed=nx * 7 + nz)
+    V = np.random.default_rng(1).uniform(-2e4, 6e4, nx)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 7, V=V, periodic=periodic)
+    got, _, info = run_gpu(D, psi, 2, 7, V=V, periodic=periodic, K=K, P=P)
+    assert info["steps_per_launch"] == K and info["points_per_lane"] == P
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_2d_fp64_full_table_bit_exact(D, periodic):
+    nx, nz = 97, 61
+    psi = W.random_state(nz, 1, nx, seed=3)
+    V = np.random.default_rng(2).uniform(-5e4, 5e4, nx * nz)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 6, V=V, periodic=periodic)
+    got, _, _ = run_gpu(D, psi, 2, 6, V=V, periodic=periodic, K=2, P=2)
+    assert _bits_equal(got, want)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_config1_free_packet_256_200_steps(D, periodic):
+    """256^2 free positive-energy packet, width 20 dx, p0 = 0.5 mc, 200 steps."""
+    psi0 = W.positive_energy_packet_2d(256, 256, DX, 20 * DX, 0.5 * C)
+    want, _ = oracle.step(psi0, 2, 1.0, C, DX, 200, periodic=periodic)
+    got, obs, _ = run_gpu(D, psi0, 2, 200, periodic=periodic)
+    assert _bits_equal(got, want)
+    o = oracle.observables(want, 2, DX, (-128 * DX, 0.0, -128 * DX))
+    assert abs(obs["norm"] - o["norm"]) <= 1e-12 * o["norm"]
+    for d in (0, 2):
+        assert abs(obs["centroid"][d] - o["centroid"][d]) <= 1e-12 * 128 * DX
+
+
+def test_klein_flux_and_observables_match_oracle(D):
+    run = W.KleinRun(side=384, V0=2.5 * C * C, p0=0.6 * C, width=20 * DX, nsteps=300, face=240)
+    psi0 = run.state()
+    V = run.potential()
+    x_min, z_min, _, _, face = run.geometry()
+    want, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=V, flux_face=face)
+    for K in (1, 2):
+        got, obs, _ = run_gpu(D, psi0, 2, run.nsteps, V=V, K=K, flux_face=face, x_min=(x_min, 0.0, z_min))
+        assert _bits_equal(got, want)
+        o = oracle.observables(want, 2, DX, (x_min, 0.0, z_min), face)
+        assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+        assert abs(obs["norm_right"] - o["norm_right"]) <= 1e-12 * o["norm"]
+        assert abs(obs["norm"] - o["norm"]) <= 1e-12 * o["norm"]
+
+
+def test_cropped_klein_512_4000_steps(D):
+    """2-D Klein step at 512^2 for the full 4000 steps (the config's step count)."""
+    cfg = W.klein_config_2d(side=512, nsteps=4000)
+    run = W.KleinRun(side=512, V0=cfg.V0, p0=cfg.p0, width=25 * DX, nsteps=4000)
+    psi0 = run.state()
+    V = run.potential()
+    x_min, z_min, _, _, face = run.geometry()
+    want, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=V, flux_face=face)
+    got, obs, _ = run_gpu(D, psi0, 2, run.nsteps, V=V, flux_face=face, x_min=(x_min, 0.0, z_min))
+    assert rel_l2(got, want) <= 1e-12
+    assert _bits_equal(got, want)
+    assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+
+
+# ------------------------------------------------------------------ 3-D FP64, bit-exact
+
+@pytest.mark.parametrize("shape", [(40, 36, 33), (7, 5, 6), (70, 9, 12)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("P", [1, 2, 4])
+def test_3d_fp64_bit_exact_coulomb(D, shape, periodic, P):
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx + ny + nz)
+    x = W.cell_centres(nx, DX, -nx * DX / 2)
+    y = W.cell_centres(ny, DX, -ny * DX / 2)
+    z = W.cell_centres(nz, DX, -nz * DX / 2)
+    r2 = x[None, None, :] ** 2 + y[None, :, None] ** 2 + z[:, None, None] ** 2
+    V = (-10.0 / np.sqrt(r2 + (2 * DX) ** 2)).reshape(-1)
+    want, _ = oracle.step(psi, 3, 1.0, C, DX, 4, V=V, periodic=periodic)
+    got, _, _ = run_gpu(D, psi, 3, 4, V=V, periodic=periodic, P=P)
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+def test_3d_flux_and_x_only_table(D):
+    nx, ny, nz = 48, 20, 24
+    psi = W.random_state(nz, ny, nx, seed=44)
+    V = np.random.default_rng(5).uniform(0, 5e4, nx)
+    want, F = oracle.step(psi, 3, 1.0, C, DX, 5, V=V, flux_face=20)
+    got, obs, _ = run_gpu(D, psi, 3, 5, V=V, flux_face=20)
+    assert _bits_equal(got, want)
+    assert abs(obs["flux_cum"] - F) <= 1e-12 * max(abs(F), 1e-300) + 1e-300
+
+
+# ------------------------------------------------------------------ FP32 storage
+
+def test_2d_fp32_error_against_fp64_oracle(D):
+    psi0 = W.positive_energy_packet_2d(256, 256, DX, 20 * DX, 0.5 * C)
+    want, _ = oracle.step(psi0, 2, 1.0, C, DX, 200, periodic=False)
+    for K, P in ((1, 4), (2, 4), (4, 2), (4, 4)):
+        got, obs, _ = run_gpu(D, psi0, 2, 200, fp32=True, K=K, P=P)
+        err = rel_l2(got.astype(np.complex128), want)
+        assert err < 2e-5, (K, P, err)
+        o = oracle.observables(want, 2, DX)
+        assert abs(obs["norm"] - o["norm"]) < 1e-5
+
+
+def test_2d_fp32_klein_flux(D):
+    run = W.KleinRun(side=384, V0=2.5 * C * C, p0=0.6 * C, width=20 * DX, nsteps=300, face=240)
+    psi0 = run.state()
+    V = run.potential()
+    x_min, z_min, _, _, face = run.geometry()
+    want, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=V, flux_face=face)
+    got, obs, _ = run_gpu(D, psi0, 2, run.nsteps, V=V, fp32=True, flux_face=face, x_min=(x_min, 0.0, z_min))
+    assert rel_l2(got.astype(np.complex128), want) < 5e-5
+    assert abs(obs["flux_cum"] - F) < 1e-5 * abs(F) + 1e-9
+
+
+def test_3d_fp32_error(D):
+    nx, ny, nz = 40, 36, 33
+    psi = W.random_state(nz, ny, nx, seed=8)
+    V = np.random.default_rng(6).uniform(-5e4, 5e4, nx * ny * nz)
+    want, _ = oracle.step(psi, 3, 1.0, C, DX, 20, V=V)
+    got, _, _ = run_gpu(D, psi, 3, 20, V=V, fp32=True)
+    assert rel_l2(got.astype(np.complex128), want) < 2e-5
+
+
+# ------------------------------------------------------------------ runtime behaviour
+
+def test_graphs_and_direct_launches_agree_bitwise(D):
+    psi = W.random_state(300, 1, 260, seed=12)
+    a, oa, _ = run_gpu(D, psi, 2, 80, graphs=True, flux_face=100)
+    b, ob, _ = run_gpu(D, psi, 2, 80, graphs=False, flux_face=100)
+    assert _bits_equal(a, b) and oa["flux_cum"] == ob["flux_cum"]
+
+
+def test_deterministic_repeat(D):
+    psi = W.random_state(200, 1, 300, seed=13)
+    a, oa, _ = run_gpu(D, psi, 2, 50, fp32=True, flux_face=150)
+    b, ob, _ = run_gpu(D, psi, 2, 50, fp32=True, flux_face=150)
+    assert np.array_equal(a.view(np.float32), b.view(np.float32))
+    assert oa == ob
+
+
+def test_checkpoint_resume_is_bitwise(D):
+    nx, nz = 200, 150
+    psi = W.random_state(nz, 1, nx, seed=14)
+    V = np.random.default_rng(9).uniform(0, 4e4, nx)
+    full, of, _ = run_gpu(D, psi, 2, 90, V=V, flux_face=90)
+    cfg = D.make_config((nx, 1, nz), flux_face=90)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi)
+        D.dirac_step(h, 37)
+        mid = np.empty_like(psi)
+        D.dirac_get_state(h, mid)
+        o_mid = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, mid)
+        D.dirac_set_counters(h, o_mid["step"], o_mid["flux_cum"])
+        D.dirac_step(h, 53)
+        end = np.empty_like(psi)
+        D.dirac_get_state(h, end)
+        o_end = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(end, full)
+    assert o_end["step"] == 90 and o_end["flux_cum"] == of["flux_cum"]
+
+
+def test_device_pointers_via_torch(D):
+    torch = pytest.importorskip("torch")
+    psi = W.random_state(64, 1, 96, seed=15)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 5)
+    stream = torch.cuda.Stream()
+    cfg = D.make_config((96, 1, 64), stream=stream.cuda_stream)
+    h = D.dirac_create_grid(cfg)
+    try:
+        t_in = torch.from_numpy(psi.view(np.float64)).cuda()
+        torch.cuda.synchronize()
+        D.dirac_set_state(h, t_in)
+        D.dirac_step(h, 5)
+        t_out = torch.empty_like(t_in)
+        D.dirac_get_state(h, t_out)
+        stream.synchronize()
+        dens = torch.empty((64, 1, 96), dtype=torch.float64, device="cuda")
+        D.dirac_observables(h, dens)
+    finally:
+        D.dirac_destroy(h)
+    got = t_out.cpu().numpy().view(np.complex128).reshape(psi.shape)
+    assert _bits_equal(got, want)
+    assert np.allclose(dens.cpu().numpy(), oracle.density(want), rtol=1e-14, atol=0)
+
+
+def test_nonfinite_state_is_reported(D):
+    psi = W.random_state(16, 1, 16, seed=16)
+    psi[3, 0, 4, 2] = np.nan
+    cfg = D.make_config((16, 1, 16))
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_state(h, psi)
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_observables(h)
+        assert e.value.status == D.DIRAC_ERR_NONFINITE
+    finally:
+        D.dirac_destroy(h)
+
+
+def test_autotune_preserves_state_and_result(D):
+    nx, nz = 512, 384
+    psi = W.random_state(nz, 1, nx, seed=17)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 12)
+    cfg = D.make_config((nx, 1, nz))
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_state(h, psi)
+        D.dirac_autotune(h)
+        D.dirac_step(h, 12)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+        assert D.dirac_observables(h)["step"] == 12
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want)
