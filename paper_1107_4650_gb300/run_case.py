@@ -1,0 +1,84 @@
+"""Runs one Klein-step case through libdirac with a fixed launch plan and prints its timing.
+
+  python -m paper_1107_4650_gb300.run_case --precision fp64 --side 2048 --nsteps 64 [--k 1 --p 4]
+
+Used to profile one kernel configuration (no autotuning, no CPU work after the setup) and for quick
+size sweeps.  The state is the 2-D Klein workload of the benchmark at the given side.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--side", type=int, default=2048)
+    ap.add_argument("--nsteps", type=int, default=64)
+    ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--k", type=int, default=0, help="steps per launch (0: library choice)")
+    ap.add_argument("--p", type=int, default=0, help="points per lane (0: library choice)")
+    ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--ndim", type=int, default=2)
+    args = ap.parse_args()
+
+    import torch
+
+    import paper_1107_4650_gb300 as D
+    from paper_1107_4650_gb300 import build as B
+    from paper_1107_4650_gb300 import workloads as W
+
+    B.build()
+    D.load_library()
+    prec = D.DIRAC_FP32 if args.precision == "fp32" else D.DIRAC_FP64
+    stream = torch.cuda.Stream()
+    if args.ndim == 2:
+        run = W.klein_config_2d(side=args.side, nsteps=args.nsteps)
+        x_min, z_min, _, _, face = run.geometry()
+        psi = run.state()
+        V = run.potential()
+        shape = (args.side, 1, args.side)
+        cfg = D.make_config(shape, x_min=(x_min, 0.0, z_min), flux_face=face, precision=prec,
+                            stream=stream.cuda_stream, steps_per_launch=args.k, points_per_lane=args.p,
+                            use_graphs=not args.no_graphs)
+        layout = D.DIRAC_V_X_ONLY
+    else:
+        n = args.side
+        dx = W.DX_DEFAULT
+        psi = W.gaussian_packet(n, n, dx, -n * dx / 2, -n * dx / 2, 32 * dx, 0.0, 16 * dx, 0.0, ny=n, y_min=-n * dx / 2)
+        V = W.soft_coulomb_3d(n, dx, 10.0, 2 * dx).reshape(-1)
+        shape = (n, n, n)
+        cfg = D.make_config(shape, ndim=3, precision=prec, stream=stream.cuda_stream, points_per_lane=args.p,
+                            use_graphs=not args.no_graphs)
+        layout = D.DIRAC_V_FULL
+    h = D.dirac_create_grid(cfg)
+    D.dirac_set_potential(h, V, layout)
+    host = np.ascontiguousarray(psi.astype(np.complex64 if prec == D.DIRAC_FP32 else np.complex128))
+    D.dirac_set_state(h, host)
+    times = []
+    for _ in range(args.repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        D.dirac_step(h, args.nsteps)
+        e1.record(stream)
+        stream.synchronize()
+        times.append(e0.elapsed_time(e1))
+    obs = D.dirac_observables(h)
+    info = D.dirac_get_info(h)
+    D.dirac_destroy(h)
+    cells = shape[0] * shape[1] * shape[2]
+    best = min(times)
+    print(json.dumps({"precision": args.precision, "ndim": args.ndim, "side": args.side, "nsteps": args.nsteps,
+                      "ms": best, "point_steps_per_s": cells * args.nsteps / (best / 1e3),
+                      "k": info["steps_per_launch"], "p": info["points_per_lane"],
+                      "warps": info["launch_warps"], "seg_rows": info["segment_rows"], "norm": obs["norm"],
+                      "flux": obs["flux_cum"]}))
+
+
+if __name__ == "__main__":
+    t0 = time.time()
+    main()
