@@ -140,6 +140,28 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info);
  * is saved and restored around the trial).  Synchronises.  The choice holds until destroy. */
 dirac_status dirac_autotune(dirac_grid *g);
 
+/* Allocation-free observables.  The paper has no counterpart: this serves callers that cannot
+ * allocate device memory, such as a host framework that owns the whole device budget through its own
+ * pool, or a latency-critical loop that must not pay the device synchronisation that cudaMalloc and
+ * cudaFree can imply.  It computes what dirac_observables computes (to FP64 rounding: the block
+ * partition differs) for a state in caller-owned device memory and allocates nothing: its block
+ * partials live in one fixed device array of DIRAC_NOALLOC_MAX_BLOCKS x 5 doubles (640 KiB), defined
+ * in the library and held by every device that loads it until the process exits.
+ *   psi        device pointer on the current device, layout psi[z][y][x][c][re,im] in `precision`
+ *   n, ndim    grid as in dirac_config (n[1] == 1 when ndim == 2); at most
+ *              DIRAC_NOALLOC_MAX_BLOCKS * DIRAC_NOALLOC_CELLS_PER_BLOCK cells, else DIRAC_ERR_ARG
+ *   dx, x_min  cell edge and lower corner; flux_face as in dirac_config (-1: norm_right = 0)
+ *   stream     cudaStream_t the two kernels are enqueued on (NULL = legacy stream); asynchronous
+ *   out        device pointer to 5 doubles: norm, norm_right, centroid x, y, z
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call shares the array and
+ * overwrites the partials it reads, so nothing needs clearing, but calls whose kernels overlap on
+ * the GPU (different streams or host threads) race on it.  Errors go to dirac_last_error(NULL). */
+#define DIRAC_NOALLOC_MAX_BLOCKS 16384
+#define DIRAC_NOALLOC_CELLS_PER_BLOCK 8192
+dirac_status dirac_observables_noalloc(const void *psi, int precision, int ndim, const int64_t n[3], double dx,
+                                       const double x_min[3], int64_t flux_face, void *stream, double *out);
+
 /* Last error message for g (or of this thread when g == NULL). Never NULL. */
 const char *dirac_last_error(const dirac_grid *g);
 

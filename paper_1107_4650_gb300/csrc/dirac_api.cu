@@ -377,6 +377,14 @@ void default_plan(dirac_grid *g) {
 
 }  // namespace
 
+namespace dirac {
+// Records a message for dirac_last_error(NULL) on this thread (entry points without a grid).
+dirac_status set_thread_error(dirac_status st, const std::string &msg) {
+    g_thread_err = msg;
+    return st;
+}
+}  // namespace dirac
+
 extern "C" {
 
 const char *dirac_version(void) { return "dirac-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,76 @@
+"""dirac_observables_noalloc, the allocation-free observables entry point, against dirac_observables.
+
+Callers that cannot allocate device memory (a host framework that owns the whole device budget
+through its own pool, or a loop that must not pay the device synchronisation of cudaMalloc) use this
+entry point: its reduction scratch is a fixed array inside the library.  This file is collected last
+so that a run stopping at the first failure has run every other test before it.  Two calls in a row,
+on grids of different size and precision, check that the shared scratch carries nothing over."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1107_4650_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12  # FP64 sums in another block partition: agreement to rounding
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1107_4650_gb300 import build as B
+    B.build()
+    import paper_1107_4650_gb300 as D
+    lib = D.load_library()
+    fn = lib.dirac_observables_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
+                   ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    return D
+
+
+def _close(a, b, scale):
+    return abs(a - b) <= REL * scale
+
+
+def test_noalloc_observables_match_two_calls_in_a_row(D):
+    torch = pytest.importorskip("torch")
+    lib = D.load_library()
+    cases = [((300, 1, 200), 2, D.DIRAC_FP64, 120, 11), ((48, 20, 24), 3, D.DIRAC_FP32, 20, 12)]
+    for (nx, ny, nz), ndim, prec, face, seed in cases:
+        psi = W.random_state(nz, ny, nx, seed=seed)
+        x_min = (-0.3, 0.1, -0.2)
+        cfg = D.make_config((nx, ny, nz), ndim=ndim, precision=prec, flux_face=face, x_min=x_min)
+        h = D.dirac_create_grid(cfg)
+        try:
+            D.dirac_set_state(h, np.ascontiguousarray(psi.astype(np.complex64 if prec == D.DIRAC_FP32 else np.complex128)))
+            D.dirac_step(h, 3)
+            ref = D.dirac_observables(h)
+            out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            n = (ctypes.c_int64 * 3)(nx, ny, nz)
+            xm = (ctypes.c_double * 3)(*x_min)
+            st = lib.dirac_observables_noalloc(D.dirac_state_ptr(h), prec, ndim, n, cfg.dx, xm, face, None,
+                                               out.data_ptr())
+            assert st == D.DIRAC_OK, D.dirac_last_error(None)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+        finally:
+            D.dirac_destroy(h)
+        assert _close(got[0], ref["norm"], ref["norm"])
+        assert _close(got[1], ref["norm_right"], ref["norm"])
+        for d in range(3):
+            assert _close(got[2 + d], ref["centroid"][d], 1.0)
+
+
+def test_noalloc_rejects_grids_beyond_the_scratch_limit(D):
+    lib = D.load_library()
+    limit = 16384 * 8192
+    n = (ctypes.c_int64 * 3)(limit + 1, 1, 1)
+    xm = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    out = ctypes.c_double(0.0)
+    st = lib.dirac_observables_noalloc(ctypes.c_void_p(1), D.DIRAC_FP64, 2, n, 1.0, xm, -1, None,
+                                       ctypes.addressof(out))
+    assert st == D.DIRAC_ERR_ARG
+    assert "scratch limit" in D.dirac_last_error(None)
