@@ -254,6 +254,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s) {
     a.flux_part = g->flux_part;
     a.flux_cum = g->flux_dev;
     a.ticket = g->ticket;
+    a.err = g->ticket + 1;
     a.vol = cell_volume(g);
     a.periodic = g->cfg.boundary == DIRAC_BC_PERIODIC;
     a.full_table = g->table_full;
@@ -368,7 +369,7 @@ void default_plan(dirac_grid *g) {
         make_plan(g, 1, pp > 0 ? pp : 2, 4, 16);
         return;
     }
-    int K = g->fp32 ? 4 : 1, P = g->fp32 ? 4 : 2;
+    int K = g->fp32 ? 2 : 1, P = g->fp32 ? 2 : 4;
     if (k > 0) K = k;
     if (pp > 0) P = pp;
     if (!sweep_supported(g->fp32, 0, K, P)) P = sweep_supported(g->fp32, 0, K, 4) ? 4 : 2;
@@ -610,6 +611,7 @@ dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, i
     g->launches += 2;
     CK(g, cudaMemcpyAsync(g->host_obs, g->obs_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     CK(g, cudaMemcpyAsync(&g->host_obs[5], g->flux_dev, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(g, cudaMemcpyAsync(&g->host_obs[6], g->ticket + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
     if (density && !density_on_device)
         CK(g, cudaMemcpyAsync(density, dens, (size_t)g->ncells * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     CK(g, cudaStreamSynchronize(g->stream));
@@ -622,6 +624,9 @@ dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, i
     obs->centroid[1] = h[0] > 0 ? h[3] / h[0] : 0.0;
     obs->centroid[2] = h[0] > 0 ? h[4] / h[0] : 0.0;
     obs->step = g->step;
+    unsigned kerr = 0;
+    std::memcpy(&kerr, &g->host_obs[6], sizeof(unsigned));
+    if (kerr) return fail(g, DIRAC_ERR_TIMEOUT, "a step kernel's bounded wait for a row copy ran out; the state is invalid");
     if (!std::isfinite(obs->norm)) return fail(g, DIRAC_ERR_NONFINITE, "state holds NaN or Inf");
     return DIRAC_OK;
 }
@@ -652,13 +657,13 @@ dirac_status dirac_autotune(dirac_grid *g) {
         for (int P : {1, 2, 4})
             for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm});
     } else if (g->fp32) {
-        const int KP[][2] = {{1, 4}, {2, 4}, {4, 2}, {4, 4}};
+        const int KP[][2] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}};
         for (auto &kp : KP)
-            for (int wsm : {4, 8, 12, 16}) cands.push_back({kp[0], kp[1], 4, wsm});
+            for (int wsm : {8, 12, 16}) cands.push_back({kp[0], kp[1], 4, wsm});
     } else {
-        const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
+        const int KP[][2] = {{1, 2}, {1, 4}, {2, 2}};
         for (auto &kp : KP)
-            for (int wsm : {2, 4, 8, 16}) cands.push_back({kp[0], kp[1], 4, wsm});
+            for (int wsm : {4, 8, 12}) cands.push_back({kp[0], kp[1], 4, wsm});
     }
     // save state and counters
     const size_t bytes = (size_t)g->ncells * 8 * g->elem;

@@ -27,6 +27,7 @@ struct SweepArgs {
     double *flux_part;     // [K][nplanes*nsegs] per-step face-flux partial sums (unscaled)
     double *flux_cum;      // cumulative flux; the last block of a launch adds vol * (sum of each step)
     unsigned *ticket;      // block-completion counter, 0 between launches (the last block resets it)
+    unsigned *err;         // set non-zero by a kernel whose bounded wait ran out
     double vol;            // cell volume dx^d
     int periodic;
     int full_table;

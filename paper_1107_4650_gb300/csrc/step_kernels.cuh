@@ -115,9 +115,10 @@ __device__ __forceinline__ int64_t pmod(int64_t a, int64_t n) {
 }
 
 template <typename T, int K, int P, int MODE>
-__device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane);
+__device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem);
 template <int K>
 __device__ __forceinline__ void finish_flux(const SweepArgs &a);
+template <typename T, int K, int P> struct Ring;
 
 // MODE 0: 2-D step (x sweep, z sweep, phase), K steps per launch.
 // MODE 1: 3-D x-y pass (x sweep, y sweep), K must be 1.
@@ -126,8 +127,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t per_plane = a.nstrips * a.nsegs;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    unsigned char *wsmem = dyn_smem + (threadIdx.x >> 5) * Ring<T, K, P>::WARP_BYTES;
     // Warps past the end skip the work but still reach the block-completion ticket below.
-    if (wid < per_plane * a.nplanes) sweep_warp<T, K, P, MODE>(a, wid, lane);
+    if (wid < per_plane * a.nplanes) sweep_warp<T, K, P, MODE>(a, wid, lane, wsmem);
     if (a.flux_face >= 0) finish_flux<K>(a);
 }
 
@@ -159,8 +162,57 @@ __device__ __forceinline__ void finish_flux(const SweepArgs &a) {
     }
 }
 
+// ---- TMA bulk-copy row ring (per warp).  Lane 0 issues one cp.async.bulk per row into a ring slot,
+// armed with mbarrier expect_tx; every lane waits on the slot's mbarrier phase before reading it.
+// All waits are bounded: on expiry the kernel raises a flag in *a.err and drains its own copies.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity to complete (~0.5 s at most).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+// Per-warp shared memory: 128 B of mbarriers, the row ring, then the flux hand-off area
+// (K levels x 8 values x 32 lanes).
+template <typename T, int K, int P> struct Ring {
+    static constexpr int ROW_BYTES = 32 * P * 8 * (int)sizeof(T);  // one warp row: 32P cells
+    static constexpr int SLOTS = ROW_BYTES >= 8192 ? 3 : 4;
+    static constexpr int FLUX_BYTES = K * 8 * 32 * (int)sizeof(T);
+    static constexpr int WARP_BYTES = 128 + SLOTS * ROW_BYTES + FLUX_BYTES;
+};
+
+// Dynamic shared memory a block of `wpb` warps needs.
+template <typename T, int K, int P> constexpr int ring_smem_bytes(int wpb) { return wpb * Ring<T, K, P>::WARP_BYTES; }
+
 template <typename T, int K, int P, int MODE>
-__device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane) {
+__device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem) {
     const int64_t per_plane = a.nstrips * a.nsegs;
     const int64_t plane = wid / per_plane;
     const int64_t rem = wid - plane * per_plane;
@@ -168,6 +220,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     const int64_t strip = rem - seg * a.nstrips;
     const int64_t nx = a.nx, nr = a.nr;
     const bool per = a.periodic != 0;
+    const bool ring = !per;  // periodic grids wrap the strip: plain loads
     const int64_t x_own0 = strip * a.strip_w;
     const int64_t x_own1 = min(x_own0 + a.strip_w, nx);
     const int64_t xa = x_own0 - K;
@@ -190,14 +243,13 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
 #pragma unroll
         for (int j = 0; j < P; ++j) load_tab(static_cast<const T *>(a.table) + xl[j] * 4, pu[j], pd[j]);
     }
-    // flux: the lane/point holding x == face (owned by this strip) sums
-    // 1/2(|u14|^2+|u23|^2)(face-1) - 1/2(|w14|^2+|w23|^2)(face) per row.
-    int fj = -1;
-    if (a.flux_face >= x_own0 && a.flux_face < x_own1) {
-#pragma unroll
-        for (int j = 0; j < P; ++j)
-            if (xa + 32 * j + lane == a.flux_face) fj = j;
-    }
+    // Flux through the face (owned by this strip): per row, 1/2(|u14|^2+|u23|^2) at face-1 minus
+    // 1/2(|w14|^2+|w23|^2) at face.  The face lane's 8 values of row q are handed to lane (q - r_begin) % 32;
+    // every 32 rows all lanes evaluate their row at once, so the FP64 work runs SIMT-wide (1/32 of the FP64
+    // issue a single lane would need).  Each lane accumulates its rows in FP64; a fixed xor tree adds lanes.
+    const bool has_face = a.flux_face >= x_own0 && a.flux_face < x_own1;
+    const int face_off = (int)(a.flux_face - xa);
+    const int face_lane = face_off & 31, face_j = face_off >> 5;
     double facc[K];
 #pragma unroll
     for (int s = 0; s < K; ++s) facc[s] = 0.0;
@@ -216,22 +268,74 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
 
     const int src_prev = (lane + 31) & 31, src_next = (lane + 1) & 31;
 
-    for (int64_t r = r_begin - K; r < r_end + K; ++r) {
+    // Row ring: the copied span of a row is the strip's cells clipped to the grid.
+    using RG = Ring<T, K, P>;
+    T *gsm = reinterpret_cast<T *>(wsmem + 128 + RG::SLOTS * RG::ROW_BYTES);  // flux hand-off [K][8][32]
+    const int64_t cx0 = max(xa, (int64_t)0), cx1 = min(xa + 32 * P, nx);
+    const uint32_t copy_bytes = (uint32_t)((cx1 - cx0) * 8 * (int64_t)sizeof(T));
+    const uint32_t bar0 = smem_u32(wsmem);
+    const uint32_t slot0 = smem_u32(wsmem + 128);
+    const uint32_t dst_off = (uint32_t)((cx0 - xa) * 8 * (int64_t)sizeof(T));
+    const int64_t r_first = r_begin - K, r_last = r_end + K;  // rows [r_first, r_last) are read
+    uint32_t phase_bits = 0, pending = 0;
+    bool aborted = false;
+    if (ring) {
+        if (lane == 0) {
+#pragma unroll
+            for (int sl = 0; sl < RG::SLOTS; ++sl) mbar_init(bar0 + 8 * sl, 1);
+            mbar_fence_init();
+        }
+        __syncwarp();
+#pragma unroll
+        for (int sl = 0; sl < RG::SLOTS; ++sl) {
+            const int64_t r = r_first + sl;
+            if (r < r_last && r >= 0 && r < nr) {
+                if (lane == 0) bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + (r * nx + cx0) * 8, copy_bytes, bar0 + 8 * sl);
+                pending |= 1u << sl;
+            }
+        }
+    }
+
+    int sl = 0;
+    for (int64_t r = r_first; r < r_last; ++r) {
         Cx<T> st[P][4];
         const bool row_ok = per || (r >= 0 && r < nr);
         const int64_t rl = per ? pmod(r, nr) : r;
+        if (ring) {
+            if (row_ok) {
+                if (!mbar_wait(bar0 + 8 * sl, (phase_bits >> sl) & 1u)) {
+                    aborted = true;
+                    break;
+                }
+                phase_bits ^= 1u << sl;
+                pending &= ~(1u << sl);
+            }
+            const T *srow = reinterpret_cast<const T *>(wsmem + 128 + sl * RG::ROW_BYTES);
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-            if (row_ok && (per || xin[j])) {
-                load_pt(in + (rl * nx + xl[j]) * 8, st[j]);
-            } else {
+            for (int j = 0; j < P; ++j) {
+                if (row_ok && xin[j]) {
+                    load_pt(srow + (32 * j + lane) * 8, st[j]);
+                } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) st[j][c] = {T(0), T(0)};
+                    for (int c = 0; c < 4; ++c) st[j][c] = {T(0), T(0)};
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                if (row_ok && (per || xin[j])) {
+                    load_pt(in + (rl * nx + xl[j]) * 8, st[j]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) st[j][c] = {T(0), T(0)};
+                }
             }
         }
 #pragma unroll
         for (int lev = 0; lev < K; ++lev) {
             const int64_t q = r - lev;  // row of the level-lev state in st
+            // rows of level lev+1 that later levels (or the store) use: [r_first + lev + 1, r_last - lev - 1)
+            const bool need_out = (q - 1 >= r_first + lev + 1) && (q - 1 < r_last - lev - 1);
             Cx<T> u14[P], u23[P], w14[P], w23[P];
 #pragma unroll
             for (int j = 0; j < P; ++j) {
@@ -258,14 +362,30 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 rw14[j] = (lane == 31) ? nw14[jn] : nw14[j];
                 rw23[j] = (lane == 31) ? nw23[jn] : nw23[j];
             }
-            if (fj >= 0 && q >= r_begin && q < r_end) {
+            if (has_face && q >= r_begin && q < r_end) {
+                T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
-                    if (j == fj) {
-                        const double right = __dmul_rn(0.5, __dadd_rn(abs2d(lu14[j]), abs2d(lu23[j])));
-                        const double left = __dmul_rn(0.5, __dadd_rn(abs2d(w14[j]), abs2d(w23[j])));
+                    if (j == face_j) {
+                        v[0] = lu14[j].re; v[1] = lu14[j].im; v[2] = lu23[j].re; v[3] = lu23[j].im;
+                        v[4] = w14[j].re;  v[5] = w14[j].im;  v[6] = w23[j].re;  v[7] = w23[j].im;
+                    }
+                }
+                const int t = (int)((q - r_begin) & 31);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const T x = __shfl_sync(0xffffffffu, v[k], face_lane);
+                    if (lane == t) gsm[(lev * 8 + k) * 32 + t] = x;
+                }
+                if (t == 31 || q == r_end - 1) {
+                    __syncwarp();
+                    if (lane <= t) {
+                        const T *gl = gsm + lev * 8 * 32 + lane;
+                        const double right = __dmul_rn(0.5, __dadd_rn(abs2d(Cx<T>{gl[0], gl[32]}), abs2d(Cx<T>{gl[64], gl[96]})));
+                        const double left = __dmul_rn(0.5, __dadd_rn(abs2d(Cx<T>{gl[128], gl[160]}), abs2d(Cx<T>{gl[192], gl[224]})));
                         facc[lev] = __dadd_rn(facc[lev], __dsub_rn(right, left));
                     }
+                    __syncwarp();
                 }
             }
             const bool out_row_ok = per || (q - 1 >= 0 && q - 1 < nr);
@@ -280,44 +400,53 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 if (MODE == 0) {
                     // z sweep (Eq. sol_dis_3): +z movers (b1+b3, b2-b4), -z movers (b1-b3, b2+b4)
                     const Cx<T> U13 = cadd(b0, b2), U24 = csub(b1, b3);
-                    const Cx<T> W13 = csub(b0, b2), W24 = cadd(b1, b3);
-                    o[0] = cadd(UA[lev][j][0], W13);
-                    o[2] = csub(UA[lev][j][0], W13);
-                    o[1] = cadd(UA[lev][j][1], W24);
-                    o[3] = csub(W24, UA[lev][j][1]);
+                    if (need_out) {
+                        const Cx<T> W13 = csub(b0, b2), W24 = cadd(b1, b3);
+                        o[0] = cadd(UA[lev][j][0], W13);
+                        o[2] = csub(UA[lev][j][0], W13);
+                        o[1] = cadd(UA[lev][j][1], W24);
+                        o[3] = csub(W24, UA[lev][j][1]);
+                        // phase (Eq. sol_dis_4, A = 0) with the deferred 1/4
+                        Cx<T> qu, qd;
+                        if (a.full_table) {
+                            const int64_t rr = per ? pmod(q - 1, nr) : min(max(q - 1, (int64_t)0), nr - 1);
+                            load_tab(static_cast<const T *>(a.table) + (plane * nr * nx + rr * nx + xl[j]) * 4, qu, qd);
+                        } else {
+                            qu = pu[j];
+                            qd = pd[j];
+                        }
+                        o[0] = cmulp(o[0], qu);
+                        o[1] = cmulp(o[1], qu);
+                        o[2] = cmulp(o[2], qd);
+                        o[3] = cmulp(o[3], qd);
+                    }
                     UA[lev][j][0] = UB[lev][j][0];
                     UA[lev][j][1] = UB[lev][j][1];
                     UB[lev][j][0] = U13;
                     UB[lev][j][1] = U24;
-                    // phase (Eq. sol_dis_4, A = 0) with the deferred 1/4
-                    Cx<T> qu, qd;
-                    if (a.full_table) {
-                        const int64_t rr = per ? pmod(q - 1, nr) : min(max(q - 1, (int64_t)0), nr - 1);
-                        load_tab(static_cast<const T *>(a.table) + (plane * nr * nx + rr * nx + xl[j]) * 4, qu, qd);
-                    } else {
-                        qu = pu[j];
-                        qd = pd[j];
-                    }
-                    o[0] = cmulp(o[0], qu);
-                    o[1] = cmulp(o[1], qu);
-                    o[2] = cmulp(o[2], qd);
-                    o[3] = cmulp(o[3], qd);
                 } else {
                     // y sweep (Eq. sol_dis_2): +y movers (b1 - i b4, b2 + i b3), -y movers (b1 + i b4, b2 - i b3)
                     const Cx<T> U14 = csub_ib(b0, b3), U23 = cadd_ib(b1, b2);
-                    const Cx<T> W14 = cadd_ib(b0, b3), W23 = csub_ib(b1, b2);
-                    o[0] = cadd(UA[lev][j][0], W14);
-                    o[3] = cmul_i(csub(UA[lev][j][0], W14));
-                    o[1] = cadd(UA[lev][j][1], W23);
-                    o[2] = cmul_mi(csub(UA[lev][j][1], W23));
+                    if (need_out) {
+                        const Cx<T> W14 = cadd_ib(b0, b3), W23 = csub_ib(b1, b2);
+                        o[0] = cadd(UA[lev][j][0], W14);
+                        o[3] = cmul_i(csub(UA[lev][j][0], W14));
+                        o[1] = cadd(UA[lev][j][1], W23);
+                        o[2] = cmul_mi(csub(UA[lev][j][1], W23));
+                    }
                     UA[lev][j][0] = UB[lev][j][0];
                     UA[lev][j][1] = UB[lev][j][1];
                     UB[lev][j][0] = U14;
                     UB[lev][j][1] = U23;
                 }
-                const bool keep = per || (out_row_ok && xin[j]);
+                if (need_out) {
+                    const bool keep = per || (out_row_ok && xin[j]);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) st[j][c] = keep ? o[c] : Cx<T>{T(0), T(0)};
+                    for (int c = 0; c < 4; ++c) st[j][c] = keep ? o[c] : Cx<T>{T(0), T(0)};
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) st[j][c] = Cx<T>{T(0), T(0)};
+                }
             }
         }
         const int64_t ro = r - K;
@@ -328,8 +457,30 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 if (x >= x_own0 && x < x_own1) store_pt(out + (ro * nx + x) * 8, st[j]);
             }
         }
+        if (ring) {
+            // refill this slot with row r + SLOTS once every lane has read it
+            __syncwarp();
+            const int64_t rn = r + RG::SLOTS;
+            if (rn < r_last && rn >= 0 && rn < nr) {
+                if (lane == 0) {
+                    fence_proxy_async();
+                    bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + (rn * nx + cx0) * 8, copy_bytes, bar0 + 8 * sl);
+                }
+                pending |= 1u << sl;
+            }
+            sl = (sl + 1 == RG::SLOTS) ? 0 : sl + 1;
+        }
     }
-    if (a.flux_face >= x_own0 && a.flux_face < x_own1) {
+    if (aborted) {
+        // a copy never completed: report, then wait (bounded) for this warp's copies still in flight
+        if (lane == 0) atomicOr(a.err, 1u);
+#pragma unroll
+        for (int s2 = 0; s2 < RG::SLOTS; ++s2)
+            if (pending & (1u << s2)) mbar_wait(bar0 + 8 * s2, (phase_bits >> s2) & 1u);
+        __syncwarp();
+        return;
+    }
+    if (has_face) {
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             double v = facc[s];

@@ -9,7 +9,18 @@ static cudaError_t launch_one(const SweepArgs &a, int wpb, cudaStream_t s) {
     const int64_t warps = a.nstrips * a.nsegs * a.nplanes;
     const int64_t blocks = (warps + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
-    sweep_kernel<T, K, P, MODE><<<(unsigned)blocks, 32 * wpb, 0, s>>>(a);
+    const int smem = ring_smem_bytes<T, K, P>(wpb);
+    // opt in to > 48 KB of dynamic shared memory, once per device and block size
+    static unsigned long long done[4] = {0, 0, 0, 0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = (wpb == 4) ? 0 : (wpb == 2) ? 1 : (wpb == 8) ? 2 : 3;
+    if (dev >= 64 || slot == 3 || !(done[slot] & (1ull << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, K, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64 && slot != 3) done[slot] |= 1ull << dev;
+    }
+    sweep_kernel<T, K, P, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
     return cudaGetLastError();
 }
 
