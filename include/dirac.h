@@ -140,6 +140,92 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info);
  * is saved and restored around the trial).  Synchronises.  The choice holds until destroy. */
 dirac_status dirac_autotune(dirac_grid *g);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched ensemble: many independent 2-D Klein-step scattering runs (Sec. 5.2) of uneven grid sizes
+ * and step counts, advanced together by one persistent kernel per block of steps_per_launch steps
+ * (warps take (run, strip, segment) tasks from an atomic queue), the launch sequence replayed from a
+ * CUDA graph.  Each run is the single-grid scheme of dirac_step on a side x side x-z grid with the
+ * zero boundary, the tanh step V(x) = V0/2 [1 + tanh(x/L)] centred on its flux face (x = 0 there)
+ * and the Gaussian packet [1, 0, 0, C] e^{i p0 x} exp(-((x-x0)^2 + z^2)/(4 width^2)) of Sec. 5.2.2
+ * (z = 0 mid-grid).  The result of a run is its transmission T = cumulative face flux / initial norm
+ * (R = 1 - T: the boundary is outflowing).  Cell (i, k) of a run has centre
+ * ((i - face + 1/2) dx, (k - side/2 + 1/2) dx).
+ * --------------------------------------------------------------------------------------------- */
+typedef struct dirac_batch dirac_batch; /* opaque, library-owned */
+
+typedef struct {
+    int64_t side;   /* cells per side, >= 8 */
+    int64_t face;   /* flux face / step position, in [1, side-1] */
+    int64_t nsteps; /* time steps of this run, >= 0 */
+    double V0;      /* step height (potential energy) */
+    double L;       /* step width, > 0 */
+    double p0;      /* packet momentum along x */
+    double width;   /* packet width, > 0 */
+    double x0;      /* packet centre along x (the step is at x = 0) */
+} dirac_klein_run;
+
+typedef struct {
+    int precision;          /* DIRAC_FP32 (the ensemble's storage) or DIRAC_FP64 */
+    double dx, c, m;        /* as in dirac_config; dt = dx / c */
+    void *stream;           /* cudaStream_t (NULL = legacy stream) */
+    int device;
+    int steps_per_launch;   /* 0 = library choice */
+    int points_per_lane;    /* 0 = library choice */
+    int64_t segment_rows;   /* rows per task; 0 = library choice */
+    int use_graphs;         /* 1: the launch sequence of dirac_batch_run is captured once and replayed */
+} dirac_batch_config;
+
+/* Defaults: FP32, dx = 10/8192, c = 137.0359895, m = 1, legacy stream, device 0, library tiles, graphs. */
+void dirac_batch_default_config(dirac_batch_config *cfg);
+
+/* Validates the runs, allocates every run's ping-pong state, phase table and flux scratch on the device
+ * and writes the initial packets.  Errors: DIRAC_ERR_ARG (bad run or config), DIRAC_ERR_OOM. */
+dirac_status dirac_batch_create(const dirac_klein_run *runs, int nruns, const dirac_batch_config *cfg,
+                                dirac_batch **out);
+dirac_status dirac_batch_destroy(dirac_batch *b);
+
+/* Writes the initial packets again and clears the fluxes (the batch can then run again). */
+dirac_status dirac_batch_reset(dirac_batch *b);
+
+/* Replaces run `run`'s initial state (layout of dirac_set_state, side x 1 x side cells) before
+ * dirac_batch_run; host buffers are copied before the call returns. */
+dirac_status dirac_batch_set_state(dirac_batch *b, int run, const void *psi, int on_device);
+
+/* Replaces run `run`'s x-only potential (side values, host pointer) by V; coefficients as in
+ * dirac_set_potential. */
+dirac_status dirac_batch_set_potential(dirac_batch *b, int run, const double *V, int64_t count);
+
+/* Advances every run by its nsteps (asynchronous on the batch stream); measures each run's initial norm
+ * first.  A second call needs dirac_batch_reset in between (DIRAC_ERR_STATE otherwise). */
+dirac_status dirac_batch_run(dirac_batch *b);
+
+/* Per-run results after dirac_batch_run (synchronises): T[r] = flux[r] / norm0[r]; any pointer may be NULL. */
+dirac_status dirac_batch_results(dirac_batch *b, double *T, double *flux, double *norm0);
+
+/* Copies run `run`'s current state out (after dirac_batch_run: its final state). */
+dirac_status dirac_batch_get_state(dirac_batch *b, int run, void *psi, int on_device);
+
+/* Chooses steps_per_launch, points_per_lane and segment_rows by timing trial launches on this batch, then
+ * writes the initial packets again (a state set with dirac_batch_set_state is lost). */
+dirac_status dirac_batch_autotune(dirac_batch *b);
+
+typedef struct {
+    int steps_per_launch, points_per_lane;
+    int64_t segment_rows;
+    int64_t launches;       /* kernel launches of one dirac_batch_run */
+    int64_t max_tasks;      /* tasks of the fullest launch */
+    int64_t point_steps;    /* sum over runs of side^2 x nsteps */
+    int blocks;             /* resident blocks of the persistent kernel */
+    size_t device_bytes;
+} dirac_batch_info;
+dirac_status dirac_batch_get_info(const dirac_batch *b, dirac_batch_info *info);
+const char *dirac_batch_last_error(const dirac_batch *b);
+
+/* One call: create, autotune (when cfg->steps_per_launch == 0), run, results, destroy.
+ * T_out and R_out (nullable) receive nruns values each. */
+dirac_status dirac_batch_klein(const dirac_klein_run *runs, int nruns, const dirac_batch_config *cfg, double *T_out,
+                               double *R_out);
+
 /* Allocation-free observables.  The paper has no counterpart: this serves callers that cannot
  * allocate device memory, such as a host framework that owns the whole device budget through its own
  * pool, or a latency-critical loop that must not pay the device synchronisation that cudaMalloc and

@@ -213,3 +213,139 @@ def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRA
     cfg.use_graphs = 1 if use_graphs else 0
     cfg.points_per_lane = points_per_lane
     return cfg
+
+
+# ----------------------------------------------------------------------------- batched ensemble
+
+class dirac_klein_run(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int64), ("face", ctypes.c_int64), ("nsteps", ctypes.c_int64),
+                ("V0", ctypes.c_double), ("L", ctypes.c_double), ("p0", ctypes.c_double),
+                ("width", ctypes.c_double), ("x0", ctypes.c_double)]
+
+
+class dirac_batch_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("dx", ctypes.c_double), ("c", ctypes.c_double),
+                ("m", ctypes.c_double), ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("steps_per_launch", ctypes.c_int), ("points_per_lane", ctypes.c_int),
+                ("segment_rows", ctypes.c_int64), ("use_graphs", ctypes.c_int)]
+
+
+class dirac_batch_info(ctypes.Structure):
+    _fields_ = [("steps_per_launch", ctypes.c_int), ("points_per_lane", ctypes.c_int),
+                ("segment_rows", ctypes.c_int64), ("launches", ctypes.c_int64), ("max_tasks", ctypes.c_int64),
+                ("point_steps", ctypes.c_int64), ("blocks", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+
+
+def _batch_lib():
+    lib = load_library()
+    if getattr(lib, "_batch_sigs", False):
+        return lib
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    DP = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "dirac_batch_default_config": (None, [ctypes.POINTER(dirac_batch_config)]),
+        "dirac_batch_create": (I, [ctypes.POINTER(dirac_klein_run), I, ctypes.POINTER(dirac_batch_config),
+                                   ctypes.POINTER(P)]),
+        "dirac_batch_destroy": (I, [P]),
+        "dirac_batch_reset": (I, [P]),
+        "dirac_batch_set_state": (I, [P, I, P, I]),
+        "dirac_batch_set_potential": (I, [P, I, P, I64]),
+        "dirac_batch_run": (I, [P]),
+        "dirac_batch_results": (I, [P, DP, DP, DP]),
+        "dirac_batch_get_state": (I, [P, I, P, I]),
+        "dirac_batch_autotune": (I, [P]),
+        "dirac_batch_get_info": (I, [P, ctypes.POINTER(dirac_batch_info)]),
+        "dirac_batch_last_error": (ctypes.c_char_p, [P]),
+        "dirac_batch_klein": (I, [ctypes.POINTER(dirac_klein_run), I, ctypes.POINTER(dirac_batch_config), DP, DP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    lib._batch_sigs = True
+    return lib
+
+
+def _bcheck(st: int, handle=None):
+    if st != DIRAC_OK:
+        msg = _batch_lib().dirac_batch_last_error(handle)
+        raise DiracError(st, msg.decode() if msg else "")
+
+
+def klein_runs_array(runs) -> "ctypes.Array":
+    """ctypes array of dirac_klein_run from objects with side, face, nsteps, V0, L, p0, width, x0 (or dicts)."""
+    arr = (dirac_klein_run * len(runs))()
+    for i, r in enumerate(runs):
+        get = (lambda k: r[k]) if isinstance(r, dict) else (lambda k: getattr(r, k))
+        for f, _ in dirac_klein_run._fields_:
+            setattr(arr[i], f, get(f))
+    return arr
+
+
+def dirac_batch_default_config() -> dirac_batch_config:
+    cfg = dirac_batch_config()
+    _batch_lib().dirac_batch_default_config(ctypes.byref(cfg))
+    return cfg
+
+
+def dirac_batch_create(runs, cfg: dirac_batch_config) -> ctypes.c_void_p:
+    arr = runs if isinstance(runs, ctypes.Array) else klein_runs_array(runs)
+    h = ctypes.c_void_p()
+    _bcheck(_batch_lib().dirac_batch_create(arr, len(arr), ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def dirac_batch_destroy(h) -> None:
+    _bcheck(_batch_lib().dirac_batch_destroy(h))
+
+
+def dirac_batch_reset(h) -> None:
+    _bcheck(_batch_lib().dirac_batch_reset(h), h)
+
+
+def dirac_batch_set_state(h, run: int, psi) -> None:
+    p, dev = _ptr(psi, 8)
+    _bcheck(_batch_lib().dirac_batch_set_state(h, int(run), p, dev), h)
+
+
+def dirac_batch_set_potential(h, run: int, V) -> None:
+    V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
+    _bcheck(_batch_lib().dirac_batch_set_potential(h, int(run), V.ctypes.data, V.size), h)
+
+
+def dirac_batch_run(h) -> None:
+    _bcheck(_batch_lib().dirac_batch_run(h), h)
+
+
+def dirac_batch_results(h, nruns: int) -> dict:
+    T = np.zeros(nruns)
+    F = np.zeros(nruns)
+    N = np.zeros(nruns)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _bcheck(_batch_lib().dirac_batch_results(h, T.ctypes.data_as(dp), F.ctypes.data_as(dp), N.ctypes.data_as(dp)), h)
+    return {"T": T, "flux": F, "norm0": N}
+
+
+def dirac_batch_get_state(h, run: int, out) -> None:
+    p, dev = _ptr(out, 8)
+    _bcheck(_batch_lib().dirac_batch_get_state(h, int(run), p, dev), h)
+
+
+def dirac_batch_autotune(h) -> None:
+    _bcheck(_batch_lib().dirac_batch_autotune(h), h)
+
+
+def dirac_batch_get_info(h) -> dict:
+    info = dirac_batch_info()
+    _bcheck(_batch_lib().dirac_batch_get_info(h, ctypes.byref(info)), h)
+    return {f: getattr(info, f) for f, _ in dirac_batch_info._fields_}
+
+
+def dirac_batch_klein(runs, cfg: dirac_batch_config):
+    """(T, R) arrays for the runs, in one call."""
+    arr = runs if isinstance(runs, ctypes.Array) else klein_runs_array(runs)
+    T = np.zeros(len(arr))
+    R = np.zeros(len(arr))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _bcheck(_batch_lib().dirac_batch_klein(arr, len(arr), ctypes.byref(cfg), T.ctypes.data_as(dp), R.ctypes.data_as(dp)))
+    return T, R

@@ -90,41 +90,6 @@ double cell_volume(const dirac_grid *g) {
     return ndim_of(g) == 3 ? dx * dx * dx : dx * dx;
 }
 
-// FP32 representation of (cos t, -sin t): among the float neighbours of the rounded values, the pair
-// whose squared modulus is closest to 1 (keeps the FP32 phase step unitary to ~1e-9 instead of ~1e-7).
-void round_unitary(double c, double s, float &cf, float &sf) {
-    const float c0 = (float)c, s0 = (float)s;
-    const float cs[3] = {nextafterf(c0, -2.f), c0, nextafterf(c0, 2.f)};
-    const float ss[3] = {nextafterf(s0, -2.f), s0, nextafterf(s0, 2.f)};
-    double best = 1e300;
-    cf = c0;
-    sf = s0;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            const double dc = cs[i], ds = ss[j];
-            const double err = std::fabs(dc * dc + ds * ds - 1.0);
-            const double dist = std::fabs(dc - c) + std::fabs(ds - s);
-            const double key = err + 1e-3 * dist;
-            if (key < best) {
-                best = key;
-                cf = cs[i];
-                sf = ss[j];
-            }
-        }
-}
-
-// Phase coefficients of Eq. sol_dis_4 at A = 0 for potential energy v, pre-scaled by 2^-d:
-// components 1,2: exp(-i (m c^2 dt + v dt)), components 3,4: exp(-i (v dt - m c^2 dt)).
-void phase_coeffs(double mu, double v, double dt, double scale, double out[4]) {
-    const double vdt = v * dt;
-    const double t_up = mu + vdt;
-    const double t_dn = vdt - mu;
-    out[0] = std::cos(t_up) * scale;
-    out[1] = -std::sin(t_up) * scale;
-    out[2] = std::cos(t_dn) * scale;
-    out[3] = -std::sin(t_dn) * scale;
-}
-
 dirac_status ensure_table(dirac_grid *g, size_t bytes) {
     if (bytes <= g->table_cap) return DIRAC_OK;
     if (g->table) {
@@ -379,6 +344,42 @@ void default_plan(dirac_grid *g) {
 }  // namespace
 
 namespace dirac {
+// FP32 representation of (cos t, -sin t): among the float neighbours of the rounded values, the pair
+// whose squared modulus is closest to 1 (keeps the FP32 phase step unitary to ~1e-9 instead of ~1e-7).
+void round_unitary(double c, double s, float &cf, float &sf) {
+    const float c0 = (float)c, s0 = (float)s;
+    const float cs[3] = {nextafterf(c0, -2.f), c0, nextafterf(c0, 2.f)};
+    const float ss[3] = {nextafterf(s0, -2.f), s0, nextafterf(s0, 2.f)};
+    double best = 1e300;
+    cf = c0;
+    sf = s0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const double dc = cs[i], ds = ss[j];
+            const double err = std::fabs(dc * dc + ds * ds - 1.0);
+            const double dist = std::fabs(dc - c) + std::fabs(ds - s);
+            const double key = err + 1e-3 * dist;
+            if (key < best) {
+                best = key;
+                cf = cs[i];
+                sf = ss[j];
+            }
+        }
+}
+
+// Phase coefficients of Eq. sol_dis_4 at A = 0 for potential energy v, pre-scaled by 2^-d:
+// components 1,2: exp(-i (m c^2 dt + v dt)), components 3,4: exp(-i (v dt - m c^2 dt)).
+void phase_coeffs(double mu, double v, double dt, double scale, double out[4]) {
+    const double vdt = v * dt;
+    const double t_up = mu + vdt;
+    const double t_dn = vdt - mu;
+    out[0] = std::cos(t_up) * scale;
+    out[1] = -std::sin(t_up) * scale;
+    out[2] = std::cos(t_dn) * scale;
+    out[3] = -std::sin(t_dn) * scale;
+}
+
+
 // Records a message for dirac_last_error(NULL) on this thread (entry points without a grid).
 dirac_status set_thread_error(dirac_status st, const std::string &msg) {
     g_thread_err = msg;

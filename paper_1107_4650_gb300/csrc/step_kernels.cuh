@@ -174,6 +174,9 @@ __device__ __forceinline__ void mbar_fence_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
     asm volatile(
@@ -477,9 +480,16 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
 #pragma unroll
         for (int s2 = 0; s2 < RG::SLOTS; ++s2)
             if (pending & (1u << s2)) mbar_wait(bar0 + 8 * s2, (phase_bits >> s2) & 1u);
-        __syncwarp();
-        return;
     }
+    if (ring) {
+        // release the barriers so the next task of this warp can initialise them again
+        __syncwarp();
+        if (lane == 0)
+#pragma unroll
+            for (int s2 = 0; s2 < RG::SLOTS; ++s2) mbar_inval(bar0 + 8 * s2);
+        __syncwarp();
+    }
+    if (aborted) return;
     if (has_face) {
 #pragma unroll
         for (int s = 0; s < K; ++s) {

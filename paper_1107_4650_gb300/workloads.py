@@ -144,6 +144,12 @@ class KleinRun:
         x_min, _, x_s, _, _ = self.geometry()
         return tanh_step(self.side, self.dx, x_min, x_s, self.V0, self.L)
 
+    def as_batch_fields(self) -> dict:
+        """Fields of the library's dirac_klein_run (packet centre relative to the step at x = 0)."""
+        _, _, _, x0, face = self.geometry()
+        return {"side": self.side, "face": face, "nsteps": self.nsteps, "V0": self.V0, "L": self.L,
+                "p0": self.p0, "width": self.width, "x0": x0}
+
 
 def klein_config_2d(seed: int = SEED, side: int = 2048, nsteps: int = 4000, m: float = M_E, c: float = C_AU) -> KleinRun:
     """2-D Klein step, FP64 workload: 2048^2 cells, V0 = 2.5 mc^2, L = 4 dx, width 100 dx,

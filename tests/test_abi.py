@@ -93,3 +93,17 @@ def test_null_handles_are_errors_not_crashes(lib):
     assert lib.dirac_step(None, 1) == D.DIRAC_ERR_ARG
     assert lib.dirac_destroy(None) == D.DIRAC_OK
     assert lib.dirac_set_state(None, None, 0) == D.DIRAC_ERR_ARG
+
+
+def test_batch_rejects_bad_runs_without_a_gpu(lib):
+    import paper_1107_4650_gb300 as D
+    cfg = D.dirac_batch_default_config()
+    bad = [{"side": 64, "face": 64, "nsteps": 10, "V0": 1.0, "L": 0.01, "p0": 1.0, "width": 0.01, "x0": -0.05}]
+    with pytest.raises(D.DiracError) as e:
+        D.dirac_batch_create(bad, cfg)
+    assert e.value.status == D.DIRAC_ERR_ARG
+    cfg.precision = 5
+    ok = [dict(bad[0], face=32)]
+    with pytest.raises(D.DiracError) as e:
+        D.dirac_batch_create(ok, cfg)
+    assert e.value.status == D.DIRAC_ERR_ARG

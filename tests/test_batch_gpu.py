@@ -1,0 +1,144 @@
+"""Batched Klein ensemble (one persistent kernel over many uneven runs) against the FP64 oracle.
+
+Each run of a batch must evolve exactly as a single grid does: FP64 runs are compared bit for bit
+with the oracle (same inputs, the step counts chosen odd so the single-step remainder launches run),
+fluxes to 1e-12; FP32 runs within their rounding tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4650_gb300 import workloads as W
+from tests.dirac_algebra import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+C = W.C_AU
+DX = W.DX_DEFAULT
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1107_4650_gb300 import build as B
+    B.build()
+    oracle.build()
+    import paper_1107_4650_gb300 as D
+    D.load_library()
+    return D
+
+
+def _runs():
+    return [W.KleinRun(side=96, V0=2.5 * C * C, p0=0.6 * C, width=8 * DX, nsteps=37, face=60),
+            W.KleinRun(side=64, V0=1.2 * C * C, p0=0.9 * C, width=6 * DX, nsteps=0, face=40),
+            W.KleinRun(side=130, V0=3.0 * C * C, p0=0.3 * C, width=10 * DX, nsteps=52, face=90),
+            W.KleinRun(side=72, V0=0.7 * C * C, p0=0.5 * C, width=5 * DX, nsteps=21, face=50),
+            W.KleinRun(side=160, V0=2.0 * C * C, p0=0.8 * C, width=12 * DX, nsteps=44, face=100)]
+
+
+def _run_batch(D, runs, fp32, K=2, P=0, seg=0, graphs=True, explicit=True):
+    cfg = D.dirac_batch_default_config()
+    cfg.precision = D.DIRAC_FP32 if fp32 else D.DIRAC_FP64
+    cfg.steps_per_launch = K
+    cfg.points_per_lane = P
+    cfg.segment_rows = seg
+    cfg.use_graphs = 1 if graphs else 0
+    h = D.dirac_batch_create([r.as_batch_fields() for r in runs], cfg)
+    dt = np.complex64 if fp32 else np.complex128
+    try:
+        if explicit:
+            for i, r in enumerate(runs):
+                D.dirac_batch_set_state(h, i, np.ascontiguousarray(r.state().astype(dt)))
+                D.dirac_batch_set_potential(h, i, r.potential())
+        D.dirac_batch_run(h)
+        res = D.dirac_batch_results(h, len(runs))
+        outs = []
+        for i, r in enumerate(runs):
+            o = np.empty((r.side, 1, r.side, 4), dtype=dt)
+            D.dirac_batch_get_state(h, i, o)
+            outs.append(o)
+        info = D.dirac_batch_get_info(h)
+    finally:
+        D.dirac_batch_destroy(h)
+    return outs, res, info
+
+
+def _oracle(r):
+    _, _, _, _, face = r.geometry()
+    return oracle.step(r.state(), 2, 1.0, C, r.dx, r.nsteps, V=r.potential(), flux_face=face)
+
+
+@pytest.mark.parametrize("K,P,seg", [(2, 2, 0), (1, 4, 32), (2, 2, 24)])
+def test_batch_fp64_each_run_bit_exact(D, K, P, seg):
+    runs = _runs()
+    outs, res, info = _run_batch(D, runs, fp32=False, K=K, P=P, seg=seg)
+    assert info["steps_per_launch"] == K
+    for r, got, F, n0 in zip(runs, outs, res["flux"], res["norm0"]):
+        want, Fw = _oracle(r)
+        assert np.array_equal(got.view(np.float64), want.view(np.float64)), (r.side, r.nsteps)
+        assert abs(F - Fw) <= 1e-12 * max(abs(Fw), 1e-300)
+        assert abs(n0 - oracle.observables(r.state(), 2, r.dx)["norm"]) <= 1e-12
+
+
+def test_batch_graph_and_direct_agree(D):
+    runs = _runs()
+    a, ra, _ = _run_batch(D, runs, fp32=False, graphs=True)
+    b, rb, _ = _run_batch(D, runs, fp32=False, graphs=False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.view(np.float64), y.view(np.float64))
+    assert np.array_equal(ra["flux"], rb["flux"])
+
+
+@pytest.mark.parametrize("K,P", [(2, 2), (4, 2), (1, 4)])
+def test_batch_fp32_against_oracle(D, K, P):
+    runs = _runs()
+    outs, res, _ = _run_batch(D, runs, fp32=True, K=K, P=P)
+    for r, got, F in zip(runs, outs, res["flux"]):
+        want, Fw = _oracle(r)
+        if r.nsteps == 0:
+            continue
+        assert rel_l2(got.astype(np.complex128), want) < 1e-5
+        assert abs(F - Fw) < 1e-5 * abs(Fw) + 1e-12
+
+
+def test_batch_device_packets_match_host_packets(D):
+    """The packets the library writes on the device give the transmitted fraction of the numpy packets."""
+    runs = _runs()
+    _, res_dev, _ = _run_batch(D, runs, fp32=False, explicit=False)
+    for r, T in zip(runs, res_dev["T"]):
+        if r.nsteps == 0:
+            assert T == 0.0
+            continue
+        want, Fw = _oracle(r)
+        n0 = oracle.observables(r.state(), 2, r.dx)["norm"]
+        assert abs(T - Fw / n0) < 1e-9
+
+
+def test_batch_autotune_then_run(D):
+    runs = _runs()
+    cfg = D.dirac_batch_default_config()
+    cfg.precision = D.DIRAC_FP64
+    h = D.dirac_batch_create([r.as_batch_fields() for r in runs], cfg)
+    try:
+        D.dirac_batch_autotune(h)
+        D.dirac_batch_run(h)
+        T = D.dirac_batch_results(h, len(runs))["T"]
+        with pytest.raises(D.DiracError):
+            D.dirac_batch_run(h)  # needs a reset first
+        D.dirac_batch_reset(h)
+        D.dirac_batch_run(h)
+        T2 = D.dirac_batch_results(h, len(runs))["T"]
+    finally:
+        D.dirac_batch_destroy(h)
+    assert np.allclose(T, T2, rtol=1e-12, atol=0)
+    _, ref, _ = _run_batch(D, runs, fp32=False, explicit=False)
+    assert np.allclose(T, ref["T"], rtol=1e-12, atol=1e-15)
+
+
+def test_batch_one_call(D):
+    runs = _runs()
+    cfg = D.dirac_batch_default_config()
+    cfg.precision = D.DIRAC_FP64
+    cfg.steps_per_launch = 2
+    T, R = D.dirac_batch_klein([r.as_batch_fields() for r in runs], cfg)
+    assert np.allclose(T + R, 1.0)
+    _, ref, _ = _run_batch(D, runs, fp32=False, explicit=False)
+    assert np.allclose(T, ref["T"], rtol=1e-12, atol=1e-15)
