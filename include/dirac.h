@@ -226,6 +226,58 @@ const char *dirac_batch_last_error(const dirac_batch *b);
 dirac_status dirac_batch_klein(const dirac_klein_run *runs, int nruns, const dirac_batch_config *cfg, double *T_out,
                                double *R_out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Transmission surrogate: an MLP 3 -> 256 -> 256 -> 256 -> 256 -> 1 (tanh hidden layers, sigmoid output)
+ * with BF16 weights and FP32 accumulation, trained on GPU by the library's own forward, backward and
+ * Adam kernels on transmissions the solver produced.  Inputs are reduced run parameters
+ * q = (V0 / m c^2, p0 / m c, width / dx), mapped linearly from the training box [lo, hi] to [-1, 1]^3.
+ * Queries outside the box are answered by the batched solver (the surrogate's fallback).
+ * --------------------------------------------------------------------------------------------- */
+typedef struct dirac_surrogate dirac_surrogate; /* opaque */
+
+/* Creates an untrained network (Xavier-uniform weights from a splitmix64 stream of `seed`, zero biases)
+ * for the box lo[3], hi[3] of reduced parameters.  max_batch bounds the training / inference batch. */
+dirac_status dirac_surrogate_create(const double lo[3], const double hi[3], uint64_t seed, int max_batch, void *stream,
+                                    int device, dirac_surrogate **out);
+dirac_status dirac_surrogate_destroy(dirac_surrogate *s);
+
+/* Adam training on n samples (X: n x 3 reduced parameters, T: n targets in [0, 1]), host buffers: `epochs`
+ * passes over a fresh shuffle each (splitmix64 of the seed and the epoch), mini-batches of `batch`,
+ * learning rate lr with cosine decay to lr/20.  The first call on freshly created parameters sets the
+ * output bias to the logit of the mean target (not after dirac_surrogate_set_params).  loss_out (nullable) receives the last epoch's mean squared
+ * error.  Synchronises. */
+dirac_status dirac_surrogate_train(dirac_surrogate *s, const double *X, const double *T, int64_t n, int epochs,
+                                   int batch, double lr, double *loss_out);
+
+/* Network prediction for n points (host buffers), no range check. */
+dirac_status dirac_surrogate_predict(dirac_surrogate *s, const double *X, int64_t n, double *T_out);
+
+/* Gradient of mean((y - T)^2) over the n <= max_batch samples with respect to every parameter (FP32, the
+ * parameter layout of dirac_surrogate_get_params), without updating; loss_out receives the loss. */
+dirac_status dirac_surrogate_gradient(dirac_surrogate *s, const double *X, const double *T, int64_t n, float *grad_out,
+                                      double *loss_out);
+
+/* Number of parameters (198657) and FP32 master parameters in the order W1[256][3], b1, W2[256][256], b2,
+ * W3, b3, W4, b4, w5[256], b5 (host buffers). */
+int64_t dirac_surrogate_num_params(void);
+dirac_status dirac_surrogate_get_params(dirac_surrogate *s, float *params);
+dirac_status dirac_surrogate_set_params(dirac_surrogate *s, const float *params);
+
+/* Transmission for n queries: the network inside the box, the batched solver (geometry of the Klein
+ * ensemble: side = smallest of 256, 384, 512, 768, 1024 holding 8 width + 16 cells, face 8 width + 8
+ * cells from the left edge, packet 4 widths left of the step, L = 4 dx, steps = time for the packet to
+ * travel 8 widths at its group velocity + 200, clamped to [2000, 6000]) outside it, with solver_cfg's
+ * precision.  used_solver (nullable) receives 1 for the points the solver answered. */
+dirac_status dirac_surrogate_query(dirac_surrogate *s, const double *X, int64_t n, const dirac_batch_config *solver_cfg,
+                                   double *T_out, int *used_solver);
+
+/* Ensemble geometry of one reduced query q (same rule as the fallback above), for callers that build
+ * their own batches. */
+dirac_status dirac_klein_run_from_reduced(const double q[3], double dx, double c, double m, dirac_klein_run *run);
+
+/* Last error of s (or of this thread for calls without a surrogate). Never NULL. */
+const char *dirac_surrogate_last_error(const dirac_surrogate *s);
+
 /* Allocation-free observables.  The paper has no counterpart: this serves callers that cannot
  * allocate device memory, such as a host framework that owns the whole device budget through its own
  * pool, or a latency-critical loop that must not pay the device synchronisation that cudaMalloc and

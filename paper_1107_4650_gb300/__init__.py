@@ -349,3 +349,105 @@ def dirac_batch_klein(runs, cfg: dirac_batch_config):
     dp = ctypes.POINTER(ctypes.c_double)
     _bcheck(_batch_lib().dirac_batch_klein(arr, len(arr), ctypes.byref(cfg), T.ctypes.data_as(dp), R.ctypes.data_as(dp)))
     return T, R
+
+
+# ----------------------------------------------------------------------------- transmission surrogate
+
+def _sur_lib():
+    lib = _batch_lib()
+    if getattr(lib, "_sur_sigs", False):
+        return lib
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "dirac_surrogate_create": (I, [P, P, ctypes.c_uint64, I, P, I, ctypes.POINTER(P)]),
+        "dirac_surrogate_destroy": (I, [P]),
+        "dirac_surrogate_train": (I, [P, P, P, I64, I, I, D, P]),
+        "dirac_surrogate_predict": (I, [P, P, I64, P]),
+        "dirac_surrogate_gradient": (I, [P, P, P, I64, P, P]),
+        "dirac_surrogate_num_params": (I64, []),
+        "dirac_surrogate_get_params": (I, [P, P]),
+        "dirac_surrogate_set_params": (I, [P, P]),
+        "dirac_surrogate_query": (I, [P, P, I64, ctypes.POINTER(dirac_batch_config), P, P]),
+        "dirac_klein_run_from_reduced": (I, [P, D, D, D, ctypes.POINTER(dirac_klein_run)]),
+        "dirac_surrogate_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    lib._sur_sigs = True
+    return lib
+
+
+def _scheck(st, handle=None):
+    if st != DIRAC_OK:
+        msg = _sur_lib().dirac_surrogate_last_error(handle)
+        raise DiracError(st, msg.decode() if msg else "")
+
+
+def _f64(a, cols=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def dirac_surrogate_create(lo, hi, seed: int = 0, max_batch: int = 4096, stream=None, device: int = 0):
+    lo, hi = _f64(lo), _f64(hi)
+    h = ctypes.c_void_p()
+    _scheck(_sur_lib().dirac_surrogate_create(lo.ctypes.data, hi.ctypes.data, seed, max_batch, stream, device,
+                                              ctypes.byref(h)))
+    return h
+
+
+def dirac_surrogate_destroy(h) -> None:
+    _scheck(_sur_lib().dirac_surrogate_destroy(h))
+
+
+def dirac_surrogate_train(h, X, T, epochs: int, batch: int, lr: float) -> float:
+    X, T = _f64(X), _f64(T)
+    loss = ctypes.c_double()
+    _scheck(_sur_lib().dirac_surrogate_train(h, X.ctypes.data, T.ctypes.data, len(T), epochs, batch, lr,
+                                             ctypes.addressof(loss)), h)
+    return loss.value
+
+
+def dirac_surrogate_predict(h, X) -> np.ndarray:
+    X = _f64(X)
+    out = np.zeros(X.shape[0])
+    _scheck(_sur_lib().dirac_surrogate_predict(h, X.ctypes.data, X.shape[0], out.ctypes.data), h)
+    return out
+
+
+def dirac_surrogate_gradient(h, X, T):
+    X, T = _f64(X), _f64(T)
+    g = np.zeros(_sur_lib().dirac_surrogate_num_params(), dtype=np.float32)
+    loss = ctypes.c_double()
+    _scheck(_sur_lib().dirac_surrogate_gradient(h, X.ctypes.data, T.ctypes.data, len(T), g.ctypes.data,
+                                                ctypes.addressof(loss)), h)
+    return loss.value, g
+
+
+def dirac_surrogate_get_params(h) -> np.ndarray:
+    p = np.zeros(_sur_lib().dirac_surrogate_num_params(), dtype=np.float32)
+    _scheck(_sur_lib().dirac_surrogate_get_params(h, p.ctypes.data), h)
+    return p
+
+
+def dirac_surrogate_set_params(h, params) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _scheck(_sur_lib().dirac_surrogate_set_params(h, p.ctypes.data), h)
+
+
+def dirac_surrogate_query(h, X, solver_cfg: dirac_batch_config):
+    X = _f64(X)
+    T = np.zeros(X.shape[0])
+    used = np.zeros(X.shape[0], dtype=np.int32)
+    _scheck(_sur_lib().dirac_surrogate_query(h, X.ctypes.data, X.shape[0], ctypes.byref(solver_cfg), T.ctypes.data,
+                                             used.ctypes.data), h)
+    return T, used.astype(bool)
+
+
+def dirac_klein_run_from_reduced(q, dx: float, c: float, m: float) -> dict:
+    q = _f64(q)
+    run = dirac_klein_run()
+    _scheck(_sur_lib().dirac_klein_run_from_reduced(q.ctypes.data, dx, c, m, ctypes.byref(run)))
+    return {f: getattr(run, f) for f, _ in dirac_klein_run._fields_}

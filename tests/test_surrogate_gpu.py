@@ -1,0 +1,119 @@
+"""Transmission surrogate: the GPU network's forward and backward against the CPU FP64 oracle, training,
+and a small-box Klein surrogate trained on batched-solver output and judged by the FP64 solver."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_1107_4650_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C = W.C_AU
+DX = W.DX_DEFAULT
+LO = np.array([0.5, 0.2, 10.0])
+HI = np.array([3.0, 1.0, 30.0])
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1107_4650_gb300 import build as B
+    B.build()
+    import paper_1107_4650_gb300 as D
+    D.load_library()
+    return D
+
+
+def _norm(q):
+    return (2.0 * (q - LO) / (HI - LO) - 1.0).astype(np.float32).astype(np.float64)
+
+
+def _blocks(v):
+    out, o = {}, 0
+    for name, shape in M.SHAPES:
+        n = int(np.prod(shape))
+        out[name] = v[o:o + n]
+        o += n
+    return out
+
+
+@pytest.mark.parametrize("B", [64, 300])
+def test_gradient_matches_oracle(D, B):
+    rng = np.random.default_rng(B)
+    h = D.dirac_surrogate_create(LO, HI, seed=7, max_batch=512)
+    try:
+        q = LO + (HI - LO) * rng.uniform(0, 1, (B, 3))
+        t = rng.uniform(0, 1, B)
+        loss, g = D.dirac_surrogate_gradient(h, q, t)
+        p = D.dirac_surrogate_get_params(h).astype(np.float64)
+        y = D.dirac_surrogate_predict(h, q)
+    finally:
+        D.dirac_surrogate_destroy(h)
+    lo_, go = M.loss_and_grad(p, _norm(q), t, round_bf16=True)
+    assert abs(loss - lo_) <= 1e-5 * lo_
+    assert np.max(np.abs(y - M.predict(p, _norm(q)))) < 2e-4
+    gb, ob = _blocks(g.astype(np.float64)), _blocks(go)
+    for name in gb:
+        err = np.linalg.norm(gb[name] - ob[name]) / max(np.linalg.norm(ob[name]), 1e-30)
+        assert err < 2e-2, (name, err)
+    assert np.linalg.norm(g - go) / np.linalg.norm(go) < 1e-2
+
+
+def test_training_fits_a_smooth_function(D):
+    rng = np.random.default_rng(5)
+    q = LO + (HI - LO) * rng.uniform(0, 1, (4096, 3))
+    z = _norm(q)
+    t = 1.0 / (1.0 + np.exp(-(1.5 * z[:, 0] - z[:, 1] + 0.5 * z[:, 0] * z[:, 2])))
+    h = D.dirac_surrogate_create(LO, HI, seed=3, max_batch=512)
+    try:
+        loss0, _ = D.dirac_surrogate_gradient(h, q[:512], t[:512])
+        loss = D.dirac_surrogate_train(h, q, t, epochs=60, batch=256, lr=2e-3)
+        y = D.dirac_surrogate_predict(h, q[:512])
+    finally:
+        D.dirac_surrogate_destroy(h)
+    assert loss < 1e-3 * loss0 + 2e-5
+    assert np.max(np.abs(y - t[:512])) < 0.03
+
+
+def _solver_cfg(D, fp32):
+    cfg = D.dirac_batch_default_config()
+    cfg.precision = D.DIRAC_FP32 if fp32 else D.DIRAC_FP64
+    cfg.steps_per_launch = 2
+    return cfg
+
+
+def _solve(D, qs, fp32):
+    runs = [D.dirac_klein_run_from_reduced(q, DX, C, 1.0) for q in qs]
+    T, _ = D.dirac_batch_klein(runs, _solver_cfg(D, fp32))
+    return T
+
+
+def test_klein_surrogate_small_box(D):
+    """1024 batched FP32 solves train the network; 48 held-out points are judged by the FP64 solver; queries
+    outside the box fall back to the solver; the network answers >= 100x faster than per-run FP64 solves."""
+    rng = np.random.default_rng(11)
+    q_train = LO + (HI - LO) * rng.uniform(0, 1, (1024, 3))
+    T_train = _solve(D, q_train, fp32=True)
+    q_test = LO + (HI - LO) * rng.uniform(0, 1, (48, 3))
+    t0 = time.perf_counter()
+    T_judge = _solve(D, q_test, fp32=False)
+    t_fp64 = (time.perf_counter() - t0) / len(q_test)
+    h = D.dirac_surrogate_create(LO, HI, seed=1, max_batch=1024)
+    try:
+        D.dirac_surrogate_train(h, q_train, T_train, epochs=1500, batch=64, lr=1e-3)
+        D.dirac_surrogate_predict(h, q_test)
+        t0 = time.perf_counter()
+        T_net = D.dirac_surrogate_predict(h, q_test)
+        t_net = (time.perf_counter() - t0) / len(q_test)
+        q_out = np.array([[0.4, 0.5, 20.0], [1.0, 1.2, 15.0]])
+        T_out, used = D.dirac_surrogate_query(h, np.vstack([q_test[:3], q_out]), _solver_cfg(D, True))
+    finally:
+        D.dirac_surrogate_destroy(h)
+    dT = np.abs(T_net - T_judge)
+    print("surrogate small box: mean |dT| %.2e, max %.2e; %.1f us/query vs FP64 solve %.1f ms/query"
+          % (dT.mean(), dT.max(), t_net * 1e6, t_fp64 * 1e3))
+    assert dT.mean() < 0.012 and dT.max() < 0.15
+    assert list(used) == [False, False, False, True, True]
+    assert np.allclose(T_out[3:], _solve(D, q_out, fp32=True), rtol=1e-12, atol=1e-15)
+    assert t_fp64 / t_net > 100
