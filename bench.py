@@ -38,6 +38,12 @@ import numpy as np  # noqa: E402
 FP64_BYTES_PER_POINT_STEP = 128  # 2-D, x-only table: 64 B read + 64 B written
 FP32_BYTES_PER_POINT_STEP = 64
 FLOPS_PER_POINT_STEP_2D = 56    # 32 adds (two sweeps) + 4 complex products of 6 flops
+FP64_INSTR_PER_POINT_STEP_2D = 48  # 32 DADD + 8 DMUL + 8 DFMA: what the FP64 pipe issues per 2-D point-step
+# FP64 issue roof: the recipe's nominal 1.25 TFLOP/s counts a DFMA as 2 flops -> 0.625 T FP64 instructions/s
+# (DADD and DMUL issue at the DFMA rate).  Measured on this machine's GB300 with an FMA/ADD throughput probe:
+# 0.5285 T lane-instructions/s (1.68 per SM per clock at 2.07 GHz, 152 SMs).
+FP64_ISSUE_PEAK_NOMINAL = 0.625
+FP64_ISSUE_PEAK_MEASURED = 0.5285
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel on this workload
 # (profiles/step_kernel_fp64_klein2048.md); None until captured for the kernel as it stands.
 MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": None, "fp32": None}
@@ -56,6 +62,8 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=512)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--judge-points", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -274,12 +282,14 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved_gbs = alg_bytes / mean_launch_s / 1e9
-    fp64_tflops = FLOPS_PER_POINT_STEP_2D * ncell * k_launch / mean_launch_s / 1e12
-    FP64_NOMINAL_TFLOPS = 1.25
+    fp64_tips = FP64_INSTR_PER_POINT_STEP_2D * ncell * k_launch / mean_launch_s / 1e12
     traffic = MEASURED_TRAFFIC_PER_LAUNCH["fp64"]
-    roofline = {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": fp64_tflops / FP64_NOMINAL_TFLOPS, "traffic": traffic,
-                "peak_source": "nominal FP64 rate of the recipe (no measured FP64 peak in MEASURED_PEAKS.json)",
+    roofline = {"bound": "alu", "achieved": fp64_tips, "peak": FP64_ISSUE_PEAK_NOMINAL, "unit": "T FP64-instr/s",
+                "frac": fp64_tips / FP64_ISSUE_PEAK_NOMINAL, "traffic": traffic,
+                "peak_source": "derived from the recipe's nominal FP64 rate (1.25 TFLOP/s / 2 flops per DFMA); "
+                               "MEASURED_PEAKS.json has no FP64 figure",
+                "frac_of_measured_fp64_issue": fp64_tips / FP64_ISSUE_PEAK_MEASURED,
+                "achieved_tflops": FLOPS_PER_POINT_STEP_2D * ncell * k_launch / mean_launch_s / 1e12,
                 "kernel": "dirac::sweep_kernel<double,%d,%d,0>" % (k_launch, info["points_per_lane"]),
                 "mean_launch_ms": mean_launch_s * 1e3,
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
@@ -364,6 +374,51 @@ def main():
                         "block of steps, graph-replayed; %d drawn sides raised to hold the packet"
                         % (len(runs), sorted(set(r.side for r in runs)), len(deviations)),
             "T_mean": float(np.mean(bres["T"])), "T_min": float(np.min(bres["T"])), "T_max": float(np.max(bres["T"]))}
+
+    # ---------------------------------------------------------------- transmission surrogate
+    ckpt = os.path.join(ROOT, "paper_1107_4650_gb300", "data", "surrogate_klein_box.npz")
+    if not args.no_surrogate and os.path.exists(ckpt):
+        z = np.load(ckpt)
+        lo, hi = z["lo"], z["hi"]
+        hs = D.dirac_surrogate_create(lo, hi, seed=0, max_batch=4096, stream=stream.cuda_stream, device=local)
+        D.dirac_surrogate_set_params(hs, z["params"])
+        rng = np.random.default_rng(W.SEED + 4)
+        qq = lo + (hi - lo) * rng.uniform(0, 1, (4096, 3))
+        D.dirac_surrogate_predict(hs, qq)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            D.dirac_surrogate_predict(hs, qq)
+        t_net = (time.perf_counter() - t0) / (5 * len(qq))
+        qj = qq[:args.judge_points]
+        T_net = D.dirac_surrogate_predict(hs, qj)
+        D.dirac_surrogate_destroy(hs)
+
+        def solve(qs, prec):
+            cfg_b = D.dirac_batch_default_config()
+            cfg_b.precision = prec
+            cfg_b.stream = stream.cuda_stream
+            cfg_b.device = local
+            cfg_b.steps_per_launch = 2
+            cfg_b.points_per_lane = 2
+            cfg_b.segment_rows = 256
+            runs = [D.dirac_klein_run_from_reduced(q, W.DX_DEFAULT, W.C_AU, 1.0) for q in qs]
+            t = time.perf_counter()
+            T, _ = D.dirac_batch_klein(runs, cfg_b)
+            return T, (time.perf_counter() - t) / len(qs)
+
+        T64, t64 = solve(qj, D.DIRAC_FP64)
+        dT = np.abs(T_net - T64)
+        bq = variants.get("batched_fp32", {})
+        t32 = bq["ms_per_pass"] / 1e3 / bq["runs"] if bq else None
+        variants["surrogate"] = {
+            "queries_per_s_network": 1.0 / t_net, "queries_per_s_fp64_solver": 1.0 / t64,
+            "queries_per_s_batched_fp32_solver": (1.0 / t32) if t32 else None,
+            "gain_network_over_fp64_solve": t64 / t_net,
+            "gain_batched_fp32_over_fp64_solve": (t64 / t32) if t32 else None,
+            "judged_points": len(qj), "dT_mean": float(dT.mean()), "dT_max": float(dT.max()),
+            "checkpoint": "paper_1107_4650_gb300/data/surrogate_klein_box.npz",
+            "box": "V0/mc^2 [%g, %g], p0/mc [%g, %g], width/dx [%g, %g]" % (lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]),
+            "training": json.loads(str(z["stats"])) if "stats" in z else None}
 
     # ---------------------------------------------------------------- CPU baseline (rank 0)
     cpu = None

@@ -24,6 +24,8 @@ def main():
     ap.add_argument("--p", type=int, default=0, help="points per lane (0: library choice)")
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--ndim", type=int, default=2)
+    ap.add_argument("--batch-runs", type=int, default=0, help="run this many ensemble runs as one batch instead")
+    ap.add_argument("--seg", type=int, default=256, help="batch: rows per task")
     args = ap.parse_args()
 
     import torch
@@ -36,6 +38,29 @@ def main():
     D.load_library()
     prec = D.DIRAC_FP32 if args.precision == "fp32" else D.DIRAC_FP64
     stream = torch.cuda.Stream()
+    if args.batch_runs > 0:
+        runs, _ = W.klein_ensemble(nruns=args.batch_runs)
+        cfg = D.dirac_batch_default_config()
+        cfg.precision = prec
+        cfg.stream = stream.cuda_stream
+        cfg.steps_per_launch = args.k or 2
+        cfg.points_per_lane = args.p or 2
+        cfg.segment_rows = args.seg
+        cfg.use_graphs = 0 if args.no_graphs else 1
+        hb = D.dirac_batch_create([r.as_batch_fields() for r in runs], cfg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        D.dirac_batch_run(hb)
+        e1.record(stream)
+        stream.synchronize()
+        info = D.dirac_batch_get_info(hb)
+        T = D.dirac_batch_results(hb, len(runs))["T"]
+        D.dirac_batch_destroy(hb)
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"batch_runs": len(runs), "ms": ms, "point_steps_per_s": info["point_steps"] / (ms / 1e3),
+                          "k": info["steps_per_launch"], "p": info["points_per_lane"], "seg": info["segment_rows"],
+                          "launches": info["launches"], "T_mean": float(np.mean(T))}))
+        return
     if args.ndim == 2:
         run = W.klein_config_2d(side=args.side, nsteps=args.nsteps)
         x_min, z_min, _, _, face = run.geometry()
