@@ -1,0 +1,89 @@
+"""The oracle pins catch plausible mistakes: each mutant below is a copy of the oracle's C source with one
+planted error (a flipped sign, swapped neighbours, a dropped factor, a wrong component, a wrong phase
+sign, a flux sign), built into a temporary library; at least one pin check must reject it.  CPU only."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4650_gb300 import workloads as W
+from tests import dirac_algebra as A
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "dirac_oracle.c")
+C = W.C_AU
+DX = W.DX_DEFAULT
+
+MUTANTS = {
+    "x_sweep_sign": ("o[3] = c_half(c_add(c_add(L[0], L[3]), c_sub(R[3], R[0])));",
+                     "o[3] = c_half(c_add(c_add(L[0], L[3]), c_sub(R[0], R[3])));"),
+    "x_sweep_neighbours_swapped": ("o[0] = c_half(c_add(c_add(L[0], L[3]), c_sub(R[0], R[3])));",
+                                   "o[0] = c_half(c_add(c_add(R[0], R[3]), c_sub(L[0], L[3])));"),
+    "z_sweep_component": ("o[1] = c_half(c_add(c_sub(L[1], L[3]), c_add(R[1], R[3])));",
+                          "o[1] = c_half(c_add(c_sub(L[1], L[2]), c_add(R[1], R[3])));"),
+    "y_sweep_i_sign": ("o[0] = c_half(c_add(c_sub_ib(L[0], L[3]), c_add_ib(R[0], R[3])));",
+                       "o[0] = c_half(c_add(c_add_ib(L[0], L[3]), c_sub_ib(R[0], R[3])));"),
+    "dropped_half": ("o[2] = c_half(c_add(c_add(L[0], L[2]), c_sub(R[2], R[0])));",
+                     "o[2] = c_add(c_add(L[0], L[2]), c_sub(R[2], R[0]));"),
+    "phase_mass_sign": ("double t_dn = vdt - mu;", "double t_dn = vdt + mu;"),
+    "phase_conjugate": ("cplx p_up = {cos(t_up), -sin(t_up)};", "cplx p_up = {cos(t_up), sin(t_up)};"),
+    "flux_sign": ("f += right - left;", "f += right + left;"),
+    "boundary_wrap_off_by_one": ("i = ((i % n[0]) + n[0]) % n[0];", "i = ((i % n[0]) + n[0] + 1) % n[0];"),
+}
+
+
+def _build_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    path = tmp_path / ("%s.c" % name)
+    path.write_text(src.replace(old, new))
+    so = tmp_path / ("lib%s.so" % name)
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", str(path), "-o", str(so), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P = ctypes.c_void_p
+    lib.oracle_sweep.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_int]
+    lib.oracle_step.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
+    lib.oracle_observables.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_double, oracle.D3, ctypes.c_int64, P]
+    return lib
+
+
+def _pins_pass():
+    """The quick pins of test_oracle_pins, run against whatever library oracle._lib holds."""
+    ok = True
+    for shape, axis, per in [((5, 1, 4), 0, False), ((5, 1, 4), 2, True), ((3, 4, 2), 1, False), ((4, 3, 2), 0, True)]:
+        nx, ny, nz = shape
+        psi = W.random_state(nz, ny, nx, seed=31 + axis)
+        got = oracle.sweep(psi, axis, per)
+        ok &= np.max(np.abs(got.reshape(-1) - A.sweep_matrix(shape, axis, per) @ psi.reshape(-1))) < 1e-15
+    for ndim, shape in [(2, (6, 1, 5)), (3, (3, 4, 3))]:
+        nx, ny, nz = shape
+        psi = W.random_state(nz, ny, nx, seed=5)
+        V = np.random.default_rng(3).uniform(-3e4, 3e4, nx * ny * nz)
+        got, _ = oracle.step(psi, ndim, 1.0, C, DX, 1, V=V, periodic=False)
+        step = A.sweep_matrix(shape, 2, False) @ (
+            A.sweep_matrix(shape, 1, False) @ A.sweep_matrix(shape, 0, False) if ndim == 3 else A.sweep_matrix(shape, 0, False))
+        want = A.phase_matrix(shape, 1.0, C, DX / C, V) @ step @ psi.reshape(-1)
+        ok &= np.max(np.abs(got.reshape(-1) - want)) < 5e-15
+    run = W.KleinRun(side=160, V0=2.5 * C * C, p0=0.7 * C, width=5 * DX, nsteps=20, face=80)
+    psi0 = run.state()
+    x_min, z_min, _, _, face = run.geometry()
+    o0 = oracle.observables(psi0, 2, DX, (x_min, 0.0, z_min), face)
+    out, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=run.potential(), flux_face=face)
+    o1 = oracle.observables(out, 2, DX, (x_min, 0.0, z_min), face)
+    ok &= abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
+    return bool(ok)
+
+
+def test_unmutated_oracle_passes_the_quick_pins(oracle_mod):
+    assert _pins_pass()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(oracle_mod, tmp_path, monkeypatch, name):
+    old, new = MUTANTS[name]
+    lib = _build_mutant(tmp_path, name, old, new)
+    monkeypatch.setattr(oracle, "_lib", lib)
+    assert not _pins_pass(), "mutant %s survived the pins" % name
