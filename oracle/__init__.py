@@ -53,7 +53,10 @@ def _load():
         lib.oracle_step.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
         lib.oracle_observables.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, D3, ctypes.c_int64, P]
-        for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables):
+        lib.oracle_step_strang2d.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
+        for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables,
+                  lib.oracle_step_strang2d):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -117,6 +120,23 @@ def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
                              int(flux_face), ctypes.addressof(fc))
     if rc != 0:
         raise MemoryError("oracle_step")
+    return out, fc.value
+
+
+def step_strang2d(psi, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False,
+                  flux_face: int = -1, flux_cum: float = 0.0):
+    """nsteps second-order (Strang) steps in the x-z plane (Sec. 2.4): x, z, phase(dt), z, x with
+    dt = 2 dx / c.  Returns (psi_out, flux_cum) as step()."""
+    out = _as_state(psi)
+    if out.shape[1] != 1:
+        raise ValueError("Strang steps are 2-D (ny = 1)")
+    Varr, layout = _potential(V, out)
+    fc = ctypes.c_double(flux_cum)
+    rc = _load().oracle_step_strang2d(out.ctypes.data, _dims(out), int(bool(periodic)), float(m), float(c), float(dx),
+                                      None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
+                                      int(flux_face), ctypes.addressof(fc))
+    if rc != 0:
+        raise MemoryError("oracle_step_strang2d")
     return out, fc.value
 
 

@@ -185,6 +185,26 @@ int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double 
     return 0;
 }
 
+/* nsteps steps of the second-order (Strang) splitting of Sec. 2.4 in the x-z plane: with B omitted and
+ * consecutive A steps merged, one step is A(dt/2) C(dt/2) D(dt) C(dt/2) A(dt/2).  Each half-step sweep is
+ * the one-cell characteristic shift when c dt/2 = dx, so dt = 2 dx / c here.  The face flux is added at
+ * both x sweeps of a step. */
+int oracle_step_strang2d(double *psi, const int64_t n[3], int periodic, double m, double c, double dx,
+                         const double *V, int layout, int64_t nsteps, int64_t flux_face, double *flux_cum) {
+    double dt = 2.0 * dx / c;
+    double vol = dx * dx;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
+        if (oracle_sweep(psi, n, 0, periodic)) return -1;
+        if (oracle_sweep(psi, n, 2, periodic)) return -1;
+        oracle_phase(psi, n, m, c, dt, V, layout);
+        if (oracle_sweep(psi, n, 2, periodic)) return -1;
+        if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
+        if (oracle_sweep(psi, n, 0, periodic)) return -1;
+    }
+    return 0;
+}
+
 /* Observables, summed in index order:
  *   out[0] = norm        = sum rho dx^d,  rho = sum_c |psi_c|^2
  *   out[1] = norm_right  = sum over cells with i >= flux_face of rho dx^d (0 if flux_face < 0)

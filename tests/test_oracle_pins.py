@@ -296,3 +296,47 @@ def test_oracle_klein_run_converges_to_closed_form():
         out, F = oracle.step(psi, 2, M, C, dx, nsteps, V=V, periodic=True, flux_face=face)
         errs.append(abs(F / oracle.observables(psi, 2, dx)["norm"] - T_cf) / T_cf)
     assert errs[1] < 0.01 and errs[0] / errs[1] > 3.0, errs
+
+
+# ---------------------------------------------------------------- Strang (second-order) splitting, 2-D
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_strang_step_equals_matrix_product(oracle_mod, periodic):
+    """One Strang step = S_x S_z D(2 dx/c) S_z S_x (Sec. 2.4, B omitted, consecutive A merged)."""
+    shape = (6, 1, 5)
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=41)
+    V = np.random.default_rng(42).uniform(-3e4, 3e4, nx)
+    got, _ = oracle.step_strang2d(psi, M, C, W.DX_DEFAULT, 1, V=V, periodic=periodic)
+    Sx = A.sweep_matrix(shape, 0, periodic)
+    Sz = A.sweep_matrix(shape, 2, periodic)
+    Dm = A.phase_matrix(shape, M, C, 2 * W.DX_DEFAULT / C, np.tile(V, nz))
+    want = Sx @ Sz @ Dm @ Sz @ Sx @ psi.reshape(-1)
+    assert np.max(np.abs(got.reshape(-1) - want)) < 5e-15
+
+
+def test_strang_second_order_convergence_to_continuum(oracle_mod):
+    """Strang splitting is second order (Sec. 2.4): halving dx (dt = 2 dx / c) divides the error against the
+    exact free evolution by about 4, while the first-order scheme only halves it."""
+    box = 64 * 4 * W.DX_DEFAULT
+    errs = []
+    for n in (64, 128, 256):
+        dx = box / n
+        nsteps = n // 4
+        t = nsteps * 2 * dx / C
+        psi0 = W.positive_energy_packet_2d(n, n, dx, box / 10, 0.5 * M * C)
+        got, _ = oracle.step_strang2d(psi0, M, C, dx, nsteps, periodic=True)
+        errs.append(A.rel_l2(got, A.continuum_evolution_2d(psi0, dx, t, M, C)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.3 < r1 < 4.7 and 3.3 < r2 < 4.7, errs
+
+
+def test_strang_flux_identity(oracle_mod):
+    run = W.KleinRun(side=320, V0=2.5 * C * C, p0=0.7 * C, width=8 * W.DX_DEFAULT, nsteps=40, face=180)
+    psi0 = run.state()
+    x_min, z_min, _, _, face = run.geometry()
+    o0 = oracle.observables(psi0, 2, run.dx, (x_min, 0.0, z_min), face)
+    out, F = oracle.step_strang2d(psi0, M, C, run.dx, run.nsteps, V=run.potential(), flux_face=face)
+    o1 = oracle.observables(out, 2, run.dx, (x_min, 0.0, z_min), face)
+    assert F > 1e-3
+    assert abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
