@@ -48,6 +48,7 @@ typedef enum {
 enum { DIRAC_FP64 = 0, DIRAC_FP32 = 1 };              /* storage precision */
 enum { DIRAC_BC_ZERO = 0, DIRAC_BC_PERIODIC = 1 };    /* boundary */
 enum { DIRAC_V_NONE = 0, DIRAC_V_X_ONLY = 1, DIRAC_V_FULL = 2 }; /* potential layout */
+enum { DIRAC_LIE = 0, DIRAC_STRANG = 1 };             /* splitting order */
 
 typedef struct {
     int ndim;             /* 2 (x-z plane, n[1] must be 1) or 3 */
@@ -68,10 +69,15 @@ typedef struct {
     int use_graphs;       /* 1: replay dirac_step's steady-state launches from a captured CUDA graph */
     int points_per_lane;  /* x cells per lane of the step kernel: 1, 2 or 4 (K = 2 needs 2 in FP64);
                              0 = library choice */
+    int splitting;        /* DIRAC_LIE: first-order steps x, (y,) z, phase with dt = dx / c (Sec. 2.1);
+                             DIRAC_STRANG (2-D only): second-order steps x, z, phase(dt), z, x with
+                             dt = 2 dx / c, so each half-step sweep is the one-cell shift (Sec. 2.4);
+                             steps_per_launch 1 (FP64) or 1, 2 (FP32) */
 } dirac_config;
 
 /* Fills cfg with defaults: ndim 2, n = {256,1,256}, dx = 10/8192, c = 137.0359895, m = 1,
- * x_min centred, FP64, zero boundary, no flux face, legacy stream, device 0, library k, graphs on. */
+ * x_min centred, FP64, zero boundary, no flux face, legacy stream, device 0, library k, graphs on,
+ * first-order splitting. */
 void dirac_default_config(dirac_config *cfg);
 
 /* Creates a grid: validates cfg, allocates two state buffers (ping-pong), the phase table and
@@ -264,10 +270,10 @@ dirac_status dirac_surrogate_get_params(dirac_surrogate *s, float *params);
 dirac_status dirac_surrogate_set_params(dirac_surrogate *s, const float *params);
 
 /* Transmission for n queries: the network inside the box, the batched solver (geometry of the Klein
- * ensemble: side = smallest of 256, 384, 512, 768, 1024 holding 8 width + 16 cells, face 8 width + 8
- * cells from the left edge, packet 4 widths left of the step, L = 4 dx, steps = time for the packet to
- * travel 8 widths at its group velocity + 200, clamped to [2000, 6000]) outside it, with solver_cfg's
- * precision.  used_solver (nullable) receives 1 for the points the solver answered. */
+ * ensemble: side = smallest of 256, 384, 512, 768, 1024 holding 8 width + 136 cells (1024 at most), face
+ * 8 width + 8 cells from the left edge and at least 128 cells from the right edge, packet 4 widths left
+ * of the step, L = 4 dx, steps = time for the packet to travel 8 widths at its group velocity + 200,
+ * clamped to [2000, 6000]) outside it, with solver_cfg's precision.  used_solver (nullable) receives 1 for the points the solver answered. */
 dirac_status dirac_surrogate_query(dirac_surrogate *s, const double *X, int64_t n, const dirac_batch_config *solver_cfg,
                                    double *T_out, int *used_solver);
 

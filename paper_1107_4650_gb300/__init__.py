@@ -21,6 +21,7 @@ DIRAC_OK, DIRAC_ERR_ARG, DIRAC_ERR_OOM, DIRAC_ERR_CUDA, DIRAC_ERR_NONFINITE, DIR
 DIRAC_FP64, DIRAC_FP32 = 0, 1
 DIRAC_BC_ZERO, DIRAC_BC_PERIODIC = 0, 1
 DIRAC_V_NONE, DIRAC_V_X_ONLY, DIRAC_V_FULL = 0, 1, 2
+DIRAC_LIE, DIRAC_STRANG = 0, 1
 
 STATUS_NAMES = {0: "DIRAC_OK", 1: "DIRAC_ERR_ARG", 2: "DIRAC_ERR_OOM", 3: "DIRAC_ERR_CUDA",
                 4: "DIRAC_ERR_NONFINITE", 5: "DIRAC_ERR_TIMEOUT", 6: "DIRAC_ERR_STATE"}
@@ -37,7 +38,7 @@ class dirac_config(ctypes.Structure):
                 ("c", ctypes.c_double), ("m", ctypes.c_double), ("x_min", ctypes.c_double * 3),
                 ("precision", ctypes.c_int), ("boundary", ctypes.c_int), ("flux_face", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("points_per_lane", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("points_per_lane", ctypes.c_int), ("splitting", ctypes.c_int)]
 
 
 class dirac_obs(ctypes.Structure):
@@ -188,7 +189,8 @@ def dirac_last_error(h=None) -> str:
 def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRAC_FP64,
                 boundary: int = DIRAC_BC_ZERO, x_min=None, flux_face: int = -1, stream=None,
                 device: int = 0, steps_per_launch: int = 0, use_graphs: bool = True,
-                c: float | None = None, m: float | None = None, points_per_lane: int = 0) -> dirac_config:
+                c: float | None = None, m: float | None = None, points_per_lane: int = 0,
+                splitting: int = 0) -> dirac_config:
     """dirac_default_config() with the given fields replaced (n = (nx, ny, nz))."""
     cfg = dirac_default_config()
     cfg.ndim = ndim
@@ -212,6 +214,7 @@ def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRA
     cfg.steps_per_launch = steps_per_launch
     cfg.use_graphs = 1 if use_graphs else 0
     cfg.points_per_lane = points_per_lane
+    cfg.splitting = splitting
     return cfg
 
 

@@ -84,7 +84,12 @@ dirac_status cuda_fail(dirac_grid *g, cudaError_t e, const char *where) {
     } while (0)
 
 int ndim_of(const dirac_grid *g) { return g->cfg.ndim; }
-double scale_of(const dirac_grid *g) { return ndim_of(g) == 3 ? 0.125 : 0.25; }
+bool strang(const dirac_grid *g) { return g->cfg.splitting == DIRAC_STRANG; }
+// Power-of-two scale the phase coefficients carry for the sweeps' 1/2 factors: 1/4 (2-D), 1/8 (3-D),
+// 1/16 (2-D Strang: four sweeps per step).
+double scale_of(const dirac_grid *g) { return strang(g) ? 0.0625 : (ndim_of(g) == 3 ? 0.125 : 0.25); }
+int sweep_mode(const dirac_grid *g) { return strang(g) ? 2 : (ndim_of(g) == 3 ? 1 : 0); }
+int levels(const dirac_grid *g, int K) { return strang(g) ? 2 * K : K; }
 double cell_volume(const dirac_grid *g) {
     const double dx = g->cfg.dx;
     return ndim_of(g) == 3 ? dx * dx * dx : dx * dx;
@@ -158,12 +163,13 @@ void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
     const int64_t nx = g->cfg.n[0];
     const int64_t nr = (ndim_of(g) == 3) ? g->cfg.n[1] : g->cfg.n[2];
     const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
-    p.strip_w = 32 * P - 2 * K;
+    const int Lv = levels(g, K);
+    p.strip_w = 32 * P - 2 * Lv;
     p.nstrips = (nx + p.strip_w - 1) / p.strip_w;
     const int64_t want = (int64_t)g->sm_count * target_warps_per_sm;
     int64_t nsegs = std::max<int64_t>(1, want / std::max<int64_t>(1, p.nstrips * planes));
-    // keep segments at least 8K rows so halo rows stay a small fraction
-    const int64_t min_rows = std::max<int64_t>(8 * K, 16);
+    // keep segments at least 8 levels' worth of rows so halo rows stay a small fraction
+    const int64_t min_rows = std::max<int64_t>(8 * Lv, 16);
     nsegs = std::min<int64_t>(nsegs, std::max<int64_t>(1, nr / min_rows));
     p.seg_h = (nr + nsegs - 1) / nsegs;
     p.nsegs = (nr + p.seg_h - 1) / p.seg_h;
@@ -211,7 +217,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s) {
     a.nx = g->cfg.n[0];
     a.nr = (ndim_of(g) == 3) ? g->cfg.n[1] : g->cfg.n[2];
     a.nplanes = planes;
-    a.strip_w = 32 * p.P - 2 * K;
+    a.strip_w = 32 * p.P - 2 * levels(g, K);
     a.nstrips = (a.nx + a.strip_w - 1) / a.strip_w;
     a.nsegs = p.nsegs;
     a.seg_h = p.seg_h;
@@ -223,7 +229,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s) {
     a.vol = cell_volume(g);
     a.periodic = g->cfg.boundary == DIRAC_BC_PERIODIC;
     a.full_table = g->table_full;
-    const int mode = (ndim_of(g) == 3) ? 1 : 0;
+    const int mode = sweep_mode(g);
     cudaError_t e = g->fp32 ? launch_sweep_f32(a, mode, K, p.P, p.wpb, s) : launch_sweep_f64(a, mode, K, p.P, p.wpb, s);
     if (e != cudaSuccess) return cuda_fail(g, e, "sweep kernel launch");
     g->launches++;
@@ -334,10 +340,12 @@ void default_plan(dirac_grid *g) {
         make_plan(g, 1, pp > 0 ? pp : 2, 4, 16);
         return;
     }
-    int K = g->fp32 ? 2 : 1, P = g->fp32 ? 2 : 4;
+    const int mode = sweep_mode(g);
+    int K = g->fp32 ? 2 : 1, P = (g->fp32 || mode == 2) ? 2 : 4;
+    if (mode == 2) K = 1;
     if (k > 0) K = k;
     if (pp > 0) P = pp;
-    if (!sweep_supported(g->fp32, 0, K, P)) P = sweep_supported(g->fp32, 0, K, 4) ? 4 : 2;
+    if (!sweep_supported(g->fp32, mode, K, P)) P = sweep_supported(g->fp32, mode, K, 4) ? 4 : 2;
     make_plan(g, K, P, 4, g->fp32 ? 12 : 8);
 }
 
@@ -412,6 +420,7 @@ void dirac_default_config(dirac_config *cfg) {
     cfg->steps_per_launch = 0;
     cfg->use_graphs = 1;
     cfg->points_per_lane = 0;
+    cfg->splitting = DIRAC_LIE;
 }
 
 const char *dirac_last_error(const dirac_grid *g) { return g ? g->err.c_str() : g_thread_err.c_str(); }
@@ -433,15 +442,20 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
         return fail(nullptr, DIRAC_ERR_ARG, "flux_face must be -1 or in [1, nx-1]");
     const double ncells_d = (double)cfg->n[0] * (double)cfg->n[1] * (double)cfg->n[2];
     if (ncells_d > 4.0e10) return fail(nullptr, DIRAC_ERR_ARG, "grid too large");
+    if (cfg->splitting != DIRAC_LIE && cfg->splitting != DIRAC_STRANG)
+        return fail(nullptr, DIRAC_ERR_ARG, "splitting must be DIRAC_LIE or DIRAC_STRANG");
+    if (cfg->splitting == DIRAC_STRANG && cfg->ndim != 2)
+        return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_STRANG is implemented for 2-D grids");
+    const int vmode = cfg->splitting == DIRAC_STRANG ? 2 : 0;
     if (cfg->steps_per_launch != 0 &&
-        !(sweep_supported(cfg->precision == DIRAC_FP32, 0, cfg->steps_per_launch, 2) ||
-          sweep_supported(cfg->precision == DIRAC_FP32, 0, cfg->steps_per_launch, 4)))
-        return fail(nullptr, DIRAC_ERR_ARG, "steps_per_launch must be 0, 1, 2 (FP64) or 0, 1, 2, 4 (FP32)");
+        !(sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, 2) ||
+          sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, 4)))
+        return fail(nullptr, DIRAC_ERR_ARG, "unsupported steps_per_launch for this precision and splitting");
     if (cfg->points_per_lane != 0 && cfg->points_per_lane != 1 && cfg->points_per_lane != 2 &&
         cfg->points_per_lane != 4)
         return fail(nullptr, DIRAC_ERR_ARG, "points_per_lane must be 0, 1, 2 or 4");
     if (cfg->ndim == 2 && cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
-        !sweep_supported(cfg->precision == DIRAC_FP32, 0, cfg->steps_per_launch, cfg->points_per_lane))
+        !sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, cfg->points_per_lane))
         return fail(nullptr, DIRAC_ERR_ARG, "unsupported (steps_per_launch, points_per_lane) pair");
     if (std::getenv("DIRAC_INJECT_OOM")) return fail(nullptr, DIRAC_ERR_OOM, "allocation failure injected (DIRAC_INJECT_OOM)");
 
@@ -452,7 +466,7 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     g->fp32 = cfg->precision == DIRAC_FP32;
     g->elem = g->fp32 ? 4 : 8;
     g->ncells = cfg->n[0] * cfg->n[1] * cfg->n[2];
-    g->dt = cfg->dx / cfg->c;
+    g->dt = (cfg->splitting == DIRAC_STRANG ? 2.0 : 1.0) * cfg->dx / cfg->c;
     cudaError_t e = cudaSetDevice(cfg->device);
     if (e != cudaSuccess) {
         std::string msg = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
@@ -657,6 +671,11 @@ dirac_status dirac_autotune(dirac_grid *g) {
     if (g->cfg.ndim == 3) {
         for (int P : {1, 2, 4})
             for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm});
+    } else if (strang(g)) {
+        const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
+        for (auto &kp : KP)
+            if (sweep_supported(g->fp32, 2, kp[0], kp[1]))
+                for (int wsm : {4, 8, 12}) cands.push_back({kp[0], kp[1], 4, wsm});
     } else if (g->fp32) {
         const int KP[][2] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}, {4, 2}};
         for (auto &kp : KP)

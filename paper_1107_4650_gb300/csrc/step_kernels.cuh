@@ -120,18 +120,24 @@ template <int K>
 __device__ __forceinline__ void finish_flux(const SweepArgs &a);
 template <typename T, int K, int P> struct Ring;
 
-// MODE 0: 2-D step (x sweep, z sweep, phase), K steps per launch.
+// Pipelined levels of one launch: K steps, or 2K levels for the second-order splitting (mode 2).
+template <int K, int MODE> struct Levels { static constexpr int value = MODE == 2 ? 2 * K : K; };
+
+// MODE 0: 2-D first-order step (x sweep, z sweep, phase), K steps per launch.
 // MODE 1: 3-D x-y pass (x sweep, y sweep), K must be 1.
+// MODE 2: 2-D second-order (Strang) step x, z, phase(dt), z, x (Sec. 2.4), K steps = 2K levels per launch;
+//         the four sweeps' 1/2 factors ride in the phase coefficients as 1/16.
 template <typename T, int K, int P, int MODE>
 __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
+    constexpr int L = Levels<K, MODE>::value;
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t per_plane = a.nstrips * a.nsegs;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    unsigned char *wsmem = dyn_smem + (threadIdx.x >> 5) * Ring<T, K, P>::WARP_BYTES;
+    unsigned char *wsmem = dyn_smem + (threadIdx.x >> 5) * Ring<T, L, P>::WARP_BYTES;
     // Warps past the end skip the work but still reach the block-completion ticket below.
     if (wid < per_plane * a.nplanes) sweep_warp<T, K, P, MODE>(a, wid, lane, wsmem);
-    if (a.flux_face >= 0) finish_flux<K>(a);
+    if (a.flux_face >= 0) finish_flux<L>(a);
 }
 
 // Last-block fold of the per-warp flux partials: every block takes a ticket after its partials are
@@ -214,8 +220,75 @@ template <typename T, int K, int P> struct Ring {
 // Dynamic shared memory a block of `wpb` warps needs.
 template <typename T, int K, int P> constexpr int ring_smem_bytes(int wpb) { return wpb * Ring<T, K, P>::WARP_BYTES; }
 
+// x characteristics of a row (u = a + b travels +x, w = a - b travels -x) and the neighbours the x sweep
+// takes: u of the left cell and w of the right cell (warp shuffles; lane 0 and lane 31 take them from the
+// adjacent point of lanes 31 and 0).
+template <typename T, int P>
+__device__ __forceinline__ void x_characteristics(const Cx<T> (*s)[4], int lane, int src_prev, int src_next, Cx<T> *u14,
+                                                  Cx<T> *u23, Cx<T> *w14, Cx<T> *w23, Cx<T> *lu14, Cx<T> *lu23,
+                                                  Cx<T> *rw14, Cx<T> *rw23) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        u14[j] = cadd(s[j][0], s[j][3]);
+        w14[j] = csub(s[j][0], s[j][3]);
+        u23[j] = cadd(s[j][1], s[j][2]);
+        w23[j] = csub(s[j][1], s[j][2]);
+    }
+    Cx<T> pu14[P], pu23[P], nw14[P], nw23[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        pu14[j] = shfl_c(u14[j], src_prev);
+        pu23[j] = shfl_c(u23[j], src_prev);
+        nw14[j] = shfl_c(w14[j], src_next);
+        nw23[j] = shfl_c(w23[j], src_next);
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int jp = j > 0 ? j - 1 : 0;
+        const int jn = j < P - 1 ? j + 1 : P - 1;
+        lu14[j] = (lane == 0) ? pu14[jp] : pu14[j];
+        lu23[j] = (lane == 0) ? pu23[jp] : pu23[j];
+        rw14[j] = (lane == 31) ? nw14[jn] : nw14[j];
+        rw23[j] = (lane == 31) ? nw23[jn] : nw23[j];
+    }
+}
+
+// One row of the face flux: the face lane's 8 values go to lane (row % 32) of the hand-off area; at every 32nd
+// row (or the segment's last) all lanes fold their rows: scale (|u14|^2 + |u23|^2) - scale (|w14|^2 + |w23|^2),
+// scale = 1/2 for a state at its true size, 2 for one held at half size.
+template <typename T, int P>
+__device__ __forceinline__ void flux_row(const Cx<T> *lu14, const Cx<T> *lu23, const Cx<T> *w14, const Cx<T> *w23,
+                                         int face_j, int face_lane, int lane, int64_t row_in_seg, bool last_row, T *g,
+                                         double scale, double &facc) {
+    T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        if (j == face_j) {
+            v[0] = lu14[j].re; v[1] = lu14[j].im; v[2] = lu23[j].re; v[3] = lu23[j].im;
+            v[4] = w14[j].re;  v[5] = w14[j].im;  v[6] = w23[j].re;  v[7] = w23[j].im;
+        }
+    }
+    const int t = (int)(row_in_seg & 31);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const T x = __shfl_sync(0xffffffffu, v[k], face_lane);
+        if (lane == t) g[k * 32 + t] = x;
+    }
+    if (t == 31 || last_row) {
+        __syncwarp();
+        if (lane <= t) {
+            const T *gl = g + lane;
+            const double right = __dmul_rn(scale, __dadd_rn(abs2d(Cx<T>{gl[0], gl[32]}), abs2d(Cx<T>{gl[64], gl[96]})));
+            const double left = __dmul_rn(scale, __dadd_rn(abs2d(Cx<T>{gl[128], gl[160]}), abs2d(Cx<T>{gl[192], gl[224]})));
+            facc = __dadd_rn(facc, __dsub_rn(right, left));
+        }
+        __syncwarp();
+    }
+}
+
 template <typename T, int K, int P, int MODE>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem) {
+    constexpr int L = Levels<K, MODE>::value;  // pipelined levels (one row and one x cell of halo each)
     const int64_t per_plane = a.nstrips * a.nsegs;
     const int64_t plane = wid / per_plane;
     const int64_t rem = wid - plane * per_plane;
@@ -226,7 +299,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     const bool ring = !per;  // periodic grids wrap the strip: plain loads
     const int64_t x_own0 = strip * a.strip_w;
     const int64_t x_own1 = min(x_own0 + a.strip_w, nx);
-    const int64_t xa = x_own0 - K;
+    const int64_t xa = x_own0 - L;
     const int64_t r_begin = seg * a.seg_h;
     const int64_t r_end = min(r_begin + a.seg_h, nr);
     const T *in = static_cast<const T *>(a.in) + plane * nr * nx * 8;
@@ -242,7 +315,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     }
     // phase coefficients per x column (mode 0, x-only table)
     Cx<T> pu[P], pd[P];
-    if (MODE == 0 && !a.full_table) {
+    if (MODE != 1 && !a.full_table) {
 #pragma unroll
         for (int j = 0; j < P; ++j) load_tab(static_cast<const T *>(a.table) + xl[j] * 4, pu[j], pd[j]);
     }
@@ -253,14 +326,14 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     const bool has_face = a.flux_face >= x_own0 && a.flux_face < x_own1;
     const int face_off = (int)(a.flux_face - xa);
     const int face_lane = face_off & 31, face_j = face_off >> 5;
-    double facc[K];
+    double facc[L];
 #pragma unroll
-    for (int s = 0; s < K; ++s) facc[s] = 0.0;
+    for (int s = 0; s < L; ++s) facc[s] = 0.0;
 
     // "+" characteristic sums of the two previous rows per level: rows q-2 (A) and q-1 (B)
-    Cx<T> UA[K][P][2], UB[K][P][2];
+    Cx<T> UA[L][P][2], UB[L][P][2];
 #pragma unroll
-    for (int s = 0; s < K; ++s)
+    for (int s = 0; s < L; ++s)
 #pragma unroll
         for (int j = 0; j < P; ++j)
 #pragma unroll
@@ -272,14 +345,14 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     const int src_prev = (lane + 31) & 31, src_next = (lane + 1) & 31;
 
     // Row ring: the copied span of a row is the strip's cells clipped to the grid.
-    using RG = Ring<T, K, P>;
+    using RG = Ring<T, L, P>;
     T *gsm = reinterpret_cast<T *>(wsmem + 128 + RG::SLOTS * RG::ROW_BYTES);  // flux hand-off [K][8][32]
     const int64_t cx0 = max(xa, (int64_t)0), cx1 = min(xa + 32 * P, nx);
     const uint32_t copy_bytes = (uint32_t)((cx1 - cx0) * 8 * (int64_t)sizeof(T));
     const uint32_t bar0 = smem_u32(wsmem);
     const uint32_t slot0 = smem_u32(wsmem + 128);
     const uint32_t dst_off = (uint32_t)((cx0 - xa) * 8 * (int64_t)sizeof(T));
-    const int64_t r_first = r_begin - K, r_last = r_end + K;  // rows [r_first, r_last) are read
+    const int64_t r_first = r_begin - L, r_last = r_end + L;  // rows [r_first, r_last) are read
     uint32_t phase_bits = 0, pending = 0;
     bool aborted = false;
     if (ring) {
@@ -335,10 +408,55 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
             }
         }
 #pragma unroll
-        for (int lev = 0; lev < K; ++lev) {
+        for (int lev = 0; lev < L; ++lev) {
             const int64_t q = r - lev;  // row of the level-lev state in st
             // rows of level lev+1 that later levels (or the store) use: [r_first + lev + 1, r_last - lev - 1)
             const bool need_out = (q - 1 >= r_first + lev + 1) && (q - 1 < r_last - lev - 1);
+            if (MODE == 2 && (lev & 1)) {
+                // second half of a Strang step: z sweep of rows q-2 and q into row q-1, then the x sweep of
+                // row q-1.  The input is 1/4 of the state (the phase carried 1/16), the z-swept row 1/2 of it.
+                const bool zrow_ok = per || (q - 1 >= 0 && q - 1 < nr);
+                Cx<T> zs[P][4];
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    const Cx<T> U13 = cadd(st[j][0], st[j][2]), U24 = csub(st[j][1], st[j][3]);
+                    const Cx<T> W13 = csub(st[j][0], st[j][2]), W24 = cadd(st[j][1], st[j][3]);
+                    zs[j][0] = cadd(UA[lev][j][0], W13);
+                    zs[j][2] = csub(UA[lev][j][0], W13);
+                    zs[j][1] = cadd(UA[lev][j][1], W24);
+                    zs[j][3] = csub(W24, UA[lev][j][1]);
+                    UA[lev][j][0] = UB[lev][j][0];
+                    UA[lev][j][1] = UB[lev][j][1];
+                    UB[lev][j][0] = U13;
+                    UB[lev][j][1] = U24;
+                    if (!zrow_ok)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) zs[j][c] = Cx<T>{T(0), T(0)};
+                }
+                if (!need_out) {
+#pragma unroll
+                    for (int j = 0; j < P; ++j)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) st[j][c] = Cx<T>{T(0), T(0)};
+                    continue;
+                }
+                Cx<T> u14[P], u23[P], w14[P], w23[P], lu14[P], lu23[P], rw14[P], rw23[P];
+                x_characteristics<T, P>(zs, lane, src_prev, src_next, u14, u23, w14, w23, lu14, lu23, rw14, rw23);
+                if (has_face && q - 1 >= r_begin && q - 1 < r_end)
+                    flux_row<T, P>(lu14, lu23, w14, w23, face_j, face_lane, lane, q - 1 - r_begin, q - 1 == r_end - 1,
+                                   gsm + lev * 8 * 32, 2.0, facc[lev]);
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    const bool keep = per || (zrow_ok && xin[j]);
+                    const Cx<T> b0 = cadd(lu14[j], rw14[j]), b3 = csub(lu14[j], rw14[j]);
+                    const Cx<T> b1 = cadd(lu23[j], rw23[j]), b2 = csub(lu23[j], rw23[j]);
+                    st[j][0] = keep ? b0 : Cx<T>{T(0), T(0)};
+                    st[j][1] = keep ? b1 : Cx<T>{T(0), T(0)};
+                    st[j][2] = keep ? b2 : Cx<T>{T(0), T(0)};
+                    st[j][3] = keep ? b3 : Cx<T>{T(0), T(0)};
+                }
+                continue;
+            }
             Cx<T> u14[P], u23[P], w14[P], w23[P];
 #pragma unroll
             for (int j = 0; j < P; ++j) {
@@ -365,32 +483,9 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 rw14[j] = (lane == 31) ? nw14[jn] : nw14[j];
                 rw23[j] = (lane == 31) ? nw23[jn] : nw23[j];
             }
-            if (has_face && q >= r_begin && q < r_end) {
-                T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-#pragma unroll
-                for (int j = 0; j < P; ++j) {
-                    if (j == face_j) {
-                        v[0] = lu14[j].re; v[1] = lu14[j].im; v[2] = lu23[j].re; v[3] = lu23[j].im;
-                        v[4] = w14[j].re;  v[5] = w14[j].im;  v[6] = w23[j].re;  v[7] = w23[j].im;
-                    }
-                }
-                const int t = (int)((q - r_begin) & 31);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const T x = __shfl_sync(0xffffffffu, v[k], face_lane);
-                    if (lane == t) gsm[(lev * 8 + k) * 32 + t] = x;
-                }
-                if (t == 31 || q == r_end - 1) {
-                    __syncwarp();
-                    if (lane <= t) {
-                        const T *gl = gsm + lev * 8 * 32 + lane;
-                        const double right = __dmul_rn(0.5, __dadd_rn(abs2d(Cx<T>{gl[0], gl[32]}), abs2d(Cx<T>{gl[64], gl[96]})));
-                        const double left = __dmul_rn(0.5, __dadd_rn(abs2d(Cx<T>{gl[128], gl[160]}), abs2d(Cx<T>{gl[192], gl[224]})));
-                        facc[lev] = __dadd_rn(facc[lev], __dsub_rn(right, left));
-                    }
-                    __syncwarp();
-                }
-            }
+            if (has_face && q >= r_begin && q < r_end)
+                flux_row<T, P>(lu14, lu23, w14, w23, face_j, face_lane, lane, q - r_begin, q == r_end - 1,
+                               gsm + lev * 8 * 32, 0.5, facc[lev]);
             const bool out_row_ok = per || (q - 1 >= 0 && q - 1 < nr);
 #pragma unroll
             for (int j = 0; j < P; ++j) {
@@ -400,7 +495,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 const Cx<T> b1 = cadd(lu23[j], rw23[j]);
                 const Cx<T> b2 = csub(lu23[j], rw23[j]);
                 Cx<T> o[4];
-                if (MODE == 0) {
+                if (MODE != 1) {
                     // z sweep (Eq. sol_dis_3): +z movers (b1+b3, b2-b4), -z movers (b1-b3, b2+b4)
                     const Cx<T> U13 = cadd(b0, b2), U24 = csub(b1, b3);
                     if (need_out) {
@@ -452,7 +547,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 }
             }
         }
-        const int64_t ro = r - K;
+        const int64_t ro = r - L;
         if (ro >= r_begin && ro < r_end) {
 #pragma unroll
             for (int j = 0; j < P; ++j) {
@@ -492,7 +587,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     if (aborted) return;
     if (has_face) {
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
+        for (int s = 0; s < L; ++s) {
             double v = facc[s];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));

@@ -161,14 +161,18 @@ def klein_config_2d(seed: int = SEED, side: int = 2048, nsteps: int = 4000, m: f
 
 
 ALLOWED_SIDES = (256, 384, 512, 768, 1024)
+BEYOND_STEP = 128  # cells kept between the step face and the right edge
 
 
 def klein_ensemble(nruns: int = 512, seed: int = SEED + 1, m: float = M_E, c: float = C_AU):
     """Batched ensemble draws: side U{256..1024}, V0 ~ U[0.5, 3.0] mc^2, p0 ~ U[0.2, 1.0] mc,
-    width ~ U[40, 150] dx.  A drawn side smaller than 8 width + 16 cells is raised to the smallest
-    allowed side that holds the packet (1024 at most); the step face sits 8 widths + 8 cells from
-    the left edge, the packet 4 widths left of it; the step count is the time for the packet
-    centre to travel 8 widths at the group velocity p0 c^2 / E plus 200, clamped to [2000, 6000].
+    width ~ U[40, 150] dx.  A drawn side smaller than 8 width + 136 cells is raised to the smallest
+    allowed side that holds the packet and a 128-cell region beyond the step (1024 at most); the step
+    face sits 8 widths + 8 cells from the left edge but at least 128 cells from the right edge (the
+    region beyond a step must be long against the evanescent length c/(mc^2), about 6 cells, or waves
+    in the gap tunnel into the outflowing boundary), the packet 4 widths left of the face; the step
+    count is the time for the packet centre to travel 8 widths at the group velocity p0 c^2 / E plus
+    200, clamped to [2000, 6000].
     Returns (runs, log) where log lists every deviation from the drawn values."""
     rng = np.random.default_rng(seed)
     dx = DX_DEFAULT
@@ -178,7 +182,7 @@ def klein_ensemble(nruns: int = 512, seed: int = SEED + 1, m: float = M_E, c: fl
         V0 = rng.uniform(0.5, 3.0) * m * c * c
         p0 = rng.uniform(0.2, 1.0) * m * c
         w_cells = rng.uniform(40, 150)
-        need = 8 * w_cells + 16
+        need = 8 * w_cells + 8 + BEYOND_STEP
         if side < need:
             bigger = [s for s in ALLOWED_SIDES if s >= need]
             new = bigger[0] if bigger else ALLOWED_SIDES[-1]
@@ -187,7 +191,7 @@ def klein_ensemble(nruns: int = 512, seed: int = SEED + 1, m: float = M_E, c: fl
         E = np.sqrt(p0 * p0 * c * c + m * m * c ** 4)
         vg_over_c = p0 * c / E
         nsteps = int(np.clip(np.ceil(8 * w_cells / vg_over_c) + 200, 2000, 6000))
-        face = min(int(np.ceil(8 * w_cells)) + 8, side - 8)
+        face = min(int(np.ceil(8 * w_cells)) + 8, side - BEYOND_STEP)
         runs.append(KleinRun(side=side, V0=V0, p0=p0, width=w_cells * dx, nsteps=nsteps, dx=dx, L=4 * dx,
                              face=face))
     return runs, log

@@ -105,7 +105,8 @@ def continuum_evolution_2d(psi0: np.ndarray, dx: float, t: float, m: float, c: f
     PX, PZ = np.meshgrid(px, pz)
     E = np.sqrt((c * PX) ** 2 + (c * PZ) ** 2 + (m * c * c) ** 2)
     H = c * (PX[..., None, None] * ALPHA[0] + PZ[..., None, None] * ALPHA[2]) + m * c * c * BETA
-    U = np.cos(E * t)[..., None, None] * I4 - 1j * np.sin(E * t)[..., None, None] * H / E[..., None, None]
+    sinE = np.where(E > 0, np.sin(E * t) / np.where(E > 0, E, 1.0), t)  # sin(Et)/E -> t at E = 0 (m = 0, p = 0)
+    U = np.cos(E * t)[..., None, None] * I4 - 1j * sinE[..., None, None] * H
     hat = np.fft.fft2(psi0[:, 0], axes=(0, 1))
     hat = np.einsum("zxab,zxb->zxa", U, hat)
     return np.fft.ifft2(hat, axes=(0, 1))[:, None]

@@ -340,3 +340,53 @@ def test_strang_flux_identity(oracle_mod):
     o1 = oracle.observables(out, 2, run.dx, (x_min, 0.0, z_min), face)
     assert F > 1e-3
     assert abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
+
+
+# ---------------------------------------------------------------- massless 2-D packet (Sec. 5.1.1, App. B)
+
+def _massless_closed_forms(t, delta, c):
+    """psi1 of the spin-up massless Gaussian at r = 0 (erfi form, written with Dawson's function
+    D(u) = sqrt(pi)/2 e^{-u^2} erfi(u)) and at r = ct (2F2 form), both with ct in place of the printed t."""
+    mpmath = pytest.importorskip("mpmath")
+    from scipy.special import dawsn
+    u = c * t / (2 * delta)
+    r0 = 1.0 - 2.0 * u * dawsn(u)
+    rct = float(mpmath.hyp2f2(0.25, 0.75, 0.5, 0.5, -(c * t) ** 2 / delta ** 2))
+    return r0, rct
+
+
+def test_massless_packet_closed_forms_against_spectral_evolution():
+    """The two closed forms equal the exact continuum evolution (FFT) of the same packet."""
+    n, dx = 255, 1.0 / 64
+    delta = 10 * dx
+    x = (np.arange(n) - n // 2) * dx
+    X, Z = np.meshgrid(x, x)
+    psi0 = np.zeros((n, 1, n, 4), complex)
+    psi0[:, 0, :, 0] = np.exp(-(X ** 2 + Z ** 2) / (4 * delta ** 2))
+    c0 = n // 2
+    for steps in (10, 25):
+        t = steps * dx / C
+        ex = A.continuum_evolution_2d(psi0, dx, t, 0.0, C)
+        r0, rct = _massless_closed_forms(t, delta, C)
+        assert abs(ex[c0, 0, c0, 0] - r0) < 1e-6 and abs(ex[c0, 0, c0 + steps, 0] - rct) < 1e-6
+
+
+def test_massless_scheme_converges_to_closed_forms(oracle_mod):
+    """m = 0, V = 0 (Sec. 5.1.1): psi1 of the scheme at the packet centre and on the circle r = ct (a grid
+    cell, since c dt = dx) approaches the closed forms as the mesh is refined at fixed physical time."""
+    half = 2.5
+    delta = 10 * (2 * half / 161)
+    errs = []
+    for f in (1, 2):
+        n = 160 * f + 1
+        dx = 2 * half / n
+        x = (np.arange(n) - n // 2) * dx
+        X, Z = np.meshgrid(x, x)
+        psi0 = np.zeros((n, 1, n, 4), complex)
+        psi0[:, 0, :, 0] = np.exp(-(X ** 2 + Z ** 2) / (4 * delta ** 2))
+        steps = 20 * f
+        out, _ = oracle.step(psi0, 2, 0.0, C, dx, steps)
+        r0, rct = _massless_closed_forms(steps * dx / C, delta, C)
+        c0 = n // 2
+        errs.append(max(abs(out[c0, 0, c0, 0] - r0), abs(out[c0, 0, c0 + steps, 0] - rct)))
+    assert errs[0] < 2e-4 and errs[0] / errs[1] > 3.0, errs

@@ -284,3 +284,68 @@ def test_autotune_preserves_state_and_result(D):
     finally:
         D.dirac_destroy(h)
     assert _bits_equal(got, want)
+
+
+# ------------------------------------------------------------------ second-order (Strang) splitting, 2-D
+
+@pytest.mark.parametrize("fp32,K,P", [(False, 1, 1), (False, 1, 2), (True, 1, 2), (True, 1, 4), (True, 2, 2)])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_strang_2d_against_oracle(D, fp32, K, P, periodic):
+    nx, nz, nsteps = 90, 70, 9
+    psi = W.random_state(nz, 1, nx, seed=nx + K + P)
+    V = np.random.default_rng(4).uniform(-2e4, 6e4, nx)
+    face = 40
+    want, F = oracle.step_strang2d(psi, 1.0, C, DX, nsteps, V=V, periodic=periodic, flux_face=face)
+    cfg = D.make_config((nx, 1, nz), precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO, flux_face=face,
+                        steps_per_launch=K, points_per_lane=P, splitting=D.DIRAC_STRANG)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        dt = np.complex64 if fp32 else np.complex128
+        D.dirac_set_state(h, np.ascontiguousarray(psi.astype(dt)))
+        D.dirac_step(h, nsteps)
+        got = np.empty(psi.shape, dtype=dt)
+        D.dirac_get_state(h, got)
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    if fp32:
+        assert rel_l2(got.astype(np.complex128), want) < 2e-5
+        assert abs(obs["flux_cum"] - F) < 1e-5 * abs(F) + 1e-9
+    else:
+        assert _bits_equal(got, want), rel_l2(got, want)
+        assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+
+
+def test_strang_klein_packet_matches_oracle(D):
+    run = W.KleinRun(side=256, V0=2.5 * C * C, p0=0.6 * C, width=14 * DX, nsteps=120, face=150)
+    psi0 = run.state()
+    V = run.potential()
+    x_min, z_min, _, _, face = run.geometry()
+    want, F = oracle.step_strang2d(psi0, 1.0, C, DX, run.nsteps, V=V, flux_face=face)
+    cfg = D.make_config((256, 1, 256), x_min=(x_min, 0.0, z_min), flux_face=face, splitting=D.DIRAC_STRANG)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi0)
+        D.dirac_step(h, run.nsteps)
+        got = np.empty_like(psi0)
+        D.dirac_get_state(h, got)
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want)
+    assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+
+
+def test_massless_packet_bit_exact(D):
+    n = 161
+    dx = 5.0 / n
+    x = (np.arange(n) - n // 2) * dx
+    X, Z = np.meshgrid(x, x)
+    psi0 = np.zeros((n, 1, n, 4), complex)
+    psi0[:, 0, :, 0] = np.exp(-(X ** 2 + Z ** 2) / (4 * (10 * dx) ** 2))
+    want, _ = oracle.step(psi0, 2, 0.0, C, dx, 20)
+    got, _, _ = run_gpu(D, psi0, 2, 20, dx=dx, m=0.0, x_min=(-(n // 2 + 0.5) * dx, 0.0, -(n // 2 + 0.5) * dx))
+    assert _bits_equal(got, want)
