@@ -126,6 +126,13 @@ typedef struct {
  * Returns DIRAC_ERR_NONFINITE (obs still filled) when the norm is NaN or Inf. */
 dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, int density_on_device);
 
+/* Absorbing layer (an addition to the paper's scheme, which names absorbing boundaries as future work):
+ * factors a(x) in (0, 1] per x column (count = nx, host pointer) multiplied into the phase coefficients,
+ * so the state is damped by a(x) every step.  The zero boundary of Sec. 5 partially reflects a massive
+ * wave; layers a few dozen columns deep with a(x) rising smoothly to 1 absorb it instead.  count = 0 or
+ * a = NULL removes the layer.  Rebuilds the phase table from the last potential set. */
+dirac_status dirac_set_absorber(dirac_grid *g, const double *a, int64_t count);
+
 /* Checkpoint support: sets the step counter and cumulative flux (after dirac_set_state). */
 dirac_status dirac_set_counters(dirac_grid *g, int64_t step, double flux_cum);
 
@@ -168,6 +175,8 @@ typedef struct {
     double p0;      /* packet momentum along x */
     double width;   /* packet width, > 0 */
     double x0;      /* packet centre along x (the step is at x = 0) */
+    int64_t absorb; /* absorbing-layer columns at each x edge (0: none); the initial packet is zero there */
+    double eta;     /* layer strength: factor exp(-eta s^2) per step, s = depth into the layer / absorb */
 } dirac_klein_run;
 
 typedef struct {
@@ -198,8 +207,12 @@ dirac_status dirac_batch_reset(dirac_batch *b);
 dirac_status dirac_batch_set_state(dirac_batch *b, int run, const void *psi, int on_device);
 
 /* Replaces run `run`'s x-only potential (side values, host pointer) by V; coefficients as in
- * dirac_set_potential. */
+ * dirac_set_potential, times the run's absorbing-layer factors. */
 dirac_status dirac_batch_set_potential(dirac_batch *b, int run, const double *V, int64_t count);
+
+/* Replaces run `run`'s absorbing-layer factors by a (side values in (0, 1], host pointer); they multiply the
+ * phase coefficients from the next dirac_batch_set_potential on. */
+dirac_status dirac_batch_set_absorber(dirac_batch *b, int run, const double *a, int64_t count);
 
 /* Advances every run by its nsteps (asynchronous on the batch stream); measures each run's initial norm
  * first.  A second call needs dirac_batch_reset in between (DIRAC_ERR_STATE otherwise). */
@@ -270,10 +283,11 @@ dirac_status dirac_surrogate_get_params(dirac_surrogate *s, float *params);
 dirac_status dirac_surrogate_set_params(dirac_surrogate *s, const float *params);
 
 /* Transmission for n queries: the network inside the box, the batched solver (geometry of the Klein
- * ensemble: side = smallest of 256, 384, 512, 768, 1024 holding 8 width + 136 cells (1024 at most), face
- * 8 width + 8 cells from the left edge and at least 128 cells from the right edge, packet 4 widths left
- * of the step, L = 4 dx, steps = time for the packet to travel 8 widths at its group velocity + 200,
- * clamped to [2000, 6000]) outside it, with solver_cfg's precision.  used_solver (nullable) receives 1 for the points the solver answered. */
+ * ensemble: 64-column absorbing layers (eta 0.1) at both x edges, side = smallest of 256, 384, 512, 768,
+ * 1024 holding 8 width + 264 cells (1024 at most), face 8 width + 8 cells right of the left layer and at
+ * least 192 cells from the right edge, packet 4 widths left of the step, L = 4 dx, steps = time for the
+ * packet to travel 8 widths at its group velocity + 200, clamped to [2000, 6000]) outside it, with
+ * solver_cfg's precision.  used_solver (nullable) receives 1 for the points the solver answered. */
 dirac_status dirac_surrogate_query(dirac_surrogate *s, const double *X, int64_t n, const dirac_batch_config *solver_cfg,
                                    double *T_out, int *used_solver);
 

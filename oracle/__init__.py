@@ -58,6 +58,8 @@ def _load():
         for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables,
                   lib.oracle_step_strang2d):
             f.restype = ctypes.c_int
+        lib.oracle_set_absorber.argtypes = [P]
+        lib.oracle_set_absorber.restype = None
         _lib = lib
     return _lib
 
@@ -105,19 +107,36 @@ def phase(psi, m: float, c: float, dt: float, V=None) -> np.ndarray:
     return out
 
 
+class _Absorber:
+    """Context: per-x-column damping factors a(x) multiplied into the phase coefficients (None: none)."""
+    def __init__(self, a, nx):
+        self.a = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+        if self.a is not None and self.a.size != nx:
+            raise ValueError("absorber needs one factor per x column")
+
+    def __enter__(self):
+        _load().oracle_set_absorber(None if self.a is None else self.a.ctypes.data)
+        return self
+
+    def __exit__(self, *exc):
+        _load().oracle_set_absorber(None)
+
+
 def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
-         periodic: bool = False, flux_face: int = -1, flux_cum: float = 0.0):
+         periodic: bool = False, flux_face: int = -1, flux_cum: float = 0.0, absorber=None):
     """nsteps first-order split steps (Eqs. split1-4 discretised as sol_dis_1-4), dt = dx/c.
 
     Returns (psi_out, flux_cum): the cumulative probability carried across the x face
     `flux_face` (between cells flux_face-1 and flux_face), added to the given start value.
+    `absorber`: optional per-x-column factors a(x) in (0, 1] applied with the phase (not in the paper).
     """
     out = _as_state(psi)
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    rc = _load().oracle_step(out.ctypes.data, _dims(out), int(ndim), int(bool(periodic)), float(m), float(c),
-                             float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
-                             int(flux_face), ctypes.addressof(fc))
+    with _Absorber(absorber, out.shape[2]):
+        rc = _load().oracle_step(out.ctypes.data, _dims(out), int(ndim), int(bool(periodic)), float(m), float(c),
+                                 float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
+                                 int(flux_face), ctypes.addressof(fc))
     if rc != 0:
         raise MemoryError("oracle_step")
     return out, fc.value

@@ -123,6 +123,12 @@ static double potential(const double *V, int layout, const int64_t n[3], int64_t
  * psi <- exp(-i beta m c^2 dt - i V dt) psi, i.e. components 1,2 multiplied by
  * exp(-i (m c^2 dt + V dt)) and components 3,4 by exp(-i (V dt - m c^2 dt)).
  * (The U matrix of Sec. 2.3 at A = 0 is diag(e^{-i mu}, e^{-i mu}, e^{i mu}, e^{i mu}).) */
+static const double *g_absorb = NULL;  /* optional per-x-column damping factor, see oracle_set_absorber */
+
+/* Absorbing layer (not part of the paper's scheme): a factor a(x) in (0, 1] per x column multiplied into
+ * both phase coefficients of that column, i.e. psi <- a(x) exp(-i ...) psi each step.  NULL removes it. */
+void oracle_set_absorber(const double *a) { g_absorb = a; }
+
 int oracle_phase(double *psi_d, const int64_t n[3], double m, double c, double dt,
                  const double *V, int layout) {
     cplx *psi = (cplx *)psi_d;
@@ -136,6 +142,11 @@ int oracle_phase(double *psi_d, const int64_t n[3], double m, double c, double d
                 double t_dn = vdt - mu;
                 cplx p_up = {cos(t_up), -sin(t_up)};
                 cplx p_dn = {cos(t_dn), -sin(t_dn)};
+                if (g_absorb) {
+                    const double a = g_absorb[i];
+                    p_up.re = p_up.re * a; p_up.im = p_up.im * a;
+                    p_dn.re = p_dn.re * a; p_dn.im = p_dn.im * a;
+                }
                 cplx *q = psi + ((k * n[1] + j) * n[0] + i) * 4;
                 q[0] = c_mul(q[0], p_up);
                 q[1] = c_mul(q[1], p_up);

@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dirac_step": (I, [P, I64]),
         "dirac_observables": (I, [P, ctypes.POINTER(dirac_obs), P, I]),
         "dirac_set_counters": (I, [P, I64, D]),
+        "dirac_set_absorber": (I, [P, P, I64]),
         "dirac_get_info": (I, [P, ctypes.POINTER(dirac_info)]),
         "dirac_autotune": (I, [P]),
         "dirac_last_error": (ctypes.c_char_p, [P]),
@@ -168,6 +169,15 @@ def dirac_observables(h, density=None) -> dict:
             "centroid": tuple(obs.centroid), "step": obs.step}
 
 
+def dirac_set_absorber(h, a) -> None:
+    """Per-x-column damping factors in (0, 1] (None: remove)."""
+    if a is None:
+        _check(load_library().dirac_set_absorber(h, None, 0), h)
+        return
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    _check(load_library().dirac_set_absorber(h, a.ctypes.data, a.size), h)
+
+
 def dirac_set_counters(h, step: int, flux_cum: float) -> None:
     _check(load_library().dirac_set_counters(h, int(step), float(flux_cum)), h)
 
@@ -223,7 +233,8 @@ def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRA
 class dirac_klein_run(ctypes.Structure):
     _fields_ = [("side", ctypes.c_int64), ("face", ctypes.c_int64), ("nsteps", ctypes.c_int64),
                 ("V0", ctypes.c_double), ("L", ctypes.c_double), ("p0", ctypes.c_double),
-                ("width", ctypes.c_double), ("x0", ctypes.c_double)]
+                ("width", ctypes.c_double), ("x0", ctypes.c_double), ("absorb", ctypes.c_int64),
+                ("eta", ctypes.c_double)]
 
 
 class dirac_batch_config(ctypes.Structure):
@@ -253,6 +264,7 @@ def _batch_lib():
         "dirac_batch_reset": (I, [P]),
         "dirac_batch_set_state": (I, [P, I, P, I]),
         "dirac_batch_set_potential": (I, [P, I, P, I64]),
+        "dirac_batch_set_absorber": (I, [P, I, P, I64]),
         "dirac_batch_run": (I, [P]),
         "dirac_batch_results": (I, [P, DP, DP, DP]),
         "dirac_batch_get_state": (I, [P, I, P, I]),
@@ -279,7 +291,7 @@ def klein_runs_array(runs) -> "ctypes.Array":
     """ctypes array of dirac_klein_run from objects with side, face, nsteps, V0, L, p0, width, x0 (or dicts)."""
     arr = (dirac_klein_run * len(runs))()
     for i, r in enumerate(runs):
-        get = (lambda k: r[k]) if isinstance(r, dict) else (lambda k: getattr(r, k))
+        get = (lambda k: r.get(k, 0)) if isinstance(r, dict) else (lambda k: getattr(r, k, 0))
         for f, _ in dirac_klein_run._fields_:
             setattr(arr[i], f, get(f))
     return arr
@@ -314,6 +326,11 @@ def dirac_batch_set_state(h, run: int, psi) -> None:
 def dirac_batch_set_potential(h, run: int, V) -> None:
     V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
     _bcheck(_batch_lib().dirac_batch_set_potential(h, int(run), V.ctypes.data, V.size), h)
+
+
+def dirac_batch_set_absorber(h, run: int, a) -> None:
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    _bcheck(_batch_lib().dirac_batch_set_absorber(h, int(run), a.ctypes.data, a.size), h)
 
 
 def dirac_batch_run(h) -> None:

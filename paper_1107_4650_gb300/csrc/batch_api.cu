@@ -49,6 +49,8 @@ struct dirac_batch {
     int64_t nchunks = 0;
     int64_t *d_cell_off = nullptr;
     double *d_init = nullptr;  // x0, k0, width, C per run
+    int64_t *d_absorb = nullptr;
+    std::vector<std::vector<double>> mask;  // absorbing-layer factors per run (side values)
     unsigned *counters = nullptr;  // counter, ticket, err, pad
     int *d_order_main = nullptr, *d_order_rem = nullptr;
     int64_t *d_off_main = nullptr, *d_off_rem = nullptr;
@@ -189,6 +191,7 @@ dirac_status init_states(dirac_batch *b) {
     ia.k0 = b->d_init + b->nruns;
     ia.width = b->d_init + 2 * b->nruns;
     ia.spinC = b->d_init + 3 * b->nruns;
+    ia.absorb = b->d_absorb;
     ia.nruns = b->nruns;
     ia.dx = b->cfg.dx;
     BCK(b, launch_batch_init(ia, b->fp32, b->stream));
@@ -287,7 +290,8 @@ dirac_status dirac_batch_create(const dirac_klein_run *runs, int nruns, const di
     for (int r = 0; r < nruns; ++r) {
         const dirac_klein_run &k = runs[r];
         if (k.side < 8 || k.side > 65536 || k.face < 1 || k.face > k.side - 1 || k.nsteps < 0 || !(k.L > 0) ||
-            !(k.width > 0) || !std::isfinite(k.V0) || !std::isfinite(k.p0) || !std::isfinite(k.x0))
+            !(k.width > 0) || !std::isfinite(k.V0) || !std::isfinite(k.p0) || !std::isfinite(k.x0) ||
+            k.absorb < 0 || 2 * k.absorb > k.side || !(k.eta >= 0) || !std::isfinite(k.eta))
             return bfail(nullptr, DIRAC_ERR_ARG, "run " + std::to_string(r) + " has an invalid field");
     }
     const int fp32 = cfg->precision == DIRAC_FP32;
@@ -339,6 +343,20 @@ dirac_status dirac_batch_create(const dirac_klein_run *runs, int nruns, const di
     if ((st = balloc(b, &b->d_cell_off, (nruns + 1) * sizeof(int64_t))) != DIRAC_OK) return fail_release(st);
     if ((st = balloc(b, &b->d_chunk_off, (nruns + 1) * sizeof(int64_t))) != DIRAC_OK) return fail_release(st);
     if ((st = balloc(b, &b->d_init, 4 * nruns * sizeof(double))) != DIRAC_OK) return fail_release(st);
+    if ((st = balloc(b, &b->d_absorb, nruns * sizeof(int64_t))) != DIRAC_OK) return fail_release(st);
+    std::vector<int64_t> absorb(nruns);
+    b->mask.resize(nruns);
+    for (int r = 0; r < nruns; ++r) {
+        const dirac_klein_run &k = runs[r];
+        absorb[r] = k.absorb;
+        b->mask[r].assign(k.side, 1.0);
+        for (int64_t i = 0; i < k.side && k.absorb > 0; ++i) {
+            const double sl = std::min(1.0, std::max(0.0, (double)(k.absorb - i) / (double)k.absorb));
+            const double sr = std::min(1.0, std::max(0.0, (double)(i - (k.side - k.absorb) + 1) / (double)k.absorb));
+            const double sv = std::max(sl, sr);
+            b->mask[r][i] = std::exp(-k.eta * sv * sv);
+        }
+    }
     std::vector<int64_t> cell_off(nruns + 1, 0), chunk_off(nruns + 1, 0);
     std::vector<double> init(4 * nruns);
     b->hrun.resize(nruns);
@@ -366,6 +384,7 @@ dirac_status dirac_batch_create(const dirac_klein_run *runs, int nruns, const di
     e = cudaMemcpy(b->d_cell_off, cell_off.data(), (nruns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_chunk_off, chunk_off.data(), (nruns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_init, init.data(), 4 * nruns * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_absorb, absorb.data(), nruns * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->counters, 0, 4 * sizeof(unsigned));
     if (e != cudaSuccess) return fail_release(bcuda(b, e, "batch setup copies"));
     if ((st = plan(b)) != DIRAC_OK) return fail_release(st);
@@ -415,8 +434,16 @@ dirac_status dirac_batch_set_potential(dirac_batch *b, int run, const double *V,
             double p[4];
             phase_coeffs(mu, V[i], dt, 1.0, p);
             float cu, su, cd, sd;
-            round_unitary(p[0], p[1], cu, su);
-            round_unitary(p[2], p[3], cd, sd);
+            const double a = b->mask[run][i];
+            if (a == 1.0) {
+                round_unitary(p[0], p[1], cu, su);
+                round_unitary(p[2], p[3], cd, sd);
+            } else {
+                cu = (float)(p[0] * a);
+                su = (float)(p[1] * a);
+                cd = (float)(p[2] * a);
+                sd = (float)(p[3] * a);
+            }
             h[i * 4 + 0] = cu * 0.25f;
             h[i * 4 + 1] = su * 0.25f;
             h[i * 4 + 2] = cd * 0.25f;
@@ -427,10 +454,19 @@ dirac_status dirac_batch_set_potential(dirac_batch *b, int run, const double *V,
         std::vector<double> h(side * 4);
         for (int64_t i = 0; i < side; ++i) {
             if (!std::isfinite(V[i])) return bfail(b, DIRAC_ERR_ARG, "potential holds a non-finite value");
-            phase_coeffs(mu, V[i], dt, 0.25, &h[i * 4]);
+            phase_coeffs_masked(mu, V[i], dt, b->mask[run][i], 0.25, &h[i * 4]);
         }
         BCK(b, cudaMemcpy(const_cast<void *>(b->hrun[run].table), h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
+    return DIRAC_OK;
+}
+
+dirac_status dirac_batch_set_absorber(dirac_batch *b, int run, const double *a, int64_t count) {
+    if (!b || !a || run < 0 || run >= (b ? b->nruns : 0)) return bfail(b, DIRAC_ERR_ARG, "dirac_batch_set_absorber: bad argument");
+    if (count != b->runs[run].side) return bfail(b, DIRAC_ERR_ARG, "dirac_batch_set_absorber: count must equal side");
+    for (int64_t i = 0; i < count; ++i)
+        if (!(a[i] > 0.0 && a[i] <= 1.0)) return bfail(b, DIRAC_ERR_ARG, "absorber factors must lie in (0, 1]");
+    b->mask[run].assign(a, a + count);
     return DIRAC_OK;
 }
 

@@ -113,6 +113,7 @@ struct InitArgs {
     const BatchRunDev *runs;
     const int64_t *cell_off;   // [nruns + 1]
     const double *x0, *k0, *width, *spinC;  // per run
+    const int64_t *absorb;     // absorbing-layer columns per run: the packet is zero there
     int nruns;
     double dx;
 };
@@ -138,6 +139,11 @@ __global__ void batch_init_kernel(const InitArgs ia) {
         sincos(ia.k0[lo] * x, &sn, &cs);
         const double C = ia.spinC[lo];
         T *p = static_cast<T *>(R.psi[0]) + c * 8;
+        if (i < ia.absorb[lo] || i >= R.side - ia.absorb[lo]) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) p[q] = T(0);
+            continue;
+        }
         p[0] = (T)(amp * cs);
         p[1] = (T)(amp * sn);
         p[2] = T(0); p[3] = T(0); p[4] = T(0); p[5] = T(0);

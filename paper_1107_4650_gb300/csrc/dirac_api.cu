@@ -47,6 +47,9 @@ struct dirac_grid {
     size_t flux_part_cap = 0;  // doubles
     double *flux_dev = nullptr;
     unsigned *ticket = nullptr;
+    std::vector<double> absorb;      // per-x-column damping factors (empty: none)
+    std::vector<double> v_host;      // last potential set (for rebuilding the table)
+    int v_layout = DIRAC_V_NONE;
     double *obs_partial = nullptr;
     double *obs_out = nullptr;
     double *host_obs = nullptr;  // pinned [8]
@@ -127,11 +130,19 @@ dirac_status upload_table(dirac_grid *g, const double *V, int layout, int64_t co
 #pragma omp parallel for schedule(static)
         for (int64_t e = 0; e < nentries; ++e) {
             const double v = (layout == DIRAC_V_NONE) ? 0.0 : V[e];
+            const double a = g->absorb.empty() ? 1.0 : g->absorb[e % g->cfg.n[0]];
             double p[4];
             phase_coeffs(mu, v, g->dt, 1.0, p);
             float cu, su, cd, sd;
-            round_unitary(p[0], p[1], cu, su);
-            round_unitary(p[2], p[3], cd, sd);
+            if (a == 1.0) {
+                round_unitary(p[0], p[1], cu, su);
+                round_unitary(p[2], p[3], cd, sd);
+            } else {
+                cu = (float)(p[0] * a);
+                su = (float)(p[1] * a);
+                cd = (float)(p[2] * a);
+                sd = (float)(p[3] * a);
+            }
             h[e * 4 + 0] = cu * (float)scale;
             h[e * 4 + 1] = su * (float)scale;
             h[e * 4 + 2] = cd * (float)scale;
@@ -144,7 +155,10 @@ dirac_status upload_table(dirac_grid *g, const double *V, int layout, int64_t co
 #pragma omp parallel for schedule(static)
         for (int64_t e = 0; e < nentries; ++e) {
             const double v = (layout == DIRAC_V_NONE) ? 0.0 : V[e];
-            phase_coeffs(mu, v, g->dt, scale, &h[e * 4]);
+            if (g->absorb.empty())
+                phase_coeffs(mu, v, g->dt, scale, &h[e * 4]);
+            else
+                phase_coeffs_masked(mu, v, g->dt, g->absorb[e % g->cfg.n[0]], scale, &h[e * 4]);
         }
         CK(g, cudaMemcpyAsync(g->table, h.data(), bytes, cudaMemcpyHostToDevice, g->stream));
         CK(g, cudaStreamSynchronize(g->stream));
@@ -388,6 +402,16 @@ void phase_coeffs(double mu, double v, double dt, double scale, double out[4]) {
 }
 
 
+void phase_coeffs_masked(double mu, double v, double dt, double a, double scale, double out[4]) {
+    const double vdt = v * dt;
+    const double t_up = mu + vdt;
+    const double t_dn = vdt - mu;
+    out[0] = std::cos(t_up) * a * scale;
+    out[1] = -std::sin(t_up) * a * scale;
+    out[2] = std::cos(t_dn) * a * scale;
+    out[3] = -std::sin(t_dn) * a * scale;
+}
+
 // Records a message for dirac_last_error(NULL) on this thread (entry points without a grid).
 dirac_status set_thread_error(dirac_status st, const std::string &msg) {
     g_thread_err = msg;
@@ -530,7 +554,11 @@ dirac_status dirac_destroy(dirac_grid *g) {
 dirac_status dirac_set_potential(dirac_grid *g, const double *V, int layout, int64_t count) {
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     CK(g, cudaSetDevice(g->cfg.device));
-    if (layout == DIRAC_V_NONE) return upload_table(g, nullptr, layout, 0);
+    if (layout == DIRAC_V_NONE) {
+        g->v_host.clear();
+        g->v_layout = DIRAC_V_NONE;
+        return upload_table(g, nullptr, layout, 0);
+    }
     if (!V) return fail(g, DIRAC_ERR_ARG, "dirac_set_potential: null V");
     if (layout == DIRAC_V_X_ONLY) {
         if (count != g->cfg.n[0]) return fail(g, DIRAC_ERR_ARG, "DIRAC_V_X_ONLY needs count == nx");
@@ -541,7 +569,25 @@ dirac_status dirac_set_potential(dirac_grid *g, const double *V, int layout, int
     }
     for (int64_t i = 0; i < count; ++i)
         if (!std::isfinite(V[i])) return fail(g, DIRAC_ERR_ARG, "potential holds a non-finite value");
+    g->v_host.assign(V, V + count);
+    g->v_layout = layout;
     return upload_table(g, V, layout, count);
+}
+
+dirac_status dirac_set_absorber(dirac_grid *g, const double *a, int64_t count) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    CK(g, cudaSetDevice(g->cfg.device));
+    if (!a || count == 0) {
+        g->absorb.clear();
+    } else {
+        if (count != g->cfg.n[0]) return fail(g, DIRAC_ERR_ARG, "dirac_set_absorber needs count == nx");
+        for (int64_t i = 0; i < count; ++i)
+            if (!(a[i] > 0.0 && a[i] <= 1.0)) return fail(g, DIRAC_ERR_ARG, "absorber factors must lie in (0, 1]");
+        g->absorb.assign(a, a + count);
+    }
+    const bool have_v = g->v_layout != DIRAC_V_NONE && !g->v_host.empty();
+    return upload_table(g, have_v ? g->v_host.data() : nullptr, have_v ? g->v_layout : DIRAC_V_NONE,
+                        have_v ? (int64_t)g->v_host.size() : 0);
 }
 
 dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device) {

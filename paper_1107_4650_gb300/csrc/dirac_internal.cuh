@@ -71,6 +71,9 @@ bool sweep_supported(int fp32, int mode, int K, int P);
 // Phase coefficients of Eq. sol_dis_4 at A = 0 for potential energy v, times `scale`:
 // out = (cos t_up, -sin t_up, cos t_dn, -sin t_dn), t_up = mu + v dt, t_dn = v dt - mu (FP64, libm).
 void phase_coeffs(double mu, double v, double dt, double scale, double out[4]);
+// The same coefficients times an absorbing-layer factor a (a = 1: identical to phase_coeffs):
+// out = (cos t_up * a, -sin t_up * a, ...) * scale.
+void phase_coeffs_masked(double mu, double v, double dt, double a, double scale, double out[4]);
 // FP32 pair for (c, s): the float neighbours whose squared modulus is closest to 1.
 void round_unitary(double c, double s, float &cf, float &sf);
 

@@ -314,8 +314,9 @@ dirac_status dirac_klein_run_from_reduced(const double q[3], double dx, double c
         return sfail(nullptr, DIRAC_ERR_ARG, "dirac_klein_run_from_reduced: bad arguments");
     static const int64_t sides[] = {256, 384, 512, 768, 1024};
     const double wc = q[2];
-    const int64_t beyond = 128;  // cells between the step face and the right edge
-    const double need = 8.0 * wc + 8.0 + (double)beyond;
+    const int64_t absorb = 64;   // absorbing-layer columns at each x edge
+    const int64_t beyond = 128;  // cells between the step face and the right absorbing layer
+    const double need = 8.0 * wc + 8.0 + (double)(beyond + 2 * absorb);
     int64_t side = 1024;
     for (int64_t sd : sides)
         if ((double)sd >= need) {
@@ -327,13 +328,15 @@ dirac_status dirac_klein_run_from_reduced(const double q[3], double dx, double c
     const double vg = p0 * c / E;
     const double steps = std::ceil(8.0 * wc / vg) + 200.0;
     run->side = side;
-    run->face = std::min<int64_t>((int64_t)std::ceil(8.0 * wc) + 8, side - beyond);
+    run->face = std::min<int64_t>((int64_t)std::ceil(8.0 * wc) + 8 + absorb, side - beyond - absorb);
     run->nsteps = (int64_t)std::min(6000.0, std::max(2000.0, steps));
     run->V0 = q[0] * m * c * c;
     run->L = 4.0 * dx;
     run->p0 = p0;
     run->width = wc * dx;
     run->x0 = -4.0 * wc * dx;
+    run->absorb = absorb;
+    run->eta = 0.1;
     return DIRAC_OK;
 }
 

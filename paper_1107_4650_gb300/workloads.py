@@ -117,6 +117,24 @@ def random_state(nz: int, ny: int, nx: int, seed: int) -> np.ndarray:
     return psi / np.sqrt((np.abs(psi) ** 2).sum())
 
 
+def absorber_mask(nx: int, cells: int, eta: float) -> np.ndarray:
+    """Per-x-column damping factors of an absorbing layer of `cells` columns at each x edge:
+    a = exp(-eta s^2) with s = distance into the layer / cells (1/cells at its inner column, 1 at the edge),
+    1 elsewhere.  Applied with the phase every step (not part of the paper's scheme)."""
+    if cells <= 0:
+        return np.ones(nx)
+    i = np.arange(nx)
+    s_left = np.clip((cells - i) / cells, 0.0, 1.0)
+    s_right = np.clip((i - (nx - cells) + 1) / cells, 0.0, 1.0)
+    s = np.maximum(s_left, s_right)
+    return np.exp(-eta * s * s)
+
+
+ABSORB_CELLS = 64      # absorbing layer at each x edge of an ensemble run
+ABSORB_ETA = 0.1
+BEYOND_STEP = 128      # cells kept between the step face and the right absorbing layer
+
+
 @dataclasses.dataclass
 class KleinRun:
     """One 2-D Klein-step scattering run on a square grid of `side` cells."""
@@ -128,6 +146,8 @@ class KleinRun:
     dx: float = DX_DEFAULT
     L: float = 4 * DX_DEFAULT
     face: int = -1  # flux face index (the step is centred on it)
+    absorb: int = 0  # absorbing-layer columns at each x edge (0: none)
+    eta: float = ABSORB_ETA
 
     def geometry(self):
         """(x_min, z_min, x_s, x0): the step sits on face `face` (x = 0), the packet 4 widths left of it."""
@@ -137,8 +157,16 @@ class KleinRun:
         return x_min, z_min, 0.0, -4.0 * self.width, face
 
     def state(self, m: float = M_E, c: float = C_AU) -> np.ndarray:
+        """The Gaussian packet (normalised over the grid), zero inside the absorbing layers."""
         x_min, z_min, x_s, x0, _ = self.geometry()
-        return gaussian_packet(self.side, self.side, self.dx, x_min, z_min, x0, 0.0, self.width, self.p0, m, c)
+        psi = gaussian_packet(self.side, self.side, self.dx, x_min, z_min, x0, 0.0, self.width, self.p0, m, c)
+        if self.absorb > 0:
+            psi[:, :, :self.absorb, :] = 0
+            psi[:, :, self.side - self.absorb:, :] = 0
+        return psi
+
+    def mask(self) -> np.ndarray:
+        return absorber_mask(self.side, self.absorb, self.eta)
 
     def potential(self) -> np.ndarray:
         x_min, _, x_s, _, _ = self.geometry()
@@ -148,7 +176,7 @@ class KleinRun:
         """Fields of the library's dirac_klein_run (packet centre relative to the step at x = 0)."""
         _, _, _, x0, face = self.geometry()
         return {"side": self.side, "face": face, "nsteps": self.nsteps, "V0": self.V0, "L": self.L,
-                "p0": self.p0, "width": self.width, "x0": x0}
+                "p0": self.p0, "width": self.width, "x0": x0, "absorb": self.absorb, "eta": self.eta}
 
 
 def klein_config_2d(seed: int = SEED, side: int = 2048, nsteps: int = 4000, m: float = M_E, c: float = C_AU) -> KleinRun:
@@ -161,19 +189,19 @@ def klein_config_2d(seed: int = SEED, side: int = 2048, nsteps: int = 4000, m: f
 
 
 ALLOWED_SIDES = (256, 384, 512, 768, 1024)
-BEYOND_STEP = 128  # cells kept between the step face and the right edge
 
 
 def klein_ensemble(nruns: int = 512, seed: int = SEED + 1, m: float = M_E, c: float = C_AU):
     """Batched ensemble draws: side U{256..1024}, V0 ~ U[0.5, 3.0] mc^2, p0 ~ U[0.2, 1.0] mc,
-    width ~ U[40, 150] dx.  A drawn side smaller than 8 width + 136 cells is raised to the smallest
-    allowed side that holds the packet and a 128-cell region beyond the step (1024 at most); the step
-    face sits 8 widths + 8 cells from the left edge but at least 128 cells from the right edge (the
-    region beyond a step must be long against the evanescent length c/(mc^2), about 6 cells, or waves
-    in the gap tunnel into the outflowing boundary), the packet 4 widths left of the face; the step
-    count is the time for the packet centre to travel 8 widths at the group velocity p0 c^2 / E plus
-    200, clamped to [2000, 6000].
-    Returns (runs, log) where log lists every deviation from the drawn values."""
+    width ~ U[40, 150] dx.  Each run has 64-column absorbing layers at both x edges (the zero boundary
+    reflects part of a massive wave, and a reflection that comes back across the face corrupts the
+    transmitted fraction).  A drawn side smaller than 8 width + 264 cells is raised to the smallest allowed
+    side that holds the packet clear of the left layer and 128 cells plus the right layer beyond the step
+    (1024 at most; wider packets are cut at the left layer); the step face sits 8 widths + 8 cells right of
+    the left layer but at least 128 + 64 cells from the right edge, the packet 4 widths left of the face;
+    the step count is the time for the packet centre to travel 8 widths at the group velocity p0 c^2 / E
+    plus 200, clamped to [2000, 6000].  Returns (runs, log) where log lists every deviation from the drawn
+    values."""
     rng = np.random.default_rng(seed)
     dx = DX_DEFAULT
     runs, log = [], []
@@ -182,7 +210,7 @@ def klein_ensemble(nruns: int = 512, seed: int = SEED + 1, m: float = M_E, c: fl
         V0 = rng.uniform(0.5, 3.0) * m * c * c
         p0 = rng.uniform(0.2, 1.0) * m * c
         w_cells = rng.uniform(40, 150)
-        need = 8 * w_cells + 8 + BEYOND_STEP
+        need = 8 * w_cells + 8 + BEYOND_STEP + 2 * ABSORB_CELLS
         if side < need:
             bigger = [s for s in ALLOWED_SIDES if s >= need]
             new = bigger[0] if bigger else ALLOWED_SIDES[-1]
@@ -191,7 +219,7 @@ def klein_ensemble(nruns: int = 512, seed: int = SEED + 1, m: float = M_E, c: fl
         E = np.sqrt(p0 * p0 * c * c + m * m * c ** 4)
         vg_over_c = p0 * c / E
         nsteps = int(np.clip(np.ceil(8 * w_cells / vg_over_c) + 200, 2000, 6000))
-        face = min(int(np.ceil(8 * w_cells)) + 8, side - BEYOND_STEP)
+        face = min(int(np.ceil(8 * w_cells)) + 8 + ABSORB_CELLS, side - BEYOND_STEP - ABSORB_CELLS)
         runs.append(KleinRun(side=side, V0=V0, p0=p0, width=w_cells * dx, nsteps=nsteps, dx=dx, L=4 * dx,
-                             face=face))
+                             face=face, absorb=ABSORB_CELLS, eta=ABSORB_ETA))
     return runs, log

@@ -47,6 +47,8 @@ def _run_batch(D, runs, fp32, K=2, P=0, seg=0, graphs=True, explicit=True):
         if explicit:
             for i, r in enumerate(runs):
                 D.dirac_batch_set_state(h, i, np.ascontiguousarray(r.state().astype(dt)))
+                if r.absorb:
+                    D.dirac_batch_set_absorber(h, i, r.mask())
                 D.dirac_batch_set_potential(h, i, r.potential())
         D.dirac_batch_run(h)
         res = D.dirac_batch_results(h, len(runs))
@@ -63,7 +65,43 @@ def _run_batch(D, runs, fp32, K=2, P=0, seg=0, graphs=True, explicit=True):
 
 def _oracle(r):
     _, _, _, _, face = r.geometry()
-    return oracle.step(r.state(), 2, 1.0, C, r.dx, r.nsteps, V=r.potential(), flux_face=face)
+    return oracle.step(r.state(), 2, 1.0, C, r.dx, r.nsteps, V=r.potential(), flux_face=face,
+                       absorber=r.mask() if r.absorb else None)
+
+
+def _absorbing_runs():
+    return [W.KleinRun(side=140, V0=2.5 * C * C, p0=0.6 * C, width=8 * DX, nsteps=41, face=80, absorb=20, eta=0.1),
+            W.KleinRun(side=96, V0=1.5 * C * C, p0=0.9 * C, width=5 * DX, nsteps=30, face=50, absorb=16, eta=0.2)]
+
+
+def test_batch_absorbing_layers_bit_exact(D):
+    runs = _absorbing_runs()
+    outs, res, _ = _run_batch(D, runs, fp32=False)
+    for r, got, F in zip(runs, outs, res["flux"]):
+        want, Fw = _oracle(r)
+        assert np.array_equal(got.view(np.float64), want.view(np.float64))
+        assert abs(F - Fw) <= 1e-12 * max(abs(Fw), 1e-300)
+
+
+def test_batch_device_packets_zero_in_the_layers(D):
+    runs = _absorbing_runs()
+    _, res, _ = _run_batch(D, runs, fp32=False, explicit=False)
+    for r, T in zip(runs, res["T"]):
+        want, Fw = _oracle(r)
+        assert abs(T - Fw / oracle.observables(r.state(), 2, r.dx)["norm"]) < 1e-9
+
+
+def test_ensemble_geometry_gives_smooth_transmission(D):
+    """Neighbouring step heights at the widest packets give neighbouring transmissions (without the
+    absorbing layers, waves reflected at the edges came back across the face and T jumped by 2x)."""
+    qs = np.array([[V0, 0.943, 144.0] for V0 in np.linspace(2.70, 2.77, 6)])
+    runs = [D.dirac_klein_run_from_reduced(q, DX, C, 1.0) for q in qs]
+    cfg = D.dirac_batch_default_config()
+    cfg.precision = D.DIRAC_FP32
+    cfg.steps_per_launch = 2
+    T, _ = D.dirac_batch_klein(runs, cfg)
+    d = np.diff(T)
+    assert np.all(d > 0) and np.max(np.abs(np.diff(d))) < 0.2 * np.max(np.abs(d)) + 1e-4, T
 
 
 @pytest.mark.parametrize("K,P,seg", [(2, 2, 0), (1, 4, 32), (2, 2, 24)])

@@ -390,3 +390,34 @@ def test_massless_scheme_converges_to_closed_forms(oracle_mod):
         c0 = n // 2
         errs.append(max(abs(out[c0, 0, c0, 0] - r0), abs(out[c0, 0, c0 + steps, 0] - rct)))
     assert errs[0] < 2e-4 and errs[0] / errs[1] > 3.0, errs
+
+
+# ---------------------------------------------------------------- absorbing layers (ensemble geometry)
+
+def test_absorbing_layers_recover_the_open_domain_transmission(oracle_mod):
+    """The zero boundary partially reflects a massive wave; 64-column layers a(x) = exp(-0.1 s^2) at both x
+    edges absorb it: on a small domain (z-uniform reduction) the transmitted fraction then matches a domain
+    wide enough that nothing reaches its edges before the run ends."""
+    import math
+    dx = W.DX_DEFAULT
+    pr, wc, V0r, nsteps = 0.943, 60.0, 2.72, 2000
+    w, p0, V0 = wc * dx, pr * C, V0r * C * C
+
+    def T(nx, face, absorb):
+        x_min = -face * dx
+        run = W.KleinRun(side=nx, V0=V0, p0=p0, width=w, nsteps=nsteps, face=face, absorb=absorb)
+        psi = W.gaussian_packet(nx, 1, dx, x_min, 0.0, -4 * w, 0.0, w, p0)
+        if absorb:
+            psi[:, :, :absorb, :] = 0
+            psi[:, :, nx - absorb:, :] = 0
+        V = W.tanh_step(nx, dx, x_min, 0.0, V0, 4 * dx)
+        _, F = oracle.step(psi, 2, M, C, dx, nsteps, V=V, periodic=True, flux_face=face,
+                           absorber=run.mask() if absorb else None)
+        return F / oracle.observables(psi, 2, dx)["norm"]
+
+    ref = T(8192, 4000, 0)
+    face = int(math.ceil(8 * wc)) + 8 + 64
+    with_layers = T(face + 128 + 64, face, 64)
+    without = T(face + 128 + 64, face, 0)
+    assert abs(with_layers - ref) < 1e-4, (with_layers, ref)
+    assert abs(without - ref) > 10 * abs(with_layers - ref)

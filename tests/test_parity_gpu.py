@@ -349,3 +349,25 @@ def test_massless_packet_bit_exact(D):
     want, _ = oracle.step(psi0, 2, 0.0, C, dx, 20)
     got, _, _ = run_gpu(D, psi0, 2, 20, dx=dx, m=0.0, x_min=(-(n // 2 + 0.5) * dx, 0.0, -(n // 2 + 0.5) * dx))
     assert _bits_equal(got, want)
+
+
+def test_absorbing_layer_bit_exact(D):
+    run = W.KleinRun(side=200, V0=2.5 * C * C, p0=0.7 * C, width=10 * DX, nsteps=150, face=120, absorb=24, eta=0.1)
+    psi0 = run.state()
+    V = run.potential()
+    x_min, z_min, _, _, face = run.geometry()
+    want, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=V, flux_face=face, absorber=run.mask())
+    cfg = D.make_config((200, 1, 200), x_min=(x_min, 0.0, z_min), flux_face=face)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_absorber(h, run.mask())
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi0)
+        D.dirac_step(h, run.nsteps)
+        got = np.empty_like(psi0)
+        D.dirac_get_state(h, got)
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want)
+    assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
