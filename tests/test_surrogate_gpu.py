@@ -117,3 +117,26 @@ def test_klein_surrogate_small_box(D):
     assert list(used) == [False, False, False, True, True]
     assert np.allclose(T_out[3:], _solve(D, q_out, fp32=True), rtol=1e-12, atol=1e-15)
     assert t_fp64 / t_net > 100
+
+
+def test_shipped_checkpoint_against_fp64_solver(D):
+    """The shipped network (20000 FP32-labelled runs over V0/mc^2 in [0.5, 3], p0/mc in [0.2, 1], width/dx in
+    [40, 150]) predicts the FP64 batched solver's transmission on fresh points of the box."""
+    import os
+    path = os.path.join(os.path.dirname(D.__file__), "data", "surrogate_klein_box.npz")
+    z = np.load(path)
+    lo, hi = z["lo"], z["hi"]
+    rng = np.random.default_rng(W.SEED + 5)
+    q = lo + (hi - lo) * rng.uniform(0.0, 1.0, (24, 3))
+    h = D.dirac_surrogate_create(lo, hi, seed=0, max_batch=64)
+    try:
+        D.dirac_surrogate_set_params(h, z["params"])
+        T_net = D.dirac_surrogate_predict(h, q)
+    finally:
+        D.dirac_surrogate_destroy(h)
+    cfg = D.dirac_batch_default_config()
+    cfg.precision = D.DIRAC_FP64
+    cfg.steps_per_launch = 2
+    T64, _ = D.dirac_batch_klein([D.dirac_klein_run_from_reduced(x, DX, C, 1.0) for x in q], cfg)
+    dT = np.abs(T_net - T64)
+    assert dT.mean() < 1e-3 and dT.max() < 5e-3, (dT.mean(), dT.max())
