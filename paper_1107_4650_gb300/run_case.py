@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--ndim", type=int, default=2)
     ap.add_argument("--batch-runs", type=int, default=0, help="run this many ensemble runs as one batch instead")
     ap.add_argument("--seg", type=int, default=256, help="batch: rows per task")
+    ap.add_argument("--mlp", type=int, default=0,
+                    help="instead: train the transmission network this many epochs on seeded random targets")
     args = ap.parse_args()
 
     import torch
@@ -38,6 +40,25 @@ def main():
     D.load_library()
     prec = D.DIRAC_FP32 if args.precision == "fp32" else D.DIRAC_FP64
     stream = torch.cuda.Stream()
+    if args.mlp > 0:
+        lo, hi = np.array([0.5, 0.2, 40.0]), np.array([3.0, 1.0, 150.0])
+        rng = np.random.default_rng(W.SEED + 6)
+        X = lo + (hi - lo) * rng.uniform(0.0, 1.0, (4096, 3))
+        T = rng.uniform(0.0, 0.3, 4096)
+        hs = D.dirac_surrogate_create(lo, hi, seed=1, max_batch=4096, stream=stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loss = D.dirac_surrogate_train(hs, X, T, args.mlp, 256, 1e-3)
+        e1.record(stream)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        D.dirac_surrogate_predict(hs, X)
+        t_pred = time.perf_counter() - t0
+        D.dirac_surrogate_destroy(hs)
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"mlp_epochs": args.mlp, "train_ms": ms, "ms_per_iteration": ms / (args.mlp * 16),
+                          "loss": loss, "predict_4096_s": t_pred}))
+        return
     if args.batch_runs > 0:
         runs, _ = W.klein_ensemble(nruns=args.batch_runs)
         cfg = D.dirac_batch_default_config()
