@@ -44,9 +44,11 @@ FP64_INSTR_PER_POINT_STEP_2D = 48  # 32 DADD + 8 DMUL + 8 DFMA: what the FP64 pi
 # 0.5285 T lane-instructions/s (1.68 per SM per clock at 2.07 GHz, 152 SMs).
 FP64_ISSUE_PEAK_NOMINAL = 0.625
 FP64_ISSUE_PEAK_MEASURED = 0.5285
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel on this workload
-# (profiles/step_kernel_fp64_klein2048.md); None until captured for the kernel as it stands.
-MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": None, "fp32": None}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel on the 2048^2 workload, keyed
+# by (steps per launch, points per lane) of the captured variant (profiles/step_kernel_fp64_klein2048.md,
+# profiles/step_kernel_fp32_klein2048.md).  A variant without a capture reports null.
+MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": {(1, 2): 277.570816e6 + 216.754944e6},
+                               "fp32": {(2, 2): 147.689984e6 + 85.383424e6}}
 
 
 def parse():
@@ -283,7 +285,8 @@ def main():
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved_gbs = alg_bytes / mean_launch_s / 1e9
     fp64_tips = FP64_INSTR_PER_POINT_STEP_2D * ncell * k_launch / mean_launch_s / 1e12
-    traffic = MEASURED_TRAFFIC_PER_LAUNCH["fp64"]
+    traffic = (MEASURED_TRAFFIC_PER_LAUNCH["fp64"].get((k_launch, info["points_per_lane"]))
+               if args.side == 2048 else None)
     roofline = {"bound": "alu", "achieved": fp64_tips, "peak": FP64_ISSUE_PEAK_NOMINAL, "unit": "T FP64-instr/s",
                 "frac": fp64_tips / FP64_ISSUE_PEAK_NOMINAL, "traffic": traffic,
                 "peak_source": "derived from the recipe's nominal FP64 rate (1.25 TFLOP/s / 2 flops per DFMA); "
@@ -338,6 +341,8 @@ def main():
                             "steps_per_launch": k32, "points_per_lane": i32["points_per_lane"],
                             "effective_hbm_frac": eff / hbm_peak,
                             "step_kernel_algorithmic_gbs": FP32_BYTES_PER_POINT_STEP * ncell * k32 / mean32 / 1e9,
+                            "traffic_per_launch": (MEASURED_TRAFFIC_PER_LAUNCH["fp32"].get((k32, i32["points_per_lane"]))
+                                                   if args.side == 2048 else None),
                             "T": o32["flux_cum"] / n0, "T_fp64": obs["flux_cum"] / n0}
         D.dirac_destroy(h32)
 

@@ -60,6 +60,8 @@ def _load():
             f.restype = ctypes.c_int
         lib.oracle_set_absorber.argtypes = [P]
         lib.oracle_set_absorber.restype = None
+        lib.oracle_set_vector_potential.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_set_vector_potential.restype = None
         _lib = lib
     return _lib
 
@@ -122,21 +124,43 @@ class _Absorber:
         _load().oracle_set_absorber(None)
 
 
+class _VectorPotential:
+    """Context: per-step uniform vector-potential integrals At[n] = (At_x, At_y, At_z) (None: none)."""
+    def __init__(self, At, step0):
+        self.At = None if At is None else np.ascontiguousarray(At, dtype=np.float64).reshape(-1, 3)
+        self.step0 = int(step0)
+
+    def __enter__(self):
+        if self.At is None:
+            _load().oracle_set_vector_potential(None, 0, 0)
+        else:
+            _load().oracle_set_vector_potential(self.At.ctypes.data, self.At.shape[0], self.step0)
+        return self
+
+    def __exit__(self, *exc):
+        _load().oracle_set_vector_potential(None, 0, 0)
+
+
 def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
-         periodic: bool = False, flux_face: int = -1, flux_cum: float = 0.0, absorber=None):
+         periodic: bool = False, flux_face: int = -1, flux_cum: float = 0.0, absorber=None,
+         A_tilde=None, step0: int = 0):
     """nsteps first-order split steps (Eqs. split1-4 discretised as sol_dis_1-4), dt = dx/c.
 
     Returns (psi_out, flux_cum): the cumulative probability carried across the x face
     `flux_face` (between cells flux_face-1 and flux_face), added to the given start value.
     `absorber`: optional per-x-column factors a(x) in (0, 1] applied with the phase (not in the paper).
+    `A_tilde`: optional (nt, 3) array of uniform vector-potential integrals e int A dt per step (Eq. field_dis1);
+    step s of this call uses row step0 + s, and the phase is the full matrix of Eq. sol_dis_4.
     """
     out = _as_state(psi)
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    with _Absorber(absorber, out.shape[2]):
+    with _Absorber(absorber, out.shape[2]), _VectorPotential(A_tilde, step0):
         rc = _load().oracle_step(out.ctypes.data, _dims(out), int(ndim), int(bool(periodic)), float(m), float(c),
                                  float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
                                  int(flux_face), ctypes.addressof(fc))
+    if rc == -2:
+        raise ValueError("the vector-potential table ends before the last step")
     if rc != 0:
         raise MemoryError("oracle_step")
     return out, fc.value

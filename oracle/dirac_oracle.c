@@ -24,7 +24,11 @@
  *   - the phase multiplies by p = (cos t, -sin t) with t = m*c*c*dt + V*dt for
  *     components 1,2 and t = V*dt - m*c*c*dt for components 3,4, the complex
  *     product taken as re = fma(z.re, p.re, -(z.im*p.im)),
- *     im = fma(z.re, p.im, z.im*p.re).
+ *     im = fma(z.re, p.im, z.im*p.re);
+ *   - with a uniform vector potential the phase is the 4x4 matrix U exp(-i V dt): each entry of U times
+ *     g = (cos(V dt), -sin(V dt)) as the complex product above, then psi'_a = sum over b = 1..4 in order of
+ *     M_ab psi_b, accumulated from zero as re = fma(z.re, p.re, fma(-z.im, p.im, re)),
+ *     im = fma(z.re, p.im, fma(z.im, p.re, im)) with z = psi_b, p = M_ab.
  * Compiled with -ffp-contract=off so that no other contraction happens.
  */
 #include <math.h>
@@ -177,6 +181,82 @@ static double face_flux(const cplx *psi, const int64_t n[3], int periodic, int64
     return f * vol;
 }
 
+/* Uniform vector potential (not needed by the paper's runs, Sec. 2.3 states the general step).  When a
+ * table is set, step s of oracle_step (counted from step0) applies the full matrix of Eq. sol_dis_4,
+ *   psi <- U exp(-i V dt) psi,  U = exp(-i beta m c^2 dt + i alpha.At),
+ * with At = (At_x, At_y, At_z) = g_avec[3 (step0 + s) ..] the time integral of e A over the step
+ * (Eq. field_dis1, supplied by the caller).  NULL removes it. */
+static const double *g_avec = NULL;
+static int64_t g_avec_n = 0, g_avec_step0 = 0;
+
+void oracle_set_vector_potential(const double *At, int64_t nsteps_table, int64_t step0) {
+    g_avec = At;
+    g_avec_n = nsteps_table;
+    g_avec_step0 = step0;
+}
+
+/* acc + z p, taken as re = fma(z.re, p.re, fma(-z.im, p.im, acc.re)), im = fma(z.re, p.im, fma(z.im, p.re, acc.im)) */
+static inline cplx c_mac(cplx acc, cplx z, cplx p) {
+    cplx r;
+    r.re = fma(z.re, p.re, fma(-z.im, p.im, acc.re));
+    r.im = fma(z.re, p.im, fma(z.im, p.re, acc.im));
+    return r;
+}
+
+/* The 4x4 matrix U of Sec. 2.3 (the closed form of exp(i(beta F + alpha.F)) with F = -m c^2 dt and
+ * F = At), written out entry by entry as the paper prints it:
+ *   diagonal:  cos(A) -+ i (m c^2 dt / A) sin(A)   (- for components 1,2, + for 3,4)
+ *   (1,3), (3,1):  i At_z sin(A)/A        (2,4), (4,2):  -i At_z sin(A)/A
+ *   (1,4), (3,2):  (i At_x + At_y) sin(A)/A     (2,3), (4,1):  (i At_x - At_y) sin(A)/A
+ * A = sqrt((m c^2 dt)^2 + At.At), summed as ((mu^2 + At_x^2) + At_y^2) + At_z^2; sin(A)/A -> 1 at A = 0. */
+static void u_matrix(double mu, const double At[3], cplx U[4][4]) {
+    const double A = sqrt(((mu * mu + At[0] * At[0]) + At[1] * At[1]) + At[2] * At[2]);
+    const double sA = A > 0.0 ? sin(A) / A : 1.0;
+    const double cA = cos(A);
+    const double ax = At[0] * sA, ay = At[1] * sA, az = At[2] * sA, ms = mu * sA;
+    memset(U, 0, 16 * sizeof(cplx));
+    U[0][0].re = cA; U[0][0].im = -ms;
+    U[1][1].re = cA; U[1][1].im = -ms;
+    U[2][2].re = cA; U[2][2].im = ms;
+    U[3][3].re = cA; U[3][3].im = ms;
+    U[0][2].im = az;  U[2][0].im = az;
+    U[1][3].im = -az; U[3][1].im = -az;
+    U[0][3].re = ay;  U[0][3].im = ax;  U[2][1].re = ay;  U[2][1].im = ax;
+    U[1][2].re = -ay; U[1][2].im = ax;  U[3][0].re = -ay; U[3][0].im = ax;
+}
+
+/* Eq. sol_dis_4 with a uniform vector potential: psi <- (U exp(-i V dt)) psi per cell, the scalar factor
+ * g = (cos(V dt), -sin(V dt)) (times the absorbing-layer factor when one is set) multiplied into every
+ * entry first (M = U g as a complex product), then psi'_a = sum_b M_ab psi_b over b = 1..4 in order,
+ * accumulated with c_mac from zero. */
+static int oracle_phase_A(double *psi_d, const int64_t n[3], double m, double c, double dt,
+                          const double *V, int layout, const double At[3]) {
+    cplx *psi = (cplx *)psi_d;
+    const double mu = m * c * c * dt;
+    cplx U[4][4];
+    u_matrix(mu, At, U);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i) {
+                const double vdt = potential(V, layout, n, i, j, k) * dt;
+                cplx g = {cos(vdt), -sin(vdt)};
+                if (g_absorb) {
+                    g.re = g.re * g_absorb[i];
+                    g.im = g.im * g_absorb[i];
+                }
+                cplx *q = psi + ((k * n[1] + j) * n[0] + i) * 4;
+                cplx o[4];
+                for (int a = 0; a < 4; ++a) {
+                    cplx acc = {0.0, 0.0};
+                    for (int b = 0; b < 4; ++b) acc = c_mac(acc, q[b], c_mul(U[a][b], g));
+                    o[a] = acc;
+                }
+                for (int a = 0; a < 4; ++a) q[a] = o[a];
+            }
+    return 0;
+}
+
 /* nsteps steps of the first-order splitting, Eqs. split1-split4 in the discrete
  * form sol_dis_1-sol_dis_4: x sweep, y sweep (3-D only), z sweep, phase.  dt = dx/c
  * (c dt = a, K = 1, Sec. 2.3).  If flux_face >= 0 the probability crossing that x
@@ -191,7 +271,13 @@ int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double 
         if (oracle_sweep(psi, n, 0, periodic)) return -1;
         if (ndim == 3 && oracle_sweep(psi, n, 1, periodic)) return -1;
         if (oracle_sweep(psi, n, 2, periodic)) return -1;
-        oracle_phase(psi, n, m, c, dt, V, layout);
+        if (g_avec) {
+            const int64_t t = g_avec_step0 + s;
+            if (t < 0 || t >= g_avec_n) return -2;
+            oracle_phase_A(psi, n, m, c, dt, V, layout, g_avec + 3 * t);
+        } else {
+            oracle_phase(psi, n, m, c, dt, V, layout);
+        }
     }
     return 0;
 }

@@ -130,6 +130,28 @@ def absorber_mask(nx: int, cells: int, eta: float) -> np.ndarray:
     return np.exp(-eta * s * s)
 
 
+def laser_A_tilde(nsteps: int, dt: float, A0: float, omega: float, ncycles: float, pol=(1.0, 0.0, 0.0),
+                  charge: float = -1.0, step0: int = 0) -> np.ndarray:
+    """Per-step integrals At_n = e * int_{t_n}^{t_{n+1}} A(t) dt (Eq. field_dis1) of a uniform (dipole)
+    laser pulse A(t) = A0 sin^2(pi t / tau) sin(omega t) pol for 0 <= t <= tau = 2 pi ncycles / omega, zero
+    after, with t_n = (step0 + n) dt.  The integral is analytic: with W = 2 pi / tau,
+    sin^2(W t / 2) sin(omega t) = sin(omega t)/2 - [sin((omega + W) t) + sin((omega - W) t)]/4.
+    Returns an (nsteps, 3) array (input data: the scheme itself never integrates the field)."""
+    tau = 2.0 * np.pi * ncycles / omega
+    Wf = 2.0 * np.pi / tau
+
+    def F(t):
+        t = np.clip(t, 0.0, tau)
+        out = -np.cos(omega * t) / (2.0 * omega)
+        for w in (omega + Wf, omega - Wf):
+            out = out + (np.cos(w * t) / (4.0 * w) if w != 0.0 else -t * 0.0)
+        return out
+
+    t = (step0 + np.arange(nsteps + 1)) * dt
+    integ = F(t[1:]) - F(t[:-1])
+    return charge * A0 * integ[:, None] * np.asarray(pol, dtype=np.float64)[None, :]
+
+
 ABSORB_CELLS = 64      # absorbing layer at each x edge of an ensemble run
 ABSORB_ETA = 0.1
 BEYOND_STEP = 128      # cells kept between the step face and the right absorbing layer

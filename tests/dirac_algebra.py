@@ -116,3 +116,25 @@ def rel_l2(a, b) -> float:
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def phase_matrix_A_cell(m, c, dt, v, At) -> np.ndarray:
+    """exp(-i dt (beta m c^2 + v - alpha.(At/dt))) for one cell, by scipy's matrix exponential of the 4x4
+    generator (Eq. sol_dis_4 before the closed form of Sec. 2.3 is applied)."""
+    from scipy.linalg import expm
+    G = -1j * (m * c * c * dt) * BETA - 1j * v * dt * I4 + 1j * sum(a * M for a, M in zip(At, ALPHA))
+    return expm(G)
+
+
+def dft_exact_evolution_2d_A(psi0: np.ndarray, mu: float, At_steps, m_c2_dt=None) -> np.ndarray:
+    """psi after len(At_steps) periodic V = 0 steps with a uniform vector potential: mode by mode
+    U_n = exp(-i beta mu + i alpha.At_n) e^{-i alpha_z th_z} e^{-i alpha_x th_x} (matrix exponential by scipy)."""
+    from scipy.linalg import expm
+    nz, _, nx, _ = psi0.shape
+    hat = np.fft.fft2(psi0[:, 0], axes=(0, 1))
+    KX, KZ = np.meshgrid(np.arange(nx), np.arange(nz))
+    S = amplification_2d(KX, KZ, nx, nz, 0.0)  # sweeps only (mu = 0: the mass phase is the identity)
+    for At in At_steps:
+        UA = expm(-1j * mu * BETA + 1j * sum(a * M for a, M in zip(At, ALPHA)))
+        hat = np.einsum("ab,zxbc,zxc->zxa", UA, S, hat)
+    return np.fft.ifft2(hat, axes=(0, 1))[:, None]

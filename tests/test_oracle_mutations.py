@@ -31,6 +31,10 @@ MUTANTS = {
     "phase_conjugate": ("cplx p_up = {cos(t_up), -sin(t_up)};", "cplx p_up = {cos(t_up), sin(t_up)};"),
     "flux_sign": ("f += right - left;", "f += right + left;"),
     "boundary_wrap_off_by_one": ("i = ((i % n[0]) + n[0]) % n[0];", "i = ((i % n[0]) + n[0] + 1) % n[0];"),
+    "A_z_entry_sign": ("U[1][3].im = -az; U[3][1].im = -az;", "U[1][3].im = az; U[3][1].im = -az;"),
+    "A_y_entry_sign": ("U[0][3].re = ay;  U[0][3].im = ax;", "U[0][3].re = -ay;  U[0][3].im = ax;"),
+    "A_mass_term_sign": ("U[0][0].re = cA; U[0][0].im = -ms;", "U[0][0].re = cA; U[0][0].im = ms;"),
+    "A_row_order": ("acc = c_mac(acc, q[b], c_mul(U[a][b], g));", "acc = c_mac(acc, q[b], c_mul(U[b][a], g));"),
 }
 
 
@@ -47,6 +51,10 @@ def _build_mutant(tmp_path, name, old, new):
     lib.oracle_step.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
     lib.oracle_observables.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_double, oracle.D3, ctypes.c_int64, P]
+    lib.oracle_set_absorber.argtypes = [P]
+    lib.oracle_set_absorber.restype = None
+    lib.oracle_set_vector_potential.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
+    lib.oracle_set_vector_potential.restype = None
     return lib
 
 
@@ -74,6 +82,18 @@ def _pins_pass():
     out, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=run.potential(), flux_face=face)
     o1 = oracle.observables(out, 2, DX, (x_min, 0.0, z_min), face)
     ok &= abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
+    # uniform vector potential: one-cell phase against the matrix exponential, Fourier evolution
+    rng = np.random.default_rng(12)
+    At = rng.uniform(-1.5, 1.5, (3, 3))
+    psi = rng.standard_normal((1, 1, 1, 4)) + 1j * rng.standard_normal((1, 1, 1, 4))
+    got, _ = oracle.step(psi, 2, 1.0, C, DX, 3, V=np.array([2e4]), periodic=True, A_tilde=At)
+    want = psi.reshape(4)
+    for a in At:
+        want = A.phase_matrix_A_cell(1.0, C, DX / C, 2e4, a) @ want
+    ok &= np.max(np.abs(got.reshape(4) - want)) < 1e-13
+    psi = W.random_state(9, 1, 10, seed=93)
+    got, _ = oracle.step(psi, 2, 1.0, C, DX, 4, periodic=True, A_tilde=At[[0, 1, 2, 0]])
+    ok &= A.rel_l2(got, A.dft_exact_evolution_2d_A(psi, C * DX, At[[0, 1, 2, 0]])) < 1e-13
     return bool(ok)
 
 

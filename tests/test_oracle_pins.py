@@ -421,3 +421,108 @@ def test_absorbing_layers_recover_the_open_domain_transmission(oracle_mod):
     without = T(face + 128 + 64, face, 0)
     assert abs(with_layers - ref) < 1e-4, (with_layers, ref)
     assert abs(without - ref) > 10 * abs(with_layers - ref)
+
+
+# ---------------------------------------------------------------- uniform vector potential (Eq. sol_dis_4, Sec. 2.3)
+
+def _random_At(n, seed, scale=1.5):
+    rng = np.random.default_rng(seed)
+    At = rng.uniform(-scale, scale, (n, 3))
+    At[1] = 0.0  # one step with no field
+    return At
+
+
+def test_vector_potential_phase_is_the_matrix_exponential(oracle_mod):
+    """On a one-cell periodic grid the sweeps are the identity, so a step is the phase alone: U exp(-i V dt)
+    must equal the matrix exponential of the generator, for fields from 0 to several radians and for several
+    consecutive steps with different fields."""
+    At = _random_At(6, 71)
+    At[3] = [0.0, 0.0, 2.9]
+    At[4] = [3.1, -0.4, 0.2]
+    dt = W.DX_DEFAULT / C
+    for ndim, shape in ((2, (1, 1, 1, 4)), (3, (1, 1, 1, 4))):
+        rng = np.random.default_rng(5 + ndim)
+        psi = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+        v = 3.7e4
+        out, _ = oracle.step(psi, ndim, M, C, W.DX_DEFAULT, len(At), V=np.array([v]), periodic=True, A_tilde=At)
+        want = psi.reshape(4)
+        for a in At:
+            want = A.phase_matrix_A_cell(M, C, dt, v, a) @ want
+        assert np.max(np.abs(out.reshape(4) - want)) < 1e-14 * np.max(np.abs(want)) * len(At)
+
+
+def test_vector_potential_step_against_fourier_evolution(oracle_mod):
+    """Periodic 2-D grid, V = 0, a different uniform field each step: the scheme is diagonal in Fourier
+    space, mode k advancing by exp(-i beta mu + i alpha.At_n) e^{-i alpha_z th_z} e^{-i alpha_x th_x}."""
+    nx, nz, nsteps = 14, 11, 7
+    psi = W.random_state(nz, 1, nx, seed=91)
+    At = _random_At(nsteps, 92, scale=0.8)
+    mu = M * C * C * W.DX_DEFAULT / C
+    out, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, nsteps, periodic=True, A_tilde=At)
+    want = A.dft_exact_evolution_2d_A(psi, mu, At)
+    assert A.rel_l2(out, want) < 1e-13
+
+
+def test_vector_potential_table_offset_and_bounds(oracle_mod):
+    """step0 selects the table row of the first step; running past the table is an error."""
+    psi = W.random_state(6, 1, 5, seed=3)
+    At = _random_At(5, 4)
+    a, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 3, periodic=True, A_tilde=At, step0=2)
+    b, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 3, periodic=True, A_tilde=At[2:])
+    assert np.array_equal(a, b)
+    with pytest.raises(ValueError):
+        oracle.step(psi, 2, M, C, W.DX_DEFAULT, 4, periodic=True, A_tilde=At, step0=2)
+
+
+def test_vector_potential_keeps_the_norm_and_reduces_to_the_field_free_step(oracle_mod):
+    """The phase matrix is unitary (periodic norm conserved to round-off over 200 steps); a table of zeros
+    gives the field-free step up to the rounding of the two forms of the mass phase."""
+    nx, nz = 24, 20
+    psi = W.random_state(nz, 1, nx, seed=8)
+    V = np.random.default_rng(9).uniform(-3e4, 3e4, nx)
+    At = _random_At(200, 10, scale=2.0)
+    out, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 200, V=V, periodic=True, A_tilde=At)
+    n0 = oracle.observables(psi, 2, W.DX_DEFAULT)["norm"]
+    assert abs(oracle.observables(out, 2, W.DX_DEFAULT)["norm"] - n0) < 200 * 1e-15 * n0
+    zero, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 20, V=V, periodic=True, A_tilde=np.zeros((20, 3)))
+    free, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 20, V=V, periodic=True)
+    assert A.rel_l2(zero, free) < 1e-14
+
+
+def test_vector_potential_uniform_field_accelerates_a_packet(oracle_mod):
+    """Physics: a uniform field E along x (A = -E t, At_n = e (A(t_{n+1}) + A(t_n)) dt / 2) changes the
+    mean kinetic momentum of a positive-energy packet at the rate e E (Lorentz force, Sec. 2 Hamiltonian):
+    the packet's centroid velocity responds in the direction of e E."""
+    nx, nz = 160, 24
+    dx = 4 * W.DX_DEFAULT
+    dt = dx / C
+    psi = W.gaussian_packet(nx, nz, dx, -nx * dx / 2, -nz * dx / 2, 0.0, 0.0, 12 * dx, 0.3 * C)
+    E = 2.0e5
+    nsteps = 60
+    t = np.arange(nsteps + 1) * dt
+    A = -E * t
+    At = np.zeros((nsteps, 3))
+    At[:, 0] = -1.0 * 0.5 * (A[1:] + A[:-1]) * dt  # e = -1
+    x_min = (-nx * dx / 2, 0.0, -nz * dx / 2)
+    free, _ = oracle.step(psi, 2, M, C, dx, nsteps, periodic=True)
+    kick, _ = oracle.step(psi, 2, M, C, dx, nsteps, periodic=True, A_tilde=At)
+    xf = oracle.observables(free, 2, dx, x_min)["centroid"][0]
+    xk = oracle.observables(kick, 2, dx, x_min)["centroid"][0]
+    assert xk < xf  # force e E = -E < 0 decelerates the +x moving electron
+
+
+def test_laser_field_integrals_match_quadrature():
+    """The per-step field integrals of the pulse generator equal numerical quadrature of e A(t)."""
+    from scipy.integrate import quad
+    dt = 50 * W.DX_DEFAULT / C
+    A0, omega, ncyc = 3.0e3, 0.057 * 400, 2.0
+    tau = 2 * np.pi * ncyc / omega
+    n = int(np.ceil(tau / dt)) + 5
+    At = W.laser_A_tilde(n, dt, A0, omega, ncyc, pol=(0.6, 0.0, 0.8))
+
+    def A_of_t(t):
+        return A0 * np.sin(np.pi * t / tau) ** 2 * np.sin(omega * t) if 0 <= t <= tau else 0.0
+    for k in (0, 3, n // 2, n - 6, n - 1):
+        want = -quad(A_of_t, k * dt, (k + 1) * dt, epsabs=1e-14, epsrel=1e-12, points=[tau])[0]
+        assert abs(At[k, 0] - 0.6 * want) < 1e-9 * A0 * dt and abs(At[k, 2] - 0.8 * want) < 1e-9 * A0 * dt
+    assert At[-1, 0] == 0.0 and At[:, 1].max() == 0.0
