@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dirac_observables": (I, [P, ctypes.POINTER(dirac_obs), P, I]),
         "dirac_set_counters": (I, [P, I64, D]),
         "dirac_set_absorber": (I, [P, P, I64]),
+        "dirac_set_vector_potential": (I, [P, P, I64]),
         "dirac_get_info": (I, [P, ctypes.POINTER(dirac_info)]),
         "dirac_autotune": (I, [P]),
         "dirac_last_error": (ctypes.c_char_p, [P]),
@@ -176,6 +177,15 @@ def dirac_set_absorber(h, a) -> None:
         return
     a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
     _check(load_library().dirac_set_absorber(h, a.ctypes.data, a.size), h)
+
+
+def dirac_set_vector_potential(h, A_tilde) -> None:
+    """Uniform vector-potential field integrals, an (nsteps, 3) array (None: remove the field)."""
+    if A_tilde is None:
+        _check(load_library().dirac_set_vector_potential(h, None, 0), h)
+        return
+    At = np.ascontiguousarray(A_tilde, dtype=np.float64).reshape(-1, 3)
+    _check(load_library().dirac_set_vector_potential(h, At.ctypes.data, At.shape[0]), h)
 
 
 def dirac_set_counters(h, step: int, flux_cum: float) -> None:

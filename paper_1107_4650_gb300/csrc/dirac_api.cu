@@ -50,6 +50,10 @@ struct dirac_grid {
     std::vector<double> absorb;      // per-x-column damping factors (empty: none)
     std::vector<double> v_host;      // last potential set (for rebuilding the table)
     int v_layout = DIRAC_V_NONE;
+    std::vector<double> avec;        // uniform vector potential: field integrals, 3 per step (empty: none)
+    double *ucoef = nullptr;         // device: 12 doubles of U entries per step
+    size_t ucoef_cap = 0;            // bytes
+    bool tuning = false;             // autotune timing runs: table rows taken modulo its length
     double *obs_partial = nullptr;
     double *obs_out = nullptr;
     double *host_obs = nullptr;  // pinned [8]
@@ -91,7 +95,11 @@ bool strang(const dirac_grid *g) { return g->cfg.splitting == DIRAC_STRANG; }
 // Power-of-two scale the phase coefficients carry for the sweeps' 1/2 factors: 1/4 (2-D), 1/8 (3-D),
 // 1/16 (2-D Strang: four sweeps per step).
 double scale_of(const dirac_grid *g) { return strang(g) ? 0.0625 : (ndim_of(g) == 3 ? 0.125 : 0.25); }
-int sweep_mode(const dirac_grid *g) { return strang(g) ? 2 : (ndim_of(g) == 3 ? 1 : 0); }
+int sweep_mode(const dirac_grid *g) {
+    if (strang(g)) return 2;
+    if (ndim_of(g) == 3) return 1;
+    return g->avec.empty() ? 0 : 3;
+}
 int levels(const dirac_grid *g, int K) { return strang(g) ? 2 * K : K; }
 double cell_volume(const dirac_grid *g) {
     const double dx = g->cfg.dx;
@@ -118,7 +126,8 @@ dirac_status ensure_table(dirac_grid *g, size_t bytes) {
 }
 
 dirac_status upload_table(dirac_grid *g, const double *V, int layout, int64_t count) {
-    const double mu = g->cfg.m * g->cfg.c * g->cfg.c * g->dt;
+    // with a vector potential the mass term lives in the U matrix and the table holds exp(-i V dt) alone
+    const double mu = sweep_mode(g) == 3 ? 0.0 : g->cfg.m * g->cfg.c * g->cfg.c * g->dt;
     const double scale = scale_of(g);
     const int64_t nentries = (layout == DIRAC_V_FULL) ? g->ncells : g->cfg.n[0];
     (void)count;
@@ -220,7 +229,7 @@ dirac_status ensure_flux_part(dirac_grid *g) {
 
 // One block of work: K steps (2-D) or one step (3-D), from psi[parity] to psi[parity ^ 1] (2-D) or back
 // to psi[parity] (3-D).  Enqueued on s.  K_override > 0 runs that many steps with P from the plan.
-dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s) {
+dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int64_t step0) {
     const Plan &p = g->plan;
     const bool flux = g->cfg.flux_face >= 0;
     const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
@@ -243,6 +252,9 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s) {
     a.vol = cell_volume(g);
     a.periodic = g->cfg.boundary == DIRAC_BC_PERIODIC;
     a.full_table = g->table_full;
+    a.ucoef = g->ucoef;
+    a.ucoef_n = (int64_t)(g->avec.size() / 3);
+    a.step0 = step0;
     const int mode = sweep_mode(g);
     cudaError_t e = g->fp32 ? launch_sweep_f32(a, mode, K, p.P, p.wpb, s) : launch_sweep_f64(a, mode, K, p.P, p.wpb, s);
     if (e != cudaSuccess) return cuda_fail(g, e, "sweep kernel launch");
@@ -278,7 +290,7 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
     const int64_t l0 = g->launches;
     dirac_status st = DIRAC_OK;
     for (int b = 0; b < kGraphBlocks && st == DIRAC_OK; ++b) {
-        st = enqueue_block(g, par, g->plan.K, g->cap_stream);
+        st = enqueue_block(g, par, g->plan.K, g->cap_stream, 0);
         par ^= block_flips(g);
     }
     cudaGraph_t graph = nullptr;
@@ -304,7 +316,12 @@ dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
     const int K = (ndim_of(g) == 3) ? 1 : g->plan.K;
     int64_t blocks = nsteps / K;
     int64_t rem = nsteps % K;
-    if (g->cfg.use_graphs && blocks >= kGraphBlocks) {
+    const bool field = sweep_mode(g) == 3;
+    if (field && !g->tuning && g->step + nsteps > (int64_t)(g->avec.size() / 3))
+        return fail(g, DIRAC_ERR_ARG, "the vector-potential table ends before step " + std::to_string(g->step + nsteps));
+    int64_t t = g->step;  // step index of the next launch (selects the field's table row)
+    // launches with a field take their step index as an argument: no graph replay
+    if (g->cfg.use_graphs && !field && blocks >= kGraphBlocks) {
         while (blocks >= kGraphBlocks) {
             cudaGraphExec_t ex = nullptr;
             dirac_status st = get_graph(g, g->cur, &ex);
@@ -316,14 +333,16 @@ dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
         }
     }
     for (int64_t b = 0; b < blocks; ++b) {
-        dirac_status st = enqueue_block(g, g->cur, K, g->stream);
+        dirac_status st = enqueue_block(g, g->cur, K, g->stream, t);
         if (st != DIRAC_OK) return st;
         g->cur ^= block_flips(g);
+        t += K;
     }
     for (int64_t r = 0; r < rem; ++r) {
-        dirac_status st = enqueue_block(g, g->cur, 1, g->stream);
+        dirac_status st = enqueue_block(g, g->cur, 1, g->stream, t);
         if (st != DIRAC_OK) return st;
         g->cur ^= block_flips(g);
+        t += 1;
     }
     g->step += nsteps;
     return DIRAC_OK;
@@ -337,6 +356,7 @@ void release(dirac_grid *g) {
     for (auto &p : g->psi)
         if (p) cudaFree(p);
     if (g->table) cudaFree(g->table);
+    if (g->ucoef) cudaFree(g->ucoef);
     if (g->flux_part) cudaFree(g->flux_part);
     if (g->flux_dev) cudaFree(g->flux_dev);
     if (g->ticket) cudaFree(g->ticket);
@@ -355,11 +375,15 @@ void default_plan(dirac_grid *g) {
         return;
     }
     const int mode = sweep_mode(g);
-    int K = g->fp32 ? 2 : 1, P = (g->fp32 || mode == 2) ? 2 : 4;
+    int K = g->fp32 ? 2 : 1, P = (g->fp32 || mode >= 2) ? 2 : 4;
     if (mode == 2) K = 1;
     if (k > 0) K = k;
     if (pp > 0) P = pp;
     if (!sweep_supported(g->fp32, mode, K, P)) P = sweep_supported(g->fp32, mode, K, 4) ? 4 : 2;
+    if (!sweep_supported(g->fp32, mode, K, P)) {
+        K = 1;
+        P = 2;
+    }
     make_plan(g, K, P, 4, g->fp32 ? 12 : 8);
 }
 
@@ -410,6 +434,17 @@ void phase_coeffs_masked(double mu, double v, double dt, double a, double scale,
     out[1] = -std::sin(t_up) * a * scale;
     out[2] = std::cos(t_dn) * a * scale;
     out[3] = -std::sin(t_dn) * a * scale;
+}
+
+void u_entries(double mu, const double At[3], double out[12]) {
+    const double A = std::sqrt(((mu * mu + At[0] * At[0]) + At[1] * At[1]) + At[2] * At[2]);
+    const double sA = A > 0.0 ? std::sin(A) / A : 1.0;
+    const double cA = std::cos(A);
+    const double ax = At[0] * sA, ay = At[1] * sA, az = At[2] * sA, ms = mu * sA;
+    const double e[12] = {cA, -ms,  cA, ms,     // Dup (components 1,2), Ddn (3,4)
+                          0.0, az,  0.0, -az,   // Ez = i At_z s/A, -Ez
+                          ay, ax,   -ay, ax};   // Ep = (i At_x + At_y) s/A, Em = (i At_x - At_y) s/A
+    for (int i = 0; i < 12; ++i) out[i] = e[i];
 }
 
 // Records a message for dirac_last_error(NULL) on this thread (entry points without a grid).
@@ -590,6 +625,50 @@ dirac_status dirac_set_absorber(dirac_grid *g, const double *a, int64_t count) {
                         have_v ? (int64_t)g->v_host.size() : 0);
 }
 
+dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, int64_t nsteps_table) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
+    const bool clear = !A_tilde || nsteps_table == 0;
+    if (!clear && (ndim_of(g) != 2 || strang(g)))
+        return fail(g, DIRAC_ERR_ARG, "a vector potential is implemented for 2-D first-order (DIRAC_LIE) grids");
+    if (!clear)
+        for (int64_t i = 0; i < 3 * nsteps_table; ++i)
+            if (!std::isfinite(A_tilde[i])) return fail(g, DIRAC_ERR_ARG, "vector-potential table holds a non-finite value");
+    CK(g, cudaSetDevice(g->cfg.device));
+    const int mode_before = sweep_mode(g);
+    if (clear) {
+        g->avec.clear();
+    } else {
+        const size_t bytes = (size_t)nsteps_table * 12 * sizeof(double);
+        if (bytes > g->ucoef_cap) {
+            if (g->ucoef) {
+                cudaFree(g->ucoef);
+                g->device_bytes -= g->ucoef_cap;
+                g->ucoef = nullptr;
+                g->ucoef_cap = 0;
+            }
+            CK(g, cudaMalloc(&g->ucoef, bytes));
+            g->ucoef_cap = bytes;
+            g->device_bytes += bytes;
+        }
+        const double mu = g->cfg.m * g->cfg.c * g->cfg.c * g->dt;
+        std::vector<double> h((size_t)nsteps_table * 12);
+        for (int64_t n = 0; n < nsteps_table; ++n) u_entries(mu, A_tilde + 3 * n, &h[(size_t)n * 12]);
+        CK(g, cudaMemcpyAsync(g->ucoef, h.data(), bytes, cudaMemcpyHostToDevice, g->stream));
+        CK(g, cudaStreamSynchronize(g->stream));
+        g->avec.assign(A_tilde, A_tilde + 3 * nsteps_table);
+    }
+    if (sweep_mode(g) != mode_before) {
+        default_plan(g);
+        dirac_status st = ensure_flux_part(g);
+        if (st != DIRAC_OK) return st;
+        const bool have_v = g->v_layout != DIRAC_V_NONE && !g->v_host.empty();
+        return upload_table(g, have_v ? g->v_host.data() : nullptr, have_v ? g->v_layout : DIRAC_V_NONE,
+                            have_v ? (int64_t)g->v_host.size() : 0);
+    }
+    return DIRAC_OK;
+}
+
 dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device) {
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     if (!psi) return fail(g, DIRAC_ERR_ARG, "dirac_set_state: null psi");
@@ -717,6 +796,11 @@ dirac_status dirac_autotune(dirac_grid *g) {
     if (g->cfg.ndim == 3) {
         for (int P : {1, 2, 4})
             for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm});
+    } else if (sweep_mode(g) == 3) {
+        const int KP[][2] = {{1, 1}, {1, 2}, {2, 2}};
+        for (auto &kp : KP)
+            if (sweep_supported(g->fp32, 3, kp[0], kp[1]))
+                for (int wsm : {4, 8, 12}) cands.push_back({kp[0], kp[1], 4, wsm});
     } else if (strang(g)) {
         const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
         for (auto &kp : KP)
@@ -749,6 +833,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
     double best_t = 1e300;
     const int use_graphs = g->cfg.use_graphs;
     g->cfg.use_graphs = 0;
+    g->tuning = true;
     dirac_status st = DIRAC_OK;
     for (const Cand &c : cands) {
         make_plan(g, c.K, c.P, c.wpb, c.wsm);
@@ -771,6 +856,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
         }
     }
     g->cfg.use_graphs = use_graphs;
+    g->tuning = false;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st == DIRAC_OK) {

@@ -13,6 +13,7 @@ namespace dirac {
 //   mode 0 (2-D step):   plane = the x-z grid, rows run along z; one launch runs K full steps
 //                        (x sweep, z sweep, phase), the sweeps' 1/2 factors folded into the
 //                        phase table as 1/4.
+//   mode 3 (2-D step with a uniform vector potential): as mode 0 with the full phase matrix.
 //   mode 1 (3-D, x-y):   planes = z slices, rows run along y; x sweep then y sweep, no phase,
 //                        output left at 4x the swept state (exact scaling, no rounding).
 // Each warp owns an x strip of `strip_w` cells and a segment of `seg_h` rows of one plane.
@@ -31,6 +32,11 @@ struct SweepArgs {
     double vol;            // cell volume dx^d
     int periodic;
     int full_table;
+    // mode 3 (uniform vector potential): per-step entries of U (Sec. 2.3) as 6 complex values
+    // (Dup, Ddn, Ez, -Ez, Ep, Em) = 12 doubles per step; level s of a launch uses step (step0 + s) mod ucoef_n
+    const double *ucoef;
+    int64_t ucoef_n;
+    int64_t step0;
 };
 
 // Arguments of the 3-D z-sweep + phase kernel: the input is 4x the x-y swept state, the table is
@@ -67,6 +73,10 @@ cudaError_t launch_observables(const ObsArgs &a, int fp32, int nblocks, cudaStre
 
 // Instantiated (K, P) pairs of the sweep kernels.
 bool sweep_supported(int fp32, int mode, int K, int P);
+
+// Entries of the U matrix of Sec. 2.3 for mu = m c^2 dt and the field integral At (12 doubles:
+// Dup, Ddn, Ez, -Ez, Ep, Em as (re, im)); A = sqrt(((mu^2 + At_x^2) + At_y^2) + At_z^2), sin(A)/A -> 1 at A = 0.
+void u_entries(double mu, const double At[3], double out[12]);
 
 // Phase coefficients of Eq. sol_dis_4 at A = 0 for potential energy v, times `scale`:
 // out = (cos t_up, -sin t_up, cos t_dn, -sin t_dn), t_up = mu + v dt, t_dn = v dt - mu (FP64, libm).

@@ -61,6 +61,10 @@ template <typename T> __device__ __forceinline__ Cx<T> cmul_mi(Cx<T> a) { return
 template <typename T> __device__ __forceinline__ Cx<T> cmulp(Cx<T> z, Cx<T> p) {
     return {Ar<T>::fma(z.re, p.re, -Ar<T>::mul(z.im, p.im)), Ar<T>::fma(z.re, p.im, Ar<T>::mul(z.im, p.re))};
 }
+// acc + z p with re = fma(z.re, p.re, fma(-z.im, p.im, acc.re)), im = fma(z.re, p.im, fma(z.im, p.re, acc.im))
+template <typename T> __device__ __forceinline__ Cx<T> cmac(Cx<T> acc, Cx<T> z, Cx<T> p) {
+    return {Ar<T>::fma(z.re, p.re, Ar<T>::fma(-z.im, p.im, acc.re)), Ar<T>::fma(z.re, p.im, Ar<T>::fma(z.im, p.re, acc.im))};
+}
 template <typename T> __device__ __forceinline__ double abs2d(Cx<T> a) {
     double r = (double)a.re, i = (double)a.im;
     return __dadd_rn(__dmul_rn(r, r), __dmul_rn(i, i));
@@ -127,6 +131,8 @@ template <int K, int MODE> struct Levels { static constexpr int value = MODE == 
 // MODE 1: 3-D x-y pass (x sweep, y sweep), K must be 1.
 // MODE 2: 2-D second-order (Strang) step x, z, phase(dt), z, x (Sec. 2.4), K steps = 2K levels per launch;
 //         the four sweeps' 1/2 factors ride in the phase coefficients as 1/16.
+// MODE 3: 2-D first-order step with a uniform vector potential: the phase is the full 4x4 matrix of
+//         Eq. sol_dis_4, U(step) exp(-i V dt), with the table holding g = exp(-i V dt) / 4 per column or cell.
 template <typename T, int K, int P, int MODE>
 __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     constexpr int L = Levels<K, MODE>::value;
@@ -319,6 +325,24 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
 #pragma unroll
         for (int j = 0; j < P; ++j) load_tab(static_cast<const T *>(a.table) + xl[j] * 4, pu[j], pd[j]);
     }
+    // MODE 3: entries of U for the step of each level (Dup, Ddn, Ez, -Ez, Ep, Em; Sec. 2.3), and with an
+    // x-only table the entries times this lane's g per cell (M = U g, formed once per task)
+    constexpr int LA = MODE == 3 ? L : 1;
+    Cx<T> UM[LA][6];
+    Cx<T> MA[LA][MODE == 3 ? P : 1][6];
+    if (MODE == 3) {
+#pragma unroll
+        for (int lev = 0; lev < LA; ++lev) {
+            const double *u = a.ucoef + ((a.step0 + lev) % a.ucoef_n) * 12;
+#pragma unroll
+            for (int e = 0; e < 6; ++e) UM[lev][e] = Cx<T>{(T)__ldg(u + 2 * e), (T)__ldg(u + 2 * e + 1)};
+            if (!a.full_table)
+#pragma unroll
+                for (int j = 0; j < (MODE == 3 ? P : 1); ++j)
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) MA[lev][j][e] = cmulp(UM[lev][e], pu[j]);
+        }
+    }
     // Flux through the face (owned by this strip): per row, 1/2(|u14|^2+|u23|^2) at face-1 minus
     // 1/2(|w14|^2+|w23|^2) at face.  The face lane's 8 values of row q are handed to lane (q - r_begin) % 32;
     // every 32 rows all lanes evaluate their row at once, so the FP64 work runs SIMT-wide (1/32 of the FP64
@@ -504,7 +528,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                         o[2] = csub(UA[lev][j][0], W13);
                         o[1] = cadd(UA[lev][j][1], W24);
                         o[3] = csub(W24, UA[lev][j][1]);
-                        // phase (Eq. sol_dis_4, A = 0) with the deferred 1/4
+                        // phase (Eq. sol_dis_4) with the deferred 1/4
                         Cx<T> qu, qd;
                         if (a.full_table) {
                             const int64_t rr = per ? pmod(q - 1, nr) : min(max(q - 1, (int64_t)0), nr - 1);
@@ -513,10 +537,27 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                             qu = pu[j];
                             qd = pd[j];
                         }
-                        o[0] = cmulp(o[0], qu);
-                        o[1] = cmulp(o[1], qu);
-                        o[2] = cmulp(o[2], qd);
-                        o[3] = cmulp(o[3], qd);
+                        if (MODE == 3) {
+                            // psi'_a = sum_b (U_ab g) psi_b over the non-zero entries, columns in order
+                            Cx<T> m6[6];
+#pragma unroll
+                            for (int e = 0; e < 6; ++e)
+                                m6[e] = a.full_table ? cmulp(UM[MODE == 3 ? lev : 0][e], qu) : MA[MODE == 3 ? lev : 0][MODE == 3 ? j : 0][e];
+                            const Cx<T> z0 = {T(0), T(0)};
+                            const Cx<T> n0 = cmac(cmac(cmac(z0, o[0], m6[0]), o[2], m6[2]), o[3], m6[4]);
+                            const Cx<T> n1 = cmac(cmac(cmac(z0, o[1], m6[0]), o[2], m6[5]), o[3], m6[3]);
+                            const Cx<T> n2 = cmac(cmac(cmac(z0, o[0], m6[2]), o[1], m6[4]), o[2], m6[1]);
+                            const Cx<T> n3 = cmac(cmac(cmac(z0, o[0], m6[5]), o[1], m6[3]), o[3], m6[1]);
+                            o[0] = n0;
+                            o[1] = n1;
+                            o[2] = n2;
+                            o[3] = n3;
+                        } else {
+                            o[0] = cmulp(o[0], qu);
+                            o[1] = cmulp(o[1], qu);
+                            o[2] = cmulp(o[2], qd);
+                            o[3] = cmulp(o[3], qd);
+                        }
                     }
                     UA[lev][j][0] = UB[lev][j][0];
                     UA[lev][j][1] = UB[lev][j][1];

@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--ndim", type=int, default=2)
     ap.add_argument("--batch-runs", type=int, default=0, help="run this many ensemble runs as one batch instead")
     ap.add_argument("--seg", type=int, default=256, help="batch: rows per task")
+    ap.add_argument("--field", action="store_true",
+                    help="2-D: add a uniform two-cycle laser pulse (vector potential) over the run")
     ap.add_argument("--mlp", type=int, default=0,
                     help="instead: train the transmission network this many epochs on seeded random targets")
     args = ap.parse_args()
@@ -102,11 +104,17 @@ def main():
                             use_graphs=not args.no_graphs)
         layout = D.DIRAC_V_FULL
     h = D.dirac_create_grid(cfg)
+    if args.field:
+        total = args.nsteps * args.repeat
+        dt = W.DX_DEFAULT / W.C_AU
+        D.dirac_set_vector_potential(h, W.laser_A_tilde(total, dt, 2.0e4, 2 * np.pi / (total * dt / 2), 2.0))
     D.dirac_set_potential(h, V, layout)
     host = np.ascontiguousarray(psi.astype(np.complex64 if prec == D.DIRAC_FP32 else np.complex128))
     D.dirac_set_state(h, host)
     times = []
-    for _ in range(args.repeat):
+    for it in range(args.repeat):
+        if args.field:
+            D.dirac_set_counters(h, it * args.nsteps, 0.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         D.dirac_step(h, args.nsteps)

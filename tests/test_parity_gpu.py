@@ -371,3 +371,132 @@ def test_absorbing_layer_bit_exact(D):
         D.dirac_destroy(h)
     assert _bits_equal(got, want)
     assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+
+
+# ------------------------------------------------------------------ uniform vector potential (Eq. sol_dis_4, Sec. 2.3)
+
+def _field_table(n, seed, scale=1.2):
+    rng = np.random.default_rng(seed)
+    At = rng.uniform(-scale, scale, (n, 3))
+    At[2] = 0.0
+    return At
+
+
+def _run_field(D, psi, nsteps, At, V=None, periodic=False, fp32=False, K=0, P=0, flux_face=-1, start=0,
+               absorber=None, x_min=None):
+    nz, ny, nx, _ = psi.shape
+    cfg = D.make_config((nx, ny, nz), precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO, flux_face=flux_face,
+                        steps_per_launch=K, points_per_lane=P, x_min=x_min)
+    h = D.dirac_create_grid(cfg)
+    try:
+        if absorber is not None:
+            D.dirac_set_absorber(h, absorber)
+        D.dirac_set_vector_potential(h, At)
+        if V is not None:
+            D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY if V.size == nx else D.DIRAC_V_FULL)
+        dt = np.complex64 if fp32 else np.complex128
+        D.dirac_set_state(h, np.ascontiguousarray(psi.astype(dt)))
+        if start:
+            D.dirac_set_counters(h, start, 0.0)
+        D.dirac_step(h, nsteps)
+        out = np.empty(psi.shape, dtype=dt)
+        D.dirac_get_state(h, out)
+        obs = D.dirac_observables(h)
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    return out, obs, info
+
+
+@pytest.mark.parametrize("shape", [(70, 45), (5, 7), (130, 33)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("K,P", [(1, 1), (1, 2)])
+def test_vector_potential_fp64_bit_exact(D, shape, periodic, K, P):
+    nx, nz = shape
+    psi = W.random_state(nz, 1, nx, seed=nx + 3 * nz)
+    V = np.random.default_rng(4).uniform(-2e4, 6e4, nx)
+    At = _field_table(9, nx)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 9, V=V, periodic=periodic, A_tilde=At)
+    got, _, info = _run_field(D, psi, 9, At, V=V, periodic=periodic, K=K, P=P)
+    assert info["steps_per_launch"] == K and info["points_per_lane"] == P
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+def test_vector_potential_full_table_offset_flux_absorber(D):
+    """Per-cell potential, a step counter starting inside the table, the face flux and an absorbing layer
+    together; bit-exact state, flux to 1e-12."""
+    nx, nz = 96, 40
+    psi = W.random_state(nz, 1, nx, seed=17)
+    V = np.random.default_rng(18).uniform(-4e4, 4e4, nx * nz)
+    At = _field_table(20, 19, scale=2.5)
+    a = W.absorber_mask(nx, 12, 0.2)
+    want, F = oracle.step(psi, 2, 1.0, C, DX, 11, V=V, flux_face=50, A_tilde=At, step0=6, absorber=a)
+    got, obs, _ = _run_field(D, psi, 11, At, V=V, flux_face=50, start=6, absorber=a, K=1, P=2)
+    assert _bits_equal(got, want)
+    assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+
+
+def test_vector_potential_laser_packet_fp64_and_fp32(D):
+    """A Gaussian packet in a two-cycle laser pulse (analytic field integrals) on a 256 x 192 grid: FP64
+    bit-exact over 300 steps, FP32 storage within its rounding tolerance."""
+    nx, nz, nsteps = 256, 192, 300
+    dx = 4 * DX
+    dt = dx / C
+    x_min = (-nx * dx / 2, 0.0, -nz * dx / 2)
+    psi = W.gaussian_packet(nx, nz, dx, x_min[0], x_min[2], 0.0, 0.0, 16 * dx, 0.3 * C)
+    omega = 2 * np.pi / (nsteps * dt / 2)
+    At = W.laser_A_tilde(nsteps, dt, 4.0e4, omega, 2.0, pol=(0.8, 0.0, 0.6))
+    want, _ = oracle.step(psi, 2, 1.0, C, dx, nsteps, A_tilde=At)
+    got, _, _ = _run_field_dx(D, psi, nsteps, At, dx, K=1, P=2)
+    assert _bits_equal(got, want)
+    g32, _, _ = _run_field_dx(D, psi, nsteps, At, dx, fp32=True, K=2, P=2)
+    assert rel_l2(g32.astype(np.complex128), want) < 5e-5
+
+
+def _run_field_dx(D, psi, nsteps, At, dx, fp32=False, K=0, P=0):
+    nz, ny, nx, _ = psi.shape
+    cfg = D.make_config((nx, ny, nz), dx=dx, precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64,
+                        steps_per_launch=K, points_per_lane=P)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_vector_potential(h, At)
+        dt = np.complex64 if fp32 else np.complex128
+        D.dirac_set_state(h, np.ascontiguousarray(psi.astype(dt)))
+        D.dirac_step(h, nsteps)
+        out = np.empty(psi.shape, dtype=dt)
+        D.dirac_get_state(h, out)
+        obs = D.dirac_observables(h)
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    return out, obs, info
+
+
+def test_vector_potential_table_end_and_removal(D):
+    """Stepping past the table is refused with nothing enqueued; removing the field returns to the
+    field-free kernel (bit-exact with the oracle's field-free step); autotune keeps the state."""
+    nx, nz = 40, 30
+    psi = W.random_state(nz, 1, nx, seed=23)
+    At = _field_table(6, 24)
+    cfg = D.make_config((nx, 1, nz))
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_vector_potential(h, At)
+        D.dirac_set_state(h, psi)
+        D.dirac_autotune(h)
+        D.dirac_step(h, 4)
+        with pytest.raises(D.DiracError):
+            D.dirac_step(h, 3)
+        mid = np.empty_like(psi)
+        D.dirac_get_state(h, mid)
+        want, _ = oracle.step(psi, 2, 1.0, C, DX, 4, A_tilde=At)
+        assert _bits_equal(mid, want)
+        D.dirac_set_vector_potential(h, None)
+        D.dirac_step(h, 5)
+        out = np.empty_like(psi)
+        D.dirac_get_state(h, out)
+        want2, _ = oracle.step(want, 2, 1.0, C, DX, 5)
+        assert _bits_equal(out, want2)
+    finally:
+        D.dirac_destroy(h)
