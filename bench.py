@@ -39,6 +39,7 @@ FP64_BYTES_PER_POINT_STEP = 128  # 2-D, x-only table: 64 B read + 64 B written
 FP32_BYTES_PER_POINT_STEP = 64
 FLOPS_PER_POINT_STEP_2D = 56    # 32 adds (two sweeps) + 4 complex products of 6 flops
 FP64_INSTR_PER_POINT_STEP_2D = 48  # 32 DADD + 8 DMUL + 8 DFMA: what the FP64 pipe issues per 2-D point-step
+FP64_INSTR_PER_POINT_STEP_2D_FIELD = 80  # with a vector potential: 32 DADD + 12 complex multiply-adds of 4 DFMA
 # FP64 issue roof: the recipe's nominal 1.25 TFLOP/s counts a DFMA as 2 flops -> 0.625 T FP64 instructions/s
 # (DADD and DMUL issue at the DFMA rate).  Measured on this machine's GB300 with an FMA/ADD throughput probe:
 # 0.5285 T lane-instructions/s (1.68 per SM per clock at 2.07 GHz, 152 SMs).
@@ -63,6 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-field", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--judge-points", type=int, default=16)
@@ -345,6 +347,34 @@ def main():
                                                    if args.side == 2048 else None),
                             "T": o32["flux_cum"] / n0, "T_fp64": obs["flux_cum"] / n0}
         D.dirac_destroy(h32)
+
+    # ---------------------------------------------------------------- FP64 with a laser field
+    if not args.no_field:
+        nf = 400
+        hf = make_grid(D.DIRAC_FP64)
+        dtf = run.dx / W.C_AU
+        D.dirac_set_vector_potential(hf, W.laser_A_tilde(nf * 3, dtf, 2.0e4, 2 * np.pi / (nf * dtf / 2), 2.0,
+                                                         pol=(0.8, 0.0, 0.6)))
+        D.dirac_set_state(hf, dev_state)
+        D.dirac_autotune(hf)
+        inf_ = D.dirac_get_info(hf)
+        D.dirac_step(hf, nf)  # warm-up (table rows 0..nf-1)
+        ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        ef0.record(stream)
+        D.dirac_step(hf, nf)
+        ef1.record(stream)
+        stream.synchronize()
+        tf = max_over_ranks(ef0.elapsed_time(ef1))
+        D.dirac_destroy(hf)
+        vf = ncell * nf * world / (tf / 1e3)
+        variants["fp64_laser_field"] = {
+            "value": vf, "unit": "point-steps/s", "steps": nf, "steps_per_launch": inf_["steps_per_launch"],
+            "points_per_lane": inf_["points_per_lane"],
+            "workload": "the 2048^2 Klein FP64 grid in a uniform two-cycle laser pulse (vector potential, full "
+                        "phase matrix of Eq. sol_dis_4), %d timed steps" % nf,
+            "fp64_instr_per_point_step": FP64_INSTR_PER_POINT_STEP_2D_FIELD,
+            "frac_of_measured_fp64_issue": FP64_INSTR_PER_POINT_STEP_2D_FIELD * vf / world / 1e12 / FP64_ISSUE_PEAK_MEASURED}
 
     # ---------------------------------------------------------------- batched ensemble (FP32)
     if not args.no_batch:

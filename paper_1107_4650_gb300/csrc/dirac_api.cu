@@ -376,7 +376,7 @@ void default_plan(dirac_grid *g) {
     }
     const int mode = sweep_mode(g);
     int K = g->fp32 ? 2 : 1, P = (g->fp32 || mode >= 2) ? 2 : 4;
-    if (mode == 2) K = 1;
+    if (mode == 2 || mode == 3) K = 1;  // measured: the field's phase matrix makes k = 2 register-bound
     if (k > 0) K = k;
     if (pp > 0) P = pp;
     if (!sweep_supported(g->fp32, mode, K, P)) P = sweep_supported(g->fp32, mode, K, 4) ? 4 : 2;
