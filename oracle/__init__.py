@@ -62,6 +62,8 @@ def _load():
         lib.oracle_set_absorber.restype = None
         lib.oracle_set_vector_potential.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
         lib.oracle_set_vector_potential.restype = None
+        lib.oracle_set_shift.argtypes = [ctypes.c_int64]
+        lib.oracle_set_shift.restype = None
         _lib = lib
     return _lib
 
@@ -92,10 +94,28 @@ def _potential(V, psi):
     raise ValueError("potential must have nx entries (one per x column) or one per cell")
 
 
-def sweep(psi, axis: int, periodic: bool = False) -> np.ndarray:
-    """One directional sub-step (Eq. sol_dis_1/2/3 for axis 0/1/2); returns a new array."""
+class _Shift:
+    """Context: characteristic shift K (c dt = K dx, Sec. 2.3); 1 outside the context."""
+    def __init__(self, K):
+        if int(K) < 1:
+            raise ValueError("the characteristic shift must be >= 1")
+        self.K = int(K)
+
+    def __enter__(self):
+        _load().oracle_set_shift(self.K)
+        return self
+
+    def __exit__(self, *exc):
+        _load().oracle_set_shift(1)
+
+
+def sweep(psi, axis: int, periodic: bool = False, shift: int = 1) -> np.ndarray:
+    """One directional sub-step (Eq. sol_dis_1/2/3 for axis 0/1/2) with neighbours at +-shift cells; returns a
+    new array."""
     out = _as_state(psi)
-    if _load().oracle_sweep(out.ctypes.data, _dims(out), int(axis), int(bool(periodic))) != 0:
+    with _Shift(shift):
+        rc = _load().oracle_sweep(out.ctypes.data, _dims(out), int(axis), int(bool(periodic)))
+    if rc != 0:
         raise MemoryError("oracle_sweep")
     return out
 
@@ -143,7 +163,7 @@ class _VectorPotential:
 
 def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
          periodic: bool = False, flux_face: int = -1, flux_cum: float = 0.0, absorber=None,
-         A_tilde=None, step0: int = 0):
+         A_tilde=None, step0: int = 0, shift: int = 1):
     """nsteps first-order split steps (Eqs. split1-4 discretised as sol_dis_1-4), dt = dx/c.
 
     Returns (psi_out, flux_cum): the cumulative probability carried across the x face
@@ -151,11 +171,12 @@ def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
     `absorber`: optional per-x-column factors a(x) in (0, 1] applied with the phase (not in the paper).
     `A_tilde`: optional (nt, 3) array of uniform vector-potential integrals e int A dt per step (Eq. field_dis1);
     step s of this call uses row step0 + s, and the phase is the full matrix of Eq. sol_dis_4.
+    `shift`: characteristic shift K, c dt = K dx (Sec. 2.3): dt = K dx / c and neighbours at +-K cells.
     """
     out = _as_state(psi)
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    with _Absorber(absorber, out.shape[2]), _VectorPotential(A_tilde, step0):
+    with _Absorber(absorber, out.shape[2]), _VectorPotential(A_tilde, step0), _Shift(shift):
         rc = _load().oracle_step(out.ctypes.data, _dims(out), int(ndim), int(bool(periodic)), float(m), float(c),
                                  float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
                                  int(flux_face), ctypes.addressof(fc))
@@ -167,7 +188,7 @@ def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
 
 
 def step_strang2d(psi, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False,
-                  flux_face: int = -1, flux_cum: float = 0.0):
+                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1):
     """nsteps second-order (Strang) steps in the x-z plane (Sec. 2.4): x, z, phase(dt), z, x with
     dt = 2 dx / c.  Returns (psi_out, flux_cum) as step()."""
     out = _as_state(psi)
@@ -175,9 +196,10 @@ def step_strang2d(psi, m: float, c: float, dx: float, nsteps: int, V=None, perio
         raise ValueError("Strang steps are 2-D (ny = 1)")
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    rc = _load().oracle_step_strang2d(out.ctypes.data, _dims(out), int(bool(periodic)), float(m), float(c), float(dx),
-                                      None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
-                                      int(flux_face), ctypes.addressof(fc))
+    with _Shift(shift):
+        rc = _load().oracle_step_strang2d(out.ctypes.data, _dims(out), int(bool(periodic)), float(m), float(c),
+                                          float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
+                                          int(flux_face), ctypes.addressof(fc))
     if rc != 0:
         raise MemoryError("oracle_step_strang2d")
     return out, fc.value

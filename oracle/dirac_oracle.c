@@ -94,6 +94,13 @@ static void sweep_cell(cplx *o, const cplx *L, const cplx *R, int axis) {
     }
 }
 
+/* Characteristic shift K (Sec. 2.3): with c dt = K a the solution of each directional equation moves the
+ * characteristics by K cells, so L = psi(i - K e_d), R = psi(i + K e_d).  The paper takes K = 1; any
+ * K >= 1 is exact in each direction.  Set by oracle_set_shift (default 1); dt = K dx / c in the steps. */
+static int64_t g_shift = 1;
+
+void oracle_set_shift(int64_t K) { g_shift = K >= 1 ? K : 1; }
+
 /* Sweep along `axis` (0 = x, 1 = y, 2 = z) of the whole grid, in place. */
 int oracle_sweep(double *psi_d, const int64_t n[3], int axis, int periodic) {
     cplx *psi = (cplx *)psi_d;
@@ -101,7 +108,7 @@ int oracle_sweep(double *psi_d, const int64_t n[3], int axis, int periodic) {
     cplx *out = (cplx *)malloc((size_t)total * 4 * sizeof(cplx));
     if (!out) return -1;
     int64_t d[3] = {0, 0, 0};
-    d[axis] = 1;
+    d[axis] = g_shift;
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n[2]; ++k)
         for (int64_t j = 0; j < n[1]; ++j)
@@ -162,20 +169,26 @@ int oracle_phase(double *psi_d, const int64_t n[3], double m, double c, double d
 
 /* Probability carried across the face between cells face-1 and face during one
  * x sweep (Sec. 2.2 and App. A): the +c characteristics (psi1+psi4, psi2+psi3)/sqrt2
- * of cell face-1 move right, the -c characteristics (psi1-psi4, psi2-psi3)/sqrt2 of
- * cell face move left.  With c dt = dx a whole cell's characteristic content moves
- * one cell, so the probability is the density times the cell volume dx^d, summed
- * over all (j,k) in index order. */
+ * of cells face-K .. face-1 move right across it, the -c characteristics
+ * (psi1-psi4, psi2-psi3)/sqrt2 of cells face .. face+K-1 move left across it (shift K).
+ * A whole cell's characteristic content moves, so the probability is the density
+ * times the cell volume dx^d, summed over all (j,k) in index order (cells in
+ * increasing i within a row). */
 static double face_flux(const cplx *psi, const int64_t n[3], int periodic, int64_t face, double vol) {
     double f = 0.0;
     for (int64_t k = 0; k < n[2]; ++k)
         for (int64_t j = 0; j < n[1]; ++j) {
-            const cplx *a = cell(psi, n, periodic, face - 1, j, k);
-            const cplx *b = cell(psi, n, periodic, face, j, k);
-            a = a ? a : ZERO4;
-            b = b ? b : ZERO4;
-            double right = 0.5 * (c_abs2(c_add(a[0], a[3])) + c_abs2(c_add(a[1], a[2])));
-            double left = 0.5 * (c_abs2(c_sub(b[0], b[3])) + c_abs2(c_sub(b[1], b[2])));
+            double right = 0.0, left = 0.0;
+            for (int64_t i = face - g_shift; i < face; ++i) {
+                const cplx *a = cell(psi, n, periodic, i, j, k);
+                a = a ? a : ZERO4;
+                right += 0.5 * (c_abs2(c_add(a[0], a[3])) + c_abs2(c_add(a[1], a[2])));
+            }
+            for (int64_t i = face; i < face + g_shift; ++i) {
+                const cplx *b = cell(psi, n, periodic, i, j, k);
+                b = b ? b : ZERO4;
+                left += 0.5 * (c_abs2(c_sub(b[0], b[3])) + c_abs2(c_sub(b[1], b[2])));
+            }
             f += right - left;
         }
     return f * vol;
@@ -264,7 +277,7 @@ static int oracle_phase_A(double *psi_d, const int64_t n[3], double m, double c,
 int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double m, double c,
                 double dx, const double *V, int layout, int64_t nsteps, int64_t flux_face,
                 double *flux_cum) {
-    double dt = dx / c;
+    double dt = (double)g_shift * dx / c;
     double vol = (ndim == 3) ? dx * dx * dx : dx * dx;
     for (int64_t s = 0; s < nsteps; ++s) {
         if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
@@ -288,7 +301,7 @@ int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double 
  * both x sweeps of a step. */
 int oracle_step_strang2d(double *psi, const int64_t n[3], int periodic, double m, double c, double dx,
                          const double *V, int layout, int64_t nsteps, int64_t flux_face, double *flux_cum) {
-    double dt = 2.0 * dx / c;
+    double dt = 2.0 * (double)g_shift * dx / c;
     double vol = dx * dx;
     for (int64_t s = 0; s < nsteps; ++s) {
         if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);

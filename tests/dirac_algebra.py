@@ -20,16 +20,16 @@ BETA = np.kron(np.diag([1.0, -1.0]), I2).astype(np.complex128)
 ALPHA = [np.kron(SX, s) for s in (SX, SY, SZ)]  # [[0, s], [s, 0]]
 
 
-def sweep_matrix(n, axis: int, periodic: bool) -> np.ndarray:
+def sweep_matrix(n, axis: int, periodic: bool, shift: int = 1) -> np.ndarray:
     """Dense matrix of one directional sweep on a grid n = (nx, ny, nz), state flattened as
-    ((k*ny + j)*nx + i)*4 + c."""
+    ((k*ny + j)*nx + i)*4 + c; neighbours at +-shift cells (c dt = shift * dx)."""
     nx, ny, nz = n
     N = nx * ny * nz
     M = np.zeros((4 * N, 4 * N), dtype=np.complex128)
     Pp = 0.5 * (I4 + ALPHA[axis])
     Pm = 0.5 * (I4 - ALPHA[axis])
     d = [0, 0, 0]
-    d[axis] = 1
+    d[axis] = shift
 
     def idx(i, j, k):
         if periodic:
@@ -84,13 +84,13 @@ def amplification_2d(kx, kz, nx, nz, mu):
     return Ub @ Uz @ Ux
 
 
-def dft_exact_evolution_2d(psi0: np.ndarray, nsteps: int, mu: float) -> np.ndarray:
+def dft_exact_evolution_2d(psi0: np.ndarray, nsteps: int, mu: float, shift: int = 1) -> np.ndarray:
     """psi after nsteps of the periodic V = 0 scheme, computed mode by mode in Fourier space.
-    psi0 has shape (nz, 1, nx, 4)."""
+    psi0 has shape (nz, 1, nx, 4).  With characteristic shift K a sweep moves by K cells: th = 2 pi k K / N."""
     nz, _, nx, _ = psi0.shape
     hat = np.fft.fft2(psi0[:, 0], axes=(0, 1))
     KX, KZ = np.meshgrid(np.arange(nx), np.arange(nz))
-    U = amplification_2d(KX, KZ, nx, nz, mu)
+    U = amplification_2d(shift * KX, shift * KZ, nx, nz, mu)
     Un = np.linalg.matrix_power(U, nsteps)
     hat = np.einsum("zxab,zxb->zxa", Un, hat)
     return np.fft.ifft2(hat, axes=(0, 1))[:, None]

@@ -34,6 +34,9 @@ MUTANTS = {
     "A_z_entry_sign": ("U[1][3].im = -az; U[3][1].im = -az;", "U[1][3].im = az; U[3][1].im = -az;"),
     "A_y_entry_sign": ("U[0][3].re = ay;  U[0][3].im = ax;", "U[0][3].re = -ay;  U[0][3].im = ax;"),
     "A_mass_term_sign": ("U[0][0].re = cA; U[0][0].im = -ms;", "U[0][0].re = cA; U[0][0].im = ms;"),
+    "shift_ignored_in_sweep": ("d[axis] = g_shift;", "d[axis] = 1;"),
+    "shift_flux_window": ("for (int64_t i = face - g_shift; i < face; ++i) {", "for (int64_t i = face - 1; i < face; ++i) {"),
+    "shift_time_step": ("double dt = (double)g_shift * dx / c;", "double dt = dx / c;"),
     "A_row_order": ("acc = c_mac(acc, q[b], c_mul(U[a][b], g));", "acc = c_mac(acc, q[b], c_mul(U[b][a], g));"),
 }
 
@@ -55,6 +58,8 @@ def _build_mutant(tmp_path, name, old, new):
     lib.oracle_set_absorber.restype = None
     lib.oracle_set_vector_potential.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
     lib.oracle_set_vector_potential.restype = None
+    lib.oracle_set_shift.argtypes = [ctypes.c_int64]
+    lib.oracle_set_shift.restype = None
     return lib
 
 
@@ -94,6 +99,20 @@ def _pins_pass():
     psi = W.random_state(9, 1, 10, seed=93)
     got, _ = oracle.step(psi, 2, 1.0, C, DX, 4, periodic=True, A_tilde=At[[0, 1, 2, 0]])
     ok &= A.rel_l2(got, A.dft_exact_evolution_2d_A(psi, C * DX, At[[0, 1, 2, 0]])) < 1e-13
+    # characteristic shift 3: explicit sweep matrix, Fourier evolution, flux identity
+    psi = W.random_state(5, 1, 8, seed=94)
+    got = oracle.sweep(psi, 0, False, shift=3)
+    ok &= np.max(np.abs(got.reshape(-1) - A.sweep_matrix((8, 1, 5), 0, False, shift=3) @ psi.reshape(-1))) < 1e-15
+    psi = W.random_state(12, 1, 14, seed=95)
+    got, _ = oracle.step(psi, 2, 1.0, C, DX, 3, periodic=True, shift=3)
+    ok &= A.rel_l2(got, A.dft_exact_evolution_2d(psi, 3, C * 3 * DX, shift=3)) < 1e-13
+    run = W.KleinRun(side=200, V0=2.5 * C * C, p0=0.7 * C, width=6 * DX, nsteps=12, face=100)
+    psi0 = run.state()
+    x_min, z_min, _, _, face = run.geometry()
+    o0 = oracle.observables(psi0, 2, DX, (x_min, 0.0, z_min), face)
+    out, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=run.potential(), flux_face=face, shift=3)
+    o1 = oracle.observables(out, 2, DX, (x_min, 0.0, z_min), face)
+    ok &= abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
     return bool(ok)
 
 

@@ -526,3 +526,53 @@ def test_laser_field_integrals_match_quadrature():
         want = -quad(A_of_t, k * dt, (k + 1) * dt, epsabs=1e-14, epsrel=1e-12, points=[tau])[0]
         assert abs(At[k, 0] - 0.6 * want) < 1e-9 * A0 * dt and abs(At[k, 2] - 0.8 * want) < 1e-9 * A0 * dt
     assert At[-1, 0] == 0.0 and At[:, 1].max() == 0.0
+
+
+# ---------------------------------------------------------------- characteristic shift K > 1 (c dt = K dx, Sec. 2.3)
+
+@pytest.mark.parametrize("K", [2, 3])
+@pytest.mark.parametrize("shape,axis,periodic", [((7, 1, 5), 0, False), ((6, 1, 8), 2, True), ((9, 1, 4), 0, True),
+                                                 ((4, 5, 3), 1, False), ((3, 2, 7), 2, False)])
+def test_shift_sweeps_equal_explicit_matrices(oracle_mod, K, shape, axis, periodic):
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=40 + K + axis)
+    got = oracle.sweep(psi, axis, periodic, shift=K)
+    want = A.sweep_matrix(shape, axis, periodic, shift=K) @ psi.reshape(-1)
+    assert np.max(np.abs(got.reshape(-1) - want)) < 1e-15
+
+
+@pytest.mark.parametrize("K", [2, 5])
+def test_shift_step_against_fourier_evolution(oracle_mod, K):
+    """Periodic V = 0: with c dt = K dx every mode advances by e^{-i beta mu} e^{-i alpha_z th_z} e^{-i alpha_x th_x},
+    th = 2 pi k K / N and mu = m c^2 K dx / c."""
+    nx, nz, nsteps = 24, 18, 9
+    psi = W.random_state(nz, 1, nx, seed=60 + K)
+    out, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, nsteps, periodic=True, shift=K)
+    want = A.dft_exact_evolution_2d(psi, nsteps, M * C * K * W.DX_DEFAULT, shift=K)
+    assert A.rel_l2(out, want) < 1e-13
+
+
+def test_shift_error_is_first_order_in_dt(oracle_mod):
+    """The shifts are exact in each direction, so at a fixed physical time the error against the continuum
+    evolution (App. B) is the first-order splitting error: it doubles each time K (and dt) doubles."""
+    n, dx = 128, 0.25 * W.DX_DEFAULT
+    psi = W.gaussian_packet(n, n, dx, -n * dx / 2, -n * dx / 2, 0.0, 0.0, 12 * dx, 0.5 * C)
+    T = 64
+    exact = A.continuum_evolution_2d(psi, dx, T * dx / C, M, C)
+    errs = [A.rel_l2(oracle.step(psi, 2, M, C, dx, T // K, periodic=True, shift=K)[0], exact) for K in (1, 2, 4)]
+    assert errs[0] < 0.07
+    for lo, hi in zip(errs, errs[1:]):
+        assert 1.8 < hi / lo < 2.2, errs
+
+
+def test_shift_flux_identity(oracle_mod):
+    """K = 3: the probability counted across the face (three cells of characteristics each way per x sweep)
+    equals the change of the norm right of the face while nothing reaches the edges."""
+    run = W.KleinRun(side=200, V0=2.5 * C * C, p0=0.7 * C, width=6 * W.DX_DEFAULT, nsteps=12, face=100)
+    psi0 = run.state()
+    x_min, z_min, _, _, face = run.geometry()
+    o0 = oracle.observables(psi0, 2, run.dx, (x_min, 0.0, z_min), face)
+    out, F = oracle.step(psi0, 2, M, C, run.dx, run.nsteps, V=run.potential(), flux_face=face, shift=3)
+    o1 = oracle.observables(out, 2, run.dx, (x_min, 0.0, z_min), face)
+    assert F > 1e-3
+    assert abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
