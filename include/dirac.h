@@ -73,6 +73,10 @@ typedef struct {
                              DIRAC_STRANG (2-D only): second-order steps x, z, phase(dt), z, x with
                              dt = 2 dx / c, so each half-step sweep is the one-cell shift (Sec. 2.4);
                              steps_per_launch 1 (FP64) or 1, 2 (FP32) */
+    int char_shift;       /* characteristic shift K of Sec. 2.3: c dt = K dx, each sweep moves the
+                             characteristics by K cells and dt = K dx / c.  0 or 1: the paper's K = 1;
+                             2, 3 or 4: 2-D first-order (DIRAC_LIE) grids without a vector potential,
+                             one step per launch */
 } dirac_config;
 
 /* Fills cfg with defaults: ndim 2, n = {256,1,256}, dx = 10/8192, c = 137.0359895, m = 1,

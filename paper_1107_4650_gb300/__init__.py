@@ -38,7 +38,8 @@ class dirac_config(ctypes.Structure):
                 ("c", ctypes.c_double), ("m", ctypes.c_double), ("x_min", ctypes.c_double * 3),
                 ("precision", ctypes.c_int), ("boundary", ctypes.c_int), ("flux_face", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("points_per_lane", ctypes.c_int), ("splitting", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("points_per_lane", ctypes.c_int), ("splitting", ctypes.c_int),
+                ("char_shift", ctypes.c_int)]
 
 
 class dirac_obs(ctypes.Structure):
@@ -210,7 +211,7 @@ def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRA
                 boundary: int = DIRAC_BC_ZERO, x_min=None, flux_face: int = -1, stream=None,
                 device: int = 0, steps_per_launch: int = 0, use_graphs: bool = True,
                 c: float | None = None, m: float | None = None, points_per_lane: int = 0,
-                splitting: int = 0) -> dirac_config:
+                splitting: int = 0, char_shift: int = 0) -> dirac_config:
     """dirac_default_config() with the given fields replaced (n = (nx, ny, nz))."""
     cfg = dirac_default_config()
     cfg.ndim = ndim
@@ -235,6 +236,7 @@ def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRA
     cfg.use_graphs = 1 if use_graphs else 0
     cfg.points_per_lane = points_per_lane
     cfg.splitting = splitting
+    cfg.char_shift = char_shift
     return cfg
 
 

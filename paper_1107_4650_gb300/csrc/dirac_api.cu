@@ -95,12 +95,16 @@ bool strang(const dirac_grid *g) { return g->cfg.splitting == DIRAC_STRANG; }
 // Power-of-two scale the phase coefficients carry for the sweeps' 1/2 factors: 1/4 (2-D), 1/8 (3-D),
 // 1/16 (2-D Strang: four sweeps per step).
 double scale_of(const dirac_grid *g) { return strang(g) ? 0.0625 : (ndim_of(g) == 3 ? 0.125 : 0.25); }
+int char_shift(const dirac_grid *g) { return g->cfg.char_shift > 1 ? g->cfg.char_shift : 1; }
 int sweep_mode(const dirac_grid *g) {
     if (strang(g)) return 2;
     if (ndim_of(g) == 3) return 1;
+    if (char_shift(g) > 1) return 4;
     return g->avec.empty() ? 0 : 3;
 }
 int levels(const dirac_grid *g, int K) { return strang(g) ? 2 * K : K; }
+// x halo cells of a strip (each side) for K steps per launch
+int halo_of(const dirac_grid *g, int K) { return sweep_mode(g) == 4 ? char_shift(g) : levels(g, K); }
 double cell_volume(const dirac_grid *g) {
     const double dx = g->cfg.dx;
     return ndim_of(g) == 3 ? dx * dx * dx : dx * dx;
@@ -186,7 +190,7 @@ void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
     const int64_t nx = g->cfg.n[0];
     const int64_t nr = (ndim_of(g) == 3) ? g->cfg.n[1] : g->cfg.n[2];
     const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
-    const int Lv = levels(g, K);
+    const int Lv = halo_of(g, K);
     p.strip_w = 32 * P - 2 * Lv;
     p.nstrips = (nx + p.strip_w - 1) / p.strip_w;
     const int64_t want = (int64_t)g->sm_count * target_warps_per_sm;
@@ -240,7 +244,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     a.nx = g->cfg.n[0];
     a.nr = (ndim_of(g) == 3) ? g->cfg.n[1] : g->cfg.n[2];
     a.nplanes = planes;
-    a.strip_w = 32 * p.P - 2 * levels(g, K);
+    a.strip_w = 32 * p.P - 2 * halo_of(g, K);
     a.nstrips = (a.nx + a.strip_w - 1) / a.strip_w;
     a.nsegs = p.nsegs;
     a.seg_h = p.seg_h;
@@ -256,7 +260,9 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     a.ucoef_n = (int64_t)(g->avec.size() / 3);
     a.step0 = step0;
     const int mode = sweep_mode(g);
-    cudaError_t e = g->fp32 ? launch_sweep_f32(a, mode, K, p.P, p.wpb, s) : launch_sweep_f64(a, mode, K, p.P, p.wpb, s);
+    cudaError_t e = mode == 4 ? launch_shift(a, g->fp32, char_shift(g), p.P, p.wpb, s)
+                    : g->fp32 ? launch_sweep_f32(a, mode, K, p.P, p.wpb, s)
+                              : launch_sweep_f64(a, mode, K, p.P, p.wpb, s);
     if (e != cudaSuccess) return cuda_fail(g, e, "sweep kernel launch");
     g->launches++;
     if (ndim_of(g) == 3) {
@@ -372,6 +378,10 @@ void default_plan(dirac_grid *g) {
     const int k = g->cfg.steps_per_launch, pp = g->cfg.points_per_lane;
     if (ndim_of(g) == 3) {
         make_plan(g, 1, pp > 0 ? pp : 2, 4, 16);
+        return;
+    }
+    if (sweep_mode(g) == 4) {
+        make_plan(g, 1, (pp == 1) ? 1 : 2, 4, 8);
         return;
     }
     const int mode = sweep_mode(g);
@@ -505,6 +515,15 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
         return fail(nullptr, DIRAC_ERR_ARG, "splitting must be DIRAC_LIE or DIRAC_STRANG");
     if (cfg->splitting == DIRAC_STRANG && cfg->ndim != 2)
         return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_STRANG is implemented for 2-D grids");
+    if (cfg->char_shift < 0 || cfg->char_shift > 4)
+        return fail(nullptr, DIRAC_ERR_ARG, "char_shift must be 0 (= 1), 1, 2, 3 or 4");
+    if (cfg->char_shift > 1) {
+        if (cfg->ndim != 2 || cfg->splitting != DIRAC_LIE)
+            return fail(nullptr, DIRAC_ERR_ARG, "char_shift > 1 is implemented for 2-D first-order (DIRAC_LIE) grids");
+        if (cfg->steps_per_launch > 1)
+            return fail(nullptr, DIRAC_ERR_ARG, "char_shift > 1 runs one step per launch (steps_per_launch 0 or 1)");
+        if (cfg->points_per_lane == 4) return fail(nullptr, DIRAC_ERR_ARG, "char_shift > 1 needs points_per_lane 0, 1 or 2");
+    }
     const int vmode = cfg->splitting == DIRAC_STRANG ? 2 : 0;
     if (cfg->steps_per_launch != 0 &&
         !(sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, 2) ||
@@ -513,7 +532,7 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->points_per_lane != 0 && cfg->points_per_lane != 1 && cfg->points_per_lane != 2 &&
         cfg->points_per_lane != 4)
         return fail(nullptr, DIRAC_ERR_ARG, "points_per_lane must be 0, 1, 2 or 4");
-    if (cfg->ndim == 2 && cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
+    if (cfg->ndim == 2 && cfg->char_shift <= 1 && cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
         !sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, cfg->points_per_lane))
         return fail(nullptr, DIRAC_ERR_ARG, "unsupported (steps_per_launch, points_per_lane) pair");
     if (std::getenv("DIRAC_INJECT_OOM")) return fail(nullptr, DIRAC_ERR_OOM, "allocation failure injected (DIRAC_INJECT_OOM)");
@@ -526,6 +545,7 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     g->elem = g->fp32 ? 4 : 8;
     g->ncells = cfg->n[0] * cfg->n[1] * cfg->n[2];
     g->dt = (cfg->splitting == DIRAC_STRANG ? 2.0 : 1.0) * cfg->dx / cfg->c;
+    if (cfg->char_shift > 1) g->dt = (double)cfg->char_shift * cfg->dx / cfg->c;
     cudaError_t e = cudaSetDevice(cfg->device);
     if (e != cudaSuccess) {
         std::string msg = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
@@ -629,8 +649,8 @@ dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, in
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
     const bool clear = !A_tilde || nsteps_table == 0;
-    if (!clear && (ndim_of(g) != 2 || strang(g)))
-        return fail(g, DIRAC_ERR_ARG, "a vector potential is implemented for 2-D first-order (DIRAC_LIE) grids");
+    if (!clear && (ndim_of(g) != 2 || strang(g) || char_shift(g) > 1))
+        return fail(g, DIRAC_ERR_ARG, "a vector potential is implemented for 2-D first-order (DIRAC_LIE) grids with char_shift 1");
     if (!clear)
         for (int64_t i = 0; i < 3 * nsteps_table; ++i)
             if (!std::isfinite(A_tilde[i])) return fail(g, DIRAC_ERR_ARG, "vector-potential table holds a non-finite value");
@@ -796,6 +816,9 @@ dirac_status dirac_autotune(dirac_grid *g) {
     if (g->cfg.ndim == 3) {
         for (int P : {1, 2, 4})
             for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm});
+    } else if (sweep_mode(g) == 4) {
+        for (int P : {1, 2})
+            for (int wsm : {4, 8, 12, 16}) cands.push_back({1, P, 4, wsm});
     } else if (sweep_mode(g) == 3) {
         const int KP[][2] = {{1, 1}, {1, 2}, {2, 2}};
         for (auto &kp : KP)

@@ -14,6 +14,7 @@ namespace dirac {
 //                        (x sweep, z sweep, phase), the sweeps' 1/2 factors folded into the
 //                        phase table as 1/4.
 //   mode 3 (2-D step with a uniform vector potential): as mode 0 with the full phase matrix.
+//   mode 4 (2-D step with characteristic shift S > 1): shift_kernels.cuh, one step per launch.
 //   mode 1 (3-D, x-y):   planes = z slices, rows run along y; x sweep then y sweep, no phase,
 //                        output left at 4x the swept state (exact scaling, no rounding).
 // Each warp owns an x strip of `strip_w` cells and a segment of `seg_h` rows of one plane.
@@ -73,6 +74,11 @@ cudaError_t launch_observables(const ObsArgs &a, int fp32, int nblocks, cudaStre
 
 // Instantiated (K, P) pairs of the sweep kernels.
 bool sweep_supported(int fp32, int mode, int K, int P);
+
+// Characteristic-shift step kernel (mode 4: 2-D first-order step with c dt = S dx, one step per launch,
+// strips of 32 P - 2 S owned cells); S in 2..4, P in {1, 2}.
+cudaError_t launch_shift(const SweepArgs &a, int fp32, int S, int P, int warps_per_block, cudaStream_t s);
+bool shift_supported(int S, int P);
 
 // Entries of the U matrix of Sec. 2.3 for mu = m c^2 dt and the field integral At (12 doubles:
 // Dup, Ddn, Ez, -Ez, Ep, Em as (re, im)); A = sqrt(((mu^2 + At_x^2) + At_y^2) + At_z^2), sin(A)/A -> 1 at A = 0.

@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--ndim", type=int, default=2)
     ap.add_argument("--batch-runs", type=int, default=0, help="run this many ensemble runs as one batch instead")
     ap.add_argument("--seg", type=int, default=256, help="batch: rows per task")
+    ap.add_argument("--shift", type=int, default=0, help="2-D: characteristic shift K (c dt = K dx)")
     ap.add_argument("--field", action="store_true",
                     help="2-D: add a uniform two-cycle laser pulse (vector potential) over the run")
     ap.add_argument("--mlp", type=int, default=0,
@@ -92,7 +93,7 @@ def main():
         shape = (args.side, 1, args.side)
         cfg = D.make_config(shape, x_min=(x_min, 0.0, z_min), flux_face=face, precision=prec,
                             stream=stream.cuda_stream, steps_per_launch=args.k, points_per_lane=args.p,
-                            use_graphs=not args.no_graphs)
+                            use_graphs=not args.no_graphs, char_shift=args.shift)
         layout = D.DIRAC_V_X_ONLY
     else:
         n = args.side

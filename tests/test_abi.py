@@ -115,3 +115,15 @@ def test_strang_needs_a_2d_grid(lib):
     with pytest.raises(D.DiracError) as e:
         D.dirac_create_grid(cfg)
     assert e.value.status == D.DIRAC_ERR_ARG
+
+
+def test_char_shift_validation(lib):
+    import paper_1107_4650_gb300 as D
+    for kw in (dict(char_shift=5), dict(char_shift=-1), dict(char_shift=2, ndim=3, n=(8, 8, 8)),
+               dict(char_shift=2, splitting=D.DIRAC_STRANG), dict(char_shift=3, steps_per_launch=2),
+               dict(char_shift=2, points_per_lane=4)):
+        n = kw.pop("n", (16, 1, 16))
+        cfg = D.make_config(n, **kw)
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_create_grid(cfg)
+        assert e.value.status == D.DIRAC_ERR_ARG

@@ -500,3 +500,65 @@ def test_vector_potential_table_end_and_removal(D):
         assert _bits_equal(out, want2)
     finally:
         D.dirac_destroy(h)
+
+
+# ------------------------------------------------------------------ characteristic shift K > 1 (c dt = K dx, Sec. 2.3)
+
+def _run_shift(D, psi, nsteps, S, V=None, periodic=False, fp32=False, P=0, flux_face=-1, graphs=True, x_min=None):
+    nz, ny, nx, _ = psi.shape
+    cfg = D.make_config((nx, ny, nz), precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO, flux_face=flux_face,
+                        points_per_lane=P, use_graphs=graphs, x_min=x_min, char_shift=S)
+    h = D.dirac_create_grid(cfg)
+    try:
+        if V is not None:
+            D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY if V.size == nx else D.DIRAC_V_FULL)
+        dt = np.complex64 if fp32 else np.complex128
+        D.dirac_set_state(h, np.ascontiguousarray(psi.astype(dt)))
+        D.dirac_step(h, nsteps)
+        out = np.empty(psi.shape, dtype=dt)
+        D.dirac_get_state(h, out)
+        obs = D.dirac_observables(h)
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    return out, obs, info
+
+
+@pytest.mark.parametrize("S", [2, 3, 4])
+@pytest.mark.parametrize("P", [1, 2])
+@pytest.mark.parametrize("shape", [(70, 45), (9, 6), (131, 37)])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_shift_fp64_bit_exact(D, S, P, shape, periodic):
+    nx, nz = shape
+    psi = W.random_state(nz, 1, nx, seed=7 * nx + nz + S)
+    V = np.random.default_rng(S).uniform(-2e4, 6e4, nx)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 7, V=V, periodic=periodic, shift=S)
+    got, _, info = _run_shift(D, psi, 7, S, V=V, periodic=periodic, P=P)
+    assert info["points_per_lane"] == P and info["strip_width"] == 32 * P - 2 * S
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("S", [2, 4])
+def test_shift_full_table_flux_graphs(D, S):
+    """Per-cell potential, the face flux (S cells of characteristics each way) and graph replay over 70 steps:
+    bit-exact state, flux within 1e-12 of the oracle, graphs and direct launches identical."""
+    run = W.KleinRun(side=192, V0=2.5 * C * C, p0=0.7 * C, width=8 * DX, nsteps=70, face=110)
+    psi0 = run.state()
+    x_min, z_min, _, _, face = run.geometry()
+    Vfull = np.tile(run.potential(), (192, 1)).reshape(-1) + np.random.default_rng(3).uniform(-1e3, 1e3, 192 * 192)
+    want, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=Vfull, flux_face=face, shift=S)
+    got, obs, _ = _run_shift(D, psi0, run.nsteps, S, V=Vfull, flux_face=face, x_min=(x_min, 0.0, z_min))
+    direct, obs2, _ = _run_shift(D, psi0, run.nsteps, S, V=Vfull, flux_face=face, graphs=False,
+                                 x_min=(x_min, 0.0, z_min))
+    assert _bits_equal(got, want) and _bits_equal(direct, want)
+    assert F > 1e-3 and abs(obs["flux_cum"] - F) <= 1e-12 * abs(F) and obs2["flux_cum"] == obs["flux_cum"]
+
+
+def test_shift_fp32_against_oracle(D):
+    nx, nz = 160, 96
+    psi = W.gaussian_packet(nx, nz, DX, -nx * DX / 2, -nz * DX / 2, 0.0, 0.0, 10 * DX, 0.4 * C)
+    V = np.random.default_rng(5).uniform(-1e4, 1e4, nx)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 60, V=V, periodic=True, shift=3)
+    got, _, _ = _run_shift(D, psi, 60, 3, V=V, periodic=True, fp32=True)
+    assert rel_l2(got.astype(np.complex128), want) < 2e-5
