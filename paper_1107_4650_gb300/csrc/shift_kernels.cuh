@@ -8,8 +8,11 @@
 //   sweep:  u = a + b, w = a - b;  a' = u(-S) + w(+S), b' = u(-S) - w(+S)   (1/2 factors deferred)
 //   phase:  re = fma(z.re, p.re, -(z.im p.im)),  im = fma(z.re, p.im, z.im p.re), p carrying 1/4.
 // The face flux of a row is the +c characteristics of cells face-S..face-1 minus the -c characteristics
-// of cells face..face+S-1 (each 1/2 (|u14|^2 + |u23|^2) or 1/2 (|w14|^2 + |w23|^2)), summed per lane in
-// FP64 by the strip that owns the face, then across the warp.
+// of cells face..face+S-1 (each 1/2 (|u14|^2 + |u23|^2) or 1/2 (|w14|^2 + |w23|^2)), evaluated by the
+// strip that owns the face: each lane holds at most one cell of each range (S < 32), adds its value to a
+// partial in the storage type, and folds the partial into an FP64 sum every 32 rows, so the face warp's
+// extra work stays a few instructions per row (FP64 issues far slower than FP32 on this GPU); the 1/2 is
+// applied once to the warp's sum (exact power-of-two scaling).
 #pragma once
 
 #include "step_kernels.cuh"
@@ -47,6 +50,14 @@ __device__ __forceinline__ void shift_warp(const SweepArgs &a, const int64_t wid
     const int64_t face = a.flux_face;
     const bool has_face = face >= x_own0 && face < x_own1;
     double facc = 0.0;
+    T fpart = T(0);
+    int jr = -1, jl = -1;  // point group of this lane's cell in [face - S, face) and in [face, face + S)
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int64_t x = xa + 32 * j + lane;
+        if (x >= face - S && x < face) jr = j;
+        if (x >= face && x < face + S) jl = j;
+    }
 
     Cx<T> UH[2 * S][P][2];
 #pragma unroll
@@ -95,13 +106,26 @@ __device__ __forceinline__ void shift_warp(const SweepArgs &a, const int64_t wid
                 nw23[j] = shfl_c(w23[j], src_next);
             }
             if (has_face && r >= r_begin && r < r_end) {
+                if (jr >= 0 || jl >= 0) {
+                    Cx<T> ra = {T(0), T(0)}, rb = ra, la = ra, lb = ra;
 #pragma unroll
-                for (int j = 0; j < P; ++j) {
-                    const int64_t x = xa + 32 * j + lane;
-                    if (x >= face - S && x < face)
-                        facc = __dadd_rn(facc, __dmul_rn(0.5, __dadd_rn(abs2d(u14[j]), abs2d(u23[j]))));
-                    if (x >= face && x < face + S)
-                        facc = __dsub_rn(facc, __dmul_rn(0.5, __dadd_rn(abs2d(w14[j]), abs2d(w23[j]))));
+                    for (int j = 0; j < P; ++j) {
+                        if (j == jr) {
+                            ra = u14[j];
+                            rb = u23[j];
+                        }
+                        if (j == jl) {
+                            la = w14[j];
+                            lb = w23[j];
+                        }
+                    }
+                    const T vr = Ar<T>::fma(ra.re, ra.re, Ar<T>::fma(ra.im, ra.im, Ar<T>::fma(rb.re, rb.re, Ar<T>::mul(rb.im, rb.im))));
+                    const T vl = Ar<T>::fma(la.re, la.re, Ar<T>::fma(la.im, la.im, Ar<T>::fma(lb.re, lb.re, Ar<T>::mul(lb.im, lb.im))));
+                    fpart = Ar<T>::add(fpart, Ar<T>::sub(vr, vl));
+                }
+                if (((r - r_begin) & 31) == 31 || r == r_end - 1) {
+                    facc = __dadd_rn(facc, (double)fpart);
+                    fpart = T(0);
                 }
             }
             const int64_t q = r - S;  // output row: rows q - S (ring slot t) and q + S (this row)
@@ -150,7 +174,7 @@ __device__ __forceinline__ void shift_warp(const SweepArgs &a, const int64_t wid
     if (has_face) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) facc = __dadd_rn(facc, __shfl_xor_sync(0xffffffffu, facc, o));
-        if (lane == 0) a.flux_part[seg] = facc;
+        if (lane == 0) a.flux_part[seg] = __dmul_rn(0.5, facc);
     }
 }
 
