@@ -70,22 +70,39 @@ __device__ __forceinline__ void shift_warp(const SweepArgs &a, const int64_t wid
     const int src_prev = (lane + 32 - S) & 31, src_next = (lane + S) & 31;
     const int64_t r_first = r_begin - S, r_last = r_end + S;
 
+    // row r of the state (zero outside the grid under the zero boundary)
+    auto load_row = [&](int64_t r, Cx<T> (*dst)[4]) {
+        const bool row_ok = per || (r >= 0 && r < nr);
+        const int64_t rl = per ? pmod(r, nr) : r;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if (row_ok && (per || xin[j])) {
+                load_pt(in + (rl * nx + xl[j]) * 8, dst[j]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dst[j][c] = {T(0), T(0)};
+            }
+        }
+    };
+    // FP32 storage is bandwidth-bound: the next row's loads are issued before this row's arithmetic
+    constexpr bool PREFETCH = sizeof(T) == 4;
+    Cx<T> nxt[PREFETCH ? P : 1][4];
+    if (PREFETCH) load_row(r_first, nxt);
+
     for (int64_t r0 = r_first; r0 < r_last; r0 += 2 * S) {
 #pragma unroll
         for (int t = 0; t < 2 * S; ++t) {
             const int64_t r = r0 + t;
             if (r >= r_last) break;
             Cx<T> st[P][4];
-            const bool row_ok = per || (r >= 0 && r < nr);
-            const int64_t rl = per ? pmod(r, nr) : r;
+            if (PREFETCH) {
 #pragma unroll
-            for (int j = 0; j < P; ++j) {
-                if (row_ok && (per || xin[j])) {
-                    load_pt(in + (rl * nx + xl[j]) * 8, st[j]);
-                } else {
+                for (int j = 0; j < P; ++j)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) st[j][c] = {T(0), T(0)};
-                }
+                    for (int c = 0; c < 4; ++c) st[j][c] = nxt[PREFETCH ? j : 0][c];
+                if (r + 1 < r_last) load_row(r + 1, nxt);
+            } else {
+                load_row(r, st);
             }
             // x characteristics; u of cell x - S and w of cell x + S by shuffle (lanes < S take the previous
             // point group, lanes >= 32 - S the next one)
