@@ -27,6 +27,9 @@ struct Plan {
     int64_t strip_w = 0, nstrips = 0, nsegs = 0, seg_h = 0;
     int z_threads = 128;
     int64_t z_nsegs = 1, z_seg_h = 0;
+    // 3-D: fused single-pass step (fused3d_kernels.cuh) instead of the x-y pass + z/phase pass
+    int fused3d = 0, f_warps = 16;
+    int64_t f_nstrips = 0, f_nytiles = 0, f_nzsegs = 0, f_zseg_h = 0;
 };
 
 }  // namespace
@@ -208,6 +211,14 @@ void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
         zs = std::min<int64_t>(zs, std::max<int64_t>(1, nz / 32));
         p.z_seg_h = (nz + zs - 1) / zs;
         p.z_nsegs = (nz + p.z_seg_h - 1) / p.z_seg_h;
+        // fused pass: 30-cell strips x (warps - 2)-row tiles, z segments until ~8 blocks per SM have work
+        p.f_nstrips = (g->cfg.n[0] + 29) / 30;
+        p.f_nytiles = (g->cfg.n[1] + (p.f_warps - 2) - 1) / (p.f_warps - 2);
+        const int64_t tiles = p.f_nstrips * p.f_nytiles;
+        int64_t fz = std::max<int64_t>(1, (8 * (int64_t)g->sm_count + tiles - 1) / tiles);
+        fz = std::min<int64_t>(fz, std::max<int64_t>(1, nz / 16));
+        p.f_zseg_h = (nz + fz - 1) / fz;
+        p.f_nzsegs = (nz + p.f_zseg_h - 1) / p.f_zseg_h;
     }
     for (auto &x : g->graph)
         if (x) {
@@ -218,7 +229,9 @@ void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
 
 dirac_status ensure_flux_part(dirac_grid *g) {
     const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
-    const size_t need = (size_t)8 * planes * std::max<int64_t>(g->plan.nsegs, 1);
+    size_t need = (size_t)8 * planes * std::max<int64_t>(g->plan.nsegs, 1);
+    if (ndim_of(g) == 3 && g->plan.fused3d)
+        need = std::max(need, (size_t)(g->plan.f_nzsegs * g->plan.f_nytiles * g->plan.f_warps));
     if (need <= g->flux_part_cap) return DIRAC_OK;
     if (g->flux_part) {
         cudaFree(g->flux_part);
@@ -260,6 +273,15 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     a.ucoef_n = (int64_t)(g->avec.size() / 3);
     a.step0 = step0;
     const int mode = sweep_mode(g);
+    if (mode == 1 && p.fused3d) {
+        a.nsegs = p.f_nzsegs * p.f_nytiles * p.f_warps;  // flux parts of the fused pass
+        a.nplanes = 1;
+        cudaError_t e = launch_fused3d(a, g->fp32, p.f_warps, g->cfg.n[1], g->cfg.n[2], p.f_nstrips, p.f_nytiles,
+                                       p.f_nzsegs, p.f_zseg_h, s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "fused 3-D step launch");
+        g->launches++;
+        return DIRAC_OK;
+    }
     cudaError_t e = mode == 4 ? launch_shift(a, g->fp32, char_shift(g), p.P, p.wpb, s)
                     : g->fp32 ? launch_sweep_f32(a, mode, K, p.P, p.wpb, s)
                               : launch_sweep_f64(a, mode, K, p.P, p.wpb, s);
@@ -284,7 +306,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     return DIRAC_OK;
 }
 
-int block_flips(const dirac_grid *g) { return ndim_of(g) == 3 ? 0 : 1; }
+int block_flips(const dirac_grid *g) { return (ndim_of(g) == 3 && !g->plan.fused3d) ? 0 : 1; }
 
 dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
     if (g->graph[parity]) {
@@ -316,7 +338,7 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
     return DIRAC_OK;
 }
 
-int64_t launches_per_block(const dirac_grid *g) { return 1 + (ndim_of(g) == 3 ? 1 : 0); }
+int64_t launches_per_block(const dirac_grid *g) { return 1 + ((ndim_of(g) == 3 && !g->plan.fused3d) ? 1 : 0); }
 
 dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
     const int K = (ndim_of(g) == 3) ? 1 : g->plan.K;
@@ -377,6 +399,9 @@ void release(dirac_grid *g) {
 void default_plan(dirac_grid *g) {
     const int k = g->cfg.steps_per_launch, pp = g->cfg.points_per_lane;
     if (ndim_of(g) == 3) {
+        // points_per_lane 0: the fused single-pass step; 1, 2 or 4: the x-y pass + z/phase pass with that P
+        g->plan.fused3d = pp > 0 ? 0 : 1;
+        g->plan.f_warps = g->cfg.n[1] <= 12 ? 8 : 16;  // short y extents: 6-row tiles waste fewer halo rows
         make_plan(g, 1, pp > 0 ? pp : 2, 4, 16);
         return;
     }
@@ -800,6 +825,12 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
     info->launch_warps = p.nstrips * p.nsegs * planes;
     info->strip_width = p.strip_w;
     info->segment_rows = p.seg_h;
+    if (g->cfg.ndim == 3 && p.fused3d) {
+        info->points_per_lane = 1;
+        info->launch_warps = p.f_nstrips * p.f_nytiles * p.f_nzsegs * p.f_warps;
+        info->strip_width = 30;
+        info->segment_rows = p.f_zseg_h;
+    }
     info->graphs = g->cfg.use_graphs;
     info->kernel_launches = g->launches;
     info->device_bytes = g->device_bytes;
@@ -811,11 +842,13 @@ dirac_status dirac_autotune(dirac_grid *g) {
     CK(g, cudaSetDevice(g->cfg.device));
     struct Cand {
         int K, P, wpb, wsm;
+        int fused = 0;  // 3-D: warps per block of the fused pass (0: two-pass path)
     };
     std::vector<Cand> cands;
     if (g->cfg.ndim == 3) {
         for (int P : {1, 2, 4})
-            for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm});
+            for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});
+        for (int fw : {8, 16}) cands.push_back({1, 2, 4, 16, fw});
     } else if (sweep_mode(g) == 4) {
         for (int P : {1, 2})
             for (int wsm : {4, 8, 12, 16}) cands.push_back({1, P, 4, wsm});
@@ -852,13 +885,15 @@ dirac_status dirac_autotune(dirac_grid *g) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    Cand best = {g->plan.K, g->plan.P, g->plan.wpb, 0};
+    Cand best = {g->plan.K, g->plan.P, g->plan.wpb, 0, g->plan.fused3d ? g->plan.f_warps : 0};
     double best_t = 1e300;
     const int use_graphs = g->cfg.use_graphs;
     g->cfg.use_graphs = 0;
     g->tuning = true;
     dirac_status st = DIRAC_OK;
     for (const Cand &c : cands) {
+        g->plan.fused3d = c.fused ? 1 : 0;
+        if (c.fused) g->plan.f_warps = c.fused;
         make_plan(g, c.K, c.P, c.wpb, c.wsm);
         st = ensure_flux_part(g);
         if (st != DIRAC_OK) break;
@@ -883,6 +918,8 @@ dirac_status dirac_autotune(dirac_grid *g) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st == DIRAC_OK) {
+        g->plan.fused3d = best.fused ? 1 : 0;
+        if (best.fused) g->plan.f_warps = best.fused;
         make_plan(g, best.K, best.P, best.wpb, best.wsm ? best.wsm : 8);
         st = ensure_flux_part(g);
     }

@@ -80,6 +80,12 @@ bool sweep_supported(int fp32, int mode, int K, int P);
 cudaError_t launch_shift(const SweepArgs &a, int fp32, int S, int P, int warps_per_block, cudaStream_t s);
 bool shift_supported(int S, int P);
 
+// Fused 3-D step (x, y, z sweeps and phase in one pass, one step per launch): blocks of `warps` (8 or 16)
+// warps own a 30-cell x strip and warps - 2 rows along y and stream a z segment of zseg_h planes.  Flux
+// parts: nzsegs * nytiles * warps (a.nsegs * a.nplanes must equal that).
+cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
+                           int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s);
+
 // Entries of the U matrix of Sec. 2.3 for mu = m c^2 dt and the field integral At (12 doubles:
 // Dup, Ddn, Ez, -Ez, Ep, Em as (re, im)); A = sqrt(((mu^2 + At_x^2) + At_y^2) + At_z^2), sin(A)/A -> 1 at A = 0.
 void u_entries(double mu, const double At[3], double out[12]);

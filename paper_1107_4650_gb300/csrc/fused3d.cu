@@ -1,0 +1,21 @@
+// Instantiations of the fused 3-D step kernel (8 or 16 warps per block: 6 or 14 owned rows per tile).
+#include "fused3d_kernels.cuh"
+
+namespace dirac {
+
+cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
+                           int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s) {
+    Fused3DArgs A{};
+    A.s = a;
+    A.ny = ny;
+    A.nz = nz;
+    A.nstrips = nstrips;
+    A.nytiles = nytiles;
+    A.nzsegs = nzsegs;
+    A.zseg_h = zseg_h;
+    if (warps == 16) return fp32 ? launch_fused3d_one<float, 16>(A, s) : launch_fused3d_one<double, 16>(A, s);
+    if (warps == 8) return fp32 ? launch_fused3d_one<float, 8>(A, s) : launch_fused3d_one<double, 8>(A, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dirac

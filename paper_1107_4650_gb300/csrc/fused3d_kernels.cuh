@@ -1,0 +1,165 @@
+// Fused 3-D first-order step: x sweep, y sweep, z sweep and phase (Eqs. sol_dis_1-sol_dis_4) in one pass
+// over HBM, one step per launch.
+//
+// A block of W warps owns an x strip of 30 cells (one halo cell each side, lane l holds cell xa + l) and
+// a tile of W - 2 rows along y; warp w handles row y0 - 1 + w, so warps 0 and W-1 carry the y halo rows.
+// The block streams the planes of its z segment (plus one halo plane each side):
+//   * each warp loads its row of the plane, x-sweeps it with warp shuffles and writes the row's y
+//     characteristics (U = "+y" movers, W = "-y" movers) to shared memory (double-buffered by plane);
+//   * after one block barrier the owned warps y-sweep their row from the rows above and below;
+//   * the z sweep keeps the "+z" sums of the two previous planes per cell in registers (output plane
+//     k - 1 = U(k - 2) + W(k)), then the phase with the table pre-scaled by 1/8, and the store.
+// Arithmetic order is that of the two-kernel 3-D path (x-y pass at 4x scale, then z sweep and phase), so
+// the FP64 result is the same bit for bit.  Face flux: the lanes holding cells face-1 and face of owned
+// rows and planes add 1/2 (|u14|^2+|u23|^2) and subtract 1/2 (|w14|^2+|w23|^2) of the state entering the x
+// sweep, to a storage-type partial folded into FP64 every 32 planes.
+#pragma once
+
+#include "step_kernels.cuh"
+
+namespace dirac {
+
+struct Fused3DArgs {
+    SweepArgs s;          // in, out, table, flux fields; s.nsegs * s.nplanes = flux parts
+    int64_t ny, nz;
+    int64_t nstrips, nytiles, nzsegs, zseg_h;
+};
+
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A) {
+    constexpr int H = W - 2;
+    const SweepArgs &a = A.s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t b = blockIdx.x;
+    const int64_t strip = b % A.nstrips;
+    const int64_t rest = b / A.nstrips;
+    const int64_t ytile = rest % A.nytiles;
+    const int64_t zseg = rest / A.nytiles;
+    const int64_t nx = a.nx, ny = A.ny, nz = A.nz;
+    const bool per = a.periodic != 0;
+    const int64_t x_own0 = strip * 30, x_own1 = min(x_own0 + 30, nx);
+    const int64_t x = x_own0 - 1 + lane;
+    const int64_t y = ytile * H - 1 + w;
+    const bool owned_row = w >= 1 && w <= H && y < ny;
+    const int64_t z_begin = zseg * A.zseg_h, z_end = min(z_begin + A.zseg_h, nz);
+    const bool xin = x >= 0 && x < nx, yin = y >= 0 && y < ny;
+    const int64_t xl = per ? pmod(x, nx) : min(max(x, (int64_t)0), nx - 1);
+    const int64_t yl = per ? pmod(y, ny) : min(max(y, (int64_t)0), ny - 1);
+    const T *in = static_cast<const T *>(a.in);
+    T *out = static_cast<T *>(a.out);
+    const T *tab = static_cast<const T *>(a.table);
+
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    Cx<T> *ych = reinterpret_cast<Cx<T> *>(dyn_smem);  // [2][W][4][32]
+
+    Cx<T> pu, pd;
+    if (!a.full_table) load_tab(tab + xl * 4, pu, pd);
+    const int64_t face = a.flux_face;
+    const bool face_lane = owned_row && face >= x_own0 && face < x_own1 && (x == face - 1 || x == face);
+    double facc = 0.0;
+    T fpart = T(0);
+
+    Cx<T> UA[2] = {{T(0), T(0)}, {T(0), T(0)}}, UB[2] = {{T(0), T(0)}, {T(0), T(0)}};
+
+    auto load_row = [&](int64_t k, Cx<T> s[4]) {
+        const bool ok = per || (yin && k >= 0 && k < nz && xin);
+        if (ok) {
+            const int64_t kl = per ? pmod(k, nz) : k;
+            load_pt(in + ((kl * ny + yl) * nx + xl) * 8, s);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s[c] = {T(0), T(0)};
+        }
+    };
+    Cx<T> nxt[4];
+    load_row(z_begin - 1, nxt);
+
+    for (int64_t k = z_begin - 1; k <= z_end; ++k) {
+        Cx<T> st[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) st[c] = nxt[c];
+        if (k + 1 <= z_end) load_row(k + 1, nxt);
+        // x characteristics and the x sweep (neighbours by shuffle; lanes 0 and 31 are halo cells)
+        const Cx<T> u14 = cadd(st[0], st[3]), w14 = csub(st[0], st[3]);
+        const Cx<T> u23 = cadd(st[1], st[2]), w23 = csub(st[1], st[2]);
+        if (face_lane && k >= z_begin && k < z_end) {
+            const T v = (x == face - 1)
+                            ? Ar<T>::fma(u14.re, u14.re, Ar<T>::fma(u14.im, u14.im, Ar<T>::fma(u23.re, u23.re, Ar<T>::mul(u23.im, u23.im))))
+                            : -Ar<T>::fma(w14.re, w14.re, Ar<T>::fma(w14.im, w14.im, Ar<T>::fma(w23.re, w23.re, Ar<T>::mul(w23.im, w23.im))));
+            fpart = Ar<T>::add(fpart, v);
+            if (((k - z_begin) & 31) == 31 || k == z_end - 1) {
+                facc = __dadd_rn(facc, (double)fpart);
+                fpart = T(0);
+            }
+        }
+        const Cx<T> lu14 = shfl_c(u14, (lane + 31) & 31), lu23 = shfl_c(u23, (lane + 31) & 31);
+        const Cx<T> rw14 = shfl_c(w14, (lane + 1) & 31), rw23 = shfl_c(w23, (lane + 1) & 31);
+        const Cx<T> b0 = cadd(lu14, rw14), b3 = csub(lu14, rw14);
+        const Cx<T> b1 = cadd(lu23, rw23), b2 = csub(lu23, rw23);
+        // y characteristics (Eq. sol_dis_2): "+y" movers (b1 - i b4, b2 + i b3), "-y" movers (b1 + i b4, b2 - i b3)
+        Cx<T> *buf = ych + (size_t)((k - z_begin + 1) & 1) * (W * 4 * 32);
+        buf[(w * 4 + 0) * 32 + lane] = csub_ib(b0, b3);
+        buf[(w * 4 + 1) * 32 + lane] = cadd_ib(b1, b2);
+        buf[(w * 4 + 2) * 32 + lane] = cadd_ib(b0, b3);
+        buf[(w * 4 + 3) * 32 + lane] = csub_ib(b1, b2);
+        __syncthreads();
+        if (owned_row) {
+            // y sweep of row y: "+y" movers of row y-1, "-y" movers of row y+1 (x2 again: 4x the state)
+            const Cx<T> U14 = buf[((w - 1) * 4 + 0) * 32 + lane], U23 = buf[((w - 1) * 4 + 1) * 32 + lane];
+            const Cx<T> W14 = buf[((w + 1) * 4 + 2) * 32 + lane], W23 = buf[((w + 1) * 4 + 3) * 32 + lane];
+            Cx<T> s[4];
+            s[0] = cadd(U14, W14);
+            s[3] = cmul_i(csub(U14, W14));
+            s[1] = cadd(U23, W23);
+            s[2] = cmul_mi(csub(U23, W23));
+            // z sweep (Eq. sol_dis_3): +z movers (s1+s3, s2-s4) of plane k-2, -z movers (s1-s3, s2+s4) of plane k
+            const Cx<T> U13 = cadd(s[0], s[2]), U24 = csub(s[1], s[3]);
+            const Cx<T> W13 = csub(s[0], s[2]), W24 = cadd(s[1], s[3]);
+            const int64_t zo = k - 1;
+            if (zo >= z_begin && zo < z_end) {
+                Cx<T> o[4];
+                o[0] = cadd(UA[0], W13);
+                o[2] = csub(UA[0], W13);
+                o[1] = cadd(UA[1], W24);
+                o[3] = csub(W24, UA[1]);
+                Cx<T> qu = pu, qd = pd;
+                if (a.full_table) load_tab(tab + ((zo * ny + y) * nx + xl) * 4, qu, qd);
+                o[0] = cmulp(o[0], qu);
+                o[1] = cmulp(o[1], qu);
+                o[2] = cmulp(o[2], qd);
+                o[3] = cmulp(o[3], qd);
+                if (x >= x_own0 && x < x_own1) store_pt(out + ((zo * ny + y) * nx + x) * 8, o);
+            }
+            UA[0] = UB[0];
+            UA[1] = UB[1];
+            UB[0] = U13;
+            UB[1] = U24;
+        }
+    }
+    if (face >= 0 && face >= x_own0 && face < x_own1) {
+        // one flux part per (y tile, z segment, warp) of the strip that owns the face; halo warps write 0
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) facc = __dadd_rn(facc, __shfl_xor_sync(0xffffffffu, facc, o));
+        if (lane == 0) a.flux_part[(zseg * A.nytiles + ytile) * W + w] = __dmul_rn(0.5, facc);
+    }
+    if (face >= 0) finish_flux<1>(a);
+}
+
+template <typename T, int W>
+static cudaError_t launch_fused3d_one(const Fused3DArgs &A, cudaStream_t s) {
+    const int64_t blocks = A.nstrips * A.nytiles * A.nzsegs;
+    if (blocks <= 0) return cudaSuccess;
+    const int smem = 2 * W * 4 * 32 * (int)sizeof(Cx<T>);
+    static unsigned long long done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !(done & (1ull << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(fused3d_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) done |= 1ull << dev;
+    }
+    fused3d_kernel<T, W><<<(unsigned)blocks, 32 * W, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace dirac

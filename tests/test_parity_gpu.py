@@ -123,10 +123,12 @@ def test_cropped_klein_512_4000_steps(D):
 
 # ------------------------------------------------------------------ 3-D FP64, bit-exact
 
-@pytest.mark.parametrize("shape", [(40, 36, 33), (7, 5, 6), (70, 9, 12)])
+@pytest.mark.parametrize("shape", [(40, 36, 33), (7, 5, 6), (70, 9, 12), (95, 31, 40)])
 @pytest.mark.parametrize("periodic", [False, True])
-@pytest.mark.parametrize("P", [1, 2, 4])
+@pytest.mark.parametrize("P", [0, 1, 2, 4])
 def test_3d_fp64_bit_exact_coulomb(D, shape, periodic, P):
+    """P = 0 runs the fused single-pass 3-D step (16-warp tiles, or 8 for ny <= 12), P = 1, 2, 4 the x-y pass
+    plus the z/phase pass."""
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx + ny + nz)
     x = W.cell_centres(nx, DX, -nx * DX / 2)
@@ -135,18 +137,42 @@ def test_3d_fp64_bit_exact_coulomb(D, shape, periodic, P):
     r2 = x[None, None, :] ** 2 + y[None, :, None] ** 2 + z[:, None, None] ** 2
     V = (-10.0 / np.sqrt(r2 + (2 * DX) ** 2)).reshape(-1)
     want, _ = oracle.step(psi, 3, 1.0, C, DX, 4, V=V, periodic=periodic)
-    got, _, _ = run_gpu(D, psi, 3, 4, V=V, periodic=periodic, P=P)
+    got, _, info = run_gpu(D, psi, 3, 4, V=V, periodic=periodic, P=P)
+    assert info["strip_width"] == (30 if P == 0 else 32 * P - 2)
     assert _bits_equal(got, want), rel_l2(got, want)
 
 
-def test_3d_flux_and_x_only_table(D):
+@pytest.mark.parametrize("P", [0, 2])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_3d_flux_and_x_only_table(D, P, graphs):
     nx, ny, nz = 48, 20, 24
     psi = W.random_state(nz, ny, nx, seed=44)
     V = np.random.default_rng(5).uniform(0, 5e4, nx)
-    want, F = oracle.step(psi, 3, 1.0, C, DX, 5, V=V, flux_face=20)
-    got, obs, _ = run_gpu(D, psi, 3, 5, V=V, flux_face=20)
+    want, F = oracle.step(psi, 3, 1.0, C, DX, 37, V=V, flux_face=20)
+    got, obs, _ = run_gpu(D, psi, 3, 37, V=V, flux_face=20, P=P, graphs=graphs)
     assert _bits_equal(got, want)
     assert abs(obs["flux_cum"] - F) <= 1e-12 * max(abs(F), 1e-300) + 1e-300
+
+
+def test_3d_fused_autotune_keeps_state(D):
+    """Autotune over the two-pass and fused 3-D candidates restores the state; the result after it is
+    bit-exact whichever plan it picks."""
+    nx, ny, nz = 64, 40, 36
+    psi = W.random_state(nz, ny, nx, seed=45)
+    V = np.random.default_rng(6).uniform(-4e4, 4e4, nx * ny * nz)
+    want, _ = oracle.step(psi, 3, 1.0, C, DX, 6, V=V)
+    cfg = D.make_config((nx, ny, nz), ndim=3)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+        D.dirac_set_state(h, psi)
+        D.dirac_autotune(h)
+        D.dirac_step(h, 6)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want)
 
 
 # ------------------------------------------------------------------ FP32 storage
