@@ -55,8 +55,9 @@ def _load():
         lib.oracle_observables.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, D3, ctypes.c_int64, P]
         lib.oracle_step_strang2d.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
+        lib.oracle_step_strang3d.argtypes = lib.oracle_step_strang2d.argtypes
         for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables,
-                  lib.oracle_step_strang2d):
+                  lib.oracle_step_strang2d, lib.oracle_step_strang3d):
             f.restype = ctypes.c_int
         lib.oracle_set_absorber.argtypes = [P]
         lib.oracle_set_absorber.restype = None
@@ -202,6 +203,23 @@ def step_strang2d(psi, m: float, c: float, dx: float, nsteps: int, V=None, perio
                                           int(flux_face), ctypes.addressof(fc))
     if rc != 0:
         raise MemoryError("oracle_step_strang2d")
+    return out, fc.value
+
+
+def step_strang3d(psi, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False,
+                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1):
+    """nsteps second-order (Strang) steps in 3-D (Sec. 2.4): A(dt/4) B(dt/2) A(dt/4) C(dt/2) D(dt) C(dt/2)
+    A(dt/4) B(dt/2) A(dt/4) with c dt / 4 = shift * dx: x sweeps move `shift` cells, y and z sweeps 2 shift.
+    Returns (psi_out, flux_cum) as step()."""
+    out = _as_state(psi)
+    Varr, layout = _potential(V, out)
+    fc = ctypes.c_double(flux_cum)
+    with _Shift(shift):
+        rc = _load().oracle_step_strang3d(out.ctypes.data, _dims(out), int(bool(periodic)), float(m), float(c),
+                                          float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
+                                          int(flux_face), ctypes.addressof(fc))
+    if rc != 0:
+        raise MemoryError("oracle_step_strang3d")
     return out, fc.value
 
 

@@ -101,14 +101,14 @@ static int64_t g_shift = 1;
 
 void oracle_set_shift(int64_t K) { g_shift = K >= 1 ? K : 1; }
 
-/* Sweep along `axis` (0 = x, 1 = y, 2 = z) of the whole grid, in place. */
-int oracle_sweep(double *psi_d, const int64_t n[3], int axis, int periodic) {
+/* Sweep along `axis` (0 = x, 1 = y, 2 = z) of the whole grid, in place, with neighbours `shift` cells away. */
+static int sweep_shift(double *psi_d, const int64_t n[3], int axis, int periodic, int64_t shift) {
     cplx *psi = (cplx *)psi_d;
     int64_t total = n[0] * n[1] * n[2];
     cplx *out = (cplx *)malloc((size_t)total * 4 * sizeof(cplx));
     if (!out) return -1;
     int64_t d[3] = {0, 0, 0};
-    d[axis] = g_shift;
+    d[axis] = shift;
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n[2]; ++k)
         for (int64_t j = 0; j < n[1]; ++j)
@@ -120,6 +120,11 @@ int oracle_sweep(double *psi_d, const int64_t n[3], int axis, int periodic) {
     memcpy(psi, out, (size_t)total * 4 * sizeof(cplx));
     free(out);
     return 0;
+}
+
+/* Sweep along `axis` with the characteristic shift set by oracle_set_shift. */
+int oracle_sweep(double *psi_d, const int64_t n[3], int axis, int periodic) {
+    return sweep_shift(psi_d, n, axis, periodic, g_shift);
 }
 
 /* Potential energy at cell (i,j,k): layout 0 = none (V = 0), 1 = one value per
@@ -311,6 +316,30 @@ int oracle_step_strang2d(double *psi, const int64_t n[3], int periodic, double m
         if (oracle_sweep(psi, n, 2, periodic)) return -1;
         if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
         if (oracle_sweep(psi, n, 0, periodic)) return -1;
+    }
+    return 0;
+}
+
+/* nsteps steps of the second-order splitting of Sec. 2.4 in 3-D: A(dt/4) B(dt/2) A(dt/4) C(dt/2) D(dt)
+ * C(dt/2) A(dt/4) B(dt/2) A(dt/4).  With c dt/4 = K dx (K = the characteristic shift) each A sweep moves
+ * the characteristics by K cells and each B and C sweep by 2K cells, so dt = 4 K dx / c.  The face flux is
+ * added at each of the four x sweeps of a step (shift K). */
+int oracle_step_strang3d(double *psi, const int64_t n[3], int periodic, double m, double c, double dx,
+                         const double *V, int layout, int64_t nsteps, int64_t flux_face, double *flux_cum) {
+    const double dt = 4.0 * (double)g_shift * dx / c;
+    const double vol = dx * dx * dx;
+    const int axes[9] = {0, 1, 0, 2, -1, 2, 0, 1, 0};
+    for (int64_t s = 0; s < nsteps; ++s) {
+        for (int q = 0; q < 9; ++q) {
+            const int ax = axes[q];
+            if (ax < 0) {
+                oracle_phase(psi, n, m, c, dt, V, layout);
+                continue;
+            }
+            if (ax == 0 && flux_face >= 0 && flux_cum)
+                *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
+            if (sweep_shift(psi, n, ax, periodic, ax == 0 ? g_shift : 2 * g_shift)) return -1;
+        }
     }
     return 0;
 }

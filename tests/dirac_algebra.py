@@ -138,3 +138,21 @@ def dft_exact_evolution_2d_A(psi0: np.ndarray, mu: float, At_steps, m_c2_dt=None
         UA = expm(-1j * mu * BETA + 1j * sum(a * M for a, M in zip(At, ALPHA)))
         hat = np.einsum("ab,zxbc,zxc->zxa", UA, S, hat)
     return np.fft.ifft2(hat, axes=(0, 1))[:, None]
+
+
+def continuum_evolution_3d(psi0: np.ndarray, dx: float, t: float, m: float, c: float) -> np.ndarray:
+    """Exact free evolution e^{-i (c alpha.p + beta m c^2) t} in Fourier space on the periodic 3-D grid
+    (psi0 shape (nz, ny, nx, 4))."""
+    nz, ny, nx, _ = psi0.shape
+    px = 2 * np.pi * np.fft.fftfreq(nx, d=dx)
+    py = 2 * np.pi * np.fft.fftfreq(ny, d=dx)
+    pz = 2 * np.pi * np.fft.fftfreq(nz, d=dx)
+    PZ, PY, PX = np.meshgrid(pz, py, px, indexing="ij")
+    E = np.sqrt((c * PX) ** 2 + (c * PY) ** 2 + (c * PZ) ** 2 + (m * c * c) ** 2)
+    H = c * (PX[..., None, None] * ALPHA[0] + PY[..., None, None] * ALPHA[1] + PZ[..., None, None] * ALPHA[2]) \
+        + m * c * c * BETA
+    sinE = np.where(E > 0, np.sin(E * t) / np.where(E > 0, E, 1.0), t)
+    U = np.cos(E * t)[..., None, None] * I4 - 1j * sinE[..., None, None] * H
+    hat = np.fft.fftn(psi0, axes=(0, 1, 2))
+    hat = np.einsum("zyxab,zyxb->zyxa", U, hat)
+    return np.fft.ifftn(hat, axes=(0, 1, 2))

@@ -37,6 +37,8 @@ MUTANTS = {
     "shift_ignored_in_sweep": ("d[axis] = g_shift;", "d[axis] = 1;"),
     "shift_flux_window": ("for (int64_t i = face - g_shift; i < face; ++i) {", "for (int64_t i = face - 1; i < face; ++i) {"),
     "shift_time_step": ("double dt = (double)g_shift * dx / c;", "double dt = dx / c;"),
+    "strang3d_order": ("const int axes[9] = {0, 1, 0, 2, -1, 2, 0, 1, 0};", "const int axes[9] = {1, 0, 0, 2, -1, 2, 0, 1, 0};"),
+    "strang3d_half_step_shift": ("ax == 0 ? g_shift : 2 * g_shift", "ax == 0 ? g_shift : g_shift"),
     "A_row_order": ("acc = c_mac(acc, q[b], c_mul(U[a][b], g));", "acc = c_mac(acc, q[b], c_mul(U[b][a], g));"),
 }
 
@@ -58,6 +60,8 @@ def _build_mutant(tmp_path, name, old, new):
     lib.oracle_set_absorber.restype = None
     lib.oracle_set_vector_potential.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
     lib.oracle_set_vector_potential.restype = None
+    lib.oracle_step_strang3d.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
     lib.oracle_set_shift.argtypes = [ctypes.c_int64]
     lib.oracle_set_shift.restype = None
     return lib
@@ -113,6 +117,15 @@ def _pins_pass():
     out, F = oracle.step(psi0, 2, 1.0, C, DX, run.nsteps, V=run.potential(), flux_face=face, shift=3)
     o1 = oracle.observables(out, 2, DX, (x_min, 0.0, z_min), face)
     ok &= abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
+    # 3-D Strang step against its explicit matrix product
+    shape = (5, 4, 6)
+    psi = W.random_state(6, 4, 5, seed=96)
+    Vc = np.random.default_rng(97).uniform(-3e4, 3e4, 120)
+    got, _ = oracle.step_strang3d(psi, 1.0, C, DX, 1, V=Vc, periodic=True)
+    Ax, By, Cz = (A.sweep_matrix(shape, 0, True), A.sweep_matrix(shape, 1, True, shift=2),
+                  A.sweep_matrix(shape, 2, True, shift=2))
+    want = Ax @ By @ Ax @ Cz @ A.phase_matrix(shape, 1.0, C, 4 * DX / C, Vc) @ Cz @ Ax @ By @ Ax @ psi.reshape(-1)
+    ok &= np.max(np.abs(got.reshape(-1) - want)) < 5e-15
     return bool(ok)
 
 

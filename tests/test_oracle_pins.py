@@ -576,3 +576,67 @@ def test_shift_flux_identity(oracle_mod):
     o1 = oracle.observables(out, 2, run.dx, (x_min, 0.0, z_min), face)
     assert F > 1e-3
     assert abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
+
+
+# ---------------------------------------------------------------- Strang (second-order) splitting, 3-D
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("K", [1, 2])
+def test_strang3d_step_equals_matrix_product(oracle_mod, periodic, K):
+    """One 3-D Strang step (Sec. 2.4) = A B A C D C A B A with A moving K cells and B, C 2K cells
+    (c dt / 4 = K dx), D over dt = 4 K dx / c, as explicit matrices."""
+    shape = (7, 5, 6)
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=51 + K)
+    V = np.random.default_rng(52).uniform(-3e4, 3e4, nx * ny * nz)
+    got, _ = oracle.step_strang3d(psi, M, C, W.DX_DEFAULT, 1, V=V, periodic=periodic, shift=K)
+    Ax = A.sweep_matrix(shape, 0, periodic, shift=K)
+    By = A.sweep_matrix(shape, 1, periodic, shift=2 * K)
+    Cz = A.sweep_matrix(shape, 2, periodic, shift=2 * K)
+    Dm = A.phase_matrix(shape, M, C, 4 * K * W.DX_DEFAULT / C, V)
+    want = Ax @ By @ Ax @ Cz @ Dm @ Cz @ Ax @ By @ Ax @ psi.reshape(-1)
+    assert np.max(np.abs(got.reshape(-1) - want)) < 5e-15
+
+
+def test_strang3d_second_order_convergence_to_continuum(oracle_mod):
+    """3-D Strang steps are second order: halving dx (dt = 4 dx / c) at a fixed physical time divides the
+    error against the exact free evolution by about 4; the first-order 3-D scheme only halves it."""
+    box = 16 * W.DX_DEFAULT
+    errs, errs_lie = [], []
+    for n in (32, 64):
+        dx = box / n
+        nsteps = n // 8
+        t = nsteps * 4 * dx / C
+        x = (np.arange(n) - n // 2) * dx
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        psi0 = np.zeros((n, n, n, 4), complex)
+        env = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (4 * (box / 10) ** 2))
+        psi0[..., 0] = env * np.exp(1j * 0.5 * M * C * X)
+        psi0[..., 3] = 0.2 * env * np.exp(1j * 0.5 * M * C * X)
+        exact = A.continuum_evolution_3d(psi0, dx, t, M, C)
+        got, _ = oracle.step_strang3d(psi0, M, C, dx, nsteps, periodic=True)
+        errs.append(A.rel_l2(got, exact))
+        lie, _ = oracle.step(psi0, 3, M, C, dx, 4 * nsteps, periodic=True)
+        errs_lie.append(A.rel_l2(lie, exact))
+    assert 3.2 < errs[0] / errs[1] < 4.8, errs
+    assert 1.6 < errs_lie[0] / errs_lie[1] < 2.4, errs_lie
+    assert errs[1] < errs_lie[1]
+
+
+def test_strang3d_flux_identity(oracle_mod):
+    """The probability counted across the face at the four x sweeps of each step equals the change of the
+    norm right of it (periodic y and z, the packet far from the x ends for the 20-cell light cone)."""
+    nx, ny, nz = 160, 12, 10
+    dx = W.DX_DEFAULT
+    x = W.cell_centres(nx, dx, -80 * dx)
+    psi0 = np.zeros((nz, ny, nx, 4), complex)
+    env = np.exp(-((x + 12 * dx) ** 2) / (4 * (4 * dx) ** 2))[None, None, :]
+    psi0[..., 0] = env * np.exp(1j * 0.8 * C * x)[None, None, :]
+    psi0[..., 3] = W.spinor_C(0.8 * C) * psi0[..., 0]  # positive-energy spinor moving along +x
+    psi0 /= np.sqrt(oracle.observables(psi0, 3, dx)["norm"])
+    V = np.random.default_rng(53).uniform(-2e3, 2e3, nx)
+    o0 = oracle.observables(psi0, 3, dx, (-80 * dx, 0.0, 0.0), 80)
+    out, F = oracle.step_strang3d(psi0, M, C, dx, 5, V=V, periodic=True, flux_face=80)
+    o1 = oracle.observables(out, 3, dx, (-80 * dx, 0.0, 0.0), 80)
+    assert F > 1e-3
+    assert abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
