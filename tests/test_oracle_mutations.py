@@ -34,7 +34,7 @@ MUTANTS = {
     "A_z_entry_sign": ("U[1][3].im = -az; U[3][1].im = -az;", "U[1][3].im = az; U[3][1].im = -az;"),
     "A_y_entry_sign": ("U[0][3].re = ay;  U[0][3].im = ax;", "U[0][3].re = -ay;  U[0][3].im = ax;"),
     "A_mass_term_sign": ("U[0][0].re = cA; U[0][0].im = -ms;", "U[0][0].re = cA; U[0][0].im = ms;"),
-    "shift_ignored_in_sweep": ("d[axis] = g_shift;", "d[axis] = 1;"),
+    "shift_ignored_in_sweep": ("d[axis] = shift;", "d[axis] = 1;"),
     "shift_flux_window": ("for (int64_t i = face - g_shift; i < face; ++i) {", "for (int64_t i = face - 1; i < face; ++i) {"),
     "shift_time_step": ("double dt = (double)g_shift * dx / c;", "double dt = dx / c;"),
     "strang3d_order": ("const int axes[9] = {0, 1, 0, 2, -1, 2, 0, 1, 0};", "const int axes[9] = {1, 0, 0, 2, -1, 2, 0, 1, 0};"),
@@ -118,9 +118,9 @@ def _pins_pass():
     o1 = oracle.observables(out, 2, DX, (x_min, 0.0, z_min), face)
     ok &= abs((o1["norm_right"] - o0["norm_right"]) - F) < 1e-13
     # 3-D Strang step against its explicit matrix product
-    shape = (5, 4, 6)
-    psi = W.random_state(6, 4, 5, seed=96)
-    Vc = np.random.default_rng(97).uniform(-3e4, 3e4, 120)
+    shape = (5, 7, 6)  # 7 rows: a two-cell y shift does not wrap onto itself
+    psi = W.random_state(6, 7, 5, seed=96)
+    Vc = np.random.default_rng(97).uniform(-3e4, 3e4, 210)
     got, _ = oracle.step_strang3d(psi, 1.0, C, DX, 1, V=Vc, periodic=True)
     Ax, By, Cz = (A.sweep_matrix(shape, 0, True), A.sweep_matrix(shape, 1, True, shift=2),
                   A.sweep_matrix(shape, 2, True, shift=2))
