@@ -70,9 +70,11 @@ typedef struct {
     int points_per_lane;  /* x cells per lane of the step kernel: 1, 2 or 4 (K = 2 needs 2 in FP64);
                              0 = library choice */
     int splitting;        /* DIRAC_LIE: first-order steps x, (y,) z, phase with dt = dx / c (Sec. 2.1);
-                             DIRAC_STRANG (2-D only): second-order steps x, z, phase(dt), z, x with
-                             dt = 2 dx / c, so each half-step sweep is the one-cell shift (Sec. 2.4);
-                             steps_per_launch 1 (FP64) or 1, 2 (FP32) */
+                             DIRAC_STRANG: second-order steps (Sec. 2.4).  2-D: x, z, phase(dt), z, x with
+                             dt = 2 dx / c, so each half-step sweep is the one-cell shift; steps_per_launch
+                             1 (FP64) or 1, 2 (FP32).  3-D: A B A C D C A B A with dt = 4 dx / c, x sweeps
+                             moving one cell and y, z sweeps two (c dt/2 = 2 dx), eight single-sweep
+                             launches per step */
     int char_shift;       /* characteristic shift K of Sec. 2.3: c dt = K dx, each sweep moves the
                              characteristics by K cells and dt = K dx / c.  0 or 1: the paper's K = 1;
                              2, 3 or 4: 2-D first-order (DIRAC_LIE) grids without a vector potential,

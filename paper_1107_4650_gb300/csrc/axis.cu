@@ -1,0 +1,39 @@
+// Launchers of the single-sweep kernels used by the 3-D second-order step.
+#include "axis_kernels.cuh"
+
+namespace dirac {
+
+template <typename T>
+static cudaError_t launch_axis_t(const AxisArgs &a, int axis, int phase, int blocks, cudaStream_t s) {
+    if (axis == 0 && !phase) axis_kernel<T, 0, false><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 1 && !phase) axis_kernel<T, 1, false><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 2 && !phase) axis_kernel<T, 2, false><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 2 && phase) axis_kernel<T, 2, true><<<blocks, 256, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz, int axis,
+                        int64_t shift, int periodic, int full_table, int phase, int64_t flux_face, double fscale,
+                        double vol, double *flux_part, double *flux_cum, unsigned *ticket, int fp32, int blocks,
+                        cudaStream_t s) {
+    AxisArgs a{};
+    a.in = in;
+    a.out = out;
+    a.table = table;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.shift = shift;
+    a.periodic = periodic;
+    a.full_table = full_table;
+    a.flux_face = axis == 0 ? flux_face : -1;
+    a.fscale = fscale;
+    a.vol = vol;
+    a.flux_part = flux_part;
+    a.flux_cum = flux_cum;
+    a.ticket = ticket;
+    return fp32 ? launch_axis_t<float>(a, axis, phase, blocks, s) : launch_axis_t<double>(a, axis, phase, blocks, s);
+}
+
+}  // namespace dirac

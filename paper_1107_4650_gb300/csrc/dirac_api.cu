@@ -97,10 +97,15 @@ int ndim_of(const dirac_grid *g) { return g->cfg.ndim; }
 bool strang(const dirac_grid *g) { return g->cfg.splitting == DIRAC_STRANG; }
 // Power-of-two scale the phase coefficients carry for the sweeps' 1/2 factors: 1/4 (2-D), 1/8 (3-D),
 // 1/16 (2-D Strang: four sweeps per step).
-double scale_of(const dirac_grid *g) { return strang(g) ? 0.0625 : (ndim_of(g) == 3 ? 0.125 : 0.25); }
+// Power-of-two scale the phase coefficients carry for the sweeps' 1/2 factors: 1/4 (2-D), 1/8 (3-D),
+// 1/16 (2-D Strang: four sweeps per step), 1/256 (3-D Strang: eight sweeps per step).
+double scale_of(const dirac_grid *g) {
+    if (strang(g)) return ndim_of(g) == 3 ? 1.0 / 256.0 : 0.0625;
+    return ndim_of(g) == 3 ? 0.125 : 0.25;
+}
 int char_shift(const dirac_grid *g) { return g->cfg.char_shift > 1 ? g->cfg.char_shift : 1; }
 int sweep_mode(const dirac_grid *g) {
-    if (strang(g)) return 2;
+    if (strang(g)) return ndim_of(g) == 3 ? 6 : 2;
     if (ndim_of(g) == 3) return 1;
     if (char_shift(g) > 1) return 4;
     return g->avec.empty() ? 0 : 3;
@@ -227,11 +232,18 @@ void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
         }
 }
 
+// Grid of the single-sweep kernels (grid-stride): up to 8 blocks of 256 threads per SM.
+int axis_blocks(const dirac_grid *g) {
+    const int64_t need = (g->ncells + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, 8 * (int64_t)g->sm_count));
+}
+
 dirac_status ensure_flux_part(dirac_grid *g) {
     const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
     size_t need = (size_t)8 * planes * std::max<int64_t>(g->plan.nsegs, 1);
     if (ndim_of(g) == 3 && g->plan.fused3d)
         need = std::max(need, (size_t)(g->plan.f_nzsegs * g->plan.f_nytiles * g->plan.f_warps));
+    if (sweep_mode(g) == 6) need = std::max(need, (size_t)axis_blocks(g));
     if (need <= g->flux_part_cap) return DIRAC_OK;
     if (g->flux_part) {
         cudaFree(g->flux_part);
@@ -273,6 +285,26 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     a.ucoef_n = (int64_t)(g->avec.size() / 3);
     a.step0 = step0;
     const int mode = sweep_mode(g);
+    if (mode == 6) {
+        // 3-D second-order step (Sec. 2.4): A(1) B(2) A(1) C(2) D C(2) A(1) B(2) A(1), cells moved per sweep in
+        // parentheses.  Each sweep doubles the state and the table carries 1/256, so the state entering the
+        // four x sweeps is 1, 4, 1/8 and 1/2 times the true state (flux scale 1/2 over its square).
+        static const int axes[8] = {0, 1, 0, 2, 2, 0, 1, 0};
+        static const double fscale[8] = {0.5, 0, 0.5 / 16.0, 0, 0, 0.5 * 64.0, 0, 0.5 * 4.0};
+        const int blocks = axis_blocks(g);
+        int par = parity;
+        for (int q = 0; q < 8; ++q) {
+            const int ax = axes[q];
+            cudaError_t e = launch_axis(g->psi[par], g->psi[par ^ 1], g->table, g->cfg.n[0], g->cfg.n[1], g->cfg.n[2], ax,
+                                        ax == 0 ? 1 : 2, a.periodic, g->table_full, q == 3 ? 1 : 0,
+                                        ax == 0 ? a.flux_face : -1, fscale[q], a.vol, g->flux_part, g->flux_dev,
+                                        g->ticket, g->fp32, blocks, s);
+            if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order sweep launch");
+            g->launches++;
+            par ^= 1;
+        }
+        return DIRAC_OK;
+    }
     if (mode == 1 && p.fused3d) {
         a.nsegs = p.f_nzsegs * p.f_nytiles * p.f_warps;  // flux parts of the fused pass
         a.nplanes = 1;
@@ -306,7 +338,10 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     return DIRAC_OK;
 }
 
-int block_flips(const dirac_grid *g) { return (ndim_of(g) == 3 && !g->plan.fused3d) ? 0 : 1; }
+int block_flips(const dirac_grid *g) {
+    if (sweep_mode(g) == 6) return 0;  // eight sweeps per step: parity returns
+    return (ndim_of(g) == 3 && !g->plan.fused3d) ? 0 : 1;
+}
 
 dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
     if (g->graph[parity]) {
@@ -338,7 +373,10 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
     return DIRAC_OK;
 }
 
-int64_t launches_per_block(const dirac_grid *g) { return 1 + ((ndim_of(g) == 3 && !g->plan.fused3d) ? 1 : 0); }
+int64_t launches_per_block(const dirac_grid *g) {
+    if (sweep_mode(g) == 6) return 8;
+    return 1 + ((ndim_of(g) == 3 && !g->plan.fused3d) ? 1 : 0);
+}
 
 dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
     const int K = (ndim_of(g) == 3) ? 1 : g->plan.K;
@@ -538,8 +576,8 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (ncells_d > 4.0e10) return fail(nullptr, DIRAC_ERR_ARG, "grid too large");
     if (cfg->splitting != DIRAC_LIE && cfg->splitting != DIRAC_STRANG)
         return fail(nullptr, DIRAC_ERR_ARG, "splitting must be DIRAC_LIE or DIRAC_STRANG");
-    if (cfg->splitting == DIRAC_STRANG && cfg->ndim != 2)
-        return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_STRANG is implemented for 2-D grids");
+    if (cfg->splitting == DIRAC_STRANG && cfg->ndim == 3 && cfg->steps_per_launch > 1)
+        return fail(nullptr, DIRAC_ERR_ARG, "3-D DIRAC_STRANG runs one step per launch block (steps_per_launch 0 or 1)");
     if (cfg->char_shift < 0 || cfg->char_shift > 4)
         return fail(nullptr, DIRAC_ERR_ARG, "char_shift must be 0 (= 1), 1, 2, 3 or 4");
     if (cfg->char_shift > 1) {
@@ -569,7 +607,7 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     g->fp32 = cfg->precision == DIRAC_FP32;
     g->elem = g->fp32 ? 4 : 8;
     g->ncells = cfg->n[0] * cfg->n[1] * cfg->n[2];
-    g->dt = (cfg->splitting == DIRAC_STRANG ? 2.0 : 1.0) * cfg->dx / cfg->c;
+    g->dt = (cfg->splitting == DIRAC_STRANG ? (cfg->ndim == 3 ? 4.0 : 2.0) : 1.0) * cfg->dx / cfg->c;
     if (cfg->char_shift > 1) g->dt = (double)cfg->char_shift * cfg->dx / cfg->c;
     cudaError_t e = cudaSetDevice(cfg->device);
     if (e != cudaSuccess) {
@@ -840,6 +878,7 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
 dirac_status dirac_autotune(dirac_grid *g) {
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     CK(g, cudaSetDevice(g->cfg.device));
+    if (sweep_mode(g) == 6) return DIRAC_OK;  // the 3-D second-order step has a single launch plan
     struct Cand {
         int K, P, wpb, wsm;
         int fused = 0;  // 3-D: warps per block of the fused pass (0: two-pass path)

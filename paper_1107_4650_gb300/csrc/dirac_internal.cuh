@@ -80,6 +80,14 @@ bool sweep_supported(int fp32, int mode, int K, int P);
 cudaError_t launch_shift(const SweepArgs &a, int fp32, int S, int P, int warps_per_block, cudaStream_t s);
 bool shift_supported(int S, int P);
 
+// One sweep of the whole grid along `axis` with the characteristics moved `shift` cells (output 2x the
+// swept state), optionally followed by the phase from `table` (z sweeps only); x sweeps accumulate the face
+// flux scaled by fscale when flux_face >= 0 (parts: one per block).  Used by the 3-D second-order step.
+cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz, int axis,
+                        int64_t shift, int periodic, int full_table, int phase, int64_t flux_face, double fscale,
+                        double vol, double *flux_part, double *flux_cum, unsigned *ticket, int fp32, int blocks,
+                        cudaStream_t s);
+
 // Fused 3-D step (x, y, z sweeps and phase in one pass, one step per launch): blocks of `warps` (8 or 16)
 // warps own a 30-cell x strip and warps - 2 rows along y and stream a z segment of zseg_h planes.  Flux
 // parts: nzsegs * nytiles * warps (a.nsegs * a.nplanes must equal that).

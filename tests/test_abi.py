@@ -109,9 +109,9 @@ def test_batch_rejects_bad_runs_without_a_gpu(lib):
     assert e.value.status == D.DIRAC_ERR_ARG
 
 
-def test_strang_needs_a_2d_grid(lib):
+def test_strang_3d_runs_one_step_per_block(lib):
     import paper_1107_4650_gb300 as D
-    cfg = D.make_config((16, 16, 16), ndim=3, splitting=D.DIRAC_STRANG)
+    cfg = D.make_config((16, 16, 16), ndim=3, splitting=D.DIRAC_STRANG, steps_per_launch=2)
     with pytest.raises(D.DiracError) as e:
         D.dirac_create_grid(cfg)
     assert e.value.status == D.DIRAC_ERR_ARG

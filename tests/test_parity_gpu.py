@@ -588,3 +588,63 @@ def test_shift_fp32_against_oracle(D):
     want, _ = oracle.step(psi, 2, 1.0, C, DX, 60, V=V, periodic=True, shift=3)
     got, _, _ = _run_shift(D, psi, 60, 3, V=V, periodic=True, fp32=True)
     assert rel_l2(got.astype(np.complex128), want) < 2e-5
+
+
+# ------------------------------------------------------------------ 3-D second-order (Strang) splitting
+
+@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("full", [False, True])
+def test_strang3d_fp64_bit_exact(D, shape, periodic, full):
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx * ny + nz)
+    rng = np.random.default_rng(nz)
+    V = rng.uniform(-4e4, 4e4, nx * ny * nz if full else nx)
+    want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 5, V=V, periodic=periodic)
+    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL if full else D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi)
+        D.dirac_step(h, 5)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_strang3d_flux_graphs_fp32(D, fp32):
+    """A positive-energy packet crossing the face: 40 steps (graph replay), flux at the four x sweeps of
+    every step against the oracle; FP32 storage within its rounding tolerance."""
+    nx, ny, nz = 160, 12, 10
+    x = W.cell_centres(nx, DX, -80 * DX)
+    psi = np.zeros((nz, ny, nx, 4), complex)
+    env = np.exp(-((x + 12 * DX) ** 2) / (4 * (4 * DX) ** 2))[None, None, :]
+    psi[..., 0] = env * np.exp(1j * 0.8 * C * x)[None, None, :]
+    psi[..., 3] = W.spinor_C(0.8 * C) * psi[..., 0]
+    psi /= np.sqrt(oracle.observables(psi, 3, DX)["norm"])
+    V = np.random.default_rng(53).uniform(-2e3, 2e3, nx)
+    want, F = oracle.step_strang3d(psi, 1.0, C, DX, 40, V=V, periodic=True, flux_face=80)
+    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, boundary=D.DIRAC_BC_PERIODIC,
+                        flux_face=80, precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64)
+    h = D.dirac_create_grid(cfg)
+    dt = np.complex64 if fp32 else np.complex128
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, np.ascontiguousarray(psi.astype(dt)))
+        D.dirac_step(h, 40)
+        got = np.empty(psi.shape, dtype=dt)
+        D.dirac_get_state(h, got)
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    assert F > 0.1
+    if fp32:
+        assert rel_l2(got.astype(np.complex128), want) < 5e-5
+        assert abs(obs["flux_cum"] - F) < 1e-5 * abs(F)
+    else:
+        assert _bits_equal(got, want)
+        assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
