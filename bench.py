@@ -16,8 +16,9 @@ grid-point-steps per second (cells x time steps / s).
              point-step) against the FP64 rate.
   cpu_baseline  the FP64 CPU oracle on this host's cores, on a bounded sample of the same run.
 
-With --gpus N > 1 (torchrun), every rank runs an independent replica (the path is one grid and is
-not sharded); value = all ranks' point-steps / the slowest rank's time.
+With --gpus N > 1 (torchrun), every rank runs an independent replica of the single-grid legs (one grid per
+GPU, not sharded) and its own share of a global ensemble draw in the batched leg; value = all ranks'
+point-steps / the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -251,12 +252,10 @@ def main():
         launches = D.dirac_get_info(h)["kernel_launches"] - l0
         return total, inner, launches
 
+    from paper_1107_4650_gb300 import distributed as PD
+
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return PD.max_over_ranks(x, world, device="cuda")
 
     # ---------------------------------------------------------------- FP64, device-resident
     h = make_grid(D.DIRAC_FP64)
@@ -378,7 +377,8 @@ def main():
 
     # ---------------------------------------------------------------- batched ensemble (FP32)
     if not args.no_batch:
-        runs, deviations = W.klein_ensemble(nruns=args.batch_runs)
+        # independent runs: each rank takes batch_runs of one global draw of batch_runs * world (weak scaling)
+        runs, _, deviations = PD.ensemble_shard(args.batch_runs, rank, world)
         bcfg = D.dirac_batch_default_config()
         bcfg.precision = D.DIRAC_FP32
         bcfg.stream = stream.cuda_stream
