@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-field", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--side3d", type=int, default=384)
     ap.add_argument("--batch-runs", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--judge-points", type=int, default=16)
@@ -374,6 +376,50 @@ def main():
                         "phase matrix of Eq. sol_dis_4), %d timed steps" % nf,
             "fp64_instr_per_point_step": FP64_INSTR_PER_POINT_STEP_2D_FIELD,
             "frac_of_measured_fp64_issue": FP64_INSTR_PER_POINT_STEP_2D_FIELD * vf / world / 1e12 / FP64_ISSUE_PEAK_MEASURED}
+
+    # ---------------------------------------------------------------- 3-D soft-Coulomb grid (first and second order)
+    if not args.no_3d:
+        n3 = args.side3d
+        dx3 = W.DX_DEFAULT
+        psi3 = W.gaussian_packet(n3, n3, dx3, -n3 * dx3 / 2, -n3 * dx3 / 2, 32 * dx3, 0.0, 16 * dx3, 0.0, ny=n3,
+                                 y_min=-n3 * dx3 / 2)
+        V3 = W.soft_coulomb_3d(n3, dx3, 10.0, 2 * dx3).reshape(-1)
+        for prec, pname in ((D.DIRAC_FP64, "fp64"), (D.DIRAC_FP32, "fp32")):
+            dev3 = torch.from_numpy(psi3.astype(np.complex128 if prec == D.DIRAC_FP64 else np.complex64)
+                                    .view(np.float64 if prec == D.DIRAC_FP64 else np.float32)).to(f"cuda:{local}")
+            for split, sname, per_step in ((D.DIRAC_LIE, "first_order", 1), (D.DIRAC_STRANG, "strang", 4)):
+                cfg3 = D.make_config((n3, n3, n3), ndim=3, precision=prec, splitting=split, stream=stream.cuda_stream,
+                                     device=local)
+                h3 = D.dirac_create_grid(cfg3)
+                D.dirac_set_potential(h3, V3, D.DIRAC_V_FULL)
+                D.dirac_set_state(h3, dev3)
+                n_steps3 = 12 if split == D.DIRAC_LIE else 4
+                D.dirac_step(h3, n_steps3)  # warm-up
+                e30, e31 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                stream.synchronize()
+                e30.record(stream)
+                D.dirac_step(h3, n_steps3)
+                e31.record(stream)
+                stream.synchronize()
+                t3 = max_over_ranks(e30.elapsed_time(e31))
+                o3 = D.dirac_observables(h3)
+                D.dirac_destroy(h3)
+                v3 = n3 ** 3 * n_steps3 * world / (t3 / 1e3)
+                instr = 64 if split == D.DIRAC_LIE else 144
+                entry = {"value": v3, "unit": "point-steps/s", "steps": n_steps3, "ms_per_step": t3 / n_steps3,
+                         "physical_time_per_step_dx_over_c": per_step,
+                         "first_order_equivalent_point_steps_per_s": v3 * per_step,
+                         "workload": "%d^3 soft-Coulomb grid (Z = 10, per-cell table), %s splitting" % (n3, sname),
+                         "norm_end": o3["norm"]}
+                if prec == D.DIRAC_FP64:
+                    entry["fp64_instr_per_point_step"] = instr
+                    entry["frac_of_measured_fp64_issue"] = instr * v3 / world / 1e12 / FP64_ISSUE_PEAK_MEASURED
+                else:
+                    bytes3 = 80 if split == D.DIRAC_LIE else 8 * 64 + 16
+                    entry["bytes_per_point_step"] = bytes3
+                    entry["effective_hbm_frac"] = bytes3 * v3 / world / 1e9 / hbm_peak
+                variants["%s_3d_%s" % (pname, sname)] = entry
+            del dev3
 
     # ---------------------------------------------------------------- batched ensemble (FP32)
     if not args.no_batch:

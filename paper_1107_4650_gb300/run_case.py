@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--batch-runs", type=int, default=0, help="run this many ensemble runs as one batch instead")
     ap.add_argument("--seg", type=int, default=256, help="batch: rows per task")
     ap.add_argument("--shift", type=int, default=0, help="2-D: characteristic shift K (c dt = K dx)")
+    ap.add_argument("--strang", action="store_true", help="second-order splitting (2-D or 3-D)")
     ap.add_argument("--field", action="store_true",
                     help="2-D: add a uniform two-cycle laser pulse (vector potential) over the run")
     ap.add_argument("--mlp", type=int, default=0,
@@ -93,7 +94,8 @@ def main():
         shape = (args.side, 1, args.side)
         cfg = D.make_config(shape, x_min=(x_min, 0.0, z_min), flux_face=face, precision=prec,
                             stream=stream.cuda_stream, steps_per_launch=args.k, points_per_lane=args.p,
-                            use_graphs=not args.no_graphs, char_shift=args.shift)
+                            use_graphs=not args.no_graphs, char_shift=args.shift,
+                            splitting=D.DIRAC_STRANG if args.strang else D.DIRAC_LIE)
         layout = D.DIRAC_V_X_ONLY
     else:
         n = args.side
@@ -102,7 +104,7 @@ def main():
         V = W.soft_coulomb_3d(n, dx, 10.0, 2 * dx).reshape(-1)
         shape = (n, n, n)
         cfg = D.make_config(shape, ndim=3, precision=prec, stream=stream.cuda_stream, points_per_lane=args.p,
-                            use_graphs=not args.no_graphs)
+                            use_graphs=not args.no_graphs, splitting=D.DIRAC_STRANG if args.strang else D.DIRAC_LIE)
         layout = D.DIRAC_V_FULL
     h = D.dirac_create_grid(cfg)
     if args.field:
