@@ -180,3 +180,46 @@ def test_batch_one_call(D):
     assert np.allclose(T + R, 1.0)
     _, ref, _ = _run_batch(D, runs, fp32=False, explicit=False)
     assert np.allclose(T, ref["T"], rtol=1e-12, atol=1e-15)
+
+
+def test_full_512_run_ensemble_sampled_outputs(D):
+    """The benchmark's 512-run ensemble (sides, geometry, absorbing layers; FP64 storage, k = 2) with every
+    run cut to 40 steps: for 6 runs, 3 sampled cells each recomputed by the oracle on their light-cone crops,
+    bit for bit; every run's transmission finite."""
+    import dataclasses
+    full, _ = W.klein_ensemble(nruns=512)
+    runs = [dataclasses.replace(r, nsteps=40) for r in full]
+    cfg = D.dirac_batch_default_config()
+    cfg.precision = D.DIRAC_FP64
+    cfg.steps_per_launch = 2
+    h = D.dirac_batch_create([r.as_batch_fields() for r in runs], cfg)
+    picks = [0, 77, 150, 311, 480, 511]
+    outs = {}
+    try:
+        for i in picks:  # the sampled runs take the host's packet, layers and potential (the rest their device ones)
+            r = runs[i]
+            D.dirac_batch_set_state(h, i, r.state())
+            D.dirac_batch_set_absorber(h, i, r.mask())
+            D.dirac_batch_set_potential(h, i, r.potential())
+        D.dirac_batch_run(h)
+        res = D.dirac_batch_results(h, len(runs))
+        for i in picks:
+            r = runs[i]
+            o = np.empty((r.side, 1, r.side, 4), dtype=np.complex128)
+            D.dirac_batch_get_state(h, i, o)
+            outs[i] = o
+    finally:
+        D.dirac_batch_destroy(h)
+    assert np.all(np.isfinite(res["T"]))
+    for i in picks:
+        r = runs[i]
+        psi0 = r.state()
+        V = r.potential()
+        a = r.mask()
+        _, _, _, _, face = r.geometry()
+        for (z, x) in [(r.side // 2, face), (r.side // 2, face - 30), (r.side - 1, r.absorb - 1)]:
+            sz = slice(max(0, z - 41), min(r.side, z + 42))
+            sx = slice(max(0, x - 41), min(r.side, x + 42))
+            want, _ = oracle.step(psi0[sz, :, sx], 2, 1.0, C, r.dx, 40, V=V[sx], absorber=a[sx])
+            got = outs[i][z, 0, x]
+            assert np.array_equal(got.view(np.float64), want[z - sz.start, 0, x - sx.start].view(np.float64)), (i, z, x)

@@ -648,3 +648,76 @@ def test_strang3d_flux_graphs_fp32(D, fp32):
     else:
         assert _bits_equal(got, want)
         assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+
+
+# ------------------------------------------------------------------ full-size workloads, sampled outputs
+
+def _light_cone_crop(shape_zyx, cell, radius):
+    """Index ranges (per axis) of the cells within `radius` of `cell`, clipped to the grid.  After n <= radius - 1
+    steps the value at `cell` depends only on these cells (one cell per sweep per step), and an edge of the
+    crop that is not an edge of the grid lies beyond that cone, so the oracle on the crop reproduces it."""
+    return tuple(slice(max(0, c - radius), min(n, c + radius + 1)) for c, n in zip(cell, shape_zyx))
+
+
+def test_full_size_2048_fp64_sampled_outputs_bit_exact(D):
+    """The 2048^2 FP64 Klein grid in the benchmark's launch configuration (autotuned plan, graph replay):
+    64 steps, 12 sampled cells (the face, the step, the packet, edges and corners) each recomputed by the oracle
+    on its light-cone crop, bit for bit; the flux identity over the whole grid."""
+    run = W.klein_config_2d(side=2048, nsteps=64)
+    x_min, z_min, _, _, face = run.geometry()
+    psi0 = run.state()
+    V = run.potential()
+    cfg = D.make_config((2048, 1, 2048), x_min=(x_min, 0.0, z_min), flux_face=face)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi0)
+        D.dirac_autotune(h)
+        o0 = D.dirac_observables(h)
+        D.dirac_step(h, run.nsteps)
+        got = np.empty_like(psi0)
+        D.dirac_get_state(h, got)
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    n = run.nsteps
+    cx = int(-x_min / DX - 4 * run.width / DX)  # packet centre column
+    cells = [(1024, face), (1024, face - 1), (1024, cx), (1000, cx + 37), (0, cx), (2047, face + 3), (5, 0),
+             (2047, 2047), (0, 2047), (1500, 60), (777, 1999), (1024, 2040)]
+    for (z, x) in cells:
+        sz, sx = _light_cone_crop((2048, 2048), (z, x), n + 1)
+        want, _ = oracle.step(psi0[sz, :, sx], 2, 1.0, C, DX, n, V=V[sx])
+        wz, wx = z - sz.start, x - sx.start
+        assert np.array_equal(got[z, 0, x].view(np.float64), want[wz, 0, wx].view(np.float64)), (z, x)
+    x = W.cell_centres(2048, DX, x_min)
+    rho0 = (np.abs(psi0) ** 2).sum(axis=(1, 3))
+    rho1 = (np.abs(got) ** 2).sum(axis=(1, 3))
+    dright = (rho1[:, face:].sum() - rho0[:, face:].sum()) * DX * DX
+    assert abs(dright - obs["flux_cum"]) < 1e-12 * max(abs(dright), 1e-30) + 1e-15
+
+
+def test_full_size_384_cubed_sampled_outputs_bit_exact(D):
+    """The 384^3 soft-Coulomb grid (per-cell FP64 table, fused 3-D pass): 6 steps, 8 sampled cells recomputed
+    by the oracle on their light-cone crops, bit for bit."""
+    n3 = 384
+    dx = DX
+    psi0 = W.gaussian_packet(n3, n3, dx, -n3 * dx / 2, -n3 * dx / 2, 32 * dx, 0.0, 16 * dx, 0.0, ny=n3,
+                             y_min=-n3 * dx / 2)
+    V = W.soft_coulomb_3d(n3, dx, 10.0, 2 * dx)
+    cfg = D.make_config((n3, n3, n3), ndim=3)
+    h = D.dirac_create_grid(cfg)
+    nsteps = 6
+    try:
+        D.dirac_set_potential(h, V.reshape(-1), D.DIRAC_V_FULL)
+        D.dirac_set_state(h, psi0)
+        D.dirac_step(h, nsteps)
+        got = np.empty_like(psi0)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    for cell in [(192, 192, 192), (192, 192, 224), (0, 0, 0), (383, 200, 17), (100, 383, 383), (191, 5, 300),
+                 (250, 250, 150), (7, 380, 192)]:
+        sl = _light_cone_crop((n3, n3, n3), cell, nsteps + 1)
+        want, _ = oracle.step(psi0[sl], 3, 1.0, C, dx, nsteps, V=V[sl].reshape(-1))
+        loc = tuple(c - s.start for c, s in zip(cell, sl))
+        assert np.array_equal(got[cell].view(np.float64), want[loc].view(np.float64)), cell
