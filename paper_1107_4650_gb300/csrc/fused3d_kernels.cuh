@@ -71,14 +71,32 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
             for (int c = 0; c < 4; ++c) s[c] = {T(0), T(0)};
         }
     };
-    Cx<T> nxt[4];
+    // rows of the next planes in flight: one ahead in FP64 (bound by the FP64 pipe), two ahead in FP32
+    // (bound by load latency with 16 warps per SM)
+    constexpr bool DEEP = sizeof(T) == 4;
+    Cx<T> nxt[4], nxt2[DEEP ? 4 : 1];
     load_row(z_begin - 1, nxt);
+    if (DEEP) load_row(z_begin, nxt2);
+
+    // per-cell table entries of the next output plane, loaded one plane ahead (full table only)
+    Cx<T> tu = pu, td = pd, tu_next = pu, td_next = pd;
 
     for (int64_t k = z_begin - 1; k <= z_end; ++k) {
+        if (a.full_table && owned_row) {
+            tu = tu_next;
+            td = td_next;
+            if (k >= z_begin && k < z_end) load_tab(tab + ((k * ny + y) * nx + xl) * 4, tu_next, td_next);
+        }
         Cx<T> st[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) st[c] = nxt[c];
-        if (k + 1 <= z_end) load_row(k + 1, nxt);
+        if (DEEP) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) nxt[c] = nxt2[DEEP ? c : 0];
+            if (k + 2 <= z_end) load_row(k + 2, nxt2);
+        } else {
+            if (k + 1 <= z_end) load_row(k + 1, nxt);
+        }
         // x characteristics and the x sweep (neighbours by shuffle; lanes 0 and 31 are halo cells)
         const Cx<T> u14 = cadd(st[0], st[3]), w14 = csub(st[0], st[3]);
         const Cx<T> u23 = cadd(st[1], st[2]), w23 = csub(st[1], st[2]);
@@ -122,8 +140,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
                 o[2] = csub(UA[0], W13);
                 o[1] = cadd(UA[1], W24);
                 o[3] = csub(W24, UA[1]);
-                Cx<T> qu = pu, qd = pd;
-                if (a.full_table) load_tab(tab + ((zo * ny + y) * nx + xl) * 4, qu, qd);
+                const Cx<T> qu = a.full_table ? tu : pu, qd = a.full_table ? td : pd;
                 o[0] = cmulp(o[0], qu);
                 o[1] = cmulp(o[1], qu);
                 o[2] = cmulp(o[2], qd);
