@@ -28,6 +28,7 @@ def main():
     ap.add_argument("--seg", type=int, default=256, help="batch: rows per task")
     ap.add_argument("--shift", type=int, default=0, help="2-D: characteristic shift K (c dt = K dx)")
     ap.add_argument("--strang", action="store_true", help="second-order splitting (2-D or 3-D)")
+    ap.add_argument("--autotune", action="store_true", help="let dirac_autotune choose the launch plan first")
     ap.add_argument("--field", action="store_true",
                     help="2-D: add a uniform two-cycle laser pulse (vector potential) over the run")
     ap.add_argument("--mlp", type=int, default=0,
@@ -114,6 +115,8 @@ def main():
     D.dirac_set_potential(h, V, layout)
     host = np.ascontiguousarray(psi.astype(np.complex64 if prec == D.DIRAC_FP32 else np.complex128))
     D.dirac_set_state(h, host)
+    if args.autotune:
+        D.dirac_autotune(h)
     times = []
     for it in range(args.repeat):
         if args.field:
