@@ -393,6 +393,8 @@ def main():
                 h3 = D.dirac_create_grid(cfg3)
                 D.dirac_set_potential(h3, V3, D.DIRAC_V_FULL)
                 D.dirac_set_state(h3, dev3)
+                D.dirac_autotune(h3)  # fused single pass or x-y + z/phase passes, whichever is faster here
+                i3 = D.dirac_get_info(h3)
                 n_steps3 = 12 if split == D.DIRAC_LIE else 4
                 D.dirac_step(h3, n_steps3)  # warm-up
                 e30, e31 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -410,6 +412,9 @@ def main():
                          "physical_time_per_step_dx_over_c": per_step,
                          "first_order_equivalent_point_steps_per_s": v3 * per_step,
                          "workload": "%d^3 soft-Coulomb grid (Z = 10, per-cell table), %s splitting" % (n3, sname),
+                         "plan": {D.DIRAC_PLAN_3D_FUSED: "fused single pass",
+                                  D.DIRAC_PLAN_3D_TWO_PASS: "x-y pass + z/phase pass, P=%d" % i3["points_per_lane"],
+                                  D.DIRAC_PLAN_3D_STRANG: "eight single-sweep launches"}.get(i3["plan"], str(i3["plan"])),
                          "norm_end": o3["norm"]}
                 if prec == D.DIRAC_FP64:
                     entry["fp64_instr_per_point_step"] = instr

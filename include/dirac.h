@@ -165,7 +165,19 @@ typedef struct {
     int graphs;             /* 1 when dirac_step replays a CUDA graph */
     int64_t kernel_launches;/* kernels enqueued by this grid so far (all kinds) */
     size_t device_bytes;    /* device memory owned by the grid */
+    int plan;               /* DIRAC_PLAN_*: which kernels one step runs */
 } dirac_info;
+
+/* dirac_info.plan */
+enum {
+    DIRAC_PLAN_STEP_2D = 0,      /* fused 2-D first-order step, k steps per launch */
+    DIRAC_PLAN_STRANG_2D = 1,    /* fused 2-D second-order step */
+    DIRAC_PLAN_FIELD_2D = 2,     /* 2-D first-order step with the vector-potential phase matrix */
+    DIRAC_PLAN_SHIFT_2D = 3,     /* 2-D first-order step with characteristic shift > 1 */
+    DIRAC_PLAN_3D_TWO_PASS = 4,  /* 3-D x-y pass + z/phase pass */
+    DIRAC_PLAN_3D_FUSED = 5,     /* 3-D single pass */
+    DIRAC_PLAN_3D_STRANG = 6     /* 3-D second-order step: eight single-sweep launches */
+};
 
 dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info);
 

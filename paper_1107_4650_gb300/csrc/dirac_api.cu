@@ -863,6 +863,11 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
     info->launch_warps = p.nstrips * p.nsegs * planes;
     info->strip_width = p.strip_w;
     info->segment_rows = p.seg_h;
+    static const int plan_of_mode[7] = {DIRAC_PLAN_STEP_2D, DIRAC_PLAN_3D_TWO_PASS, DIRAC_PLAN_STRANG_2D,
+                                        DIRAC_PLAN_FIELD_2D, DIRAC_PLAN_SHIFT_2D, DIRAC_PLAN_3D_FUSED,
+                                        DIRAC_PLAN_3D_STRANG};
+    const int mode = sweep_mode(g);
+    info->plan = (mode == 1 && p.fused3d) ? DIRAC_PLAN_3D_FUSED : plan_of_mode[mode];
     if (g->cfg.ndim == 3 && p.fused3d) {
         info->points_per_lane = 1;
         info->launch_warps = p.f_nstrips * p.f_nytiles * p.f_nzsegs * p.f_warps;

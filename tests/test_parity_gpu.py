@@ -138,6 +138,7 @@ def test_3d_fp64_bit_exact_coulomb(D, shape, periodic, P):
     V = (-10.0 / np.sqrt(r2 + (2 * DX) ** 2)).reshape(-1)
     want, _ = oracle.step(psi, 3, 1.0, C, DX, 4, V=V, periodic=periodic)
     got, _, info = run_gpu(D, psi, 3, 4, V=V, periodic=periodic, P=P)
+    assert info["plan"] == (D.DIRAC_PLAN_3D_FUSED if P == 0 else D.DIRAC_PLAN_3D_TWO_PASS)
     assert info["strip_width"] == (30 if P == 0 else 32 * P - 2)
     assert _bits_equal(got, want), rel_l2(got, want)
 
