@@ -722,3 +722,71 @@ def test_full_size_384_cubed_sampled_outputs_bit_exact(D):
         want, _ = oracle.step(psi0[sl], 3, 1.0, C, dx, nsteps, V=V[sl].reshape(-1))
         loc = tuple(c - s.start for c, s in zip(cell, sl))
         assert np.array_equal(got[cell].view(np.float64), want[loc].view(np.float64)), cell
+
+
+# ------------------------------------------------------------------ degenerate grids
+
+_DEGENERATE_2D = [(1, 1), (1, 9), (9, 1), (33, 1), (1, 40), (2, 3)]
+
+
+@pytest.mark.parametrize("shape", _DEGENERATE_2D)
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("variant", ["k1", "k2", "strang", "shift2", "field"])
+def test_degenerate_2d_grids_bit_exact(D, shape, periodic, variant):
+    """Single-row, single-column and tiny grids in every 2-D step variant, against the oracle bit for bit."""
+    nx, nz = shape
+    psi = W.random_state(nz, 1, nx, seed=nx * 100 + nz)
+    V = np.random.default_rng(nx + nz).uniform(-3e4, 3e4, nx)
+    At = np.random.default_rng(3).uniform(-1, 1, (5, 3))
+    kw = dict(V=V, periodic=periodic)
+    if variant == "strang":
+        want, _ = oracle.step_strang2d(psi, 1.0, C, DX, 5, **kw)
+    elif variant == "shift2":
+        want, _ = oracle.step(psi, 2, 1.0, C, DX, 5, shift=2, **kw)
+    elif variant == "field":
+        want, _ = oracle.step(psi, 2, 1.0, C, DX, 5, A_tilde=At, **kw)
+    else:
+        want, _ = oracle.step(psi, 2, 1.0, C, DX, 5, **kw)
+    cfg = D.make_config((nx, 1, nz), boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO,
+                        steps_per_launch=2 if variant == "k2" else 0,
+                        splitting=D.DIRAC_STRANG if variant == "strang" else D.DIRAC_LIE,
+                        char_shift=2 if variant == "shift2" else 0)
+    h = D.dirac_create_grid(cfg)
+    try:
+        if variant == "field":
+            D.dirac_set_vector_potential(h, At)
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi)
+        D.dirac_step(h, 0)
+        D.dirac_step(h, 5)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 1), (3, 1, 7), (1, 1, 9), (31, 2, 3)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("variant", ["fused", "two_pass", "strang"])
+def test_degenerate_3d_grids_bit_exact(D, shape, periodic, variant):
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx * 7 + ny * 3 + nz)
+    V = np.random.default_rng(nx + ny + nz).uniform(-3e4, 3e4, nx * ny * nz)
+    if variant == "strang":
+        want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 3, V=V, periodic=periodic)
+    else:
+        want, _ = oracle.step(psi, 3, 1.0, C, DX, 3, V=V, periodic=periodic)
+    cfg = D.make_config((nx, ny, nz), ndim=3, boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO,
+                        points_per_lane=1 if variant == "two_pass" else 0,
+                        splitting=D.DIRAC_STRANG if variant == "strang" else D.DIRAC_LIE)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+        D.dirac_set_state(h, psi)
+        D.dirac_step(h, 3)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want), rel_l2(got, want)
