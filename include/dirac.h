@@ -129,7 +129,11 @@ typedef struct {
 /* Reductions of the current state (Sec. 5.2.1: R and T are integrals of |psi|^2), accumulated in
  * FP64, deterministic.  density (nullable) receives rho per cell in FP64, [z][y][x], on the device
  * when density_on_device != 0, else on the host.  Synchronises the grid's stream.
- * Returns DIRAC_ERR_NONFINITE (obs still filled) when the norm is NaN or Inf. */
+ * Returns DIRAC_ERR_NONFINITE (obs still filled) when the norm is NaN or Inf, and DIRAC_ERR_TIMEOUT when
+ * a step kernel gave up waiting for a row copy since the last dirac_set_state (every such wait is bounded
+ * by about one second; the state is then invalid and dirac_set_state clears the report).  Setting the
+ * environment variable DIRAC_INJECT_STALL before dirac_create_grid makes every zero-boundary step launch of
+ * that grid stall one copy on purpose, to test this path. */
 dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, int density_on_device);
 
 /* Absorbing layer (an addition to the paper's scheme, which names absorbing boundaries as future work):

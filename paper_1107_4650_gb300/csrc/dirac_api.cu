@@ -57,6 +57,7 @@ struct dirac_grid {
     double *ucoef = nullptr;         // device: 12 doubles of U entries per step
     size_t ucoef_cap = 0;            // bytes
     bool tuning = false;             // autotune timing runs: table rows taken modulo its length
+    int inject_stall = 0;            // DIRAC_INJECT_STALL set at creation: every step launch stalls one copy
     double *obs_partial = nullptr;
     double *obs_out = nullptr;
     double *host_obs = nullptr;  // pinned [8]
@@ -284,6 +285,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     a.ucoef = g->ucoef;
     a.ucoef_n = (int64_t)(g->avec.size() / 3);
     a.step0 = step0;
+    a.inject_stall = g->inject_stall;
     const int mode = sweep_mode(g);
     if (mode == 6) {
         // 3-D second-order step (Sec. 2.4): A(1) B(2) A(1) C(2) D C(2) A(1) B(2) A(1), cells moved per sweep in
@@ -603,6 +605,7 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     dirac_grid *g = new (std::nothrow) dirac_grid();
     if (!g) return fail(nullptr, DIRAC_ERR_OOM, "host allocation failed");
     g->cfg = *cfg;
+    g->inject_stall = std::getenv("DIRAC_INJECT_STALL") ? 1 : 0;
     g->stream = static_cast<cudaStream_t>(cfg->stream);
     g->fp32 = cfg->precision == DIRAC_FP32;
     g->elem = g->fp32 ? 4 : 8;
@@ -760,6 +763,7 @@ dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device) {
     CK(g, cudaMemcpyAsync(g->psi[g->cur], psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                           g->stream));
     CK(g, cudaMemsetAsync(g->flux_dev, 0, sizeof(double), g->stream));
+    CK(g, cudaMemsetAsync(g->ticket + 1, 0, sizeof(unsigned), g->stream));  // clear a reported timeout
     if (!on_device) CK(g, cudaStreamSynchronize(g->stream));
     g->step = 0;
     return DIRAC_OK;

@@ -38,6 +38,9 @@ struct SweepArgs {
     const double *ucoef;
     int64_t ucoef_n;
     int64_t step0;
+    // failure-detection test hook (DIRAC_INJECT_STALL): the launch's first warp makes its first row-copy
+    // wait run out, so the kernel reports DIRAC_ERR_TIMEOUT through *err
+    int inject_stall;
 };
 
 // Arguments of the 3-D z-sweep + phase kernel: the input is 4x the x-y swept state, the table is

@@ -205,11 +205,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity to complete (~0.5 s at most).
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase with the given parity to complete: gives up after about one second of the
+// global timer (checked every 64 polls), or after 2^24 polls whatever the timer says.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 24); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it > 32) __nanosleep(64);
+        if ((it & 63) == 63 && global_ns() - t0 > 1000000000ull) return false;
     }
     return false;
 }
@@ -390,7 +399,14 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
         for (int sl = 0; sl < RG::SLOTS; ++sl) {
             const int64_t r = r_first + sl;
             if (r < r_last && r >= 0 && r < nr) {
-                if (lane == 0) bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + (r * nx + cx0) * 8, copy_bytes, bar0 + 8 * sl);
+                if (lane == 0) {
+                    // failure-detection test hook: the first warp of the launch announces 16 bytes more than
+                    // its first row copy delivers, so that slot's phase never completes and its bounded wait
+                    // runs out (the copy itself completes normally)
+                    if (a.inject_stall && wid == 0 && sl == 0)
+                        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], 16;" ::"r"(bar0) : "memory");
+                    bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + (r * nx + cx0) * 8, copy_bytes, bar0 + 8 * sl);
+                }
                 pending |= 1u << sl;
             }
         }

@@ -790,3 +790,33 @@ def test_degenerate_3d_grids_bit_exact(D, shape, periodic, variant):
     finally:
         D.dirac_destroy(h)
     assert _bits_equal(got, want), rel_l2(got, want)
+
+
+# ------------------------------------------------------------------ failure detection without a GPU fault
+
+def test_stalled_row_copy_is_reported_and_the_context_survives(D, monkeypatch):
+    """DIRAC_INJECT_STALL makes the first warp's first row-copy wait of each launch run out (the copy itself
+    completes; its barrier expects 16 bytes more): the kernel gives up after its bounded wait, the host reads
+    DIRAC_ERR_TIMEOUT, and the same process then steps a fresh grid bit-exactly with the oracle."""
+    import time
+    nx, nz = 200, 64
+    psi = W.random_state(nz, 1, nx, seed=66)
+    monkeypatch.setenv("DIRAC_INJECT_STALL", "1")
+    h = D.dirac_create_grid(D.make_config((nx, 1, nz), steps_per_launch=1, points_per_lane=2))
+    monkeypatch.delenv("DIRAC_INJECT_STALL")
+    try:
+        D.dirac_set_state(h, psi)
+        t0 = time.perf_counter()
+        D.dirac_step(h, 1)
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_observables(h)
+        waited = time.perf_counter() - t0
+        assert e.value.status == D.DIRAC_ERR_TIMEOUT
+        assert 0.5 < waited < 20.0, waited
+        D.dirac_set_state(h, psi)  # clears the report; nothing stepped since
+        D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 3)
+    got, _, _ = run_gpu(D, psi, 2, 3)
+    assert _bits_equal(got, want)
