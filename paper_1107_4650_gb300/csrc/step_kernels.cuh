@@ -395,6 +395,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
             mbar_fence_init();
         }
         __syncwarp();
+        bool stall = a.inject_stall && wid == 0;
 #pragma unroll
         for (int sl = 0; sl < RG::SLOTS; ++sl) {
             const int64_t r = r_first + sl;
@@ -403,10 +404,12 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                     // failure-detection test hook: the first warp of the launch announces 16 bytes more than
                     // its first row copy delivers, so that slot's phase never completes and its bounded wait
                     // runs out (the copy itself completes normally)
-                    if (a.inject_stall && wid == 0 && sl == 0)
-                        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], 16;" ::"r"(bar0) : "memory");
+                    if (stall)
+                        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], 16;" ::"r"(bar0 + 8 * sl)
+                                     : "memory");
                     bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + (r * nx + cx0) * 8, copy_bytes, bar0 + 8 * sl);
                 }
+                stall = false;
                 pending |= 1u << sl;
             }
         }
