@@ -1,4 +1,4 @@
-"""Trains the Klein-transmission surrogate over the ensemble's parameter box and judges it.
+"""Trains the Klein-transmission surrogate over the ensemble's parameter box and checks it against the FP64 solver.
 
   python -m paper_1107_4650_gb300.surrogate_train --train 20000 --heldout 1000 --out surrogate.npz
 
@@ -64,7 +64,7 @@ def main():
     t_label = time.perf_counter() - t0
     t0 = time.perf_counter()
     T_te = solve(D, W, q_te, fp32=False)
-    t_judge = time.perf_counter() - t0
+    t_check = time.perf_counter() - t0
     h = D.dirac_surrogate_create(LO, HI, seed=W.SEED, max_batch=4096)
     t0 = time.perf_counter()
     loss = D.dirac_surrogate_train(h, q_tr, T_tr, epochs=args.epochs, batch=args.batch, lr=args.lr)
@@ -80,7 +80,7 @@ def main():
              "final_train_mse": loss, "dT_mean": float(dT.mean()), "dT_p99": float(np.quantile(dT, 0.99)),
              "dT_max": float(dT.max()), "frac_dT_le_1e-3": float((dT <= 1e-3).mean()),
              "s_per_query_net": t_net / len(q_te), "s_per_query_fp32_batch": t_label / len(q_tr),
-             "s_per_query_fp64_batch": t_judge / len(q_te), "label_s": t_label, "judge_s": t_judge,
+             "s_per_query_fp64_batch": t_check / len(q_te), "label_s": t_label, "check_s": t_check,
              "train_s": t_train, "T_train_mean": float(T_tr.mean()), "T_train_max": float(T_tr.max())}
     np.savez(args.out, params=params, lo=LO, hi=HI, stats=json.dumps(stats), q_train=q_tr, T_train=T_tr,
              q_heldout=q_te, T_heldout_fp64=T_te)

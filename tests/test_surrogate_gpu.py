@@ -1,5 +1,5 @@
 """Transmission surrogate: the GPU network's forward and backward against the CPU FP64 oracle, training,
-and a small-box Klein surrogate trained on batched-solver output and judged by the FP64 solver."""
+and a small-box Klein surrogate trained on batched-solver output and checked against the FP64 solver."""
 import time
 
 import numpy as np
@@ -90,14 +90,14 @@ def _solve(D, qs, fp32):
 
 
 def test_klein_surrogate_small_box(D):
-    """1024 batched FP32 solves train the network; 48 held-out points are judged by the FP64 solver; queries
+    """1024 batched FP32 solves train the network; 48 held-out points are checked against the FP64 solver; queries
     outside the box fall back to the solver; the network answers >= 100x faster than per-run FP64 solves."""
     rng = np.random.default_rng(11)
     q_train = LO + (HI - LO) * rng.uniform(0, 1, (1024, 3))
     T_train = _solve(D, q_train, fp32=True)
     q_test = LO + (HI - LO) * rng.uniform(0, 1, (48, 3))
     t0 = time.perf_counter()
-    T_judge = _solve(D, q_test, fp32=False)
+    T_fp64 = _solve(D, q_test, fp32=False)
     t_fp64 = (time.perf_counter() - t0) / len(q_test)
     h = D.dirac_surrogate_create(LO, HI, seed=1, max_batch=1024)
     try:
@@ -110,7 +110,7 @@ def test_klein_surrogate_small_box(D):
         T_out, used = D.dirac_surrogate_query(h, np.vstack([q_test[:3], q_out]), _solver_cfg(D, True))
     finally:
         D.dirac_surrogate_destroy(h)
-    dT = np.abs(T_net - T_judge)
+    dT = np.abs(T_net - T_fp64)
     print("surrogate small box: mean |dT| %.2e, max %.2e; %.1f us/query vs FP64 solve %.1f ms/query"
           % (dT.mean(), dT.max(), t_net * 1e6, t_fp64 * 1e3))
     assert dT.mean() < 0.012 and dT.max() < 0.15
