@@ -3,7 +3,7 @@
 //
 // Rounding points (the CPU gradient oracle mirrors them):
 //   layer 1:        z1 = x . bf16(W1)^T + b1 in FP32 (K = 3, CUDA cores)
-//   layers 2..4:    z = bf16(h) . bf16(W)^T + b, BF16 tensor-core products, FP32 accumulation
+//   layers 2..4:    z = bf16(h) . bf16(W)^T + b, BF16 tensor-core products (tcgen05), FP32 accumulation
 //   output:         z5 = bf16(h4) . bf16(w5) + b5 (FP32 dot), y = sigmoid(z5)
 //   backward:       dz5 = 2 (y - t) y (1 - y) / B; dW5 = sum_b dz5 bf16(h4); dh4 = dz5 bf16(w5);
 //                   dz = dh (1 - h^2);  dW = bf16(dz)^T . bf16(h_prev) and dh_prev = bf16(dz) . bf16(W)
@@ -19,88 +19,193 @@ namespace mlp {
 
 namespace {
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// ---- tcgen05 (5th-generation tensor core) GEMM for the hidden layers.
+//
+// C[M x N] (FP32, row-major, ldc) = sum_k A(m,k) B(k,n) (+ C when accumulate), A(m,k) = A[m*sam + k*sak],
+// B(k,n) = B[k*sbk + n*sbn], BF16 operands with arbitrary strides (the backward pass reads transposes).
+// One CTA of 4 warps computes a 128 x 256 tile of C in tensor memory: K is consumed in chunks of 64,
+// staged by all threads into shared memory in the canonical no-swizzle K-major layout (8-row x 16-byte
+// core matrices; K-direction core-matrix stride 128 B, 8-row-group stride 256 B; one 16-deep K slab per
+// MMA), double-buffered so the next chunk is staged while the tensor core consumes the current one.
+// One thread issues tcgen05.mma (M = 128, N = 256, K = 16, BF16 x BF16 -> FP32) and commits each chunk
+// to an mbarrier; every wait is bounded (about one second of the global timer) and a timeout sets
+// *err instead of hanging.  The accumulator (256 TMEM columns) is read back with tcgen05.ld, each warp
+// its 32 lanes = 32 rows of the tile.
+constexpr int GM = 128, GN = 256, GK = 64;
+constexpr int A_SLAB = GM * 16 * 2;  // bytes of one 16-deep K slab of the A tile (4 KB)
+constexpr int B_SLAB = GN * 16 * 2;  // (8 KB)
+constexpr int STAGE_BYTES = 4 * A_SLAB + 4 * B_SLAB;  // 48 KB per K chunk
+constexpr int GEMM_SMEM = 2 * STAGE_BYTES + 1024;     // two stages + alignment slack
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// C[M x N] (FP32, row-major, ldc) = sum_k A(m,k) B(k,n), A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]
-// (BF16, arbitrary strides).  Block tile 64 x 64, K tile 32; 4 warps, each a 32 x 32 sub-tile made of
-// 2 x 4 mma.sync.m16n8k16 tiles.  Tiles are staged in shared memory element by element (the strided
-// reads cover the transposed operands of the backward pass).
-constexpr int TM = 64, TN = 64, TK = 32;
-
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *A, int64_t sam, int64_t sak,
-                                                        const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, float *C,
-                                                        int64_t ldc, int M, int N, int K, int accumulate) {
-    __shared__ __nv_bfloat16 As[TM][TK + 8];
-    __shared__ __nv_bfloat16 Bs[TN][TK + 8];  // stored [n][k]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += TK) {
-        for (int e = tid; e < TM * TK; e += blockDim.x) {
-            const int r = e / TK, c = e % TK;
-            const int m = m0 + r, k = k0 + c;
-            As[r][c] = (m < M && k < K) ? A[(int64_t)m * sam + (int64_t)k * sak] : zero;
-        }
-        for (int e = tid; e < TN * TK; e += blockDim.x) {
-            const int r = e / TK, c = e % TK;
-            const int n = n0 + r, k = k0 + c;
-            Bs[r][c] = (n < N && k < K) ? B[(int64_t)k * sbk + (int64_t)n * sbn] : zero;
-        }
-        __syncthreads();
-        const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-        for (int kk = 0; kk < TK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16;
-                af[i][0] = pack_bf16(As[r + g][kk + 2 * t], As[r + g][kk + 2 * t + 1]);
-                af[i][1] = pack_bf16(As[r + g + 8][kk + 2 * t], As[r + g + 8][kk + 2 * t + 1]);
-                af[i][2] = pack_bf16(As[r + g][kk + 2 * t + 8], As[r + g][kk + 2 * t + 9]);
-                af[i][3] = pack_bf16(As[r + g + 8][kk + 2 * t + 8], As[r + g + 8][kk + 2 * t + 9]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + j * 8;
-                bfr[j][0] = pack_bf16(Bs[c + g][kk + 2 * t], Bs[c + g][kk + 2 * t + 1]);
-                bfr[j][1] = pack_bf16(Bs[c + g][kk + 2 * t + 8], Bs[c + g][kk + 2 * t + 9]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                        "{%0,%1,%2,%3};"
-                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-                        : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
-        }
-        __syncthreads();
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = timer_ns();
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (it > 32) __nanosleep(64);
+        if ((it & 63) == 63 && timer_ns() - t0 > 1000000000ull) return false;
     }
-    const int g = lane >> 2, t = lane & 3;
+    return false;
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major; start address, LBO (K-direction core-matrix
+// stride) and SBO (8-row-group stride) in 16-byte units, descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Byte offset of element (row, k) of a K chunk whose 16-deep slabs are `slab` bytes apart.
+__device__ __forceinline__ int tile_off(int row, int k, int slab) {
+    return (k >> 4) * slab + (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Stages rows [r0, r0 + rows) x k [k0, k0 + 64) of X(r,k) = X[r*sr + k*sk] (zero outside [0,R) x [0,K)).
+__device__ __forceinline__ void stage(unsigned char *dst, int slab, const __nv_bfloat16 *X, int64_t sr, int64_t sk,
+                                      int r0, int rows, int R, int k0, int K) {
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    if (sk == 1 && (sr & 7) == 0 && ((uintptr_t)X & 15) == 0 && k0 + GK <= K) {
+        // K-contiguous source: 8 elements (16 bytes) per load, one core-matrix row per store
+        for (int e = threadIdx.x; e < rows * (GK / 8); e += blockDim.x) {
+            const int r = e / (GK / 8), c = e % (GK / 8);
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (r0 + r < R) v = *reinterpret_cast<const uint4 *>(X + (int64_t)(r0 + r) * sr + k0 + 8 * c);
+            *reinterpret_cast<uint4 *>(dst + tile_off(r, 8 * c, slab)) = v;
+        }
+    } else if (sr == 1) {
+        // row-contiguous source (a transpose): consecutive threads take consecutive rows
+        for (int e = threadIdx.x; e < rows * GK; e += blockDim.x) {
+            const int k = e / rows, r = e % rows;
+            const int rr = r0 + r, kk = k0 + k;
+            *reinterpret_cast<__nv_bfloat16 *>(dst + tile_off(r, k, slab)) =
+                (rr < R && kk < K) ? X[(int64_t)rr + (int64_t)kk * sk] : zero;
+        }
+    } else {
+        for (int e = threadIdx.x; e < rows * GK; e += blockDim.x) {
+            const int r = e / GK, k = e % GK;
+            const int rr = r0 + r, kk = k0 + k;
+            *reinterpret_cast<__nv_bfloat16 *>(dst + tile_off(r, k, slab)) =
+                (rr < R && kk < K) ? X[(int64_t)rr * sr + (int64_t)kk * sk] : zero;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __nv_bfloat16 *A, int64_t sam, int64_t sak,
+                                                           const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, float *C,
+                                                           int64_t ldc, int M, int N, int K, int accumulate, unsigned *err) {
+    extern __shared__ unsigned char gsm_raw[];
+    unsigned char *gsm = reinterpret_cast<unsigned char *>(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+    const int nchunks = (K + GK - 1) / GK;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (nchunks > 0) {
+        stage(gsm, A_SLAB, A, sam, sak, m0, GM, M, 0, K);
+        stage(gsm + 4 * A_SLAB, B_SLAB, B, sbn, sbk, n0, GN, N, 0, K);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = 256, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+        unsigned char *buf = gsm + (c & 1) * STAGE_BYTES;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staged stores -> tensor core's view
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < GK / 16; ++j) {
+                const uint64_t ad = umma_desc(smem_addr(buf + j * A_SLAB));
+                const uint64_t bd = umma_desc(smem_addr(buf + 4 * A_SLAB + j * B_SLAB));
+                const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                             "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&mbar[c & 1]))
+                         : "memory");
+        }
+        if (c + 1 < nchunks) {
+            // the other buffer was read by chunk c - 1: wait for its commit before overwriting it
+            if (c >= 1) ok = __syncthreads_and(bar_wait(smem_addr(&mbar[(c - 1) & 1]), (uint32_t)(((c - 1) >> 1) & 1)));
+            if (ok) {
+                unsigned char *nb = gsm + ((c + 1) & 1) * STAGE_BYTES;
+                stage(nb, A_SLAB, A, sam, sak, m0, GM, M, (c + 1) * GK, K);
+                stage(nb + 4 * A_SLAB, B_SLAB, B, sbn, sbk, n0, GN, N, (c + 1) * GK, K);
+            }
+        }
+    }
+    // commits complete in order: the last one covers every MMA
+    if (ok && nchunks > 0)
+        ok = __syncthreads_and(bar_wait(smem_addr(&mbar[(nchunks - 1) & 1]), (uint32_t)(((nchunks - 1) >> 1) & 1)));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < GN; c0 += 32) {
+            uint32_t r[32];
+            if (nchunks > 0) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < 32; ++j) r[j] = 0u;
+            }
+            if (m < M) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int m = m0 + wm + i * 16 + g + (q >= 2 ? 8 : 0);
-                const int n = n0 + wn + j * 8 + 2 * t + (q & 1);
-                if (m < M && n < N) {
-                    float *p = C + (int64_t)m * ldc + n;
-                    *p = accumulate ? (*p + acc[i][j][q]) : acc[i][j][q];
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n < N) {
+                        float *p = C + (int64_t)m * ldc + n;
+                        const float v = __uint_as_float(r[j]);
+                        *p = accumulate ? (*p + v) : v;
+                    }
                 }
             }
+        }
+    } else if (lane == 0) {
+        atomicOr(err, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
 // z1 = x . bf16(W1)^T + b1, h1 = tanh(z1); x is [B][3] FP32, W1 [256][3] BF16.
@@ -239,9 +344,18 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 cudaError_t gemm_bf16(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B, int64_t sbk, int64_t sbn,
-                      float *C, int64_t ldc, int M, int N, int K, int accumulate, cudaStream_t s) {
-    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-    gemm_bf16_kernel<<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, accumulate);
+                      float *C, int64_t ldc, int M, int N, int K, int accumulate, unsigned *err, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    static unsigned long long attr_set = 0;  // per device: > 48 KB of dynamic shared memory opted in
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !(attr_set & (1ull << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) attr_set |= 1ull << dev;
+    }
+    dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
+    gemm_bf16_kernel<<<grid, 128, GEMM_SMEM, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, accumulate, err);
     return cudaGetLastError();
 }
 
@@ -253,7 +367,7 @@ cudaError_t forward(const Net &n, const Acts &a, const float *x, int Bn, cudaStr
     if (e != cudaSuccess) return e;
     for (int l = 1; l < 4; ++l) {
         // z_l[b][j] = sum_k bf16(h_{l-1})[b][k] bf16(W_l)[j][k]
-        e = gemm_bf16(a.hb[l - 1], HID, 1, n.wb + n.off_w[l], 1, HID, a.h[l], HID, Bn, HID, HID, 0, s);
+        e = gemm_bf16(a.hb[l - 1], HID, 1, n.wb + n.off_w[l], 1, HID, a.h[l], HID, Bn, HID, HID, 0, n.err, s);
         if (e != cudaSuccess) return e;
         bias_tanh_kernel<<<nblk(E, 256), 256, 0, s>>>(a.h[l], n.p + n.off_b[l], a.hb[l], Bn);
         e = cudaGetLastError();
@@ -273,11 +387,11 @@ cudaError_t backward(const Net &n, const Acts &a, const float *x, const float *t
     if (e != cudaSuccess) return e;
     for (int l = 3; l >= 1; --l) {
         // dW_l[j][k] = sum_b bf16(dz)[b][j] bf16(h_{l-1})[b][k]:  A(m=j, k=b) = dzb[b*HID + j], B(k=b, n=k) = hb[b*HID + k]
-        e = gemm_bf16(a.dzb, 1, HID, a.hb[l - 1], HID, 1, g + n.off_w[l], HID, HID, HID, Bn, 0, s);
+        e = gemm_bf16(a.dzb, 1, HID, a.hb[l - 1], HID, 1, g + n.off_w[l], HID, HID, HID, Bn, 0, n.err, s);
         if (e != cudaSuccess) return e;
         colsum_kernel<<<HID, 256, 0, s>>>(a.dz, g + n.off_b[l], Bn, HID);
         // dh_{l-1}[b][k] = sum_j bf16(dz)[b][j] bf16(W_l)[j][k]:  A(m=b, k=j) = dzb[b*HID + j], B(k=j, n=k) = W[j*HID + k]
-        e = gemm_bf16(a.dzb, HID, 1, n.wb + n.off_w[l], HID, 1, a.dh, HID, Bn, HID, HID, 0, s);
+        e = gemm_bf16(a.dzb, HID, 1, n.wb + n.off_w[l], HID, 1, a.dh, HID, Bn, HID, HID, 0, n.err, s);
         if (e != cudaSuccess) return e;
         tanh_bwd_kernel<<<nblk(E, 256), 256, 0, s>>>(a.dh, nullptr, nullptr, a.h[l - 1], a.dz, a.dzb, Bn, 0);
         e = cudaGetLastError();

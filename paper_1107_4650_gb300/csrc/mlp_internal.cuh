@@ -17,6 +17,7 @@ struct Net {
     float *p = nullptr;           // FP32 master parameters
     float *m = nullptr, *v = nullptr;  // Adam moments
     __nv_bfloat16 *wb = nullptr;  // BF16 copy of p
+    unsigned *err = nullptr;      // set by a GEMM whose bounded tensor-core wait ran out
     int64_t off_w[5], off_b[5];
 };
 
@@ -40,8 +41,9 @@ inline void layout(Net &n) {
     n.off_b[4] = o; o += 1;
 }
 
+// C = A . B (+ C) on the tensor cores (tcgen05, accumulator in tensor memory); see mlp.cu.
 cudaError_t gemm_bf16(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B, int64_t sbk, int64_t sbn,
-                      float *C, int64_t ldc, int M, int N, int K, int accumulate, cudaStream_t s);
+                      float *C, int64_t ldc, int M, int N, int K, int accumulate, unsigned *err, cudaStream_t s);
 cudaError_t forward(const Net &n, const Acts &a, const float *x, int Bn, cudaStream_t s);
 cudaError_t backward(const Net &n, const Acts &a, const float *x, const float *t, float *g, int Bn, cudaStream_t s);
 cudaError_t adam(const Net &n, const float *g, float lr, int64_t step, cudaStream_t s);

@@ -101,6 +101,15 @@ dirac_status stage(dirac_surrogate *s, const double *X, const double *T, int64_t
     return DIRAC_OK;
 }
 
+// Reads (and clears) the flag a GEMM sets when its bounded wait for the tensor cores ran out.
+dirac_status check_tensor_waits(dirac_surrogate *s) {
+    unsigned flag = 0;
+    SCK(s, cudaMemcpy(&flag, s->net.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (!flag) return DIRAC_OK;
+    SCK(s, cudaMemset(s->net.err, 0, sizeof(unsigned)));
+    return sfail(s, DIRAC_ERR_TIMEOUT, "a tensor-core GEMM's bounded wait ran out; results are invalid");
+}
+
 }  // namespace
 
 extern "C" {
@@ -150,6 +159,8 @@ dirac_status dirac_surrogate_create(const double lo[3], const double hi[3], uint
     if (e == cudaSuccess) e = salloc(s, &s->xb, B * 3 * sizeof(float));
     if (e == cudaSuccess) e = salloc(s, &s->tb, B * sizeof(float));
     if (e == cudaSuccess) e = salloc(s, &s->idx, B * sizeof(int));
+    if (e == cudaSuccess) e = salloc(s, &s->net.err, 16);
+    if (e == cudaSuccess) e = cudaMemset(s->net.err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost(&s->host_pinned, B * 4 * sizeof(float));
     if (e != cudaSuccess) return bail(scuda(s, e, "surrogate allocation"));
     // Xavier-uniform weights, zero biases
@@ -210,6 +221,8 @@ dirac_status dirac_surrogate_gradient(dirac_surrogate *s, const double *X, const
     SCK(s, cudaMemcpyAsync(grad_out, s->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
     SCK(s, cudaMemcpyAsync(sq.data(), s->acts.sqerr, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
     SCK(s, cudaStreamSynchronize(s->stream));
+    st = check_tensor_waits(s);
+    if (st != DIRAC_OK) return st;
     if (loss_out) {
         double L = 0;
         for (float v : sq) L += v;
@@ -289,6 +302,8 @@ dirac_status dirac_surrogate_train(dirac_surrogate *s, const double *X, const do
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     cleanup();
     if (e != cudaSuccess) return scuda(s, e, "training step");
+    dirac_status st = check_tensor_waits(s);
+    if (st != DIRAC_OK) return st;
     if (loss_out) *loss_out = last;
     return DIRAC_OK;
 }
@@ -306,7 +321,7 @@ dirac_status dirac_surrogate_predict(dirac_surrogate *s, const double *X, int64_
         SCK(s, cudaStreamSynchronize(s->stream));
         for (int b = 0; b < nb; ++b) T_out[i0 + b] = y[b];
     }
-    return DIRAC_OK;
+    return check_tensor_waits(s);
 }
 
 dirac_status dirac_klein_run_from_reduced(const double q[3], double dx, double c, double m, dirac_klein_run *run) {
