@@ -23,18 +23,19 @@ namespace {
 //
 // C[M x N] (FP32, row-major, ldc) = sum_k A(m,k) B(k,n) (+ C when accumulate), A(m,k) = A[m*sam + k*sak],
 // B(k,n) = B[k*sbk + n*sbn], BF16 operands with arbitrary strides (the backward pass reads transposes).
-// One CTA of 4 warps computes a 128 x 256 tile of C in tensor memory: K is consumed in chunks of 64,
+// One CTA of 4 warps computes a 128 x 64 tile of C in tensor memory: K is consumed in chunks of 64,
 // staged by all threads into shared memory in the canonical no-swizzle K-major layout (8-row x 16-byte
 // core matrices; K-direction core-matrix stride 128 B, 8-row-group stride 256 B; one 16-deep K slab per
 // MMA), double-buffered so the next chunk is staged while the tensor core consumes the current one.
-// One thread issues tcgen05.mma (M = 128, N = 256, K = 16, BF16 x BF16 -> FP32) and commits each chunk
+// One thread issues tcgen05.mma (M = 128, N = 64, K = 16, BF16 x BF16 -> FP32) and commits each chunk
 // to an mbarrier; every wait is bounded (about one second of the global timer) and a timeout sets
-// *err instead of hanging.  The accumulator (256 TMEM columns) is read back with tcgen05.ld, each warp
-// its 32 lanes = 32 rows of the tile.
-constexpr int GM = 128, GN = 256, GK = 64;
+// *err instead of hanging.  The accumulator (64 TMEM columns) is read back with tcgen05.ld, each warp
+// its 32 lanes = 32 rows of the tile.  The 64-wide N tile gives a 256 x 256 product 8 CTAs: these GEMMs
+// are small, so the time goes to staging operands, which more CTAs run in parallel.
+constexpr int GM = 128, GN = 64, GK = 64;
 constexpr int A_SLAB = GM * 16 * 2;  // bytes of one 16-deep K slab of the A tile (4 KB)
-constexpr int B_SLAB = GN * 16 * 2;  // (8 KB)
-constexpr int STAGE_BYTES = 4 * A_SLAB + 4 * B_SLAB;  // 48 KB per K chunk
+constexpr int B_SLAB = GN * 16 * 2;  // (2 KB)
+constexpr int STAGE_BYTES = 4 * A_SLAB + 4 * B_SLAB;  // 24 KB per K chunk
 constexpr int GEMM_SMEM = 2 * STAGE_BYTES + 1024;     // two stages + alignment slack
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -84,8 +85,17 @@ __device__ __forceinline__ void stage(unsigned char *dst, int slab, const __nv_b
             if (r0 + r < R) v = *reinterpret_cast<const uint4 *>(X + (int64_t)(r0 + r) * sr + k0 + 8 * c);
             *reinterpret_cast<uint4 *>(dst + tile_off(r, 8 * c, slab)) = v;
         }
+    } else if (sr == 1 && (sk & 7) == 0 && ((uintptr_t)X & 15) == 0 && r0 + rows <= R && k0 + GK <= K) {
+        // row-contiguous source (a transpose), whole tile inside: 8 rows of one k per 16-byte load
+        for (int e = threadIdx.x; e < (rows / 8) * GK; e += blockDim.x) {
+            const int k = e / (rows / 8), r8 = 8 * (e % (rows / 8));
+            const uint4 v = *reinterpret_cast<const uint4 *>(X + (int64_t)(r0 + r8) + (int64_t)(k0 + k) * sk);
+            const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) *reinterpret_cast<__nv_bfloat16 *>(dst + tile_off(r8 + i, k, slab)) = h[i];
+        }
     } else if (sr == 1) {
-        // row-contiguous source (a transpose): consecutive threads take consecutive rows
+        // row-contiguous source at the edges: consecutive threads take consecutive rows
         for (int e = threadIdx.x; e < rows * GK; e += blockDim.x) {
             const int k = e / rows, r = e % rows;
             const int rr = r0 + r, kk = k0 + k;
@@ -102,7 +112,7 @@ __device__ __forceinline__ void stage(unsigned char *dst, int slab, const __nv_b
     }
 }
 
-__global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __nv_bfloat16 *A, int64_t sam, int64_t sak,
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *A, int64_t sam, int64_t sak,
                                                            const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, float *C,
                                                            int64_t ldc, int M, int N, int K, int accumulate, unsigned *err) {
     extern __shared__ unsigned char gsm_raw[];
@@ -113,7 +123,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __nv_bfloat16 *
     const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
     const int nchunks = (K + GK - 1) / GK;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(&tmem_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __nv_bfloat16 *
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = 256, M = 128
+    // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = 64, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
@@ -205,7 +215,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __nv_bfloat16 *
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 // z1 = x . bf16(W1)^T + b1, h1 = tanh(z1); x is [B][3] FP32, W1 [256][3] BF16.
