@@ -377,6 +377,39 @@ def main():
             "fp64_instr_per_point_step": FP64_INSTR_PER_POINT_STEP_2D_FIELD,
             "frac_of_measured_fp64_issue": FP64_INSTR_PER_POINT_STEP_2D_FIELD * vf / world / 1e12 / FP64_ISSUE_PEAK_MEASURED}
 
+    # ---------------------------------------------------------------- 2-D second order and characteristic shifts
+    if not args.no_field:
+        for vname, kw, per_step in (("fp64_strang2d", dict(splitting=D.DIRAC_STRANG), 2),
+                                    ("fp64_shift2", dict(char_shift=2), 2), ("fp64_shift4", dict(char_shift=4), 4)):
+            cfgv = D.make_config((args.side, 1, args.side), x_min=(x_min, 0.0, z_min), flux_face=face,
+                                 stream=stream.cuda_stream, device=local, **kw)
+            hv = D.dirac_create_grid(cfgv)
+            D.dirac_set_potential(hv, V, D.DIRAC_V_X_ONLY)
+            D.dirac_set_state(hv, dev_state)
+            D.dirac_autotune(hv)
+            nv = 400
+            D.dirac_step(hv, 64)  # warm-up
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            ev0.record(stream)
+            D.dirac_step(hv, nv)
+            ev1.record(stream)
+            stream.synchronize()
+            tv = max_over_ranks(ev0.elapsed_time(ev1))
+            iv = D.dirac_get_info(hv)
+            D.dirac_destroy(hv)
+            vv = ncell * nv * world / (tv / 1e3)
+            instr = 80 if vname == "fp64_strang2d" else FP64_INSTR_PER_POINT_STEP_2D  # Strang: 4 sweeps + phase
+            variants[vname] = {
+                "value": vv, "unit": "point-steps/s", "steps": nv, "ms_per_step": tv / nv,
+                "physical_time_per_step_dx_over_c": per_step, "first_order_equivalent_point_steps_per_s": vv * per_step,
+                "steps_per_launch": iv["steps_per_launch"], "points_per_lane": iv["points_per_lane"],
+                "workload": "the 2048^2 Klein FP64 grid, %s" % ("second-order (Strang) steps of 2 dx/c"
+                                                             if vname == "fp64_strang2d" else
+                                                             "first-order steps with c dt = %d dx" % per_step),
+                "fp64_instr_per_point_step": instr,
+                "frac_of_measured_fp64_issue": instr * vv / world / 1e12 / FP64_ISSUE_PEAK_MEASURED}
+
     # ---------------------------------------------------------------- 3-D soft-Coulomb grid (first and second order)
     if not args.no_3d:
         n3 = args.side3d
