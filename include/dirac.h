@@ -284,7 +284,9 @@ dirac_status dirac_batch_klein(const dirac_klein_run *runs, int nruns, const dir
 /* ---------------------------------------------------------------------------------------------
  * Transmission surrogate: an MLP 3 -> 256 -> 256 -> 256 -> 256 -> 1 (tanh hidden layers, sigmoid output)
  * with BF16 weights and FP32 accumulation, trained on GPU by the library's own forward, backward and
- * Adam kernels on transmissions the solver produced.  Inputs are reduced run parameters
+ * Adam kernels on transmissions the solver produced.  The hidden-layer products run on the tensor cores
+ * (tcgen05, accumulator in tensor memory); train, predict and gradient return DIRAC_ERR_TIMEOUT if one
+ * of their bounded (about one second) waits for the tensor cores ran out.  Inputs are reduced run parameters
  * q = (V0 / m c^2, p0 / m c, width / dx), mapped linearly from the training box [lo, hi] to [-1, 1]^3.
  * Queries outside the box are answered by the batched solver (the surrogate's fallback).
  * --------------------------------------------------------------------------------------------- */
