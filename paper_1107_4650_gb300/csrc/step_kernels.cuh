@@ -328,8 +328,6 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
         xin[j] = (x >= 0 && x < nx);
         xl[j] = per ? pmod(x, nx) : min(max(x, (int64_t)0), nx - 1);
     }
-    // every cell of the strip inside the grid (warp-uniform): in-grid rows then need no ghost-zero masking
-    const bool strip_in = xa >= 0 && xa + 32 * P <= nx;
     // phase coefficients per x column (mode 0, x-only table)
     Cx<T> pu[P], pd[P];
     if (MODE != 1 && !a.full_table) {
@@ -490,23 +488,15 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 if (has_face && q - 1 >= r_begin && q - 1 < r_end)
                     flux_row<T, P>(lu14, lu23, w14, w23, face_j, face_lane, lane, q - 1 - r_begin, q - 1 == r_end - 1,
                                    gsm + lev * 8 * 32, 2.0, facc[lev]);
-                const bool unmasked = per || (zrow_ok && strip_in);
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
+                    const bool keep = per || (zrow_ok && xin[j]);
                     const Cx<T> b0 = cadd(lu14[j], rw14[j]), b3 = csub(lu14[j], rw14[j]);
                     const Cx<T> b1 = cadd(lu23[j], rw23[j]), b2 = csub(lu23[j], rw23[j]);
-                    if (unmasked) {
-                        st[j][0] = b0;
-                        st[j][1] = b1;
-                        st[j][2] = b2;
-                        st[j][3] = b3;
-                    } else {
-                        const bool keep = zrow_ok && xin[j];
-                        st[j][0] = keep ? b0 : Cx<T>{T(0), T(0)};
-                        st[j][1] = keep ? b1 : Cx<T>{T(0), T(0)};
-                        st[j][2] = keep ? b2 : Cx<T>{T(0), T(0)};
-                        st[j][3] = keep ? b3 : Cx<T>{T(0), T(0)};
-                    }
+                    st[j][0] = keep ? b0 : Cx<T>{T(0), T(0)};
+                    st[j][1] = keep ? b1 : Cx<T>{T(0), T(0)};
+                    st[j][2] = keep ? b2 : Cx<T>{T(0), T(0)};
+                    st[j][3] = keep ? b3 : Cx<T>{T(0), T(0)};
                 }
                 continue;
             }
@@ -608,14 +598,9 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                     UB[lev][j][1] = U23;
                 }
                 if (need_out) {
-                    if (per || (out_row_ok && strip_in)) {
+                    const bool keep = per || (out_row_ok && xin[j]);
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) st[j][c] = o[c];
-                    } else {
-                        const bool keep = out_row_ok && xin[j];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) st[j][c] = keep ? o[c] : Cx<T>{T(0), T(0)};
-                    }
+                    for (int c = 0; c < 4; ++c) st[j][c] = keep ? o[c] : Cx<T>{T(0), T(0)};
                 } else {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) st[j][c] = Cx<T>{T(0), T(0)};
