@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-field", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-paper-klein", action="store_true")
     ap.add_argument("--side3d", type=int, default=384)
     ap.add_argument("--batch-runs", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true")
@@ -458,6 +459,15 @@ def main():
                     entry["effective_hbm_frac"] = bytes3 * v3 / world / 1e9 / hbm_peak
                 variants["%s_3d_%s" % (pname, sname)] = entry
             del dev3
+
+    # ---------------------------------------------------------------- the paper's own 2-D Klein run, FP32
+    if not args.no_paper_klein:
+        from paper_1107_4650_gb300 import paper_klein2d as PK
+        pk = PK.run("fp32", stream=stream, device=local)
+        variants["paper_klein2d_fp32"] = {
+            "value": pk["point_steps_per_s"] * world, "unit": "point-steps/s", "workload": pk["run"],
+            "T_flux": pk["T_flux"], "R_left": pk["R_left"], "paper_T_R": [0.2407, 0.7593],
+            "gpu_s": pk["gpu_ms"] / 1e3, "paper_wall_s": 22.0 * 3600.0, "paper_processes": 256}
 
     # ---------------------------------------------------------------- batched ensemble (FP32)
     if not args.no_batch:
