@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-field", action="store_true")
+    ap.add_argument("--no-2d-variants", action="store_true", help="skip the 2-D Strang and shift legs")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-paper-klein", action="store_true")
     ap.add_argument("--side3d", type=int, default=384)
@@ -379,7 +380,7 @@ def main():
             "frac_of_measured_fp64_issue": FP64_INSTR_PER_POINT_STEP_2D_FIELD * vf / world / 1e12 / FP64_ISSUE_PEAK_MEASURED}
 
     # ---------------------------------------------------------------- 2-D second order and characteristic shifts
-    if not args.no_field:
+    if not args.no_2d_variants:
         for vname, kw, per_step in (("fp64_strang2d", dict(splitting=D.DIRAC_STRANG), 2),
                                     ("fp64_shift2", dict(char_shift=2), 2), ("fp64_shift4", dict(char_shift=4), 4)):
             cfgv = D.make_config((args.side, 1, args.side), x_min=(x_min, 0.0, z_min), flux_face=face,
