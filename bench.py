@@ -43,9 +43,9 @@ FP64_INSTR_PER_POINT_STEP_2D = 48  # 32 DADD + 8 DMUL + 8 DFMA: what the FP64 pi
 FP64_INSTR_PER_POINT_STEP_2D_FIELD = 80  # with a vector potential: 32 DADD + 12 complex multiply-adds of 4 DFMA
 # FP64 issue roof: the recipe's nominal 1.25 TFLOP/s counts a DFMA as 2 flops -> 0.625 T FP64 instructions/s
 # (DADD and DMUL issue at the DFMA rate).  Measured on this machine's GB300 with an FMA/ADD throughput probe:
-# 0.5285 T lane-instructions/s (1.68 per SM per clock at 2.07 GHz, 152 SMs).
+# 0.5276 T lane-instructions/s (1.68 per SM per clock at 2.07 GHz, 152 SMs; `python -m paper_1107_4650_gb300.peak_probe`).
 FP64_ISSUE_PEAK_NOMINAL = 0.625
-FP64_ISSUE_PEAK_MEASURED = 0.5285
+FP64_ISSUE_PEAK_MEASURED = 0.5276
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel on the 2048^2 workload, keyed
 # by (steps per launch, points per lane) of the captured variant (profiles/step_kernel_fp64_klein2048.md,
 # profiles/step_kernel_fp32_klein2048.md).  A variant without a capture reports null.
