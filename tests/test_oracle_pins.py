@@ -658,3 +658,18 @@ def test_absorber_step_equals_explicit_matrices(oracle_mod, periodic):
     want = damp @ step @ damp @ step @ psi.reshape(-1)
     assert np.max(np.abs(got.reshape(-1) - want)) < 1e-14
     assert a[0] < a[1] < a[2] < 1.0 and a[3] == 1.0 and a[-1] < a[-2]
+
+
+def test_packet_averaged_transmission_limits():
+    """The momentum average of Eq. trans_co tends to the plane-wave value for a wide packet, and equals a
+    direct quadrature of the same Gaussian weight for a narrow one."""
+    k0, V0, L = 100.0, 2 * C * C + 1e4, 0.0025
+    wide = klein.packet_averaged_transmission(k0, 50.0, V0, L)
+    assert abs(wide - klein.transmission_closed_form(k0, V0, L)) < 1e-6
+    width = 0.05
+    from scipy.integrate import quad
+    sig = 1.0 / (2 * width)
+    num = quad(lambda p: np.exp(-0.5 * ((p - k0) / sig) ** 2) * klein.transmission_closed_form(p, V0, L),
+               k0 - 6 * sig, k0 + 6 * sig, limit=200)[0]
+    den = quad(lambda p: np.exp(-0.5 * ((p - k0) / sig) ** 2), k0 - 6 * sig, k0 + 6 * sig)[0]
+    assert abs(klein.packet_averaged_transmission(k0, width, V0, L) - num / den) < 1e-4
