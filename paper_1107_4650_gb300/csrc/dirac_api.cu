@@ -112,6 +112,10 @@ int sweep_mode(const dirac_grid *g) {
     return g->avec.empty() ? 0 : 3;
 }
 int levels(const dirac_grid *g, int K) { return strang(g) ? 2 * K : K; }
+// a uniform vector potential is set (2-D: mode 3; 3-D: the fused pass with the phase matrix)
+bool field_on(const dirac_grid *g) { return !g->avec.empty(); }
+// 3-D steps run as the fused single pass (chosen by the plan, or required by a vector potential)
+bool fused_pass(const dirac_grid *g) { return ndim_of(g) == 3 && (g->plan.fused3d || field_on(g)); }
 // x halo cells of a strip (each side) for K steps per launch
 int halo_of(const dirac_grid *g, int K) { return sweep_mode(g) == 4 ? char_shift(g) : levels(g, K); }
 double cell_volume(const dirac_grid *g) {
@@ -140,7 +144,7 @@ dirac_status ensure_table(dirac_grid *g, size_t bytes) {
 
 dirac_status upload_table(dirac_grid *g, const double *V, int layout, int64_t count) {
     // with a vector potential the mass term lives in the U matrix and the table holds exp(-i V dt) alone
-    const double mu = sweep_mode(g) == 3 ? 0.0 : g->cfg.m * g->cfg.c * g->cfg.c * g->dt;
+    const double mu = field_on(g) ? 0.0 : g->cfg.m * g->cfg.c * g->cfg.c * g->dt;
     const double scale = scale_of(g);
     const int64_t nentries = (layout == DIRAC_V_FULL) ? g->ncells : g->cfg.n[0];
     (void)count;
@@ -242,8 +246,7 @@ int axis_blocks(const dirac_grid *g) {
 dirac_status ensure_flux_part(dirac_grid *g) {
     const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
     size_t need = (size_t)8 * planes * std::max<int64_t>(g->plan.nsegs, 1);
-    if (ndim_of(g) == 3 && g->plan.fused3d)
-        need = std::max(need, (size_t)(g->plan.f_nzsegs * g->plan.f_nytiles * g->plan.f_warps));
+    if (fused_pass(g)) need = std::max(need, (size_t)(g->plan.f_nzsegs * g->plan.f_nytiles * g->plan.f_warps));
     if (sweep_mode(g) == 6) need = std::max(need, (size_t)axis_blocks(g));
     if (need <= g->flux_part_cap) return DIRAC_OK;
     if (g->flux_part) {
@@ -307,7 +310,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
         }
         return DIRAC_OK;
     }
-    if (mode == 1 && p.fused3d) {
+    if (mode == 1 && fused_pass(g)) {
         a.nsegs = p.f_nzsegs * p.f_nytiles * p.f_warps;  // flux parts of the fused pass
         a.nplanes = 1;
         cudaError_t e = launch_fused3d(a, g->fp32, p.f_warps, g->cfg.n[1], g->cfg.n[2], p.f_nstrips, p.f_nytiles,
@@ -342,7 +345,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
 
 int block_flips(const dirac_grid *g) {
     if (sweep_mode(g) == 6) return 0;  // eight sweeps per step: parity returns
-    return (ndim_of(g) == 3 && !g->plan.fused3d) ? 0 : 1;
+    return (ndim_of(g) == 3 && !fused_pass(g)) ? 0 : 1;
 }
 
 dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
@@ -377,14 +380,14 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
 
 int64_t launches_per_block(const dirac_grid *g) {
     if (sweep_mode(g) == 6) return 8;
-    return 1 + ((ndim_of(g) == 3 && !g->plan.fused3d) ? 1 : 0);
+    return 1 + ((ndim_of(g) == 3 && !fused_pass(g)) ? 1 : 0);
 }
 
 dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
     const int K = (ndim_of(g) == 3) ? 1 : g->plan.K;
     int64_t blocks = nsteps / K;
     int64_t rem = nsteps % K;
-    const bool field = sweep_mode(g) == 3;
+    const bool field = field_on(g);
     if (field && !g->tuning && g->step + nsteps > (int64_t)(g->avec.size() / 3))
         return fail(g, DIRAC_ERR_ARG, "the vector-potential table ends before step " + std::to_string(g->step + nsteps));
     int64_t t = g->step;  // step index of the next launch (selects the field's table row)
@@ -715,13 +718,13 @@ dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, in
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
     const bool clear = !A_tilde || nsteps_table == 0;
-    if (!clear && (ndim_of(g) != 2 || strang(g) || char_shift(g) > 1))
-        return fail(g, DIRAC_ERR_ARG, "a vector potential is implemented for 2-D first-order (DIRAC_LIE) grids with char_shift 1");
+    if (!clear && (strang(g) || char_shift(g) > 1))
+        return fail(g, DIRAC_ERR_ARG, "a vector potential is implemented for first-order (DIRAC_LIE) grids with char_shift 1");
     if (!clear)
         for (int64_t i = 0; i < 3 * nsteps_table; ++i)
             if (!std::isfinite(A_tilde[i])) return fail(g, DIRAC_ERR_ARG, "vector-potential table holds a non-finite value");
     CK(g, cudaSetDevice(g->cfg.device));
-    const int mode_before = sweep_mode(g);
+    const bool field_before = field_on(g);
     if (clear) {
         g->avec.clear();
     } else {
@@ -744,7 +747,7 @@ dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, in
         CK(g, cudaStreamSynchronize(g->stream));
         g->avec.assign(A_tilde, A_tilde + 3 * nsteps_table);
     }
-    if (sweep_mode(g) != mode_before) {
+    if (field_on(g) != field_before) {
         default_plan(g);
         dirac_status st = ensure_flux_part(g);
         if (st != DIRAC_OK) return st;
@@ -871,8 +874,8 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
                                         DIRAC_PLAN_FIELD_2D, DIRAC_PLAN_SHIFT_2D, DIRAC_PLAN_3D_FUSED,
                                         DIRAC_PLAN_3D_STRANG};
     const int mode = sweep_mode(g);
-    info->plan = (mode == 1 && p.fused3d) ? DIRAC_PLAN_3D_FUSED : plan_of_mode[mode];
-    if (g->cfg.ndim == 3 && p.fused3d) {
+    info->plan = (mode == 1 && fused_pass(g)) ? DIRAC_PLAN_3D_FUSED : plan_of_mode[mode];
+    if (fused_pass(g)) {
         info->points_per_lane = 1;
         info->launch_warps = p.f_nstrips * p.f_nytiles * p.f_nzsegs * p.f_warps;
         info->strip_width = 30;
@@ -894,8 +897,9 @@ dirac_status dirac_autotune(dirac_grid *g) {
     };
     std::vector<Cand> cands;
     if (g->cfg.ndim == 3) {
-        for (int P : {1, 2, 4})
-            for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});
+        if (!field_on(g))  // with a vector potential only the fused pass applies the phase matrix
+            for (int P : {1, 2, 4})
+                for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});
         for (int fw : {8, 16}) cands.push_back({1, 2, 4, 16, fw});
     } else if (sweep_mode(g) == 4) {
         for (int P : {1, 2})

@@ -1,4 +1,5 @@
-// Instantiations of the fused 3-D step kernel (8 or 16 warps per block: 6 or 14 owned rows per tile).
+// Instantiations of the fused 3-D step kernel (8 or 16 warps per block: 6 or 14 owned rows per tile; with
+// and without a uniform vector potential).
 #include "fused3d_kernels.cuh"
 
 namespace dirac {
@@ -13,8 +14,14 @@ cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int64_t ny, 
     A.nytiles = nytiles;
     A.nzsegs = nzsegs;
     A.zseg_h = zseg_h;
-    if (warps == 16) return fp32 ? launch_fused3d_one<float, 16>(A, s) : launch_fused3d_one<double, 16>(A, s);
-    if (warps == 8) return fp32 ? launch_fused3d_one<float, 8>(A, s) : launch_fused3d_one<double, 8>(A, s);
+    const bool field = a.ucoef != nullptr && a.ucoef_n > 0;
+    if (field) {
+        if (warps == 16) return fp32 ? launch_fused3d_one<float, 16, true>(A, s) : launch_fused3d_one<double, 16, true>(A, s);
+        if (warps == 8) return fp32 ? launch_fused3d_one<float, 8, true>(A, s) : launch_fused3d_one<double, 8, true>(A, s);
+    } else {
+        if (warps == 16) return fp32 ? launch_fused3d_one<float, 16, false>(A, s) : launch_fused3d_one<double, 16, false>(A, s);
+        if (warps == 8) return fp32 ? launch_fused3d_one<float, 8, false>(A, s) : launch_fused3d_one<double, 8, false>(A, s);
+    }
     return cudaErrorInvalidValue;
 }
 

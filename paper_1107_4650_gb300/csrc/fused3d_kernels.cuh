@@ -13,6 +13,9 @@
 // the FP64 result is the same bit for bit.  Face flux: the lanes holding cells face-1 and face of owned
 // rows and planes add 1/2 (|u14|^2+|u23|^2) and subtract 1/2 (|w14|^2+|w23|^2) of the state entering the x
 // sweep, to a storage-type partial folded into FP64 every 32 planes.
+// FIELD: a uniform vector potential; the phase is the 4 x 4 matrix U(step) exp(-i V dt) of Eq. sol_dis_4
+// (table entry g = exp(-i V dt) / 8 times each entry of U, then the column-ordered fma chains of the 2-D
+// kernel), one launch = one step whose index selects the row of the U table.
 #pragma once
 
 #include "step_kernels.cuh"
@@ -25,7 +28,7 @@ struct Fused3DArgs {
     int64_t nstrips, nytiles, nzsegs, zseg_h;
 };
 
-template <typename T, int W>
+template <typename T, int W, bool FIELD>
 __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A) {
     constexpr int H = W - 2;
     const SweepArgs &a = A.s;
@@ -54,6 +57,12 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
 
     Cx<T> pu, pd;
     if (!a.full_table) load_tab(tab + xl * 4, pu, pd);
+    Cx<T> UM[FIELD ? 6 : 1];  // entries of U for this launch's step: Dup, Ddn, Ez, -Ez, Ep, Em
+    if (FIELD) {
+        const double *u = a.ucoef + (a.step0 % a.ucoef_n) * 12;
+#pragma unroll
+        for (int e = 0; e < (FIELD ? 6 : 1); ++e) UM[e] = Cx<T>{(T)__ldg(u + 2 * e), (T)__ldg(u + 2 * e + 1)};
+    }
     const int64_t face = a.flux_face;
     const bool face_lane = owned_row && face >= x_own0 && face < x_own1 && (x == face - 1 || x == face);
     double facc = 0.0;
@@ -141,10 +150,25 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
                 o[1] = cadd(UA[1], W24);
                 o[3] = csub(W24, UA[1]);
                 const Cx<T> qu = a.full_table ? tu : pu, qd = a.full_table ? td : pd;
-                o[0] = cmulp(o[0], qu);
-                o[1] = cmulp(o[1], qu);
-                o[2] = cmulp(o[2], qd);
-                o[3] = cmulp(o[3], qd);
+                if (FIELD) {
+                    Cx<T> m6[FIELD ? 6 : 1];
+#pragma unroll
+                    for (int e = 0; e < (FIELD ? 6 : 1); ++e) m6[e] = cmulp(UM[e], qu);
+                    const Cx<T> z0 = {T(0), T(0)};
+                    const Cx<T> n0 = cmac(cmac(cmac(z0, o[0], m6[0]), o[2], m6[2]), o[3], m6[4]);
+                    const Cx<T> n1 = cmac(cmac(cmac(z0, o[1], m6[0]), o[2], m6[5]), o[3], m6[3]);
+                    const Cx<T> n2 = cmac(cmac(cmac(z0, o[0], m6[2]), o[1], m6[4]), o[2], m6[1]);
+                    const Cx<T> n3 = cmac(cmac(cmac(z0, o[0], m6[5]), o[1], m6[3]), o[3], m6[1]);
+                    o[0] = n0;
+                    o[1] = n1;
+                    o[2] = n2;
+                    o[3] = n3;
+                } else {
+                    o[0] = cmulp(o[0], qu);
+                    o[1] = cmulp(o[1], qu);
+                    o[2] = cmulp(o[2], qd);
+                    o[3] = cmulp(o[3], qd);
+                }
                 if (x >= x_own0 && x < x_own1) store_pt(out + ((zo * ny + y) * nx + x) * 8, o);
             }
             UA[0] = UB[0];
@@ -162,7 +186,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
     if (face >= 0) finish_flux<1>(a);
 }
 
-template <typename T, int W>
+template <typename T, int W, bool FIELD>
 static cudaError_t launch_fused3d_one(const Fused3DArgs &A, cudaStream_t s) {
     const int64_t blocks = A.nstrips * A.nytiles * A.nzsegs;
     if (blocks <= 0) return cudaSuccess;
@@ -171,11 +195,11 @@ static cudaError_t launch_fused3d_one(const Fused3DArgs &A, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 64 || !(done & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(fused3d_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(fused3d_kernel<T, W, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         if (dev < 64) done |= 1ull << dev;
     }
-    fused3d_kernel<T, W><<<(unsigned)blocks, 32 * W, smem, s>>>(A);
+    fused3d_kernel<T, W, FIELD><<<(unsigned)blocks, 32 * W, smem, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -861,3 +861,57 @@ def test_paper_klein_solver_value_in_1d_reduction(D):
     assert abs(T - g["T_2d_solver"]) < 1.5e-4 and abs(R - g["R_2d_solver"]) < 1.5e-4, (T, R)
     assert abs(obs["norm_right"] / n0 - T) < 1e-6          # nothing re-crossed the face
     assert klein.transmission_closed_form(k0, V0, L) - T > 0.02  # the analytic value is not what the mesh gives
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (40, 13, 9)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("full", [False, True])
+def test_vector_potential_3d_bit_exact(D, shape, periodic, full):
+    """3-D first-order steps in a uniform vector potential (the fused pass with the phase matrix) against the
+    oracle, bit for bit, with a step counter starting inside the table."""
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx + ny + nz)
+    V = np.random.default_rng(ny).uniform(-4e4, 4e4, nx * ny * nz if full else nx)
+    At = _field_table(12, nz, scale=1.5)
+    want, _ = oracle.step(psi, 3, 1.0, C, DX, 5, V=V, periodic=periodic, A_tilde=At, step0=3)
+    cfg = D.make_config((nx, ny, nz), ndim=3, boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_vector_potential(h, At)
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL if full else D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi)
+        D.dirac_set_counters(h, 3, 0.0)
+        D.dirac_step(h, 5)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    assert info["plan"] == D.DIRAC_PLAN_3D_FUSED
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+def test_vector_potential_3d_fp32_and_autotune(D):
+    nx, ny, nz = 64, 30, 24
+    psi = W.random_state(nz, ny, nx, seed=99)
+    V = np.random.default_rng(98).uniform(-4e4, 4e4, nx * ny * nz)
+    At = _field_table(40, 97, scale=1.0)
+    want, _ = oracle.step(psi, 3, 1.0, C, DX, 20, V=V, A_tilde=At)
+    for fp32 in (False, True):
+        cfg = D.make_config((nx, ny, nz), ndim=3, precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64)
+        h = D.dirac_create_grid(cfg)
+        dt = np.complex64 if fp32 else np.complex128
+        try:
+            D.dirac_set_vector_potential(h, At)
+            D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+            D.dirac_set_state(h, np.ascontiguousarray(psi.astype(dt)))
+            D.dirac_autotune(h)
+            D.dirac_step(h, 20)
+            got = np.empty(psi.shape, dtype=dt)
+            D.dirac_get_state(h, got)
+        finally:
+            D.dirac_destroy(h)
+        if fp32:
+            assert rel_l2(got.astype(np.complex128), want) < 2e-5
+        else:
+            assert _bits_equal(got, want)
