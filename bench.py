@@ -49,8 +49,8 @@ FP64_ISSUE_PEAK_MEASURED = 0.5276
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel on the 2048^2 workload, keyed
 # by (steps per launch, points per lane) of the captured variant (profiles/step_kernel_fp64_klein2048.md,
 # profiles/step_kernel_fp32_klein2048.md).  A variant without a capture reports null.
-MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": {(1, 2): 277.570816e6 + 216.754944e6},
-                               "fp32": {(2, 2): 147.689984e6 + 85.383424e6}}
+MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": {(1, 2): 277.515264e6 + 216.816896e6},
+                               "fp32": {(2, 2): 147.680256e6 + 85.511168e6}}
 
 
 def parse():
