@@ -915,3 +915,22 @@ def test_vector_potential_3d_fp32_and_autotune(D):
             assert rel_l2(got.astype(np.complex128), want) < 2e-5
         else:
             assert _bits_equal(got, want)
+
+
+def test_zone_edge_massless_packet_moves_forward_at_c(D):
+    """No fermion doubling (Sec. 3): a massless right-moving packet (psi1 = psi4) carried at k dx = 0.9 pi, where a
+    central-difference scheme would reverse its group velocity (d/dk sin(k dx) < 0), moves by exactly one cell per
+    step in +x on the GPU, bit-exactly as the oracle does."""
+    nx, nsteps = 512, 50
+    x = np.arange(nx) * DX
+    env = np.exp(-((np.arange(nx) - 150.0) ** 2) / (4 * 10.0 ** 2)) * np.exp(1j * 0.9 * np.pi * np.arange(nx))
+    psi = np.zeros((1, 1, nx, 4), complex)
+    psi[0, 0, :, 0] = env
+    psi[0, 0, :, 3] = env
+    psi /= np.sqrt((np.abs(psi) ** 2).sum() * DX * DX)
+    want, _ = oracle.step(psi, 2, 0.0, C, DX, nsteps, periodic=True)
+    got, obs, _ = run_gpu(D, psi, 2, nsteps, periodic=True, m=0.0, x_min=(0.0, 0.0, 0.0))
+    assert _bits_equal(got, want)
+    assert np.allclose(np.abs(got[0, 0, :, 0]), np.abs(np.roll(psi[0, 0, :, 0], nsteps)), atol=1e-14)
+    c0 = (x * (np.abs(psi) ** 2).sum(axis=(0, 1, 3))).sum() / (np.abs(psi) ** 2).sum()
+    assert abs(obs["centroid"][0] - DX / 2 - (c0 + nsteps * DX)) < 1e-9 * DX
