@@ -189,18 +189,21 @@ def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
 
 
 def step_strang2d(psi, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False,
-                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1):
+                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1, A_tilde=None, step0: int = 0):
     """nsteps second-order (Strang) steps in the x-z plane (Sec. 2.4): x, z, phase(dt), z, x with
-    dt = 2 dx / c.  Returns (psi_out, flux_cum) as step()."""
+    dt = 2 dx / c.  A_tilde / step0: a uniform vector potential as in step() (the phase matrix over dt).
+    Returns (psi_out, flux_cum) as step()."""
     out = _as_state(psi)
     if out.shape[1] != 1:
         raise ValueError("Strang steps are 2-D (ny = 1)")
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    with _Shift(shift):
+    with _Shift(shift), _VectorPotential(A_tilde, step0):
         rc = _load().oracle_step_strang2d(out.ctypes.data, _dims(out), int(bool(periodic)), float(m), float(c),
                                           float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
                                           int(flux_face), ctypes.addressof(fc))
+    if rc == -2:
+        raise ValueError("the vector-potential table ends before the last step")
     if rc != 0:
         raise MemoryError("oracle_step_strang2d")
     return out, fc.value

@@ -301,7 +301,8 @@ int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double 
 }
 
 /* nsteps steps of the second-order (Strang) splitting of Sec. 2.4 in the x-z plane: with B omitted and
- * consecutive A steps merged, one step is A(dt/2) C(dt/2) D(dt) C(dt/2) A(dt/2).  Each half-step sweep is
+ * consecutive A steps merged, one step is A(dt/2) C(dt/2) D(dt) C(dt/2) A(dt/2) (D with the full phase
+ * matrix when a vector potential is set: row step0 + s of its table is the integral over the whole step).  Each half-step sweep is
  * the one-cell characteristic shift when c dt/2 = dx, so dt = 2 dx / c here.  The face flux is added at
  * both x sweeps of a step. */
 int oracle_step_strang2d(double *psi, const int64_t n[3], int periodic, double m, double c, double dx,
@@ -312,7 +313,13 @@ int oracle_step_strang2d(double *psi, const int64_t n[3], int periodic, double m
         if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
         if (oracle_sweep(psi, n, 0, periodic)) return -1;
         if (oracle_sweep(psi, n, 2, periodic)) return -1;
-        oracle_phase(psi, n, m, c, dt, V, layout);
+        if (g_avec) {  /* uniform vector potential: the full phase matrix over the whole step dt */
+            const int64_t t = g_avec_step0 + s;
+            if (t < 0 || t >= g_avec_n) return -2;
+            oracle_phase_A(psi, n, m, c, dt, V, layout, g_avec + 3 * t);
+        } else {
+            oracle_phase(psi, n, m, c, dt, V, layout);
+        }
         if (oracle_sweep(psi, n, 2, periodic)) return -1;
         if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
         if (oracle_sweep(psi, n, 0, periodic)) return -1;

@@ -673,3 +673,24 @@ def test_packet_averaged_transmission_limits():
                k0 - 6 * sig, k0 + 6 * sig, limit=200)[0]
     den = quad(lambda p: np.exp(-0.5 * ((p - k0) / sig) ** 2), k0 - 6 * sig, k0 + 6 * sig)[0]
     assert abs(klein.packet_averaged_transmission(k0, width, V0, L) - num / den) < 1e-4
+
+
+def test_strang_with_vector_potential_equals_matrix_product(oracle_mod):
+    """A 2-D Strang step in a uniform field = S_x S_z (phase matrix over dt = 2 dx / c with the step's field
+    integral) S_z S_x, the phase matrix from scipy's matrix exponential."""
+    shape = (6, 1, 5)
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=61)
+    V = np.random.default_rng(62).uniform(-3e4, 3e4, nx)
+    At = np.random.default_rng(63).uniform(-1.2, 1.2, (3, 3))
+    got, _ = oracle.step_strang2d(psi, M, C, W.DX_DEFAULT, 2, V=V, periodic=True, A_tilde=At, step0=1)
+    Sx = A.sweep_matrix(shape, 0, True)
+    Sz = A.sweep_matrix(shape, 2, True)
+    dt = 2 * W.DX_DEFAULT / C
+    want = psi.reshape(-1)
+    for a in At[1:3]:
+        Dm = np.zeros((4 * nx * nz, 4 * nx * nz), complex)
+        for cell in range(nx * nz):
+            Dm[4 * cell:4 * cell + 4, 4 * cell:4 * cell + 4] = A.phase_matrix_A_cell(M, C, dt, V[cell % nx], a)
+        want = Sx @ Sz @ Dm @ Sz @ Sx @ want
+    assert np.max(np.abs(got.reshape(-1) - want)) < 1e-14
