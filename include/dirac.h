@@ -150,9 +150,10 @@ dirac_status dirac_set_absorber(dirac_grid *g, const double *a, int64_t count);
  *            evaluates the integrals (analytically or by quadrature; e = -1 for an electron in a.u.).
  *   Step n is counted by the grid's step counter (0 after dirac_set_state, set by dirac_set_counters).
  * Copied; the entries of U are formed once per step on the host in FP64 and applied on the device.
- * First-order (DIRAC_LIE) grids with char_shift 0 or 1, 2-D or 3-D (3-D steps then run the fused single
- * pass).  NULL or nsteps_table = 0 removes the field.
- * Errors: DIRAC_ERR_ARG for a Strang grid or char_shift > 1, a negative count or a non-finite entry.
+ * First-order (DIRAC_LIE) grids, 2-D or 3-D (3-D steps then run the fused single pass), and 2-D
+ * second-order (DIRAC_STRANG) grids, whose phase spans the whole step dt = 2 dx / c (At_n its integral over
+ * it); char_shift 0 or 1.  NULL or nsteps_table = 0 removes the field.
+ * Errors: DIRAC_ERR_ARG for a 3-D Strang grid or char_shift > 1, a negative count or a non-finite entry.
  * dirac_step returns DIRAC_ERR_ARG, enqueuing nothing, when the step counter would pass the table's end.
  * Steps with a field are launched one block of steps_per_launch at a time (no graph replay: each launch
  * takes its step index); the phase costs 48 instead of 16 FP64 instructions per point-step. */
@@ -181,7 +182,8 @@ enum {
     DIRAC_PLAN_SHIFT_2D = 3,     /* 2-D first-order step with characteristic shift > 1 */
     DIRAC_PLAN_3D_TWO_PASS = 4,  /* 3-D x-y pass + z/phase pass */
     DIRAC_PLAN_3D_FUSED = 5,     /* 3-D single pass */
-    DIRAC_PLAN_3D_STRANG = 6     /* 3-D second-order step: eight single-sweep launches */
+    DIRAC_PLAN_3D_STRANG = 6,    /* 3-D second-order step: eight single-sweep launches */
+    DIRAC_PLAN_STRANG_FIELD_2D = 7 /* 2-D second-order step with the vector-potential phase matrix */
 };
 
 dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info);

@@ -106,7 +106,7 @@ double scale_of(const dirac_grid *g) {
 }
 int char_shift(const dirac_grid *g) { return g->cfg.char_shift > 1 ? g->cfg.char_shift : 1; }
 int sweep_mode(const dirac_grid *g) {
-    if (strang(g)) return ndim_of(g) == 3 ? 6 : 2;
+    if (strang(g)) return ndim_of(g) == 3 ? 6 : (g->avec.empty() ? 2 : 5);
     if (ndim_of(g) == 3) return 1;
     if (char_shift(g) > 1) return 4;
     return g->avec.empty() ? 0 : 3;
@@ -454,7 +454,8 @@ void default_plan(dirac_grid *g) {
     }
     const int mode = sweep_mode(g);
     int K = g->fp32 ? 2 : 1, P = (g->fp32 || mode >= 2) ? 2 : 4;
-    if (mode == 2 || mode == 3) K = 1;  // measured: the field's phase matrix makes k = 2 register-bound
+    if (mode == 2 || mode == 3 || mode == 5) K = 1;  // measured: the field's phase matrix makes k = 2 register-bound
+    if (mode == 5 && !g->fp32) P = 1;  // the FP64 two-level matrix step spills at P = 2
     if (k > 0) K = k;
     if (pp > 0) P = pp;
     if (!sweep_supported(g->fp32, mode, K, P)) P = sweep_supported(g->fp32, mode, K, 4) ? 4 : 2;
@@ -718,8 +719,9 @@ dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, in
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
     const bool clear = !A_tilde || nsteps_table == 0;
-    if (!clear && (strang(g) || char_shift(g) > 1))
-        return fail(g, DIRAC_ERR_ARG, "a vector potential is implemented for first-order (DIRAC_LIE) grids with char_shift 1");
+    if (!clear && ((strang(g) && ndim_of(g) == 3) || char_shift(g) > 1))
+        return fail(g, DIRAC_ERR_ARG,
+                    "a vector potential is implemented for first-order grids and 2-D second-order grids, char_shift 1");
     if (!clear)
         for (int64_t i = 0; i < 3 * nsteps_table; ++i)
             if (!std::isfinite(A_tilde[i])) return fail(g, DIRAC_ERR_ARG, "vector-potential table holds a non-finite value");
@@ -871,7 +873,7 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
     info->strip_width = p.strip_w;
     info->segment_rows = p.seg_h;
     static const int plan_of_mode[7] = {DIRAC_PLAN_STEP_2D, DIRAC_PLAN_3D_TWO_PASS, DIRAC_PLAN_STRANG_2D,
-                                        DIRAC_PLAN_FIELD_2D, DIRAC_PLAN_SHIFT_2D, DIRAC_PLAN_3D_FUSED,
+                                        DIRAC_PLAN_FIELD_2D, DIRAC_PLAN_SHIFT_2D, DIRAC_PLAN_STRANG_FIELD_2D,
                                         DIRAC_PLAN_3D_STRANG};
     const int mode = sweep_mode(g);
     info->plan = (mode == 1 && fused_pass(g)) ? DIRAC_PLAN_3D_FUSED : plan_of_mode[mode];
@@ -904,10 +906,10 @@ dirac_status dirac_autotune(dirac_grid *g) {
     } else if (sweep_mode(g) == 4) {
         for (int P : {1, 2})
             for (int wsm : {4, 8, 12, 16}) cands.push_back({1, P, 4, wsm});
-    } else if (sweep_mode(g) == 3) {
+    } else if (sweep_mode(g) == 3 || sweep_mode(g) == 5) {
         const int KP[][2] = {{1, 1}, {1, 2}, {2, 2}};
         for (auto &kp : KP)
-            if (sweep_supported(g->fp32, 3, kp[0], kp[1]))
+            if (sweep_supported(g->fp32, sweep_mode(g), kp[0], kp[1]))
                 for (int wsm : {4, 8, 12}) cands.push_back({kp[0], kp[1], 4, wsm});
     } else if (strang(g)) {
         const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};

@@ -125,7 +125,7 @@ __device__ __forceinline__ void finish_flux(const SweepArgs &a);
 template <typename T, int K, int P> struct Ring;
 
 // Pipelined levels of one launch: K steps, or 2K levels for the second-order splitting (mode 2).
-template <int K, int MODE> struct Levels { static constexpr int value = MODE == 2 ? 2 * K : K; };
+template <int K, int MODE> struct Levels { static constexpr int value = (MODE == 2 || MODE == 5) ? 2 * K : K; };
 
 // MODE 0: 2-D first-order step (x sweep, z sweep, phase), K steps per launch.
 // MODE 1: 3-D x-y pass (x sweep, y sweep), K must be 1.
@@ -133,6 +133,8 @@ template <int K, int MODE> struct Levels { static constexpr int value = MODE == 
 //         the four sweeps' 1/2 factors ride in the phase coefficients as 1/16.
 // MODE 3: 2-D first-order step with a uniform vector potential: the phase is the full 4x4 matrix of
 //         Eq. sol_dis_4, U(step) exp(-i V dt), with the table holding g = exp(-i V dt) / 4 per column or cell.
+// MODE 5: MODE 2 with a uniform vector potential (the phase of each step's first level is the matrix, the
+//         table holding g = exp(-i V dt) / 16).
 template <typename T, int K, int P, int MODE>
 __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     constexpr int L = Levels<K, MODE>::value;
@@ -334,22 +336,23 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
 #pragma unroll
         for (int j = 0; j < P; ++j) load_tab(static_cast<const T *>(a.table) + xl[j] * 4, pu[j], pd[j]);
     }
-    // MODE 3: entries of U for the step of each level (Dup, Ddn, Ez, -Ez, Ep, Em; Sec. 2.3), and with an
-    // x-only table the entries times this lane's g per cell (M = U g, formed once per task)
-    constexpr int LA = MODE == 3 ? L : 1;
+    // MODES 3 and 5: entries of U for each step of the launch (Dup, Ddn, Ez, -Ez, Ep, Em; Sec. 2.3), and with
+    // an x-only table the entries times this lane's g per cell (M = U g, formed once per task)
+    constexpr bool FLD = MODE == 3 || MODE == 5;
+    constexpr int LA = FLD ? K : 1;
     Cx<T> UM[LA][6];
-    Cx<T> MA[LA][MODE == 3 ? P : 1][6];
-    if (MODE == 3) {
+    Cx<T> MA[LA][FLD ? P : 1][6];
+    if (FLD) {
 #pragma unroll
-        for (int lev = 0; lev < LA; ++lev) {
-            const double *u = a.ucoef + ((a.step0 + lev) % a.ucoef_n) * 12;
+        for (int st = 0; st < LA; ++st) {
+            const double *u = a.ucoef + ((a.step0 + st) % a.ucoef_n) * 12;
 #pragma unroll
-            for (int e = 0; e < 6; ++e) UM[lev][e] = Cx<T>{(T)__ldg(u + 2 * e), (T)__ldg(u + 2 * e + 1)};
+            for (int e = 0; e < 6; ++e) UM[st][e] = Cx<T>{(T)__ldg(u + 2 * e), (T)__ldg(u + 2 * e + 1)};
             if (!a.full_table)
 #pragma unroll
-                for (int j = 0; j < (MODE == 3 ? P : 1); ++j)
+                for (int j = 0; j < (FLD ? P : 1); ++j)
 #pragma unroll
-                    for (int e = 0; e < 6; ++e) MA[lev][j][e] = cmulp(UM[lev][e], pu[j]);
+                    for (int e = 0; e < 6; ++e) MA[st][j][e] = cmulp(UM[st][e], pu[j]);
         }
     }
     // Flux through the face (owned by this strip): per row, 1/2(|u14|^2+|u23|^2) at face-1 minus
@@ -455,7 +458,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
             const int64_t q = r - lev;  // row of the level-lev state in st
             // rows of level lev+1 that later levels (or the store) use: [r_first + lev + 1, r_last - lev - 1)
             const bool need_out = (q - 1 >= r_first + lev + 1) && (q - 1 < r_last - lev - 1);
-            if (MODE == 2 && (lev & 1)) {
+            if ((MODE == 2 || MODE == 5) && (lev & 1)) {
                 // second half of a Strang step: z sweep of rows q-2 and q into row q-1, then the x sweep of
                 // row q-1.  The input is 1/4 of the state (the phase carried 1/16), the z-swept row 1/2 of it.
                 const bool zrow_ok = per || (q - 1 >= 0 && q - 1 < nr);
@@ -556,12 +559,14 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                             qu = pu[j];
                             qd = pd[j];
                         }
-                        if (MODE == 3) {
+                        if (FLD) {
                             // psi'_a = sum_b (U_ab g) psi_b over the non-zero entries, columns in order
+                            constexpr int SPL = MODE == 5 ? 2 : 1;  // levels per step
                             Cx<T> m6[6];
 #pragma unroll
                             for (int e = 0; e < 6; ++e)
-                                m6[e] = a.full_table ? cmulp(UM[MODE == 3 ? lev : 0][e], qu) : MA[MODE == 3 ? lev : 0][MODE == 3 ? j : 0][e];
+                                m6[e] = a.full_table ? cmulp(UM[FLD ? lev / SPL : 0][e], qu)
+                                                     : MA[FLD ? lev / SPL : 0][FLD ? j : 0][e];
                             const Cx<T> z0 = {T(0), T(0)};
                             const Cx<T> n0 = cmac(cmac(cmac(z0, o[0], m6[0]), o[2], m6[2]), o[3], m6[4]);
                             const Cx<T> n1 = cmac(cmac(cmac(z0, o[1], m6[0]), o[2], m6[5]), o[3], m6[3]);

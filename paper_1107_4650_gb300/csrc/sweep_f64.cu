@@ -12,6 +12,9 @@ cudaError_t launch_sweep_f64(const SweepArgs &a, int mode, int K, int P, int wpb
     } else if (mode == 2) {
         if (K == 1 && P == 2) return launch_one<double, 1, 2, 2>(a, wpb, s);
         if (K == 1 && P == 1) return launch_one<double, 1, 1, 2>(a, wpb, s);
+    } else if (mode == 5) {
+        if (K == 1 && P == 1) return launch_one<double, 1, 1, 5>(a, wpb, s);
+        if (K == 1 && P == 2) return launch_one<double, 1, 2, 5>(a, wpb, s);
     } else if (mode == 3) {
         if (K == 1 && P == 1) return launch_one<double, 1, 1, 3>(a, wpb, s);
         if (K == 1 && P == 2) return launch_one<double, 1, 2, 3>(a, wpb, s);

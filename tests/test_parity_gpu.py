@@ -934,3 +934,34 @@ def test_zone_edge_massless_packet_moves_forward_at_c(D):
     assert np.allclose(np.abs(got[0, 0, :, 0]), np.abs(np.roll(psi[0, 0, :, 0], nsteps)), atol=1e-14)
     c0 = (x * (np.abs(psi) ** 2).sum(axis=(0, 1, 3))).sum() / (np.abs(psi) ** 2).sum()
     assert abs(obs["centroid"][0] - DX / 2 - (c0 + nsteps * DX)) < 1e-9 * DX
+
+
+@pytest.mark.parametrize("shape", [(70, 45), (9, 6), (130, 33)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("P", [1, 2])
+def test_strang_with_vector_potential_bit_exact(D, shape, periodic, P):
+    """2-D second-order steps in a uniform field (the phase matrix over dt = 2 dx / c) against the oracle."""
+    nx, nz = shape
+    psi = W.random_state(nz, 1, nx, seed=nx * 3 + nz + P)
+    V = np.random.default_rng(nz).uniform(-3e4, 5e4, nx)
+    At = _field_table(10, nx + 1, scale=1.3)
+    want, F = oracle.step_strang2d(psi, 1.0, C, DX, 6, V=V, periodic=periodic, A_tilde=At, step0=2,
+                                   flux_face=nx // 2)
+    cfg = D.make_config((nx, 1, nz), splitting=D.DIRAC_STRANG, points_per_lane=P, flux_face=nx // 2,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_vector_potential(h, At)
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi)
+        D.dirac_set_counters(h, 2, 0.0)
+        D.dirac_step(h, 6)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+        obs = D.dirac_observables(h)
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    assert info["plan"] == D.DIRAC_PLAN_STRANG_FIELD_2D and info["points_per_lane"] == P
+    assert _bits_equal(got, want), rel_l2(got, want)
+    assert abs(obs["flux_cum"] - F) <= 1e-12 * max(abs(F), 1e-300) + 1e-300
