@@ -210,17 +210,20 @@ def step_strang2d(psi, m: float, c: float, dx: float, nsteps: int, V=None, perio
 
 
 def step_strang3d(psi, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False,
-                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1):
+                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1, A_tilde=None, step0: int = 0):
     """nsteps second-order (Strang) steps in 3-D (Sec. 2.4): A(dt/4) B(dt/2) A(dt/4) C(dt/2) D(dt) C(dt/2)
     A(dt/4) B(dt/2) A(dt/4) with c dt / 4 = shift * dx: x sweeps move `shift` cells, y and z sweeps 2 shift.
+    A_tilde / step0: a uniform vector potential as in step() (the phase matrix over dt).
     Returns (psi_out, flux_cum) as step()."""
     out = _as_state(psi)
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    with _Shift(shift):
+    with _Shift(shift), _VectorPotential(A_tilde, step0):
         rc = _load().oracle_step_strang3d(out.ctypes.data, _dims(out), int(bool(periodic)), float(m), float(c),
                                           float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
                                           int(flux_face), ctypes.addressof(fc))
+    if rc == -2:
+        raise ValueError("the vector-potential table ends before the last step")
     if rc != 0:
         raise MemoryError("oracle_step_strang3d")
     return out, fc.value

@@ -340,7 +340,13 @@ int oracle_step_strang3d(double *psi, const int64_t n[3], int periodic, double m
         for (int q = 0; q < 9; ++q) {
             const int ax = axes[q];
             if (ax < 0) {
-                oracle_phase(psi, n, m, c, dt, V, layout);
+                if (g_avec) {  /* uniform vector potential: the full phase matrix over the whole step dt */
+                    const int64_t t = g_avec_step0 + s;
+                    if (t < 0 || t >= g_avec_n) return -2;
+                    oracle_phase_A(psi, n, m, c, dt, V, layout, g_avec + 3 * t);
+                } else {
+                    oracle_phase(psi, n, m, c, dt, V, layout);
+                }
                 continue;
             }
             if (ax == 0 && flux_face >= 0 && flux_cum)

@@ -694,3 +694,20 @@ def test_strang_with_vector_potential_equals_matrix_product(oracle_mod):
             Dm[4 * cell:4 * cell + 4, 4 * cell:4 * cell + 4] = A.phase_matrix_A_cell(M, C, dt, V[cell % nx], a)
         want = Sx @ Sz @ Dm @ Sz @ Sx @ want
     assert np.max(np.abs(got.reshape(-1) - want)) < 1e-14
+
+
+def test_strang3d_with_vector_potential_equals_matrix_product(oracle_mod):
+    shape = (5, 4, 3)
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=71)
+    V = np.random.default_rng(72).uniform(-3e4, 3e4, nx * ny * nz)
+    At = np.random.default_rng(73).uniform(-1.0, 1.0, (2, 3))
+    got, _ = oracle.step_strang3d(psi, M, C, W.DX_DEFAULT, 1, V=V, periodic=True, A_tilde=At, step0=1)
+    Ax, By, Cz = (A.sweep_matrix(shape, 0, True), A.sweep_matrix(shape, 1, True, shift=2),
+                  A.sweep_matrix(shape, 2, True, shift=2))
+    dt = 4 * W.DX_DEFAULT / C
+    Dm = np.zeros((4 * nx * ny * nz,) * 2, complex)
+    for cell in range(nx * ny * nz):
+        Dm[4 * cell:4 * cell + 4, 4 * cell:4 * cell + 4] = A.phase_matrix_A_cell(M, C, dt, V[cell], At[1])
+    want = Ax @ By @ Ax @ Cz @ Dm @ Cz @ Ax @ By @ Ax @ psi.reshape(-1)
+    assert np.max(np.abs(got.reshape(-1) - want)) < 1e-14
