@@ -5,19 +5,24 @@ namespace dirac {
 
 template <typename T>
 static cudaError_t launch_axis_t(const AxisArgs &a, int axis, int phase, int blocks, cudaStream_t s) {
-    if (axis == 0 && !phase) axis_kernel<T, 0, false><<<blocks, 256, 0, s>>>(a);
-    else if (axis == 1 && !phase) axis_kernel<T, 1, false><<<blocks, 256, 0, s>>>(a);
-    else if (axis == 2 && !phase) axis_kernel<T, 2, false><<<blocks, 256, 0, s>>>(a);
-    else if (axis == 2 && phase) axis_kernel<T, 2, true><<<blocks, 256, 0, s>>>(a);
+    const bool field = a.ucoef != nullptr && a.ucoef_n > 0;
+    if (axis == 0 && !phase) axis_kernel<T, 0, false, false><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 1 && !phase) axis_kernel<T, 1, false, false><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 2 && !phase) axis_kernel<T, 2, false, false><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 2 && phase && !field) axis_kernel<T, 2, true, false><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 2 && phase && field) axis_kernel<T, 2, true, true><<<blocks, 256, 0, s>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
 cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz, int axis,
                         int64_t shift, int periodic, int full_table, int phase, int64_t flux_face, double fscale,
-                        double vol, double *flux_part, double *flux_cum, unsigned *ticket, int fp32, int blocks,
-                        cudaStream_t s) {
+                        double vol, double *flux_part, double *flux_cum, unsigned *ticket, const double *ucoef,
+                        int64_t ucoef_n, int64_t step0, int fp32, int blocks, cudaStream_t s) {
     AxisArgs a{};
+    a.ucoef = ucoef;
+    a.ucoef_n = ucoef_n;
+    a.step0 = step0;
     a.in = in;
     a.out = out;
     a.table = table;

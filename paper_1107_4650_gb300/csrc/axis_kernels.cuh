@@ -34,9 +34,12 @@ struct AxisArgs {
     double *flux_part;   // [gridDim.x]
     double *flux_cum;
     unsigned *ticket;
+    // uniform vector potential (phase epilogue only): 12 doubles of U entries per step, this launch's step
+    const double *ucoef;
+    int64_t ucoef_n, step0;
 };
 
-template <typename T, int AXIS, bool PHASE>
+template <typename T, int AXIS, bool PHASE, bool FIELD>
 __global__ void __launch_bounds__(256) axis_kernel(const AxisArgs a) {
     const int64_t nx = a.nx, ny = a.ny, nz = a.nz, S = a.shift;
     const int64_t ncells = nx * ny * nz;
@@ -47,6 +50,12 @@ __global__ void __launch_bounds__(256) axis_kernel(const AxisArgs a) {
     const int64_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? nx : nx * ny);
     const int64_t n_ax = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
     double facc = 0.0;
+    Cx<T> UM[FIELD ? 6 : 1];  // U entries of this step: Dup, Ddn, Ez, -Ez, Ep, Em (Sec. 2.3)
+    if (FIELD) {
+        const double *u = a.ucoef + (a.step0 % a.ucoef_n) * 12;
+#pragma unroll
+        for (int e = 0; e < (FIELD ? 6 : 1); ++e) UM[e] = Cx<T>{(T)__ldg(u + 2 * e), (T)__ldg(u + 2 * e + 1)};
+    }
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, t;
         if (ncells <= 0x7fffffff) {  // 32-bit index arithmetic when the grid allows it (uniform branch)
@@ -105,10 +114,26 @@ __global__ void __launch_bounds__(256) axis_kernel(const AxisArgs a) {
         if (PHASE) {
             Cx<T> pu, pd;
             load_tab(tab + (a.full_table ? c : i) * 4, pu, pd);
-            o[0] = cmulp(o[0], pu);
-            o[1] = cmulp(o[1], pu);
-            o[2] = cmulp(o[2], pd);
-            o[3] = cmulp(o[3], pd);
+            if (FIELD) {
+                // (U_ab g) psi_b over the non-zero entries, columns in order, g = the table's exp(-i V dt)
+                Cx<T> m6[FIELD ? 6 : 1];
+#pragma unroll
+                for (int e = 0; e < (FIELD ? 6 : 1); ++e) m6[e] = cmulp(UM[e], pu);
+                const Cx<T> z0 = {T(0), T(0)};
+                const Cx<T> n0 = cmac(cmac(cmac(z0, o[0], m6[0]), o[2], m6[2]), o[3], m6[4]);
+                const Cx<T> n1 = cmac(cmac(cmac(z0, o[1], m6[0]), o[2], m6[5]), o[3], m6[3]);
+                const Cx<T> n2 = cmac(cmac(cmac(z0, o[0], m6[2]), o[1], m6[4]), o[2], m6[1]);
+                const Cx<T> n3 = cmac(cmac(cmac(z0, o[0], m6[5]), o[1], m6[3]), o[3], m6[1]);
+                o[0] = n0;
+                o[1] = n1;
+                o[2] = n2;
+                o[3] = n3;
+            } else {
+                o[0] = cmulp(o[0], pu);
+                o[1] = cmulp(o[1], pu);
+                o[2] = cmulp(o[2], pd);
+                o[3] = cmulp(o[3], pd);
+            }
         }
         store_pt(out + c * 8, o);
     }

@@ -303,7 +303,8 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
             cudaError_t e = launch_axis(g->psi[par], g->psi[par ^ 1], g->table, g->cfg.n[0], g->cfg.n[1], g->cfg.n[2], ax,
                                         ax == 0 ? 1 : 2, a.periodic, g->table_full, q == 3 ? 1 : 0,
                                         ax == 0 ? a.flux_face : -1, fscale[q], a.vol, g->flux_part, g->flux_dev,
-                                        g->ticket, g->fp32, blocks, s);
+                                        g->ticket, q == 3 ? a.ucoef : nullptr, q == 3 ? a.ucoef_n : 0, step0,
+                                        g->fp32, blocks, s);
             if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order sweep launch");
             g->launches++;
             par ^= 1;
@@ -719,9 +720,8 @@ dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, in
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
     const bool clear = !A_tilde || nsteps_table == 0;
-    if (!clear && ((strang(g) && ndim_of(g) == 3) || char_shift(g) > 1))
-        return fail(g, DIRAC_ERR_ARG,
-                    "a vector potential is implemented for first-order grids and 2-D second-order grids, char_shift 1");
+    if (!clear && char_shift(g) > 1)
+        return fail(g, DIRAC_ERR_ARG, "a vector potential is implemented for char_shift 0 or 1");
     if (!clear)
         for (int64_t i = 0; i < 3 * nsteps_table; ++i)
             if (!std::isfinite(A_tilde[i])) return fail(g, DIRAC_ERR_ARG, "vector-potential table holds a non-finite value");

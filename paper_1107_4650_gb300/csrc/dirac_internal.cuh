@@ -86,10 +86,11 @@ bool shift_supported(int S, int P);
 // One sweep of the whole grid along `axis` with the characteristics moved `shift` cells (output 2x the
 // swept state), optionally followed by the phase from `table` (z sweeps only); x sweeps accumulate the face
 // flux scaled by fscale when flux_face >= 0 (parts: one per block).  Used by the 3-D second-order step.
+// With ucoef (12 doubles per step, ucoef_n steps) the phase is the vector-potential matrix of step step0.
 cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz, int axis,
                         int64_t shift, int periodic, int full_table, int phase, int64_t flux_face, double fscale,
-                        double vol, double *flux_part, double *flux_cum, unsigned *ticket, int fp32, int blocks,
-                        cudaStream_t s);
+                        double vol, double *flux_part, double *flux_cum, unsigned *ticket, const double *ucoef,
+                        int64_t ucoef_n, int64_t step0, int fp32, int blocks, cudaStream_t s);
 
 // Fused 3-D step (x, y, z sweeps and phase in one pass, one step per launch): blocks of `warps` (8 or 16)
 // warps own a 30-cell x strip and warps - 2 rows along y and stream a z segment of zseg_h planes.  Flux

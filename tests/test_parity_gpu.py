@@ -965,3 +965,27 @@ def test_strang_with_vector_potential_bit_exact(D, shape, periodic, P):
     assert info["plan"] == D.DIRAC_PLAN_STRANG_FIELD_2D and info["points_per_lane"] == P
     assert _bits_equal(got, want), rel_l2(got, want)
     assert abs(obs["flux_cum"] - F) <= 1e-12 * max(abs(F), 1e-300) + 1e-300
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6)])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_strang3d_with_vector_potential_bit_exact(D, shape, periodic):
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx * ny + nz + 1)
+    V = np.random.default_rng(nz + 1).uniform(-4e4, 4e4, nx * ny * nz)
+    At = _field_table(8, ny, scale=1.1)
+    want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 4, V=V, periodic=periodic, A_tilde=At, step0=1)
+    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_vector_potential(h, At)
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+        D.dirac_set_state(h, psi)
+        D.dirac_set_counters(h, 1, 0.0)
+        D.dirac_step(h, 4)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want), rel_l2(got, want)
