@@ -152,8 +152,8 @@ dirac_status dirac_set_absorber(dirac_grid *g, const double *a, int64_t count);
  * Copied; the entries of U are formed once per step on the host in FP64 and applied on the device.
  * First-order (DIRAC_LIE) grids, 2-D or 3-D (3-D steps then run the fused single pass), and second-order
  * (DIRAC_STRANG) grids, whose phase spans the whole step dt (2 dx / c in 2-D, 4 dx / c in 3-D; At_n its
- * integral over it); char_shift 0 or 1.  NULL or nsteps_table = 0 removes the field.
- * Errors: DIRAC_ERR_ARG for char_shift > 1, a negative count or a non-finite entry.
+ * integral over it), and 2-D grids with char_shift > 1 (dt = K dx / c).  NULL or nsteps_table = 0 removes
+ * the field.  Errors: DIRAC_ERR_ARG for a negative count or a non-finite entry.
  * dirac_step returns DIRAC_ERR_ARG, enqueuing nothing, when the step counter would pass the table's end.
  * Steps with a field are launched one block of steps_per_launch at a time (no graph replay: each launch
  * takes its step index); the phase costs 48 instead of 16 FP64 instructions per point-step. */

@@ -450,7 +450,9 @@ void default_plan(dirac_grid *g) {
         return;
     }
     if (sweep_mode(g) == 4) {
-        make_plan(g, 1, (pp == 1) ? 1 : 2, 4, 8);
+        // FP64 with the field's phase matrix spills at two points per lane
+        const int P = pp == 1 || pp == 2 ? pp : ((field_on(g) && !g->fp32) ? 1 : 2);
+        make_plan(g, 1, P, 4, 8);
         return;
     }
     const int mode = sweep_mode(g);
@@ -720,8 +722,6 @@ dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, in
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
     const bool clear = !A_tilde || nsteps_table == 0;
-    if (!clear && char_shift(g) > 1)
-        return fail(g, DIRAC_ERR_ARG, "a vector potential is implemented for char_shift 0 or 1");
     if (!clear)
         for (int64_t i = 0; i < 3 * nsteps_table; ++i)
             if (!std::isfinite(A_tilde[i])) return fail(g, DIRAC_ERR_ARG, "vector-potential table holds a non-finite value");

@@ -1,4 +1,5 @@
-// Instantiations of the characteristic-shift step kernel (c dt = S dx, S = 2, 3, 4).
+// Instantiations of the characteristic-shift step kernel (c dt = S dx, S = 2, 3, 4; with and without a uniform
+// vector potential).
 #include "shift_kernels.cuh"
 
 namespace dirac {

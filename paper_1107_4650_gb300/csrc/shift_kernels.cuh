@@ -19,7 +19,8 @@
 
 namespace dirac {
 
-template <typename T, int S, int P>
+// FIELD: a uniform vector potential; the phase is U(step) exp(-i V dt) applied as in the one-cell field mode.
+template <typename T, int S, int P, bool FIELD>
 __device__ __forceinline__ void shift_warp(const SweepArgs &a, const int64_t wid, const int lane) {
     const int64_t seg = wid / a.nstrips;
     const int64_t strip = wid - seg * a.nstrips;
@@ -46,6 +47,12 @@ __device__ __forceinline__ void shift_warp(const SweepArgs &a, const int64_t wid
     if (!a.full_table) {
 #pragma unroll
         for (int j = 0; j < P; ++j) load_tab(tab + xl[j] * 4, pu[j], pd[j]);
+    }
+    Cx<T> UM[FIELD ? 6 : 1];  // U entries of this launch's step (Dup, Ddn, Ez, -Ez, Ep, Em)
+    if (FIELD) {
+        const double *u = a.ucoef + (a.step0 % a.ucoef_n) * 12;
+#pragma unroll
+        for (int e = 0; e < (FIELD ? 6 : 1); ++e) UM[e] = Cx<T>{(T)__ldg(u + 2 * e), (T)__ldg(u + 2 * e + 1)};
     }
     const int64_t face = a.flux_face;
     const bool has_face = face >= x_own0 && face < x_own1;
@@ -176,10 +183,25 @@ __device__ __forceinline__ void shift_warp(const SweepArgs &a, const int64_t wid
                         qu = pu[j];
                         qd = pd[j];
                     }
-                    o[0] = cmulp(o[0], qu);
-                    o[1] = cmulp(o[1], qu);
-                    o[2] = cmulp(o[2], qd);
-                    o[3] = cmulp(o[3], qd);
+                    if (FIELD) {
+                        Cx<T> m6[FIELD ? 6 : 1];
+#pragma unroll
+                        for (int e = 0; e < (FIELD ? 6 : 1); ++e) m6[e] = cmulp(UM[e], qu);
+                        const Cx<T> z0 = {T(0), T(0)};
+                        const Cx<T> n0 = cmac(cmac(cmac(z0, o[0], m6[0]), o[2], m6[2]), o[3], m6[4]);
+                        const Cx<T> n1 = cmac(cmac(cmac(z0, o[1], m6[0]), o[2], m6[5]), o[3], m6[3]);
+                        const Cx<T> n2 = cmac(cmac(cmac(z0, o[0], m6[2]), o[1], m6[4]), o[2], m6[1]);
+                        const Cx<T> n3 = cmac(cmac(cmac(z0, o[0], m6[5]), o[1], m6[3]), o[3], m6[1]);
+                        o[0] = n0;
+                        o[1] = n1;
+                        o[2] = n2;
+                        o[3] = n3;
+                    } else {
+                        o[0] = cmulp(o[0], qu);
+                        o[1] = cmulp(o[1], qu);
+                        o[2] = cmulp(o[2], qd);
+                        o[3] = cmulp(o[3], qd);
+                    }
                     const int64_t x = xa + 32 * j + lane;
                     if (x >= x_own0 && x < x_own1) store_pt(out + (q * nx + x) * 8, o);
                 }
@@ -195,11 +217,11 @@ __device__ __forceinline__ void shift_warp(const SweepArgs &a, const int64_t wid
     }
 }
 
-template <typename T, int S, int P>
+template <typename T, int S, int P, bool FIELD>
 __global__ void __launch_bounds__(128) shift_kernel(const SweepArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (wid < a.nstrips * a.nsegs) shift_warp<T, S, P>(a, wid, lane);
+    if (wid < a.nstrips * a.nsegs) shift_warp<T, S, P, FIELD>(a, wid, lane);
     if (a.flux_face >= 0) finish_flux<1>(a);
 }
 
@@ -208,7 +230,10 @@ static cudaError_t launch_shift_one(const SweepArgs &a, int wpb, cudaStream_t s)
     const int64_t warps = a.nstrips * a.nsegs;
     const int64_t blocks = (warps + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
-    shift_kernel<T, S, P><<<(unsigned)blocks, 32 * wpb, 0, s>>>(a);
+    if (a.ucoef != nullptr && a.ucoef_n > 0)
+        shift_kernel<T, S, P, true><<<(unsigned)blocks, 32 * wpb, 0, s>>>(a);
+    else
+        shift_kernel<T, S, P, false><<<(unsigned)blocks, 32 * wpb, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -989,3 +989,31 @@ def test_strang3d_with_vector_potential_bit_exact(D, shape, periodic):
     finally:
         D.dirac_destroy(h)
     assert _bits_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("S", [2, 3])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("full", [False, True])
+def test_shift_with_vector_potential_bit_exact(D, S, periodic, full):
+    nx, nz = 90, 41
+    psi = W.random_state(nz, 1, nx, seed=S * 10 + nz)
+    V = np.random.default_rng(S).uniform(-3e4, 5e4, nx * nz if full else nx)
+    At = _field_table(9, S + 20, scale=1.2)
+    want, F = oracle.step(psi, 2, 1.0, C, DX, 6, V=V, periodic=periodic, A_tilde=At, step0=2, shift=S,
+                          flux_face=45)
+    cfg = D.make_config((nx, 1, nz), char_shift=S, flux_face=45,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_vector_potential(h, At)
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL if full else D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi)
+        D.dirac_set_counters(h, 2, 0.0)
+        D.dirac_step(h, 6)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want), rel_l2(got, want)
+    assert abs(obs["flux_cum"] - F) <= 1e-12 * max(abs(F), 1e-300) + 1e-300
