@@ -49,6 +49,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default="surrogate.npz")
+    ap.add_argument("--data", default="", help="reuse the labelled sets saved in an earlier --out file")
     args = ap.parse_args()
 
     import paper_1107_4650_gb300 as D
@@ -57,14 +58,21 @@ def main():
 
     B.build()
     D.load_library()
-    q_tr = draw(args.train, W.SEED + 2)
-    q_te = draw(args.heldout, W.SEED + 3)
-    t0 = time.perf_counter()
-    T_tr = solve(D, W, q_tr, fp32=True)
-    t_label = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    T_te = solve(D, W, q_te, fp32=False)
-    t_check = time.perf_counter() - t0
+    if args.data:
+        z = np.load(args.data)
+        q_tr, T_tr, q_te, T_te = z["q_train"], z["T_train"], z["q_heldout"], z["T_heldout_fp64"]
+        old = json.loads(str(z["stats"]))
+        t_label, t_check = old["label_s"], old["check_s"]
+        args.train, args.heldout = len(q_tr), len(q_te)
+    else:
+        q_tr = draw(args.train, W.SEED + 2)
+        q_te = draw(args.heldout, W.SEED + 3)
+        t0 = time.perf_counter()
+        T_tr = solve(D, W, q_tr, fp32=True)
+        t_label = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        T_te = solve(D, W, q_te, fp32=False)
+        t_check = time.perf_counter() - t0
     h = D.dirac_surrogate_create(LO, HI, seed=W.SEED, max_batch=4096)
     t0 = time.perf_counter()
     loss = D.dirac_surrogate_train(h, q_tr, T_tr, epochs=args.epochs, batch=args.batch, lr=args.lr)
