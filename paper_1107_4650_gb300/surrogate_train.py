@@ -62,7 +62,7 @@ def main():
         z = np.load(args.data)
         q_tr, T_tr, q_te, T_te = z["q_train"], z["T_train"], z["q_heldout"], z["T_heldout_fp64"]
         old = json.loads(str(z["stats"]))
-        t_label, t_check = old["label_s"], old["check_s"]
+        t_label, t_check = old.get("label_s", 0.0), old.get("check_s", old.get("judge_s", 0.0))
         args.train, args.heldout = len(q_tr), len(q_te)
     else:
         q_tr = draw(args.train, W.SEED + 2)
