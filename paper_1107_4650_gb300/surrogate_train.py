@@ -1,6 +1,6 @@
 """Trains the Klein-transmission surrogate over the ensemble's parameter box and checks it against the FP64 solver.
 
-  python -m paper_1107_4650_gb300.surrogate_train --train 20000 --heldout 1000 --out surrogate.npz
+  python -m paper_1107_4650_gb300.surrogate_train --train 20000 --heldout 1000 --epochs 6000 --out surrogate.npz
 
 1. Draws `train` and `heldout` reduced parameter sets q = (V0/mc^2, p0/mc, width/dx) uniformly over the box
    [0.5, 3.0] x [0.2, 1.0] x [40, 150] (numpy PCG64, seeds 20111107+2 and +3).
@@ -45,7 +45,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=20000)
     ap.add_argument("--heldout", type=int, default=1000)
-    ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--epochs", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default="surrogate.npz")
