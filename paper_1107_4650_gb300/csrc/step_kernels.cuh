@@ -118,7 +118,10 @@ __device__ __forceinline__ int64_t pmod(int64_t a, int64_t n) {
     return r < 0 ? r + n : r;
 }
 
-template <typename T, int K, int P, int MODE>
+// Rows per iteration of the row loop (1 or 2; measured per variant: two rows let the history registers
+// alternate instead of moving, which pays where the loop body is short).
+template <typename T, int K, int MODE> struct RowUnroll { static constexpr int value = (sizeof(T) == 4 && K == 1 && MODE == 0) ? 2 : 1; };
+template <typename T, int K, int P, int MODE, int UNR = RowUnroll<T, K, MODE>::value>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem);
 template <int K>
 __device__ __forceinline__ void finish_flux(const SweepArgs &a);
@@ -237,6 +240,21 @@ template <typename T, int K, int P> struct Ring {
 // Dynamic shared memory a block of `wpb` warps needs.
 template <typename T, int K, int P> constexpr int ring_smem_bytes(int wpb) { return wpb * Ring<T, K, P>::WARP_BYTES; }
 
+// Records row q's "+" sums in the two-slot history: with two rows per iteration into the slot that held row
+// q - 2 (`older`); with one, slot 0 takes slot 1 (row q - 1) and slot 1 takes row q.
+template <typename T, int UNR>
+__device__ __forceinline__ void push_row(Cx<T> (&s0)[2], Cx<T> (&s1)[2], Cx<T> (&older)[2], Cx<T> v0, Cx<T> v1) {
+    if (UNR == 2) {
+        older[0] = v0;
+        older[1] = v1;
+    } else {
+        s0[0] = s1[0];
+        s0[1] = s1[1];
+        s1[0] = v0;
+        s1[1] = v1;
+    }
+}
+
 // x characteristics of a row (u = a + b travels +x, w = a - b travels -x) and the neighbours the x sweep
 // takes: u of the left cell and w of the right cell (warp shuffles; lane 0 and lane 31 take them from the
 // adjacent point of lanes 31 and 0).
@@ -303,7 +321,7 @@ __device__ __forceinline__ void flux_row(const Cx<T> *lu14, const Cx<T> *lu23, c
     }
 }
 
-template <typename T, int K, int P, int MODE>
+template <typename T, int K, int P, int MODE, int UNR>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem) {
     constexpr int L = Levels<K, MODE>::value;  // pipelined levels (one row and one x cell of halo each)
     const int64_t per_plane = a.nstrips * a.nsegs;
@@ -367,16 +385,19 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     for (int s = 0; s < L; ++s) facc[s] = 0.0;
 
     // "+" characteristic sums of the two previous rows per level: rows q-2 (A) and q-1 (B)
-    Cx<T> UA[L][P][2], UB[L][P][2];
+    // The two previous rows' sums per level sit in two register slots.  With rows taken in pairs (UNR = 2),
+    // row q of level lev reads slot (pair position + lev) & 1, which holds row q - 2, and overwrites it with
+    // row q: the slot indices are compile-time constants and nothing moves.  With UNR = 1, slot 0 holds row
+    // q - 2 and slot 1 row q - 1, shifted down after each row.
+    Cx<T> UH[2][L][P][2];
 #pragma unroll
-    for (int s = 0; s < L; ++s)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int j = 0; j < P; ++j)
+        for (int s = 0; s < L; ++s)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                UA[s][j][h] = {T(0), T(0)};
-                UB[s][j][h] = {T(0), T(0)};
-            }
+            for (int j = 0; j < P; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) UH[t][s][j][h] = {T(0), T(0)};
 
     const int src_prev = (lane + 31) & 31, src_next = (lane + 1) & 31;
 
@@ -419,7 +440,11 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     }
 
     int sl = 0;
-    for (int64_t r = r_first; r < r_last; ++r) {
+    for (int64_t r0 = r_first; r0 < r_last && !aborted; r0 += UNR) {
+#pragma unroll
+    for (int par = 0; par < UNR; ++par) {
+        const int64_t r = r0 + par;
+        if (r >= r_last) break;
         Cx<T> st[P][4];
         const bool row_ok = per || (r >= 0 && r < nr);
         const int64_t rl = per ? pmod(r, nr) : r;
@@ -467,14 +492,12 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 for (int j = 0; j < P; ++j) {
                     const Cx<T> U13 = cadd(st[j][0], st[j][2]), U24 = csub(st[j][1], st[j][3]);
                     const Cx<T> W13 = csub(st[j][0], st[j][2]), W24 = cadd(st[j][1], st[j][3]);
-                    zs[j][0] = cadd(UA[lev][j][0], W13);
-                    zs[j][2] = csub(UA[lev][j][0], W13);
-                    zs[j][1] = cadd(UA[lev][j][1], W24);
-                    zs[j][3] = csub(W24, UA[lev][j][1]);
-                    UA[lev][j][0] = UB[lev][j][0];
-                    UA[lev][j][1] = UB[lev][j][1];
-                    UB[lev][j][0] = U13;
-                    UB[lev][j][1] = U24;
+                    Cx<T>(&UO)[2] = UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j];  // row q - 2
+                    zs[j][0] = cadd(UO[0], W13);
+                    zs[j][2] = csub(UO[0], W13);
+                    zs[j][1] = cadd(UO[1], W24);
+                    zs[j][3] = csub(W24, UO[1]);
+                    push_row<T, UNR>(UH[0][lev][j], UH[1][lev][j], UO, U13, U24);
                     if (!zrow_ok)
 #pragma unroll
                         for (int c = 0; c < 4; ++c) zs[j][c] = Cx<T>{T(0), T(0)};
@@ -546,10 +569,10 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                     const Cx<T> U13 = cadd(b0, b2), U24 = csub(b1, b3);
                     if (need_out) {
                         const Cx<T> W13 = csub(b0, b2), W24 = cadd(b1, b3);
-                        o[0] = cadd(UA[lev][j][0], W13);
-                        o[2] = csub(UA[lev][j][0], W13);
-                        o[1] = cadd(UA[lev][j][1], W24);
-                        o[3] = csub(W24, UA[lev][j][1]);
+                        o[0] = cadd(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][0], W13);
+                        o[2] = csub(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][0], W13);
+                        o[1] = cadd(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][1], W24);
+                        o[3] = csub(W24, UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][1]);
                         // phase (Eq. sol_dis_4) with the deferred 1/4
                         Cx<T> qu, qd;
                         if (a.full_table) {
@@ -583,24 +606,18 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                             o[3] = cmulp(o[3], qd);
                         }
                     }
-                    UA[lev][j][0] = UB[lev][j][0];
-                    UA[lev][j][1] = UB[lev][j][1];
-                    UB[lev][j][0] = U13;
-                    UB[lev][j][1] = U24;
+                    push_row<T, UNR>(UH[0][lev][j], UH[1][lev][j], UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j], U13, U24);
                 } else {
                     // y sweep (Eq. sol_dis_2): +y movers (b1 - i b4, b2 + i b3), -y movers (b1 + i b4, b2 - i b3)
                     const Cx<T> U14 = csub_ib(b0, b3), U23 = cadd_ib(b1, b2);
                     if (need_out) {
                         const Cx<T> W14 = cadd_ib(b0, b3), W23 = csub_ib(b1, b2);
-                        o[0] = cadd(UA[lev][j][0], W14);
-                        o[3] = cmul_i(csub(UA[lev][j][0], W14));
-                        o[1] = cadd(UA[lev][j][1], W23);
-                        o[2] = cmul_mi(csub(UA[lev][j][1], W23));
+                        o[0] = cadd(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][0], W14);
+                        o[3] = cmul_i(csub(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][0], W14));
+                        o[1] = cadd(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][1], W23);
+                        o[2] = cmul_mi(csub(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][1], W23));
                     }
-                    UA[lev][j][0] = UB[lev][j][0];
-                    UA[lev][j][1] = UB[lev][j][1];
-                    UB[lev][j][0] = U14;
-                    UB[lev][j][1] = U23;
+                    push_row<T, UNR>(UH[0][lev][j], UH[1][lev][j], UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j], U14, U23);
                 }
                 if (need_out) {
                     const bool keep = per || (out_row_ok && xin[j]);
@@ -633,6 +650,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
             }
             sl = (sl + 1 == RG::SLOTS) ? 0 : sl + 1;
         }
+    }
     }
     if (aborted) {
         // a copy never completed: report, then wait (bounded) for this warp's copies still in flight
