@@ -449,15 +449,22 @@ def main():
                          "workload": "%d^3 soft-Coulomb grid (Z = 10, per-cell table), %s splitting" % (n3, sname),
                          "plan": {D.DIRAC_PLAN_3D_FUSED: "fused single pass",
                                   D.DIRAC_PLAN_3D_TWO_PASS: "x-y pass + z/phase pass, P=%d" % i3["points_per_lane"],
-                                  D.DIRAC_PLAN_3D_STRANG: "eight single-sweep launches"}.get(i3["plan"], str(i3["plan"])),
+                                  D.DIRAC_PLAN_3D_STRANG: "eight single-sweep launches",
+                                  D.DIRAC_PLAN_3D_STRANG_FUSED: "three fused passes (x-y-x, z-phase-z, x-y-x)"}
+                                 .get(i3["plan"], str(i3["plan"])),
                          "norm_end": o3["norm"]}
                 if prec == D.DIRAC_FP64:
                     entry["fp64_instr_per_point_step"] = instr
                     entry["frac_of_measured_fp64_issue"] = instr * v3 / world / 1e12 / FP64_ISSUE_PEAK_MEASURED
                 else:
+                    # second order: the unfused basis is eight single sweeps (8 x 64 B + the 16 B table); the
+                    # three fused passes move 3 x 64 + 16 B
                     bytes3 = 80 if split == D.DIRAC_LIE else 8 * 64 + 16
                     entry["bytes_per_point_step"] = bytes3
                     entry["effective_hbm_frac"] = bytes3 * v3 / world / 1e9 / hbm_peak
+                    if i3["plan"] == D.DIRAC_PLAN_3D_STRANG_FUSED:
+                        entry["pass_bytes_per_point_step"] = 3 * 64 + 16
+                        entry["hbm_frac_of_pass_bytes"] = (3 * 64 + 16) * v3 / world / 1e9 / hbm_peak
                 variants["%s_3d_%s" % (pname, sname)] = entry
             del dev3
 

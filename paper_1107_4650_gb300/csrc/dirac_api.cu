@@ -30,6 +30,9 @@ struct Plan {
     // 3-D: fused single-pass step (fused3d_kernels.cuh) instead of the x-y pass + z/phase pass
     int fused3d = 0, f_warps = 16;
     int64_t f_nstrips = 0, f_nytiles = 0, f_nzsegs = 0, f_zseg_h = 0;
+    // 3-D second-order step: three fused passes (strang3d_kernels.cuh) instead of eight single sweeps
+    int s3_fused = 0, s3_warps = 16, s3_zfactor = 4;
+    int64_t s3_nstrips = 0, s3_nytiles = 0, s3_nzsegs = 0, s3_zseg_h = 0, s3_z_nsegs = 1, s3_z_seg_h = 0;
 };
 
 }  // namespace
@@ -115,7 +118,9 @@ int levels(const dirac_grid *g, int K) { return strang(g) ? 2 * K : K; }
 // a uniform vector potential is set (2-D: mode 3; 3-D: the fused pass with the phase matrix)
 bool field_on(const dirac_grid *g) { return !g->avec.empty(); }
 // 3-D steps run as the fused single pass (chosen by the plan, or required by a vector potential)
-bool fused_pass(const dirac_grid *g) { return ndim_of(g) == 3 && (g->plan.fused3d || field_on(g)); }
+bool fused_pass(const dirac_grid *g) { return ndim_of(g) == 3 && !strang(g) && (g->plan.fused3d || field_on(g)); }
+// 3-D second-order step as the x-y-x, z-phase-z, x-y-x passes
+bool strang3d_fused(const dirac_grid *g) { return sweep_mode(g) == 6 && g->plan.s3_fused; }
 // x halo cells of a strip (each side) for K steps per launch
 int halo_of(const dirac_grid *g, int K) { return sweep_mode(g) == 4 ? char_shift(g) : levels(g, K); }
 double cell_volume(const dirac_grid *g) {
@@ -229,6 +234,20 @@ void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
         fz = std::min<int64_t>(fz, std::max<int64_t>(1, nz / 16));
         p.f_zseg_h = (nz + fz - 1) / fz;
         p.f_nzsegs = (nz + p.f_zseg_h - 1) / p.f_zseg_h;
+        // second-order passes: x-y-x blocks over 28-cell strips x (warps - 4)-row tiles x z segments (planes
+        // are independent: ~8 blocks per SM of work); z-phase-z columns x z segments (~s3_zfactor x 1024
+        // threads per SM, segments of at least 16 planes: four halo planes each side)
+        p.s3_nstrips = (g->cfg.n[0] + 27) / 28;
+        p.s3_nytiles = (g->cfg.n[1] + (p.s3_warps - 4) - 1) / (p.s3_warps - 4);
+        const int64_t s3_tiles = p.s3_nstrips * p.s3_nytiles;
+        int64_t sz = std::max<int64_t>(1, (8 * (int64_t)g->sm_count + s3_tiles - 1) / s3_tiles);
+        sz = std::min<int64_t>(sz, nz);
+        p.s3_zseg_h = (nz + sz - 1) / sz;
+        p.s3_nzsegs = (nz + p.s3_zseg_h - 1) / p.s3_zseg_h;
+        int64_t zz = std::max<int64_t>(1, ((int64_t)p.s3_zfactor * 1024 * g->sm_count + ncol / 2) / std::max<int64_t>(1, ncol));
+        zz = std::min<int64_t>(zz, std::max<int64_t>(1, nz / 16));
+        p.s3_z_seg_h = (nz + zz - 1) / zz;
+        p.s3_z_nsegs = (nz + p.s3_z_seg_h - 1) / p.s3_z_seg_h;
     }
     for (auto &x : g->graph)
         if (x) {
@@ -248,6 +267,8 @@ dirac_status ensure_flux_part(dirac_grid *g) {
     size_t need = (size_t)8 * planes * std::max<int64_t>(g->plan.nsegs, 1);
     if (fused_pass(g)) need = std::max(need, (size_t)(g->plan.f_nzsegs * g->plan.f_nytiles * g->plan.f_warps));
     if (sweep_mode(g) == 6) need = std::max(need, (size_t)axis_blocks(g));
+    if (strang3d_fused(g))
+        need = std::max(need, (size_t)(2 * g->plan.s3_nzsegs * g->plan.s3_nytiles * g->plan.s3_warps));
     if (need <= g->flux_part_cap) return DIRAC_OK;
     if (g->flux_part) {
         cudaFree(g->flux_part);
@@ -290,6 +311,31 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     a.step0 = step0;
     a.inject_stall = g->inject_stall;
     const int mode = sweep_mode(g);
+    if (mode == 6 && p.s3_fused) {
+        // 3-D second-order step (Sec. 2.4) as three passes: x-y-x, z-phase-z, x-y-x.  Each sweep doubles the
+        // state and the table carries 1/256, so the states entering the four x sweeps are 1, 4, 1/8 and 1/2
+        // times the true state (flux scale 1/2 over its square); the step leaves the state in psi[parity ^ 1].
+        const int64_t ny = g->cfg.n[1], nz = g->cfg.n[2];
+        a.nsegs = p.s3_nzsegs * p.s3_nytiles * p.s3_warps;  // flux parts per x sweep
+        a.nplanes = 1;
+        a.in = g->psi[parity];
+        a.out = g->psi[parity ^ 1];
+        cudaError_t e = launch_strang_xy(a, g->fp32, p.s3_warps, ny, nz, p.s3_nstrips, p.s3_nytiles, p.s3_nzsegs,
+                                         p.s3_zseg_h, 0.5, 0.5 / 16.0, s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order x-y-x pass launch");
+        g->launches++;
+        e = launch_strang_z(g->psi[parity ^ 1], g->psi[parity], g->table, g->cfg.n[0], ny, nz, a.periodic,
+                            g->table_full, a.ucoef, a.ucoef_n, step0, p.s3_z_nsegs, p.s3_z_seg_h, g->fp32, s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order z-phase-z pass launch");
+        g->launches++;
+        a.in = g->psi[parity];
+        a.out = g->psi[parity ^ 1];
+        e = launch_strang_xy(a, g->fp32, p.s3_warps, ny, nz, p.s3_nstrips, p.s3_nytiles, p.s3_nzsegs, p.s3_zseg_h,
+                             0.5 * 64.0, 0.5 * 4.0, s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order x-y-x pass launch");
+        g->launches++;
+        return DIRAC_OK;
+    }
     if (mode == 6) {
         // 3-D second-order step (Sec. 2.4): A(1) B(2) A(1) C(2) D C(2) A(1) B(2) A(1), cells moved per sweep in
         // parentheses.  Each sweep doubles the state and the table carries 1/256, so the state entering the
@@ -345,7 +391,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
 }
 
 int block_flips(const dirac_grid *g) {
-    if (sweep_mode(g) == 6) return 0;  // eight sweeps per step: parity returns
+    if (sweep_mode(g) == 6) return g->plan.s3_fused ? 1 : 0;  // three passes flip the parity, eight sweeps return
     return (ndim_of(g) == 3 && !fused_pass(g)) ? 0 : 1;
 }
 
@@ -380,7 +426,7 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
 }
 
 int64_t launches_per_block(const dirac_grid *g) {
-    if (sweep_mode(g) == 6) return 8;
+    if (sweep_mode(g) == 6) return g->plan.s3_fused ? 3 : 8;
     return 1 + ((ndim_of(g) == 3 && !fused_pass(g)) ? 1 : 0);
 }
 
@@ -446,6 +492,11 @@ void default_plan(dirac_grid *g) {
         // points_per_lane 0: the fused single-pass step; 1, 2 or 4: the x-y pass + z/phase pass with that P
         g->plan.fused3d = pp > 0 ? 0 : 1;
         g->plan.f_warps = g->cfg.n[1] <= 12 ? 8 : 16;  // short y extents: 6-row tiles waste fewer halo rows
+        // second-order step: points_per_lane 1 = eight single-sweep launches, 2 = the three fused passes,
+        // 0 = library choice (fused passes for FP32 storage, which is bandwidth-bound; single sweeps for
+        // FP64, which is bound by the FP64 pipe and would recompute the x-y-x pass's halo cells)
+        g->plan.s3_fused = pp == 1 ? 0 : (pp == 2 ? 1 : (g->fp32 ? 1 : 0));
+        g->plan.s3_warps = 16;
         make_plan(g, 1, pp > 0 ? pp : 2, 4, 16);
         return;
     }
@@ -877,6 +928,13 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
                                         DIRAC_PLAN_3D_STRANG};
     const int mode = sweep_mode(g);
     info->plan = (mode == 1 && fused_pass(g)) ? DIRAC_PLAN_3D_FUSED : plan_of_mode[mode];
+    if (strang3d_fused(g)) {
+        info->plan = DIRAC_PLAN_3D_STRANG_FUSED;
+        info->points_per_lane = 1;
+        info->launch_warps = p.s3_nstrips * p.s3_nytiles * p.s3_nzsegs * p.s3_warps;
+        info->strip_width = 28;
+        info->segment_rows = p.s3_zseg_h;
+    }
     if (fused_pass(g)) {
         info->points_per_lane = 1;
         info->launch_warps = p.f_nstrips * p.f_nytiles * p.f_nzsegs * p.f_warps;
@@ -892,13 +950,18 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
 dirac_status dirac_autotune(dirac_grid *g) {
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     CK(g, cudaSetDevice(g->cfg.device));
-    if (sweep_mode(g) == 6) return DIRAC_OK;  // the 3-D second-order step has a single launch plan
     struct Cand {
         int K, P, wpb, wsm;
         int fused = 0;  // 3-D: warps per block of the fused pass (0: two-pass path)
+        int s3 = 0;     // 3-D second order: 0 = eight single sweeps, else warps per block of the x-y-x pass
+        int s3z = 4;    // and the z-phase-z pass's threads per SM / 1024
     };
     std::vector<Cand> cands;
-    if (g->cfg.ndim == 3) {
+    if (sweep_mode(g) == 6) {
+        cands.push_back({1, 2, 4, 16, 0, 0});
+        for (int sw : {16, 32})
+            for (int zf : {2, 4, 8}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
+    } else if (g->cfg.ndim == 3) {
         if (!field_on(g))  // with a vector potential only the fused pass applies the phase matrix
             for (int P : {1, 2, 4})
                 for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});
@@ -939,7 +1002,8 @@ dirac_status dirac_autotune(dirac_grid *g) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    Cand best = {g->plan.K, g->plan.P, g->plan.wpb, 0, g->plan.fused3d ? g->plan.f_warps : 0};
+    Cand best = {g->plan.K, g->plan.P, g->plan.wpb, 0, g->plan.fused3d ? g->plan.f_warps : 0,
+                 g->plan.s3_fused ? g->plan.s3_warps : 0, g->plan.s3_zfactor};
     double best_t = 1e300;
     const int use_graphs = g->cfg.use_graphs;
     g->cfg.use_graphs = 0;
@@ -948,6 +1012,9 @@ dirac_status dirac_autotune(dirac_grid *g) {
     for (const Cand &c : cands) {
         g->plan.fused3d = c.fused ? 1 : 0;
         if (c.fused) g->plan.f_warps = c.fused;
+        g->plan.s3_fused = c.s3 ? 1 : 0;
+        if (c.s3) g->plan.s3_warps = c.s3;
+        g->plan.s3_zfactor = c.s3z;
         make_plan(g, c.K, c.P, c.wpb, c.wsm);
         st = ensure_flux_part(g);
         if (st != DIRAC_OK) break;
@@ -974,6 +1041,9 @@ dirac_status dirac_autotune(dirac_grid *g) {
     if (st == DIRAC_OK) {
         g->plan.fused3d = best.fused ? 1 : 0;
         if (best.fused) g->plan.f_warps = best.fused;
+        g->plan.s3_fused = best.s3 ? 1 : 0;
+        if (best.s3) g->plan.s3_warps = best.s3;
+        g->plan.s3_zfactor = best.s3z;
         make_plan(g, best.K, best.P, best.wpb, best.wsm ? best.wsm : 8);
         st = ensure_flux_part(g);
     }

@@ -98,6 +98,18 @@ cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx
 cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
                            int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s);
 
+// 3-D second-order step as three passes (strang3d_kernels.cuh).  x-y-x pass: blocks of `warps` (16 or 32)
+// warps own a 28-cell x strip and warps - 4 rows along y over a z segment of zseg_h planes; fscale0/1 scale
+// the face flux of its two x sweeps; flux parts [2][nzsegs * nytiles * warps] (a.nsegs * a.nplanes must
+// equal nzsegs * nytiles * warps).  z-phase-z pass: one thread per column over nsegs segments of seg_h planes,
+// the phase from `table` (or, with ucoef, the vector-potential matrix of step step0).
+cudaError_t launch_strang_xy(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
+                             int64_t nytiles, int64_t nzsegs, int64_t zseg_h, double fscale0, double fscale1,
+                             cudaStream_t s);
+cudaError_t launch_strang_z(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz,
+                            int periodic, int full_table, const double *ucoef, int64_t ucoef_n, int64_t step0,
+                            int64_t nsegs, int64_t seg_h, int fp32, cudaStream_t s);
+
 // Entries of the U matrix of Sec. 2.3 for mu = m c^2 dt and the field integral At (12 doubles:
 // Dup, Ddn, Ez, -Ez, Ep, Em as (re, im)); A = sqrt(((mu^2 + At_x^2) + At_y^2) + At_z^2), sin(A)/A -> 1 at A = 0.
 void u_entries(double mu, const double At[3], double out[12]);

@@ -1,0 +1,46 @@
+// Instantiations of the fused passes of the 3-D second-order step: the x-y-x pass with 16 or 32 warps per
+// block (12 or 28 owned rows per tile), the z-phase-z pass with and without a uniform vector potential.
+#include "strang3d_kernels.cuh"
+
+namespace dirac {
+
+cudaError_t launch_strang_xy(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
+                             int64_t nytiles, int64_t nzsegs, int64_t zseg_h, double fscale0, double fscale1,
+                             cudaStream_t s) {
+    StrangXYArgs A{};
+    A.s = a;
+    A.ny = ny;
+    A.nz = nz;
+    A.nstrips = nstrips;
+    A.nytiles = nytiles;
+    A.nzsegs = nzsegs;
+    A.zseg_h = zseg_h;
+    A.fscale0 = fscale0;
+    A.fscale1 = fscale1;
+    if (warps == 16) return fp32 ? launch_strang_xy_one<float, 16>(A, s) : launch_strang_xy_one<double, 16>(A, s);
+    if (warps == 32) return fp32 ? launch_strang_xy_one<float, 32>(A, s) : launch_strang_xy_one<double, 32>(A, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_strang_z(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz,
+                            int periodic, int full_table, const double *ucoef, int64_t ucoef_n, int64_t step0,
+                            int64_t nsegs, int64_t seg_h, int fp32, cudaStream_t s) {
+    StrangZArgs a{};
+    a.in = in;
+    a.out = out;
+    a.table = table;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.seg_h = seg_h;
+    a.periodic = periodic;
+    a.full_table = full_table;
+    a.ucoef = ucoef;
+    a.ucoef_n = ucoef_n;
+    a.step0 = step0;
+    const bool field = ucoef != nullptr && ucoef_n > 0;
+    if (field) return fp32 ? launch_strang_z_one<float, true>(a, nsegs, s) : launch_strang_z_one<double, true>(a, nsegs, s);
+    return fp32 ? launch_strang_z_one<float, false>(a, nsegs, s) : launch_strang_z_one<double, false>(a, nsegs, s);
+}
+
+}  // namespace dirac

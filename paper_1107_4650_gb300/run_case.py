@@ -134,7 +134,7 @@ def main():
     best = min(times)
     print(json.dumps({"precision": args.precision, "ndim": args.ndim, "side": args.side, "nsteps": args.nsteps,
                       "ms": best, "point_steps_per_s": cells * args.nsteps / (best / 1e3),
-                      "k": info["steps_per_launch"], "p": info["points_per_lane"],
+                      "k": info["steps_per_launch"], "p": info["points_per_lane"], "plan": info["plan"],
                       "warps": info["launch_warps"], "seg_rows": info["segment_rows"], "norm": obs["norm"],
                       "flux": obs["flux_cum"]}))
 

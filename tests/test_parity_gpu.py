@@ -593,16 +593,21 @@ def test_shift_fp32_against_oracle(D):
 
 # ------------------------------------------------------------------ 3-D second-order (Strang) splitting
 
-@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13)])
+# points_per_lane 1: eight single-sweep launches per step; 2: the x-y-x, z-phase-z, x-y-x passes
+S3_PLANS = {1: "DIRAC_PLAN_3D_STRANG", 2: "DIRAC_PLAN_3D_STRANG_FUSED"}
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13), (60, 30, 40), (29, 13, 3)])
 @pytest.mark.parametrize("periodic", [False, True])
 @pytest.mark.parametrize("full", [False, True])
-def test_strang3d_fp64_bit_exact(D, shape, periodic, full):
+@pytest.mark.parametrize("pp", [1, 2])
+def test_strang3d_fp64_bit_exact(D, shape, periodic, full, pp):
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx * ny + nz)
     rng = np.random.default_rng(nz)
     V = rng.uniform(-4e4, 4e4, nx * ny * nz if full else nx)
     want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 5, V=V, periodic=periodic)
-    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG,
+    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=pp,
                         boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
     h = D.dirac_create_grid(cfg)
     try:
@@ -611,13 +616,71 @@ def test_strang3d_fp64_bit_exact(D, shape, periodic, full):
         D.dirac_step(h, 5)
         got = np.empty_like(psi)
         D.dirac_get_state(h, got)
+        info = D.dirac_get_info(h)
     finally:
         D.dirac_destroy(h)
+    assert info["plan"] == getattr(D, S3_PLANS[pp])
+    assert info["kernel_launches"] == 5 * (8 if pp == 1 else 3)
     assert _bits_equal(got, want), rel_l2(got, want)
 
 
+@pytest.mark.parametrize("periodic", [False, True])
+def test_strang3d_fused_passes_fp32_same_bits_as_single_sweeps(D, periodic):
+    """FP32 storage: the three fused passes do the single-sweep kernels' arithmetic in the same order, so the
+    states agree bit for bit (and both stay within FP32 rounding of the FP64 oracle)."""
+    nx, ny, nz = 70, 33, 37
+    psi = W.random_state(nz, ny, nx, seed=77).astype(np.complex64)
+    V = np.random.default_rng(78).uniform(-4e4, 4e4, nx * ny * nz)
+    out = {}
+    for pp in (1, 2):
+        cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=pp, precision=D.DIRAC_FP32,
+                            boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+        h = D.dirac_create_grid(cfg)
+        try:
+            D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+            D.dirac_set_state(h, psi)
+            D.dirac_step(h, 6)
+            got = np.empty_like(psi)
+            D.dirac_get_state(h, got)
+            out[pp] = got
+        finally:
+            D.dirac_destroy(h)
+    assert np.array_equal(out[1].view(np.uint32), out[2].view(np.uint32))
+    want, _ = oracle.step_strang3d(psi.astype(np.complex128), 1.0, C, DX, 6, V=V, periodic=periodic)
+    assert rel_l2(out[2].astype(np.complex128), want) < 5e-6
+
+
+def test_strang3d_default_plans_and_autotune(D):
+    """Library choice: FP32 storage runs the fused passes, FP64 the single sweeps; dirac_autotune picks among
+    both (and the fused pass's block and segment shapes) without changing the result."""
+    nx, ny, nz = 48, 40, 36
+    psi = W.random_state(nz, ny, nx, seed=5)
+    V = np.random.default_rng(6).uniform(-4e4, 4e4, nx)
+    want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 7, V=V, periodic=False)
+    for prec, plan in ((D.DIRAC_FP32, D.DIRAC_PLAN_3D_STRANG_FUSED), (D.DIRAC_FP64, D.DIRAC_PLAN_3D_STRANG)):
+        cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, precision=prec)
+        h = D.dirac_create_grid(cfg)
+        try:
+            assert D.dirac_get_info(h)["plan"] == plan
+            D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+            st = psi.astype(np.complex64) if prec == D.DIRAC_FP32 else psi
+            D.dirac_set_state(h, st)
+            D.dirac_autotune(h)
+            assert D.dirac_get_info(h)["plan"] in (D.DIRAC_PLAN_3D_STRANG, D.DIRAC_PLAN_3D_STRANG_FUSED)
+            D.dirac_step(h, 7)
+            got = np.empty_like(st)
+            D.dirac_get_state(h, got)
+        finally:
+            D.dirac_destroy(h)
+        if prec == D.DIRAC_FP64:
+            assert _bits_equal(got, want)
+        else:
+            assert rel_l2(got.astype(np.complex128), want) < 5e-6
+
+
 @pytest.mark.parametrize("fp32", [False, True])
-def test_strang3d_flux_graphs_fp32(D, fp32):
+@pytest.mark.parametrize("pp", [1, 2])
+def test_strang3d_flux_graphs_fp32(D, fp32, pp):
     """A positive-energy packet crossing the face: 40 steps (graph replay), flux at the four x sweeps of
     every step against the oracle; FP32 storage within its rounding tolerance."""
     nx, ny, nz = 160, 12, 10
@@ -630,7 +693,7 @@ def test_strang3d_flux_graphs_fp32(D, fp32):
     V = np.random.default_rng(53).uniform(-2e3, 2e3, nx)
     want, F = oracle.step_strang3d(psi, 1.0, C, DX, 40, V=V, periodic=True, flux_face=80)
     cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, boundary=D.DIRAC_BC_PERIODIC,
-                        flux_face=80, precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64)
+                        flux_face=80, precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64, points_per_lane=pp)
     h = D.dirac_create_grid(cfg)
     dt = np.complex64 if fp32 else np.complex128
     try:
@@ -648,6 +711,7 @@ def test_strang3d_flux_graphs_fp32(D, fp32):
         assert abs(obs["flux_cum"] - F) < 1e-5 * abs(F)
     else:
         assert _bits_equal(got, want)
+        assert abs(obs["flux_cum"] - F) < 1e-12 * abs(F)
         assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
 
 
@@ -969,13 +1033,14 @@ def test_strang_with_vector_potential_bit_exact(D, shape, periodic, P):
 
 @pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6)])
 @pytest.mark.parametrize("periodic", [False, True])
-def test_strang3d_with_vector_potential_bit_exact(D, shape, periodic):
+@pytest.mark.parametrize("pp", [1, 2])
+def test_strang3d_with_vector_potential_bit_exact(D, shape, periodic, pp):
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx * ny + nz + 1)
     V = np.random.default_rng(nz + 1).uniform(-4e4, 4e4, nx * ny * nz)
     At = _field_table(8, ny, scale=1.1)
     want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 4, V=V, periodic=periodic, A_tilde=At, step0=1)
-    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG,
+    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=pp,
                         boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
     h = D.dirac_create_grid(cfg)
     try:
