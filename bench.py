@@ -430,7 +430,7 @@ def main():
                 D.dirac_set_state(h3, dev3)
                 D.dirac_autotune(h3)  # fused single pass or x-y + z/phase passes, whichever is faster here
                 i3 = D.dirac_get_info(h3)
-                n_steps3 = 12 if split == D.DIRAC_LIE else 4
+                n_steps3 = 12 if split == D.DIRAC_LIE else 32
                 D.dirac_step(h3, n_steps3)  # warm-up
                 e30, e31 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 stream.synchronize()
@@ -450,21 +450,23 @@ def main():
                          "plan": {D.DIRAC_PLAN_3D_FUSED: "fused single pass",
                                   D.DIRAC_PLAN_3D_TWO_PASS: "x-y pass + z/phase pass, P=%d" % i3["points_per_lane"],
                                   D.DIRAC_PLAN_3D_STRANG: "eight single-sweep launches",
-                                  D.DIRAC_PLAN_3D_STRANG_FUSED: "three fused passes (x-y-x, z-phase-z, x-y-x)"}
+                                  D.DIRAC_PLAN_3D_STRANG_FUSED: "fused passes: x-y-x, then per step z-phase-z and "
+                                                                "x-y-x-x-y-x (the last x-y-x)"}
                                  .get(i3["plan"], str(i3["plan"])),
                          "norm_end": o3["norm"]}
                 if prec == D.DIRAC_FP64:
                     entry["fp64_instr_per_point_step"] = instr
                     entry["frac_of_measured_fp64_issue"] = instr * v3 / world / 1e12 / FP64_ISSUE_PEAK_MEASURED
                 else:
-                    # second order: the unfused basis is eight single sweeps (8 x 64 B + the 16 B table); the
-                    # three fused passes move 3 x 64 + 16 B
+                    # second order: the unfused basis is eight single sweeps (8 x 64 B + the 16 B table); a run
+                    # of m fused steps moves m z-phase-z passes (80 B) and m + 1 x-y passes (64 B)
                     bytes3 = 80 if split == D.DIRAC_LIE else 8 * 64 + 16
                     entry["bytes_per_point_step"] = bytes3
                     entry["effective_hbm_frac"] = bytes3 * v3 / world / 1e9 / hbm_peak
                     if i3["plan"] == D.DIRAC_PLAN_3D_STRANG_FUSED:
-                        entry["pass_bytes_per_point_step"] = 3 * 64 + 16
-                        entry["hbm_frac_of_pass_bytes"] = (3 * 64 + 16) * v3 / world / 1e9 / hbm_peak
+                        moved = 80 + 64 * (n_steps3 + 1) / n_steps3
+                        entry["pass_bytes_per_point_step"] = moved
+                        entry["hbm_frac_of_pass_bytes"] = moved * v3 / world / 1e9 / hbm_peak
                 variants["%s_3d_%s" % (pname, sname)] = entry
             del dev3
 

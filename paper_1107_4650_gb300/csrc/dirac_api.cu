@@ -31,8 +31,11 @@ struct Plan {
     int fused3d = 0, f_warps = 16;
     int64_t f_nstrips = 0, f_nytiles = 0, f_nzsegs = 0, f_zseg_h = 0;
     // 3-D second-order step: three fused passes (strang3d_kernels.cuh) instead of eight single sweeps
-    int s3_fused = 0, s3_warps = 16, s3_zfactor = 4;
-    int64_t s3_nstrips = 0, s3_nytiles = 0, s3_nzsegs = 0, s3_zseg_h = 0, s3_z_nsegs = 1, s3_z_seg_h = 0;
+    int s3_fused = 0, s3_warps = 16, s3_zfactor = 2;
+    struct XY {
+        int64_t nstrips = 0, nytiles = 0, nzsegs = 0, zseg_h = 0;
+    } s3_xy[2];  // x-y-x pass (half step) and x-y-x-x-y-x pass (two half steps)
+    int64_t s3_z_nsegs = 1, s3_z_seg_h = 0;
 };
 
 }  // namespace
@@ -234,17 +237,22 @@ void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
         fz = std::min<int64_t>(fz, std::max<int64_t>(1, nz / 16));
         p.f_zseg_h = (nz + fz - 1) / fz;
         p.f_nzsegs = (nz + p.f_zseg_h - 1) / p.f_zseg_h;
-        // second-order passes: x-y-x blocks over 28-cell strips x (warps - 4)-row tiles x z segments (planes
-        // are independent: ~8 blocks per SM of work); z-phase-z columns x z segments (~s3_zfactor x 1024
-        // threads per SM, segments of at least 16 planes: four halo planes each side)
-        p.s3_nstrips = (g->cfg.n[0] + 27) / 28;
-        p.s3_nytiles = (g->cfg.n[1] + (p.s3_warps - 4) - 1) / (p.s3_warps - 4);
-        const int64_t s3_tiles = p.s3_nstrips * p.s3_nytiles;
-        int64_t sz = std::max<int64_t>(1, (8 * (int64_t)g->sm_count + s3_tiles - 1) / s3_tiles);
-        sz = std::min<int64_t>(sz, nz);
-        p.s3_zseg_h = (nz + sz - 1) / sz;
-        p.s3_nzsegs = (nz + p.s3_zseg_h - 1) / p.s3_zseg_h;
-        int64_t zz = std::max<int64_t>(1, ((int64_t)p.s3_zfactor * 1024 * g->sm_count + ncol / 2) / std::max<int64_t>(1, ncol));
+        // second-order passes: x-y-x(-x-y-x) blocks over (32 - 4 nh)-cell strips x (warps - 4 nh)-row tiles x
+        // z segments (planes are independent: ~8 blocks per SM of work); z-phase-z columns x 2 plane parities
+        // x z segments (~s3_zfactor x 1024 threads per SM, segments of at least 16 planes: four halo planes
+        // each side)
+        for (int nh = 1; nh <= 2; ++nh) {
+            Plan::XY &q = p.s3_xy[nh - 1];
+            const int own = 32 - 4 * nh, rows = p.s3_warps - 4 * nh;
+            q.nstrips = (g->cfg.n[0] + own - 1) / own;
+            q.nytiles = (g->cfg.n[1] + rows - 1) / rows;
+            const int64_t tiles = q.nstrips * q.nytiles;
+            int64_t sz = std::max<int64_t>(1, (8 * (int64_t)g->sm_count + tiles - 1) / tiles);
+            sz = std::min<int64_t>(sz, nz);
+            q.zseg_h = (nz + sz - 1) / sz;
+            q.nzsegs = (nz + q.zseg_h - 1) / q.zseg_h;
+        }
+        int64_t zz = std::max<int64_t>(1, ((int64_t)p.s3_zfactor * 1024 * g->sm_count + ncol) / std::max<int64_t>(1, 2 * ncol));
         zz = std::min<int64_t>(zz, std::max<int64_t>(1, nz / 16));
         p.s3_z_seg_h = (nz + zz - 1) / zz;
         p.s3_z_nsegs = (nz + p.s3_z_seg_h - 1) / p.s3_z_seg_h;
@@ -268,7 +276,10 @@ dirac_status ensure_flux_part(dirac_grid *g) {
     if (fused_pass(g)) need = std::max(need, (size_t)(g->plan.f_nzsegs * g->plan.f_nytiles * g->plan.f_warps));
     if (sweep_mode(g) == 6) need = std::max(need, (size_t)axis_blocks(g));
     if (strang3d_fused(g))
-        need = std::max(need, (size_t)(2 * g->plan.s3_nzsegs * g->plan.s3_nytiles * g->plan.s3_warps));
+        for (int nh = 1; nh <= 2; ++nh) {
+            const Plan::XY &q = g->plan.s3_xy[nh - 1];
+            need = std::max(need, (size_t)(2 * nh * q.nzsegs * q.nytiles * g->plan.s3_warps));
+        }
     if (need <= g->flux_part_cap) return DIRAC_OK;
     if (g->flux_part) {
         cudaFree(g->flux_part);
@@ -311,31 +322,6 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     a.step0 = step0;
     a.inject_stall = g->inject_stall;
     const int mode = sweep_mode(g);
-    if (mode == 6 && p.s3_fused) {
-        // 3-D second-order step (Sec. 2.4) as three passes: x-y-x, z-phase-z, x-y-x.  Each sweep doubles the
-        // state and the table carries 1/256, so the states entering the four x sweeps are 1, 4, 1/8 and 1/2
-        // times the true state (flux scale 1/2 over its square); the step leaves the state in psi[parity ^ 1].
-        const int64_t ny = g->cfg.n[1], nz = g->cfg.n[2];
-        a.nsegs = p.s3_nzsegs * p.s3_nytiles * p.s3_warps;  // flux parts per x sweep
-        a.nplanes = 1;
-        a.in = g->psi[parity];
-        a.out = g->psi[parity ^ 1];
-        cudaError_t e = launch_strang_xy(a, g->fp32, p.s3_warps, ny, nz, p.s3_nstrips, p.s3_nytiles, p.s3_nzsegs,
-                                         p.s3_zseg_h, 0.5, 0.5 / 16.0, s);
-        if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order x-y-x pass launch");
-        g->launches++;
-        e = launch_strang_z(g->psi[parity ^ 1], g->psi[parity], g->table, g->cfg.n[0], ny, nz, a.periodic,
-                            g->table_full, a.ucoef, a.ucoef_n, step0, p.s3_z_nsegs, p.s3_z_seg_h, g->fp32, s);
-        if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order z-phase-z pass launch");
-        g->launches++;
-        a.in = g->psi[parity];
-        a.out = g->psi[parity ^ 1];
-        e = launch_strang_xy(a, g->fp32, p.s3_warps, ny, nz, p.s3_nstrips, p.s3_nytiles, p.s3_nzsegs, p.s3_zseg_h,
-                             0.5 * 64.0, 0.5 * 4.0, s);
-        if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order x-y-x pass launch");
-        g->launches++;
-        return DIRAC_OK;
-    }
     if (mode == 6) {
         // 3-D second-order step (Sec. 2.4): A(1) B(2) A(1) C(2) D C(2) A(1) B(2) A(1), cells moved per sweep in
         // parentheses.  Each sweep doubles the state and the table carries 1/256, so the state entering the
@@ -390,8 +376,57 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     return DIRAC_OK;
 }
 
+// A run of m >= 1 second-order 3-D steps as fused passes (Sec. 2.4): x-y-x, then m z-phase-z passes
+// separated by m - 1 x-y-x-x-y-x passes, then x-y-x; 2m + 1 launches from psi[parity], ending in
+// psi[parity ^ 1].  Each sweep doubles the state and the table carries 1/256, so the states entering a step's
+// four x sweeps are 1, 4, 1/8 and 1/2 times the true state (flux scale 1/2 over its square).
+dirac_status enqueue_strang3d_run(dirac_grid *g, int parity, int64_t m, cudaStream_t s, int64_t step0) {
+    const Plan &p = g->plan;
+    const bool flux = g->cfg.flux_face >= 0;
+    const int64_t ny = g->cfg.n[1], nz = g->cfg.n[2];
+    static const double first_half[4] = {0.5, 0.5 / 16.0, 0.0, 0.0};
+    static const double second_half[4] = {0.5 * 64.0, 0.5 * 4.0, 0.0, 0.0};
+    static const double both_halves[4] = {0.5 * 64.0, 0.5 * 4.0, 0.5, 0.5 / 16.0};
+    SweepArgs a{};
+    a.table = g->table;
+    a.nx = g->cfg.n[0];
+    a.nplanes = 1;
+    a.flux_face = flux ? g->cfg.flux_face : -1;
+    a.flux_part = g->flux_part;
+    a.flux_cum = g->flux_dev;
+    a.ticket = g->ticket;
+    a.err = g->ticket + 1;
+    a.vol = cell_volume(g);
+    a.periodic = g->cfg.boundary == DIRAC_BC_PERIODIC;
+    const double *ucoef = field_on(g) ? g->ucoef : nullptr;
+    const int64_t ucoef_n = (int64_t)(g->avec.size() / 3);
+    int par = parity;
+    auto xy = [&](int nh, const double *fs) -> dirac_status {
+        const Plan::XY &q = p.s3_xy[nh - 1];
+        a.in = g->psi[par];
+        a.out = g->psi[par ^ 1];
+        a.nsegs = q.nzsegs * q.nytiles * p.s3_warps;  // flux parts per x sweep
+        cudaError_t e = launch_strang_xy(a, g->fp32, p.s3_warps, nh, ny, nz, q.nstrips, q.nytiles, q.nzsegs, q.zseg_h,
+                                         fs, s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order x-y-x pass launch");
+        g->launches++;
+        par ^= 1;
+        return DIRAC_OK;
+    };
+    dirac_status st = xy(1, first_half);
+    for (int64_t i = 0; i < m && st == DIRAC_OK; ++i) {
+        cudaError_t e = launch_strang_z(g->psi[par], g->psi[par ^ 1], g->table, a.nx, ny, nz, a.periodic, g->table_full,
+                                        ucoef, ucoef_n, step0 + i, p.s3_z_nsegs, p.s3_z_seg_h, g->fp32, s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order z-phase-z pass launch");
+        g->launches++;
+        par ^= 1;
+        st = xy(i + 1 < m ? 2 : 1, i + 1 < m ? both_halves : second_half);
+    }
+    return st;
+}
+
 int block_flips(const dirac_grid *g) {
-    if (sweep_mode(g) == 6) return g->plan.s3_fused ? 1 : 0;  // three passes flip the parity, eight sweeps return
+    if (sweep_mode(g) == 6) return 0;  // eight sweeps per step: parity returns (fused runs: enqueue_strang3d_run)
     return (ndim_of(g) == 3 && !fused_pass(g)) ? 0 : 1;
 }
 
@@ -404,9 +439,13 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
     int par = parity;
     const int64_t l0 = g->launches;
     dirac_status st = DIRAC_OK;
-    for (int b = 0; b < kGraphBlocks && st == DIRAC_OK; ++b) {
-        st = enqueue_block(g, par, g->plan.K, g->cap_stream, 0);
-        par ^= block_flips(g);
+    if (strang3d_fused(g)) {
+        st = enqueue_strang3d_run(g, par, kGraphBlocks, g->cap_stream, 0);
+    } else {
+        for (int b = 0; b < kGraphBlocks && st == DIRAC_OK; ++b) {
+            st = enqueue_block(g, par, g->plan.K, g->cap_stream, 0);
+            par ^= block_flips(g);
+        }
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
@@ -426,7 +465,7 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
 }
 
 int64_t launches_per_block(const dirac_grid *g) {
-    if (sweep_mode(g) == 6) return g->plan.s3_fused ? 3 : 8;
+    if (sweep_mode(g) == 6) return 8;
     return 1 + ((ndim_of(g) == 3 && !fused_pass(g)) ? 1 : 0);
 }
 
@@ -438,6 +477,29 @@ dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
     if (field && !g->tuning && g->step + nsteps > (int64_t)(g->avec.size() / 3))
         return fail(g, DIRAC_ERR_ARG, "the vector-potential table ends before step " + std::to_string(g->step + nsteps));
     int64_t t = g->step;  // step index of the next launch (selects the field's table row)
+    if (strang3d_fused(g)) {
+        // runs of kGraphBlocks steps from the captured graph (2 kGraphBlocks + 1 launches, parity flips), then
+        // the rest as one run
+        int64_t left = nsteps;
+        if (g->cfg.use_graphs && !field)
+            while (left >= kGraphBlocks) {
+                cudaGraphExec_t ex = nullptr;
+                dirac_status st = get_graph(g, g->cur, &ex);
+                if (st != DIRAC_OK) return st;
+                CK(g, cudaGraphLaunch(ex, g->stream));
+                g->launches += 2 * kGraphBlocks + 1;
+                g->cur ^= 1;
+                left -= kGraphBlocks;
+                t += kGraphBlocks;
+            }
+        if (left > 0) {
+            dirac_status st = enqueue_strang3d_run(g, g->cur, left, g->stream, t);
+            if (st != DIRAC_OK) return st;
+            g->cur ^= 1;
+        }
+        g->step += nsteps;
+        return DIRAC_OK;
+    }
     // launches with a field take their step index as an argument: no graph replay
     if (g->cfg.use_graphs && !field && blocks >= kGraphBlocks) {
         while (blocks >= kGraphBlocks) {
@@ -496,7 +558,7 @@ void default_plan(dirac_grid *g) {
         // 0 = library choice (fused passes for FP32 storage, which is bandwidth-bound; single sweeps for
         // FP64, which is bound by the FP64 pipe and would recompute the x-y-x pass's halo cells)
         g->plan.s3_fused = pp == 1 ? 0 : (pp == 2 ? 1 : (g->fp32 ? 1 : 0));
-        g->plan.s3_warps = 16;
+        g->plan.s3_warps = 32;  // measured at 384^3: 24 owned rows of 32 beat 8 of 16 (more recomputed halo rows)
         make_plan(g, 1, pp > 0 ? pp : 2, 4, 16);
         return;
     }
@@ -931,9 +993,10 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
     if (strang3d_fused(g)) {
         info->plan = DIRAC_PLAN_3D_STRANG_FUSED;
         info->points_per_lane = 1;
-        info->launch_warps = p.s3_nstrips * p.s3_nytiles * p.s3_nzsegs * p.s3_warps;
-        info->strip_width = 28;
-        info->segment_rows = p.s3_zseg_h;
+        const Plan::XY &q = p.s3_xy[1];
+        info->launch_warps = q.nstrips * q.nytiles * q.nzsegs * p.s3_warps;
+        info->strip_width = 24;
+        info->segment_rows = q.zseg_h;
     }
     if (fused_pass(g)) {
         info->points_per_lane = 1;
@@ -954,13 +1017,13 @@ dirac_status dirac_autotune(dirac_grid *g) {
         int K, P, wpb, wsm;
         int fused = 0;  // 3-D: warps per block of the fused pass (0: two-pass path)
         int s3 = 0;     // 3-D second order: 0 = eight single sweeps, else warps per block of the x-y-x pass
-        int s3z = 4;    // and the z-phase-z pass's threads per SM / 1024
+        int s3z = 2;    // and the z-phase-z pass's threads per SM / 1024
     };
     std::vector<Cand> cands;
     if (sweep_mode(g) == 6) {
         cands.push_back({1, 2, 4, 16, 0, 0});
         for (int sw : {16, 32})
-            for (int zf : {2, 4, 8}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
+            for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
     } else if (g->cfg.ndim == 3) {
         if (!field_on(g))  // with a vector potential only the fused pass applies the phase matrix
             for (int P : {1, 2, 4})

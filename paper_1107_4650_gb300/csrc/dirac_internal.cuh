@@ -98,14 +98,15 @@ cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx
 cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
                            int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s);
 
-// 3-D second-order step as three passes (strang3d_kernels.cuh).  x-y-x pass: blocks of `warps` (16 or 32)
-// warps own a 28-cell x strip and warps - 4 rows along y over a z segment of zseg_h planes; fscale0/1 scale
-// the face flux of its two x sweeps; flux parts [2][nzsegs * nytiles * warps] (a.nsegs * a.nplanes must
-// equal nzsegs * nytiles * warps).  z-phase-z pass: one thread per column over nsegs segments of seg_h planes,
-// the phase from `table` (or, with ucoef, the vector-potential matrix of step step0).
-cudaError_t launch_strang_xy(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
-                             int64_t nytiles, int64_t nzsegs, int64_t zseg_h, double fscale0, double fscale1,
-                             cudaStream_t s);
+// 3-D second-order step as fused passes (strang3d_kernels.cuh).  x-y-x pass (nh = 1: half a step) or
+// x-y-x-x-y-x pass (nh = 2: the second half of one step and the first half of the next): blocks of `warps`
+// (16 or 32) warps own a (32 - 4 nh)-cell x strip and warps - 4 nh rows along y over a z segment of zseg_h
+// planes; fscale[s] scales the face flux of its x sweep s; flux parts [2 nh][nzsegs * nytiles * warps]
+// (a.nsegs * a.nplanes must equal nzsegs * nytiles * warps).  z-phase-z pass: one thread per column and
+// plane parity over nsegs segments of seg_h planes, the phase from `table` (or, with ucoef, the
+// vector-potential matrix of step step0).
+cudaError_t launch_strang_xy(const SweepArgs &a, int fp32, int warps, int nh, int64_t ny, int64_t nz, int64_t nstrips,
+                             int64_t nytiles, int64_t nzsegs, int64_t zseg_h, const double fscale[4], cudaStream_t s);
 cudaError_t launch_strang_z(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz,
                             int periodic, int full_table, const double *ucoef, int64_t ucoef_n, int64_t step0,
                             int64_t nsegs, int64_t seg_h, int fp32, cudaStream_t s);

@@ -1,12 +1,12 @@
-// Instantiations of the fused passes of the 3-D second-order step: the x-y-x pass with 16 or 32 warps per
-// block (12 or 28 owned rows per tile), the z-phase-z pass with and without a uniform vector potential.
+// Instantiations of the fused passes of the 3-D second-order step: the x-y-x (half step) and x-y-x-x-y-x
+// (two half steps) passes with 16 or 32 warps per block, the z-phase-z pass with and without a uniform
+// vector potential.
 #include "strang3d_kernels.cuh"
 
 namespace dirac {
 
-cudaError_t launch_strang_xy(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
-                             int64_t nytiles, int64_t nzsegs, int64_t zseg_h, double fscale0, double fscale1,
-                             cudaStream_t s) {
+cudaError_t launch_strang_xy(const SweepArgs &a, int fp32, int warps, int nh, int64_t ny, int64_t nz, int64_t nstrips,
+                             int64_t nytiles, int64_t nzsegs, int64_t zseg_h, const double fscale[4], cudaStream_t s) {
     StrangXYArgs A{};
     A.s = a;
     A.ny = ny;
@@ -15,10 +15,14 @@ cudaError_t launch_strang_xy(const SweepArgs &a, int fp32, int warps, int64_t ny
     A.nytiles = nytiles;
     A.nzsegs = nzsegs;
     A.zseg_h = zseg_h;
-    A.fscale0 = fscale0;
-    A.fscale1 = fscale1;
-    if (warps == 16) return fp32 ? launch_strang_xy_one<float, 16>(A, s) : launch_strang_xy_one<double, 16>(A, s);
-    if (warps == 32) return fp32 ? launch_strang_xy_one<float, 32>(A, s) : launch_strang_xy_one<double, 32>(A, s);
+    for (int q = 0; q < 4; ++q) A.fscale[q] = fscale[q];
+    if (nh == 1) {
+        if (warps == 16) return fp32 ? launch_strang_xy_one<float, 16, 1>(A, s) : launch_strang_xy_one<double, 16, 1>(A, s);
+        if (warps == 32) return fp32 ? launch_strang_xy_one<float, 32, 1>(A, s) : launch_strang_xy_one<double, 32, 1>(A, s);
+    } else if (nh == 2) {
+        if (warps == 16) return fp32 ? launch_strang_xy_one<float, 16, 2>(A, s) : launch_strang_xy_one<double, 16, 2>(A, s);
+        if (warps == 32) return fp32 ? launch_strang_xy_one<float, 32, 2>(A, s) : launch_strang_xy_one<double, 32, 2>(A, s);
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -1,29 +1,34 @@
 // Fused passes of the 3-D second-order step (Sec. 2.4, dt = 4 dx / c):
 //   A(1) B(2) A(1) | C(2) D C(2) | A(1) B(2) A(1)     (cells moved per sweep in parentheses)
-// run as three passes over HBM instead of eight single-sweep launches: an x-y-x pass, a z-phase-z pass and
-// the x-y-x pass again.  Arithmetic is that of the single-sweep kernels (axis_kernels.cuh), operation by
-// operation, so the result is the same bit for bit in either storage precision; only where the
+// A run of m steps is 2m + 1 passes over HBM instead of 8m single-sweep launches:
+//   x-y-x, then m times z-phase-z, separated by x-y-x-x-y-x passes (the second half of one step and the
+// first half of the next), then x-y-x.  Arithmetic is that of the single-sweep kernels (axis_kernels.cuh),
+// operation by operation, so the result is the same bit for bit in either storage precision; only where the
 // intermediate states live changes (registers and shared memory instead of HBM).
 //
-// x-y-x pass (per z plane; planes are independent): a block of W warps owns a 28-cell x strip (lane l
-// holds cell x0 - 2 + l: two halo cells each side, one per x sweep) and W - 4 rows along y (warp w holds
-// row y0 - 2 + w: two halo rows each side for the two-cell y sweep).  Per plane:
-//   * every warp loads its row, x-sweeps it with shuffles (valid on lanes 1..30) and writes the row's
-//     y characteristics to shared memory (double-buffered by plane: one block barrier per plane);
-//   * the owned warps y-sweep their row from rows y - 2 ("+y" movers) and y + 2 ("-y" movers), zero the
-//     cells outside the grid (zero boundary), x-sweep again (valid on lanes 2..29) and store.
-// Face flux: both x sweeps add, on the face strip's owned rows, 1/2 (|u14|^2 + |u23|^2) of cell face - 1
-// and subtract 1/2 (|w14|^2 + |w23|^2) of cell face, of the state entering that sweep, times 1 / s^2 for
-// the state's scale s; one part per (sweep, z segment, y tile, warp), folded by the last block.
+// x-y-x pass (NH = 1 half step) and x-y-x-x-y-x pass (NH = 2), per z plane (planes are independent): a block
+// of W warps owns an x strip of 32 - 4 NH cells (lane l holds cell x0 - 2 NH + l: one halo cell each side per
+// x sweep) and W - 4 NH rows along y (warp w holds row y0 - 2 NH + w: two halo rows each side per two-cell
+// y sweep).  Per plane and half step:
+//   * the warps x-sweep their row with shuffles and write its y characteristics to shared memory; after a
+//     block barrier the warps two rows inside y-sweep their row from rows y - 2 ("+y" movers) and y + 2
+//     ("-y" movers), zero the cells outside the grid (zero boundary), x-sweep again;
+//   * NH = 2: that state (zeroed outside the grid) starts the next half step the same way, two rows further in.
+// The owned lanes of the owned rows store.  NH = 1 double-buffers its shared rows by plane (one barrier per
+// plane); NH = 2 has two barriers per plane, which order every reuse of its two single buffers.
+// Face flux: every x sweep adds, on the face strip's owned rows, 1/2 (|u14|^2 + |u23|^2) of cell face - 1 and
+// subtracts 1/2 (|w14|^2 + |w23|^2) of cell face, of the state entering it, times 1 / s^2 for the state's
+// scale s (fscale); one part per (sweep, z segment, y tile, warp), folded by the last block.
 //
 // z-phase-z pass: the two-cell z sweeps couple plane k only with planes k - 2 and k + 2, and the phase is
 // pointwise, so even and odd planes form two independent chains.  One thread per (x, y) column and plane
 // parity streams its chain over a segment of planes (plus four halo planes each side).  Input plane k
 // gives the characteristic sums U = (s1 + s3, s2 - s4) and W = (s1 - s3, s2 + s4); the first sweep's output
 // at plane j = k - 2 is U(j - 2) + W(j + 2) (U of the chain's last two planes in a register ring), the phase
-// of Eq. sol_dis_4 (table carrying the eight sweeps' 1/256) follows, cells outside the grid are zeroed,
-// and the second sweep's output at plane k - 4 is formed the same way from a second ring.  The loop takes
-// two chain planes per iteration so every ring index is a constant.
+// of Eq. sol_dis_4 (table carrying the eight sweeps' 1/256, its entries loaded with the state's planes
+// ahead of use) follows, cells outside the grid are zeroed, and the second sweep's output at plane k - 4 is
+// formed the same way from a second ring.  The loop takes two chain planes per iteration so every ring
+// index is a constant.
 #pragma once
 
 #include "step_kernels.cuh"
@@ -31,10 +36,10 @@
 namespace dirac {
 
 struct StrangXYArgs {
-    SweepArgs s;          // in, out, flux fields; flux parts [2][nzsegs * nytiles * W]
+    SweepArgs s;          // in, out, flux fields; flux parts [2 NH][nzsegs * nytiles * W]
     int64_t ny, nz;
     int64_t nstrips, nytiles, nzsegs, zseg_h;
-    double fscale0, fscale1;  // 1/2 over the square of the scale of the state entering each x sweep
+    double fscale[4];     // per x sweep: 1/2 over the square of the scale of the state entering it
 };
 
 struct StrangZArgs {
@@ -42,7 +47,7 @@ struct StrangZArgs {
     void *out;
     const void *table;
     int64_t nx, ny, nz;
-    int64_t seg_h;        // planes per z segment (blockIdx.y = segment)
+    int64_t seg_h;        // planes per z segment (blockIdx.y = 2 segment + plane parity)
     int periodic, full_table;
     const double *ucoef;  // uniform vector potential: U entries per step (12 doubles), or null
     int64_t ucoef_n, step0;
@@ -51,62 +56,117 @@ struct StrangZArgs {
 // resident blocks per SM the register budget is fitted to: two 16-warp blocks in FP32
 template <typename T, int W> struct XYMinBlocks { static constexpr int value = (sizeof(T) == 4 && W == 16) ? 2 : 1; };
 // z-phase-z pass: 128-thread blocks per SM the register budget is fitted to
-template <typename T, bool FIELD> struct ZMinBlocks { static constexpr int value = sizeof(T) == 4 ? (FIELD ? 4 : 5) : (FIELD ? 3 : 4); };
+template <typename T, bool FIELD> struct ZMinBlocks { static constexpr int value = sizeof(T) == 4 ? 4 : 3; };
 
-template <typename T, int W>
-__global__ void __launch_bounds__(32 * W, XYMinBlocks<T, W>::value) strang_xy_kernel(const StrangXYArgs A) {
-    constexpr int H = W - 4;
+template <typename T>
+__device__ __forceinline__ T face_term(Cx<T> p14, Cx<T> p23) {
+    return Ar<T>::fma(p14.re, p14.re, Ar<T>::fma(p14.im, p14.im, Ar<T>::fma(p23.re, p23.re, Ar<T>::mul(p23.im, p23.im))));
+}
+
+// A: x sweep, one cell (Eq. sol_dis_1), of a row held one cell per lane; the output (2x the swept state) is
+// valid on lanes whose two neighbours hold valid cells.  The face lanes add their term of the entering state.
+template <typename T>
+__device__ __forceinline__ void xsweep_row(const Cx<T> s[4], Cx<T> o[4], int lane, bool fl_u, bool fl_w, T &fp) {
+    const Cx<T> u14 = cadd(s[0], s[3]), w14 = csub(s[0], s[3]);
+    const Cx<T> u23 = cadd(s[1], s[2]), w23 = csub(s[1], s[2]);
+    if (fl_u) fp = Ar<T>::add(fp, face_term(u14, u23));
+    if (fl_w) fp = Ar<T>::sub(fp, face_term(w14, w23));
+    const Cx<T> lu14 = shfl_c(u14, (lane + 31) & 31), lu23 = shfl_c(u23, (lane + 31) & 31);
+    const Cx<T> rw14 = shfl_c(w14, (lane + 1) & 31), rw23 = shfl_c(w23, (lane + 1) & 31);
+    o[0] = cadd(lu14, rw14);
+    o[3] = csub(lu14, rw14);
+    o[1] = cadd(lu23, rw23);
+    o[2] = csub(lu23, rw23);
+}
+
+// y characteristics of row w (Eq. sol_dis_2): "+y" movers (a1 - i a4, a2 + i a3), "-y" movers (a1 + i a4, a2 - i a3)
+template <typename T>
+__device__ __forceinline__ void ywrite_row(Cx<T> *buf, int w, int lane, const Cx<T> a[4]) {
+    buf[(w * 4 + 0) * 32 + lane] = csub_ib(a[0], a[3]);
+    buf[(w * 4 + 1) * 32 + lane] = cadd_ib(a[1], a[2]);
+    buf[(w * 4 + 2) * 32 + lane] = cadd_ib(a[0], a[3]);
+    buf[(w * 4 + 3) * 32 + lane] = csub_ib(a[1], a[2]);
+}
+
+// B: y sweep, two cells, of row w: "+y" movers of row w - 2, "-y" movers of row w + 2
+template <typename T>
+__device__ __forceinline__ void ysweep_row(const Cx<T> *buf, int w, int lane, Cx<T> q[4]) {
+    const Cx<T> U14 = buf[((w - 2) * 4 + 0) * 32 + lane], U23 = buf[((w - 2) * 4 + 1) * 32 + lane];
+    const Cx<T> W14 = buf[((w + 2) * 4 + 2) * 32 + lane], W23 = buf[((w + 2) * 4 + 3) * 32 + lane];
+    q[0] = cadd(U14, W14);
+    q[3] = cmul_i(csub(U14, W14));
+    q[1] = cadd(U23, W23);
+    q[2] = cmul_mi(csub(U23, W23));
+}
+
+template <typename T>
+__device__ __forceinline__ void zero_pt(Cx<T> q[4]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = {T(0), T(0)};
+}
+
+// One block's planes.  FLUX: the block's strip holds the face (the face terms are formed only here); EDGE:
+// the block's cells reach outside the grid under the zero boundary (only here are cells zeroed).
+template <typename T, int W, int NH, bool FLUX, bool EDGE>
+__device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int64_t strip, const int64_t ytile,
+                                                const int64_t zseg, Cx<T> *ych) {
+    constexpr int HX = 2 * NH;       // halo lanes (x) and halo rows (y) on each side
+    constexpr int OWN = 32 - 2 * HX;
+    constexpr int H = W - 2 * HX;
+    constexpr int NS = 2 * NH;       // x sweeps per pass
     const SweepArgs &a = A.s;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t b = blockIdx.x;
-    const int64_t strip = b % A.nstrips;
-    const int64_t rest = b / A.nstrips;
-    const int64_t ytile = rest % A.nytiles;
-    const int64_t zseg = rest / A.nytiles;
     const int64_t nx = a.nx, ny = A.ny, nz = A.nz;
     const bool per = a.periodic != 0;
-    const int64_t x_own0 = strip * 28, x_own1 = min(x_own0 + 28, nx);
-    const int64_t x = x_own0 - 2 + lane;
-    const int64_t y = ytile * H - 2 + w;
-    const bool owned_row = w >= 2 && w < W - 2 && y < ny;
+    const int64_t x_own0 = strip * OWN, x_own1 = min(x_own0 + OWN, nx);
+    const int64_t x = x_own0 - HX + lane;
+    const int64_t y = ytile * H - HX + w;
+    const bool owned_row = w >= HX && w < W - HX && y < ny;
+    const bool mid_row = w >= 2 && w < W - 2;  // NH = 2: rows of the first half step's second sweep pair
     const bool own_lane = x >= x_own0 && x < x_own1;
     const int64_t z_begin = zseg * A.zseg_h, z_end = min(z_begin + A.zseg_h, nz);
-    const bool xin = x >= 0 && x < nx, yin = y >= 0 && y < ny;
+    const bool ghost = EDGE && !(x >= 0 && x < nx && y >= 0 && y < ny);  // outside the grid (zero boundary)
     const int64_t xl = per ? pmod(x, nx) : min(max(x, (int64_t)0), nx - 1);
     const int64_t yl = per ? pmod(y, ny) : min(max(y, (int64_t)0), ny - 1);
-    const T *in = static_cast<const T *>(a.in);
-    T *out = static_cast<T *>(a.out);
-
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
-    Cx<T> *ych = reinterpret_cast<Cx<T> *>(dyn_smem);  // [2][W][4][32]
+    // this lane's cell in plane z_begin (owned lanes of owned rows: xl = x, yl = y); planes nx ny 8 apart
+    const int64_t plane = nx * ny * 8;
+    const T *src = static_cast<const T *>(a.in) + ((z_begin * ny + yl) * nx + xl) * 8;
+    T *dst = static_cast<T *>(a.out) + ((z_begin * ny + yl) * nx + xl) * 8;
 
     const int64_t face = a.flux_face;
-    const bool face_warp = owned_row && face >= x_own0 && face < x_own1;
-    const bool fl_u = face_warp && x == face - 1, fl_w = face_warp && x == face;
-    double facc0 = 0.0, facc1 = 0.0;
-    T fp0 = T(0), fp1 = T(0);
-
-    const bool row_ok = per || (yin && xin);
-    auto load_row = [&](int64_t k, Cx<T> s[4]) {
-        if (row_ok) {
-            load_pt(in + ((k * ny + yl) * nx + xl) * 8, s);
-        } else {
+    const bool fw = FLUX && owned_row;  // warp-uniform
+    const bool fl_u = fw && x == face - 1, fl_w = fw && x == face;
+    double facc[NS];
+    T fp[NS];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) s[c] = {T(0), T(0)};
+    for (int q = 0; q < NS; ++q) {
+        facc[q] = 0.0;
+        fp[q] = T(0);
+    }
+    auto sweep_x = [&](const Cx<T> in4[4], Cx<T> out4[4], T &acc) {
+        if (FLUX && fw) {
+            xsweep_row(in4, out4, lane, fl_u, fl_w, acc);
+        } else {
+            xsweep_row(in4, out4, lane, false, false, acc);
         }
     };
+
     // planes in flight: two ahead in FP32 (bandwidth-bound), one in FP64
     constexpr int LA = sizeof(T) == 4 ? 2 : 1;
     Cx<T> ring[LA][4];
 #pragma unroll
-    for (int j = 0; j < LA; ++j)
-        if (z_begin + j < z_end) load_row(z_begin + j, ring[j]);
+    for (int j = 0; j < LA; ++j) {
+        if (z_begin + j < z_end) {
+            if (!ghost) {
+                load_pt(src + j * plane, ring[j]);
+            } else {
+                zero_pt(ring[j]);
+            }
+        }
+    }
+    const T *ld = src + LA * plane;
 
-    auto face_term = [&](Cx<T> p14, Cx<T> p23) -> T {
-        return Ar<T>::fma(p14.re, p14.re, Ar<T>::fma(p14.im, p14.im, Ar<T>::fma(p23.re, p23.re, Ar<T>::mul(p23.im, p23.im))));
-    };
-
-    for (int64_t k = z_begin; k < z_end; ++k) {
+    for (int64_t k = z_begin; k < z_end; ++k, ld += plane, dst += plane) {
         Cx<T> st[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) st[c] = ring[0][c];
@@ -114,73 +174,92 @@ __global__ void __launch_bounds__(32 * W, XYMinBlocks<T, W>::value) strang_xy_ke
         for (int j = 0; j + 1 < LA; ++j)
 #pragma unroll
             for (int c = 0; c < 4; ++c) ring[j][c] = ring[j + 1][c];
-        if (k + LA < z_end) load_row(k + LA, ring[LA - 1]);
-
-        // A: x sweep, one cell (Eq. sol_dis_1)
-        const Cx<T> u14 = cadd(st[0], st[3]), w14 = csub(st[0], st[3]);
-        const Cx<T> u23 = cadd(st[1], st[2]), w23 = csub(st[1], st[2]);
-        if (fl_u) fp0 = Ar<T>::add(fp0, face_term(u14, u23));
-        if (fl_w) fp0 = Ar<T>::sub(fp0, face_term(w14, w23));
-        const Cx<T> lu14 = shfl_c(u14, (lane + 31) & 31), lu23 = shfl_c(u23, (lane + 31) & 31);
-        const Cx<T> rw14 = shfl_c(w14, (lane + 1) & 31), rw23 = shfl_c(w23, (lane + 1) & 31);
-        const Cx<T> a0 = cadd(lu14, rw14), a3 = csub(lu14, rw14);
-        const Cx<T> a1 = cadd(lu23, rw23), a2 = csub(lu23, rw23);
-        // y characteristics (Eq. sol_dis_2): "+y" movers (a1 - i a4, a2 + i a3), "-y" movers (a1 + i a4, a2 - i a3)
-        Cx<T> *buf = ych + (size_t)((k - z_begin) & 1) * (W * 4 * 32);
-        buf[(w * 4 + 0) * 32 + lane] = csub_ib(a0, a3);
-        buf[(w * 4 + 1) * 32 + lane] = cadd_ib(a1, a2);
-        buf[(w * 4 + 2) * 32 + lane] = cadd_ib(a0, a3);
-        buf[(w * 4 + 3) * 32 + lane] = csub_ib(a1, a2);
-        __syncthreads();
-        if (owned_row) {
-            // B: y sweep, two cells: "+y" movers of row y - 2, "-y" movers of row y + 2
-            const Cx<T> U14 = buf[((w - 2) * 4 + 0) * 32 + lane], U23 = buf[((w - 2) * 4 + 1) * 32 + lane];
-            const Cx<T> W14 = buf[((w + 2) * 4 + 2) * 32 + lane], W23 = buf[((w + 2) * 4 + 3) * 32 + lane];
-            Cx<T> q[4];
-            q[0] = cadd(U14, W14);
-            q[3] = cmul_i(csub(U14, W14));
-            q[1] = cadd(U23, W23);
-            q[2] = cmul_mi(csub(U23, W23));
-            if (!per && !xin) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) q[c] = {T(0), T(0)};
+        if (k + LA < z_end) {
+            if (!ghost) {
+                load_pt(ld, ring[LA - 1]);
+            } else {
+                zero_pt(ring[LA - 1]);
             }
-            // A: x sweep, one cell
-            const Cx<T> v14 = cadd(q[0], q[3]), x14 = csub(q[0], q[3]);
-            const Cx<T> v23 = cadd(q[1], q[2]), x23 = csub(q[1], q[2]);
-            if (fl_u) fp1 = Ar<T>::add(fp1, face_term(v14, v23));
-            if (fl_w) fp1 = Ar<T>::sub(fp1, face_term(x14, x23));
-            const Cx<T> lv14 = shfl_c(v14, (lane + 31) & 31), lv23 = shfl_c(v23, (lane + 31) & 31);
-            const Cx<T> rx14 = shfl_c(x14, (lane + 1) & 31), rx23 = shfl_c(x23, (lane + 1) & 31);
-            Cx<T> o[4];
-            o[0] = cadd(lv14, rx14);
-            o[3] = csub(lv14, rx14);
-            o[1] = cadd(lv23, rx23);
-            o[2] = csub(lv23, rx23);
-            if (own_lane) store_pt(out + ((k * ny + y) * nx + x) * 8, o);
         }
-        if ((fl_u || fl_w) && (((k - z_begin) & 31) == 31 || k == z_end - 1)) {
-            facc0 = __dadd_rn(facc0, (double)fp0);
-            facc1 = __dadd_rn(facc1, (double)fp1);
-            fp0 = T(0);
-            fp1 = T(0);
+
+        Cx<T> t[4], q[4];
+        sweep_x(st, t, fp[0]);
+        Cx<T> *buf1 = NH == 1 ? ych + (size_t)((k - z_begin) & 1) * (W * 4 * 32) : ych;
+        ywrite_row(buf1, w, lane, t);
+        __syncthreads();
+        if (NH == 1) {
+            if (owned_row) {
+                ysweep_row(buf1, w, lane, q);
+                if (ghost) zero_pt(q);
+                sweep_x(q, t, fp[1]);
+                if (own_lane) store_pt(dst, t);
+            }
+        } else {
+            Cx<T> *buf2 = ych + W * 4 * 32;
+            if (mid_row) {
+                ysweep_row(buf1, w, lane, q);
+                if (ghost) zero_pt(q);
+                sweep_x(q, t, fp[1]);
+                if (ghost) zero_pt(t);  // the state between the two half steps
+                sweep_x(t, q, fp[NS > 2 ? 2 : 0]);
+                ywrite_row(buf2, w, lane, q);
+            }
+            __syncthreads();
+            if (owned_row) {
+                ysweep_row(buf2, w, lane, q);
+                if (ghost) zero_pt(q);
+                sweep_x(q, t, fp[NS > 3 ? 3 : 0]);
+                if (own_lane) store_pt(dst, t);
+            }
         }
-    }
-    if (face >= 0 && face >= x_own0 && face < x_own1) {
-        // one part per (sweep, z segment, y tile, warp) of the strip that owns the face; other warps write 0
+        if (FLUX && fw && (fl_u || fl_w) && (((k - z_begin) & 31) == 31 || k == z_end - 1)) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            facc0 = __dadd_rn(facc0, __shfl_xor_sync(0xffffffffu, facc0, o));
-            facc1 = __dadd_rn(facc1, __shfl_xor_sync(0xffffffffu, facc1, o));
-        }
-        const int64_t nparts = A.nzsegs * A.nytiles * W;
-        const int64_t q = (zseg * A.nytiles + ytile) * W + w;
-        if (lane == 0) {
-            a.flux_part[q] = __dmul_rn(A.fscale0, facc0);
-            a.flux_part[nparts + q] = __dmul_rn(A.fscale1, facc1);
+            for (int s2 = 0; s2 < NS; ++s2) {
+                facc[s2] = __dadd_rn(facc[s2], (double)fp[s2]);
+                fp[s2] = T(0);
+            }
         }
     }
-    if (face >= 0) finish_flux<2>(a);
+    if (FLUX) {
+        // one part per (sweep, z segment, y tile, warp) of the strip that owns the face; other warps write 0
+        const int64_t nparts = A.nzsegs * A.nytiles * W;
+        const int64_t qi = (zseg * A.nytiles + ytile) * W + w;
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2) {
+            double f = facc[s2];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) f = __dadd_rn(f, __shfl_xor_sync(0xffffffffu, f, o));
+            if (lane == 0) a.flux_part[s2 * nparts + qi] = __dmul_rn(A.fscale[s2], f);
+        }
+    }
+}
+
+template <typename T, int W, int NH>
+__global__ void __launch_bounds__(32 * W, XYMinBlocks<T, W>::value) strang_xy_kernel(const StrangXYArgs A) {
+    constexpr int HX = 2 * NH;
+    constexpr int OWN = 32 - 2 * HX;
+    constexpr int H = W - 2 * HX;
+    const SweepArgs &a = A.s;
+    const int64_t b = blockIdx.x;
+    const int64_t strip = b % A.nstrips;
+    const int64_t rest = b / A.nstrips;
+    const int64_t ytile = rest % A.nytiles;
+    const int64_t zseg = rest / A.nytiles;
+    const int64_t nx = a.nx, ny = A.ny;
+    const int64_t x0 = strip * OWN - HX, y0 = ytile * H - HX;  // the block's first lane cell and row
+    const int64_t face = a.flux_face;
+    const bool fblk = face >= 0 && face >= strip * OWN && face < min(strip * OWN + OWN, nx);
+    const bool eblk = a.periodic == 0 && (x0 < 0 || x0 + 32 > nx || y0 < 0 || y0 + W > ny);
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    Cx<T> *ych = reinterpret_cast<Cx<T> *>(dyn_smem);  // [2][W][4][32]
+    if (fblk) {
+        if (eblk) strang_xy_block<T, W, NH, true, true>(A, strip, ytile, zseg, ych);
+        else strang_xy_block<T, W, NH, true, false>(A, strip, ytile, zseg, ych);
+    } else {
+        if (eblk) strang_xy_block<T, W, NH, false, true>(A, strip, ytile, zseg, ych);
+        else strang_xy_block<T, W, NH, false, false>(A, strip, ytile, zseg, ych);
+    }
+    if (face >= 0) finish_flux<2 * NH>(a);
 }
 
 template <typename T, bool FIELD>
@@ -222,9 +301,19 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
     const int64_t k_first = z_begin - 4 + ((par - z_begin) & 1);
     const int64_t k_last = z_end + 3 - (((z_end + 3) - par) & 1);
     constexpr int LA = sizeof(T) == 4 ? 2 : 1;
-    Cx<T> pre[LA][4];
+    // the phase at plane j = k - 2 takes the table entry loaded with input plane k
+    auto load_phase = [&](int64_t k, Cx<T> &qu, Cx<T> &qd) {
+        const int64_t j = k - 2;
+        if (a.full_table && (per || (j >= 0 && j < nz))) load_tab(tab + ((per ? pmod(j, nz) : j) * ncol + col) * 4, qu, qd);
+    };
+    Cx<T> pre[LA][4], tpu[LA], tpd[LA];
 #pragma unroll
-    for (int j = 0; j < LA; ++j) load_plane(k_first + 2 * j, pre[j]);
+    for (int j = 0; j < LA; ++j) {
+        load_plane(k_first + 2 * j, pre[j]);
+        tpu[j] = pu;
+        tpd[j] = pd;
+        load_phase(k_first + 2 * j, tpu[j], tpd[j]);
+    }
 
     for (int64_t k0 = k_first; k0 <= k_last; k0 += 4) {
 #pragma unroll
@@ -234,11 +323,18 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
             Cx<T> s[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) s[c] = pre[0][c];
+            const Cx<T> qu = tpu[0], qd = tpd[0];
 #pragma unroll
-            for (int j = 0; j + 1 < LA; ++j)
+            for (int j = 0; j + 1 < LA; ++j) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) pre[j][c] = pre[j + 1][c];
-            if (k + 2 * LA <= k_last) load_plane(k + 2 * LA, pre[LA - 1]);
+                tpu[j] = tpu[j + 1];
+                tpd[j] = tpd[j + 1];
+            }
+            if (k + 2 * LA <= k_last) {
+                load_plane(k + 2 * LA, pre[LA - 1]);
+                load_phase(k + 2 * LA, tpu[LA - 1], tpd[LA - 1]);
+            }
             // C: z sweep, two cells (Eq. sol_dis_3): output plane j = k - 2 from U(k - 4) and W(k)
             const Cx<T> U13 = cadd(s[0], s[2]), U24 = csub(s[1], s[3]);
             const Cx<T> W13 = csub(s[0], s[2]), W24 = cadd(s[1], s[3]);
@@ -252,8 +348,6 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
             // D: phase of Eq. sol_dis_4 at plane j (zero outside the grid under the zero boundary)
             const int64_t j = k - 2;
             if (per || (j >= 0 && j < nz)) {
-                Cx<T> qu = pu, qd = pd;
-                if (a.full_table) load_tab(tab + ((per ? pmod(j, nz) : j) * ncol + col) * 4, qu, qd);
                 if (FIELD) {
                     // (U_ab g) psi_b over the non-zero entries, columns in order, g = the table's exp(-i V dt)
                     Cx<T> m6[FIELD ? 6 : 1];
@@ -294,7 +388,7 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
     }
 }
 
-template <typename T, int W>
+template <typename T, int W, int NH>
 static cudaError_t launch_strang_xy_one(const StrangXYArgs &A, cudaStream_t s) {
     const int64_t blocks = A.nstrips * A.nytiles * A.nzsegs;
     if (blocks <= 0) return cudaSuccess;
@@ -303,11 +397,11 @@ static cudaError_t launch_strang_xy_one(const StrangXYArgs &A, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 64 || !(done & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(strang_xy_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(strang_xy_kernel<T, W, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         if (dev < 64) done |= 1ull << dev;
     }
-    strang_xy_kernel<T, W><<<(unsigned)blocks, 32 * W, smem, s>>>(A);
+    strang_xy_kernel<T, W, NH><<<(unsigned)blocks, 32 * W, smem, s>>>(A);
     return cudaGetLastError();
 }
 

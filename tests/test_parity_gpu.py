@@ -620,7 +620,43 @@ def test_strang3d_fp64_bit_exact(D, shape, periodic, full, pp):
     finally:
         D.dirac_destroy(h)
     assert info["plan"] == getattr(D, S3_PLANS[pp])
-    assert info["kernel_launches"] == 5 * (8 if pp == 1 else 3)
+    assert info["kernel_launches"] == (5 * 8 if pp == 1 else 2 * 5 + 1)
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 33, 70])
+@pytest.mark.parametrize("graphs", [False, True])
+def test_strang3d_fused_runs_bit_exact(D, steps, graphs):
+    """Runs of m steps as 2m + 1 fused passes (the x-y-x-x-y-x pass joins consecutive steps), from a captured
+    graph of 32 steps and as a plain run of the rest, in two calls: the state after every call is the
+    oracle's, bit for bit."""
+    nx, ny, nz = 37, 26, 21
+    psi = W.random_state(nz, ny, nx, seed=steps)
+    V = np.random.default_rng(steps + 1).uniform(-4e4, 4e4, nx * ny * nz)
+    first = steps // 2
+    mid, _ = oracle.step_strang3d(psi, 1.0, C, DX, first, V=V, periodic=False) if first else (psi, 0.0)
+    want, _ = oracle.step_strang3d(mid, 1.0, C, DX, steps - first, V=V, periodic=False)
+    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=2, use_graphs=graphs)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+        D.dirac_set_state(h, psi)
+        got_mid = np.empty_like(psi)
+        if first:
+            D.dirac_step(h, first)
+            D.dirac_get_state(h, got_mid)
+        D.dirac_step(h, steps - first)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    runs = [r for r in (first, steps - first) if r]
+    # a graph holds a run of 32 steps (65 launches); the rest of a call is one run of 2 r' + 1 launches
+    launches = sum(2 * r + r // 32 + (1 if r % 32 else 0) if graphs else 2 * r + 1 for r in runs)
+    assert info["kernel_launches"] == launches
+    if first:
+        assert _bits_equal(got_mid, mid)
     assert _bits_equal(got, want), rel_l2(got, want)
 
 
