@@ -80,12 +80,13 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
             for (int c = 0; c < 4; ++c) s[c] = {T(0), T(0)};
         }
     };
-    // rows of the next planes in flight: one ahead in FP64 (bound by the FP64 pipe), two ahead in FP32
-    // (bound by load latency with 16 warps per SM)
-    constexpr bool DEEP = sizeof(T) == 4;
-    Cx<T> nxt[4], nxt2[DEEP ? 4 : 1];
-    load_row(z_begin - 1, nxt);
-    if (DEEP) load_row(z_begin, nxt2);
+    // rows of the next planes in flight: one ahead in FP64 (bound by the FP64 pipe), two in FP32 (three or
+    // four measured no faster at 256^3 and 384^3: the per-plane block barrier is the limit there)
+    constexpr int LA = sizeof(T) == 4 ? 2 : 1;
+    Cx<T> ring[LA][4];
+#pragma unroll
+    for (int j = 0; j < LA; ++j)
+        if (z_begin - 1 + j <= z_end) load_row(z_begin - 1 + j, ring[j]);
 
     // per-cell table entries of the next output plane, loaded one plane ahead (full table only)
     Cx<T> tu = pu, td = pd, tu_next = pu, td_next = pd;
@@ -98,14 +99,12 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
         }
         Cx<T> st[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) st[c] = nxt[c];
-        if (DEEP) {
+        for (int c = 0; c < 4; ++c) st[c] = ring[0][c];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) nxt[c] = nxt2[DEEP ? c : 0];
-            if (k + 2 <= z_end) load_row(k + 2, nxt2);
-        } else {
-            if (k + 1 <= z_end) load_row(k + 1, nxt);
-        }
+        for (int j = 0; j + 1 < LA; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ring[j][c] = ring[j + 1][c];
+        if (k + LA <= z_end) load_row(k + LA, ring[LA - 1]);
         // x characteristics and the x sweep (neighbours by shuffle; lanes 0 and 31 are halo cells)
         const Cx<T> u14 = cadd(st[0], st[3]), w14 = csub(st[0], st[3]);
         const Cx<T> u23 = cadd(st[1], st[2]), w23 = csub(st[1], st[2]);
