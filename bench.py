@@ -25,6 +25,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -74,6 +75,8 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--check-points", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-detail-seconds", type=float, default=3.0,
+                    help="per sample of the CPU oracle detail (one thread; 3-D grid; ensemble); 0 = skip")
     return ap.parse_args()
 
 
@@ -164,6 +167,87 @@ def cpu_baseline(run, seconds: float):
     desc = ("FP64 CPU oracle, %d OpenMP threads, %dx%d crop of the Klein run (width 50 dx), %d time steps in %.1f s"
             % (ncores, side, side, done, dt))
     return rate, ncores, desc
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+_ONE_THREAD = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+import oracle
+from paper_1107_4650_gb300 import workloads as W
+side = 512
+run = W.KleinRun(side=side, V0=%r, p0=%r, width=%r, nsteps=1, dx=%r, L=%r)
+psi, V = run.state(), run.potential()
+face = run.geometry()[4]
+done, F, t0 = 0, 0.0, time.perf_counter()
+while True:
+    psi, F = oracle.step(psi, 2, 1.0, W.C_AU, run.dx, 5, V=V, flux_face=face, flux_cum=F)
+    done += 5
+    if time.perf_counter() - t0 >= %r:
+        break
+print(json.dumps({"rate": side * side * done / (time.perf_counter() - t0), "steps": done}))
+"""
+
+
+def cpu_detail(run, seconds: float) -> dict:
+    """Oracle timings beside the headline CPU baseline, each a bounded sample of about `seconds`: the host's CPU
+    model and core count; the 2-D Klein run on one thread (512^2 crop, a child process with OMP_NUM_THREADS=1);
+    the 3-D soft-Coulomb grid (128^3 crop, first order, per-cell potential) and the ensemble (the first 16
+    runs of the draw, absorbing layers on, 10 steps each, repeated) on all cores."""
+    import oracle
+    from paper_1107_4650_gb300 import workloads as W
+    oracle.build()
+    here = os.path.dirname(os.path.abspath(__file__))
+    out = {"cpu_model": _cpu_model(), "nproc": os.cpu_count()}
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = _ONE_THREAD % (here, run.V0, run.p0, run.width / 4, run.dx, run.L, seconds)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=120 + 10 * seconds)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        out["klein2d_one_thread"] = {"value": one["rate"], "unit": "point-steps/s", "threads": 1,
+                                     "sample": "512x512 crop of the Klein run (width 25 dx), %d steps" % one["steps"]}
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError, KeyError) as e:
+        out["klein2d_one_thread"] = {"error": str(e)[:200]}
+    n3, dx = 128, W.DX_DEFAULT
+    psi3 = W.gaussian_packet(n3, n3, dx, -n3 * dx / 2, -n3 * dx / 2, 32 * dx, 0.0, 16 * dx, 0.0, ny=n3,
+                             y_min=-n3 * dx / 2)
+    V3 = W.soft_coulomb_3d(n3, dx, 10.0, 2 * dx).reshape(-1)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        psi3, _ = oracle.step(psi3, 3, 1.0, W.C_AU, dx, 2, V=V3)
+        done += 2
+        if time.perf_counter() - t0 >= seconds:
+            break
+    out["coulomb3d_all_cores"] = {"value": n3 ** 3 * done / (time.perf_counter() - t0), "unit": "point-steps/s",
+                                  "threads": os.cpu_count(),
+                                  "sample": "128^3 crop of the 3-D soft-Coulomb grid (Z = 10), %d first-order steps"
+                                            % done}
+    runs, _ = W.klein_ensemble(16, seed=W.SEED + 1)
+    states = [(r, r.state(), r.potential(), r.geometry()[4], r.mask()) for r in runs]
+    pts, passes, t0 = 0, 0, time.perf_counter()
+    while True:
+        for r, psi, V, face, mask in states:
+            oracle.step(psi, 2, 1.0, W.C_AU, r.dx, 10, V=V, flux_face=face, absorber=mask)
+            pts += r.side * r.side * 10
+        passes += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    out["ensemble_all_cores"] = {"value": pts / (time.perf_counter() - t0), "unit": "point-steps/s",
+                                 "threads": os.cpu_count(),
+                                 "sample": "first 16 runs of the ensemble draw (sides %s), 10 steps each, %d passes"
+                                           % (sorted({r.side for r in runs}), passes)}
+    return out
 
 
 def reference_arm(args, rank, world):
@@ -564,6 +648,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, desc = cpu_baseline(run, args.cpu_seconds)
         cpu = {"value": rate, "unit": "point-steps/s", "cores": cores, "kind": "oracle", "sample": desc}
+        if args.cpu_detail_seconds > 0:
+            cpu["detail"] = cpu_detail(run, args.cpu_detail_seconds)
 
     if rank == 0:
         line = {"metric": "4-spinor grid-point-steps/s", "value": value, "unit": "point-steps/s", "n_gpus": world,

@@ -686,6 +686,56 @@ def test_strang3d_fused_passes_fp32_same_bits_as_single_sweeps(D, periodic):
     assert rel_l2(out[2].astype(np.complex128), want) < 5e-6
 
 
+@pytest.mark.parametrize("pp", [1, 2])
+def test_strang3d_interior_blocks_and_face_bit_exact(D, pp):
+    """A grid wide enough that the fused passes have interior blocks (no boundary masks) next to edge blocks,
+    with the face in an interior strip: state bit-exact and the face flux within rounding of the oracle."""
+    nx, ny, nz = 80, 76, 10
+    psi = W.random_state(nz, ny, nx, seed=91)
+    V = np.random.default_rng(92).uniform(-4e4, 4e4, nx * ny * nz)
+    want, F = oracle.step_strang3d(psi, 1.0, C, DX, 6, V=V, periodic=False, flux_face=40)
+    cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=pp, flux_face=40)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+        D.dirac_set_state(h, psi)
+        D.dirac_step(h, 6)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want), rel_l2(got, want)
+    assert abs(obs["flux_cum"] - F) <= 1e-12 * abs(F) + 1e-13
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_strang3d_fused_field_fp32_same_bits_as_single_sweeps(D, periodic):
+    """FP32 storage with a uniform vector potential: fused passes and single sweeps agree bit for bit."""
+    nx, ny, nz = 45, 30, 22
+    psi = W.random_state(nz, ny, nx, seed=93).astype(np.complex64)
+    V = np.random.default_rng(94).uniform(-4e4, 4e4, nx)
+    At = _field_table(10, ny, scale=0.9)
+    out = {}
+    for pp in (1, 2):
+        cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=pp, precision=D.DIRAC_FP32,
+                            boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+        h = D.dirac_create_grid(cfg)
+        try:
+            D.dirac_set_vector_potential(h, At)
+            D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+            D.dirac_set_state(h, psi)
+            D.dirac_step(h, 7)
+            got = np.empty_like(psi)
+            D.dirac_get_state(h, got)
+            out[pp] = got
+        finally:
+            D.dirac_destroy(h)
+    assert np.array_equal(out[1].view(np.uint32), out[2].view(np.uint32))
+    want, _ = oracle.step_strang3d(psi.astype(np.complex128), 1.0, C, DX, 7, V=V, periodic=periodic, A_tilde=At)
+    assert rel_l2(out[2].astype(np.complex128), want) < 5e-6
+
+
 def test_strang3d_default_plans_and_autotune(D):
     """Library choice: FP32 storage runs the fused passes, FP64 the single sweeps; dirac_autotune picks among
     both (and the fused pass's block and segment shapes) without changing the result."""
