@@ -74,8 +74,11 @@ typedef struct {
                              dt = 2 dx / c, so each half-step sweep is the one-cell shift; steps_per_launch
                              1 (FP64) or 1, 2 (FP32).  3-D: A B A C D C A B A with dt = 4 dx / c, x sweeps
                              moving one cell and y, z sweeps two (c dt/2 = 2 dx), run as eight single-sweep
-                             launches (points_per_lane 1) or as three fused passes x-y-x, z-phase-z, x-y-x
-                             (points_per_lane 2); 0 = library choice (fused passes for FP32 storage) */
+                             launches per step (points_per_lane 1) or as fused passes (points_per_lane 2): a
+                             run of m steps (one dirac_step call, or a captured graph of 32 steps) is x-y-x,
+                             m z-phase-z passes separated by m - 1 x-y-x-x-y-x passes, then x-y-x, so the
+                             state in memory is at a step boundary only between runs; 0 = library choice
+                             (fused passes for FP32 storage, single sweeps for FP64) */
     int char_shift;       /* characteristic shift K of Sec. 2.3: c dt = K dx, each sweep moves the
                              characteristics by K cells and dt = K dx / c.  0 or 1: the paper's K = 1;
                              2, 3 or 4: 2-D first-order (DIRAC_LIE) grids without a vector potential,
@@ -185,7 +188,7 @@ enum {
     DIRAC_PLAN_3D_FUSED = 5,     /* 3-D single pass */
     DIRAC_PLAN_3D_STRANG = 6,    /* 3-D second-order step: eight single-sweep launches */
     DIRAC_PLAN_STRANG_FIELD_2D = 7, /* 2-D second-order step with the vector-potential phase matrix */
-    DIRAC_PLAN_3D_STRANG_FUSED = 8  /* 3-D second-order step: x-y-x, z-phase-z, x-y-x passes */
+    DIRAC_PLAN_3D_STRANG_FUSED = 8  /* 3-D second-order steps: x-y-x, z-phase-z, x-y-x-x-y-x, ... passes */
 };
 
 dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info);
