@@ -874,6 +874,48 @@ def test_full_size_384_cubed_sampled_outputs_bit_exact(D):
         assert np.array_equal(got[cell].view(np.float64), want[loc].view(np.float64)), cell
 
 
+@pytest.fixture(scope="module")
+def coulomb384():
+    n3 = 384
+    psi0 = W.gaussian_packet(n3, n3, DX, -n3 * DX / 2, -n3 * DX / 2, 32 * DX, 0.0, 16 * DX, 0.0, ny=n3,
+                             y_min=-n3 * DX / 2)
+    return psi0, W.soft_coulomb_3d(n3, DX, 10.0, 2 * DX)
+
+
+@pytest.mark.parametrize("prec,pp", [("fp64", 0), ("fp64", 2), ("fp32", 0)])
+def test_full_size_384_cubed_strang_sampled_outputs(D, coulomb384, prec, pp):
+    """The 384^3 soft-Coulomb grid with second-order steps in the benchmark's plans (FP64: eight single sweeps;
+    FP32: the fused passes, a 3-step run) and the fused passes in FP64: 8 sampled cells recomputed by the oracle
+    on their light-cone crops (4 cells per step along each axis), FP64 bit for bit, FP32 within its rounding."""
+    psi0, V = coulomb384
+    n3, nsteps = 384, 3
+    fp32 = prec == "fp32"
+    cfg = D.make_config((n3, n3, n3), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=pp,
+                        precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64)
+    h = D.dirac_create_grid(cfg)
+    st = psi0.astype(np.complex64) if fp32 else psi0
+    try:
+        D.dirac_set_potential(h, V.reshape(-1), D.DIRAC_V_FULL)
+        D.dirac_set_state(h, st)
+        D.dirac_step(h, nsteps)
+        got = np.empty_like(st)
+        D.dirac_get_state(h, got)
+        plan = D.dirac_get_info(h)["plan"]
+    finally:
+        D.dirac_destroy(h)
+    assert plan == (D.DIRAC_PLAN_3D_STRANG_FUSED if (fp32 or pp == 2) else D.DIRAC_PLAN_3D_STRANG)
+    scale = np.abs(psi0).max()
+    for cell in [(192, 192, 192), (192, 192, 224), (0, 0, 0), (383, 200, 17), (100, 383, 383), (191, 5, 300),
+                 (250, 250, 150), (7, 380, 192)]:
+        sl = _light_cone_crop((n3, n3, n3), cell, 4 * nsteps + 1)
+        want, _ = oracle.step_strang3d(psi0[sl], 1.0, C, DX, nsteps, V=V[sl].reshape(-1))
+        loc = tuple(c - s.start for c, s in zip(cell, sl))
+        if fp32:
+            assert np.max(np.abs(got[cell].astype(np.complex128) - want[loc])) < 1e-5 * scale, cell
+        else:
+            assert np.array_equal(got[cell].view(np.float64), want[loc].view(np.float64)), cell
+
+
 # ------------------------------------------------------------------ degenerate grids
 
 _DEGENERATE_2D = [(1, 1), (1, 9), (9, 1), (33, 1), (1, 40), (2, 3)]
