@@ -64,8 +64,10 @@ typedef struct {
                              every step (between cells i_s-1 and i_s), or -1 for none */
     void *stream;         /* cudaStream_t the grid's work is enqueued on (NULL = legacy stream) */
     int device;           /* CUDA device ordinal */
-    int steps_per_launch; /* steps fused in one 2-D kernel launch (temporal block depth): 1 or 2 for FP64,
-                             1, 2 or 4 for FP32; 0 = library choice (3-D always runs 1) */
+    int steps_per_launch; /* steps fused in one kernel launch (temporal block depth).  2-D: 1 or 2 for FP64,
+                             1, 2 or 4 for FP32.  3-D first order: 1 or 2, 2 only in the fused pass
+                             (points_per_lane 0); 3-D second order: 1.  0 = library choice (3-D: 2 for FP32
+                             storage, 1 for FP64) */
     int use_graphs;       /* 1: replay dirac_step's steady-state launches from a captured CUDA graph */
     int points_per_lane;  /* x cells per lane of the step kernel: 1, 2 or 4 (K = 2 needs 2 in FP64);
                              0 = library choice */

@@ -30,6 +30,9 @@ struct Plan {
     // 3-D: fused single-pass step (fused3d_kernels.cuh) instead of the x-y pass + z/phase pass
     int fused3d = 0, f_warps = 16;
     int64_t f_nstrips = 0, f_nytiles = 0, f_nzsegs = 0, f_zseg_h = 0;
+    // two steps per fused pass (K = 2): 28-cell strips x (f2_warps - 4)-row tiles
+    int f2_warps = 16;
+    int64_t f2_nstrips = 0, f2_nytiles = 0, f2_nzsegs = 0, f2_zseg_h = 0;
     // 3-D second-order step: three fused passes (strang3d_kernels.cuh) instead of eight single sweeps
     int s3_fused = 0, s3_warps = 16, s3_zfactor = 2;
     struct XY {
@@ -237,6 +240,16 @@ void make_plan(dirac_grid *g, int K, int P, int wpb, int target_warps_per_sm) {
         fz = std::min<int64_t>(fz, std::max<int64_t>(1, nz / 16));
         p.f_zseg_h = (nz + fz - 1) / fz;
         p.f_nzsegs = (nz + p.f_zseg_h - 1) / p.f_zseg_h;
+        // two steps per fused pass: 28-cell strips x (warps - 4)-row tiles (16 warps in FP32, 8 in FP64), z
+        // segments as above (each carries two halo planes a side)
+        p.f2_warps = g->fp32 ? 16 : 8;
+        p.f2_nstrips = (g->cfg.n[0] + 27) / 28;
+        p.f2_nytiles = (g->cfg.n[1] + (p.f2_warps - 4) - 1) / (p.f2_warps - 4);
+        const int64_t tiles2 = p.f2_nstrips * p.f2_nytiles;
+        int64_t fz2 = std::max<int64_t>(1, (8 * (int64_t)g->sm_count + tiles2 - 1) / tiles2);
+        fz2 = std::min<int64_t>(fz2, std::max<int64_t>(1, nz / 16));
+        p.f2_zseg_h = (nz + fz2 - 1) / fz2;
+        p.f2_nzsegs = (nz + p.f2_zseg_h - 1) / p.f2_zseg_h;
         // second-order passes: x-y-x(-x-y-x) blocks over (32 - 4 nh)-cell strips x (warps - 4 nh)-row tiles x
         // z segments (planes are independent: ~8 blocks per SM of work); z-phase-z columns x 2 plane parities
         // x z segments (~s3_zfactor x 1024 threads per SM, segments of at least 16 planes: four halo planes
@@ -273,7 +286,11 @@ int axis_blocks(const dirac_grid *g) {
 dirac_status ensure_flux_part(dirac_grid *g) {
     const int64_t planes = (ndim_of(g) == 3) ? g->cfg.n[2] : 1;
     size_t need = (size_t)8 * planes * std::max<int64_t>(g->plan.nsegs, 1);
-    if (fused_pass(g)) need = std::max(need, (size_t)(g->plan.f_nzsegs * g->plan.f_nytiles * g->plan.f_warps));
+    if (fused_pass(g)) {
+        need = std::max(need, (size_t)(g->plan.f_nzsegs * g->plan.f_nytiles * g->plan.f_warps));
+        if (g->plan.K == 2)
+            need = std::max(need, (size_t)(2 * g->plan.f2_nzsegs * g->plan.f2_nytiles * g->plan.f2_warps));
+    }
     if (sweep_mode(g) == 6) need = std::max(need, (size_t)axis_blocks(g));
     if (strang3d_fused(g))
         for (int nh = 1; nh <= 2; ++nh) {
@@ -344,10 +361,17 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
         return DIRAC_OK;
     }
     if (mode == 1 && fused_pass(g)) {
-        a.nsegs = p.f_nzsegs * p.f_nytiles * p.f_warps;  // flux parts of the fused pass
+        cudaError_t e;
         a.nplanes = 1;
-        cudaError_t e = launch_fused3d(a, g->fp32, p.f_warps, g->cfg.n[1], g->cfg.n[2], p.f_nstrips, p.f_nytiles,
-                                       p.f_nzsegs, p.f_zseg_h, s);
+        if (K == 2) {
+            a.nsegs = p.f2_nzsegs * p.f2_nytiles * p.f2_warps;  // flux parts per step of the fused pass
+            e = launch_fused3d(a, g->fp32, p.f2_warps, 2, g->cfg.n[1], g->cfg.n[2], p.f2_nstrips, p.f2_nytiles,
+                               p.f2_nzsegs, p.f2_zseg_h, s);
+        } else {
+            a.nsegs = p.f_nzsegs * p.f_nytiles * p.f_warps;  // flux parts of the fused pass
+            e = launch_fused3d(a, g->fp32, p.f_warps, 1, g->cfg.n[1], g->cfg.n[2], p.f_nstrips, p.f_nytiles,
+                               p.f_nzsegs, p.f_zseg_h, s);
+        }
         if (e != cudaSuccess) return cuda_fail(g, e, "fused 3-D step launch");
         g->launches++;
         return DIRAC_OK;
@@ -470,7 +494,7 @@ int64_t launches_per_block(const dirac_grid *g) {
 }
 
 dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
-    const int K = (ndim_of(g) == 3) ? 1 : g->plan.K;
+    const int K = (ndim_of(g) == 3) ? (fused_pass(g) ? g->plan.K : 1) : g->plan.K;
     int64_t blocks = nsteps / K;
     int64_t rem = nsteps % K;
     const bool field = field_on(g);
@@ -559,7 +583,11 @@ void default_plan(dirac_grid *g) {
         // FP64, which is bound by the FP64 pipe and would recompute the x-y-x pass's halo cells)
         g->plan.s3_fused = pp == 1 ? 0 : (pp == 2 ? 1 : (g->fp32 ? 1 : 0));
         g->plan.s3_warps = 32;  // measured at 384^3: 24 owned rows of 32 beat 8 of 16 (more recomputed halo rows)
-        make_plan(g, 1, pp > 0 ? pp : 2, 4, 16);
+        // first-order fused pass: steps_per_launch 1 or 2 (temporal block); library choice two in FP32
+        // storage (bandwidth-bound), one in FP64 (bound by the FP64 pipe: the second step's halo would cost)
+        int K3 = 1;
+        if (!strang(g) && (pp == 0 || field_on(g))) K3 = k == 2 ? 2 : (k == 1 ? 1 : (g->fp32 ? 2 : 1));
+        make_plan(g, K3, pp > 0 ? pp : 2, 4, 16);
         return;
     }
     if (sweep_mode(g) == 4) {
@@ -700,6 +728,10 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
         return fail(nullptr, DIRAC_ERR_ARG, "splitting must be DIRAC_LIE or DIRAC_STRANG");
     if (cfg->splitting == DIRAC_STRANG && cfg->ndim == 3 && cfg->steps_per_launch > 1)
         return fail(nullptr, DIRAC_ERR_ARG, "3-D DIRAC_STRANG runs one step per launch block (steps_per_launch 0 or 1)");
+    if (cfg->ndim == 3 && cfg->steps_per_launch > 2)
+        return fail(nullptr, DIRAC_ERR_ARG, "3-D grids run 1 or 2 steps per launch");
+    if (cfg->ndim == 3 && cfg->steps_per_launch == 2 && cfg->points_per_lane > 0)
+        return fail(nullptr, DIRAC_ERR_ARG, "3-D steps_per_launch 2 runs the fused pass (points_per_lane 0)");
     if (cfg->char_shift < 0 || cfg->char_shift > 4)
         return fail(nullptr, DIRAC_ERR_ARG, "char_shift must be 0 (= 1), 1, 2, 3 or 4");
     if (cfg->char_shift > 1) {
@@ -979,7 +1011,7 @@ dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, i
 dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
     if (!g || !info) return fail(nullptr, DIRAC_ERR_ARG, "null argument");
     const Plan &p = g->plan;
-    info->steps_per_launch = (g->cfg.ndim == 3) ? 1 : p.K;
+    info->steps_per_launch = (g->cfg.ndim == 3) ? (fused_pass(g) ? p.K : 1) : p.K;
     info->points_per_lane = p.P;
     const int64_t planes = (g->cfg.ndim == 3) ? g->cfg.n[2] : 1;
     info->launch_warps = p.nstrips * p.nsegs * planes;
@@ -1003,6 +1035,11 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
         info->launch_warps = p.f_nstrips * p.f_nytiles * p.f_nzsegs * p.f_warps;
         info->strip_width = 30;
         info->segment_rows = p.f_zseg_h;
+        if (p.K == 2) {
+            info->launch_warps = p.f2_nstrips * p.f2_nytiles * p.f2_nzsegs * p.f2_warps;
+            info->strip_width = 28;
+            info->segment_rows = p.f2_zseg_h;
+        }
     }
     info->graphs = g->cfg.use_graphs;
     info->kernel_launches = g->launches;
@@ -1029,6 +1066,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
             for (int P : {1, 2, 4})
                 for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});
         for (int fw : {8, 16}) cands.push_back({1, 2, 4, 16, fw});
+        cands.push_back({2, 2, 4, 16, 16});  // two steps per fused pass
     } else if (sweep_mode(g) == 4) {
         for (int P : {1, 2})
             for (int wsm : {4, 8, 12, 16}) cands.push_back({1, P, 4, wsm});

@@ -92,10 +92,11 @@ cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx
                         double vol, double *flux_part, double *flux_cum, unsigned *ticket, const double *ucoef,
                         int64_t ucoef_n, int64_t step0, int fp32, int blocks, cudaStream_t s);
 
-// Fused 3-D step (x, y, z sweeps and phase in one pass, one step per launch): blocks of `warps` (8 or 16)
-// warps own a 30-cell x strip and warps - 2 rows along y and stream a z segment of zseg_h planes.  Flux
-// parts: nzsegs * nytiles * warps (a.nsegs * a.nplanes must equal that).
-cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
+// Fused 3-D step (x, y, z sweeps and phase in one pass, `steps` = 1 or 2 steps per launch): blocks of
+// `warps` warps own a (32 - 2 steps)-cell x strip and warps - 2 steps rows along y and stream a z segment of
+// zseg_h planes (steps 1: 8 or 16 warps; steps 2: 16 warps in FP32, 8 in FP64).  Flux parts:
+// [steps][nzsegs * nytiles * warps] (a.nsegs * a.nplanes must equal nzsegs * nytiles * warps).
+cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int steps, int64_t ny, int64_t nz, int64_t nstrips,
                            int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s);
 
 // 3-D second-order step as fused passes (strang3d_kernels.cuh).  x-y-x pass (nh = 1: half a step) or

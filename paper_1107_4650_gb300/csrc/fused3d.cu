@@ -1,10 +1,11 @@
-// Instantiations of the fused 3-D step kernel (8 or 16 warps per block: 6 or 14 owned rows per tile; with
-// and without a uniform vector potential).
+// Instantiations of the fused 3-D step kernels: one step per pass (8 or 16 warps per block: 6 or 14 owned
+// rows per tile) and two steps per pass (FP32: 16 warps, 12 owned rows; FP64: 8 warps, 4 owned rows), with
+// and without a uniform vector potential.
 #include "fused3d_kernels.cuh"
 
 namespace dirac {
 
-cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int64_t ny, int64_t nz, int64_t nstrips,
+cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int steps, int64_t ny, int64_t nz, int64_t nstrips,
                            int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s) {
     Fused3DArgs A{};
     A.s = a;
@@ -15,6 +16,15 @@ cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int64_t ny, 
     A.nzsegs = nzsegs;
     A.zseg_h = zseg_h;
     const bool field = a.ucoef != nullptr && a.ucoef_n > 0;
+    if (steps == 2) {
+        // two steps per pass: FP32 with 16-warp blocks, FP64 with 8 (its register budget)
+        if (fp32 && warps == 16)
+            return field ? launch_fused3d2_one<float, 16, true>(A, s) : launch_fused3d2_one<float, 16, false>(A, s);
+        if (!fp32 && warps == 8)
+            return field ? launch_fused3d2_one<double, 8, true>(A, s) : launch_fused3d2_one<double, 8, false>(A, s);
+        return cudaErrorInvalidValue;
+    }
+    if (steps != 1) return cudaErrorInvalidValue;
     if (field) {
         if (warps == 16) return fp32 ? launch_fused3d_one<float, 16, true>(A, s) : launch_fused3d_one<double, 16, true>(A, s);
         if (warps == 8) return fp32 ? launch_fused3d_one<float, 8, true>(A, s) : launch_fused3d_one<double, 8, true>(A, s);

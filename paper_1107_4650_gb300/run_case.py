@@ -105,7 +105,8 @@ def main():
         V = W.soft_coulomb_3d(n, dx, 10.0, 2 * dx).reshape(-1)
         shape = (n, n, n)
         cfg = D.make_config(shape, ndim=3, precision=prec, stream=stream.cuda_stream, points_per_lane=args.p,
-                            use_graphs=not args.no_graphs, splitting=D.DIRAC_STRANG if args.strang else D.DIRAC_LIE)
+                            steps_per_launch=args.k, use_graphs=not args.no_graphs,
+                            splitting=D.DIRAC_STRANG if args.strang else D.DIRAC_LIE)
         layout = D.DIRAC_V_FULL
     h = D.dirac_create_grid(cfg)
     if args.field:

@@ -117,6 +117,17 @@ def test_strang_3d_runs_one_step_per_block(lib):
     assert e.value.status == D.DIRAC_ERR_ARG
 
 
+def test_3d_steps_per_launch_validation(lib):
+    """3-D grids run one or two steps per launch, two only in the fused pass (points_per_lane 0)."""
+    import paper_1107_4650_gb300 as D
+    for kw in (dict(steps_per_launch=4), dict(steps_per_launch=2, points_per_lane=2),
+               dict(steps_per_launch=2, points_per_lane=1)):
+        cfg = D.make_config((16, 16, 16), ndim=3, **kw)
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_create_grid(cfg)
+        assert e.value.status == D.DIRAC_ERR_ARG
+
+
 def test_char_shift_validation(lib):
     import paper_1107_4650_gb300 as D
     for kw in (dict(char_shift=5), dict(char_shift=-1), dict(char_shift=2, ndim=3, n=(8, 8, 8)),

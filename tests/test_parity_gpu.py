@@ -143,6 +143,53 @@ def test_3d_fp64_bit_exact_coulomb(D, shape, periodic, P):
     assert _bits_equal(got, want), rel_l2(got, want)
 
 
+@pytest.mark.parametrize("shape", [(40, 36, 33), (7, 5, 6), (70, 9, 12), (95, 31, 40), (3, 2, 1), (1, 1, 9)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("nsteps", [1, 2, 5, 70])
+def test_3d_two_steps_per_pass_fp64_bit_exact(D, shape, periodic, nsteps):
+    """The fused pass with two steps per launch (temporal block k = 2; an odd step count ends with a one-step
+    launch, 70 steps replay a graph): bit-exact against the oracle, per-cell table."""
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx + ny + nz + nsteps)
+    V = np.random.default_rng(nx * ny).uniform(-4e4, 4e4, nx * ny * nz)
+    want, _ = oracle.step(psi, 3, 1.0, C, DX, nsteps, V=V, periodic=periodic)
+    got, _, info = run_gpu(D, psi, 3, nsteps, V=V, periodic=periodic, K=2)
+    assert info["plan"] == D.DIRAC_PLAN_3D_FUSED and info["steps_per_launch"] == 2
+    assert info["strip_width"] == 28
+    assert _bits_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_3d_two_steps_per_pass_flux(D, fp32, graphs):
+    """Face flux of both steps of every launch (x-only table, zero boundary, 37 steps: graph replay and a
+    closing one-step launch); FP32 storage within its rounding of the oracle."""
+    nx, ny, nz = 90, 40, 48
+    psi = W.random_state(nz, ny, nx, seed=46)
+    V = np.random.default_rng(7).uniform(0, 5e4, nx)
+    want, F = oracle.step(psi, 3, 1.0, C, DX, 37, V=V, flux_face=45)
+    got, obs, info = run_gpu(D, psi, 3, 37, V=V, flux_face=45, K=2, graphs=graphs, fp32=fp32)
+    assert info["steps_per_launch"] == 2
+    if fp32:
+        assert rel_l2(got.astype(np.complex128), want) < 2e-5
+        assert abs(obs["flux_cum"] - F) < 1e-5 * abs(F) + 1e-9
+    else:
+        assert _bits_equal(got, want)
+        assert abs(obs["flux_cum"] - F) <= 1e-12 * max(abs(F), 1e-300) + 1e-300
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_3d_two_steps_per_pass_fp32_same_bits_as_one(D, periodic):
+    """FP32 storage: two steps per pass do the one-step pass's arithmetic, so the states agree bit for bit."""
+    nx, ny, nz = 77, 45, 39
+    psi = W.random_state(nz, ny, nx, seed=47)
+    V = np.random.default_rng(8).uniform(-4e4, 4e4, nx * ny * nz)
+    a, _, _ = run_gpu(D, psi, 3, 9, V=V, periodic=periodic, K=1, fp32=True)
+    b, _, info = run_gpu(D, psi, 3, 9, V=V, periodic=periodic, K=2, fp32=True)
+    assert info["steps_per_launch"] == 2
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
 @pytest.mark.parametrize("P", [0, 2])
 @pytest.mark.parametrize("graphs", [True, False])
 def test_3d_flux_and_x_only_table(D, P, graphs):
@@ -1058,15 +1105,17 @@ def test_paper_klein_solver_value_in_1d_reduction(D):
 @pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (40, 13, 9)])
 @pytest.mark.parametrize("periodic", [False, True])
 @pytest.mark.parametrize("full", [False, True])
-def test_vector_potential_3d_bit_exact(D, shape, periodic, full):
-    """3-D first-order steps in a uniform vector potential (the fused pass with the phase matrix) against the
-    oracle, bit for bit, with a step counter starting inside the table."""
+@pytest.mark.parametrize("K", [1, 2])
+def test_vector_potential_3d_bit_exact(D, shape, periodic, full, K):
+    """3-D first-order steps in a uniform vector potential (the fused pass with the phase matrix, one or two
+    steps per launch) against the oracle, bit for bit, with a step counter starting inside the table."""
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx + ny + nz)
     V = np.random.default_rng(ny).uniform(-4e4, 4e4, nx * ny * nz if full else nx)
     At = _field_table(12, nz, scale=1.5)
     want, _ = oracle.step(psi, 3, 1.0, C, DX, 5, V=V, periodic=periodic, A_tilde=At, step0=3)
-    cfg = D.make_config((nx, ny, nz), ndim=3, boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    cfg = D.make_config((nx, ny, nz), ndim=3, boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO,
+                        steps_per_launch=K)
     h = D.dirac_create_grid(cfg)
     try:
         D.dirac_set_vector_potential(h, At)
@@ -1079,7 +1128,7 @@ def test_vector_potential_3d_bit_exact(D, shape, periodic, full):
         info = D.dirac_get_info(h)
     finally:
         D.dirac_destroy(h)
-    assert info["plan"] == D.DIRAC_PLAN_3D_FUSED
+    assert info["plan"] == D.DIRAC_PLAN_3D_FUSED and info["steps_per_launch"] == K
     assert _bits_equal(got, want), rel_l2(got, want)
 
 
