@@ -413,14 +413,9 @@ static cudaError_t launch_fused3d2_one(const Fused3DArgs &A, cudaStream_t s) {
     const int64_t blocks = A.nstrips * A.nytiles * A.nzsegs;
     if (blocks <= 0) return cudaSuccess;
     const int smem = 2 * W * 4 * 32 * (int)sizeof(Cx<T>);
-    static unsigned long long done = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 64 || !(done & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(fused3d2_kernel<T, W, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) done |= 1ull << dev;
-    }
+    static std::atomic<unsigned long long> done{0};
+    cudaError_t e = optin_smem(fused3d2_kernel<T, W, FIELD>, smem, done);
+    if (e != cudaSuccess) return e;
     fused3d2_kernel<T, W, FIELD><<<(unsigned)blocks, 32 * W, smem, s>>>(A);
     return cudaGetLastError();
 }
@@ -430,14 +425,9 @@ static cudaError_t launch_fused3d_one(const Fused3DArgs &A, cudaStream_t s) {
     const int64_t blocks = A.nstrips * A.nytiles * A.nzsegs;
     if (blocks <= 0) return cudaSuccess;
     const int smem = 2 * W * 4 * 32 * (int)sizeof(Cx<T>);
-    static unsigned long long done = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 64 || !(done & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(fused3d_kernel<T, W, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) done |= 1ull << dev;
-    }
+    static std::atomic<unsigned long long> done{0};
+    cudaError_t e = optin_smem(fused3d_kernel<T, W, FIELD>, smem, done);
+    if (e != cudaSuccess) return e;
     fused3d_kernel<T, W, FIELD><<<(unsigned)blocks, 32 * W, smem, s>>>(A);
     return cudaGetLastError();
 }

@@ -8,6 +8,7 @@
 //   backward:       dz5 = 2 (y - t) y (1 - y) / B; dW5 = sum_b dz5 bf16(h4); dh4 = dz5 bf16(w5);
 //                   dz = dh (1 - h^2);  dW = bf16(dz)^T . bf16(h_prev) and dh_prev = bf16(dz) . bf16(W)
 //                   (tensor cores); db = sum_b dz (FP32); dW1 = dz1^T . x (FP32)
+#include <atomic>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -356,13 +357,15 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 cudaError_t gemm_bf16(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B, int64_t sbk, int64_t sbn,
                       float *C, int64_t ldc, int M, int N, int K, int accumulate, unsigned *err, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    static unsigned long long attr_set = 0;  // per device: > 48 KB of dynamic shared memory opted in
+    // per device: > 48 KB of dynamic shared memory opted in once
+    static std::atomic<unsigned long long> attr_set{0};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 64 || !(attr_set & (1ull << dev))) {
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (!bit || !(attr_set.load(std::memory_order_relaxed) & bit)) {
         cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
         if (e != cudaSuccess) return e;
-        if (dev < 64) attr_set |= 1ull << dev;
+        if (bit) attr_set.fetch_or(bit, std::memory_order_relaxed);
     }
     dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
     gemm_bf16_kernel<<<grid, 128, GEMM_SMEM, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, accumulate, err);

@@ -22,9 +22,24 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "dirac_internal.cuh"
 
 namespace dirac {
+
+// Opts `kernel` in to `smem` bytes of dynamic shared memory, once per device (bit `dev` of `done`; devices
+// past 63 set the attribute on every launch).  Concurrent first launches may both set it: harmless.
+template <typename K>
+static cudaError_t optin_smem(K *kernel, int smem, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_relaxed);
+    return e;
+}
 
 template <typename T> struct Ar;
 template <> struct Ar<double> {

@@ -393,14 +393,9 @@ static cudaError_t launch_strang_xy_one(const StrangXYArgs &A, cudaStream_t s) {
     const int64_t blocks = A.nstrips * A.nytiles * A.nzsegs;
     if (blocks <= 0) return cudaSuccess;
     const int smem = 2 * W * 4 * 32 * (int)sizeof(Cx<T>);
-    static unsigned long long done = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 64 || !(done & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(strang_xy_kernel<T, W, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) done |= 1ull << dev;
-    }
+    static std::atomic<unsigned long long> done{0};
+    cudaError_t e = optin_smem(strang_xy_kernel<T, W, NH>, smem, done);
+    if (e != cudaSuccess) return e;
     strang_xy_kernel<T, W, NH><<<(unsigned)blocks, 32 * W, smem, s>>>(A);
     return cudaGetLastError();
 }

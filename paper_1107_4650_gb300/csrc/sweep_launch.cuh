@@ -11,15 +11,11 @@ static cudaError_t launch_one(const SweepArgs &a, int wpb, cudaStream_t s) {
     if (blocks <= 0) return cudaSuccess;
     const int smem = ring_smem_bytes<T, Levels<K, MODE>::value, P>(wpb);
     // opt in to > 48 KB of dynamic shared memory, once per device and block size
-    static unsigned long long done[4] = {0, 0, 0, 0};
-    int dev = 0;
-    cudaGetDevice(&dev);
+    static std::atomic<unsigned long long> done[4];
     const int slot = (wpb == 4) ? 0 : (wpb == 2) ? 1 : (wpb == 8) ? 2 : 3;
-    if (dev >= 64 || slot == 3 || !(done[slot] & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, K, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        if (dev < 64 && slot != 3) done[slot] |= 1ull << dev;
-    }
+    if (slot == 3) done[3].store(0, std::memory_order_relaxed);  // other block sizes: every launch
+    cudaError_t e = optin_smem(sweep_kernel<T, K, P, MODE>, smem, done[slot]);
+    if (e != cudaSuccess) return e;
     sweep_kernel<T, K, P, MODE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
     return cudaGetLastError();
 }
