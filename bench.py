@@ -531,7 +531,8 @@ def main():
                          "physical_time_per_step_dx_over_c": per_step,
                          "first_order_equivalent_point_steps_per_s": v3 * per_step,
                          "workload": "%d^3 soft-Coulomb grid (Z = 10, per-cell table), %s splitting" % (n3, sname),
-                         "plan": {D.DIRAC_PLAN_3D_FUSED: "fused single pass",
+                         "steps_per_launch": i3["steps_per_launch"],
+                         "plan": {D.DIRAC_PLAN_3D_FUSED: "fused pass, %d step(s) per launch" % i3["steps_per_launch"],
                                   D.DIRAC_PLAN_3D_TWO_PASS: "x-y pass + z/phase pass, P=%d" % i3["points_per_lane"],
                                   D.DIRAC_PLAN_3D_STRANG: "eight single-sweep launches",
                                   D.DIRAC_PLAN_3D_STRANG_FUSED: "fused passes: x-y-x, then per step z-phase-z and "
