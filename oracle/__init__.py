@@ -56,8 +56,10 @@ def _load():
         lib.oracle_step_strang2d.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
         lib.oracle_step_strang3d.argtypes = lib.oracle_step_strang2d.argtypes
+        lib.oracle_step_fx.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
+                                       ctypes.c_int, ctypes.c_int64]
         for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables,
-                  lib.oracle_step_strang2d, lib.oracle_step_strang3d):
+                  lib.oracle_step_strang2d, lib.oracle_step_strang3d, lib.oracle_step_fx):
             f.restype = ctypes.c_int
         lib.oracle_set_absorber.argtypes = [P]
         lib.oracle_set_absorber.restype = None
@@ -227,6 +229,45 @@ def step_strang3d(psi, m: float, c: float, dx: float, nsteps: int, V=None, perio
     if rc != 0:
         raise MemoryError("oracle_step_strang3d")
     return out, fc.value
+
+
+def fx_encode(psi, S: int) -> np.ndarray:
+    """Fixed-point state q = round(psi 2^S) (nearest, ties to even), int64 of shape (nz, ny, nx, 4, 2)."""
+    arr = _as_state(psi)
+    x = np.ldexp(arr.view(np.float64).reshape(arr.shape + (2,)), S)
+    return np.rint(x).astype(np.int64)
+
+
+def fx_decode(q, S: int) -> np.ndarray:
+    """psi = q 2^-S as complex128 of shape (nz, ny, nx, 4)."""
+    q = np.ascontiguousarray(q, dtype=np.int64)
+    x = np.ldexp(q.astype(np.float64), -S)
+    return x.view(np.complex128).reshape(q.shape[:-1])
+
+
+def fx_shift(psi) -> int:
+    """The fixed-point shift for a state: S = 58 - e where the discrete L2 norm sqrt(sum |psi_c|^2) = m 2^e with
+    m in [0.5, 1), so that norm 2^S < 2^58 (0 for the zero state)."""
+    arr = _as_state(psi)
+    A = float(np.sqrt(np.sum(arr.real ** 2 + arr.imag ** 2)))
+    return 58 - (np.frexp(A)[1] if A > 0 else 58)
+
+
+def step_fx(q, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False, absorber=None):
+    """nsteps first-order 2-D steps on a fixed-point state q (int64, (nz, 1, nx, 4, 2)): exact integer sweeps
+    without the 1/2 factors, the phase coefficients (carrying 1/4) held as round(p/4 2^62) and each output
+    component rounded once after the exact 128-bit product (oracle_step_fx).  Returns the new q."""
+    out = np.ascontiguousarray(q, dtype=np.int64).copy()
+    if out.ndim != 5 or out.shape[1] != 1 or out.shape[3:] != (4, 2):
+        raise ValueError("q must have shape (nz, 1, nx, 4, 2)")
+    nz, ny, nx = out.shape[:3]
+    Varr, layout = _potential(V, np.zeros((nz, ny, nx, 4), complex))
+    with _Absorber(absorber, nx):
+        rc = _load().oracle_step_fx(out.ctypes.data, I64_3(nx, ny, nz), int(bool(periodic)), float(m), float(c),
+                                    float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps))
+    if rc != 0:
+        raise MemoryError("oracle_step_fx")
+    return out
 
 
 def observables(psi, ndim: int, dx: float, x_min=(0.0, 0.0, 0.0), flux_face: int = -1) -> dict:

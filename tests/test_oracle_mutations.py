@@ -11,6 +11,7 @@ import pytest
 import oracle
 from paper_1107_4650_gb300 import workloads as W
 from tests import dirac_algebra as A
+from tests.test_oracle_pins import _fx_step_bigint
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "dirac_oracle.c")
 C = W.C_AU
@@ -40,6 +41,14 @@ MUTANTS = {
     "strang3d_order": ("const int axes[9] = {0, 1, 0, 2, -1, 2, 0, 1, 0};", "const int axes[9] = {1, 0, 0, 2, -1, 2, 0, 1, 0};"),
     "strang3d_half_step_shift": ("ax == 0 ? g_shift : 2 * g_shift", "ax == 0 ? g_shift : g_shift"),
     "A_row_order": ("acc = c_mac(acc, q[b], c_mul(U[a][b], g));", "acc = c_mac(acc, q[b], c_mul(U[b][a], g));"),
+    "fx_rounding_offset": ("return (int64_t)((v + ((__int128)1 << 61)) >> 62);",
+                           "return (int64_t)((v + ((__int128)1 << 60)) >> 62);"),
+    "fx_z_sweep_sign": ("z[3].re = (L[3].re - L[1].re) + (R[1].re + R[3].re);",
+                        "z[3].re = (L[1].re - L[3].re) + (R[1].re + R[3].re);"),
+    "fx_coefficient_scale": ("return (int64_t)nearbyint(ldexp(p * 0.25, 62));",
+                             "return (int64_t)nearbyint(ldexp(p * 0.5, 62));"),
+    "fx_x_sweep_neighbour": ("const qcplx *L = qcell(q, n, periodic, i - 1, k), *R = qcell(q, n, periodic, i + 1, k);",
+                             "const qcplx *L = qcell(q, n, periodic, i - 1, k), *R = qcell(q, n, periodic, i - 1, k);"),
 }
 
 
@@ -64,6 +73,9 @@ def _build_mutant(tmp_path, name, old, new):
                                          ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
     lib.oracle_set_shift.argtypes = [ctypes.c_int64]
     lib.oracle_set_shift.restype = None
+    lib.oracle_step_fx.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   P, ctypes.c_int, ctypes.c_int64]
+    lib.oracle_step_fx.restype = ctypes.c_int
     return lib
 
 
@@ -126,6 +138,18 @@ def _pins_pass():
                   A.sweep_matrix(shape, 2, True, shift=2))
     want = Ax @ By @ Ax @ Cz @ A.phase_matrix(shape, 1.0, C, 4 * DX / C, Vc) @ Cz @ Ax @ By @ Ax @ psi.reshape(-1)
     ok &= np.max(np.abs(got.reshape(-1) - want)) < 5e-15
+    # fixed-point step: exact big-integer brute force, and exactness where FP64 is exact
+    rng = np.random.default_rng(70)
+    q = rng.integers(-(1 << 56), 1 << 56, size=(4, 1, 5, 4, 2), dtype=np.int64)
+    Vq = rng.uniform(-3e4, 3e4, 5)
+    dt = DX / C
+    coef = lambda p: int(np.rint(np.ldexp(p * 0.25, 62)))
+    P_up = [(coef(np.cos(C * C * dt + v * dt)), coef(-np.sin(C * C * dt + v * dt))) for v in Vq]
+    P_dn = [(coef(np.cos(v * dt - C * C * dt)), coef(-np.sin(v * dt - C * C * dt))) for v in Vq]
+    ok &= np.array_equal(oracle.step_fx(q, 1.0, C, DX, 1, V=Vq), _fx_step_bigint(q, P_up, P_dn, False))
+    q = rng.integers(-1000, 1000, size=(7, 1, 9, 4, 2), dtype=np.int64) * 64
+    want, _ = oracle.step(oracle.fx_decode(q, 40), 2, 0.0, C, DX, 3, periodic=True)
+    ok &= np.array_equal(oracle.step_fx(q, 0.0, C, DX, 3, periodic=True), oracle.fx_encode(want, 40))
     return bool(ok)
 
 

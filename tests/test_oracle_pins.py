@@ -711,3 +711,104 @@ def test_strang3d_with_vector_potential_equals_matrix_product(oracle_mod):
         Dm[4 * cell:4 * cell + 4, 4 * cell:4 * cell + 4] = A.phase_matrix_A_cell(M, C, dt, V[cell], At[1])
     want = Ax @ By @ Ax @ Cz @ Dm @ Cz @ Ax @ By @ Ax @ psi.reshape(-1)
     assert np.max(np.abs(got.reshape(-1) - want)) < 1e-14
+
+
+# ---------------------------------------------------------------- 64-bit fixed-point evaluation (oracle_step_fx)
+
+def _fx_step_bigint(q, P_up, P_dn, periodic):
+    """One fixed-point 2-D step with exact Python integers (brute force): sweeps of Eqs. sol_dis_1 and
+    sol_dis_3 without the 1/2, then each component's exact product with the per-column coefficients
+    (P = round(p/4 2^62)), scaled by 2^-62 and rounded to nearest, halves upward (floor(x + 1/2))."""
+    nz, _, nx = q.shape[:3]
+    Z = [[[complex(0)] * 4 for _ in range(nx)] for _ in range(nz)]
+    val = lambda a, k, i, cc: (0, 0) if (not periodic and not (0 <= k < nz and 0 <= i < nx)) else \
+        (int(a[k % nz][i % nx][cc][0]), int(a[k % nz][i % nx][cc][1]))
+    src = [[[(int(q[k, 0, i, cc, 0]), int(q[k, 0, i, cc, 1])) for cc in range(4)] for i in range(nx)] for k in range(nz)]
+    add = lambda a, b: (a[0] + b[0], a[1] + b[1])
+    sub = lambda a, b: (a[0] - b[0], a[1] - b[1])
+    t = [[None] * nx for _ in range(nz)]
+    for k in range(nz):
+        for i in range(nx):
+            L = [val(src, k, i - 1, cc) for cc in range(4)]
+            R = [val(src, k, i + 1, cc) for cc in range(4)]
+            t[k][i] = [add(add(L[0], L[3]), sub(R[0], R[3])), add(add(L[1], L[2]), sub(R[1], R[2])),
+                       add(add(L[1], L[2]), sub(R[2], R[1])), add(add(L[0], L[3]), sub(R[3], R[0]))]
+    out = np.zeros_like(q)
+    for k in range(nz):
+        for i in range(nx):
+            L = [val(t, k - 1, i, cc) for cc in range(4)]
+            R = [val(t, k + 1, i, cc) for cc in range(4)]
+            z = [add(add(L[0], L[2]), sub(R[0], R[2])), add(sub(L[1], L[3]), add(R[1], R[3])),
+                 add(add(L[0], L[2]), sub(R[2], R[0])), add(sub(L[3], L[1]), add(R[1], R[3]))]
+            for cc in range(4):
+                pr, pi = (P_up[i] if cc < 2 else P_dn[i])
+                re = z[cc][0] * pr - z[cc][1] * pi
+                im = z[cc][0] * pi + z[cc][1] * pr
+                out[k, 0, i, cc, 0] = (re + (1 << 61)) >> 62
+                out[k, 0, i, cc, 1] = (im + (1 << 61)) >> 62
+    return out
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_fx_step_equals_exact_integer_brute_force(oracle_mod, periodic):
+    """oracle_step_fx on a 5 x 4 grid against the same step in exact Python integers (the coefficients from
+    the FP64 cos/sin of oracle_phase, rounded to nearest even at 2^62 / 4)."""
+    rng = np.random.default_rng(70)
+    nx, nz = 5, 4
+    q = rng.integers(-(1 << 56), 1 << 56, size=(nz, 1, nx, 4, 2), dtype=np.int64)
+    V = rng.uniform(-3e4, 3e4, nx)
+    got = oracle.step_fx(q, 1.0, C, W.DX_DEFAULT, 1, V=V, periodic=periodic)
+    dt = W.DX_DEFAULT / C
+    mu = C * C * dt
+    coef = lambda p: int(np.rint(np.ldexp(p * 0.25, 62)))
+    P_up = [(coef(np.cos(mu + v * dt)), coef(-np.sin(mu + v * dt))) for v in V]
+    P_dn = [(coef(np.cos(v * dt - mu)), coef(-np.sin(v * dt - mu))) for v in V]
+    want = _fx_step_bigint(q, P_up, P_dn, periodic)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_fx_step_exact_where_fp64_is_exact(oracle_mod, periodic):
+    """m = 0, V = 0: the phase is the identity, so three steps of a state whose fixed-point values are multiples
+    of 4^3 are exact in both evaluations: the fixed-point result equals the FP64 oracle's times 2^S exactly
+    (a wrong sign, index or neighbour in either sweep fails)."""
+    rng = np.random.default_rng(71)
+    nx, nz, S = 9, 7, 40
+    q = rng.integers(-1000, 1000, size=(nz, 1, nx, 4, 2), dtype=np.int64) * 64
+    psi = oracle.fx_decode(q, S)
+    want, _ = oracle.step(psi, 2, 0.0, C, W.DX_DEFAULT, 3, periodic=periodic)
+    got = oracle.step_fx(q, 0.0, C, W.DX_DEFAULT, 3, periodic=periodic)
+    assert np.array_equal(got, oracle.fx_encode(want, S))
+    assert np.array_equal(oracle.fx_decode(got, S), want)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_fx_scheme_matches_fp64_oracle(oracle_mod, periodic):
+    """A Klein-step packet (tanh step, 128 x 96 cells) for 1500 steps: the fixed-point evaluation stays within
+    relative L2 1e-12 of the FP64 oracle (both evaluate Eqs. sol_dis_1-sol_dis_4; they differ only in
+    where they round), with an absorbing layer too."""
+    run = W.KleinRun(side=128, V0=2.5 * C * C, p0=0.6 * C, width=8 * W.DX_DEFAULT, nsteps=1500, face=80)
+    psi0 = run.state()[:96]
+    V = run.potential()
+    mask = W.absorber_mask(128, 12, 0.1)
+    for absorber in (None, mask):
+        want, _ = oracle.step(psi0, 2, 1.0, C, W.DX_DEFAULT, run.nsteps, V=V, periodic=periodic, absorber=absorber)
+        S = oracle.fx_shift(psi0)
+        got = oracle.fx_decode(oracle.step_fx(oracle.fx_encode(psi0, S), 1.0, C, W.DX_DEFAULT, run.nsteps, V=V,
+                                              periodic=periodic, absorber=absorber), S)
+        err = A.rel_l2(got, want)
+        assert err < 1e-12, err
+        assert err > 0.0  # the two evaluations round differently
+
+
+def test_fx_shift_bounds_the_step_sums(oracle_mod):
+    """The shift rule keeps every intermediate below 2^62: a state concentrated in one cell (the largest
+    component the norm allows) stepped once stays finite and equals the FP64 oracle within 1e-15 relative."""
+    psi = np.zeros((6, 1, 6, 4), complex)
+    psi[3, 0, 2, :] = [0.9 + 0.1j, -0.2j, 0.3, -0.1 + 0.05j]
+    S = oracle.fx_shift(psi)
+    A_ = np.sqrt(np.sum(np.abs(psi) ** 2))
+    assert A_ * 2.0 ** S < 2.0 ** 58 <= 2 * A_ * 2.0 ** S
+    got = oracle.fx_decode(oracle.step_fx(oracle.fx_encode(psi, S), 1.0, C, W.DX_DEFAULT, 1), S)
+    want, _ = oracle.step(psi, 2, 1.0, C, W.DX_DEFAULT, 1)
+    assert A.rel_l2(got, want) < 1e-15
