@@ -15,6 +15,8 @@ grid-point-steps per second (cells x time steps / s).
              read and written once) / its mean launch time; FP64 arithmetic (56 flops per 2-D
              point-step) against the FP64 rate.
   cpu_baseline  the FP64 CPU oracle on this host's cores, on a bounded sample of the same run.
+  variants   further legs; "fx64" runs the same workload with 64-bit fixed-point storage (exact integer
+             sweeps, the phase rounded once) and reports its relative L2 distance from the FP64 state.
 
 With --gpus N > 1 (torchrun), every rank runs an independent replica of the single-grid legs (one grid per
 GPU, not sharded) and its own share of a global ensemble draw in the batched leg; value = all ranks'
@@ -65,6 +67,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-fx64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-field", action="store_true")
     ap.add_argument("--no-2d-variants", action="store_true", help="skip the 2-D Strang and shift legs")
@@ -407,10 +410,44 @@ def main():
         e2e = {"value": point_steps / e2e_s, "unit": "point-steps/s",
                "h2d_bytes_per_step": int(psi0.nbytes + V.nbytes), "d2h_bytes_per_step": 6 * 8,
                "result": {"T": r["flux_cum"] / n0, "norm": r["norm"]}}
+    # the FP64 state after one bench step (bit-exact with the oracle) and its flux: the reference of the
+    # fixed-point leg below
+    fp64_final = torch.empty_like(dev_state)
+    D.dirac_set_state(h, dev_state)
+    D.dirac_step(h, args.nsteps)
+    D.dirac_get_state(h, fp64_final)
+    fp64_flux = D.dirac_observables(h)["flux_cum"]
     D.dirac_destroy(h)
+    variants = {}
+
+    # ---------------------------------------------------------------- 64-bit fixed-point storage (DIRAC_FX64)
+    if not args.no_fx64:
+        hx = make_grid(D.DIRAC_FX64)
+        D.dirac_set_state(hx, dev_state)
+        D.dirac_autotune(hx)
+        ix = D.dirac_get_info(hx)
+        tx, _, _ = timed_device_run(hx, dev_state, args.steps, args.warmup)
+        tx = max_over_ranks(tx)
+        vx = point_steps / (tx / 1e3)
+        fx_final = torch.empty_like(dev_state)
+        D.dirac_get_state(hx, fx_final)
+        fx_flux = D.dirac_observables(hx)["flux_cum"]
+        D.dirac_destroy(hx)
+        rel = float(torch.linalg.vector_norm(fx_final - fp64_final) / torch.linalg.vector_norm(fp64_final))
+        del fx_final
+        variants["fx64"] = {
+            "value": vx, "unit": "point-steps/s", "ms_per_step": tx / args.steps,
+            "steps_per_launch": ix["steps_per_launch"], "points_per_lane": ix["points_per_lane"],
+            "fx_shift": ix["fx_shift"], "bytes_per_point_step": FP64_BYTES_PER_POINT_STEP,
+            "hbm_frac": FP64_BYTES_PER_POINT_STEP * vx / world / 1e9 / hbm_peak,
+            "rel_l2_vs_fp64_after_%d_steps" % args.nsteps: rel,
+            "flux_rel_diff_vs_fp64": abs(fx_flux - fp64_flux) / abs(fp64_flux) if fp64_flux else None,
+            "speedup_vs_fp64": vx / value,
+            "workload": "the headline 2-D Klein run, 64-bit fixed-point storage (exact integer sweeps, phase "
+                        "rounded once after a 128-bit product)"}
+    del fp64_final
 
     # ---------------------------------------------------------------- FP32 storage variant
-    variants = {}
     if not args.no_fp32:
         h32 = make_grid(D.DIRAC_FP32)
         dev32 = torch.from_numpy(psi0.astype(np.complex64).view(np.float32)).to(f"cuda:{local}")

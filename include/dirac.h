@@ -45,7 +45,11 @@ typedef enum {
     DIRAC_ERR_STATE = 6      /* call not valid in the grid's current state */
 } dirac_status;
 
-enum { DIRAC_FP64 = 0, DIRAC_FP32 = 1 };              /* storage precision */
+/* storage precision.  DIRAC_FX64: 64-bit fixed point, q = round(psi 2^S) per real component in int64, for
+ * 2-D first-order steps: the sweeps' additions are exact and each step rounds once, in the phase (a 128-bit
+ * product with the coefficients held as round(p 2^62)).  dirac_set_state picks S from the state's discrete
+ * norm (dirac_info.fx_shift); states go in and out as complex128. */
+enum { DIRAC_FP64 = 0, DIRAC_FP32 = 1, DIRAC_FX64 = 2 };
 enum { DIRAC_BC_ZERO = 0, DIRAC_BC_PERIODIC = 1 };    /* boundary */
 enum { DIRAC_V_NONE = 0, DIRAC_V_X_ONLY = 1, DIRAC_V_FULL = 2 }; /* potential layout */
 enum { DIRAC_LIE = 0, DIRAC_STRANG = 1 };             /* splitting order */
@@ -109,15 +113,25 @@ dirac_status dirac_destroy(dirac_grid *g);
 dirac_status dirac_set_potential(dirac_grid *g, const double *V, int layout, int64_t count);
 
 /* Copies a state in (layout above, storage precision of the grid; complex128 or complex64 per
- * component).  on_device != 0: psi is a device pointer on the grid's device, read on the grid's
- * stream.  Resets the step counter and the cumulative flux to 0. */
+ * component; complex128 for DIRAC_FX64, encoded on the device with a new shift S).  on_device != 0: psi is
+ * a device pointer on the grid's device, read on the grid's stream.  Resets the step counter and the
+ * cumulative flux to 0.  DIRAC_FX64 synchronises the stream (S is chosen on the host) and returns
+ * DIRAC_ERR_NONFINITE for a state holding NaN or Inf. */
 dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device);
 
-/* Copies the current state out (same layout).  Host copies are complete when the call returns;
- * device copies are ordered on the grid's stream. */
+/* Copies the current state out (same layout; DIRAC_FX64 decodes it to complex128).  Host copies are
+ * complete when the call returns; device copies are ordered on the grid's stream. */
 dirac_status dirac_get_state(dirac_grid *g, void *psi, int on_device);
 
-/* Device pointer of the current state buffer (valid until the next dirac_step / dirac_destroy). */
+/* DIRAC_FX64 grids: the fixed-point state itself, int64 q = round(psi 2^shift) in the layout above (8 values
+ * per cell), in or out without conversion (exact checkpoints).  set: the caller's shift must keep the
+ * discrete L2 norm of q below 2^58 (see DIRAC_FX64); resets the counters like dirac_set_state.  Errors:
+ * DIRAC_ERR_ARG for another precision or a null pointer. */
+dirac_status dirac_set_state_fx(dirac_grid *g, const int64_t *q, int shift, int on_device);
+dirac_status dirac_get_state_fx(dirac_grid *g, int64_t *q, int *shift, int on_device);
+
+/* Device pointer of the current state buffer (valid until the next dirac_step / dirac_destroy).
+ * DIRAC_FX64: the int64 fixed-point values q (psi = q 2^-S, S = dirac_info.fx_shift). */
 dirac_status dirac_state_ptr(dirac_grid *g, void **dev_ptr);
 
 /* Advances nsteps >= 0 time steps (asynchronous on the grid's stream): x sweep, (y sweep), z sweep,
@@ -178,6 +192,7 @@ typedef struct {
     int64_t kernel_launches;/* kernels enqueued by this grid so far (all kinds) */
     size_t device_bytes;    /* device memory owned by the grid */
     int plan;               /* DIRAC_PLAN_*: which kernels one step runs */
+    int fx_shift;           /* DIRAC_FX64: the state's fixed-point shift S (psi = q 2^-S); 0 otherwise */
 } dirac_info;
 
 /* dirac_info.plan */

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libdirac.so")
 
 DIRAC_OK, DIRAC_ERR_ARG, DIRAC_ERR_OOM, DIRAC_ERR_CUDA, DIRAC_ERR_NONFINITE, DIRAC_ERR_TIMEOUT, DIRAC_ERR_STATE = range(7)
-DIRAC_FP64, DIRAC_FP32 = 0, 1
+DIRAC_FP64, DIRAC_FP32, DIRAC_FX64 = 0, 1, 2
 DIRAC_BC_ZERO, DIRAC_BC_PERIODIC = 0, 1
 DIRAC_V_NONE, DIRAC_V_X_ONLY, DIRAC_V_FULL = 0, 1, 2
 DIRAC_LIE, DIRAC_STRANG = 0, 1
@@ -54,7 +54,8 @@ class dirac_info(ctypes.Structure):
     _fields_ = [("steps_per_launch", ctypes.c_int), ("points_per_lane", ctypes.c_int),
                 ("launch_warps", ctypes.c_int64), ("strip_width", ctypes.c_int64),
                 ("segment_rows", ctypes.c_int64), ("graphs", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan", ctypes.c_int),
+                ("fx_shift", ctypes.c_int)]
 
 
 _lib = None
@@ -77,6 +78,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dirac_set_state": (I, [P, P, I]),
         "dirac_get_state": (I, [P, P, I]),
         "dirac_state_ptr": (I, [P, ctypes.POINTER(P)]),
+        "dirac_set_state_fx": (I, [P, P, I, I]),
+        "dirac_get_state_fx": (I, [P, P, ctypes.POINTER(I), I]),
         "dirac_step": (I, [P, I64]),
         "dirac_observables": (I, [P, ctypes.POINTER(dirac_obs), P, I]),
         "dirac_set_counters": (I, [P, I64, D]),
@@ -150,6 +153,20 @@ def dirac_set_state(h, psi) -> None:
 def dirac_get_state(h, out) -> None:
     p, dev = _ptr(out, 8)
     _check(load_library().dirac_get_state(h, p, dev), h)
+
+
+def dirac_set_state_fx(h, q, shift: int) -> None:
+    """DIRAC_FX64: set the int64 fixed-point state q (psi = q 2^-shift) without conversion."""
+    p, dev = _ptr(q, 8)
+    _check(load_library().dirac_set_state_fx(h, p, int(shift), dev), h)
+
+
+def dirac_get_state_fx(h, out) -> int:
+    """DIRAC_FX64: copy the int64 fixed-point state into out; returns its shift."""
+    p, dev = _ptr(out, 8)
+    sh = ctypes.c_int()
+    _check(load_library().dirac_get_state_fx(h, p, ctypes.byref(sh), dev), h)
+    return sh.value
 
 
 def dirac_state_ptr(h) -> int:

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libdirac.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["dirac_api.cu", "sweep_f64.cu", "sweep_f32.cu", "observables.cu", "observables_noalloc.cu", "batch.cu",
            "batch_api.cu", "mlp.cu", "surrogate_api.cu", "shift.cu", "fused3d.cu", "axis.cu",
-           "strang3d.cu"]
+           "strang3d.cu", "sweep_fx.cu"]
 HOST_FLAGS = "-fPIC,-fopenmp,-ffp-contract=off,-O2"
 
 

@@ -48,6 +48,8 @@ struct dirac_grid {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int fp32 = 0;
+    int fx = 0;        // DIRAC_FX64: int64 fixed-point state q = psi 2^fx_shift
+    int fx_shift = 0;
     size_t elem = 8;
     int64_t ncells = 0;
     void *psi[2] = {nullptr, nullptr};
@@ -162,7 +164,22 @@ dirac_status upload_table(dirac_grid *g, const double *V, int layout, int64_t co
     const size_t bytes = (size_t)nentries * 4 * g->elem;
     dirac_status st = ensure_table(g, bytes);
     if (st != DIRAC_OK) return st;
-    if (g->fp32) {
+    if (g->fx) {
+        // round(p 2^62), p = the FP64 coefficient (which carries the 1/4): the phase product of the kernel
+        std::vector<long long> h((size_t)nentries * 4);
+#pragma omp parallel for schedule(static)
+        for (int64_t e = 0; e < nentries; ++e) {
+            const double v = (layout == DIRAC_V_NONE) ? 0.0 : V[e];
+            double p[4];
+            if (g->absorb.empty())
+                phase_coeffs(mu, v, g->dt, scale, p);
+            else
+                phase_coeffs_masked(mu, v, g->dt, g->absorb[e % g->cfg.n[0]], scale, p);
+            for (int k = 0; k < 4; ++k) h[e * 4 + k] = (long long)std::nearbyint(std::ldexp(p[k], 62));
+        }
+        CK(g, cudaMemcpyAsync(g->table, h.data(), bytes, cudaMemcpyHostToDevice, g->stream));
+        CK(g, cudaStreamSynchronize(g->stream));
+    } else if (g->fp32) {
         std::vector<float> h((size_t)nentries * 4);
 #pragma omp parallel for schedule(static)
         for (int64_t e = 0; e < nentries; ++e) {
@@ -338,6 +355,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
     a.ucoef_n = (int64_t)(g->avec.size() / 3);
     a.step0 = step0;
     a.inject_stall = g->inject_stall;
+    a.flux_unit = g->fx ? std::ldexp(1.0, -2 * g->fx_shift) : 1.0;
     const int mode = sweep_mode(g);
     if (mode == 6) {
         // 3-D second-order step (Sec. 2.4): A(1) B(2) A(1) C(2) D C(2) A(1) B(2) A(1), cells moved per sweep in
@@ -377,6 +395,7 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
         return DIRAC_OK;
     }
     cudaError_t e = mode == 4 ? launch_shift(a, g->fp32, char_shift(g), p.P, p.wpb, s)
+                    : g->fx   ? launch_sweep_fx(a, mode, K, p.P, p.wpb, s)
                     : g->fp32 ? launch_sweep_f32(a, mode, K, p.P, p.wpb, s)
                               : launch_sweep_f64(a, mode, K, p.P, p.wpb, s);
     if (e != cudaSuccess) return cuda_fail(g, e, "sweep kernel launch");
@@ -572,6 +591,36 @@ void release(dirac_grid *g) {
     delete g;
 }
 
+// DIRAC_FX64 state in: the complex128 state is copied to the idle ping-pong buffer, its discrete L2 norm A
+// (square root of the sum of |psi_c|^2 over all cells and components) reduced there, the shift chosen as
+// S = 58 - e with A = m 2^e, m in [0.5, 1) (so A 2^S < 2^58: a step's sums stay below 2^62), and the state
+// encoded as q = round(psi 2^S) into the current buffer.
+dirac_status fx_load_state(dirac_grid *g, const void *psi, int on_device) {
+    const size_t bytes = (size_t)g->ncells * 8 * g->elem;
+    double *tmp = static_cast<double *>(g->psi[g->cur ^ 1]);
+    CK(g, cudaMemcpyAsync(tmp, psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    ObsArgs o{};
+    o.psi = tmp;
+    o.scale = 1.0;
+    o.nx = g->cfg.n[0];
+    o.ny = g->cfg.n[1];
+    o.nz = g->cfg.n[2];
+    o.dx = g->cfg.dx;
+    o.face = -1;
+    o.partial = g->obs_partial;
+    o.out = g->obs_out;
+    CK(g, launch_observables(o, DIRAC_FP64, g->obs_blocks, g->stream));
+    CK(g, cudaMemcpyAsync(g->host_obs, g->obs_out, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(g, cudaStreamSynchronize(g->stream));
+    const double sumsq = g->host_obs[0];
+    if (!std::isfinite(sumsq)) return fail(g, DIRAC_ERR_NONFINITE, "dirac_set_state: state holds NaN or Inf");
+    int e = 0;
+    if (sumsq > 0) std::frexp(std::sqrt(sumsq), &e);
+    g->fx_shift = 58 - e;
+    CK(g, launch_fx_encode(tmp, static_cast<long long *>(g->psi[g->cur]), g->ncells * 8, g->fx_shift, g->stream));
+    return DIRAC_OK;
+}
+
 void default_plan(dirac_grid *g) {
     const int k = g->cfg.steps_per_launch, pp = g->cfg.points_per_lane;
     if (ndim_of(g) == 3) {
@@ -597,6 +646,15 @@ void default_plan(dirac_grid *g) {
         return;
     }
     const int mode = sweep_mode(g);
+    if (g->fx) {
+        int K = k > 0 ? k : 1, P = pp > 0 ? pp : 2;
+        if (!sweep_supported_fx(mode, K, P)) {
+            K = 1;
+            P = 2;
+        }
+        make_plan(g, K, P, 4, 8);
+        return;
+    }
     int K = g->fp32 ? 2 : 1, P = (g->fp32 || mode >= 2) ? 2 : 4;
     if (mode == 2 || mode == 3 || mode == 5) K = 1;  // measured: the field's phase matrix makes k = 2 register-bound
     if (mode == 5 && !g->fp32) P = 1;  // the FP64 two-level matrix step spills at P = 2
@@ -716,8 +774,16 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->ndim == 2 && cfg->n[1] != 1) return fail(nullptr, DIRAC_ERR_ARG, "2-D grids (x-z plane) need n[1] == 1");
     if (!(cfg->dx > 0) || !(cfg->c > 0) || !std::isfinite(cfg->dx) || !std::isfinite(cfg->c) || !std::isfinite(cfg->m))
         return fail(nullptr, DIRAC_ERR_ARG, "dx and c must be finite and > 0, m finite");
-    if (cfg->precision != DIRAC_FP64 && cfg->precision != DIRAC_FP32)
-        return fail(nullptr, DIRAC_ERR_ARG, "precision must be DIRAC_FP64 or DIRAC_FP32");
+    if (cfg->precision != DIRAC_FP64 && cfg->precision != DIRAC_FP32 && cfg->precision != DIRAC_FX64)
+        return fail(nullptr, DIRAC_ERR_ARG, "precision must be DIRAC_FP64, DIRAC_FP32 or DIRAC_FX64");
+    if (cfg->precision == DIRAC_FX64) {
+        if (cfg->ndim != 2 || cfg->splitting != DIRAC_LIE || cfg->char_shift > 1)
+            return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs 2-D first-order steps (DIRAC_LIE, char_shift 0 or 1)");
+        if (cfg->steps_per_launch > 2 || (cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
+                                          !sweep_supported_fx(0, cfg->steps_per_launch, cfg->points_per_lane)) ||
+            (cfg->steps_per_launch == 2 && cfg->points_per_lane > 0 && cfg->points_per_lane != 2))
+            return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs steps_per_launch 1 (points_per_lane 1, 2, 4) or 2 (2)");
+    }
     if (cfg->boundary != DIRAC_BC_ZERO && cfg->boundary != DIRAC_BC_PERIODIC)
         return fail(nullptr, DIRAC_ERR_ARG, "boundary must be DIRAC_BC_ZERO or DIRAC_BC_PERIODIC");
     if (cfg->flux_face != -1 && (cfg->flux_face < 1 || cfg->flux_face > cfg->n[0] - 1))
@@ -742,14 +808,15 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
         if (cfg->points_per_lane == 4) return fail(nullptr, DIRAC_ERR_ARG, "char_shift > 1 needs points_per_lane 0, 1 or 2");
     }
     const int vmode = cfg->splitting == DIRAC_STRANG ? 2 : 0;
-    if (cfg->steps_per_launch != 0 &&
+    if (cfg->precision != DIRAC_FX64 && cfg->steps_per_launch != 0 &&
         !(sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, 2) ||
           sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, 4)))
         return fail(nullptr, DIRAC_ERR_ARG, "unsupported steps_per_launch for this precision and splitting");
     if (cfg->points_per_lane != 0 && cfg->points_per_lane != 1 && cfg->points_per_lane != 2 &&
         cfg->points_per_lane != 4)
         return fail(nullptr, DIRAC_ERR_ARG, "points_per_lane must be 0, 1, 2 or 4");
-    if (cfg->ndim == 2 && cfg->char_shift <= 1 && cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
+    if (cfg->precision != DIRAC_FX64 && cfg->ndim == 2 && cfg->char_shift <= 1 && cfg->steps_per_launch > 0 &&
+        cfg->points_per_lane > 0 &&
         !sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, cfg->points_per_lane))
         return fail(nullptr, DIRAC_ERR_ARG, "unsupported (steps_per_launch, points_per_lane) pair");
     if (std::getenv("DIRAC_INJECT_OOM")) return fail(nullptr, DIRAC_ERR_OOM, "allocation failure injected (DIRAC_INJECT_OOM)");
@@ -760,6 +827,7 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     g->inject_stall = std::getenv("DIRAC_INJECT_STALL") ? 1 : 0;
     g->stream = static_cast<cudaStream_t>(cfg->stream);
     g->fp32 = cfg->precision == DIRAC_FP32;
+    g->fx = cfg->precision == DIRAC_FX64;
     g->elem = g->fp32 ? 4 : 8;
     g->ncells = cfg->n[0] * cfg->n[1] * cfg->n[2];
     g->dt = (cfg->splitting == DIRAC_STRANG ? (cfg->ndim == 3 ? 4.0 : 2.0) : 1.0) * cfg->dx / cfg->c;
@@ -865,6 +933,8 @@ dirac_status dirac_set_absorber(dirac_grid *g, const double *a, int64_t count) {
 
 dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, int64_t nsteps_table) {
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (g->fx && A_tilde && nsteps_table > 0)
+        return fail(g, DIRAC_ERR_ARG, "DIRAC_FX64 grids take no vector potential");
     if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
     const bool clear = !A_tilde || nsteps_table == 0;
     if (!clear)
@@ -910,8 +980,13 @@ dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device) {
     if (!psi) return fail(g, DIRAC_ERR_ARG, "dirac_set_state: null psi");
     CK(g, cudaSetDevice(g->cfg.device));
     const size_t bytes = (size_t)g->ncells * 8 * g->elem;
-    CK(g, cudaMemcpyAsync(g->psi[g->cur], psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          g->stream));
+    if (g->fx) {
+        dirac_status st = fx_load_state(g, psi, on_device);
+        if (st != DIRAC_OK) return st;
+    } else {
+        CK(g, cudaMemcpyAsync(g->psi[g->cur], psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              g->stream));
+    }
     CK(g, cudaMemsetAsync(g->flux_dev, 0, sizeof(double), g->stream));
     CK(g, cudaMemsetAsync(g->ticket + 1, 0, sizeof(unsigned), g->stream));  // clear a reported timeout
     if (!on_device) CK(g, cudaStreamSynchronize(g->stream));
@@ -924,9 +999,45 @@ dirac_status dirac_get_state(dirac_grid *g, void *psi, int on_device) {
     if (!psi) return fail(g, DIRAC_ERR_ARG, "dirac_get_state: null psi");
     CK(g, cudaSetDevice(g->cfg.device));
     const size_t bytes = (size_t)g->ncells * 8 * g->elem;
-    CK(g, cudaMemcpyAsync(psi, g->psi[g->cur], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+    const void *src = g->psi[g->cur];
+    if (g->fx) {
+        // decoded into the idle ping-pong buffer, then copied out as complex128
+        CK(g, launch_fx_decode(static_cast<const long long *>(g->psi[g->cur]), static_cast<double *>(g->psi[g->cur ^ 1]),
+                               g->ncells * 8, g->fx_shift, g->stream));
+        src = g->psi[g->cur ^ 1];
+    }
+    CK(g, cudaMemcpyAsync(psi, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    if (!on_device) CK(g, cudaStreamSynchronize(g->stream));
+    return DIRAC_OK;
+}
+
+dirac_status dirac_set_state_fx(dirac_grid *g, const int64_t *q, int shift, int on_device) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (!g->fx) return fail(g, DIRAC_ERR_ARG, "dirac_set_state_fx needs a DIRAC_FX64 grid");
+    if (!q) return fail(g, DIRAC_ERR_ARG, "dirac_set_state_fx: null q");
+    if (shift < -1000 || shift > 1000) return fail(g, DIRAC_ERR_ARG, "dirac_set_state_fx: shift out of range");
+    CK(g, cudaSetDevice(g->cfg.device));
+    const size_t bytes = (size_t)g->ncells * 8 * sizeof(int64_t);
+    CK(g, cudaMemcpyAsync(g->psi[g->cur], q, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          g->stream));
+    CK(g, cudaMemsetAsync(g->flux_dev, 0, sizeof(double), g->stream));
+    CK(g, cudaMemsetAsync(g->ticket + 1, 0, sizeof(unsigned), g->stream));
+    if (!on_device) CK(g, cudaStreamSynchronize(g->stream));
+    g->fx_shift = shift;
+    g->step = 0;
+    return DIRAC_OK;
+}
+
+dirac_status dirac_get_state_fx(dirac_grid *g, int64_t *q, int *shift, int on_device) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (!g->fx) return fail(g, DIRAC_ERR_ARG, "dirac_get_state_fx needs a DIRAC_FX64 grid");
+    if (!q) return fail(g, DIRAC_ERR_ARG, "dirac_get_state_fx: null q");
+    CK(g, cudaSetDevice(g->cfg.device));
+    const size_t bytes = (size_t)g->ncells * 8 * sizeof(int64_t);
+    CK(g, cudaMemcpyAsync(q, g->psi[g->cur], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           g->stream));
     if (!on_device) CK(g, cudaStreamSynchronize(g->stream));
+    if (shift) *shift = g->fx_shift;
     return DIRAC_OK;
 }
 
@@ -972,6 +1083,7 @@ dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, i
     }
     ObsArgs a{};
     a.psi = g->psi[g->cur];
+    a.scale = g->fx ? std::ldexp(1.0, -g->fx_shift) : 1.0;
     a.nx = g->cfg.n[0];
     a.ny = g->cfg.n[1];
     a.nz = g->cfg.n[2];
@@ -983,7 +1095,7 @@ dirac_status dirac_observables(dirac_grid *g, dirac_obs *obs, double *density, i
     a.density = dens;
     a.partial = g->obs_partial;
     a.out = g->obs_out;
-    cudaError_t e = launch_observables(a, g->fp32, g->obs_blocks, g->stream);
+    cudaError_t e = launch_observables(a, g->fx ? DIRAC_FX64 : (g->fp32 ? DIRAC_FP32 : DIRAC_FP64), g->obs_blocks, g->stream);
     if (e != cudaSuccess) return cuda_fail(g, e, "observables launch");
     g->launches += 2;
     CK(g, cudaMemcpyAsync(g->host_obs, g->obs_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
@@ -1042,6 +1154,7 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
         }
     }
     info->graphs = g->cfg.use_graphs;
+    info->fx_shift = g->fx ? g->fx_shift : 0;
     info->kernel_launches = g->launches;
     info->device_bytes = g->device_bytes;
     return DIRAC_OK;
@@ -1061,6 +1174,10 @@ dirac_status dirac_autotune(dirac_grid *g) {
         cands.push_back({1, 2, 4, 16, 0, 0});
         for (int sw : {16, 32})
             for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
+    } else if (g->fx) {
+        const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
+        for (auto &kp : KP)
+            for (int wsm : {4, 8, 12}) cands.push_back({kp[0], kp[1], 4, wsm});
     } else if (g->cfg.ndim == 3) {
         if (!field_on(g))  // with a vector potential only the fused pass applies the phase matrix
             for (int P : {1, 2, 4})

@@ -41,6 +41,8 @@ struct SweepArgs {
     // failure-detection test hook (DIRAC_INJECT_STALL): the launch's first warp makes its first row-copy
     // wait run out, so the kernel reports DIRAC_ERR_TIMEOUT through *err
     int inject_stall;
+    // multiplies the face-flux sums: 1 for floating-point states, 2^-2S for a fixed-point state q = psi 2^S
+    double flux_unit;
 };
 
 // Arguments of the 3-D z-sweep + phase kernel: the input is 4x the x-y swept state, the table is
@@ -58,6 +60,12 @@ struct ZArgs {
 // Launchers: return cudaErrorInvalidValue for an unsupported (K, P) pair.
 cudaError_t launch_sweep_f64(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
+// 64-bit fixed-point state (DIRAC_FX64): mode 0 only
+cudaError_t launch_sweep_fx(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
+bool sweep_supported_fx(int mode, int K, int P);
+// Fixed-point state conversion: q[i] = round-to-nearest-even(x[i] 2^S), and x[i] = q[i] 2^-S (n values each)
+cudaError_t launch_fx_encode(const double *x, long long *q, int64_t n, int S, cudaStream_t s);
+cudaError_t launch_fx_decode(const long long *q, double *x, int64_t n, int S, cudaStream_t s);
 cudaError_t launch_zphase_f64(const ZArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_zphase_f32(const ZArgs &a, int threads, cudaStream_t s);
 
@@ -66,6 +74,7 @@ cudaError_t launch_zphase_f32(const ZArgs &a, int threads, cudaStream_t s);
 // density when non-null.
 struct ObsArgs {
     const void *psi;
+    double scale;           // fixed-point state: psi = q scale (unused for floating-point states)
     int64_t nx, ny, nz;
     double dx, x0, y0, z0;  // x0 = x_min + dx/2 etc. (first cell centre)
     int64_t face;
@@ -73,7 +82,8 @@ struct ObsArgs {
     double *partial;        // [nblocks][5]
     double *out;            // [5]
 };
-cudaError_t launch_observables(const ObsArgs &a, int fp32, int nblocks, cudaStream_t s);
+// precision: DIRAC_FP64, DIRAC_FP32 or DIRAC_FX64 (the state then is int64 q, psi = q * a.scale)
+cudaError_t launch_observables(const ObsArgs &a, int precision, int nblocks, cudaStream_t s);
 
 // Instantiated (K, P) pairs of the sweep kernels.
 bool sweep_supported(int fp32, int mode, int K, int P);

@@ -11,11 +11,21 @@ constexpr int OBS_THREADS = 256;
 __device__ __forceinline__ double abs2(double re, double im) { return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im)); }
 
 template <typename T>
-__device__ __forceinline__ double rho_at(const T *p) {
+__device__ __forceinline__ double rho_at(const T *p, double) {
     double s = abs2((double)p[0], (double)p[1]);
     s = __dadd_rn(s, abs2((double)p[2], (double)p[3]));
     s = __dadd_rn(s, abs2((double)p[4], (double)p[5]));
     return __dadd_rn(s, abs2((double)p[6], (double)p[7]));
+}
+// fixed-point state: each component q scale (scale a power of two: exact)
+__device__ __forceinline__ double rho_at(const long long *p, double sc) {
+    double v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = __dmul_rn(__ll2double_rn(p[c]), sc);
+    double s = abs2(v[0], v[1]);
+    s = __dadd_rn(s, abs2(v[2], v[3]));
+    s = __dadd_rn(s, abs2(v[4], v[5]));
+    return __dadd_rn(s, abs2(v[6], v[7]));
 }
 
 // Sums v over the block into lane 0 of warp 0 in a fixed order.
@@ -47,7 +57,7 @@ __global__ void __launch_bounds__(OBS_THREADS) obs_partial_kernel(const ObsArgs 
     const int64_t N = a.nx * a.ny * a.nz;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (int64_t)gridDim.x * blockDim.x) {
-        const double rho = rho_at(psi + idx * 8);
+        const double rho = rho_at(psi + idx * 8, a.scale);
         const int64_t i = idx % a.nx;
         const int64_t t = idx / a.nx;
         const int64_t j = t % a.ny;
@@ -79,9 +89,11 @@ __global__ void __launch_bounds__(OBS_THREADS) obs_final_kernel(const double *pa
 
 }  // namespace
 
-cudaError_t launch_observables(const ObsArgs &a, int fp32, int nblocks, cudaStream_t s) {
-    if (fp32)
+cudaError_t launch_observables(const ObsArgs &a, int precision, int nblocks, cudaStream_t s) {
+    if (precision == 1)
         obs_partial_kernel<float><<<nblocks, OBS_THREADS, 0, s>>>(a);
+    else if (precision == 2)
+        obs_partial_kernel<long long><<<nblocks, OBS_THREADS, 0, s>>>(a);
     else
         obs_partial_kernel<double><<<nblocks, OBS_THREADS, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();

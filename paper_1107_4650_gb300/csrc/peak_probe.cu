@@ -2,6 +2,8 @@
 // Every thread runs 8 independent dependency chains of DFMA, DADD, FFMA or FADD in registers (enough
 // independent work per SM to hide the pipe latency) and stores one sum, so the timed launch is pure
 // issue.  Prints lane-instructions per second and per SM per clock at the device's maximum SM clock.
+// Also: 64-bit integer adds (chains q += q of the neighbouring chain) and int64 <-> FP64 conversion pairs
+// (q -> double -> q + 1), the operations of a fixed-point evaluation of the sweeps.
 #include <cstdio>
 #include <cuda_runtime.h>
 
@@ -25,6 +27,54 @@ __global__ void chains(T *out, int iters) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += a[k];
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// OP 0: 64-bit integer add; OP 1: int64 -> FP64 -> int64 conversion pair (counted as two instructions)
+template <int OP>
+__global__ void int_chains(long long *out, int iters) {
+    long long q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = (long long)(threadIdx.x + 1) * (k + 3);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (OP == 0)
+                q[k] += q[k ^ 1];
+            else
+                q[k] = __double2ll_rn(__ll2double_rn(q[k])) + 1;
+        }
+    }
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += q[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int OP>
+double run_int(const char *name, int blocks, int threads, int iters, double per_iter, double sms, double clk_hz) {
+    long long *out = nullptr;
+    if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(long long)) != cudaSuccess) return -1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {  // first launch is a warm-up
+        cudaEventRecord(e0);
+        int_chains<OP><<<blocks, threads>>>(out, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    const double instr = (double)blocks * threads * 8.0 * iters * per_iter;
+    const double rate = instr / (best * 1e-3);
+    std::printf("{\"op\": \"%s\", \"ms\": %.4f, \"lane_instr_per_s\": %.4e, \"per_sm_per_clk\": %.3f}\n", name, best, rate,
+                rate / (sms * clk_hz));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    return rate;
 }
 
 template <typename T, bool FMA>
@@ -66,6 +116,8 @@ int main() {
     run<double, false>("DADD", blocks, threads, 4096, sms, clk);
     run<float, true>("FFMA", blocks, threads, 65536, sms, clk);
     run<float, false>("FADD", blocks, threads, 65536, sms, clk);
+    run_int<0>("IADD64", blocks, threads, 16384, 1.0, sms, clk);
+    run_int<1>("CVT_S64_F64_PAIR", blocks, threads, 1024, 2.0, sms, clk);
     const cudaError_t e = cudaGetLastError();
     std::printf("{\"sms\": %d, \"clock_hz\": %.4e, \"status\": \"%s\"}\n", sms, clk, cudaGetErrorString(e));
     return e == cudaSuccess ? 0 : 1;

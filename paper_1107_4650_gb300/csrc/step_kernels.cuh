@@ -55,6 +55,15 @@ template <> struct Ar<float> {
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 };
 
+// 64-bit fixed point (storage DIRAC_FX64): the state is q = psi 2^S in int64, so the sweeps' additions are
+// exact; only the phase product rounds (cmulp below).
+template <> struct Ar<long long> {
+    static __device__ __forceinline__ long long add(long long a, long long b) { return a + b; }
+    static __device__ __forceinline__ long long sub(long long a, long long b) { return a - b; }
+    static __device__ __forceinline__ long long mul(long long a, long long b) { return a * b; }
+    static __device__ __forceinline__ long long fma(long long a, long long b, long long c) { return a * b + c; }
+};
+
 template <typename T> struct Cx { T re, im; };
 
 template <typename T> __device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) {
@@ -75,6 +84,19 @@ template <typename T> __device__ __forceinline__ Cx<T> cmul_i(Cx<T> a) { return 
 template <typename T> __device__ __forceinline__ Cx<T> cmul_mi(Cx<T> a) { return {a.im, -a.re}; }
 template <typename T> __device__ __forceinline__ Cx<T> cmulp(Cx<T> z, Cx<T> p) {
     return {Ar<T>::fma(z.re, p.re, -Ar<T>::mul(z.im, p.im)), Ar<T>::fma(z.re, p.im, Ar<T>::mul(z.im, p.re))};
+}
+// Fixed point: the phase coefficient p is held as round(p 2^62) (|p| <= 1/4: the sweeps' deferred 1/4 rides
+// in it), each output component is the exact 128-bit value z.re p.re - z.im p.im (resp. z.re p.im +
+// z.im p.re), rounded once to the nearest integer after the 2^-62 (halves upward).  The exact values come
+// from three products instead of four (k1 = p.re (z.re + z.im), k2 = z.re (p.im - p.re), k3 = z.im (p.re +
+// p.im); re = k1 - k3, im = k1 + k2): integer arithmetic, so the same bits.  |z| < 2^62 and |p| <= 2^60
+// keep the sums inside int64.
+__device__ __forceinline__ long long fx_round62(__int128 v) { return (long long)((v + ((__int128)1 << 61)) >> 62); }
+template <> __device__ __forceinline__ Cx<long long> cmulp<long long>(Cx<long long> z, Cx<long long> p) {
+    const __int128 k1 = (__int128)p.re * (z.re + z.im);
+    const __int128 k2 = (__int128)z.re * (p.im - p.re);
+    const __int128 k3 = (__int128)z.im * (p.re + p.im);
+    return {fx_round62(k1 - k3), fx_round62(k1 + k2)};
 }
 // acc + z p with re = fma(z.re, p.re, fma(-z.im, p.im, acc.re)), im = fma(z.re, p.im, fma(z.im, p.re, acc.im))
 template <typename T> __device__ __forceinline__ Cx<T> cmac(Cx<T> acc, Cx<T> z, Cx<T> p) {
@@ -115,6 +137,25 @@ __device__ __forceinline__ void store_pt(float *p, const Cx<float> s[4]) {
     float4 *q = reinterpret_cast<float4 *>(p);
     q[0] = make_float4(s[0].re, s[0].im, s[1].re, s[1].im);
     q[1] = make_float4(s[2].re, s[2].im, s[3].re, s[3].im);
+}
+__device__ __forceinline__ void load_pt(const long long *p, Cx<long long> s[4]) {
+    const longlong2 *q = reinterpret_cast<const longlong2 *>(p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        longlong2 v = q[c];
+        s[c] = {v.x, v.y};
+    }
+}
+__device__ __forceinline__ void store_pt(long long *p, const Cx<long long> s[4]) {
+    longlong2 *q = reinterpret_cast<longlong2 *>(p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = make_longlong2(s[c].re, s[c].im);
+}
+__device__ __forceinline__ void load_tab(const long long *p, Cx<long long> &pu, Cx<long long> &pd) {
+    const longlong2 *q = reinterpret_cast<const longlong2 *>(p);
+    longlong2 a = q[0], b = q[1];
+    pu = {a.x, a.y};
+    pd = {b.x, b.y};
 }
 __device__ __forceinline__ void load_tab(const double *p, Cx<double> &pu, Cx<double> &pd) {
     const double2 *q = reinterpret_cast<const double2 *>(p);
@@ -528,7 +569,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 x_characteristics<T, P>(zs, lane, src_prev, src_next, u14, u23, w14, w23, lu14, lu23, rw14, rw23);
                 if (has_face && q - 1 >= r_begin && q - 1 < r_end)
                     flux_row<T, P>(lu14, lu23, w14, w23, face_j, face_lane, lane, q - 1 - r_begin, q - 1 == r_end - 1,
-                                   gsm + lev * 8 * 32, 2.0, facc[lev]);
+                                   gsm + lev * 8 * 32, 2.0 * a.flux_unit, facc[lev]);
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
                     const bool keep = per || (zrow_ok && xin[j]);
@@ -569,7 +610,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
             }
             if (has_face && q >= r_begin && q < r_end)
                 flux_row<T, P>(lu14, lu23, w14, w23, face_j, face_lane, lane, q - r_begin, q == r_end - 1,
-                               gsm + lev * 8 * 32, 0.5, facc[lev]);
+                               gsm + lev * 8 * 32, 0.5 * a.flux_unit, facc[lev]);
             const bool out_row_ok = per || (q - 1 >= 0 && q - 1 < nr);
 #pragma unroll
             for (int j = 0; j < P; ++j) {

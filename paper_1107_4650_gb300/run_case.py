@@ -16,7 +16,7 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fx64"])
     ap.add_argument("--side", type=int, default=2048)
     ap.add_argument("--nsteps", type=int, default=64)
     ap.add_argument("--repeat", type=int, default=2)
@@ -43,7 +43,7 @@ def main():
 
     B.build()
     D.load_library()
-    prec = D.DIRAC_FP32 if args.precision == "fp32" else D.DIRAC_FP64
+    prec = {"fp32": D.DIRAC_FP32, "fx64": D.DIRAC_FX64}.get(args.precision, D.DIRAC_FP64)
     stream = torch.cuda.Stream()
     if args.mlp > 0:
         lo, hi = np.array([0.5, 0.2, 40.0]), np.array([3.0, 1.0, 150.0])

@@ -128,6 +128,19 @@ def test_3d_steps_per_launch_validation(lib):
         assert e.value.status == D.DIRAC_ERR_ARG
 
 
+def test_fx64_validation(lib):
+    """DIRAC_FX64 runs 2-D first-order steps only, one or two steps per launch."""
+    import paper_1107_4650_gb300 as D
+    for n, kw in (((8, 8, 8), dict(ndim=3)), ((16, 1, 16), dict(splitting=D.DIRAC_STRANG)),
+                  ((16, 1, 16), dict(char_shift=2)), ((16, 1, 16), dict(steps_per_launch=4)),
+                  ((16, 1, 16), dict(steps_per_launch=2, points_per_lane=4)), ((16, 1, 16), dict(precision=3))):
+        kw.setdefault("precision", D.DIRAC_FX64)
+        cfg = D.make_config(n, **kw)
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_create_grid(cfg)
+        assert e.value.status == D.DIRAC_ERR_ARG
+
+
 def test_char_shift_validation(lib):
     import paper_1107_4650_gb300 as D
     for kw in (dict(char_shift=5), dict(char_shift=-1), dict(char_shift=2, ndim=3, n=(8, 8, 8)),
