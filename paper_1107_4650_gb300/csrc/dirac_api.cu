@@ -647,12 +647,13 @@ void default_plan(dirac_grid *g) {
     }
     const int mode = sweep_mode(g);
     if (g->fx) {
-        int K = k > 0 ? k : 1, P = pp > 0 ? pp : 2;
+        // one cell per lane (128 registers: four blocks per SM) and enough segments to fill them
+        int K = k > 0 ? k : 1, P = pp > 0 ? pp : 1;
         if (!sweep_supported_fx(mode, K, P)) {
             K = 1;
-            P = 2;
+            P = 1;
         }
-        make_plan(g, K, P, 4, 8);
+        make_plan(g, K, P, 4, 16);
         return;
     }
     int K = g->fp32 ? 2 : 1, P = (g->fp32 || mode >= 2) ? 2 : 4;
@@ -1177,7 +1178,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
     } else if (g->fx) {
         const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
         for (auto &kp : KP)
-            for (int wsm : {4, 8, 12}) cands.push_back({kp[0], kp[1], 4, wsm});
+            for (int wsm : {8, 12, 16, 24}) cands.push_back({kp[0], kp[1], 4, wsm});
     } else if (g->cfg.ndim == 3) {
         if (!field_on(g))  // with a vector potential only the fused pass applies the phase matrix
             for (int P : {1, 2, 4})
