@@ -56,8 +56,8 @@ def _load():
         lib.oracle_step_strang2d.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
         lib.oracle_step_strang3d.argtypes = lib.oracle_step_strang2d.argtypes
-        lib.oracle_step_fx.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
-                                       ctypes.c_int, ctypes.c_int64]
+        lib.oracle_step_fx.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
         for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables,
                   lib.oracle_step_strang2d, lib.oracle_step_strang3d, lib.oracle_step_fx):
             f.restype = ctypes.c_int
@@ -245,26 +245,30 @@ def fx_decode(q, S: int) -> np.ndarray:
     return x.view(np.complex128).reshape(q.shape[:-1])
 
 
-def fx_shift(psi) -> int:
-    """The fixed-point shift for a state: S = 58 - e where the discrete L2 norm sqrt(sum |psi_c|^2) = m 2^e with
-    m in [0.5, 1), so that norm 2^S < 2^58 (0 for the zero state)."""
+def fx_shift(psi, ndim: int = 2) -> int:
+    """The fixed-point shift for a state: S = 58 - e in 2-D (57 - e in 3-D) where the discrete L2 norm
+    sqrt(sum |psi_c|^2) = m 2^e with m in [0.5, 1), so that norm 2^S < 2^58 (2^57); 0 for the zero state."""
     arr = _as_state(psi)
     A = float(np.sqrt(np.sum(arr.real ** 2 + arr.imag ** 2)))
-    return 58 - (np.frexp(A)[1] if A > 0 else 58)
+    top = 57 if ndim == 3 else 58
+    return top - (np.frexp(A)[1] if A > 0 else top)
 
 
-def step_fx(q, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False, absorber=None):
-    """nsteps first-order 2-D steps on a fixed-point state q (int64, (nz, 1, nx, 4, 2)): exact integer sweeps
-    without the 1/2 factors, the phase coefficients (carrying 1/4) held as round(p/4 2^62) and each output
-    component rounded once after the exact 128-bit product (oracle_step_fx).  Returns the new q."""
+def step_fx(q, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False, absorber=None,
+            ndim: int = 2):
+    """nsteps first-order steps on a fixed-point state q (int64, (nz, ny, nx, 4, 2); ny = 1 in 2-D): exact
+    integer sweeps without the 1/2 factors, the phase coefficients (carrying 1/4, or 1/8 in 3-D) held as
+    round(p/4 2^62) and each output component rounded once after the exact 128-bit product
+    (oracle_step_fx).  Returns the new q."""
     out = np.ascontiguousarray(q, dtype=np.int64).copy()
-    if out.ndim != 5 or out.shape[1] != 1 or out.shape[3:] != (4, 2):
-        raise ValueError("q must have shape (nz, 1, nx, 4, 2)")
+    if out.ndim != 5 or out.shape[3:] != (4, 2) or (ndim == 2 and out.shape[1] != 1):
+        raise ValueError("q must have shape (nz, ny, nx, 4, 2), ny = 1 in 2-D")
     nz, ny, nx = out.shape[:3]
     Varr, layout = _potential(V, np.zeros((nz, ny, nx, 4), complex))
     with _Absorber(absorber, nx):
-        rc = _load().oracle_step_fx(out.ctypes.data, I64_3(nx, ny, nz), int(bool(periodic)), float(m), float(c),
-                                    float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps))
+        rc = _load().oracle_step_fx(out.ctypes.data, I64_3(nx, ny, nz), int(ndim), int(bool(periodic)), float(m),
+                                    float(c), float(dx), None if Varr is None else Varr.ctypes.data, layout,
+                                    int(nsteps))
     if rc != 0:
         raise MemoryError("oracle_step_fx")
     return out

@@ -300,60 +300,92 @@ int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double 
     return 0;
 }
 
-/* ---- 64-bit fixed-point evaluation of the first-order 2-D step ----
- * The same scheme (x sweep, z sweep, phase: Eqs. sol_dis_1, sol_dis_3, sol_dis_4 at A = 0) evaluated on an
- * int64 state q = psi 2^S (re, im interleaved, the layout above), as the GPU's fixed-point storage does:
+/* ---- 64-bit fixed-point evaluation of the first-order step ----
+ * The same scheme (x sweep, y sweep in 3-D, z sweep, phase: Eqs. sol_dis_1 - sol_dis_4 at A = 0) evaluated
+ * on an int64 state q = psi 2^S (re, im interleaved, the layout above), as the GPU's fixed-point storage does:
  *   - each sweep forms the bracketed sums of its equation without the 1/2; integer sums are exact (a
- *     step's values stay below 2^62 while the input's discrete L2 norm times 2^S is below 2^58);
- *   - the phase coefficient p (as in oracle_phase, FP64, absorber factor included) times the two deferred
- *     halves 1/4 is held as P = round(p / 4 * 2^62), rounded to nearest with ties to even;
+ *     step's values stay below 2^62 while the input's discrete L2 norm times 2^S is below 2^58 in 2-D,
+ *     2^57 in 3-D);
+ *   - the phase coefficient p (as in oracle_phase, FP64, absorber factor included) times the deferred
+ *     halves (1/4 in 2-D, 1/8 in 3-D) is held as P = round(p / 4 * 2^62) (resp. p / 8), rounded to
+ *     nearest with ties to even;
  *   - each output component is the exact 128-bit value z.re P.re - z.im P.im (resp. z.re P.im + z.im P.re),
  *     scaled by 2^-62 and rounded to the nearest integer with halves upward.
  * ZERO / PERIODIC boundaries as above.  dt = dx / c. */
 typedef struct { int64_t re, im; } qcplx;
 static const qcplx QZERO4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 
-static const qcplx *qcell(const qcplx *q, const int64_t n[3], int periodic, int64_t i, int64_t k) {
+static const qcplx *qcell(const qcplx *q, const int64_t n[3], int periodic, int64_t i, int64_t j, int64_t k) {
     if (periodic) {
         i = (i % n[0] + n[0]) % n[0];
+        j = (j % n[1] + n[1]) % n[1];
         k = (k % n[2] + n[2]) % n[2];
-    } else if (i < 0 || i >= n[0] || k < 0 || k >= n[2]) {
+    } else if (i < 0 || i >= n[0] || j < 0 || j >= n[1] || k < 0 || k >= n[2]) {
         return NULL;
     }
-    return q + (k * n[0] + i) * 4;
+    return q + ((k * n[1] + j) * n[0] + i) * 4;
 }
 
 static int64_t q_round62(__int128 v) { return (int64_t)((v + ((__int128)1 << 61)) >> 62); }
 
-static int64_t q_coef(double p) { return (int64_t)nearbyint(ldexp(p * 0.25, 62)); }
+static int64_t q_coef(double p, double halves) { return (int64_t)nearbyint(ldexp(p * halves, 62)); }
 
-int oracle_step_fx(int64_t *q_d, const int64_t n[3], int periodic, double m, double c, double dx,
+int oracle_step_fx(int64_t *q_d, const int64_t n[3], int ndim, int periodic, double m, double c, double dx,
                    const double *V, int layout, int64_t nsteps) {
-    if (n[1] != 1) return -3;
+    if ((ndim != 2 && ndim != 3) || (ndim == 2 && n[1] != 1)) return -3;
     qcplx *q = (qcplx *)q_d;
-    const int64_t total = n[0] * n[2];
+    const int64_t total = n[0] * n[1] * n[2];
     qcplx *t = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
-    if (!t) return -1;
+    qcplx *u = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
+    if (!t || !u) {
+        free(t);
+        free(u);
+        return -1;
+    }
     const double dt = dx / c, mu = m * c * c * dt;
+    const double halves = ndim == 3 ? 0.125 : 0.25;
     for (int64_t s = 0; s < nsteps; ++s) {
         /* x sweep (Eq. sol_dis_1 without the 1/2): q -> t */
 #pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < n[2]; ++k)
+            for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
-                const qcplx *L = qcell(q, n, periodic, i - 1, k), *R = qcell(q, n, periodic, i + 1, k);
+                const qcplx *L = qcell(q, n, periodic, i - 1, j, k), *R = qcell(q, n, periodic, i + 1, j, k);
                 if (!L) L = QZERO4;
                 if (!R) R = QZERO4;
-                qcplx *o = t + (k * n[0] + i) * 4;
+                qcplx *o = t + ((k * n[1] + j) * n[0] + i) * 4;
                 o[0].re = (L[0].re + L[3].re) + (R[0].re - R[3].re); o[0].im = (L[0].im + L[3].im) + (R[0].im - R[3].im);
                 o[1].re = (L[1].re + L[2].re) + (R[1].re - R[2].re); o[1].im = (L[1].im + L[2].im) + (R[1].im - R[2].im);
                 o[2].re = (L[1].re + L[2].re) + (R[2].re - R[1].re); o[2].im = (L[1].im + L[2].im) + (R[2].im - R[1].im);
                 o[3].re = (L[0].re + L[3].re) + (R[3].re - R[0].re); o[3].im = (L[0].im + L[3].im) + (R[3].im - R[0].im);
             }
+        /* y sweep (Eq. sol_dis_2 without the 1/2, 3-D only; i b = (-b.im, b.re)): t -> t via u */
+        if (ndim == 3) {
+#pragma omp parallel for schedule(static)
+            for (int64_t k = 0; k < n[2]; ++k)
+                for (int64_t j = 0; j < n[1]; ++j)
+                    for (int64_t i = 0; i < n[0]; ++i) {
+                        const qcplx *L = qcell(t, n, periodic, i, j - 1, k), *R = qcell(t, n, periodic, i, j + 1, k);
+                        if (!L) L = QZERO4;
+                        if (!R) R = QZERO4;
+                        qcplx *o = u + ((k * n[1] + j) * n[0] + i) * 4;
+                        /* (L1 - i L4) + (R1 + i R4) */
+                        o[0].re = (L[0].re + L[3].im) + (R[0].re - R[3].im); o[0].im = (L[0].im - L[3].re) + (R[0].im + R[3].re);
+                        /* (L2 + i L3) + (R2 - i R3) */
+                        o[1].re = (L[1].re - L[2].im) + (R[1].re + R[2].im); o[1].im = (L[1].im + L[2].re) + (R[1].im - R[2].re);
+                        /* (L3 - i L2) + (R3 + i R2) */
+                        o[2].re = (L[2].re + L[1].im) + (R[2].re - R[1].im); o[2].im = (L[2].im - L[1].re) + (R[2].im + R[1].re);
+                        /* (L4 + i L1) + (R4 - i R1) */
+                        o[3].re = (L[3].re - L[0].im) + (R[3].re + R[0].im); o[3].im = (L[3].im + L[0].re) + (R[3].im - R[0].re);
+                    }
+            memcpy(t, u, (size_t)total * 4 * sizeof(qcplx));
+        }
         /* z sweep (Eq. sol_dis_3 without the 1/2) and phase (Eq. sol_dis_4): t -> q */
 #pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < n[2]; ++k)
+            for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
-                const qcplx *L = qcell(t, n, periodic, i, k - 1), *R = qcell(t, n, periodic, i, k + 1);
+                const qcplx *L = qcell(t, n, periodic, i, j, k - 1), *R = qcell(t, n, periodic, i, j, k + 1);
                 if (!L) L = QZERO4;
                 if (!R) R = QZERO4;
                 qcplx z[4];
@@ -361,15 +393,16 @@ int oracle_step_fx(int64_t *q_d, const int64_t n[3], int periodic, double m, dou
                 z[1].re = (L[1].re - L[3].re) + (R[1].re + R[3].re); z[1].im = (L[1].im - L[3].im) + (R[1].im + R[3].im);
                 z[2].re = (L[0].re + L[2].re) + (R[2].re - R[0].re); z[2].im = (L[0].im + L[2].im) + (R[2].im - R[0].im);
                 z[3].re = (L[3].re - L[1].re) + (R[1].re + R[3].re); z[3].im = (L[3].im - L[1].im) + (R[1].im + R[3].im);
-                const double vdt = potential(V, layout, n, i, 0, k) * dt;
+                const double vdt = potential(V, layout, n, i, j, k) * dt;
                 const double t_up = mu + vdt, t_dn = vdt - mu;
                 double pu_re = cos(t_up), pu_im = -sin(t_up), pd_re = cos(t_dn), pd_im = -sin(t_dn);
                 if (g_absorb) {
                     const double a = g_absorb[i];
                     pu_re = pu_re * a; pu_im = pu_im * a; pd_re = pd_re * a; pd_im = pd_im * a;
                 }
-                const int64_t P[4] = {q_coef(pu_re), q_coef(pu_im), q_coef(pd_re), q_coef(pd_im)};
-                qcplx *o = q + (k * n[0] + i) * 4;
+                const int64_t P[4] = {q_coef(pu_re, halves), q_coef(pu_im, halves), q_coef(pd_re, halves),
+                                      q_coef(pd_im, halves)};
+                qcplx *o = q + ((k * n[1] + j) * n[0] + i) * 4;
                 for (int cc = 0; cc < 4; ++cc) {
                     const int64_t pr = P[cc < 2 ? 0 : 2], pi = P[cc < 2 ? 1 : 3];
                     o[cc].re = q_round62((__int128)z[cc].re * pr - (__int128)z[cc].im * pi);
@@ -378,6 +411,7 @@ int oracle_step_fx(int64_t *q_d, const int64_t n[3], int periodic, double m, dou
             }
     }
     free(t);
+    free(u);
     return 0;
 }
 

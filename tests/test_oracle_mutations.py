@@ -45,10 +45,13 @@ MUTANTS = {
                            "return (int64_t)((v + ((__int128)1 << 60)) >> 62);"),
     "fx_z_sweep_sign": ("z[3].re = (L[3].re - L[1].re) + (R[1].re + R[3].re);",
                         "z[3].re = (L[1].re - L[3].re) + (R[1].re + R[3].re);"),
-    "fx_coefficient_scale": ("return (int64_t)nearbyint(ldexp(p * 0.25, 62));",
-                             "return (int64_t)nearbyint(ldexp(p * 0.5, 62));"),
-    "fx_x_sweep_neighbour": ("const qcplx *L = qcell(q, n, periodic, i - 1, k), *R = qcell(q, n, periodic, i + 1, k);",
-                             "const qcplx *L = qcell(q, n, periodic, i - 1, k), *R = qcell(q, n, periodic, i - 1, k);"),
+    "fx_coefficient_scale": ("return (int64_t)nearbyint(ldexp(p * halves, 62));",
+                             "return (int64_t)nearbyint(ldexp(p * halves, 61));"),
+    "fx_x_sweep_neighbour": ("const qcplx *L = qcell(q, n, periodic, i - 1, j, k), *R = qcell(q, n, periodic, i + 1, j, k);",
+                             "const qcplx *L = qcell(q, n, periodic, i - 1, j, k), *R = qcell(q, n, periodic, i - 1, j, k);"),
+    "fx_y_sweep_i_sign": ("o[0].re = (L[0].re + L[3].im) + (R[0].re - R[3].im);",
+                          "o[0].re = (L[0].re - L[3].im) + (R[0].re - R[3].im);"),
+    "fx_3d_halves": ("const double halves = ndim == 3 ? 0.125 : 0.25;", "const double halves = 0.25;"),
 }
 
 
@@ -73,8 +76,8 @@ def _build_mutant(tmp_path, name, old, new):
                                          ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
     lib.oracle_set_shift.argtypes = [ctypes.c_int64]
     lib.oracle_set_shift.restype = None
-    lib.oracle_step_fx.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                   P, ctypes.c_int, ctypes.c_int64]
+    lib.oracle_step_fx.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
     lib.oracle_step_fx.restype = ctypes.c_int
     return lib
 
@@ -150,6 +153,15 @@ def _pins_pass():
     q = rng.integers(-1000, 1000, size=(7, 1, 9, 4, 2), dtype=np.int64) * 64
     want, _ = oracle.step(oracle.fx_decode(q, 40), 2, 0.0, C, DX, 3, periodic=True)
     ok &= np.array_equal(oracle.step_fx(q, 0.0, C, DX, 3, periodic=True), oracle.fx_encode(want, 40))
+    q = rng.integers(-1000, 1000, size=(5, 4, 6, 4, 2), dtype=np.int64) * 512
+    want, _ = oracle.step(oracle.fx_decode(q, 40), 3, 0.0, C, DX, 3, periodic=True)
+    ok &= np.array_equal(oracle.step_fx(q, 0.0, C, DX, 3, periodic=True, ndim=3), oracle.fx_encode(want, 40))
+    psi = W.random_state(6, 5, 7, seed=98)
+    S = oracle.fx_shift(psi, 3)
+    Vr = np.random.default_rng(99).uniform(-3e4, 3e4, 210)
+    want, _ = oracle.step(psi, 3, 1.0, C, DX, 4, V=Vr, periodic=True)
+    got = oracle.fx_decode(oracle.step_fx(oracle.fx_encode(psi, S), 1.0, C, DX, 4, V=Vr, periodic=True, ndim=3), S)
+    ok &= A.rel_l2(got, want) < 1e-13
     return bool(ok)
 
 
