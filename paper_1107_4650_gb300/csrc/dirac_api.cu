@@ -412,7 +412,8 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
         z.seg_h = p.z_seg_h;
         z.periodic = a.periodic;
         z.full_table = g->table_full;
-        e = g->fp32 ? launch_zphase_f32(z, p.z_threads, s) : launch_zphase_f64(z, p.z_threads, s);
+        e = g->fx ? launch_zphase_fx(z, p.z_threads, s)
+            : g->fp32 ? launch_zphase_f32(z, p.z_threads, s) : launch_zphase_f64(z, p.z_threads, s);
         if (e != cudaSuccess) return cuda_fail(g, e, "z-phase kernel launch");
         g->launches++;
     }
@@ -616,13 +617,21 @@ dirac_status fx_load_state(dirac_grid *g, const void *psi, int on_device) {
     if (!std::isfinite(sumsq)) return fail(g, DIRAC_ERR_NONFINITE, "dirac_set_state: state holds NaN or Inf");
     int e = 0;
     if (sumsq > 0) std::frexp(std::sqrt(sumsq), &e);
-    g->fx_shift = 58 - e;
+    g->fx_shift = (ndim_of(g) == 3 ? 57 : 58) - e;
     CK(g, launch_fx_encode(tmp, static_cast<long long *>(g->psi[g->cur]), g->ncells * 8, g->fx_shift, g->stream));
     return DIRAC_OK;
 }
 
 void default_plan(dirac_grid *g) {
     const int k = g->cfg.steps_per_launch, pp = g->cfg.points_per_lane;
+    if (ndim_of(g) == 3 && g->fx) {
+        // fixed point: the x-y pass + z/phase pass (the fused kernels take floating-point states), P = 1 by
+        // default (the 128-bit phase products' registers), first order only
+        g->plan.fused3d = 0;
+        g->plan.s3_fused = 0;
+        make_plan(g, 1, pp > 0 ? pp : 1, 4, 16);
+        return;
+    }
     if (ndim_of(g) == 3) {
         // points_per_lane 0: the fused single-pass step; 1, 2 or 4: the x-y pass + z/phase pass with that P
         g->plan.fused3d = pp > 0 ? 0 : 1;
@@ -778,12 +787,15 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->precision != DIRAC_FP64 && cfg->precision != DIRAC_FP32 && cfg->precision != DIRAC_FX64)
         return fail(nullptr, DIRAC_ERR_ARG, "precision must be DIRAC_FP64, DIRAC_FP32 or DIRAC_FX64");
     if (cfg->precision == DIRAC_FX64) {
-        if (cfg->ndim != 2 || cfg->splitting != DIRAC_LIE || cfg->char_shift > 1)
-            return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs 2-D first-order steps (DIRAC_LIE, char_shift 0 or 1)");
-        if (cfg->steps_per_launch > 2 || (cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
-                                          !sweep_supported_fx(0, cfg->steps_per_launch, cfg->points_per_lane)) ||
+        if (cfg->splitting != DIRAC_LIE || cfg->char_shift > 1)
+            return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs first-order steps (DIRAC_LIE, char_shift 0 or 1)");
+        const int fmode = cfg->ndim == 3 ? 1 : 0;
+        if (cfg->steps_per_launch > 2 || (cfg->ndim == 3 && cfg->steps_per_launch > 1) ||
+            (cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
+             !sweep_supported_fx(fmode, cfg->steps_per_launch, cfg->points_per_lane)) ||
             (cfg->steps_per_launch == 2 && cfg->points_per_lane > 0 && cfg->points_per_lane != 2))
-            return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs steps_per_launch 1 (points_per_lane 1, 2, 4) or 2 (2)");
+            return fail(nullptr, DIRAC_ERR_ARG,
+                        "DIRAC_FX64 runs steps_per_launch 1 (points_per_lane 1, 2, 4) or, in 2-D, 2 (2)");
     }
     if (cfg->boundary != DIRAC_BC_ZERO && cfg->boundary != DIRAC_BC_PERIODIC)
         return fail(nullptr, DIRAC_ERR_ARG, "boundary must be DIRAC_BC_ZERO or DIRAC_BC_PERIODIC");
@@ -1175,6 +1187,9 @@ dirac_status dirac_autotune(dirac_grid *g) {
         cands.push_back({1, 2, 4, 16, 0, 0});
         for (int sw : {16, 32})
             for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
+    } else if (g->fx && g->cfg.ndim == 3) {
+        for (int P : {1, 2, 4})
+            for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});
     } else if (g->fx) {
         const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
         for (auto &kp : KP)

@@ -60,8 +60,9 @@ struct ZArgs {
 // Launchers: return cudaErrorInvalidValue for an unsupported (K, P) pair.
 cudaError_t launch_sweep_f64(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
-// 64-bit fixed-point state (DIRAC_FX64): mode 0 only
+// 64-bit fixed-point state (DIRAC_FX64): mode 0 (2-D step) and mode 1 (3-D x-y pass) with the z/phase pass
 cudaError_t launch_sweep_fx(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
+cudaError_t launch_zphase_fx(const ZArgs &a, int threads, cudaStream_t s);
 bool sweep_supported_fx(int mode, int K, int P);
 // Fixed-point state conversion: q[i] = round-to-nearest-even(x[i] 2^S), and x[i] = q[i] 2^-S (n values each)
 cudaError_t launch_fx_encode(const double *x, long long *q, int64_t n, int S, cudaStream_t s);

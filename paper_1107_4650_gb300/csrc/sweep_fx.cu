@@ -1,10 +1,11 @@
-// 64-bit fixed-point instantiations of the 2-D step kernel (storage DIRAC_FX64) and the state conversions.
+// 64-bit fixed-point instantiations of the step kernels (storage DIRAC_FX64: the 2-D step, and the 3-D x-y
+// pass and z/phase pass) and the state conversions.
 //
 // The state is q = round(psi 2^S) in int64 with S chosen from the state's discrete L2 norm A (the square
 // root of the sum of |psi_c|^2 over all cells and components, which the unitary step does not increase):
-// A 2^S < 2^58, so a step's sums, at most 16 times a component before the phase, stay below 2^62.  The x and
-// z sweeps then add exactly; the phase (Eq. sol_dis_4, coefficients round(p 2^62) carrying the sweeps' 1/4)
-// rounds each output component once.
+// A 2^S < 2^58 in 2-D (2^57 in 3-D), so a step's sums, at most 16 (3-D: 64) times a component before the
+// phase, stay below 2^62 (2^63).  The sweeps then add exactly; the phase (Eq. sol_dis_4, coefficients
+// round(p 2^62) carrying the sweeps' 1/4, or 1/8) rounds each output component once.
 #include "sweep_launch.cuh"
 
 namespace dirac {
@@ -15,11 +16,18 @@ cudaError_t launch_sweep_fx(const SweepArgs &a, int mode, int K, int P, int wpb,
         if (K == 1 && P == 2) return launch_one<long long, 1, 2, 0>(a, wpb, s);
         if (K == 1 && P == 4) return launch_one<long long, 1, 4, 0>(a, wpb, s);
         if (K == 2 && P == 2) return launch_one<long long, 2, 2, 0>(a, wpb, s);
+    } else if (mode == 1) {  // 3-D x-y pass (the z sweep and phase follow in launch_zphase_fx)
+        if (K == 1 && P == 1) return launch_one<long long, 1, 1, 1>(a, wpb, s);
+        if (K == 1 && P == 2) return launch_one<long long, 1, 2, 1>(a, wpb, s);
+        if (K == 1 && P == 4) return launch_one<long long, 1, 4, 1>(a, wpb, s);
     }
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_zphase_fx(const ZArgs &a, int threads, cudaStream_t s) { return launch_zphase<long long>(a, threads, s); }
+
 bool sweep_supported_fx(int mode, int K, int P) {
+    if (mode == 1) return K == 1 && (P == 1 || P == 2 || P == 4);
     return mode == 0 && ((K == 1 && (P == 1 || P == 2 || P == 4)) || (K == 2 && P == 2));
 }
 

@@ -1,6 +1,6 @@
-"""DIRAC_FX64 (64-bit fixed-point storage, 2-D first-order steps): the GPU's integer state against the
+"""DIRAC_FX64 (64-bit fixed-point storage, 2-D and 3-D first-order steps): the GPU's integer state against the
 fixed-point oracle bit for bit, and the decoded state against the FP64 oracle within relative L2 1e-12 after
-the Klein workload's 4000 steps (the tolerance the FP64 path is held to)."""
+the Klein workload's 4000 steps (the tolerance the FP64 path is held to) and after 3-D Coulomb steps."""
 import numpy as np
 import pytest
 
@@ -152,3 +152,60 @@ def test_fx_autotune_restores_state(D):
     finally:
         D.dirac_destroy(h)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13), (33, 1, 4)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("P", [1, 2, 4])
+@pytest.mark.parametrize("full", [False, True])
+def test_fx_3d_bit_exact_against_fixed_point_oracle(D, shape, periodic, P, full):
+    """3-D: the x-y pass and the z/phase pass on the int64 state, against oracle_step_fx bit for bit."""
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx + ny * nz + P)
+    V = np.random.default_rng(nz + P).uniform(-4e4, 4e4, nx * ny * nz if full else nx)
+    S = oracle.fx_shift(psi, 3)
+    q0 = oracle.fx_encode(psi, S)
+    want = oracle.step_fx(q0, 1.0, C, DX, 4, V=V, periodic=periodic, ndim=3)
+    cfg = D.make_config((nx, ny, nz), ndim=3, precision=D.DIRAC_FX64, points_per_lane=P,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL if full else D.DIRAC_V_X_ONLY)
+        D.dirac_set_state_fx(h, q0, S)
+        D.dirac_step(h, 4)
+        got, _ = _q_of(D, h, (nz, ny, nx))
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    assert info["plan"] == D.DIRAC_PLAN_3D_TWO_PASS and info["points_per_lane"] == P
+    assert np.array_equal(got, want)
+
+
+def test_fx_3d_coulomb_within_1e12_of_fp64_oracle(D):
+    """A moving packet in the soft-Coulomb potential (64^3, per-cell potential, face flux, 150 steps, autotuned):
+    the decoded state within relative L2 1e-12 of the FP64 oracle, the flux within 1e-12 relative, the
+    integer state equal to the fixed-point oracle's; dirac_set_state chooses the 3-D shift."""
+    n = 64
+    psi = W.gaussian_packet(n, n, DX, -n * DX / 2, -n * DX / 2, -6 * DX, 0.0, 5 * DX, 0.4 * C, ny=n, y_min=-n * DX / 2)
+    V = W.soft_coulomb_3d(n, DX, 10.0, 2 * DX).reshape(-1)
+    want, F = oracle.step(psi, 3, 1.0, C, DX, 150, V=V, flux_face=n // 2)
+    cfg = D.make_config((n, n, n), ndim=3, precision=D.DIRAC_FX64, flux_face=n // 2)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+        D.dirac_set_state(h, psi)
+        q0, S = _q_of(D, h, (n, n, n))
+        D.dirac_autotune(h)
+        D.dirac_step(h, 150)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+        q1, _ = _q_of(D, h, (n, n, n))
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    assert S == oracle.fx_shift(psi, 3)
+    err = rel_l2(got, want)
+    print("FX64 3-D vs FP64 oracle after 150 steps: rel L2 %.3e" % err)
+    assert err <= 1e-12
+    assert F > 1e-3 and abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+    assert np.array_equal(q1, oracle.step_fx(q0, 1.0, C, DX, 150, V=V, ndim=3))
