@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchArgs b) {
         a.vol = b.vol;
         a.periodic = 0;
         a.full_table = 0;
+        a.flux_unit = 1.0;  // floating-point states
         sweep_warp<T, K, P, 0, 2>(a, (int64_t)task - b.task_off[lo], lane, wsmem);  // two rows per iteration: measured faster here
     }
     // last block folds the flux partials of every active run and resets the counters

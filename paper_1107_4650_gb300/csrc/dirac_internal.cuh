@@ -42,7 +42,7 @@ struct SweepArgs {
     // wait run out, so the kernel reports DIRAC_ERR_TIMEOUT through *err
     int inject_stall;
     // multiplies the face-flux sums: 1 for floating-point states, 2^-2S for a fixed-point state q = psi 2^S
-    double flux_unit;
+    double flux_unit = 1.0;
 };
 
 // Arguments of the 3-D z-sweep + phase kernel: the input is 4x the x-y swept state, the table is
