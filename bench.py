@@ -416,6 +416,7 @@ def main():
     D.dirac_set_state(h, dev_state)
     D.dirac_step(h, args.nsteps)
     D.dirac_get_state(h, fp64_final)
+    stream.synchronize()
     fp64_flux = D.dirac_observables(h)["flux_cum"]
     D.dirac_destroy(h)
     variants = {}
@@ -431,6 +432,7 @@ def main():
         vx = point_steps / (tx / 1e3)
         fx_final = torch.empty_like(dev_state)
         D.dirac_get_state(hx, fx_final)
+        stream.synchronize()
         fx_flux = D.dirac_observables(hx)["flux_cum"]
         D.dirac_destroy(hx)
         rel = float(torch.linalg.vector_norm(fx_final - fp64_final) / torch.linalg.vector_norm(fp64_final))
@@ -570,6 +572,7 @@ def main():
                 if split == D.DIRAC_LIE and prec != D.DIRAC_FP32:
                     fin = torch.empty_like(dev3)
                     D.dirac_get_state(h3, fin)
+                    stream.synchronize()  # the copy runs on the grid's stream; torch reads on its own
                     if prec == D.DIRAC_FP64:
                         ref3 = fin
                     elif ref3 is not None:
