@@ -246,11 +246,12 @@ def fx_decode(q, S: int) -> np.ndarray:
 
 
 def fx_shift(psi, ndim: int = 2) -> int:
-    """The fixed-point shift for a state: S = 58 - e in 2-D (57 - e in 3-D) where the discrete L2 norm
-    sqrt(sum |psi_c|^2) = m 2^e with m in [0.5, 1), so that norm 2^S < 2^58 (2^57); 0 for the zero state."""
+    """The fixed-point shift for a state: S = 60 - e in 2-D (59 - e in 3-D) where the discrete L2 norm
+    sqrt(sum |psi_c|^2) = m 2^e with m in [0.5, 1), so that norm 2^S < 2^60 (2^59); 0 for the zero state.
+    Each sweep with its 1/2 and the phase do not raise the norm, so a step's values stay below 2^62."""
     arr = _as_state(psi)
     A = float(np.sqrt(np.sum(arr.real ** 2 + arr.imag ** 2)))
-    top = 57 if ndim == 3 else 58
+    top = 59 if ndim == 3 else 60
     return top - (np.frexp(A)[1] if A > 0 else top)
 
 

@@ -304,8 +304,9 @@ int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double 
  * The same scheme (x sweep, y sweep in 3-D, z sweep, phase: Eqs. sol_dis_1 - sol_dis_4 at A = 0) evaluated
  * on an int64 state q = psi 2^S (re, im interleaved, the layout above), as the GPU's fixed-point storage does:
  *   - each sweep forms the bracketed sums of its equation without the 1/2; integer sums are exact (a
- *     step's values stay below 2^62 while the input's discrete L2 norm times 2^S is below 2^58 in 2-D,
- *     2^57 in 3-D);
+ *     step's values stay below 2^62 while the input's discrete L2 norm times 2^S is below 2^60 in 2-D,
+ *     2^59 in 3-D: each sweep with its 1/2 and the phase do not raise that norm, so j sweeps without
+ *     the 1/2 leave every component below 2^j times it);
  *   - the phase coefficient p (as in oracle_phase, FP64, absorber factor included) times the deferred
  *     halves (1/4 in 2-D, 1/8 in 3-D) is held as P = round(p / 4 * 2^62) (resp. p / 8), rounded to
  *     nearest with ties to even;

@@ -594,7 +594,9 @@ void release(dirac_grid *g) {
 
 // DIRAC_FX64 state in: the complex128 state is copied to the idle ping-pong buffer, its discrete L2 norm A
 // (square root of the sum of |psi_c|^2 over all cells and components) reduced there, the shift chosen as
-// S = 58 - e with A = m 2^e, m in [0.5, 1) (so A 2^S < 2^58: a step's sums stay below 2^62), and the state
+// S = 60 - e in 2-D, 59 - e in 3-D, with A = m 2^e, m in [0.5, 1): each sweep (with its 1/2) and the phase
+// do not raise the discrete norm, so after j of the step's sweeps (without the 1/2) a component is at most
+// 2^j A, and every sum of a step stays below 2^62 (the two-component sums below 2^62.5); and the state
 // encoded as q = round(psi 2^S) into the current buffer.
 dirac_status fx_load_state(dirac_grid *g, const void *psi, int on_device) {
     const size_t bytes = (size_t)g->ncells * 8 * g->elem;
@@ -617,7 +619,7 @@ dirac_status fx_load_state(dirac_grid *g, const void *psi, int on_device) {
     if (!std::isfinite(sumsq)) return fail(g, DIRAC_ERR_NONFINITE, "dirac_set_state: state holds NaN or Inf");
     int e = 0;
     if (sumsq > 0) std::frexp(std::sqrt(sumsq), &e);
-    g->fx_shift = (ndim_of(g) == 3 ? 57 : 58) - e;
+    g->fx_shift = (ndim_of(g) == 3 ? 59 : 60) - e;
     CK(g, launch_fx_encode(tmp, static_cast<long long *>(g->psi[g->cur]), g->ncells * 8, g->fx_shift, g->stream));
     return DIRAC_OK;
 }

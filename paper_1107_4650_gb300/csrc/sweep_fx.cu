@@ -2,9 +2,10 @@
 // pass and z/phase pass) and the state conversions.
 //
 // The state is q = round(psi 2^S) in int64 with S chosen from the state's discrete L2 norm A (the square
-// root of the sum of |psi_c|^2 over all cells and components, which the unitary step does not increase):
-// A 2^S < 2^58 in 2-D (2^57 in 3-D), so a step's sums, at most 16 (3-D: 64) times a component before the
-// phase, stay below 2^62 (2^63).  The sweeps then add exactly; the phase (Eq. sol_dis_4, coefficients
+// root of the sum of |psi_c|^2 over all cells and components): each sweep with its 1/2 and the phase are
+// contractions in that norm, so a component after j sweeps without the 1/2 is at most 2^j A; with
+// A 2^S < 2^60 in 2-D (2^59 in 3-D) every value of a step stays below 2^62 and every sum of two
+// components below 2^62.5.  The sweeps then add exactly; the phase (Eq. sol_dis_4, coefficients
 // round(p 2^62) carrying the sweeps' 1/4, or 1/8) rounds each output component once.
 #include "sweep_launch.cuh"
 
