@@ -58,8 +58,10 @@ def _load():
         lib.oracle_step_strang3d.argtypes = lib.oracle_step_strang2d.argtypes
         lib.oracle_step_fx.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
+        lib.oracle_step_strang2d_fx.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
         for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables,
-                  lib.oracle_step_strang2d, lib.oracle_step_strang3d, lib.oracle_step_fx):
+                  lib.oracle_step_strang2d, lib.oracle_step_strang3d, lib.oracle_step_fx, lib.oracle_step_strang2d_fx):
             f.restype = ctypes.c_int
         lib.oracle_set_absorber.argtypes = [P]
         lib.oracle_set_absorber.restype = None
@@ -272,6 +274,24 @@ def step_fx(q, m: float, c: float, dx: float, nsteps: int, V=None, periodic: boo
                                     int(nsteps))
     if rc != 0:
         raise MemoryError("oracle_step_fx")
+    return out
+
+
+def step_strang2d_fx(q, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False, absorber=None):
+    """nsteps second-order 2-D steps (x, z, phase over 2 dx / c, z, x; Sec. 2.4) on a fixed-point state q
+    (int64, (nz, 1, nx, 4, 2)): exact integer sweeps, the phase coefficients carrying the four sweeps' halves
+    (1/16) as round(p/16 2^62), each output component rounded once (oracle_step_strang2d_fx)."""
+    out = np.ascontiguousarray(q, dtype=np.int64).copy()
+    if out.ndim != 5 or out.shape[1] != 1 or out.shape[3:] != (4, 2):
+        raise ValueError("q must have shape (nz, 1, nx, 4, 2)")
+    nz, ny, nx = out.shape[:3]
+    Varr, layout = _potential(V, np.zeros((nz, ny, nx, 4), complex))
+    with _Absorber(absorber, nx):
+        rc = _load().oracle_step_strang2d_fx(out.ctypes.data, I64_3(nx, ny, nz), int(bool(periodic)), float(m),
+                                             float(c), float(dx), None if Varr is None else Varr.ctypes.data,
+                                             layout, int(nsteps))
+    if rc != 0:
+        raise MemoryError("oracle_step_strang2d_fx")
     return out
 
 

@@ -331,69 +331,70 @@ static int64_t q_round62(__int128 v) { return (int64_t)((v + ((__int128)1 << 61)
 
 static int64_t q_coef(double p, double halves) { return (int64_t)nearbyint(ldexp(p * halves, 62)); }
 
-int oracle_step_fx(int64_t *q_d, const int64_t n[3], int ndim, int periodic, double m, double c, double dx,
-                   const double *V, int layout, int64_t nsteps) {
-    if ((ndim != 2 && ndim != 3) || (ndim == 2 && n[1] != 1)) return -3;
-    qcplx *q = (qcplx *)q_d;
-    const int64_t total = n[0] * n[1] * n[2];
-    qcplx *t = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
-    qcplx *u = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
-    if (!t || !u) {
-        free(t);
-        free(u);
-        return -1;
-    }
-    const double dt = dx / c, mu = m * c * c * dt;
-    const double halves = ndim == 3 ? 0.125 : 0.25;
-    for (int64_t s = 0; s < nsteps; ++s) {
-        /* x sweep (Eq. sol_dis_1 without the 1/2): q -> t */
+/* x sweep (Eq. sol_dis_1 without the 1/2): in -> out */
+static void fx_sweep_x(const qcplx *in, qcplx *out, const int64_t n[3], int periodic) {
 #pragma omp parallel for schedule(static)
-        for (int64_t k = 0; k < n[2]; ++k)
-            for (int64_t j = 0; j < n[1]; ++j)
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
-                const qcplx *L = qcell(q, n, periodic, i - 1, j, k), *R = qcell(q, n, periodic, i + 1, j, k);
+                const qcplx *L = qcell(in, n, periodic, i - 1, j, k), *R = qcell(in, n, periodic, i + 1, j, k);
                 if (!L) L = QZERO4;
                 if (!R) R = QZERO4;
-                qcplx *o = t + ((k * n[1] + j) * n[0] + i) * 4;
+                qcplx *o = out + ((k * n[1] + j) * n[0] + i) * 4;
                 o[0].re = (L[0].re + L[3].re) + (R[0].re - R[3].re); o[0].im = (L[0].im + L[3].im) + (R[0].im - R[3].im);
                 o[1].re = (L[1].re + L[2].re) + (R[1].re - R[2].re); o[1].im = (L[1].im + L[2].im) + (R[1].im - R[2].im);
                 o[2].re = (L[1].re + L[2].re) + (R[2].re - R[1].re); o[2].im = (L[1].im + L[2].im) + (R[2].im - R[1].im);
                 o[3].re = (L[0].re + L[3].re) + (R[3].re - R[0].re); o[3].im = (L[0].im + L[3].im) + (R[3].im - R[0].im);
             }
-        /* y sweep (Eq. sol_dis_2 without the 1/2, 3-D only; i b = (-b.im, b.re)): t -> t via u */
-        if (ndim == 3) {
+}
+
+/* y sweep (Eq. sol_dis_2 without the 1/2; i b = (-b.im, b.re)): in -> out */
+static void fx_sweep_y(const qcplx *in, qcplx *out, const int64_t n[3], int periodic) {
 #pragma omp parallel for schedule(static)
-            for (int64_t k = 0; k < n[2]; ++k)
-                for (int64_t j = 0; j < n[1]; ++j)
-                    for (int64_t i = 0; i < n[0]; ++i) {
-                        const qcplx *L = qcell(t, n, periodic, i, j - 1, k), *R = qcell(t, n, periodic, i, j + 1, k);
-                        if (!L) L = QZERO4;
-                        if (!R) R = QZERO4;
-                        qcplx *o = u + ((k * n[1] + j) * n[0] + i) * 4;
-                        /* (L1 - i L4) + (R1 + i R4) */
-                        o[0].re = (L[0].re + L[3].im) + (R[0].re - R[3].im); o[0].im = (L[0].im - L[3].re) + (R[0].im + R[3].re);
-                        /* (L2 + i L3) + (R2 - i R3) */
-                        o[1].re = (L[1].re - L[2].im) + (R[1].re + R[2].im); o[1].im = (L[1].im + L[2].re) + (R[1].im - R[2].re);
-                        /* (L3 - i L2) + (R3 + i R2) */
-                        o[2].re = (L[2].re + L[1].im) + (R[2].re - R[1].im); o[2].im = (L[2].im - L[1].re) + (R[2].im + R[1].re);
-                        /* (L4 + i L1) + (R4 - i R1) */
-                        o[3].re = (L[3].re - L[0].im) + (R[3].re + R[0].im); o[3].im = (L[3].im + L[0].re) + (R[3].im - R[0].re);
-                    }
-            memcpy(t, u, (size_t)total * 4 * sizeof(qcplx));
-        }
-        /* z sweep (Eq. sol_dis_3 without the 1/2) and phase (Eq. sol_dis_4): t -> q */
-#pragma omp parallel for schedule(static)
-        for (int64_t k = 0; k < n[2]; ++k)
-            for (int64_t j = 0; j < n[1]; ++j)
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
-                const qcplx *L = qcell(t, n, periodic, i, j, k - 1), *R = qcell(t, n, periodic, i, j, k + 1);
+                const qcplx *L = qcell(in, n, periodic, i, j - 1, k), *R = qcell(in, n, periodic, i, j + 1, k);
                 if (!L) L = QZERO4;
                 if (!R) R = QZERO4;
-                qcplx z[4];
+                qcplx *o = out + ((k * n[1] + j) * n[0] + i) * 4;
+                /* (L1 - i L4) + (R1 + i R4) */
+                o[0].re = (L[0].re + L[3].im) + (R[0].re - R[3].im); o[0].im = (L[0].im - L[3].re) + (R[0].im + R[3].re);
+                /* (L2 + i L3) + (R2 - i R3) */
+                o[1].re = (L[1].re - L[2].im) + (R[1].re + R[2].im); o[1].im = (L[1].im + L[2].re) + (R[1].im - R[2].re);
+                /* (L3 - i L2) + (R3 + i R2) */
+                o[2].re = (L[2].re + L[1].im) + (R[2].re - R[1].im); o[2].im = (L[2].im - L[1].re) + (R[2].im + R[1].re);
+                /* (L4 + i L1) + (R4 - i R1) */
+                o[3].re = (L[3].re - L[0].im) + (R[3].re + R[0].im); o[3].im = (L[3].im + L[0].re) + (R[3].im - R[0].re);
+            }
+}
+
+/* z sweep (Eq. sol_dis_3 without the 1/2): in -> out */
+static void fx_sweep_z(const qcplx *in, qcplx *out, const int64_t n[3], int periodic) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i) {
+                const qcplx *L = qcell(in, n, periodic, i, j, k - 1), *R = qcell(in, n, periodic, i, j, k + 1);
+                if (!L) L = QZERO4;
+                if (!R) R = QZERO4;
+                qcplx *z = out + ((k * n[1] + j) * n[0] + i) * 4;
                 z[0].re = (L[0].re + L[2].re) + (R[0].re - R[2].re); z[0].im = (L[0].im + L[2].im) + (R[0].im - R[2].im);
                 z[1].re = (L[1].re - L[3].re) + (R[1].re + R[3].re); z[1].im = (L[1].im - L[3].im) + (R[1].im + R[3].im);
                 z[2].re = (L[0].re + L[2].re) + (R[2].re - R[0].re); z[2].im = (L[0].im + L[2].im) + (R[2].im - R[0].im);
                 z[3].re = (L[3].re - L[1].re) + (R[1].re + R[3].re); z[3].im = (L[3].im - L[1].im) + (R[1].im + R[3].im);
+            }
+}
+
+/* Phase (Eq. sol_dis_4 at A = 0) over dt, in place: P = round(p * halves * 2^62), each output component
+ * round((z.re P.re - z.im P.im) 2^-62) (resp. z.re P.im + z.im P.re) from the exact 128-bit value. */
+static void fx_phase(qcplx *q, const int64_t n[3], double m, double c, double dt, const double *V, int layout,
+                     double halves) {
+    const double mu = m * c * c * dt;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i) {
                 const double vdt = potential(V, layout, n, i, j, k) * dt;
                 const double t_up = mu + vdt, t_dn = vdt - mu;
                 double pu_re = cos(t_up), pu_im = -sin(t_up), pd_re = cos(t_dn), pd_im = -sin(t_dn);
@@ -406,13 +407,59 @@ int oracle_step_fx(int64_t *q_d, const int64_t n[3], int ndim, int periodic, dou
                 qcplx *o = q + ((k * n[1] + j) * n[0] + i) * 4;
                 for (int cc = 0; cc < 4; ++cc) {
                     const int64_t pr = P[cc < 2 ? 0 : 2], pi = P[cc < 2 ? 1 : 3];
-                    o[cc].re = q_round62((__int128)z[cc].re * pr - (__int128)z[cc].im * pi);
-                    o[cc].im = q_round62((__int128)z[cc].re * pi + (__int128)z[cc].im * pr);
+                    const qcplx z = o[cc];
+                    o[cc].re = q_round62((__int128)z.re * pr - (__int128)z.im * pi);
+                    o[cc].im = q_round62((__int128)z.re * pi + (__int128)z.im * pr);
                 }
             }
+}
+
+/* nsteps first-order steps (x, y in 3-D, z, phase), dt = dx / c. */
+int oracle_step_fx(int64_t *q_d, const int64_t n[3], int ndim, int periodic, double m, double c, double dx,
+                   const double *V, int layout, int64_t nsteps) {
+    if ((ndim != 2 && ndim != 3) || (ndim == 2 && n[1] != 1)) return -3;
+    qcplx *q = (qcplx *)q_d;
+    const int64_t total = n[0] * n[1] * n[2];
+    qcplx *t = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
+    qcplx *u = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
+    if (!t || !u) {
+        free(t);
+        free(u);
+        return -1;
+    }
+    const double halves = ndim == 3 ? 0.125 : 0.25;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        fx_sweep_x(q, t, n, periodic);
+        if (ndim == 3) {
+            fx_sweep_y(t, u, n, periodic);
+            memcpy(t, u, (size_t)total * 4 * sizeof(qcplx));
+        }
+        fx_sweep_z(t, q, n, periodic);
+        fx_phase(q, n, m, c, dx / c, V, layout, halves);
     }
     free(t);
     free(u);
+    return 0;
+}
+
+/* nsteps second-order steps in the x-z plane (Sec. 2.4): x, z, phase over dt = 2 dx / c with the four
+ * sweeps' halves (1/16) in its coefficients, z, x.  The phase output is a quarter of the state (rounded at
+ * that scale); the last two sweeps double it twice, exactly. */
+int oracle_step_strang2d_fx(int64_t *q_d, const int64_t n[3], int periodic, double m, double c, double dx,
+                            const double *V, int layout, int64_t nsteps) {
+    if (n[1] != 1) return -3;
+    qcplx *q = (qcplx *)q_d;
+    const int64_t total = n[0] * n[2];
+    qcplx *t = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
+    if (!t) return -1;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        fx_sweep_x(q, t, n, periodic);
+        fx_sweep_z(t, q, n, periodic);
+        fx_phase(q, n, m, c, 2.0 * dx / c, V, layout, 0.0625);
+        fx_sweep_z(q, t, n, periodic);
+        fx_sweep_x(t, q, n, periodic);
+    }
+    free(t);
     return 0;
 }
 

@@ -47,11 +47,14 @@ MUTANTS = {
                         "z[3].re = (L[1].re - L[3].re) + (R[1].re + R[3].re);"),
     "fx_coefficient_scale": ("return (int64_t)nearbyint(ldexp(p * halves, 62));",
                              "return (int64_t)nearbyint(ldexp(p * halves, 61));"),
-    "fx_x_sweep_neighbour": ("const qcplx *L = qcell(q, n, periodic, i - 1, j, k), *R = qcell(q, n, periodic, i + 1, j, k);",
-                             "const qcplx *L = qcell(q, n, periodic, i - 1, j, k), *R = qcell(q, n, periodic, i - 1, j, k);"),
+    "fx_x_sweep_neighbour": ("const qcplx *L = qcell(in, n, periodic, i - 1, j, k), *R = qcell(in, n, periodic, i + 1, j, k);",
+                             "const qcplx *L = qcell(in, n, periodic, i - 1, j, k), *R = qcell(in, n, periodic, i - 1, j, k);"),
     "fx_y_sweep_i_sign": ("o[0].re = (L[0].re + L[3].im) + (R[0].re - R[3].im);",
                           "o[0].re = (L[0].re - L[3].im) + (R[0].re - R[3].im);"),
     "fx_3d_halves": ("const double halves = ndim == 3 ? 0.125 : 0.25;", "const double halves = 0.25;"),
+    "fx_strang_halves": ("fx_phase(q, n, m, c, 2.0 * dx / c, V, layout, 0.0625);", "fx_phase(q, n, m, c, 2.0 * dx / c, V, layout, 0.125);"),
+    "fx_strang_order": ("        fx_sweep_z(q, t, n, periodic);\n        fx_sweep_x(t, q, n, periodic);\n    }\n    free(t);\n    return 0;",
+                        "        fx_sweep_x(q, t, n, periodic);\n        fx_sweep_z(t, q, n, periodic);\n    }\n    free(t);\n    return 0;"),
 }
 
 
@@ -74,11 +77,15 @@ def _build_mutant(tmp_path, name, old, new):
     lib.oracle_set_vector_potential.restype = None
     lib.oracle_step_strang3d.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P]
+    lib.oracle_step_strang2d.argtypes = lib.oracle_step_strang3d.argtypes
     lib.oracle_set_shift.argtypes = [ctypes.c_int64]
     lib.oracle_set_shift.restype = None
     lib.oracle_step_fx.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
     lib.oracle_step_fx.restype = ctypes.c_int
+    lib.oracle_step_strang2d_fx.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
+    lib.oracle_step_strang2d_fx.restype = ctypes.c_int
     return lib
 
 
@@ -162,6 +169,15 @@ def _pins_pass():
     want, _ = oracle.step(psi, 3, 1.0, C, DX, 4, V=Vr, periodic=True)
     got = oracle.fx_decode(oracle.step_fx(oracle.fx_encode(psi, S), 1.0, C, DX, 4, V=Vr, periodic=True, ndim=3), S)
     ok &= A.rel_l2(got, want) < 1e-13
+    # fixed-point second-order 2-D step: exact where FP64 is exact, and within 1e-13 of the FP64 Strang step
+    q = rng.integers(-1000, 1000, size=(6, 1, 7, 4, 2), dtype=np.int64) * 4096
+    want, _ = oracle.step_strang2d(oracle.fx_decode(q, 40), 0.0, C, DX, 3, periodic=True)
+    ok &= np.array_equal(oracle.step_strang2d_fx(q, 0.0, C, DX, 3, periodic=True), oracle.fx_encode(want, 40))
+    psi = W.random_state(9, 1, 11, seed=100)
+    S = oracle.fx_shift(psi)
+    Vr = np.random.default_rng(101).uniform(-3e4, 3e4, 11)
+    want, _ = oracle.step_strang2d(psi, 1.0, C, DX, 5, V=Vr)
+    ok &= A.rel_l2(oracle.fx_decode(oracle.step_strang2d_fx(oracle.fx_encode(psi, S), 1.0, C, DX, 5, V=Vr), S), want) < 1e-13
     return bool(ok)
 
 

@@ -847,3 +847,28 @@ def test_fx_3d_scheme_matches_fp64_oracle(oracle_mod, periodic):
     got = oracle.fx_decode(oracle.step_fx(oracle.fx_encode(psi, S), 1.0, C, dx, 60, V=V, periodic=periodic, ndim=3), S)
     err = A.rel_l2(got, want)
     assert 0.0 < err < 1e-12, err
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_fx_strang2d_exact_where_fp64_is_exact(oracle_mod, periodic):
+    """Second-order 2-D step in fixed point: m = 0, V = 0 and values that are multiples of 16^3 make three steps
+    exact in both evaluations (the phase divides by 16 exactly), so they agree exactly."""
+    rng = np.random.default_rng(73)
+    q = rng.integers(-1000, 1000, size=(7, 1, 9, 4, 2), dtype=np.int64) * 4096
+    want, _ = oracle.step_strang2d(oracle.fx_decode(q, 40), 0.0, C, W.DX_DEFAULT, 3, periodic=periodic)
+    got = oracle.step_strang2d_fx(q, 0.0, C, W.DX_DEFAULT, 3, periodic=periodic)
+    assert np.array_equal(got, oracle.fx_encode(want, 40))
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_fx_strang2d_matches_fp64_oracle(oracle_mod, periodic):
+    """A Klein-step packet for 800 second-order steps: the fixed-point evaluation within relative L2 1e-12 of
+    the FP64 Strang oracle."""
+    run = W.KleinRun(side=128, V0=2.5 * C * C, p0=0.6 * C, width=8 * W.DX_DEFAULT, nsteps=800, face=80)
+    psi0 = run.state()[:96]
+    V = run.potential()
+    want, _ = oracle.step_strang2d(psi0, 1.0, C, W.DX_DEFAULT, run.nsteps, V=V, periodic=periodic)
+    S = oracle.fx_shift(psi0)
+    q = oracle.step_strang2d_fx(oracle.fx_encode(psi0, S), 1.0, C, W.DX_DEFAULT, run.nsteps, V=V, periodic=periodic)
+    err = A.rel_l2(oracle.fx_decode(q, S), want)
+    assert 0.0 < err < 1e-12, err
