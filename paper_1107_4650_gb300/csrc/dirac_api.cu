@@ -789,10 +789,11 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->precision != DIRAC_FP64 && cfg->precision != DIRAC_FP32 && cfg->precision != DIRAC_FX64)
         return fail(nullptr, DIRAC_ERR_ARG, "precision must be DIRAC_FP64, DIRAC_FP32 or DIRAC_FX64");
     if (cfg->precision == DIRAC_FX64) {
-        if (cfg->splitting != DIRAC_LIE || cfg->char_shift > 1)
-            return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs first-order steps (DIRAC_LIE, char_shift 0 or 1)");
-        const int fmode = cfg->ndim == 3 ? 1 : 0;
-        if (cfg->steps_per_launch > 2 || (cfg->ndim == 3 && cfg->steps_per_launch > 1) ||
+        if ((cfg->splitting != DIRAC_LIE && !(cfg->splitting == DIRAC_STRANG && cfg->ndim == 2)) || cfg->char_shift > 1)
+            return fail(nullptr, DIRAC_ERR_ARG,
+                        "DIRAC_FX64 runs first-order steps and 2-D second-order steps (char_shift 0 or 1)");
+        const int fmode = cfg->ndim == 3 ? 1 : (cfg->splitting == DIRAC_STRANG ? 2 : 0);
+        if (cfg->steps_per_launch > 2 || ((cfg->ndim == 3 || fmode == 2) && cfg->steps_per_launch > 1) ||
             (cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
              !sweep_supported_fx(fmode, cfg->steps_per_launch, cfg->points_per_lane)) ||
             (cfg->steps_per_launch == 2 && cfg->points_per_lane > 0 && cfg->points_per_lane != 2))
@@ -1195,7 +1196,8 @@ dirac_status dirac_autotune(dirac_grid *g) {
     } else if (g->fx) {
         const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
         for (auto &kp : KP)
-            for (int wsm : {8, 12, 16, 24}) cands.push_back({kp[0], kp[1], 4, wsm});
+            if (sweep_supported_fx(sweep_mode(g), kp[0], kp[1]))
+                for (int wsm : {8, 12, 16, 24}) cands.push_back({kp[0], kp[1], 4, wsm});
     } else if (g->cfg.ndim == 3) {
         if (!field_on(g))  // with a vector potential only the fused pass applies the phase matrix
             for (int P : {1, 2, 4})

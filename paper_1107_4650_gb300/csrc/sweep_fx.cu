@@ -17,6 +17,9 @@ cudaError_t launch_sweep_fx(const SweepArgs &a, int mode, int K, int P, int wpb,
         if (K == 1 && P == 2) return launch_one<long long, 1, 2, 0>(a, wpb, s);
         if (K == 1 && P == 4) return launch_one<long long, 1, 4, 0>(a, wpb, s);
         if (K == 2 && P == 2) return launch_one<long long, 2, 2, 0>(a, wpb, s);
+    } else if (mode == 2) {  // 2-D second-order step
+        if (K == 1 && P == 1) return launch_one<long long, 1, 1, 2>(a, wpb, s);
+        if (K == 1 && P == 2) return launch_one<long long, 1, 2, 2>(a, wpb, s);
     } else if (mode == 1) {  // 3-D x-y pass (the z sweep and phase follow in launch_zphase_fx)
         if (K == 1 && P == 1) return launch_one<long long, 1, 1, 1>(a, wpb, s);
         if (K == 1 && P == 2) return launch_one<long long, 1, 2, 1>(a, wpb, s);
@@ -29,6 +32,7 @@ cudaError_t launch_zphase_fx(const ZArgs &a, int threads, cudaStream_t s) { retu
 
 bool sweep_supported_fx(int mode, int K, int P) {
     if (mode == 1) return K == 1 && (P == 1 || P == 2 || P == 4);
+    if (mode == 2) return K == 1 && (P == 1 || P == 2);
     return mode == 0 && ((K == 1 && (P == 1 || P == 2 || P == 4)) || (K == 2 && P == 2));
 }
 

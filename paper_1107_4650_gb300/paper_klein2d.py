@@ -1,6 +1,6 @@
 """The paper's 2-D Klein-paradox run (Sec. 5.2.2) at its full size on one GPU.
 
-  python -m paper_1107_4650_gb300.paper_klein2d [--precision fp64|fp32] [--steps 12000]
+  python -m paper_1107_4650_gb300.paper_klein2d [--precision fp64|fp32|fx64] [--steps 12000]
 
 Mesh 24576 x 8192 over x in [-15, 15], z in [-5, 5] a.u. (dx = 10/8192 a.u.), second-order splitting
 (dt = 2 dx / c = 1.78e-5 a.u.), 12000 steps to t = 0.214 a.u., zero boundary; step V(x) = V0/2 (1 + tanh(x/L))
@@ -52,7 +52,8 @@ def run(precision: str = "fp64", steps: int = 12000, x0: float = -6.0, stream=No
     del outer
     stream = stream if stream is not None else torch.cuda.Stream(device=dev)
     cfg = D.make_config((nx, 1, nz), dx=dx, x_min=(x_min, 0.0, z_min), flux_face=face, splitting=D.DIRAC_STRANG,
-                        precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64, stream=stream.cuda_stream, device=device)
+                        precision={"fp32": D.DIRAC_FP32, "fx64": D.DIRAC_FX64}.get(precision, D.DIRAC_FP64),
+                        stream=stream.cuda_stream, device=device)
     h = D.dirac_create_grid(cfg)
     try:
         D.dirac_set_potential(h, W.tanh_step(nx, dx, x_min, 0.0, V0, L), D.DIRAC_V_X_ONLY)
@@ -88,7 +89,7 @@ def run(precision: str = "fp64", steps: int = 12000, x0: float = -6.0, stream=No
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fx64"])
     ap.add_argument("--steps", type=int, default=12000)
     ap.add_argument("--x0", type=float, default=-6.0)
     args = ap.parse_args()

@@ -129,10 +129,11 @@ def test_3d_steps_per_launch_validation(lib):
 
 
 def test_fx64_validation(lib):
-    """DIRAC_FX64 runs first-order steps only, one or (2-D) two steps per launch."""
+    """DIRAC_FX64 runs first-order steps (one or, in 2-D, two per launch) and 2-D second-order steps (one)."""
     import paper_1107_4650_gb300 as D
     for n, kw in (((8, 8, 8), dict(ndim=3, steps_per_launch=2)), ((8, 8, 8), dict(ndim=3, splitting=D.DIRAC_STRANG)),
-                  ((16, 1, 16), dict(splitting=D.DIRAC_STRANG)),
+                  ((16, 1, 16), dict(splitting=D.DIRAC_STRANG, steps_per_launch=2)),
+                  ((16, 1, 16), dict(splitting=D.DIRAC_STRANG, steps_per_launch=1, points_per_lane=4)),
                   ((16, 1, 16), dict(char_shift=2)), ((16, 1, 16), dict(steps_per_launch=4)),
                   ((16, 1, 16), dict(steps_per_launch=2, points_per_lane=4)), ((16, 1, 16), dict(precision=3))):
         kw.setdefault("precision", D.DIRAC_FX64)

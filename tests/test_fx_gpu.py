@@ -209,3 +209,60 @@ def test_fx_3d_coulomb_within_1e12_of_fp64_oracle(D):
     assert err <= 1e-12
     assert F > 1e-3 and abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
     assert np.array_equal(q1, oracle.step_fx(q0, 1.0, C, DX, 150, V=V, ndim=3))
+
+
+@pytest.mark.parametrize("shape", [(70, 45), (130, 33), (5, 7), (1, 9)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("P", [1, 2])
+def test_fx_strang2d_bit_exact_against_fixed_point_oracle(D, shape, periodic, P):
+    """Second-order 2-D steps (x, z, phase, z, x as two pipelined levels) on the int64 state, bit for bit."""
+    nx, nz = shape
+    psi = W.random_state(nz, 1, nx, seed=nx * nz + P + 7)
+    V = np.random.default_rng(nx + P).uniform(-4e4, 4e4, nx)
+    S = oracle.fx_shift(psi)
+    q0 = oracle.fx_encode(psi, S)
+    want = oracle.step_strang2d_fx(q0, 1.0, C, DX, 5, V=V, periodic=periodic)
+    cfg = D.make_config((nx, 1, nz), precision=D.DIRAC_FX64, splitting=D.DIRAC_STRANG, points_per_lane=P,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state_fx(h, q0, S)
+        D.dirac_step(h, 5)
+        got, _ = _q_of(D, h, (nz, 1, nx))
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    assert info["plan"] == D.DIRAC_PLAN_STRANG_2D and info["points_per_lane"] == P
+    assert np.array_equal(got, want)
+
+
+def test_fx_strang2d_klein_within_1e12_of_fp64_oracle(D):
+    """The second-order Klein step at 384^2 for 1500 steps with the face flux (graphs, autotuned): decoded state
+    within relative L2 1e-12 of the FP64 Strang oracle, flux within 1e-12 relative, integer state equal to
+    the fixed-point oracle's."""
+    run = W.KleinRun(side=384, V0=2.5 * C * C, p0=0.6 * C, width=20 * DX, nsteps=1500, face=240)
+    psi0 = run.state()
+    V = run.potential()
+    x_min, z_min, _, _, face = run.geometry()
+    want, F = oracle.step_strang2d(psi0, 1.0, C, DX, run.nsteps, V=V, flux_face=face)
+    cfg = D.make_config((384, 1, 384), precision=D.DIRAC_FX64, splitting=D.DIRAC_STRANG, flux_face=face,
+                        x_min=(x_min, 0.0, z_min))
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi0)
+        q0, S = _q_of(D, h, (384, 1, 384))
+        D.dirac_autotune(h)
+        D.dirac_step(h, run.nsteps)
+        got = np.empty_like(psi0)
+        D.dirac_get_state(h, got)
+        q1, _ = _q_of(D, h, (384, 1, 384))
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    err = rel_l2(got, want)
+    print("FX64 Strang vs FP64 oracle after 1500 steps: rel L2 %.3e" % err)
+    assert err <= 1e-12
+    assert F > 0.01 and abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+    assert np.array_equal(q1, oracle.step_strang2d_fx(q0, 1.0, C, DX, run.nsteps, V=V))
