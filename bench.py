@@ -504,8 +504,11 @@ def main():
 
     # ---------------------------------------------------------------- 2-D second order and characteristic shifts
     if not args.no_2d_variants:
-        for vname, kw, per_step in (("fp64_strang2d", dict(splitting=D.DIRAC_STRANG), 2),
-                                    ("fp64_shift2", dict(char_shift=2), 2), ("fp64_shift4", dict(char_shift=4), 4)):
+        legs2 = [("fp64_strang2d", dict(splitting=D.DIRAC_STRANG), 2), ("fp64_shift2", dict(char_shift=2), 2),
+                 ("fp64_shift4", dict(char_shift=4), 4)]
+        if not args.no_fx64:
+            legs2.append(("fx64_strang2d", dict(splitting=D.DIRAC_STRANG, precision=D.DIRAC_FX64), 2))
+        for vname, kw, per_step in legs2:
             cfgv = D.make_config((args.side, 1, args.side), x_min=(x_min, 0.0, z_min), flux_face=face,
                                  stream=stream.cuda_stream, device=local, **kw)
             hv = D.dirac_create_grid(cfgv)
@@ -525,6 +528,16 @@ def main():
             D.dirac_destroy(hv)
             vv = ncell * nv * world / (tv / 1e3)
             instr = 80 if vname == "fp64_strang2d" else FP64_INSTR_PER_POINT_STEP_2D  # Strang: 4 sweeps + phase
+            if vname.startswith("fx64"):
+                variants[vname] = {
+                    "value": vv, "unit": "point-steps/s", "steps": nv, "ms_per_step": tv / nv,
+                    "physical_time_per_step_dx_over_c": per_step,
+                    "first_order_equivalent_point_steps_per_s": vv * per_step,
+                    "steps_per_launch": iv["steps_per_launch"], "points_per_lane": iv["points_per_lane"],
+                    "workload": "the 2048^2 Klein grid, second-order steps of 2 dx/c, 64-bit fixed-point storage",
+                    "hbm_frac": FP64_BYTES_PER_POINT_STEP * vv / world / 1e9 / hbm_peak,
+                    "speedup_vs_fp64": (vv / variants["fp64_strang2d"]["value"]) if "fp64_strang2d" in variants else None}
+                continue
             variants[vname] = {
                 "value": vv, "unit": "point-steps/s", "steps": nv, "ms_per_step": tv / nv,
                 "physical_time_per_step_dx_over_c": per_step, "first_order_equivalent_point_steps_per_s": vv * per_step,
