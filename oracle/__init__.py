@@ -60,8 +60,10 @@ def _load():
                                        ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
         lib.oracle_step_strang2d_fx.argtypes = [P, I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
+        lib.oracle_step_strang3d_fx.argtypes = lib.oracle_step_strang2d_fx.argtypes
         for f in (lib.oracle_sweep, lib.oracle_phase, lib.oracle_step, lib.oracle_observables,
-                  lib.oracle_step_strang2d, lib.oracle_step_strang3d, lib.oracle_step_fx, lib.oracle_step_strang2d_fx):
+                  lib.oracle_step_strang2d, lib.oracle_step_strang3d, lib.oracle_step_fx, lib.oracle_step_strang2d_fx,
+                  lib.oracle_step_strang3d_fx):
             f.restype = ctypes.c_int
         lib.oracle_set_absorber.argtypes = [P]
         lib.oracle_set_absorber.restype = None
@@ -247,13 +249,14 @@ def fx_decode(q, S: int) -> np.ndarray:
     return x.view(np.complex128).reshape(q.shape[:-1])
 
 
-def fx_shift(psi, ndim: int = 2) -> int:
-    """The fixed-point shift for a state: S = 60 - e in 2-D (59 - e in 3-D) where the discrete L2 norm
-    sqrt(sum |psi_c|^2) = m 2^e with m in [0.5, 1), so that norm 2^S < 2^60 (2^59); 0 for the zero state.
-    Each sweep with its 1/2 and the phase do not raise the norm, so a step's values stay below 2^62."""
+def fx_shift(psi, ndim: int = 2, strang: bool = False) -> int:
+    """The fixed-point shift for a state: S = 60 - e in 2-D (59 - e for 3-D first-order steps, 57 - e for 3-D
+    second-order steps) where the discrete L2 norm sqrt(sum |psi_c|^2) = m 2^e with m in [0.5, 1); 0 for the
+    zero state.  Each sweep with its 1/2 and the phase do not raise the norm, so a step's values (2^j times
+    it after j sweeps without the 1/2: j = 2, 3, 4 before the phase) stay below 2^62."""
     arr = _as_state(psi)
     A = float(np.sqrt(np.sum(arr.real ** 2 + arr.imag ** 2)))
-    top = 59 if ndim == 3 else 60
+    top = (57 if strang else 59) if ndim == 3 else 60
     return top - (np.frexp(A)[1] if A > 0 else top)
 
 
@@ -292,6 +295,23 @@ def step_strang2d_fx(q, m: float, c: float, dx: float, nsteps: int, V=None, peri
                                              layout, int(nsteps))
     if rc != 0:
         raise MemoryError("oracle_step_strang2d_fx")
+    return out
+
+
+def step_strang3d_fx(q, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False):
+    """nsteps second-order 3-D steps (Sec. 2.4: A(1) B(2) A(1) C(2) D C(2) A(1) B(2) A(1), dt = 4 dx / c) on a
+    fixed-point state q (int64, (nz, ny, nx, 4, 2)), the eight halves (1/256) in the phase coefficients
+    (oracle_step_strang3d_fx)."""
+    out = np.ascontiguousarray(q, dtype=np.int64).copy()
+    if out.ndim != 5 or out.shape[3:] != (4, 2):
+        raise ValueError("q must have shape (nz, ny, nx, 4, 2)")
+    nz, ny, nx = out.shape[:3]
+    Varr, layout = _potential(V, np.zeros((nz, ny, nx, 4), complex))
+    rc = _load().oracle_step_strang3d_fx(out.ctypes.data, I64_3(nx, ny, nz), int(bool(periodic)), float(m),
+                                         float(c), float(dx), None if Varr is None else Varr.ctypes.data, layout,
+                                         int(nsteps))
+    if rc != 0:
+        raise MemoryError("oracle_step_strang3d_fx")
     return out
 
 

@@ -331,13 +331,13 @@ static int64_t q_round62(__int128 v) { return (int64_t)((v + ((__int128)1 << 61)
 
 static int64_t q_coef(double p, double halves) { return (int64_t)nearbyint(ldexp(p * halves, 62)); }
 
-/* x sweep (Eq. sol_dis_1 without the 1/2): in -> out */
-static void fx_sweep_x(const qcplx *in, qcplx *out, const int64_t n[3], int periodic) {
+/* x sweep (Eq. sol_dis_1 without the 1/2), characteristics moved sh cells: in -> out */
+static void fx_sweep_x(const qcplx *in, qcplx *out, const int64_t n[3], int periodic, int64_t sh) {
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n[2]; ++k)
         for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
-                const qcplx *L = qcell(in, n, periodic, i - 1, j, k), *R = qcell(in, n, periodic, i + 1, j, k);
+                const qcplx *L = qcell(in, n, periodic, i - sh, j, k), *R = qcell(in, n, periodic, i + sh, j, k);
                 if (!L) L = QZERO4;
                 if (!R) R = QZERO4;
                 qcplx *o = out + ((k * n[1] + j) * n[0] + i) * 4;
@@ -348,13 +348,13 @@ static void fx_sweep_x(const qcplx *in, qcplx *out, const int64_t n[3], int peri
             }
 }
 
-/* y sweep (Eq. sol_dis_2 without the 1/2; i b = (-b.im, b.re)): in -> out */
-static void fx_sweep_y(const qcplx *in, qcplx *out, const int64_t n[3], int periodic) {
+/* y sweep (Eq. sol_dis_2 without the 1/2; i b = (-b.im, b.re)), sh cells: in -> out */
+static void fx_sweep_y(const qcplx *in, qcplx *out, const int64_t n[3], int periodic, int64_t sh) {
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n[2]; ++k)
         for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
-                const qcplx *L = qcell(in, n, periodic, i, j - 1, k), *R = qcell(in, n, periodic, i, j + 1, k);
+                const qcplx *L = qcell(in, n, periodic, i, j - sh, k), *R = qcell(in, n, periodic, i, j + sh, k);
                 if (!L) L = QZERO4;
                 if (!R) R = QZERO4;
                 qcplx *o = out + ((k * n[1] + j) * n[0] + i) * 4;
@@ -369,13 +369,13 @@ static void fx_sweep_y(const qcplx *in, qcplx *out, const int64_t n[3], int peri
             }
 }
 
-/* z sweep (Eq. sol_dis_3 without the 1/2): in -> out */
-static void fx_sweep_z(const qcplx *in, qcplx *out, const int64_t n[3], int periodic) {
+/* z sweep (Eq. sol_dis_3 without the 1/2), sh cells: in -> out */
+static void fx_sweep_z(const qcplx *in, qcplx *out, const int64_t n[3], int periodic, int64_t sh) {
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n[2]; ++k)
         for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
-                const qcplx *L = qcell(in, n, periodic, i, j, k - 1), *R = qcell(in, n, periodic, i, j, k + 1);
+                const qcplx *L = qcell(in, n, periodic, i, j, k - sh), *R = qcell(in, n, periodic, i, j, k + sh);
                 if (!L) L = QZERO4;
                 if (!R) R = QZERO4;
                 qcplx *z = out + ((k * n[1] + j) * n[0] + i) * 4;
@@ -429,12 +429,12 @@ int oracle_step_fx(int64_t *q_d, const int64_t n[3], int ndim, int periodic, dou
     }
     const double halves = ndim == 3 ? 0.125 : 0.25;
     for (int64_t s = 0; s < nsteps; ++s) {
-        fx_sweep_x(q, t, n, periodic);
+        fx_sweep_x(q, t, n, periodic, 1);
         if (ndim == 3) {
-            fx_sweep_y(t, u, n, periodic);
+            fx_sweep_y(t, u, n, periodic, 1);
             memcpy(t, u, (size_t)total * 4 * sizeof(qcplx));
         }
-        fx_sweep_z(t, q, n, periodic);
+        fx_sweep_z(t, q, n, periodic, 1);
         fx_phase(q, n, m, c, dx / c, V, layout, halves);
     }
     free(t);
@@ -453,11 +453,35 @@ int oracle_step_strang2d_fx(int64_t *q_d, const int64_t n[3], int periodic, doub
     qcplx *t = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
     if (!t) return -1;
     for (int64_t s = 0; s < nsteps; ++s) {
-        fx_sweep_x(q, t, n, periodic);
-        fx_sweep_z(t, q, n, periodic);
+        fx_sweep_x(q, t, n, periodic, 1);
+        fx_sweep_z(t, q, n, periodic, 1);
         fx_phase(q, n, m, c, 2.0 * dx / c, V, layout, 0.0625);
-        fx_sweep_z(q, t, n, periodic);
-        fx_sweep_x(t, q, n, periodic);
+        fx_sweep_z(q, t, n, periodic, 1);
+        fx_sweep_x(t, q, n, periodic, 1);
+    }
+    free(t);
+    return 0;
+}
+
+/* nsteps second-order 3-D steps (Sec. 2.4): A(1) B(2) A(1) C(2) D C(2) A(1) B(2) A(1), the cells moved
+ * by each sweep in parentheses, dt = 4 dx / c, the eight sweeps' halves (1/256) in the phase coefficients.
+ * The state entering the phase is 16 times the true one and leaves it at 1/16 (rounded at that scale). */
+int oracle_step_strang3d_fx(int64_t *q_d, const int64_t n[3], int periodic, double m, double c, double dx,
+                            const double *V, int layout, int64_t nsteps) {
+    qcplx *q = (qcplx *)q_d;
+    const int64_t total = n[0] * n[1] * n[2];
+    qcplx *t = (qcplx *)malloc((size_t)total * 4 * sizeof(qcplx));
+    if (!t) return -1;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        fx_sweep_x(q, t, n, periodic, 1);
+        fx_sweep_y(t, q, n, periodic, 2);
+        fx_sweep_x(q, t, n, periodic, 1);
+        fx_sweep_z(t, q, n, periodic, 2);
+        fx_phase(q, n, m, c, 4.0 * dx / c, V, layout, 1.0 / 256.0);
+        fx_sweep_z(q, t, n, periodic, 2);
+        fx_sweep_x(t, q, n, periodic, 1);
+        fx_sweep_y(q, t, n, periodic, 2);
+        fx_sweep_x(t, q, n, periodic, 1);
     }
     free(t);
     return 0;

@@ -47,14 +47,16 @@ MUTANTS = {
                         "z[3].re = (L[1].re - L[3].re) + (R[1].re + R[3].re);"),
     "fx_coefficient_scale": ("return (int64_t)nearbyint(ldexp(p * halves, 62));",
                              "return (int64_t)nearbyint(ldexp(p * halves, 61));"),
-    "fx_x_sweep_neighbour": ("const qcplx *L = qcell(in, n, periodic, i - 1, j, k), *R = qcell(in, n, periodic, i + 1, j, k);",
-                             "const qcplx *L = qcell(in, n, periodic, i - 1, j, k), *R = qcell(in, n, periodic, i - 1, j, k);"),
+    "fx_x_sweep_neighbour": ("const qcplx *L = qcell(in, n, periodic, i - sh, j, k), *R = qcell(in, n, periodic, i + sh, j, k);",
+                             "const qcplx *L = qcell(in, n, periodic, i - sh, j, k), *R = qcell(in, n, periodic, i - sh, j, k);"),
     "fx_y_sweep_i_sign": ("o[0].re = (L[0].re + L[3].im) + (R[0].re - R[3].im);",
                           "o[0].re = (L[0].re - L[3].im) + (R[0].re - R[3].im);"),
     "fx_3d_halves": ("const double halves = ndim == 3 ? 0.125 : 0.25;", "const double halves = 0.25;"),
     "fx_strang_halves": ("fx_phase(q, n, m, c, 2.0 * dx / c, V, layout, 0.0625);", "fx_phase(q, n, m, c, 2.0 * dx / c, V, layout, 0.125);"),
-    "fx_strang_order": ("        fx_sweep_z(q, t, n, periodic);\n        fx_sweep_x(t, q, n, periodic);\n    }\n    free(t);\n    return 0;",
-                        "        fx_sweep_x(q, t, n, periodic);\n        fx_sweep_z(t, q, n, periodic);\n    }\n    free(t);\n    return 0;"),
+    "fx_strang_order": ("        fx_sweep_z(q, t, n, periodic, 1);\n        fx_sweep_x(t, q, n, periodic, 1);\n    }",
+                        "        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 1);\n    }"),
+    "fx_strang3d_shift": ("        fx_sweep_y(t, q, n, periodic, 2);\n        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 2);",
+                          "        fx_sweep_y(t, q, n, periodic, 1);\n        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 2);"),
 }
 
 
@@ -86,6 +88,8 @@ def _build_mutant(tmp_path, name, old, new):
     lib.oracle_step_strang2d_fx.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
     lib.oracle_step_strang2d_fx.restype = ctypes.c_int
+    lib.oracle_step_strang3d_fx.argtypes = lib.oracle_step_strang2d_fx.argtypes
+    lib.oracle_step_strang3d_fx.restype = ctypes.c_int
     return lib
 
 
@@ -178,6 +182,17 @@ def _pins_pass():
     Vr = np.random.default_rng(101).uniform(-3e4, 3e4, 11)
     want, _ = oracle.step_strang2d(psi, 1.0, C, DX, 5, V=Vr)
     ok &= A.rel_l2(oracle.fx_decode(oracle.step_strang2d_fx(oracle.fx_encode(psi, S), 1.0, C, DX, 5, V=Vr), S), want) < 1e-13
+    # fixed-point second-order 3-D step: exact where FP64 is exact (7 rows: a two-cell shift does not wrap onto
+    # itself), and within 1e-13 of the FP64 3-D Strang step
+    q = rng.integers(-1000, 1000, size=(6, 7, 5, 4, 2), dtype=np.int64) * 65536
+    want, _ = oracle.step_strang3d(oracle.fx_decode(q, 40), 0.0, C, DX, 2, periodic=True)
+    ok &= np.array_equal(oracle.step_strang3d_fx(q, 0.0, C, DX, 2, periodic=True), oracle.fx_encode(want, 40))
+    psi = W.random_state(6, 7, 5, seed=102)
+    S = oracle.fx_shift(psi, 3, strang=True)
+    Vr = np.random.default_rng(103).uniform(-3e4, 3e4, 210)
+    want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 3, V=Vr, periodic=True)
+    got = oracle.fx_decode(oracle.step_strang3d_fx(oracle.fx_encode(psi, S), 1.0, C, DX, 3, V=Vr, periodic=True), S)
+    ok &= A.rel_l2(got, want) < 1e-13
     return bool(ok)
 
 

@@ -872,3 +872,27 @@ def test_fx_strang2d_matches_fp64_oracle(oracle_mod, periodic):
     q = oracle.step_strang2d_fx(oracle.fx_encode(psi0, S), 1.0, C, W.DX_DEFAULT, run.nsteps, V=V, periodic=periodic)
     err = A.rel_l2(oracle.fx_decode(q, S), want)
     assert 0.0 < err < 1e-12, err
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_fx_strang3d_exact_where_fp64_is_exact(oracle_mod, periodic):
+    """Second-order 3-D step in fixed point: m = 0, V = 0 and values that are multiples of 256^2 make two steps
+    exact in both evaluations (the phase divides by 256 exactly), so they agree exactly."""
+    rng = np.random.default_rng(74)
+    q = rng.integers(-1000, 1000, size=(6, 7, 5, 4, 2), dtype=np.int64) * 65536
+    want, _ = oracle.step_strang3d(oracle.fx_decode(q, 40), 0.0, C, W.DX_DEFAULT, 2, periodic=periodic)
+    got = oracle.step_strang3d_fx(q, 0.0, C, W.DX_DEFAULT, 2, periodic=periodic)
+    assert np.array_equal(got, oracle.fx_encode(want, 40))
+
+
+def test_fx_strang3d_matches_fp64_oracle(oracle_mod):
+    """A 3-D packet in the soft-Coulomb potential (24^3) for 30 second-order steps: the fixed-point evaluation
+    within relative L2 1e-12 of the FP64 Strang oracle."""
+    n, dx = 24, W.DX_DEFAULT
+    psi = W.gaussian_packet(n, n, dx, -n * dx / 2, -n * dx / 2, 3 * dx, 0.0, 4 * dx, 0.3 * C, ny=n, y_min=-n * dx / 2)
+    V = W.soft_coulomb_3d(n, dx, 10.0, 2 * dx).reshape(-1)
+    S = oracle.fx_shift(psi, 3, strang=True)
+    want, _ = oracle.step_strang3d(psi, 1.0, C, dx, 30, V=V)
+    got = oracle.fx_decode(oracle.step_strang3d_fx(oracle.fx_encode(psi, S), 1.0, C, dx, 30, V=V), S)
+    err = A.rel_l2(got, want)
+    assert 0.0 < err < 1e-12, err
