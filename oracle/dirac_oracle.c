@@ -464,8 +464,9 @@ int oracle_step_strang2d_fx(int64_t *q_d, const int64_t n[3], int periodic, doub
 }
 
 /* nsteps second-order 3-D steps (Sec. 2.4): A(1) B(2) A(1) C(2) D C(2) A(1) B(2) A(1), the cells moved
- * by each sweep in parentheses, dt = 4 dx / c, the eight sweeps' halves (1/256) in the phase coefficients.
- * The state entering the phase is 16 times the true one and leaves it at 1/16 (rounded at that scale). */
+ * by each sweep in parentheses, dt = 4 dx / c.  The state entering the phase is 16 times the true one; the
+ * phase coefficients carry those four halves (1/16), so its output is the true state, rounded at that
+ * scale; the last four sweeps leave 16 times it, divided back by 16 with rounding to nearest (halves up). */
 int oracle_step_strang3d_fx(int64_t *q_d, const int64_t n[3], int periodic, double m, double c, double dx,
                             const double *V, int layout, int64_t nsteps) {
     qcplx *q = (qcplx *)q_d;
@@ -477,11 +478,12 @@ int oracle_step_strang3d_fx(int64_t *q_d, const int64_t n[3], int periodic, doub
         fx_sweep_y(t, q, n, periodic, 2);
         fx_sweep_x(q, t, n, periodic, 1);
         fx_sweep_z(t, q, n, periodic, 2);
-        fx_phase(q, n, m, c, 4.0 * dx / c, V, layout, 1.0 / 256.0);
+        fx_phase(q, n, m, c, 4.0 * dx / c, V, layout, 1.0 / 16.0);
         fx_sweep_z(q, t, n, periodic, 2);
         fx_sweep_x(t, q, n, periodic, 1);
         fx_sweep_y(q, t, n, periodic, 2);
         fx_sweep_x(t, q, n, periodic, 1);
+        for (int64_t e = 0; e < total * 8; ++e) q_d[e] = (q_d[e] + 8) >> 4;
     }
     free(t);
     return 0;

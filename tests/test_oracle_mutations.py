@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_1107_4650_gb300 import workloads as W
 from tests import dirac_algebra as A
-from tests.test_oracle_pins import _fx_step_bigint
+from tests.test_oracle_pins import _fx_step_bigint, _fx_strang3d_free_periodic
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "dirac_oracle.c")
 C = W.C_AU
@@ -55,6 +55,7 @@ MUTANTS = {
     "fx_strang_halves": ("fx_phase(q, n, m, c, 2.0 * dx / c, V, layout, 0.0625);", "fx_phase(q, n, m, c, 2.0 * dx / c, V, layout, 0.125);"),
     "fx_strang_order": ("        fx_sweep_z(q, t, n, periodic, 1);\n        fx_sweep_x(t, q, n, periodic, 1);\n    }",
                         "        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 1);\n    }"),
+    "fx_strang3d_final_rounding": ("q_d[e] = (q_d[e] + 8) >> 4;", "q_d[e] = (q_d[e] + 0) >> 4;"),
     "fx_strang3d_shift": ("        fx_sweep_y(t, q, n, periodic, 2);\n        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 2);",
                           "        fx_sweep_y(t, q, n, periodic, 1);\n        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 2);"),
 }
@@ -193,6 +194,8 @@ def _pins_pass():
     want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 3, V=Vr, periodic=True)
     got = oracle.fx_decode(oracle.step_strang3d_fx(oracle.fx_encode(psi, S), 1.0, C, DX, 3, V=Vr, periodic=True), S)
     ok &= A.rel_l2(got, want) < 1e-13
+    q = rng.integers(-(1 << 40), 1 << 40, size=(6, 7, 5, 4, 2), dtype=np.int64)
+    ok &= np.array_equal(oracle.step_strang3d_fx(q, 0.0, C, DX, 2, periodic=True), _fx_strang3d_free_periodic(q, 2))
     return bool(ok)
 
 

@@ -896,3 +896,55 @@ def test_fx_strang3d_matches_fp64_oracle(oracle_mod):
     got = oracle.fx_decode(oracle.step_strang3d_fx(oracle.fx_encode(psi, S), 1.0, C, dx, 30, V=V), S)
     err = A.rel_l2(got, want)
     assert 0.0 < err < 1e-12, err
+
+
+def _fx_strang3d_free_periodic(q, nsteps):
+    """The fixed-point second-order 3-D step at m = 0, V = 0 on a periodic grid, in numpy int64 (an independent
+    restatement): the phase is then the identity with the four halves, i.e. round(z / 16), and the last sweep
+    divides by 16 with the same rounding (floor((z + 8) / 16)).  q: (nz, ny, nx, 4, 2)."""
+    q = q.astype(np.int64).copy()
+    re, im = 0, 1
+
+    def sweep(v, axis, sh):
+        ax = {0: 2, 1: 1, 2: 0}[axis]  # array axis of x, y, z
+        L = np.roll(v, sh, axis=ax)     # v at i - sh
+        R = np.roll(v, -sh, axis=ax)    # v at i + sh
+        o = np.empty_like(v)
+        if axis == 0:
+            o[..., 0, :] = (L[..., 0, :] + L[..., 3, :]) + (R[..., 0, :] - R[..., 3, :])
+            o[..., 1, :] = (L[..., 1, :] + L[..., 2, :]) + (R[..., 1, :] - R[..., 2, :])
+            o[..., 2, :] = (L[..., 1, :] + L[..., 2, :]) + (R[..., 2, :] - R[..., 1, :])
+            o[..., 3, :] = (L[..., 0, :] + L[..., 3, :]) + (R[..., 3, :] - R[..., 0, :])
+        elif axis == 2:
+            o[..., 0, :] = (L[..., 0, :] + L[..., 2, :]) + (R[..., 0, :] - R[..., 2, :])
+            o[..., 1, :] = (L[..., 1, :] - L[..., 3, :]) + (R[..., 1, :] + R[..., 3, :])
+            o[..., 2, :] = (L[..., 0, :] + L[..., 2, :]) + (R[..., 2, :] - R[..., 0, :])
+            o[..., 3, :] = (L[..., 3, :] - L[..., 1, :]) + (R[..., 1, :] + R[..., 3, :])
+        else:
+            # (a - i b) = (a.re + b.im, a.im - b.re); (a + i b) = (a.re - b.im, a.im + b.re)
+            def minus_i(a, b):
+                return np.stack([a[..., re] + b[..., im], a[..., im] - b[..., re]], axis=-1)
+
+            def plus_i(a, b):
+                return np.stack([a[..., re] - b[..., im], a[..., im] + b[..., re]], axis=-1)
+            o[..., 0, :] = minus_i(L[..., 0, :], L[..., 3, :]) + plus_i(R[..., 0, :], R[..., 3, :])
+            o[..., 1, :] = plus_i(L[..., 1, :], L[..., 2, :]) + minus_i(R[..., 1, :], R[..., 2, :])
+            o[..., 2, :] = minus_i(L[..., 2, :], L[..., 1, :]) + plus_i(R[..., 2, :], R[..., 1, :])
+            o[..., 3, :] = plus_i(L[..., 3, :], L[..., 0, :]) + minus_i(R[..., 3, :], R[..., 0, :])
+        return o
+
+    for _ in range(nsteps):
+        q = sweep(sweep(sweep(sweep(q, 0, 1), 1, 2), 0, 1), 2, 2)
+        q = (q + 8) >> 4
+        q = sweep(sweep(sweep(sweep(q, 2, 2), 0, 1), 1, 2), 0, 1)
+        q = (q + 8) >> 4
+    return q
+
+
+def test_fx_strang3d_rounding_against_numpy_restatement(oracle_mod):
+    """m = 0, V = 0, periodic: oracle_step_strang3d_fx equals an independent numpy int64 restatement bit for bit
+    on values that are not multiples of 16, so both roundings (the phase's and the last sweep's) are pinned."""
+    rng = np.random.default_rng(75)
+    q = rng.integers(-(1 << 40), 1 << 40, size=(6, 7, 5, 4, 2), dtype=np.int64)
+    got = oracle.step_strang3d_fx(q, 0.0, C, W.DX_DEFAULT, 2, periodic=True)
+    assert np.array_equal(got, _fx_strang3d_free_periodic(q, 2))
