@@ -555,15 +555,13 @@ def main():
         psi3 = W.gaussian_packet(n3, n3, dx3, -n3 * dx3 / 2, -n3 * dx3 / 2, 32 * dx3, 0.0, 16 * dx3, 0.0, ny=n3,
                                  y_min=-n3 * dx3 / 2)
         V3 = W.soft_coulomb_3d(n3, dx3, 10.0, 2 * dx3).reshape(-1)
-        ref3 = None  # the FP64 first-order state after the leg (warm-up + timed steps): the fixed-point reference
+        ref3 = {}  # the FP64 states after each leg (warm-up + timed steps): the fixed-point references
         precs3 = [(D.DIRAC_FP64, "fp64"), (D.DIRAC_FP32, "fp32")] + ([] if args.no_fx64 else [(D.DIRAC_FX64, "fx64")])
         for prec, pname in precs3:
             wide = prec != D.DIRAC_FP32  # complex128 in (FP64 and fixed point)
             dev3 = torch.from_numpy(psi3.astype(np.complex128 if wide else np.complex64)
                                     .view(np.float64 if wide else np.float32)).to(f"cuda:{local}")
-            splits = ((D.DIRAC_LIE, "first_order", 1),) if prec == D.DIRAC_FX64 else \
-                ((D.DIRAC_LIE, "first_order", 1), (D.DIRAC_STRANG, "strang", 4))
-            for split, sname, per_step in splits:
+            for split, sname, per_step in ((D.DIRAC_LIE, "first_order", 1), (D.DIRAC_STRANG, "strang", 4)):
                 cfg3 = D.make_config((n3, n3, n3), ndim=3, precision=prec, splitting=split, stream=stream.cuda_stream,
                                      device=local)
                 h3 = D.dirac_create_grid(cfg3)
@@ -582,15 +580,16 @@ def main():
                 t3 = max_over_ranks(e30.elapsed_time(e31))
                 o3 = D.dirac_observables(h3)
                 rel3 = None
-                if split == D.DIRAC_LIE and prec != D.DIRAC_FP32:
+                if prec != D.DIRAC_FP32:
                     fin = torch.empty_like(dev3)
                     D.dirac_get_state(h3, fin)
                     stream.synchronize()  # the copy runs on the grid's stream; torch reads on its own
                     if prec == D.DIRAC_FP64:
-                        ref3 = fin
-                    elif ref3 is not None:
-                        rel3 = float(torch.linalg.vector_norm(fin - ref3) / torch.linalg.vector_norm(ref3))
-                        del fin
+                        ref3[split] = fin
+                    elif split in ref3:
+                        ref = ref3.pop(split)
+                        rel3 = float(torch.linalg.vector_norm(fin - ref) / torch.linalg.vector_norm(ref))
+                        del fin, ref
                 D.dirac_destroy(h3)
                 v3 = n3 ** 3 * n_steps3 * world / (t3 / 1e3)
                 instr = 64 if split == D.DIRAC_LIE else 144
@@ -610,15 +609,17 @@ def main():
                     entry["fp64_instr_per_point_step"] = instr
                     entry["frac_of_measured_fp64_issue"] = instr * v3 / world / 1e12 / FP64_ISSUE_PEAK_MEASURED
                 elif prec == D.DIRAC_FX64:
-                    # algorithmic: the state read and written once plus the per-cell int64 table (32 B); the
-                    # two passes move 2 x 128 + 32 B
+                    # algorithmic: the state read and written once plus the per-cell int64 table (32 B); first
+                    # order moves 2 x 128 + 32 B in its two passes, second order 8 x 128 + 32 B in its eight
+                    # single sweeps
+                    moved = 288 if split == D.DIRAC_LIE else 8 * 128 + 32
                     entry["bytes_per_point_step"] = 160
                     entry["hbm_frac"] = 160 * v3 / world / 1e9 / hbm_peak
-                    entry["two_pass_bytes_per_point_step"] = 288
-                    entry["hbm_frac_of_pass_bytes"] = 288 * v3 / world / 1e9 / hbm_peak
+                    entry["pass_bytes_per_point_step"] = moved
+                    entry["hbm_frac_of_pass_bytes"] = moved * v3 / world / 1e9 / hbm_peak
                     entry["rel_l2_vs_fp64_after_%d_steps" % (2 * n_steps3)] = rel3
-                    entry["speedup_vs_fp64"] = (v3 / variants["fp64_3d_first_order"]["value"]
-                                                if "fp64_3d_first_order" in variants else None)
+                    ref_name = "fp64_3d_%s" % sname
+                    entry["speedup_vs_fp64"] = (v3 / variants[ref_name]["value"]) if ref_name in variants else None
                     entry["workload"] += ", 64-bit fixed-point storage"
                 else:
                     # second order: the unfused basis is eight single sweeps (8 x 64 B + the 16 B table); a run

@@ -46,11 +46,12 @@ typedef enum {
 } dirac_status;
 
 /* storage precision.  DIRAC_FX64: 64-bit fixed point, q = round(psi 2^S) per real component in int64, for
- * first-order steps (2-D: the fused step kernel, k = 1 or 2; 3-D: the x-y pass + z/phase pass) and 2-D
- * second-order steps (one per launch): the sweeps' additions are exact and each step rounds once, in the
- * phase (a 128-bit product with the coefficients held as round(p 2^62)).  dirac_set_state picks S from
- * the state's discrete norm (dirac_info.fx_shift); states go in and out as complex128.  No vector
- * potential, 3-D second-order steps or char_shift > 1. */
+ * first-order steps (2-D: the fused step kernel, k = 1 or 2; 3-D: the x-y pass + z/phase pass) and
+ * second-order steps (2-D: one per launch; 3-D: eight single sweeps, the phase carrying the first four
+ * halves and the last sweep dividing by 16 with rounding): the sweeps' additions are exact and each step
+ * rounds once (twice in 3-D second order), in the phase (a 128-bit product with the coefficients held as
+ * round(p 2^62)).  dirac_set_state picks S from the state's discrete norm (dirac_info.fx_shift); states go
+ * in and out as complex128.  No vector potential or char_shift > 1. */
 enum { DIRAC_FP64 = 0, DIRAC_FP32 = 1, DIRAC_FX64 = 2 };
 enum { DIRAC_BC_ZERO = 0, DIRAC_BC_PERIODIC = 1 };    /* boundary */
 enum { DIRAC_V_NONE = 0, DIRAC_V_X_ONLY = 1, DIRAC_V_FULL = 2 }; /* potential layout */

@@ -3,14 +3,21 @@
 
 namespace dirac {
 
+// the phase-matrix variant exists for floating-point states only
+template <typename T> static void launch_axis_field(const AxisArgs &a, int blocks, cudaStream_t s) {
+    axis_kernel<T, 2, true, true><<<blocks, 256, 0, s>>>(a);
+}
+template <> void launch_axis_field<long long>(const AxisArgs &, int, cudaStream_t) {}
+
 template <typename T>
 static cudaError_t launch_axis_t(const AxisArgs &a, int axis, int phase, int blocks, cudaStream_t s) {
     const bool field = a.ucoef != nullptr && a.ucoef_n > 0;
+    if (sizeof(T) == 8 && (T)0.5 == (T)0 && field) return cudaErrorInvalidValue;  // fixed point: no phase matrix
     if (axis == 0 && !phase) axis_kernel<T, 0, false, false><<<blocks, 256, 0, s>>>(a);
     else if (axis == 1 && !phase) axis_kernel<T, 1, false, false><<<blocks, 256, 0, s>>>(a);
     else if (axis == 2 && !phase) axis_kernel<T, 2, false, false><<<blocks, 256, 0, s>>>(a);
     else if (axis == 2 && phase && !field) axis_kernel<T, 2, true, false><<<blocks, 256, 0, s>>>(a);
-    else if (axis == 2 && phase && field) axis_kernel<T, 2, true, true><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 2 && phase && field) launch_axis_field<T>(a, blocks, s);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -18,8 +25,9 @@ static cudaError_t launch_axis_t(const AxisArgs &a, int axis, int phase, int blo
 cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz, int axis,
                         int64_t shift, int periodic, int full_table, int phase, int64_t flux_face, double fscale,
                         double vol, double *flux_part, double *flux_cum, unsigned *ticket, const double *ucoef,
-                        int64_t ucoef_n, int64_t step0, int fp32, int blocks, cudaStream_t s) {
+                        int64_t ucoef_n, int64_t step0, int precision, int rshift, int blocks, cudaStream_t s) {
     AxisArgs a{};
+    a.rshift = rshift;
     a.ucoef = ucoef;
     a.ucoef_n = ucoef_n;
     a.step0 = step0;
@@ -38,7 +46,9 @@ cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx
     a.flux_part = flux_part;
     a.flux_cum = flux_cum;
     a.ticket = ticket;
-    return fp32 ? launch_axis_t<float>(a, axis, phase, blocks, s) : launch_axis_t<double>(a, axis, phase, blocks, s);
+    if (precision == 1) return launch_axis_t<float>(a, axis, phase, blocks, s);
+    if (precision == 2) return launch_axis_t<long long>(a, axis, phase, blocks, s);
+    return launch_axis_t<double>(a, axis, phase, blocks, s);
 }
 
 }  // namespace dirac

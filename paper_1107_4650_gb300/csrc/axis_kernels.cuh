@@ -37,7 +37,17 @@ struct AxisArgs {
     // uniform vector potential (phase epilogue only): 12 doubles of U entries per step, this launch's step
     const double *ucoef;
     int64_t ucoef_n, step0;
+    // fixed-point states: the output divided by 2^rshift, rounded to nearest (halves up); 0 = none
+    int rshift;
 };
+
+// Fixed point: o / 2^r rounded to nearest, halves upward (floating-point states never ask for it).
+template <typename T> __device__ __forceinline__ void round_shift(Cx<T> (&)[4], int) {}
+template <> __device__ __forceinline__ void round_shift<long long>(Cx<long long> (&o)[4], int r) {
+    const long long half = 1ll << (r - 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = Cx<long long>{(o[q].re + half) >> r, (o[q].im + half) >> r};
+}
 
 template <typename T, int AXIS, bool PHASE, bool FIELD>
 __global__ void __launch_bounds__(256) axis_kernel(const AxisArgs a) {
@@ -135,6 +145,7 @@ __global__ void __launch_bounds__(256) axis_kernel(const AxisArgs a) {
                 o[3] = cmulp(o[3], pd);
             }
         }
+        if (a.rshift > 0) round_shift(o, a.rshift);
         store_pt(out + c * 8, o);
     }
     if (AXIS == 0 && a.flux_face >= 0) {

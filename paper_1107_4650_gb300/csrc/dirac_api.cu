@@ -112,6 +112,8 @@ bool strang(const dirac_grid *g) { return g->cfg.splitting == DIRAC_STRANG; }
 // Power-of-two scale the phase coefficients carry for the sweeps' 1/2 factors: 1/4 (2-D), 1/8 (3-D),
 // 1/16 (2-D Strang: four sweeps per step), 1/256 (3-D Strang: eight sweeps per step).
 double scale_of(const dirac_grid *g) {
+    // fixed-point 3-D second-order steps: the phase carries the first four halves, the last sweep the rest
+    if (strang(g) && ndim_of(g) == 3 && g->fx) return 0.0625;
     if (strang(g)) return ndim_of(g) == 3 ? 1.0 / 256.0 : 0.0625;
     return ndim_of(g) == 3 ? 0.125 : 0.25;
 }
@@ -363,15 +365,20 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
         // four x sweeps is 1, 4, 1/8 and 1/2 times the true state (flux scale 1/2 over its square).
         static const int axes[8] = {0, 1, 0, 2, 2, 0, 1, 0};
         static const double fscale[8] = {0.5, 0, 0.5 / 16.0, 0, 0, 0.5 * 64.0, 0, 0.5 * 4.0};
+        // fixed point: the phase carries only the first four halves (1/16), so the state entering the last
+        // two x sweeps is 2 and 8 times the true one, and the last sweep divides by 16 with rounding
+        static const double fscale_fx[8] = {0.5, 0, 0.5 / 16.0, 0, 0, 0.5 / 4.0, 0, 0.5 / 64.0};
         const int blocks = axis_blocks(g);
         int par = parity;
         for (int q = 0; q < 8; ++q) {
             const int ax = axes[q];
             cudaError_t e = launch_axis(g->psi[par], g->psi[par ^ 1], g->table, g->cfg.n[0], g->cfg.n[1], g->cfg.n[2], ax,
                                         ax == 0 ? 1 : 2, a.periodic, g->table_full, q == 3 ? 1 : 0,
-                                        ax == 0 ? a.flux_face : -1, fscale[q], a.vol, g->flux_part, g->flux_dev,
-                                        g->ticket, q == 3 ? a.ucoef : nullptr, q == 3 ? a.ucoef_n : 0, step0,
-                                        g->fp32, blocks, s);
+                                        ax == 0 ? a.flux_face : -1, (g->fx ? fscale_fx[q] : fscale[q]) * a.flux_unit,
+                                        a.vol, g->flux_part, g->flux_dev, g->ticket, q == 3 ? a.ucoef : nullptr,
+                                        q == 3 ? a.ucoef_n : 0, step0,
+                                        g->fx ? DIRAC_FX64 : (g->fp32 ? DIRAC_FP32 : DIRAC_FP64),
+                                        (g->fx && q == 7) ? 4 : 0, blocks, s);
             if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order sweep launch");
             g->launches++;
             par ^= 1;
@@ -619,7 +626,7 @@ dirac_status fx_load_state(dirac_grid *g, const void *psi, int on_device) {
     if (!std::isfinite(sumsq)) return fail(g, DIRAC_ERR_NONFINITE, "dirac_set_state: state holds NaN or Inf");
     int e = 0;
     if (sumsq > 0) std::frexp(std::sqrt(sumsq), &e);
-    g->fx_shift = (ndim_of(g) == 3 ? 59 : 60) - e;
+    g->fx_shift = (ndim_of(g) == 3 ? (strang(g) ? 57 : 59) : 60) - e;
     CK(g, launch_fx_encode(tmp, static_cast<long long *>(g->psi[g->cur]), g->ncells * 8, g->fx_shift, g->stream));
     return DIRAC_OK;
 }
@@ -789,12 +796,15 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->precision != DIRAC_FP64 && cfg->precision != DIRAC_FP32 && cfg->precision != DIRAC_FX64)
         return fail(nullptr, DIRAC_ERR_ARG, "precision must be DIRAC_FP64, DIRAC_FP32 or DIRAC_FX64");
     if (cfg->precision == DIRAC_FX64) {
-        if ((cfg->splitting != DIRAC_LIE && !(cfg->splitting == DIRAC_STRANG && cfg->ndim == 2)) || cfg->char_shift > 1)
+        if (cfg->char_shift > 1)
+            return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs characteristic shift 1 (char_shift 0 or 1)");
+        if (cfg->ndim == 3 && cfg->splitting == DIRAC_STRANG && cfg->points_per_lane > 1)
             return fail(nullptr, DIRAC_ERR_ARG,
-                        "DIRAC_FX64 runs first-order steps and 2-D second-order steps (char_shift 0 or 1)");
+                        "DIRAC_FX64 3-D second-order steps run as single sweeps (points_per_lane 0 or 1)");
         const int fmode = cfg->ndim == 3 ? 1 : (cfg->splitting == DIRAC_STRANG ? 2 : 0);
+        const bool strang3 = cfg->ndim == 3 && cfg->splitting == DIRAC_STRANG;
         if (cfg->steps_per_launch > 2 || ((cfg->ndim == 3 || fmode == 2) && cfg->steps_per_launch > 1) ||
-            (cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
+            (!strang3 && cfg->steps_per_launch > 0 && cfg->points_per_lane > 0 &&
              !sweep_supported_fx(fmode, cfg->steps_per_launch, cfg->points_per_lane)) ||
             (cfg->steps_per_launch == 2 && cfg->points_per_lane > 0 && cfg->points_per_lane != 2))
             return fail(nullptr, DIRAC_ERR_ARG,
@@ -1188,8 +1198,9 @@ dirac_status dirac_autotune(dirac_grid *g) {
     std::vector<Cand> cands;
     if (sweep_mode(g) == 6) {
         cands.push_back({1, 2, 4, 16, 0, 0});
-        for (int sw : {16, 32})
-            for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
+        if (!g->fx)  // the fused passes take floating-point states
+            for (int sw : {16, 32})
+                for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
     } else if (g->fx && g->cfg.ndim == 3) {
         for (int P : {1, 2, 4})
             for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});

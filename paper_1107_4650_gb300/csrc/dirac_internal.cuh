@@ -98,10 +98,12 @@ bool shift_supported(int S, int P);
 // swept state), optionally followed by the phase from `table` (z sweeps only); x sweeps accumulate the face
 // flux scaled by fscale when flux_face >= 0 (parts: one per block).  Used by the 3-D second-order step.
 // With ucoef (12 doubles per step, ucoef_n steps) the phase is the vector-potential matrix of step step0.
+// precision: DIRAC_FP64, DIRAC_FP32 or DIRAC_FX64 (int64 state; no vector potential; rshift > 0 divides the
+// output by 2^rshift with rounding to nearest, halves up).
 cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz, int axis,
                         int64_t shift, int periodic, int full_table, int phase, int64_t flux_face, double fscale,
                         double vol, double *flux_part, double *flux_cum, unsigned *ticket, const double *ucoef,
-                        int64_t ucoef_n, int64_t step0, int fp32, int blocks, cudaStream_t s);
+                        int64_t ucoef_n, int64_t step0, int precision, int rshift, int blocks, cudaStream_t s);
 
 // Fused 3-D step (x, y, z sweeps and phase in one pass, `steps` = 1 or 2 steps per launch): blocks of
 // `warps` warps own a (32 - 2 steps)-cell x strip and warps - 2 steps rows along y and stream a z segment of

@@ -129,9 +129,11 @@ def test_3d_steps_per_launch_validation(lib):
 
 
 def test_fx64_validation(lib):
-    """DIRAC_FX64 runs first-order steps (one or, in 2-D, two per launch) and 2-D second-order steps (one)."""
+    """DIRAC_FX64 runs first-order steps (one or, in 2-D, two per launch) and second-order steps (one; 3-D as
+    single sweeps)."""
     import paper_1107_4650_gb300 as D
-    for n, kw in (((8, 8, 8), dict(ndim=3, steps_per_launch=2)), ((8, 8, 8), dict(ndim=3, splitting=D.DIRAC_STRANG)),
+    for n, kw in (((8, 8, 8), dict(ndim=3, steps_per_launch=2)), ((8, 8, 8), dict(ndim=3, splitting=D.DIRAC_STRANG,
+                                                                                     points_per_lane=2)),
                   ((16, 1, 16), dict(splitting=D.DIRAC_STRANG, steps_per_launch=2)),
                   ((16, 1, 16), dict(splitting=D.DIRAC_STRANG, steps_per_launch=1, points_per_lane=4)),
                   ((16, 1, 16), dict(char_shift=2)), ((16, 1, 16), dict(steps_per_launch=4)),

@@ -266,3 +266,59 @@ def test_fx_strang2d_klein_within_1e12_of_fp64_oracle(D):
     assert err <= 1e-12
     assert F > 0.01 and abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
     assert np.array_equal(q1, oracle.step_strang2d_fx(q0, 1.0, C, DX, run.nsteps, V=V))
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("full", [False, True])
+def test_fx_strang3d_bit_exact_against_fixed_point_oracle(D, shape, periodic, full):
+    """3-D second-order steps as eight single sweeps on the int64 state, against oracle_step_strang3d_fx."""
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx * 3 + ny + nz)
+    V = np.random.default_rng(ny + nz).uniform(-4e4, 4e4, nx * ny * nz if full else nx)
+    S = oracle.fx_shift(psi, 3, strang=True)
+    q0 = oracle.fx_encode(psi, S)
+    want = oracle.step_strang3d_fx(q0, 1.0, C, DX, 3, V=V, periodic=periodic)
+    cfg = D.make_config((nx, ny, nz), ndim=3, precision=D.DIRAC_FX64, splitting=D.DIRAC_STRANG,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL if full else D.DIRAC_V_X_ONLY)
+        D.dirac_set_state_fx(h, q0, S)
+        D.dirac_step(h, 3)
+        got, _ = _q_of(D, h, (nz, ny, nx))
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    assert info["plan"] == D.DIRAC_PLAN_3D_STRANG
+    assert np.array_equal(got, want)
+
+
+def test_fx_strang3d_coulomb_within_1e12_of_fp64_oracle(D):
+    """3-D second-order steps in the soft-Coulomb potential (48^3, face flux, 40 steps, autotuned, graphs): the
+    decoded state within relative L2 1e-12 of the FP64 oracle, flux within 1e-12 relative, integer state equal
+    to the fixed-point oracle's; dirac_set_state picks the second-order shift."""
+    n = 48
+    psi = W.gaussian_packet(n, n, DX, -n * DX / 2, -n * DX / 2, -6 * DX, 0.0, 4 * DX, 0.4 * C, ny=n, y_min=-n * DX / 2)
+    V = W.soft_coulomb_3d(n, DX, 10.0, 2 * DX).reshape(-1)
+    want, F = oracle.step_strang3d(psi, 1.0, C, DX, 40, V=V, flux_face=n // 2)
+    cfg = D.make_config((n, n, n), ndim=3, precision=D.DIRAC_FX64, splitting=D.DIRAC_STRANG, flux_face=n // 2)
+    h = D.dirac_create_grid(cfg)
+    try:
+        D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
+        D.dirac_set_state(h, psi)
+        q0, S = _q_of(D, h, (n, n, n))
+        D.dirac_autotune(h)
+        D.dirac_step(h, 40)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+        q1, _ = _q_of(D, h, (n, n, n))
+        obs = D.dirac_observables(h)
+    finally:
+        D.dirac_destroy(h)
+    assert S == oracle.fx_shift(psi, 3, strang=True)
+    err = rel_l2(got, want)
+    print("FX64 3-D Strang vs FP64 oracle after 40 steps: rel L2 %.3e" % err)
+    assert err <= 1e-12
+    assert F > 1e-3 and abs(obs["flux_cum"] - F) <= 1e-12 * abs(F)
+    assert np.array_equal(q1, oracle.step_strang3d_fx(q0, 1.0, C, DX, 40, V=V))
