@@ -3,9 +3,13 @@
 // independent work per SM to hide the pipe latency) and stores one sum, so the timed launch is pure
 // issue.  Prints lane-instructions per second and per SM per clock at the device's maximum SM clock.
 // Also: 64-bit integer adds (chains q += q of the neighbouring chain) and int64 <-> FP64 conversion pairs
-// (q -> double -> q + 1), the operations of a fixed-point evaluation of the sweeps.
+// (q -> double -> q + 1), the operations of a fixed-point evaluation of the sweeps.  And binary64 additions
+// on the integer units (iadd_rn), alone and interleaved with hardware DADD chains, to see whether the two
+// pipes overlap.
 #include <cstdio>
 #include <cuda_runtime.h>
+
+#include "iadd64.cuh"
 
 namespace {
 
@@ -48,6 +52,57 @@ __global__ void int_chains(long long *out, int iters) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += q[k];
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// ND hardware DADD chains and NS integer-unit addition chains per thread, interleaved
+template <int ND, int NS>
+__global__ void mixed_chains(double *out, int iters) {
+    double a[ND > 0 ? ND : 1], b[NS > 0 ? NS : 1];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) b[k] = 1.0 + 1e-3 * (threadIdx.x + 2 * k + 1);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < (ND > NS ? ND : NS); ++k) {
+            if (k < ND) a[k] = __dadd_rn(a[k], 1e-7);
+            if (k < NS) b[k] = dirac::iadd_rn(b[k], (k & 1) ? -3e-8 : 1e-7);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) s += a[k];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) s += b[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int ND, int NS>
+double run_mixed(const char *name, int blocks, int threads, int iters, double sms, double clk_hz) {
+    double *out = nullptr;
+    if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) return -1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {  // first launch is a warm-up
+        cudaEventRecord(e0);
+        mixed_chains<ND, NS><<<blocks, threads>>>(out, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    const double adds = (double)blocks * threads * (double)(ND + NS) * iters;
+    const double rate = adds / (best * 1e-3);
+    std::printf("{\"op\": \"%s\", \"dadd_chains\": %d, \"int_unit_chains\": %d, \"ms\": %.4f, \"adds_per_s\": %.4e, "
+                "\"adds_per_sm_per_clk\": %.3f}\n",
+                name, ND, NS, best, rate, rate / (sms * clk_hz));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    return rate;
 }
 
 template <int OP>
@@ -118,6 +173,11 @@ int main() {
     run<float, false>("FADD", blocks, threads, 65536, sms, clk);
     run_int<0>("IADD64", blocks, threads, 16384, 1.0, sms, clk);
     run_int<1>("CVT_S64_F64_PAIR", blocks, threads, 1024, 2.0, sms, clk);
+    run_mixed<8, 0>("ADD_MIX", blocks, threads, 1024, sms, clk);
+    run_mixed<0, 8>("ADD_MIX", blocks, threads, 1024, sms, clk);
+    run_mixed<8, 2>("ADD_MIX", blocks, threads, 1024, sms, clk);
+    run_mixed<8, 4>("ADD_MIX", blocks, threads, 1024, sms, clk);
+    run_mixed<8, 8>("ADD_MIX", blocks, threads, 1024, sms, clk);
     const cudaError_t e = cudaGetLastError();
     std::printf("{\"sms\": %d, \"clock_hz\": %.4e, \"status\": \"%s\"}\n", sms, clk, cudaGetErrorString(e));
     return e == cudaSuccess ? 0 : 1;

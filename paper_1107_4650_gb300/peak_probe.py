@@ -20,7 +20,7 @@ EXE = os.path.join(HERE, "_build", "peak_probe")
 
 def main() -> int:
     os.makedirs(os.path.dirname(EXE), exist_ok=True)
-    subprocess.check_call([_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", EXE, SRC])
+    subprocess.check_call([_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-I", os.path.dirname(SRC), "-o", EXE, SRC])
     return subprocess.call([EXE])
 
 

@@ -69,6 +69,66 @@ def test_2d_fp64_bit_exact_random(D, shape, periodic, K, P):
     assert _bits_equal(got, want), rel_l2(got, want)
 
 
+def _edge_value_state(nz, nx, seed):
+    """Random spinors with cells planted where binary64 additions take their edge cases: zeros of both signs,
+    subnormals, magnitudes of 2^-1000, 2^-955 and 2^1015 (the largest a step's sums keep finite), exact
+    cancellation (components equal or opposite, so u or w of a characteristic pair is 0), ulp-level
+    cancellation, and sums that land near rounding ties."""
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal((nz, 1, nx, 4)) + 1j * rng.standard_normal((nz, 1, nx, 4))
+    flat = psi.reshape(-1, 4)
+    n = flat.shape[0]
+    kinds = rng.integers(0, 10, n)
+    for c in range(n):
+        k = kinds[c]
+        v = flat[c]
+        if k == 0:
+            v[:] = 0.0
+        elif k == 1:
+            v[:] = np.array([-0.0, 0.0, -0.0, 0.0]) + 1j * np.array([0.0, -0.0, -0.0, 0.0])
+        elif k == 2:
+            v[:] = v * 5e-324 * 7
+        elif k == 3:
+            v[:] = v * 2.0 ** -1000
+        elif k == 4:
+            v[:] = v * 2.0 ** 1015
+        elif k == 5:
+            v[3] = v[0]
+            v[2] = -v[1]
+        elif k == 6:
+            v[3] = v[0] * (1 + 2.0 ** -52)
+            v[2] = -v[1] * (1 - 2.0 ** -53)
+        elif k == 7:
+            v[3] = v[0] * 2.0 ** -53
+            v[2] = v[1] * 3 * 2.0 ** -54
+        elif k == 8:
+            v[:] = v * 2.0 ** -955
+    return psi
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("P", [1, 2, 4])
+def test_2d_fp64_edge_values_bit_exact(D, periodic, P):
+    """Zeros of both signs, subnormals, extreme magnitudes and exact cancellation through the step."""
+    nx, nz = 97, 43
+    psi = _edge_value_state(nz, nx, seed=11 + P)
+    V = np.random.default_rng(5).uniform(-2e4, 6e4, nx)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 3, V=V, periodic=periodic)
+    assert np.isfinite(want).all()
+    cfg = D.make_config((nx, 1, nz), boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO,
+                        steps_per_launch=1, points_per_lane=P)
+    h = D.dirac_create_grid(cfg)
+    try:  # no observables: the norm of the 2^1015 cells is not finite
+        D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h, psi)
+        D.dirac_step(h, 3)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    assert _bits_equal(got, want)
+
+
 @pytest.mark.parametrize("periodic", [False, True])
 def test_2d_fp64_full_table_bit_exact(D, periodic):
     nx, nz = 97, 61
