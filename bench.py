@@ -610,9 +610,10 @@ def main():
                     entry["frac_of_measured_fp64_issue"] = instr * v3 / world / 1e12 / FP64_ISSUE_PEAK_MEASURED
                 elif prec == D.DIRAC_FX64:
                     # algorithmic: the state read and written once plus the per-cell int64 table (32 B); first
-                    # order moves 2 x 128 + 32 B in its two passes, second order 8 x 128 + 32 B in its eight
-                    # single sweeps
-                    moved = 288 if split == D.DIRAC_LIE else 8 * 128 + 32
+                    # order moves that in the fused pass and 2 x 128 + 32 B in its two passes, second order
+                    # 8 x 128 + 32 B in its eight single sweeps
+                    moved = (160 if i3["plan"] == D.DIRAC_PLAN_3D_FUSED else 288) if split == D.DIRAC_LIE \
+                        else 8 * 128 + 32
                     entry["bytes_per_point_step"] = 160
                     entry["hbm_frac"] = 160 * v3 / world / 1e9 / hbm_peak
                     entry["pass_bytes_per_point_step"] = moved

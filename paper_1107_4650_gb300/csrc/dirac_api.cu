@@ -390,11 +390,11 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
         a.nplanes = 1;
         if (K == 2) {
             a.nsegs = p.f2_nzsegs * p.f2_nytiles * p.f2_warps;  // flux parts per step of the fused pass
-            e = launch_fused3d(a, g->fp32, p.f2_warps, 2, g->cfg.n[1], g->cfg.n[2], p.f2_nstrips, p.f2_nytiles,
+            e = launch_fused3d(a, g->fx ? 2 : g->fp32, p.f2_warps, 2, g->cfg.n[1], g->cfg.n[2], p.f2_nstrips, p.f2_nytiles,
                                p.f2_nzsegs, p.f2_zseg_h, s);
         } else {
             a.nsegs = p.f_nzsegs * p.f_nytiles * p.f_warps;  // flux parts of the fused pass
-            e = launch_fused3d(a, g->fp32, p.f_warps, 1, g->cfg.n[1], g->cfg.n[2], p.f_nstrips, p.f_nytiles,
+            e = launch_fused3d(a, g->fx ? 2 : g->fp32, p.f_warps, 1, g->cfg.n[1], g->cfg.n[2], p.f_nstrips, p.f_nytiles,
                                p.f_nzsegs, p.f_zseg_h, s);
         }
         if (e != cudaSuccess) return cuda_fail(g, e, "fused 3-D step launch");
@@ -634,9 +634,10 @@ dirac_status fx_load_state(dirac_grid *g, const void *psi, int on_device) {
 void default_plan(dirac_grid *g) {
     const int k = g->cfg.steps_per_launch, pp = g->cfg.points_per_lane;
     if (ndim_of(g) == 3 && g->fx) {
-        // fixed point: the x-y pass + z/phase pass (the fused kernels take floating-point states), P = 1 by
-        // default (the 128-bit phase products' registers), first order only
-        g->plan.fused3d = 0;
+        // fixed point, first order: points_per_lane 0 = the fused single pass (one step per pass), 1, 2 or 4 =
+        // the x-y pass + z/phase pass with that P; second order: single sweeps
+        g->plan.fused3d = pp > 0 ? 0 : 1;
+        g->plan.f_warps = g->cfg.n[1] <= 12 ? 8 : 16;
         g->plan.s3_fused = 0;
         make_plan(g, 1, pp > 0 ? pp : 1, 4, 16);
         return;
@@ -1204,6 +1205,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
     } else if (g->fx && g->cfg.ndim == 3) {
         for (int P : {1, 2, 4})
             for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});
+        for (int fw : {8, 16}) cands.push_back({1, 1, 4, 16, fw});  // the fused single pass
     } else if (g->fx) {
         const int KP[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}};
         for (auto &kp : KP)

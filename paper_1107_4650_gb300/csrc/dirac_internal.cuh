@@ -107,10 +107,11 @@ cudaError_t launch_axis(const void *in, void *out, const void *table, int64_t nx
 
 // Fused 3-D step (x, y, z sweeps and phase in one pass, `steps` = 1 or 2 steps per launch): blocks of
 // `warps` warps own a (32 - 2 steps)-cell x strip and warps - 2 steps rows along y and stream a z segment of
-// zseg_h planes (steps 1: 8 or 16 warps; steps 2: 16 warps in FP32, 8 in FP64).  Flux parts:
+// zseg_h planes (steps 1: 8 or 16 warps; steps 2: 16 warps in FP32, 8 in FP64; 64-bit fixed point: steps 1,
+// no vector potential).  precision: 0 FP64, 1 FP32, 2 int64 fixed point.  Flux parts:
 // [steps][nzsegs * nytiles * warps] (a.nsegs * a.nplanes must equal nzsegs * nytiles * warps).
-cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int steps, int64_t ny, int64_t nz, int64_t nstrips,
-                           int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s);
+cudaError_t launch_fused3d(const SweepArgs &a, int precision, int warps, int steps, int64_t ny, int64_t nz,
+                           int64_t nstrips, int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s);
 
 // 3-D second-order step as fused passes (strang3d_kernels.cuh).  x-y-x pass (nh = 1: half a step) or
 // x-y-x-x-y-x pass (nh = 2: the second half of one step and the first half of the next): blocks of `warps`

@@ -5,8 +5,9 @@
 
 namespace dirac {
 
-cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int steps, int64_t ny, int64_t nz, int64_t nstrips,
-                           int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s) {
+cudaError_t launch_fused3d(const SweepArgs &a, int precision, int warps, int steps, int64_t ny, int64_t nz,
+                           int64_t nstrips, int64_t nytiles, int64_t nzsegs, int64_t zseg_h, cudaStream_t s) {
+    const int fp32 = precision == 1;
     Fused3DArgs A{};
     A.s = a;
     A.ny = ny;
@@ -16,6 +17,12 @@ cudaError_t launch_fused3d(const SweepArgs &a, int fp32, int warps, int steps, i
     A.nzsegs = nzsegs;
     A.zseg_h = zseg_h;
     const bool field = a.ucoef != nullptr && a.ucoef_n > 0;
+    if (precision == 2) {  // 64-bit fixed point: one step per pass, no vector potential
+        if (steps != 1 || field) return cudaErrorInvalidValue;
+        if (warps == 16) return launch_fused3d_one<long long, 16, false>(A, s);
+        if (warps == 8) return launch_fused3d_one<long long, 8, false>(A, s);
+        return cudaErrorInvalidValue;
+    }
     if (steps == 2) {
         // two steps per pass: FP32 with 16-warp blocks, FP64 with 8 (its register budget)
         if (fp32 && warps == 16)

@@ -16,6 +16,9 @@
 // FIELD: a uniform vector potential; the phase is the 4 x 4 matrix U(step) exp(-i V dt) of Eq. sol_dis_4
 // (table entry g = exp(-i V dt) / 8 times each entry of U, then the column-ordered fma chains of the 2-D
 // kernel), one launch = one step whose index selects the row of the U table.
+// 64-bit fixed-point states (T = long long): the sweeps are exact integer sums, so any order gives the bits
+// of the two-kernel path; the phase is the rounded 128-bit product (the table holding round(p 2^62) with the
+// 1/8); the face terms are formed in FP64 from the converted values and scaled by the state's 2^-2S.
 #pragma once
 
 #include "step_kernels.cuh"
@@ -27,6 +30,18 @@ struct Fused3DArgs {
     int64_t ny, nz;
     int64_t nstrips, nytiles, nzsegs, zseg_h;
 };
+
+// accumulator type of the face terms: the storage type, FP64 for fixed-point states
+template <typename T> struct FaceAcc { using type = T; };
+template <> struct FaceAcc<long long> { using type = double; };
+
+// |p14|^2 + |p23|^2 as a fused chain in the accumulator type
+template <typename T>
+__device__ __forceinline__ typename FaceAcc<T>::type face_sq(Cx<T> p14, Cx<T> p23) {
+    using F = typename FaceAcc<T>::type;
+    return Ar<F>::fma((F)p14.re, (F)p14.re,
+                      Ar<F>::fma((F)p14.im, (F)p14.im, Ar<F>::fma((F)p23.re, (F)p23.re, Ar<F>::mul((F)p23.im, (F)p23.im))));
+}
 
 template <typename T, int W, bool FIELD>
 __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A) {
@@ -66,7 +81,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
     const int64_t face = a.flux_face;
     const bool face_lane = owned_row && face >= x_own0 && face < x_own1 && (x == face - 1 || x == face);
     double facc = 0.0;
-    T fpart = T(0);
+    typename FaceAcc<T>::type fpart = 0;
 
     Cx<T> UA[2] = {{T(0), T(0)}, {T(0), T(0)}}, UB[2] = {{T(0), T(0)}, {T(0), T(0)}};
 
@@ -114,13 +129,12 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
         const Cx<T> u14 = cadd(st[0], st[3]), w14 = csub(st[0], st[3]);
         const Cx<T> u23 = cadd(st[1], st[2]), w23 = csub(st[1], st[2]);
         if (face_lane && k >= z_begin && k < z_end) {
-            const T v = (x == face - 1)
-                            ? Ar<T>::fma(u14.re, u14.re, Ar<T>::fma(u14.im, u14.im, Ar<T>::fma(u23.re, u23.re, Ar<T>::mul(u23.im, u23.im))))
-                            : -Ar<T>::fma(w14.re, w14.re, Ar<T>::fma(w14.im, w14.im, Ar<T>::fma(w23.re, w23.re, Ar<T>::mul(w23.im, w23.im))));
-            fpart = Ar<T>::add(fpart, v);
+            using F = typename FaceAcc<T>::type;
+            const F v = (x == face - 1) ? face_sq(u14, u23) : -face_sq(w14, w23);
+            fpart = Ar<F>::add(fpart, v);
             if (((k - z_begin) & 31) == 31 || k == z_end - 1) {
                 facc = __dadd_rn(facc, (double)fpart);
-                fpart = T(0);
+                fpart = 0;
             }
         }
         const Cx<T> lu14 = shfl_c(u14, (lane + 31) & 31), lu23 = shfl_c(u23, (lane + 31) & 31);
@@ -185,7 +199,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
         // one flux part per (y tile, z segment, warp) of the strip that owns the face; halo warps write 0
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) facc = __dadd_rn(facc, __shfl_xor_sync(0xffffffffu, facc, o));
-        if (lane == 0) a.flux_part[(zseg * A.nytiles + ytile) * W + w] = __dmul_rn(0.5, facc);
+        if (lane == 0) a.flux_part[(zseg * A.nytiles + ytile) * W + w] = __dmul_rn(0.5 * a.flux_unit, facc);
     }
     if (face >= 0) finish_flux<1>(a);
 }

@@ -154,12 +154,13 @@ def test_fx_autotune_restores_state(D):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13), (33, 1, 4)])
+@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13), (33, 1, 4), (70, 30, 37)])
 @pytest.mark.parametrize("periodic", [False, True])
-@pytest.mark.parametrize("P", [1, 2, 4])
+@pytest.mark.parametrize("P", [0, 1, 2, 4])
 @pytest.mark.parametrize("full", [False, True])
 def test_fx_3d_bit_exact_against_fixed_point_oracle(D, shape, periodic, P, full):
-    """3-D: the x-y pass and the z/phase pass on the int64 state, against oracle_step_fx bit for bit."""
+    """3-D on the int64 state, against oracle_step_fx bit for bit: the fused single pass (points_per_lane 0:
+    30-cell strips, 14-row tiles, several z segments at 70 x 30 x 37) and the x-y pass + z/phase pass."""
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx + ny * nz + P)
     V = np.random.default_rng(nz + P).uniform(-4e4, 4e4, nx * ny * nz if full else nx)
@@ -177,14 +178,19 @@ def test_fx_3d_bit_exact_against_fixed_point_oracle(D, shape, periodic, P, full)
         info = D.dirac_get_info(h)
     finally:
         D.dirac_destroy(h)
-    assert info["plan"] == D.DIRAC_PLAN_3D_TWO_PASS and info["points_per_lane"] == P
+    if P == 0:
+        assert info["plan"] == D.DIRAC_PLAN_3D_FUSED
+    else:
+        assert info["plan"] == D.DIRAC_PLAN_3D_TWO_PASS and info["points_per_lane"] == P
     assert np.array_equal(got, want)
 
 
-def test_fx_3d_coulomb_within_1e12_of_fp64_oracle(D):
-    """A moving packet in the soft-Coulomb potential (64^3, per-cell potential, face flux, 150 steps, autotuned):
-    the decoded state within relative L2 1e-12 of the FP64 oracle, the flux within 1e-12 relative, the
-    integer state equal to the fixed-point oracle's; dirac_set_state chooses the 3-D shift."""
+@pytest.mark.parametrize("tune", [True, False])
+def test_fx_3d_coulomb_within_1e12_of_fp64_oracle(D, tune):
+    """A moving packet in the soft-Coulomb potential (64^3, per-cell potential, face flux, 150 steps; autotuned,
+    and the default fused pass): the decoded state within relative L2 1e-12 of the FP64 oracle, the flux
+    within 1e-12 relative, the integer state equal to the fixed-point oracle's; dirac_set_state chooses the
+    3-D shift."""
     n = 64
     psi = W.gaussian_packet(n, n, DX, -n * DX / 2, -n * DX / 2, -6 * DX, 0.0, 5 * DX, 0.4 * C, ny=n, y_min=-n * DX / 2)
     V = W.soft_coulomb_3d(n, DX, 10.0, 2 * DX).reshape(-1)
@@ -195,7 +201,10 @@ def test_fx_3d_coulomb_within_1e12_of_fp64_oracle(D):
         D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
         D.dirac_set_state(h, psi)
         q0, S = _q_of(D, h, (n, n, n))
-        D.dirac_autotune(h)
+        if tune:
+            D.dirac_autotune(h)
+        else:
+            assert D.dirac_get_info(h)["plan"] == D.DIRAC_PLAN_3D_FUSED
         D.dirac_step(h, 150)
         got = np.empty_like(psi)
         D.dirac_get_state(h, got)
