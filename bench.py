@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--check-points", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=0.0,
+                    help="--impl reference: oracle seconds per step (0: about 60 s over all steps, 2 s at least)")
     ap.add_argument("--cpu-detail-seconds", type=float, default=3.0,
                     help="per sample of the CPU oracle detail (one thread; 3-D grid; ensemble); 0 = skip")
     return ap.parse_args()
@@ -258,9 +260,9 @@ def reference_arm(args, rank, world):
         return
     from paper_1107_4650_gb300 import workloads as W
     run = W.klein_config_2d(side=args.side, nsteps=args.nsteps)
-    per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per = args.ref_step_seconds if args.ref_step_seconds > 0 else max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_baseline(run, 1.0)
+        cpu_baseline(run, min(1.0, per))
     vals = []
     cores, desc = None, ""
     for _ in range(args.steps):
