@@ -129,8 +129,8 @@ dirac_status dirac_get_state(dirac_grid *g, void *psi, int on_device);
 
 /* DIRAC_FX64 grids: the fixed-point state itself, int64 q = round(psi 2^shift) in the layout above (8 values
  * per cell), in or out without conversion (exact checkpoints).  set: the caller's shift must keep the
- * discrete L2 norm of q below 2^60 in 2-D, 2^59 in 3-D (see DIRAC_FX64); resets the counters like
- * dirac_set_state.  Errors:
+ * discrete L2 norm of q below 2^60 in 2-D, 2^59 in 3-D first order and 2^57 in 3-D second order (the
+ * shifts dirac_set_state picks; see DIRAC_FX64); resets the counters like dirac_set_state.  Errors:
  * DIRAC_ERR_ARG for another precision or a null pointer. */
 dirac_status dirac_set_state_fx(dirac_grid *g, const int64_t *q, int shift, int on_device);
 dirac_status dirac_get_state_fx(dirac_grid *g, int64_t *q, int *shift, int on_device);
