@@ -44,16 +44,18 @@ FP32_BYTES_PER_POINT_STEP = 64
 FLOPS_PER_POINT_STEP_2D = 56    # 32 adds (two sweeps) + 4 complex products of 6 flops
 FP64_INSTR_PER_POINT_STEP_2D = 48  # 32 DADD + 8 DMUL + 8 DFMA: what the FP64 pipe issues per 2-D point-step
 FP64_INSTR_PER_POINT_STEP_2D_FIELD = 80  # with a vector potential: 32 DADD + 12 complex multiply-adds of 4 DFMA
-# FP64 issue roof: the recipe's nominal 1.25 TFLOP/s counts a DFMA as 2 flops -> 0.625 T FP64 instructions/s
-# (DADD and DMUL issue at the DFMA rate).  Measured on this machine's GB300 with an FMA/ADD throughput probe:
-# 0.5276 T lane-instructions/s (1.68 per SM per clock at 2.07 GHz, 152 SMs; `python -m paper_1107_4650_gb300.peak_probe`).
-FP64_ISSUE_PEAK_NOMINAL = 0.625
-FP64_ISSUE_PEAK_MEASURED = 0.5276
+# FP64 issue roof from GB300's unit counts and clock: 1.25 TFLOP/s FP64 with a DFMA counted as two flops is two
+# FP64 instructions per SM per clock (DADD and DMUL issue at the DFMA rate): 2 x 152 SMs x 2.07 GHz.
+FP64_INSTR_PER_SM_CLOCK = 2
+SM_COUNT = 152
+FP64_ISSUE_PEAK_NOMINAL = FP64_INSTR_PER_SM_CLOCK * SM_COUNT * 2.07e9 / 1e12  # 0.629 T FP64 instructions/s
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel on the 2048^2 workload, keyed
 # by (steps per launch, points per lane) of the captured variant (profiles/step_kernel_fp64_klein2048.md,
 # profiles/step_kernel_fp32_klein2048.md).  A variant without a capture reports null.
-MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": {(1, 2): 277.515264e6 + 216.816896e6},
+MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": {(1, 2): 277.515264e6 + 216.816896e6, (1, 4): 287.006976e6 + 216.340992e6},
                                "fp32": {(2, 2): 147.680256e6 + 85.511168e6}}
+# ncu sm__pipe_fp64_cycles_active of the same captures (fraction of active cycles)
+MEASURED_FP64_PIPE = {(1, 2): 0.836, (1, 4): 0.8375}
 
 
 def parse():
@@ -263,18 +265,25 @@ def reference_arm(args, rank, world):
     per = args.ref_step_seconds if args.ref_step_seconds > 0 else max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(run, min(1.0, per))
-    vals = []
+    vals, secs = [], []
     cores, desc = None, ""
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         v, cores, desc = cpu_baseline(run, per)
+        secs.append(time.perf_counter() - t0)
         vals.append(v)
     value = float(np.mean(vals))
-    ms = args.side * args.side * args.nsteps / value * 1e3
+    sampled_ms = float(np.mean(secs)) * 1e3
+    full_ms = args.side * args.side * args.nsteps / value * 1e3
     line = {"impl": "reference", "metric": "4-spinor grid-point-steps/s", "value": value, "unit": "point-steps/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sampled_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "2-D Klein step FP64 %dx%d, %d time steps per bench step (CPU oracle on a "
-                                   "bounded 1024^2 crop, rate per point-step)" % (args.side, args.side, args.nsteps)},
+            "config": {"workload": "2-D Klein step FP64 %dx%d, %d time steps (CPU oracle: each bench step is a "
+                                   "bounded sample of about %.0f s on a 1024^2 crop of the run with the packet width "
+                                   "halved to 50 dx so that it fits the crop; value is the sample's rate per "
+                                   "point-step)" % (args.side, args.side, args.nsteps, per),
+                       "sampled_seconds_per_step": sampled_ms / 1e3,
+                       "extrapolated_ms_for_the_full_%d_steps_at_%d^2" % (args.nsteps, args.side): full_ms},
             "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -383,14 +392,16 @@ def main():
                if args.side == 2048 else None)
     roofline = {"bound": "alu", "achieved": fp64_tips, "peak": FP64_ISSUE_PEAK_NOMINAL, "unit": "T FP64-instr/s",
                 "frac": fp64_tips / FP64_ISSUE_PEAK_NOMINAL, "traffic": traffic,
-                "peak_source": "derived from the recipe's nominal FP64 rate (1.25 TFLOP/s / 2 flops per DFMA); "
+                "peak_source": "derived from unit counts and clock: 2 FP64 instructions per SM per clock (GB300's "
+                               "1.25 TFLOP/s FP64, a DFMA counted as two flops) x 152 SMs x 2.07 GHz; "
                                "MEASURED_PEAKS.json has no FP64 figure",
-                "frac_of_measured_fp64_issue": fp64_tips / FP64_ISSUE_PEAK_MEASURED,
+                "ncu_fp64_pipe_active": MEASURED_FP64_PIPE.get((k_launch, info["points_per_lane"])),
                 "achieved_tflops": FLOPS_PER_POINT_STEP_2D * ncell * k_launch / mean_launch_s / 1e12,
                 "kernel": "dirac::sweep_kernel<double,%d,%d,0>" % (k_launch, info["points_per_lane"]),
                 "mean_launch_ms": mean_launch_s * 1e3,
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-                        "peak_source": hbm_src, "algorithmic_bytes_per_launch": alg_bytes}}
+                        "peak_source": hbm_src, "algorithmic_bytes_per_launch": alg_bytes,
+                        "basis": "128 B per FP64 point-step (state read and written once, x-only table)"}}
 
     # ---------------------------------------------------------------- e2e through host buffers
     e2e = None
@@ -502,7 +513,7 @@ def main():
             "workload": "the 2048^2 Klein FP64 grid in a uniform two-cycle laser pulse (vector potential, full "
                         "phase matrix of Eq. sol_dis_4), %d timed steps" % nf,
             "fp64_instr_per_point_step": FP64_INSTR_PER_POINT_STEP_2D_FIELD,
-            "frac_of_measured_fp64_issue": FP64_INSTR_PER_POINT_STEP_2D_FIELD * vf / world / 1e12 / FP64_ISSUE_PEAK_MEASURED}
+            "frac_of_fp64_issue_roof": FP64_INSTR_PER_POINT_STEP_2D_FIELD * vf / world / 1e12 / FP64_ISSUE_PEAK_NOMINAL}
 
     # ---------------------------------------------------------------- 2-D second order and characteristic shifts
     if not args.no_2d_variants:
@@ -548,7 +559,7 @@ def main():
                                                              if vname == "fp64_strang2d" else
                                                              "first-order steps with c dt = %d dx" % per_step),
                 "fp64_instr_per_point_step": instr,
-                "frac_of_measured_fp64_issue": instr * vv / world / 1e12 / FP64_ISSUE_PEAK_MEASURED}
+                "frac_of_fp64_issue_roof": instr * vv / world / 1e12 / FP64_ISSUE_PEAK_NOMINAL}
 
     # ---------------------------------------------------------------- 3-D soft-Coulomb grid (first and second order)
     if not args.no_3d:
@@ -609,7 +620,7 @@ def main():
                          "norm_end": o3["norm"]}
                 if prec == D.DIRAC_FP64:
                     entry["fp64_instr_per_point_step"] = instr
-                    entry["frac_of_measured_fp64_issue"] = instr * v3 / world / 1e12 / FP64_ISSUE_PEAK_MEASURED
+                    entry["frac_of_fp64_issue_roof"] = instr * v3 / world / 1e12 / FP64_ISSUE_PEAK_NOMINAL
                 elif prec == D.DIRAC_FX64:
                     # algorithmic: the state read and written once plus the per-cell int64 table (32 B); first
                     # order moves that in the fused pass and 2 x 128 + 32 B in its two passes, second order

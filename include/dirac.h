@@ -373,16 +373,22 @@ const char *dirac_surrogate_last_error(const dirac_surrogate *s);
  * partition differs) for a state in caller-owned device memory and allocates nothing: its block
  * partials live in one fixed device array of DIRAC_NOALLOC_MAX_BLOCKS x 5 doubles (640 KiB), defined
  * in the library and held by every device that loads it until the process exits.
- *   psi        device pointer on the current device, layout psi[z][y][x][c][re,im] in `precision`
+ *   psi        device pointer on the current device, layout psi[z][y][x][c][re,im]; `precision` is
+ *              DIRAC_FP64 (complex128) or DIRAC_FP32 (complex64) only: a fixed-point (DIRAC_FX64) state,
+ *              such as dirac_state_ptr returns for a DIRAC_FX64 grid, is rejected with DIRAC_ERR_ARG
  *   n, ndim    grid as in dirac_config (n[1] == 1 when ndim == 2); at most
  *              DIRAC_NOALLOC_MAX_BLOCKS * DIRAC_NOALLOC_CELLS_PER_BLOCK cells, else DIRAC_ERR_ARG
  *   dx, x_min  cell edge and lower corner; flux_face as in dirac_config (-1: norm_right = 0)
  *   stream     cudaStream_t the two kernels are enqueued on (NULL = legacy stream); asynchronous
  *   out        device pointer to 5 doubles: norm, norm_right, centroid x, y, z
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call shares the array and
- * overwrites the partials it reads, so nothing needs clearing, but calls whose kernels overlap on
- * the GPU (different streams or host threads) race on it.  Errors go to dirac_last_error(NULL). */
+ * A call outside a stream capture looks up the array's device address (cudaGetSymbolAddress, which
+ * allocates nothing) with the current device, so after cudaDeviceReset the next such call finds the
+ * reloaded array; a call inside a capture uses the address the last uncaptured call on that device
+ * found, so make the first call on a device before any stream capture (DIRAC_ERR_CUDA otherwise).
+ * Every call shares the array and overwrites the partials it reads, so nothing needs clearing, but
+ * calls whose kernels overlap on the GPU (different streams or host threads) race on it.  The result
+ * is written asynchronously, so unlike dirac_observables this call never returns DIRAC_ERR_NONFINITE:
+ * a state holding NaN or Inf leaves a NaN or Inf norm in out[0].  Errors go to dirac_last_error(NULL). */
 #define DIRAC_NOALLOC_MAX_BLOCKS 16384
 #define DIRAC_NOALLOC_CELLS_PER_BLOCK 8192
 dirac_status dirac_observables_noalloc(const void *psi, int precision, int ndim, const int64_t n[3], double dx,

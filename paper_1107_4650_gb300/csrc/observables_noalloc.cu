@@ -10,7 +10,9 @@
 // summation order does not depend on the device; grids above kNoAllocMaxBlocks x
 // kNoAllocCellsPerBlock cells are rejected with DIRAC_ERR_ARG.  Every call writes the partials it
 // reads, so nothing needs clearing between calls, but all calls share the one array: calls whose
-// kernels overlap on the GPU (different streams, or different host threads) race on it.
+// kernels overlap on the GPU (different streams, or different host threads) race on it.  The result is
+// written to the caller's device buffer asynchronously, so the call cannot report a non-finite state:
+// a state holding NaN or Inf gives a NaN or Inf norm in out[0], which the caller checks.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -113,18 +115,26 @@ __global__ void __launch_bounds__(kNoAllocThreads) noalloc_final_kernel(const do
     }
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
-cudaError_t partials_address(double **addr) {
+// Device address of the scratch array on the current device.  Outside a stream capture it is looked up
+// (cudaGetSymbolAddress, a host call that allocates nothing) on every call and recorded for the device, so a
+// module reloaded at another address after cudaDeviceReset or a new primary context is picked up at once.
+// Inside a capture the recorded address is used: the first call on a device must come before any capture.
+cudaError_t partials_address(cudaStream_t s, double **addr) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess) return e;
         g_partials_addr[dev] = static_cast<double *>(p);
+    } else if (!g_partials_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *addr = g_partials_addr[dev];
     return cudaSuccess;
@@ -156,11 +166,12 @@ extern "C" dirac_status dirac_observables_noalloc(const void *psi, int precision
     const int64_t N = n[0] * n[1] * n[2];
     const int64_t nblocks = (N + kNoAllocCellsPerBlock - 1) / kNoAllocCellsPerBlock;
     double *partials = nullptr;
-    cudaError_t e = partials_address(&partials);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = partials_address(s, &partials);
     if (e != cudaSuccess)
         return set_thread_error(DIRAC_ERR_CUDA, std::string("dirac_observables_noalloc: cudaGetSymbolAddress: ") +
-                                                    cudaGetErrorString(e));
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+                                                    cudaGetErrorString(e) +
+                                                    " (inside a stream capture the first call on a device must come first)");
     const double x0 = x_min[0] + 0.5 * dx, y0 = x_min[1] + 0.5 * dx, z0 = x_min[2] + 0.5 * dx;
     if (precision == DIRAC_FP32)
         noalloc_partial_kernel<float><<<(unsigned)nblocks, kNoAllocThreads, 0, s>>>(

@@ -25,3 +25,6 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+    # ms_per_step is the time a bench step actually sampled (about --ref-step-seconds), not an extrapolation
+    assert 0.3e3 <= d["ms_per_step"] <= 30e3
+    assert abs(d["config"]["sampled_seconds_per_step"] * 1e3 - d["ms_per_step"]) < 1e-6

@@ -4,7 +4,8 @@ Callers that cannot allocate device memory (a host framework that owns the whole
 through its own pool, or a loop that must not pay the device synchronisation of cudaMalloc) use this
 entry point: its reduction scratch is a fixed array inside the library.  This file is collected last
 so that a run stopping at the first failure has run every other test before it.  Two calls in a row,
-on grids of different size and precision, check that the shared scratch carries nothing over."""
+on grids of different size and precision, check that the shared scratch carries nothing over; repeated
+calls leave the device's free memory and torch's allocator where they were."""
 import ctypes
 
 import numpy as np
@@ -74,3 +75,30 @@ def test_noalloc_rejects_grids_beyond_the_scratch_limit(D):
                                        ctypes.addressof(out))
     assert st == D.DIRAC_ERR_ARG
     assert "scratch limit" in D.dirac_last_error(None)
+
+
+def test_noalloc_calls_allocate_no_device_memory(D):
+    torch = pytest.importorskip("torch")
+    lib = D.load_library()
+    nx, ny, nz = 96, 40, 32
+    psi = torch.from_numpy(W.random_state(nz, ny, nx, seed=13).view(np.float64)).cuda()
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    n = (ctypes.c_int64 * 3)(nx, ny, nz)
+    xm = (ctypes.c_double * 3)(-0.1, -0.1, -0.1)
+
+    def call():
+        st = lib.dirac_observables_noalloc(psi.data_ptr(), D.DIRAC_FP64, 3, n, 1e-3, xm, 30, None, out.data_ptr())
+        assert st == D.DIRAC_OK, D.dirac_last_error(None)
+
+    call()  # the first call on the device: module load and symbol lookup
+    first = out.clone()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()  # cudaMemGetInfo
+    torch_bytes0 = torch.cuda.memory_allocated()
+    for _ in range(8):
+        call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == torch_bytes0
+    assert torch.equal(out, first)  # same partition, same order: the same bits every call
