@@ -1,6 +1,6 @@
 """The oracle pins catch plausible mistakes: each mutant below is a copy of the oracle's C source with one
 planted error (a flipped sign, swapped neighbours, a dropped factor, a wrong component, a wrong phase
-sign, a flux sign), built into a temporary library; at least one pin check must reject it.  CPU only."""
+sign, a flux sign, a centroid or face off by a cell or an axis), built into a temporary library; at least one pin check must reject it.  CPU only."""
 import ctypes
 import os
 import subprocess
@@ -56,6 +56,10 @@ MUTANTS = {
     "fx_strang_order": ("        fx_sweep_z(q, t, n, periodic, 1);\n        fx_sweep_x(t, q, n, periodic, 1);\n    }",
                         "        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 1);\n    }"),
     "fx_strang3d_final_rounding": ("q_d[e] = (q_d[e] + 8) >> 4;", "q_d[e] = (q_d[e] + 0) >> 4;"),
+    "centroid_half_cell": ("sx += (x_min[0] + (i + 0.5) * dx) * rho;", "sx += (x_min[0] + i * dx) * rho;"),
+    "centroid_y_index": ("sy += (x_min[1] + (j + 0.5) * dx) * rho;", "sy += (x_min[1] + (k + 0.5) * dx) * rho;"),
+    "norm_right_off_by_one": ("if (flux_face >= 0 && i >= flux_face) sr += rho;",
+                              "if (flux_face >= 0 && i > flux_face) sr += rho;"),
     "fx_strang3d_shift": ("        fx_sweep_y(t, q, n, periodic, 2);\n        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 2);",
                           "        fx_sweep_y(t, q, n, periodic, 1);\n        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 2);"),
 }
@@ -196,6 +200,13 @@ def _pins_pass():
     ok &= A.rel_l2(got, want) < 1e-13
     q = rng.integers(-(1 << 40), 1 << 40, size=(6, 7, 5, 4, 2), dtype=np.int64)
     ok &= np.array_equal(oracle.step_strang3d_fx(q, 0.0, C, DX, 2, periodic=True), _fx_strang3d_free_periodic(q, 2))
+    # observables of a one-cell 3-D state: norm, centroid = the cell's centre, norm right of the face
+    psi = np.zeros((7, 6, 8, 4), np.complex128)
+    psi[2, 3, 4] = [0.5 + 0.25j, -0.75j, 1.0, 0.5]
+    for face, right in ((4, True), (5, False)):
+        o = oracle.observables(psi, 3, 0.25, (-1.0, 0.5, 2.0), flux_face=face)
+        ok &= o["norm"] == 2.125 * 0.25 ** 3 and o["norm_right"] == (o["norm"] if right else 0.0)
+        ok &= max(abs(a - b) for a, b in zip(o["centroid"], (-1.0 + 4.5 * 0.25, 0.5 + 3.5 * 0.25, 2.0 + 2.5 * 0.25))) < 1e-15
     return bool(ok)
 
 

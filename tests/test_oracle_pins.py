@@ -243,6 +243,93 @@ def test_observables_invariants(oracle_mod):
     assert o["norm_right"] == o["norm"]
 
 
+def _continuum_velocity_x(psi0, dx):
+    """<v_x> = sum_p |phi(p)|^2 c^2 p_x / E(p) / sum_p |phi(p)|^2 of a positive-energy packet (the free Dirac
+    velocity c alpha_x in a positive-energy eigenstate is c^2 p / E), over the periodic box's DFT modes."""
+    nz, _, nx, _ = psi0.shape
+    hat = np.fft.fft2(psi0[:, 0], axes=(0, 1))
+    w = (np.abs(hat) ** 2).sum(-1)
+    PX, PZ = np.meshgrid(2 * np.pi * np.fft.fftfreq(nx, d=dx), 2 * np.pi * np.fft.fftfreq(nz, d=dx))
+    E = np.sqrt((C * PX) ** 2 + (C * PZ) ** 2 + (M * C * C) ** 2)
+    return float((w * C * C * PX / E).sum() / w.sum())
+
+
+def _oracle_centroid_velocity(nx, nz, dx, nsteps):
+    psi0 = W.positive_energy_packet_2d(nx, nz, dx, 20 * W.DX_DEFAULT, 0.5 * M * C)
+    x_min = (-nx * dx / 2, 0.0, -nz * dx / 2)
+    x0 = oracle.observables(psi0, 2, dx, x_min)["centroid"][0]
+    out, _ = oracle.step(psi0, 2, M, C, dx, nsteps, periodic=True)
+    x1 = oracle.observables(out, 2, dx, x_min)["centroid"][0]
+    return (x1 - x0) / (nsteps * dx / C), _continuum_velocity_x(psi0, dx)
+
+
+def test_config1_centroid_velocity_against_continuum(oracle_mod):
+    """The free packet of width 20 dx with p0 = 0.5 mc (the 256^2 workload, here in a box twice as long in x so
+    that the packet does not reach the periodic wrap in 200 steps) moves at the continuum velocity
+    int |phi(p)|^2 c^2 p / E(p) dp = 0.4346 c to within 1.5 % (measured 1.0 %: the discrete dispersion
+    cos(w dt) = cos(mu) cos(k dx) bends the group velocity at k0 dx = 0.08, mu = 0.17, Sec. 3), and that error
+    falls at least threefold when dx and dt halve over the same box and time (the dispersion error is of
+    second order in dt; measured 5x).  A sweep that moved a characteristic the wrong way, lost a component or
+    dropped the 1/2 would change the velocity by far more."""
+    dx = W.DX_DEFAULT
+    v, vc = _oracle_centroid_velocity(512, 256, dx, 200)
+    assert 0.40 * C < vc < 0.45 * C
+    e1 = abs(v / vc - 1.0)
+    assert e1 < 0.015, (v / C, vc / C)
+    v2, vc2 = _oracle_centroid_velocity(1024, 512, dx / 2, 400)
+    e2 = abs(v2 / vc2 - 1.0)
+    assert e2 < e1 / 3, (e1, e2)
+
+
+def test_config1_centroid_against_dft_exact_evolution(oracle_mod):
+    """On the 256^2 periodic grid the oracle's centroid after 200 steps equals the centroid of the mode-by-mode
+    Fourier evolution of the same scheme (Sec. 3.2), in x and z, to round-off."""
+    n, dx = 256, W.DX_DEFAULT
+    psi0 = W.positive_energy_packet_2d(n, n, dx, 20 * dx, 0.5 * M * C)
+    x_min = (-n * dx / 2, 0.0, -n * dx / 2)
+    got, _ = oracle.step(psi0, 2, M, C, dx, 200, periodic=True)
+    want = A.dft_exact_evolution_2d(psi0, 200, M * C * C * dx / C)
+    cg = oracle.observables(got, 2, dx, x_min)["centroid"]
+    cw = oracle.observables(np.ascontiguousarray(want), 2, dx, x_min)["centroid"]
+    assert abs(cg[0] - cw[0]) < 1e-12 * abs(cw[0])
+    assert abs(cg[2] - cw[2]) < 1e-12 * dx
+
+
+@pytest.mark.parametrize("cell", [(2, 3, 4), (0, 5, 1), (6, 0, 3), (1, 2, 0)])
+def test_observables_of_single_cell_states(oracle_mod, cell):
+    """A state non-zero in one cell (k, j, i) of a 3-D grid: norm = rho dx^3, centroid = that cell's centre
+    x_min + (index + 1/2) dx on every axis (Sec. 2.3), norm_right = norm exactly when i >= face and 0 when
+    i = face - 1.  A transposed axis, a missing half cell or an off-by-one at the face fails here."""
+    nz, ny, nx = 7, 6, 8
+    dx = 0.25
+    x_min = (-1.0, 0.5, 2.0)
+    k, j, i = cell
+    psi = np.zeros((nz, ny, nx, 4), np.complex128)
+    psi[k, j, i] = [0.5 + 0.25j, -0.75j, 1.0, 0.5]
+    rho = 0.25 + 0.0625 + 0.5625 + 1.0 + 0.25
+    for face in (i, i + 1, max(i - 1, 1), 1):
+        o = oracle.observables(psi, 3, dx, x_min, flux_face=face)
+        assert o["norm"] == rho * dx ** 3
+        want = [x_min[0] + (i + 0.5) * dx, x_min[1] + (j + 0.5) * dx, x_min[2] + (k + 0.5) * dx]
+        for d in range(3):
+            assert abs(o["centroid"][d] - want[d]) < 1e-15 * max(1.0, abs(want[d])), (d, o["centroid"], want)
+        assert o["norm_right"] == (o["norm"] if i >= face else 0.0), face
+
+
+def test_observables_two_cells_weighted_centroid(oracle_mod):
+    """Two cells of weights 1 and 3 in a 2-D (x-z) grid: the centroid is the weighted mean of their centres."""
+    nz, nx, dx = 5, 9, 0.5
+    x_min = (0.0, 0.0, -1.0)
+    psi = np.zeros((nz, 1, nx, 4), np.complex128)
+    psi[1, 0, 2, 0] = 1.0
+    psi[4, 0, 7, 3] = np.sqrt(3.0)
+    o = oracle.observables(psi, 2, dx, x_min, flux_face=5)
+    assert abs(o["norm"] - 4 * dx * dx) < 1e-15
+    assert abs(o["centroid"][0] - (1 * 2.5 + 3 * 7.5) * dx / 4) < 1e-14
+    assert abs(o["centroid"][2] - (-1.0 + (1 * 1.5 + 3 * 4.5) * dx / 4)) < 1e-14
+    assert abs(o["norm_right"] - 3 * dx * dx) < 1e-15
+
+
 # ---------------------------------------------------------------- Klein closed form
 
 def test_klein_worked_example_matches_printed_values():
