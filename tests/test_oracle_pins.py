@@ -388,16 +388,18 @@ def test_oracle_klein_run_converges_to_closed_form():
 # ---------------------------------------------------------------- Strang (second-order) splitting, 2-D
 
 @pytest.mark.parametrize("periodic", [False, True])
-def test_strang_step_equals_matrix_product(oracle_mod, periodic):
-    """One Strang step = S_x S_z D(2 dx/c) S_z S_x (Sec. 2.4, B omitted, consecutive A merged)."""
-    shape = (6, 1, 5)
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_strang_step_equals_matrix_product(oracle_mod, periodic, K):
+    """One Strang step = S_x S_z D(2 K dx/c) S_z S_x (Sec. 2.4, B omitted, consecutive A merged), each sweep
+    moving the characteristics K cells (c dt / 2 = K dx, Sec. 2.3)."""
+    shape = (8, 1, 7)  # wider than 2K: a shift does not wrap onto itself
     nx, ny, nz = shape
-    psi = W.random_state(nz, ny, nx, seed=41)
+    psi = W.random_state(nz, ny, nx, seed=41 + K)
     V = np.random.default_rng(42).uniform(-3e4, 3e4, nx)
-    got, _ = oracle.step_strang2d(psi, M, C, W.DX_DEFAULT, 1, V=V, periodic=periodic)
-    Sx = A.sweep_matrix(shape, 0, periodic)
-    Sz = A.sweep_matrix(shape, 2, periodic)
-    Dm = A.phase_matrix(shape, M, C, 2 * W.DX_DEFAULT / C, np.tile(V, nz))
+    got, _ = oracle.step_strang2d(psi, M, C, W.DX_DEFAULT, 1, V=V, periodic=periodic, shift=K)
+    Sx = A.sweep_matrix(shape, 0, periodic, shift=K)
+    Sz = A.sweep_matrix(shape, 2, periodic, shift=K)
+    Dm = A.phase_matrix(shape, M, C, 2 * K * W.DX_DEFAULT / C, np.tile(V, nz))
     want = Sx @ Sz @ Dm @ Sz @ Sx @ psi.reshape(-1)
     assert np.max(np.abs(got.reshape(-1) - want)) < 5e-15
 
@@ -683,6 +685,30 @@ def test_strang3d_step_equals_matrix_product(oracle_mod, periodic, K):
     Dm = A.phase_matrix(shape, M, C, 4 * K * W.DX_DEFAULT / C, V)
     want = Ax @ By @ Ax @ Cz @ Dm @ Cz @ Ax @ By @ Ax @ psi.reshape(-1)
     assert np.max(np.abs(got.reshape(-1) - want)) < 5e-15
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("K", [2, 3])
+def test_3d_step_with_shift_equals_matrix_product(oracle_mod, periodic, K):
+    """One first-order 3-D step with c dt = K dx (Sec. 2.3) = D(K dx / c) S_z S_y S_x, every sweep moving the
+    characteristics K cells, as explicit matrices; face flux over the K cells each side of the face."""
+    shape = (7, 8, 9)
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=61 + K)
+    V = np.random.default_rng(62).uniform(-3e4, 3e4, nx * ny * nz)
+    got, _ = oracle.step(psi, 3, M, C, W.DX_DEFAULT, 1, V=V, periodic=periodic, shift=K)
+    Sx, Sy, Sz = (A.sweep_matrix(shape, a, periodic, shift=K) for a in range(3))
+    Dm = A.phase_matrix(shape, M, C, K * W.DX_DEFAULT / C, V)
+    want = Dm @ Sz @ Sy @ Sx @ psi.reshape(-1)
+    assert np.max(np.abs(got.reshape(-1) - want)) < 5e-15
+    if not periodic:
+        face = 4
+        psi[:, :, nx - K:] = 0.0  # nothing leaves through the right edge: the right of the face gains exactly F
+        _, F = oracle.step(psi, 3, M, C, W.DX_DEFAULT, 1, V=V, flux_face=face, shift=K)
+        before = (np.abs(psi[:, :, face:]) ** 2).sum()
+        after = (np.abs((Sx @ psi.reshape(-1)).reshape(psi.shape)[:, :, face:]) ** 2).sum()
+        assert abs(F - (after - before) * W.DX_DEFAULT ** 3) < 1e-13 * W.DX_DEFAULT ** 3 * max(before, after)
+        assert F > 0
 
 
 def test_strang3d_second_order_convergence_to_continuum(oracle_mod):
