@@ -71,6 +71,8 @@ def _load():
         lib.oracle_set_vector_potential.restype = None
         lib.oracle_set_shift.argtypes = [ctypes.c_int64]
         lib.oracle_set_shift.restype = None
+        lib.oracle_set_field.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_set_field.restype = None
         _lib = lib
     return _lib
 
@@ -168,9 +170,38 @@ class _VectorPotential:
         _load().oracle_set_vector_potential(None, 0, 0)
 
 
+class _Field:
+    """Context: a separable space-time field (a, w, F) or None.  a: 3 values per cell (the profile of e A,
+    [z][y][x][d]) or None; w: 1 value per cell (the profile of the time-dependent part of V) or None; F: (nt, 4)
+    per-step integrals (F_x, F_y, F_z, F_V) of the envelopes; step s of a call uses row step0 + s."""
+    def __init__(self, field, step0, ncells):
+        self.field = field
+        self.step0 = int(step0)
+        if field is None:
+            return
+        a, w, F = field
+        self.a = None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        self.w = None if w is None else np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+        self.F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 4)
+        if self.a is not None and self.a.size != 3 * ncells:
+            raise ValueError("the field profile a needs 3 values per cell")
+        if self.w is not None and self.w.size != ncells:
+            raise ValueError("the field profile w needs 1 value per cell")
+
+    def __enter__(self):
+        if self.field is not None:
+            _load().oracle_set_field(None if self.a is None else self.a.ctypes.data,
+                                     None if self.w is None else self.w.ctypes.data, self.F.ctypes.data,
+                                     self.F.shape[0], self.step0)
+        return self
+
+    def __exit__(self, *exc):
+        _load().oracle_set_field(None, None, None, 0, 0)
+
+
 def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
          periodic: bool = False, flux_face: int = -1, flux_cum: float = 0.0, absorber=None,
-         A_tilde=None, step0: int = 0, shift: int = 1):
+         A_tilde=None, step0: int = 0, shift: int = 1, field=None):
     """nsteps first-order split steps (Eqs. split1-4 discretised as sol_dis_1-4), dt = dx/c.
 
     Returns (psi_out, flux_cum): the cumulative probability carried across the x face
@@ -179,11 +210,14 @@ def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
     `A_tilde`: optional (nt, 3) array of uniform vector-potential integrals e int A dt per step (Eq. field_dis1);
     step s of this call uses row step0 + s, and the phase is the full matrix of Eq. sol_dis_4.
     `shift`: characteristic shift K, c dt = K dx (Sec. 2.3): dt = K dx / c and neighbours at +-K cells.
+    `field`: optional separable space-time field (a, w, F) (see _Field): per cell and step the phase matrix of
+    Eq. sol_dis_4 with At(i) = F_xyz a(i) and V~(i) = V(i) dt + F_V w(i) (Eqs. field_dis1, field_dis2).
     """
     out = _as_state(psi)
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    with _Absorber(absorber, out.shape[2]), _VectorPotential(A_tilde, step0), _Shift(shift):
+    with _Absorber(absorber, out.shape[2]), _VectorPotential(A_tilde, step0), _Shift(shift), \
+            _Field(field, step0, out.size // 4):
         rc = _load().oracle_step(out.ctypes.data, _dims(out), int(ndim), int(bool(periodic)), float(m), float(c),
                                  float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
                                  int(flux_face), ctypes.addressof(fc))
@@ -195,16 +229,18 @@ def step(psi, ndim: int, m: float, c: float, dx: float, nsteps: int, V=None,
 
 
 def step_strang2d(psi, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False,
-                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1, A_tilde=None, step0: int = 0):
+                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1, A_tilde=None, step0: int = 0,
+                  field=None):
     """nsteps second-order (Strang) steps in the x-z plane (Sec. 2.4): x, z, phase(dt), z, x with
-    dt = 2 dx / c.  A_tilde / step0: a uniform vector potential as in step() (the phase matrix over dt).
+    dt = 2 dx / c.  A_tilde / step0: a uniform vector potential as in step() (the phase matrix over dt); field:
+    a separable space-time field as in step(), its integrals spanning the whole step.
     Returns (psi_out, flux_cum) as step()."""
     out = _as_state(psi)
     if out.shape[1] != 1:
         raise ValueError("Strang steps are 2-D (ny = 1)")
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    with _Shift(shift), _VectorPotential(A_tilde, step0):
+    with _Shift(shift), _VectorPotential(A_tilde, step0), _Field(field, step0, out.size // 4):
         rc = _load().oracle_step_strang2d(out.ctypes.data, _dims(out), int(bool(periodic)), float(m), float(c),
                                           float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
                                           int(flux_face), ctypes.addressof(fc))
@@ -216,15 +252,17 @@ def step_strang2d(psi, m: float, c: float, dx: float, nsteps: int, V=None, perio
 
 
 def step_strang3d(psi, m: float, c: float, dx: float, nsteps: int, V=None, periodic: bool = False,
-                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1, A_tilde=None, step0: int = 0):
+                  flux_face: int = -1, flux_cum: float = 0.0, shift: int = 1, A_tilde=None, step0: int = 0,
+                  field=None):
     """nsteps second-order (Strang) steps in 3-D (Sec. 2.4): A(dt/4) B(dt/2) A(dt/4) C(dt/2) D(dt) C(dt/2)
     A(dt/4) B(dt/2) A(dt/4) with c dt / 4 = shift * dx: x sweeps move `shift` cells, y and z sweeps 2 shift.
-    A_tilde / step0: a uniform vector potential as in step() (the phase matrix over dt).
+    A_tilde / step0: a uniform vector potential as in step() (the phase matrix over dt); field: a separable
+    space-time field as in step(), its integrals spanning the whole step.
     Returns (psi_out, flux_cum) as step()."""
     out = _as_state(psi)
     Varr, layout = _potential(V, out)
     fc = ctypes.c_double(flux_cum)
-    with _Shift(shift), _VectorPotential(A_tilde, step0):
+    with _Shift(shift), _VectorPotential(A_tilde, step0), _Field(field, step0, out.size // 4):
         rc = _load().oracle_step_strang3d(out.ctypes.data, _dims(out), int(bool(periodic)), float(m), float(c),
                                           float(dx), None if Varr is None else Varr.ctypes.data, layout, int(nsteps),
                                           int(flux_face), ctypes.addressof(fc))

@@ -243,6 +243,18 @@ static void u_matrix(double mu, const double At[3], cplx U[4][4]) {
     U[1][2].re = -ay; U[1][2].im = ax;  U[3][0].re = -ay; U[3][0].im = ax;
 }
 
+/* q <- M q for one cell with M = U g: each entry multiplied by g first (complex product), then
+ * q'_a = sum_b M_ab q_b over b = 1..4 in order, accumulated with c_mac from zero. */
+static void apply_ug(cplx *q, cplx U[4][4], cplx g) {
+    cplx o[4];
+    for (int a = 0; a < 4; ++a) {
+        cplx acc = {0.0, 0.0};
+        for (int b = 0; b < 4; ++b) acc = c_mac(acc, q[b], c_mul(U[a][b], g));
+        o[a] = acc;
+    }
+    for (int a = 0; a < 4; ++a) q[a] = o[a];
+}
+
 /* Eq. sol_dis_4 with a uniform vector potential: psi <- (U exp(-i V dt)) psi per cell, the scalar factor
  * g = (cos(V dt), -sin(V dt)) (times the absorbing-layer factor when one is set) multiplied into every
  * entry first (M = U g as a complex product), then psi'_a = sum_b M_ab psi_b over b = 1..4 in order,
@@ -263,16 +275,72 @@ static int oracle_phase_A(double *psi_d, const int64_t n[3], double m, double c,
                     g.re = g.re * g_absorb[i];
                     g.im = g.im * g_absorb[i];
                 }
-                cplx *q = psi + ((k * n[1] + j) * n[0] + i) * 4;
-                cplx o[4];
-                for (int a = 0; a < 4; ++a) {
-                    cplx acc = {0.0, 0.0};
-                    for (int b = 0; b < 4; ++b) acc = c_mac(acc, q[b], c_mul(U[a][b], g));
-                    o[a] = acc;
-                }
-                for (int a = 0; a < 4; ++a) q[a] = o[a];
+                apply_ug(psi + ((k * n[1] + j) * n[0] + i) * 4, U, g);
             }
     return 0;
+}
+
+/* Fields that vary in space and time (Sec. 2.3: the phase matrix U(i) of Eq. sol_dis_4 built from the field
+ * integral At(i) of Eq. field_dis1 at each cell, and the scalar integral V~(i) of Eq. field_dis2), for fields
+ * of the separable form
+ *   e A_d(t, x) = f_d(t) a_d(x)  (d = x, y, z)   and   V(t, x) = V(x) + f_V(t) w(x),
+ * whose integrals over step n are exactly  At_d(i) = F_d a_d(i)  and  V~(i) = V(i) dt + F_V w(i)  with
+ * F = (F_x, F_y, F_z, F_V) the integrals of the envelopes over the step (supplied by the caller: row
+ * step0 + s of its table for step s of a call) and the profiles a (3 per cell, [z][y][x][d]) and w (1 per
+ * cell).  A NULL profile is zero.  Per cell: psi <- (U(At(i)) g) psi with g = (cos V~, -sin V~) (times the
+ * absorber factor), U and the product as for the uniform field. */
+static const double *g_fa = NULL, *g_fw = NULL, *g_fenv = NULL;
+static int64_t g_fenv_n = 0, g_fenv_step0 = 0;
+
+void oracle_set_field(const double *a, const double *w, const double *F, int64_t nsteps_table, int64_t step0) {
+    g_fa = a;
+    g_fw = w;
+    g_fenv = F;
+    g_fenv_n = nsteps_table;
+    g_fenv_step0 = step0;
+}
+
+static int oracle_phase_field(double *psi_d, const int64_t n[3], double m, double c, double dt,
+                              const double *V, int layout, const double F[4]) {
+    cplx *psi = (cplx *)psi_d;
+    const double mu = m * c * c * dt;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i) {
+                const int64_t cidx = (k * n[1] + j) * n[0] + i;
+                double At[3] = {0.0, 0.0, 0.0};
+                if (g_fa)
+                    for (int d = 0; d < 3; ++d) At[d] = F[d] * g_fa[3 * cidx + d];
+                double vt = potential(V, layout, n, i, j, k) * dt;
+                if (g_fw) vt = vt + F[3] * g_fw[cidx];
+                cplx U[4][4];
+                u_matrix(mu, At, U);
+                cplx g = {cos(vt), -sin(vt)};
+                if (g_absorb) {
+                    g.re = g.re * g_absorb[i];
+                    g.im = g.im * g_absorb[i];
+                }
+                apply_ug(psi + cidx * 4, U, g);
+            }
+    return 0;
+}
+
+/* The phase sub-step of step s of a call: the space-time field when one is set, else the uniform vector
+ * potential when one is set, else Eq. sol_dis_4 at A = 0.  Returns -2 when the field's table ends before it. */
+static int phase_step(double *psi, const int64_t n[3], double m, double c, double dt, const double *V, int layout,
+                      int64_t s) {
+    if (g_fenv) {
+        const int64_t t = g_fenv_step0 + s;
+        if (t < 0 || t >= g_fenv_n) return -2;
+        return oracle_phase_field(psi, n, m, c, dt, V, layout, g_fenv + 4 * t);
+    }
+    if (g_avec) {
+        const int64_t t = g_avec_step0 + s;
+        if (t < 0 || t >= g_avec_n) return -2;
+        return oracle_phase_A(psi, n, m, c, dt, V, layout, g_avec + 3 * t);
+    }
+    return oracle_phase(psi, n, m, c, dt, V, layout);
 }
 
 /* nsteps steps of the first-order splitting, Eqs. split1-split4 in the discrete
@@ -289,13 +357,7 @@ int oracle_step(double *psi, const int64_t n[3], int ndim, int periodic, double 
         if (oracle_sweep(psi, n, 0, periodic)) return -1;
         if (ndim == 3 && oracle_sweep(psi, n, 1, periodic)) return -1;
         if (oracle_sweep(psi, n, 2, periodic)) return -1;
-        if (g_avec) {
-            const int64_t t = g_avec_step0 + s;
-            if (t < 0 || t >= g_avec_n) return -2;
-            oracle_phase_A(psi, n, m, c, dt, V, layout, g_avec + 3 * t);
-        } else {
-            oracle_phase(psi, n, m, c, dt, V, layout);
-        }
+        if (phase_step(psi, n, m, c, dt, V, layout, s)) return -2;
     }
     return 0;
 }
@@ -502,13 +564,8 @@ int oracle_step_strang2d(double *psi, const int64_t n[3], int periodic, double m
         if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
         if (oracle_sweep(psi, n, 0, periodic)) return -1;
         if (oracle_sweep(psi, n, 2, periodic)) return -1;
-        if (g_avec) {  /* uniform vector potential: the full phase matrix over the whole step dt */
-            const int64_t t = g_avec_step0 + s;
-            if (t < 0 || t >= g_avec_n) return -2;
-            oracle_phase_A(psi, n, m, c, dt, V, layout, g_avec + 3 * t);
-        } else {
-            oracle_phase(psi, n, m, c, dt, V, layout);
-        }
+        /* a field's phase matrix spans the whole step dt */
+        if (phase_step(psi, n, m, c, dt, V, layout, s)) return -2;
         if (oracle_sweep(psi, n, 2, periodic)) return -1;
         if (flux_face >= 0 && flux_cum) *flux_cum += face_flux((const cplx *)psi, n, periodic, flux_face, vol);
         if (oracle_sweep(psi, n, 0, periodic)) return -1;
@@ -528,14 +585,8 @@ int oracle_step_strang3d(double *psi, const int64_t n[3], int periodic, double m
     for (int64_t s = 0; s < nsteps; ++s) {
         for (int q = 0; q < 9; ++q) {
             const int ax = axes[q];
-            if (ax < 0) {
-                if (g_avec) {  /* uniform vector potential: the full phase matrix over the whole step dt */
-                    const int64_t t = g_avec_step0 + s;
-                    if (t < 0 || t >= g_avec_n) return -2;
-                    oracle_phase_A(psi, n, m, c, dt, V, layout, g_avec + 3 * t);
-                } else {
-                    oracle_phase(psi, n, m, c, dt, V, layout);
-                }
+            if (ax < 0) {  /* a field's phase matrix spans the whole step dt */
+                if (phase_step(psi, n, m, c, dt, V, layout, s)) return -2;
                 continue;
             }
             if (ax == 0 && flux_face >= 0 && flux_cum)

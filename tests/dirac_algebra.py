@@ -156,3 +156,16 @@ def continuum_evolution_3d(psi0: np.ndarray, dx: float, t: float, m: float, c: f
     hat = np.fft.fftn(psi0, axes=(0, 1, 2))
     hat = np.einsum("zyxab,zyxb->zyxa", U, hat)
     return np.fft.ifftn(hat, axes=(0, 1, 2))
+
+
+def phase_matrix_field(n, m, c, dt, vt_cells, At_cells) -> np.ndarray:
+    """Block-diagonal exp(-i beta m c^2 dt - i V~(i) + i alpha.At(i)) per cell (scipy's matrix exponential of
+    each cell's 4x4 generator); vt_cells: V~ per cell, At_cells: (ncells, 3), cells in flattened order."""
+    from scipy.linalg import expm
+    nx, ny, nz = n
+    N = nx * ny * nz
+    M = np.zeros((4 * N, 4 * N), dtype=np.complex128)
+    for o in range(N):
+        G = -1j * (m * c * c * dt) * BETA - 1j * vt_cells[o] * I4 + 1j * sum(a * Al for a, Al in zip(At_cells[o], ALPHA))
+        M[4 * o:4 * o + 4, 4 * o:4 * o + 4] = expm(G)
+    return M

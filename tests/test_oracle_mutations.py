@@ -60,6 +60,11 @@ MUTANTS = {
     "centroid_y_index": ("sy += (x_min[1] + (j + 0.5) * dx) * rho;", "sy += (x_min[1] + (k + 0.5) * dx) * rho;"),
     "norm_right_off_by_one": ("if (flux_face >= 0 && i >= flux_face) sr += rho;",
                               "if (flux_face >= 0 && i > flux_face) sr += rho;"),
+    "field_profile_component": ("for (int d = 0; d < 3; ++d) At[d] = F[d] * g_fa[3 * cidx + d];",
+                                "for (int d = 0; d < 3; ++d) At[d] = F[d] * g_fa[3 * cidx];"),
+    "field_scalar_envelope": ("if (g_fw) vt = vt + F[3] * g_fw[cidx];", "if (g_fw) vt = vt + F[2] * g_fw[cidx];"),
+    "field_step_row": ("return oracle_phase_field(psi, n, m, c, dt, V, layout, g_fenv + 4 * t);",
+                       "return oracle_phase_field(psi, n, m, c, dt, V, layout, g_fenv + 4 * s);"),
     "fx_strang3d_shift": ("        fx_sweep_y(t, q, n, periodic, 2);\n        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 2);",
                           "        fx_sweep_y(t, q, n, periodic, 1);\n        fx_sweep_x(q, t, n, periodic, 1);\n        fx_sweep_z(t, q, n, periodic, 2);"),
 }
@@ -87,6 +92,8 @@ def _build_mutant(tmp_path, name, old, new):
     lib.oracle_step_strang2d.argtypes = lib.oracle_step_strang3d.argtypes
     lib.oracle_set_shift.argtypes = [ctypes.c_int64]
     lib.oracle_set_shift.restype = None
+    lib.oracle_set_field.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64]
+    lib.oracle_set_field.restype = None
     lib.oracle_step_fx.argtypes = [P, oracle.I64_3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, P, ctypes.c_int, ctypes.c_int64]
     lib.oracle_step_fx.restype = ctypes.c_int
@@ -200,6 +207,17 @@ def _pins_pass():
     ok &= A.rel_l2(got, want) < 1e-13
     q = rng.integers(-(1 << 40), 1 << 40, size=(6, 7, 5, 4, 2), dtype=np.int64)
     ok &= np.array_equal(oracle.step_strang3d_fx(q, 0.0, C, DX, 2, periodic=True), _fx_strang3d_free_periodic(q, 2))
+    # a field varying from cell to cell: one step against the per-cell matrix exponentials (table row 1)
+    shape = (5, 1, 4)
+    psi = W.random_state(4, 1, 5, seed=104)
+    rng = np.random.default_rng(105)
+    Vf = rng.uniform(-3e4, 3e4, 20)
+    a, w, F = rng.uniform(-1, 1, (20, 3)), rng.uniform(-2, 2, 20), rng.uniform(-1, 1, (3, 4))
+    got, _ = oracle.step(psi, 2, 1.0, C, DX, 1, V=Vf, field=(a, w, F), step0=1)
+    dtf = DX / C
+    want = A.phase_matrix_field(shape, 1.0, C, dtf, Vf * dtf + F[1, 3] * w, F[1, :3][None, :] * a) @ \
+        A.sweep_matrix(shape, 2, False) @ A.sweep_matrix(shape, 0, False) @ psi.reshape(-1)
+    ok &= np.max(np.abs(got.reshape(-1) - want)) < 5e-15
     # observables of a one-cell 3-D state: norm, centroid = the cell's centre, norm right of the face
     psi = np.zeros((7, 6, 8, 4), np.complex128)
     psi[2, 3, 4] = [0.5 + 0.25j, -0.75j, 1.0, 0.5]

@@ -828,6 +828,101 @@ def test_strang3d_with_vector_potential_equals_matrix_product(oracle_mod):
 
 # ---------------------------------------------------------------- 64-bit fixed-point evaluation (oracle_step_fx)
 
+# ---------------------------------------------------------------- fields varying in space and time
+
+def _field(ncells, nt, seed, a_scale=1.0, w_scale=2.0):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-1.0, 1.0, (ncells, 3)) * a_scale
+    w = rng.uniform(-1.0, 1.0, ncells) * w_scale
+    F = rng.uniform(-1.0, 1.0, (nt, 4))
+    return a, w, F
+
+
+@pytest.mark.parametrize("ndim,shape", [(2, (6, 1, 5)), (3, (4, 3, 3))])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_field_step_equals_matrix_product(oracle_mod, ndim, shape, periodic):
+    """One first-order step with a field that varies from cell to cell (Sec. 2.3, Eqs. sol_dis_4, field_dis1,
+    field_dis2): D S_z (S_y) S_x with D block-diagonal, each block the matrix exponential of
+    -i beta m c^2 dt - i V~(i) + i alpha.At(i), At(i) = F_xyz a(i), V~(i) = V(i) dt + F_V w(i)."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    psi = W.random_state(nz, ny, nx, seed=71)
+    V = np.random.default_rng(72).uniform(-3e4, 3e4, N)
+    a, w, F = _field(N, 3, 73)
+    dt = W.DX_DEFAULT / C
+    got, _ = oracle.step(psi, ndim, M, C, W.DX_DEFAULT, 1, V=V, periodic=periodic, field=(a, w, F), step0=1)
+    S = A.sweep_matrix(shape, 0, periodic)
+    if ndim == 3:
+        S = A.sweep_matrix(shape, 1, periodic) @ S
+    S = A.sweep_matrix(shape, 2, periodic) @ S
+    Dm = A.phase_matrix_field(shape, M, C, dt, V * dt + F[1, 3] * w, F[1, :3][None, :] * a)
+    want = Dm @ S @ psi.reshape(-1)
+    assert np.max(np.abs(got.reshape(-1) - want)) < 5e-15
+
+
+@pytest.mark.parametrize("strang", [False, True])
+def test_field_strang_steps_equal_matrix_products(oracle_mod, strang):
+    """Second-order steps with a cell field: 2-D S_x S_z D(2 dx/c) S_z S_x and 3-D A B A C D(4 dx/c) C A B A, the
+    field's integrals spanning the whole step (Sec. 2.4)."""
+    rng = np.random.default_rng(74)
+    for ndim, shape in ((2, (7, 1, 6)), (3, (5, 7, 6))):
+        nx, ny, nz = shape
+        N = nx * ny * nz
+        psi = W.random_state(nz, ny, nx, seed=75 + ndim)
+        V = rng.uniform(-3e4, 3e4, N)
+        a, w, F = _field(N, 2, 76 + ndim)
+        if ndim == 2:
+            dt = 2 * W.DX_DEFAULT / C
+            got, _ = oracle.step_strang2d(psi, M, C, W.DX_DEFAULT, 1, V=V, field=(a, w, F))
+            Sx, Sz = A.sweep_matrix(shape, 0, False), A.sweep_matrix(shape, 2, False)
+            Dm = A.phase_matrix_field(shape, M, C, dt, V * dt + F[0, 3] * w, F[0, :3][None, :] * a)
+            want = Sx @ Sz @ Dm @ Sz @ Sx @ psi.reshape(-1)
+        else:
+            dt = 4 * W.DX_DEFAULT / C
+            got, _ = oracle.step_strang3d(psi, M, C, W.DX_DEFAULT, 1, V=V, periodic=True, field=(a, w, F))
+            Ax, By, Cz = (A.sweep_matrix(shape, 0, True), A.sweep_matrix(shape, 1, True, shift=2),
+                          A.sweep_matrix(shape, 2, True, shift=2))
+            Dm = A.phase_matrix_field(shape, M, C, dt, V * dt + F[0, 3] * w, F[0, :3][None, :] * a)
+            want = Ax @ By @ Ax @ Cz @ Dm @ Cz @ Ax @ By @ Ax @ psi.reshape(-1)
+        assert np.max(np.abs(got.reshape(-1) - want)) < 5e-15, ndim
+
+
+def test_field_with_unit_profile_is_the_uniform_vector_potential(oracle_mod):
+    """a(i) = (1, 1, 1) in every cell and w = 0: the cell field is the uniform field At^n = (F_x, F_y, F_z)^n,
+    bit for bit (same closed form, same products)."""
+    nx, nz = 11, 9
+    psi = W.random_state(nz, 1, nx, seed=77)
+    V = np.random.default_rng(78).uniform(-3e4, 3e4, nx)
+    rng = np.random.default_rng(79)
+    F = np.zeros((5, 4))
+    F[:, :3] = rng.uniform(-1.5, 1.5, (5, 3))
+    ones = np.ones((nz * nx, 3))
+    got, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 5, V=V, field=(ones, None, F))
+    want, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 5, V=V, A_tilde=F[:, :3])
+    assert np.array_equal(got.view(np.float64), want.view(np.float64))
+
+
+def test_time_dependent_uniform_potential_is_a_global_phase(oracle_mod):
+    """V(t, x) = V(x) + f_V(t) with w = 1: the extra potential is uniform in space, commutes with every sub-step
+    and multiplies the state by exp(-i sum_n F_V^n) (Eq. field_dis2 integrated step by step)."""
+    nx, nz = 24, 20
+    psi = W.random_state(nz, 1, nx, seed=80)
+    V = np.random.default_rng(81).uniform(-3e4, 3e4, nx)
+    F = np.zeros((30, 4))
+    F[:, 3] = np.random.default_rng(82).uniform(-0.8, 0.8, 30)
+    ones = np.ones(nz * nx)
+    got, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 30, V=V, periodic=True, field=(None, ones, F))
+    ref, _ = oracle.step(psi, 2, M, C, W.DX_DEFAULT, 30, V=V, periodic=True)
+    assert A.rel_l2(got, ref * np.exp(-1j * F[:, 3].sum())) < 1e-13
+    assert A.rel_l2(got, ref) > 0.1  # the phase is not trivial
+
+
+def test_field_table_end_is_an_error(oracle_mod):
+    psi = W.random_state(4, 1, 5, seed=83)
+    with pytest.raises(ValueError):
+        oracle.step(psi, 2, M, C, W.DX_DEFAULT, 3, field=(None, None, np.zeros((2, 4))))
+
+
 def _fx_step_bigint(q, P_up, P_dn, periodic):
     """One fixed-point 2-D step with exact Python integers (brute force): sweeps of Eqs. sol_dis_1 and
     sol_dis_3 without the 1/2, then each component's exact product with the per-column coefficients
