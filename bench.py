@@ -74,7 +74,11 @@ def parse():
     ap.add_argument("--no-field", action="store_true")
     ap.add_argument("--no-2d-variants", action="store_true", help="skip the 2-D Strang and shift legs")
     ap.add_argument("--no-3d", action="store_true")
-    ap.add_argument("--no-paper-klein", action="store_true")
+    ap.add_argument("--paper-klein", action="store_true",
+                    help="also run the paper's full 24576 x 8192 Klein experiment in FP32 (about 40 s)")
+    ap.add_argument("--no-config3", action="store_true", help="skip the 384^3 x 1000-step soft-Coulomb sweep over Z")
+    ap.add_argument("--config3-steps", type=int, default=1000)
+    ap.add_argument("--config3-z", default="1,2,5,10,20")
     ap.add_argument("--side3d", type=int, default=384)
     ap.add_argument("--batch-runs", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true")
@@ -430,7 +434,8 @@ def main():
     D.dirac_step(h, args.nsteps)
     D.dirac_get_state(h, fp64_final)
     stream.synchronize()
-    fp64_flux = D.dirac_observables(h)["flux_cum"]
+    obs_final = D.dirac_observables(h)
+    fp64_flux, fp64_norm = obs_final["flux_cum"], obs_final["norm"]
     D.dirac_destroy(h)
     variants = {}
 
@@ -446,7 +451,8 @@ def main():
         fx_final = torch.empty_like(dev_state)
         D.dirac_get_state(hx, fx_final)
         stream.synchronize()
-        fx_flux = D.dirac_observables(hx)["flux_cum"]
+        obs_fx = D.dirac_observables(hx)
+        fx_flux = obs_fx["flux_cum"]
         D.dirac_destroy(hx)
         rel = float(torch.linalg.vector_norm(fx_final - fp64_final) / torch.linalg.vector_norm(fp64_final))
         del fx_final
@@ -457,10 +463,10 @@ def main():
             "hbm_frac": FP64_BYTES_PER_POINT_STEP * vx / world / 1e9 / hbm_peak,
             "rel_l2_vs_fp64_after_%d_steps" % args.nsteps: rel,
             "flux_rel_diff_vs_fp64": abs(fx_flux - fp64_flux) / abs(fp64_flux) if fp64_flux else None,
+            "norm_drift_vs_fp64": obs_fx["norm"] - fp64_norm, "dT_vs_fp64": (fx_flux - fp64_flux) / n0,
             "speedup_vs_fp64": vx / value,
             "workload": "the headline 2-D Klein run, 64-bit fixed-point storage (exact integer sweeps, phase "
                         "rounded once after a 128-bit product)"}
-    del fp64_final
 
     # ---------------------------------------------------------------- FP32 storage variant
     if not args.no_fp32:
@@ -472,6 +478,14 @@ def main():
         i32 = D.dirac_get_info(h32)
         t32, in32, _ = timed_device_run(h32, dev32, args.steps, 1)
         o32 = D.dirac_observables(h32)
+        # the state after the timed run is the FP32 state after the full nsteps from psi0: its distance from the
+        # FP64 state (bit-exact with the oracle) is the error FP32 storage adds
+        fin32 = torch.empty_like(dev32)
+        D.dirac_get_state(h32, fin32)
+        stream.synchronize()
+        fin32 = torch.view_as_real(torch.view_as_complex(fin32.view(-1, 2)).to(torch.complex128)).view(-1)
+        rel32 = float(torch.linalg.vector_norm(fin32 - fp64_final.view(-1)) / torch.linalg.vector_norm(fp64_final))
+        del fin32
         t32 = max_over_ranks(t32)
         k32 = i32["steps_per_launch"]
         launches32 = args.steps * (args.nsteps // k32 + args.nsteps % k32)
@@ -484,8 +498,13 @@ def main():
                             "step_kernel_algorithmic_gbs": FP32_BYTES_PER_POINT_STEP * ncell * k32 / mean32 / 1e9,
                             "traffic_per_launch": (MEASURED_TRAFFIC_PER_LAUNCH["fp32"].get((k32, i32["points_per_lane"]))
                                                    if args.side == 2048 else None),
-                            "T": o32["flux_cum"] / n0, "T_fp64": obs["flux_cum"] / n0}
+                            "T": o32["flux_cum"] / n0, "T_fp64": fp64_flux / n0,
+                            "error_vs_fp64_after_%d_steps" % args.nsteps: {
+                                "rel_l2_psi": rel32, "norm_drift": o32["norm"] - fp64_norm,
+                                "norm_fp32": o32["norm"], "norm_fp64": fp64_norm,
+                                "dT": (o32["flux_cum"] - fp64_flux) / n0}}
         D.dirac_destroy(h32)
+    del fp64_final
 
     # ---------------------------------------------------------------- FP64 with a laser field
     if not args.no_field:
@@ -649,8 +668,72 @@ def main():
             del dev3
         del ref3
 
+    # ---------------------------------------------------------------- config 3: 384^3 soft Coulomb, 1000 steps, Z sweep
+    if not args.no_config3 and not args.no_3d:
+        n3 = args.side3d
+        dx3 = W.DX_DEFAULT
+        zs = [float(z) for z in args.config3_z.split(",") if z.strip()]
+        nst = args.config3_steps
+        psi3 = W.gaussian_packet(n3, n3, dx3, -n3 * dx3 / 2, -n3 * dx3 / 2, 32 * dx3, 0.0, 16 * dx3, 0.0, ny=n3,
+                                 y_min=-n3 * dx3 / 2)
+        norm0 = float(np.sum(np.abs(psi3) ** 2) * dx3 ** 3)
+        per_z = {("%g" % z): {} for z in zs}
+        fp64_states = {}
+        timing = {}
+        precs = [(D.DIRAC_FP64, "fp64"), (D.DIRAC_FP32, "fp32")] + ([] if args.no_fx64 else [(D.DIRAC_FX64, "fx64")])
+        for prec, pname in precs:
+            wide = prec != D.DIRAC_FP32
+            dev3 = torch.from_numpy(psi3.astype(np.complex128 if wide else np.complex64)
+                                    .view(np.float64 if wide else np.float32)).to(f"cuda:{local}")
+            h3 = D.dirac_create_grid(D.make_config((n3, n3, n3), ndim=3, precision=prec, stream=stream.cuda_stream,
+                                                   device=local))
+            ms_total, plan3 = 0.0, None
+            for zi, Z in enumerate(zs):
+                D.dirac_set_potential(h3, W.soft_coulomb_3d(n3, dx3, Z, 2 * dx3).reshape(-1), D.DIRAC_V_FULL)
+                D.dirac_set_state(h3, dev3)
+                if zi == 0:
+                    D.dirac_autotune(h3)
+                    plan3 = D.dirac_get_info(h3)
+                ec0, ec1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                stream.synchronize()
+                ec0.record(stream)
+                D.dirac_step(h3, nst)
+                ec1.record(stream)
+                stream.synchronize()
+                ms_total += ec0.elapsed_time(ec1)
+                o3 = D.dirac_observables(h3)
+                fin = torch.empty_like(dev3)
+                D.dirac_get_state(h3, fin)
+                stream.synchronize()
+                if not wide:
+                    fin = torch.view_as_real(torch.view_as_complex(fin.view(-1, 2)).to(torch.complex128)).view(-1)
+                fin = fin.view(-1)
+                key = "%g" % Z
+                rec = {"norm_end": o3["norm"], "centroid": o3["centroid"]}
+                if prec == D.DIRAC_FP64:
+                    fp64_states[key] = (fin, o3["norm"])
+                    rec["norm_change_from_start"] = o3["norm"] - norm0
+                else:
+                    ref, ref_norm = fp64_states[key]
+                    rec["rel_l2_psi_vs_fp64"] = float(torch.linalg.vector_norm(fin - ref) / torch.linalg.vector_norm(ref))
+                    rec["norm_drift_vs_fp64"] = o3["norm"] - ref_norm
+                    del fin
+                per_z[key][pname] = rec
+            D.dirac_destroy(h3)
+            del dev3
+            timing[pname] = {"value": n3 ** 3 * nst * len(zs) * world / (max_over_ranks(ms_total) / 1e3),
+                             "unit": "point-steps/s", "plan": plan3["plan"],
+                             "steps_per_launch": plan3["steps_per_launch"], "points_per_lane": plan3["points_per_lane"]}
+        del fp64_states
+        variants["config3_coulomb%d_%d_steps" % (n3, nst)] = {
+            "workload": "%d^3 grid, V = -Z / sqrt(r^2 + (2 dx)^2) centred, spin-up Gaussian width 16 dx at rest "
+                        "offset +32 dx in x, zero boundary, %d first-order steps per Z; FP32 storage and 64-bit fixed "
+                        "point compared with the FP64 state (bit-exact with the oracle) after the same steps"
+                        % (n3, nst),
+            "norm_start": norm0, "per_Z": per_z, "rates": timing}
+
     # ---------------------------------------------------------------- the paper's own 2-D Klein run, FP32
-    if not args.no_paper_klein:
+    if args.paper_klein:
         from paper_1107_4650_gb300 import paper_klein2d as PK
         pk = PK.run("fp32", stream=stream, device=local)
         variants["paper_klein2d_fp32"] = {
