@@ -90,9 +90,23 @@ typedef struct {
                              state in memory is at a step boundary only between runs; 0 = library choice
                              (fused passes for FP32 storage, single sweeps for FP64) */
     int char_shift;       /* characteristic shift K of Sec. 2.3: c dt = K dx, each sweep moves the
-                             characteristics by K cells and dt = K dx / c.  0 or 1: the paper's K = 1;
-                             2, 3 or 4: 2-D first-order (DIRAC_LIE) grids without a vector potential,
-                             one step per launch */
+                             characteristics by K cells.  0 or 1: the paper's K = 1; 2, 3 or 4 (FP64 or FP32
+                             storage, one step per launch): 2-D first order (dt = K dx / c, the fused
+                             shift kernel), 3-D first order (dt = K dx / c) and 2-D second order
+                             (dt = 2 K dx / c) as single-sweep launches, 3-D second order (dt = 4 K dx / c,
+                             x sweeps moving K cells and y, z sweeps 2 K) as eight single sweeps; a vector
+                             potential is allowed with each of them */
+    void *ext_state[2];   /* optional caller-owned device buffers used as the grid's two ping-pong state
+                             buffers (both NULL: the grid allocates its own).  Each holds one state,
+                             nx ny nz x 8 values of the storage type (double, float, or int64 for DIRAC_FX64),
+                             on cfg.device, 16-byte aligned, not overlapping.  The grid adopts ext_state[0] as
+                             its current state as it stands (nothing is copied or cleared; for DIRAC_FX64 the
+                             values are q with shift 0 until a dirac_set_state), reads and writes both buffers
+                             on its stream while it lives (steps, dirac_get_state's decoding, autotuning),
+                             never frees them, and does not count them in dirac_info.device_bytes.  The caller
+                             keeps them alive until dirac_destroy and orders its own writes to them before the
+                             grid's next call on its stream; dirac_info.state_index says which one holds the
+                             current state. */
 } dirac_config;
 
 /* Fills cfg with defaults: ndim 2, n = {256,1,256}, dx = 10/8192, c = 137.0359895, m = 1,
@@ -100,10 +114,12 @@ typedef struct {
  * first-order splitting. */
 void dirac_default_config(dirac_config *cfg);
 
-/* Creates a grid: validates cfg, allocates two state buffers (ping-pong), the phase table and
- * scratch on cfg->device, zero state, V = 0.  Errors: DIRAC_ERR_ARG for an invalid config,
- * DIRAC_ERR_OOM when allocation fails (nothing is leaked), DIRAC_ERR_CUDA otherwise.
- * The grid owns all its device memory; free it with dirac_destroy. */
+/* Creates a grid: validates cfg, allocates two state buffers (ping-pong; none when cfg->ext_state
+ * supplies them), the phase table and scratch on cfg->device, zero state (the contents of ext_state[0]
+ * when given), V = 0.  Errors: DIRAC_ERR_ARG for an invalid config (including one ext_state pointer
+ * without the other, a buffer that is not device memory of cfg->device, not 16-byte aligned, or two
+ * buffers closer than one state's size), DIRAC_ERR_OOM when allocation fails (nothing is leaked),
+ * DIRAC_ERR_CUDA otherwise.  The grid owns the device memory it allocated; free it with dirac_destroy. */
 dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out);
 
 /* Releases every resource of the grid (waits for its stream first).  NULL is accepted. */
@@ -135,7 +151,8 @@ dirac_status dirac_get_state(dirac_grid *g, void *psi, int on_device);
 dirac_status dirac_set_state_fx(dirac_grid *g, const int64_t *q, int shift, int on_device);
 dirac_status dirac_get_state_fx(dirac_grid *g, int64_t *q, int *shift, int on_device);
 
-/* Device pointer of the current state buffer (valid until the next dirac_step / dirac_destroy).
+/* Device pointer of the current state buffer (valid until the next dirac_step / dirac_destroy; with
+ * cfg.ext_state it is ext_state[dirac_info.state_index]).
  * DIRAC_FX64: the int64 fixed-point values q (psi = q 2^-S, S = dirac_info.fx_shift). */
 dirac_status dirac_state_ptr(dirac_grid *g, void **dev_ptr);
 
@@ -184,6 +201,29 @@ dirac_status dirac_set_absorber(dirac_grid *g, const double *a, int64_t count);
  * takes its step index); the phase costs 48 instead of 16 FP64 instructions per point-step. */
 dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, int64_t nsteps_table);
 
+/* Fields varying in space and time (Sec. 2.3: the phase matrix U(i) of Eq. sol_dis_4 with the field integral
+ * At(i) = e int_{t_n}^{t_{n+1}} A(t, x_i) dt of Eq. field_dis1 at every cell, and the scalar integral
+ * V~(i) = int V(t, x_i) dt of Eq. field_dis2), for fields of the separable form
+ *     e A_d(t, x) = f_d(t) a_d(x)   (d = x, y, z)     and     V(t, x) = V(x) + f_V(t) w(x),
+ * V(x) the static potential of dirac_set_potential, whose integrals over step n are exactly
+ *     At_d(i) = F_d^n a_d(i)     and     V~(i) = V(i) dt + F_V^n w(i),
+ * F^n = int_{t_n}^{t_{n+1}} f(t) dt the envelopes' integrals over the step (the caller evaluates them,
+ * analytically or by quadrature).  Per cell and step the phase is psi <- U(At(i)) exp(-i V~(i)) psi, U the
+ * closed form of Sec. 2.3 with mu = m c^2 dt, formed on the device in FP64 (its sin and cos agree with the
+ * host's to an ulp or two, so FP64 results agree with an FP64 evaluation on the host to about 1e-15 per step
+ * rather than bit for bit).  Arguments (host buffers, copied):
+ *   a  3 doubles per cell, [z][y][x][d] (NULL: no vector potential);
+ *   w  1 double per cell, [z][y][x] (NULL: no time-dependent scalar potential);
+ *   F  4 doubles per step, (F_x, F_y, F_z, F_V) of step n at [4n, 4n+4); step n is counted by the grid's step
+ *      counter, as for dirac_set_vector_potential; NULL or nsteps_table = 0 removes the field.
+ * Every step form runs with it (2-D and 3-D, first and second order, whose phase spans the whole step dt, and
+ * char_shift 1-4) as single-sweep launches (DIRAC_PLAN_FIELD_SWEEPS), one step per block, no graph replay;
+ * FP64 and FP32 storage.  Errors: DIRAC_ERR_ARG for a non-finite entry, a negative count or a DIRAC_FX64 grid,
+ * DIRAC_ERR_STATE while a uniform vector potential is set (the two are exclusive: a(i) = (1, 1, 1) is the
+ * uniform field).  dirac_step returns DIRAC_ERR_ARG, enqueuing nothing, when the step counter would pass the
+ * table's end. */
+dirac_status dirac_set_field(dirac_grid *g, const double *a, const double *w, const double *F, int64_t nsteps_table);
+
 /* Checkpoint support: sets the step counter and cumulative flux (after dirac_set_state). */
 dirac_status dirac_set_counters(dirac_grid *g, int64_t step, double flux_cum);
 
@@ -198,6 +238,7 @@ typedef struct {
     size_t device_bytes;    /* device memory owned by the grid */
     int plan;               /* DIRAC_PLAN_*: which kernels one step runs */
     int fx_shift;           /* DIRAC_FX64: the state's fixed-point shift S (psi = q 2^-S); 0 otherwise */
+    int state_index;        /* 0 or 1: the ping-pong buffer (ext_state[i] when given) holding the current state */
 } dirac_info;
 
 /* dirac_info.plan */
@@ -210,7 +251,10 @@ enum {
     DIRAC_PLAN_3D_FUSED = 5,     /* 3-D single pass */
     DIRAC_PLAN_3D_STRANG = 6,    /* 3-D second-order step: eight single-sweep launches */
     DIRAC_PLAN_STRANG_FIELD_2D = 7, /* 2-D second-order step with the vector-potential phase matrix */
-    DIRAC_PLAN_3D_STRANG_FUSED = 8  /* 3-D second-order steps: x-y-x, z-phase-z, x-y-x-x-y-x, ... passes */
+    DIRAC_PLAN_3D_STRANG_FUSED = 8, /* 3-D second-order steps: x-y-x, z-phase-z, x-y-x-x-y-x, ... passes */
+    DIRAC_PLAN_SHIFT_SWEEPS = 9,    /* char_shift > 1 as single-sweep launches: 3-D first order x y z+phase,
+                                       2-D second order x z+phase z x */
+    DIRAC_PLAN_FIELD_SWEEPS = 10    /* a field varying in space and time (dirac_set_field): single-sweep launches */
 };
 
 dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info);
@@ -349,6 +393,14 @@ dirac_status dirac_surrogate_gradient(dirac_surrogate *s, const double *X, const
 int64_t dirac_surrogate_num_params(void);
 dirac_status dirac_surrogate_get_params(dirac_surrogate *s, float *params);
 dirac_status dirac_surrogate_set_params(dirac_surrogate *s, const float *params);
+
+/* Checkpoint of the network at `path` (a file; the surrogate counterpart of a training run's checkpoint
+ * path): the box lo/hi, the FP32 master parameters, the Adam moments and step and the shuffle seed, so that
+ * training resumes where it stopped.  save overwrites the file; load replaces the surrogate's box, seed,
+ * parameters and optimizer state (max_batch, stream and device stay).  Errors: DIRAC_ERR_ARG for a file that cannot be opened, a
+ * short or foreign file, or a checkpoint of another parameter count. */
+dirac_status dirac_surrogate_save(dirac_surrogate *s, const char *path);
+dirac_status dirac_surrogate_load(dirac_surrogate *s, const char *path);
 
 /* Transmission for n queries: the network inside the box, the batched solver (geometry of the Klein
  * ensemble: 64-column absorbing layers (eta 0.1) at both x edges, side = smallest of 256, 384, 512, 768,

@@ -24,7 +24,7 @@ DIRAC_V_NONE, DIRAC_V_X_ONLY, DIRAC_V_FULL = 0, 1, 2
 DIRAC_LIE, DIRAC_STRANG = 0, 1
 DIRAC_PLAN_STEP_2D, DIRAC_PLAN_STRANG_2D, DIRAC_PLAN_FIELD_2D, DIRAC_PLAN_SHIFT_2D = 0, 1, 2, 3
 DIRAC_PLAN_3D_TWO_PASS, DIRAC_PLAN_3D_FUSED, DIRAC_PLAN_3D_STRANG, DIRAC_PLAN_STRANG_FIELD_2D = 4, 5, 6, 7
-DIRAC_PLAN_3D_STRANG_FUSED = 8
+DIRAC_PLAN_3D_STRANG_FUSED, DIRAC_PLAN_SHIFT_SWEEPS, DIRAC_PLAN_FIELD_SWEEPS = 8, 9, 10
 
 STATUS_NAMES = {0: "DIRAC_OK", 1: "DIRAC_ERR_ARG", 2: "DIRAC_ERR_OOM", 3: "DIRAC_ERR_CUDA",
                 4: "DIRAC_ERR_NONFINITE", 5: "DIRAC_ERR_TIMEOUT", 6: "DIRAC_ERR_STATE"}
@@ -42,7 +42,7 @@ class dirac_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("boundary", ctypes.c_int), ("flux_face", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("points_per_lane", ctypes.c_int), ("splitting", ctypes.c_int),
-                ("char_shift", ctypes.c_int)]
+                ("char_shift", ctypes.c_int), ("ext_state", ctypes.c_void_p * 2)]
 
 
 class dirac_obs(ctypes.Structure):
@@ -55,7 +55,7 @@ class dirac_info(ctypes.Structure):
                 ("launch_warps", ctypes.c_int64), ("strip_width", ctypes.c_int64),
                 ("segment_rows", ctypes.c_int64), ("graphs", ctypes.c_int),
                 ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan", ctypes.c_int),
-                ("fx_shift", ctypes.c_int)]
+                ("fx_shift", ctypes.c_int), ("state_index", ctypes.c_int)]
 
 
 _lib = None
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dirac_set_counters": (I, [P, I64, D]),
         "dirac_set_absorber": (I, [P, P, I64]),
         "dirac_set_vector_potential": (I, [P, P, I64]),
+        "dirac_set_field": (I, [P, P, P, P, I64]),
         "dirac_get_info": (I, [P, ctypes.POINTER(dirac_info)]),
         "dirac_autotune": (I, [P]),
         "dirac_last_error": (ctypes.c_char_p, [P]),
@@ -209,6 +210,19 @@ def dirac_set_vector_potential(h, A_tilde) -> None:
     _check(load_library().dirac_set_vector_potential(h, At.ctypes.data, At.shape[0]), h)
 
 
+def dirac_set_field(h, a, w, F) -> None:
+    """Separable space-time field: a (3 per cell, or None), w (1 per cell, or None) and the (nsteps, 4) envelope
+    integrals F = (F_x, F_y, F_z, F_V) per step (None: remove the field)."""
+    if F is None:
+        _check(load_library().dirac_set_field(h, None, None, None, 0), h)
+        return
+    Fa = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 4)
+    aa = None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+    _check(load_library().dirac_set_field(h, None if aa is None else aa.ctypes.data,
+                                          None if ww is None else ww.ctypes.data, Fa.ctypes.data, Fa.shape[0]), h)
+
+
 def dirac_set_counters(h, step: int, flux_cum: float) -> None:
     _check(load_library().dirac_set_counters(h, int(step), float(flux_cum)), h)
 
@@ -231,8 +245,9 @@ def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRA
                 boundary: int = DIRAC_BC_ZERO, x_min=None, flux_face: int = -1, stream=None,
                 device: int = 0, steps_per_launch: int = 0, use_graphs: bool = True,
                 c: float | None = None, m: float | None = None, points_per_lane: int = 0,
-                splitting: int = 0, char_shift: int = 0) -> dirac_config:
-    """dirac_default_config() with the given fields replaced (n = (nx, ny, nz))."""
+                splitting: int = 0, char_shift: int = 0, ext_state=None) -> dirac_config:
+    """dirac_default_config() with the given fields replaced (n = (nx, ny, nz)).  ext_state: two caller-owned
+    device buffers (torch CUDA tensors or raw device addresses) the grid uses as its ping-pong state buffers."""
     cfg = dirac_default_config()
     cfg.ndim = ndim
     for d in range(3):
@@ -257,6 +272,11 @@ def make_config(n, ndim: int = 2, dx: float | None = None, precision: int = DIRA
     cfg.points_per_lane = points_per_lane
     cfg.splitting = splitting
     cfg.char_shift = char_shift
+    if ext_state is not None:
+        if len(ext_state) != 2:
+            raise ValueError("ext_state takes two buffers")
+        for i, b in enumerate(ext_state):
+            cfg.ext_state[i] = b.data_ptr() if hasattr(b, "data_ptr") else b
     return cfg
 
 
@@ -419,6 +439,8 @@ def _sur_lib():
         "dirac_surrogate_num_params": (I64, []),
         "dirac_surrogate_get_params": (I, [P, P]),
         "dirac_surrogate_set_params": (I, [P, P]),
+        "dirac_surrogate_save": (I, [P, ctypes.c_char_p]),
+        "dirac_surrogate_load": (I, [P, ctypes.c_char_p]),
         "dirac_surrogate_query": (I, [P, P, I64, ctypes.POINTER(dirac_batch_config), P, P]),
         "dirac_klein_run_from_reduced": (I, [P, D, D, D, ctypes.POINTER(dirac_klein_run)]),
         "dirac_surrogate_last_error": (ctypes.c_char_p, [P]),
@@ -487,6 +509,16 @@ def dirac_surrogate_get_params(h) -> np.ndarray:
 def dirac_surrogate_set_params(h, params) -> None:
     p = np.ascontiguousarray(params, dtype=np.float32)
     _scheck(_sur_lib().dirac_surrogate_set_params(h, p.ctypes.data), h)
+
+
+def dirac_surrogate_save(h, path: str) -> None:
+    """Checkpoint: box, FP32 parameters and Adam state to the file at path."""
+    _scheck(_sur_lib().dirac_surrogate_save(h, os.fsencode(path)), h)
+
+
+def dirac_surrogate_load(h, path: str) -> None:
+    """Restores box, parameters and Adam state from a checkpoint written by dirac_surrogate_save."""
+    _scheck(_sur_lib().dirac_surrogate_load(h, os.fsencode(path)), h)
 
 
 def dirac_surrogate_query(h, X, solver_cfg: dirac_batch_config):

@@ -5,7 +5,7 @@ namespace dirac {
 
 // the phase-matrix variant exists for floating-point states only
 template <typename T> static void launch_axis_field(const AxisArgs &a, int blocks, cudaStream_t s) {
-    axis_kernel<T, 2, true, true><<<blocks, 256, 0, s>>>(a);
+    axis_kernel<T, 2, true, 1><<<blocks, 256, 0, s>>>(a);
 }
 template <> void launch_axis_field<long long>(const AxisArgs &, int, cudaStream_t) {}
 
@@ -13,12 +13,22 @@ template <typename T>
 static cudaError_t launch_axis_t(const AxisArgs &a, int axis, int phase, int blocks, cudaStream_t s) {
     const bool field = a.ucoef != nullptr && a.ucoef_n > 0;
     if (sizeof(T) == 8 && (T)0.5 == (T)0 && field) return cudaErrorInvalidValue;  // fixed point: no phase matrix
-    if (axis == 0 && !phase) axis_kernel<T, 0, false, false><<<blocks, 256, 0, s>>>(a);
-    else if (axis == 1 && !phase) axis_kernel<T, 1, false, false><<<blocks, 256, 0, s>>>(a);
-    else if (axis == 2 && !phase) axis_kernel<T, 2, false, false><<<blocks, 256, 0, s>>>(a);
-    else if (axis == 2 && phase && !field) axis_kernel<T, 2, true, false><<<blocks, 256, 0, s>>>(a);
+    if (axis == 0 && !phase) axis_kernel<T, 0, false, 0><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 1 && !phase) axis_kernel<T, 1, false, 0><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 2 && !phase) axis_kernel<T, 2, false, 0><<<blocks, 256, 0, s>>>(a);
+    else if (axis == 2 && phase && !field) axis_kernel<T, 2, true, 0><<<blocks, 256, 0, s>>>(a);
     else if (axis == 2 && phase && field) launch_axis_field<T>(a, blocks, s);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axis_cellfield(const AxisArgs &a, int precision, int blocks, cudaStream_t s) {
+    if (precision == 1)
+        axis_kernel<float, 2, true, 2><<<blocks, 256, 0, s>>>(a);
+    else if (precision == 0)
+        axis_kernel<double, 2, true, 2><<<blocks, 256, 0, s>>>(a);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

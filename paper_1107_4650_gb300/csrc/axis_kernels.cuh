@@ -20,26 +20,59 @@
 
 namespace dirac {
 
-struct AxisArgs {
-    const void *in;
-    void *out;
-    const void *table;   // phase epilogue: (pu, pd) per x column or per cell, pre-scaled
-    int64_t nx, ny, nz;
-    int64_t shift;
-    int periodic;
-    int full_table;
-    int64_t flux_face;   // x sweeps: face index, or -1
-    double fscale;       // multiplies the summed |.|^2 of the face cells
-    double vol;          // cell volume
-    double *flux_part;   // [gridDim.x]
-    double *flux_cum;
-    unsigned *ticket;
-    // uniform vector potential (phase epilogue only): 12 doubles of U entries per step, this launch's step
-    const double *ucoef;
-    int64_t ucoef_n, step0;
-    // fixed-point states: the output divided by 2^rshift, rounded to nearest (halves up); 0 = none
-    int rshift;
-};
+// psi'_a = sum_b M_ab psi_b over the non-zero entries of M = U g (Dup, Ddn, Ez, -Ez, Ep, Em), columns in order,
+// accumulated with cmac from zero (a product with a zero entry would add exactly nothing).
+template <typename T> __device__ __forceinline__ void apply_m6(Cx<T> (&o)[4], const Cx<T> (&m6)[6]) {
+    const Cx<T> z0 = {T(0), T(0)};
+    const Cx<T> n0 = cmac(cmac(cmac(z0, o[0], m6[0]), o[2], m6[2]), o[3], m6[4]);
+    const Cx<T> n1 = cmac(cmac(cmac(z0, o[1], m6[0]), o[2], m6[5]), o[3], m6[3]);
+    const Cx<T> n2 = cmac(cmac(cmac(z0, o[0], m6[2]), o[1], m6[4]), o[2], m6[1]);
+    const Cx<T> n3 = cmac(cmac(cmac(z0, o[0], m6[5]), o[1], m6[3]), o[3], m6[1]);
+    o[0] = n0;
+    o[1] = n1;
+    o[2] = n2;
+    o[3] = n3;
+}
+
+// Entries of M = U(At) g for cell c (column i) of a field varying in space and time (Sec. 2.3, Eqs. sol_dis_4,
+// field_dis1, field_dis2): At_d = F_d a_d(c), V~ = V dt + F_V w(c), U the closed form of exp(i(beta F + alpha.F))
+// with F = -m c^2 dt and At, A = sqrt(((mu^2 + At_x^2) + At_y^2) + At_z^2), sin(A)/A -> 1 at A = 0, g =
+// (cos V~, -sin V~) times the absorber factor and the power-of-two scale of the sweeps' halves.  All in FP64
+// (CUDA's sin and cos, within an ulp or two of the host's), then rounded to the storage type.
+template <typename T>
+__device__ __forceinline__ void cell_field_matrix(const AxisArgs &a, int64_t c, int64_t i, Cx<T> (&m6)[6]) {
+    double At[3] = {0.0, 0.0, 0.0};
+    if (a.fa)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) At[d] = __dmul_rn(a.fenv[d], __ldg(a.fa + 3 * c + d));
+    double vt = a.fvdt ? __ldg(a.fvdt + (a.fvdt_full ? c : i)) : 0.0;
+    if (a.fw) vt = __dadd_rn(vt, __dmul_rn(a.fenv[3], __ldg(a.fw + c)));
+    const double mu = a.fmu;
+    const double A2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(mu, mu), __dmul_rn(At[0], At[0])), __dmul_rn(At[1], At[1])),
+                                __dmul_rn(At[2], At[2]));
+    const double A = __dsqrt_rn(A2);
+    double sA = 1.0, cA = 1.0;
+    if (A > 0.0) {
+        double sn;
+        sincos(A, &sn, &cA);
+        sA = __ddiv_rn(sn, A);
+    }
+    const double ax = __dmul_rn(At[0], sA), ay = __dmul_rn(At[1], sA), az = __dmul_rn(At[2], sA), ms = __dmul_rn(mu, sA);
+    double sv, cv;
+    sincos(vt, &sv, &cv);
+    Cx<double> g = {cv, -sv};
+    if (a.fabs) {
+        const double f = __ldg(a.fabs + i);
+        g = {__dmul_rn(g.re, f), __dmul_rn(g.im, f)};
+    }
+    g = {__dmul_rn(g.re, a.fscale_phase), __dmul_rn(g.im, a.fscale_phase)};
+    const Cx<double> U6[6] = {{cA, -ms}, {cA, ms}, {0.0, az}, {0.0, -az}, {ay, ax}, {-ay, ax}};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const Cx<double> p = cmulp(U6[e], g);
+        m6[e] = Cx<T>{(T)p.re, (T)p.im};
+    }
+}
 
 // Fixed point: o / 2^r rounded to nearest, halves upward (floating-point states never ask for it).
 template <typename T> __device__ __forceinline__ void round_shift(Cx<T> (&)[4], int) {}
@@ -49,8 +82,9 @@ template <> __device__ __forceinline__ void round_shift<long long>(Cx<long long>
     for (int q = 0; q < 4; ++q) o[q] = Cx<long long>{(o[q].re + half) >> r, (o[q].im + half) >> r};
 }
 
-template <typename T, int AXIS, bool PHASE, bool FIELD>
+template <typename T, int AXIS, bool PHASE, int FLD>
 __global__ void __launch_bounds__(256) axis_kernel(const AxisArgs a) {
+    constexpr bool FIELD = FLD == 1;
     const int64_t nx = a.nx, ny = a.ny, nz = a.nz, S = a.shift;
     const int64_t ncells = nx * ny * nz;
     const bool per = a.periodic != 0;
@@ -124,7 +158,12 @@ __global__ void __launch_bounds__(256) axis_kernel(const AxisArgs a) {
         if (PHASE) {
             Cx<T> pu, pd;
             load_tab(tab + (a.full_table ? c : i) * 4, pu, pd);
-            if (FIELD) {
+            if (FLD == 2) {
+                // a field varying in space and time: this cell's U(At(i)) exp(-i V~(i)) times the sweeps' scale
+                Cx<T> m6[6];
+                cell_field_matrix<T>(a, c, i, m6);
+                apply_m6(o, m6);
+            } else if (FIELD) {
                 // (U_ab g) psi_b over the non-zero entries, columns in order, g = the table's exp(-i V dt)
                 Cx<T> m6[FIELD ? 6 : 1];
 #pragma unroll

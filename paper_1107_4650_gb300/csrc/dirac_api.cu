@@ -53,6 +53,7 @@ struct dirac_grid {
     size_t elem = 8;
     int64_t ncells = 0;
     void *psi[2] = {nullptr, nullptr};
+    bool ext = false;  // psi[] are the caller's buffers (cfg.ext_state): never freed, not in device_bytes
     int cur = 0;
     void *table = nullptr;
     size_t table_cap = 0;  // bytes
@@ -67,6 +68,11 @@ struct dirac_grid {
     std::vector<double> avec;        // uniform vector potential: field integrals, 3 per step (empty: none)
     double *ucoef = nullptr;         // device: 12 doubles of U entries per step
     size_t ucoef_cap = 0;            // bytes
+    // field varying in space and time (dirac_set_field): envelope integrals (4 per step; empty: none) on the host,
+    // profiles a (3 per cell) and w (1 per cell), V dt per table entry and absorber factors on the device
+    std::vector<double> fenv;
+    double *fa_dev = nullptr, *fw_dev = nullptr, *fvdt_dev = nullptr, *fabs_dev = nullptr;
+    size_t fa_bytes = 0, fw_bytes = 0, fvdt_bytes = 0, fabs_bytes = 0;
     bool tuning = false;             // autotune timing runs: table rows taken modulo its length
     int inject_stall = 0;            // DIRAC_INJECT_STALL set at creation: every step launch stalls one copy
     double *obs_partial = nullptr;
@@ -118,9 +124,14 @@ double scale_of(const dirac_grid *g) {
     return ndim_of(g) == 3 ? 0.125 : 0.25;
 }
 int char_shift(const dirac_grid *g) { return g->cfg.char_shift > 1 ? g->cfg.char_shift : 1; }
+// Step form: 0 2-D first order, 1 3-D first order, 2 2-D second order, 3 2-D first order with a vector potential,
+// 4 2-D first order with char_shift > 1, 5 2-D second order with a vector potential, 6 3-D second order (any
+// char_shift), 7 single-sweep launches with char_shift > 1 (3-D first order, 2-D second order), 8 single-sweep
+// launches with a field varying in space and time (every dimension, splitting and char_shift).
 int sweep_mode(const dirac_grid *g) {
-    if (strang(g)) return ndim_of(g) == 3 ? 6 : (g->avec.empty() ? 2 : 5);
-    if (ndim_of(g) == 3) return 1;
+    if (!g->fenv.empty()) return 8;
+    if (strang(g)) return ndim_of(g) == 3 ? 6 : (char_shift(g) > 1 ? 7 : (g->avec.empty() ? 2 : 5));
+    if (ndim_of(g) == 3) return char_shift(g) > 1 ? 7 : 1;
     if (char_shift(g) > 1) return 4;
     return g->avec.empty() ? 0 : 3;
 }
@@ -128,9 +139,12 @@ int levels(const dirac_grid *g, int K) { return strang(g) ? 2 * K : K; }
 // a uniform vector potential is set (2-D: mode 3; 3-D: the fused pass with the phase matrix)
 bool field_on(const dirac_grid *g) { return !g->avec.empty(); }
 // 3-D steps run as the fused single pass (chosen by the plan, or required by a vector potential)
-bool fused_pass(const dirac_grid *g) { return ndim_of(g) == 3 && !strang(g) && (g->plan.fused3d || field_on(g)); }
+bool cellfield_on(const dirac_grid *g) { return !g->fenv.empty(); }
+bool fused_pass(const dirac_grid *g) {
+    return ndim_of(g) == 3 && !strang(g) && char_shift(g) == 1 && !cellfield_on(g) && (g->plan.fused3d || field_on(g));
+}
 // 3-D second-order step as the x-y-x, z-phase-z, x-y-x passes
-bool strang3d_fused(const dirac_grid *g) { return sweep_mode(g) == 6 && g->plan.s3_fused; }
+bool strang3d_fused(const dirac_grid *g) { return sweep_mode(g) == 6 && g->plan.s3_fused && char_shift(g) == 1; }
 // x halo cells of a strip (each side) for K steps per launch
 int halo_of(const dirac_grid *g, int K) { return sweep_mode(g) == 4 ? char_shift(g) : levels(g, K); }
 double cell_volume(const dirac_grid *g) {
@@ -156,6 +170,8 @@ dirac_status ensure_table(dirac_grid *g, size_t bytes) {
         }
     return DIRAC_OK;
 }
+
+dirac_status upload_field_aux(dirac_grid *g);
 
 dirac_status upload_table(dirac_grid *g, const double *V, int layout, int64_t count) {
     // with a vector potential the mass term lives in the U matrix and the table holds exp(-i V dt) alone
@@ -220,7 +236,40 @@ dirac_status upload_table(dirac_grid *g, const double *V, int layout, int64_t co
         CK(g, cudaStreamSynchronize(g->stream));
     }
     g->table_full = (layout == DIRAC_V_FULL);
+    return cellfield_on(g) ? upload_field_aux(g) : DIRAC_OK;
+}
+
+// Copies n doubles from the host to a device array of the grid, (re)allocating it to fit; n = 0 frees it.
+dirac_status put_doubles(dirac_grid *g, double *&dev, size_t &bytes, const double *host, size_t n) {
+    const size_t need = n * sizeof(double);
+    if (need == 0 || need > bytes) {
+        if (dev) {
+            cudaFree(dev);
+            g->device_bytes -= bytes;
+        }
+        dev = nullptr;
+        bytes = 0;
+        if (need == 0) return DIRAC_OK;
+        CK(g, cudaMalloc(&dev, need));
+        bytes = need;
+        g->device_bytes += need;
+    }
+    CK(g, cudaMemcpyAsync(dev, host, need, cudaMemcpyHostToDevice, g->stream));
+    CK(g, cudaStreamSynchronize(g->stream));
     return DIRAC_OK;
+}
+
+// The cell-field plan's per-entry V dt (host products V * dt, per x column or per cell as the potential was set) and
+// absorber factors, refreshed whenever the potential, the absorber or the field changes.
+dirac_status upload_field_aux(dirac_grid *g) {
+    std::vector<double> vdt;
+    if (g->v_layout != DIRAC_V_NONE) {
+        vdt.resize(g->v_host.size());
+        for (size_t e = 0; e < vdt.size(); ++e) vdt[e] = g->v_host[e] * g->dt;
+    }
+    dirac_status st = put_doubles(g, g->fvdt_dev, g->fvdt_bytes, vdt.data(), vdt.size());
+    if (st != DIRAC_OK) return st;
+    return put_doubles(g, g->fabs_dev, g->fabs_bytes, g->absorb.data(), g->absorb.size());
 }
 
 // Launch geometry for (K, P, warps per block): strips of 32P - 2K owned cells, segments sized so the
@@ -310,7 +359,7 @@ dirac_status ensure_flux_part(dirac_grid *g) {
         if (g->plan.K == 2)
             need = std::max(need, (size_t)(2 * g->plan.f2_nzsegs * g->plan.f2_nytiles * g->plan.f2_warps));
     }
-    if (sweep_mode(g) == 6) need = std::max(need, (size_t)axis_blocks(g));
+    if (sweep_mode(g) >= 6) need = std::max(need, (size_t)axis_blocks(g));
     if (strang3d_fused(g))
         for (int nh = 1; nh <= 2; ++nh) {
             const Plan::XY &q = g->plan.s3_xy[nh - 1];
@@ -369,17 +418,105 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
         // two x sweeps is 2 and 8 times the true one, and the last sweep divides by 16 with rounding
         static const double fscale_fx[8] = {0.5, 0, 0.5 / 16.0, 0, 0, 0.5 / 4.0, 0, 0.5 / 64.0};
         const int blocks = axis_blocks(g);
+        const int64_t K = char_shift(g);  // c dt / 4 = K dx: x sweeps move K cells, y and z sweeps 2 K
         int par = parity;
         for (int q = 0; q < 8; ++q) {
             const int ax = axes[q];
             cudaError_t e = launch_axis(g->psi[par], g->psi[par ^ 1], g->table, g->cfg.n[0], g->cfg.n[1], g->cfg.n[2], ax,
-                                        ax == 0 ? 1 : 2, a.periodic, g->table_full, q == 3 ? 1 : 0,
+                                        ax == 0 ? K : 2 * K, a.periodic, g->table_full, q == 3 ? 1 : 0,
                                         ax == 0 ? a.flux_face : -1, (g->fx ? fscale_fx[q] : fscale[q]) * a.flux_unit,
                                         a.vol, g->flux_part, g->flux_dev, g->ticket, q == 3 ? a.ucoef : nullptr,
                                         q == 3 ? a.ucoef_n : 0, step0,
                                         g->fx ? DIRAC_FX64 : (g->fp32 ? DIRAC_FP32 : DIRAC_FP64),
                                         (g->fx && q == 7) ? 4 : 0, blocks, s);
             if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order sweep launch");
+            g->launches++;
+            par ^= 1;
+        }
+        return DIRAC_OK;
+    }
+    if (mode == 8) {
+        // a field varying in space and time as single-sweep launches: the sweeps of the grid's step form (shift K),
+        // the phase epilogue of its z sweep forming U(At(i)) exp(-i V~(i)) per cell from the profiles and this step's
+        // envelope integrals (Sec. 2.3, Eqs. sol_dis_4, field_dis1, field_dis2).  Each sweep doubles the state; the
+        // phase carries the halves.  First order 2-D: x z+phase; 3-D: x y z+phase; second order 2-D: x z+phase z x;
+        // 3-D: A B A C+phase C A B A (x moving K cells, y and z 2 K), flux scales as for the single-sweep plans.
+        struct Sw {
+            int axis, phase;
+            double fscale;
+        };
+        static const Sw lie2[2] = {{0, 0, 0.5}, {2, 1, 0.0}};
+        static const Sw lie3[3] = {{0, 0, 0.5}, {1, 0, 0.0}, {2, 1, 0.0}};
+        static const Sw strang2[4] = {{0, 0, 0.5}, {2, 1, 0.0}, {2, 0, 0.0}, {0, 0, 2.0}};
+        static const Sw strang3[8] = {{0, 0, 0.5},        {1, 0, 0.0}, {0, 0, 0.5 / 16.0}, {2, 1, 0.0},
+                                      {2, 0, 0.0}, {0, 0, 0.5 * 64.0}, {1, 0, 0.0}, {0, 0, 0.5 * 4.0}};
+        const bool s3 = strang(g) && ndim_of(g) == 3;
+        const Sw *seq = strang(g) ? (s3 ? strang3 : strang2) : (ndim_of(g) == 3 ? lie3 : lie2);
+        const int nseq = strang(g) ? (s3 ? 8 : 4) : (ndim_of(g) == 3 ? 3 : 2);
+        const int64_t K = char_shift(g);
+        const int64_t nrows = (int64_t)(g->fenv.size() / 4);
+        const double *F = &g->fenv[4 * (size_t)(step0 % nrows)];
+        const int blocks = axis_blocks(g);
+        const int prec = g->fp32 ? DIRAC_FP32 : DIRAC_FP64;
+        int par = parity;
+        for (int q = 0; q < nseq; ++q) {
+            const Sw &w = seq[q];
+            const int64_t sh = (s3 && w.axis != 0) ? 2 * K : K;
+            cudaError_t e;
+            if (w.phase) {
+                AxisArgs z{};
+                z.in = g->psi[par];
+                z.out = g->psi[par ^ 1];
+                z.table = g->table;
+                z.nx = g->cfg.n[0];
+                z.ny = g->cfg.n[1];
+                z.nz = g->cfg.n[2];
+                z.shift = sh;
+                z.periodic = a.periodic;
+                z.flux_face = -1;
+                z.fa = g->fa_dev;
+                z.fw = g->fw_dev;
+                z.fvdt = g->fvdt_dev;
+                z.fvdt_full = g->v_layout == DIRAC_V_FULL;
+                z.fabs = g->fabs_dev;
+                for (int d = 0; d < 4; ++d) z.fenv[d] = F[d];
+                z.fmu = g->cfg.m * g->cfg.c * g->cfg.c * g->dt;
+                z.fscale_phase = scale_of(g);
+                e = launch_axis_cellfield(z, prec, blocks, s);
+            } else {
+                e = launch_axis(g->psi[par], g->psi[par ^ 1], g->table, g->cfg.n[0], g->cfg.n[1], g->cfg.n[2], w.axis,
+                                sh, a.periodic, g->table_full, 0, w.axis == 0 ? a.flux_face : -1, w.fscale, a.vol,
+                                g->flux_part, g->flux_dev, g->ticket, nullptr, 0, step0, prec, 0, blocks, s);
+            }
+            if (e != cudaSuccess) return cuda_fail(g, e, "cell-field sweep launch");
+            g->launches++;
+            par ^= 1;
+        }
+        return DIRAC_OK;
+    }
+    if (mode == 7) {
+        // characteristic shift K > 1 as single-sweep launches (Sec. 2.3: c dt = K dx per sweep), each sweep doubling
+        // the state and the table carrying the halves: 3-D first order x(K) y(K) z(K)+phase over dt = K dx / c, the
+        // state entering the x sweep at its true size (flux scale 1/2); 2-D second order x(K) z(K)+phase z(K) x(K)
+        // over dt = 2 K dx / c, the state entering the second x sweep at half its true size (flux scale 2)
+        struct Sw {
+            int axis, phase;
+            double fscale;
+        };
+        static const Sw lie3[3] = {{0, 0, 0.5}, {1, 0, 0.0}, {2, 1, 0.0}};
+        static const Sw strang2[4] = {{0, 0, 0.5}, {2, 1, 0.0}, {2, 0, 0.0}, {0, 0, 2.0}};
+        const Sw *seq = ndim_of(g) == 3 ? lie3 : strang2;
+        const int nseq = ndim_of(g) == 3 ? 3 : 4;
+        const int blocks = axis_blocks(g);
+        int par = parity;
+        for (int q = 0; q < nseq; ++q) {
+            const Sw &w = seq[q];
+            cudaError_t e = launch_axis(g->psi[par], g->psi[par ^ 1], g->table, g->cfg.n[0], g->cfg.n[1], g->cfg.n[2],
+                                        w.axis, char_shift(g), a.periodic, g->table_full, w.phase,
+                                        w.axis == 0 ? a.flux_face : -1, w.fscale, a.vol, g->flux_part, g->flux_dev,
+                                        g->ticket, w.phase ? a.ucoef : nullptr, w.phase ? a.ucoef_n : 0, step0,
+                                        g->fp32 ? DIRAC_FP32 : DIRAC_FP64, 0, blocks, s);
+            if (e != cudaSuccess) return cuda_fail(g, e, "characteristic-shift sweep launch");
             g->launches++;
             par ^= 1;
         }
@@ -478,6 +615,8 @@ dirac_status enqueue_strang3d_run(dirac_grid *g, int parity, int64_t m, cudaStre
 
 int block_flips(const dirac_grid *g) {
     if (sweep_mode(g) == 6) return 0;  // eight sweeps per step: parity returns (fused runs: enqueue_strang3d_run)
+    if (sweep_mode(g) == 7) return ndim_of(g) == 3 ? 1 : 0;  // three or four single sweeps
+    if (sweep_mode(g) == 8) return (ndim_of(g) == 3 && !strang(g)) ? 1 : 0;  // two, three, four or eight sweeps
     return (ndim_of(g) == 3 && !fused_pass(g)) ? 0 : 1;
 }
 
@@ -517,6 +656,8 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
 
 int64_t launches_per_block(const dirac_grid *g) {
     if (sweep_mode(g) == 6) return 8;
+    if (sweep_mode(g) == 7) return ndim_of(g) == 3 ? 3 : 4;
+    if (sweep_mode(g) == 8) return strang(g) ? (ndim_of(g) == 3 ? 8 : 4) : (ndim_of(g) == 3 ? 3 : 2);
     return 1 + ((ndim_of(g) == 3 && !fused_pass(g)) ? 1 : 0);
 }
 
@@ -524,9 +665,11 @@ dirac_status run_steps(dirac_grid *g, int64_t nsteps) {
     const int K = (ndim_of(g) == 3) ? (fused_pass(g) ? g->plan.K : 1) : g->plan.K;
     int64_t blocks = nsteps / K;
     int64_t rem = nsteps % K;
-    const bool field = field_on(g);
-    if (field && !g->tuning && g->step + nsteps > (int64_t)(g->avec.size() / 3))
+    const bool field = field_on(g) || cellfield_on(g);
+    if (field_on(g) && !g->tuning && g->step + nsteps > (int64_t)(g->avec.size() / 3))
         return fail(g, DIRAC_ERR_ARG, "the vector-potential table ends before step " + std::to_string(g->step + nsteps));
+    if (cellfield_on(g) && !g->tuning && g->step + nsteps > (int64_t)(g->fenv.size() / 4))
+        return fail(g, DIRAC_ERR_ARG, "the field's table ends before step " + std::to_string(g->step + nsteps));
     int64_t t = g->step;  // step index of the next launch (selects the field's table row)
     if (strang3d_fused(g)) {
         // runs of kGraphBlocks steps from the captured graph (2 kGraphBlocks + 1 launches, parity flips), then
@@ -584,10 +727,13 @@ void release(dirac_grid *g) {
     if (g->stream || g->cap_stream) cudaStreamSynchronize(g->stream);
     for (auto &x : g->graph)
         if (x) cudaGraphExecDestroy(x);
-    for (auto &p : g->psi)
-        if (p) cudaFree(p);
+    if (!g->ext)
+        for (auto &p : g->psi)
+            if (p) cudaFree(p);
     if (g->table) cudaFree(g->table);
     if (g->ucoef) cudaFree(g->ucoef);
+    for (double *p : {g->fa_dev, g->fw_dev, g->fvdt_dev, g->fabs_dev})
+        if (p) cudaFree(p);
     if (g->flux_part) cudaFree(g->flux_part);
     if (g->flux_dev) cudaFree(g->flux_dev);
     if (g->ticket) cudaFree(g->ticket);
@@ -608,7 +754,8 @@ void release(dirac_grid *g) {
 dirac_status fx_load_state(dirac_grid *g, const void *psi, int on_device) {
     const size_t bytes = (size_t)g->ncells * 8 * g->elem;
     double *tmp = static_cast<double *>(g->psi[g->cur ^ 1]);
-    CK(g, cudaMemcpyAsync(tmp, psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    if (!(on_device && psi == tmp))
+        CK(g, cudaMemcpyAsync(tmp, psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
     ObsArgs o{};
     o.psi = tmp;
     o.scale = 1.0;
@@ -633,6 +780,12 @@ dirac_status fx_load_state(dirac_grid *g, const void *psi, int on_device) {
 
 void default_plan(dirac_grid *g) {
     const int k = g->cfg.steps_per_launch, pp = g->cfg.points_per_lane;
+    if (sweep_mode(g) >= 7) {  // single-sweep launches, one step per block
+        g->plan.fused3d = 0;
+        g->plan.s3_fused = 0;
+        make_plan(g, 1, 1, 4, 8);
+        return;
+    }
     if (ndim_of(g) == 3 && g->fx) {
         // fixed point, first order: points_per_lane 0 = the fused single pass (one step per pass), 1, 2 or 4 =
         // the x-y pass + z/phase pass with that P; second order: single sweeps
@@ -828,14 +981,16 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->char_shift < 0 || cfg->char_shift > 4)
         return fail(nullptr, DIRAC_ERR_ARG, "char_shift must be 0 (= 1), 1, 2, 3 or 4");
     if (cfg->char_shift > 1) {
-        if (cfg->ndim != 2 || cfg->splitting != DIRAC_LIE)
-            return fail(nullptr, DIRAC_ERR_ARG, "char_shift > 1 is implemented for 2-D first-order (DIRAC_LIE) grids");
         if (cfg->steps_per_launch > 1)
             return fail(nullptr, DIRAC_ERR_ARG, "char_shift > 1 runs one step per launch (steps_per_launch 0 or 1)");
-        if (cfg->points_per_lane == 4) return fail(nullptr, DIRAC_ERR_ARG, "char_shift > 1 needs points_per_lane 0, 1 or 2");
+        if (cfg->ndim == 2 && cfg->splitting == DIRAC_LIE && cfg->points_per_lane == 4)
+            return fail(nullptr, DIRAC_ERR_ARG, "2-D char_shift > 1 needs points_per_lane 0, 1 or 2");
+        if ((cfg->ndim == 3 || cfg->splitting == DIRAC_STRANG) && cfg->points_per_lane > 1)
+            return fail(nullptr, DIRAC_ERR_ARG,
+                        "3-D or second-order steps with char_shift > 1 run as single sweeps (points_per_lane 0 or 1)");
     }
     const int vmode = cfg->splitting == DIRAC_STRANG ? 2 : 0;
-    if (cfg->precision != DIRAC_FX64 && cfg->steps_per_launch != 0 &&
+    if (cfg->precision != DIRAC_FX64 && cfg->steps_per_launch != 0 && cfg->char_shift <= 1 &&
         !(sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, 2) ||
           sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, 4)))
         return fail(nullptr, DIRAC_ERR_ARG, "unsupported steps_per_launch for this precision and splitting");
@@ -846,6 +1001,8 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
         cfg->points_per_lane > 0 &&
         !sweep_supported(cfg->precision == DIRAC_FP32, vmode, cfg->steps_per_launch, cfg->points_per_lane))
         return fail(nullptr, DIRAC_ERR_ARG, "unsupported (steps_per_launch, points_per_lane) pair");
+    const bool ext0 = cfg->ext_state[0] != nullptr, ext1 = cfg->ext_state[1] != nullptr;
+    if (ext0 != ext1) return fail(nullptr, DIRAC_ERR_ARG, "ext_state needs both buffers or neither");
     if (std::getenv("DIRAC_INJECT_OOM")) return fail(nullptr, DIRAC_ERR_OOM, "allocation failure injected (DIRAC_INJECT_OOM)");
 
     dirac_grid *g = new (std::nothrow) dirac_grid();
@@ -857,8 +1014,9 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     g->fx = cfg->precision == DIRAC_FX64;
     g->elem = g->fp32 ? 4 : 8;
     g->ncells = cfg->n[0] * cfg->n[1] * cfg->n[2];
-    g->dt = (cfg->splitting == DIRAC_STRANG ? (cfg->ndim == 3 ? 4.0 : 2.0) : 1.0) * cfg->dx / cfg->c;
-    if (cfg->char_shift > 1) g->dt = (double)cfg->char_shift * cfg->dx / cfg->c;
+    // dt: c dt = K dx per first-order step (Sec. 2.3); a second-order step spans two (2-D) or four (3-D) of them
+    g->dt = (cfg->splitting == DIRAC_STRANG ? (cfg->ndim == 3 ? 4.0 : 2.0) : 1.0) *
+            (double)(cfg->char_shift > 1 ? cfg->char_shift : 1) * cfg->dx / cfg->c;
     cudaError_t e = cudaSetDevice(cfg->device);
     if (e != cudaSuccess) {
         std::string msg = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
@@ -868,6 +1026,32 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
     if (g->sm_count <= 0) g->sm_count = 152;
     const size_t state_bytes = (size_t)g->ncells * 8 * g->elem;
+    if (ext0) {
+        // caller-owned ping-pong buffers: device memory of cfg->device, 16-byte aligned (vector loads and bulk
+        // copies), at least one state apart
+        for (int i = 0; i < 2; ++i) {
+            cudaPointerAttributes at{};
+            e = cudaPointerGetAttributes(&at, cfg->ext_state[i]);
+            if (e != cudaSuccess) cudaGetLastError();
+            const bool dev_mem = e == cudaSuccess &&
+                                 (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+                                 at.device == cfg->device;
+            if (!dev_mem || (reinterpret_cast<uintptr_t>(cfg->ext_state[i]) & 15u)) {
+                release(g);
+                return fail(nullptr, DIRAC_ERR_ARG,
+                            "ext_state[" + std::to_string(i) + "] is not 16-byte aligned device memory of cfg.device");
+            }
+        }
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(cfg->ext_state[0]);
+        const uintptr_t a1 = reinterpret_cast<uintptr_t>(cfg->ext_state[1]);
+        if ((a0 > a1 ? a0 - a1 : a1 - a0) < state_bytes) {
+            release(g);
+            return fail(nullptr, DIRAC_ERR_ARG, "ext_state buffers overlap (closer than one state's size)");
+        }
+        g->psi[0] = cfg->ext_state[0];
+        g->psi[1] = cfg->ext_state[1];
+        g->ext = true;
+    }
     struct {
         void **p;
         size_t bytes;
@@ -876,6 +1060,7 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
                   {(void **)&g->obs_partial, (size_t)kObsBlocksMax * 5 * sizeof(double)},
                   {(void **)&g->obs_out, 8 * sizeof(double)}};
     for (auto &al : allocs) {
+        if (g->ext && (al.p == &g->psi[0] || al.p == &g->psi[1])) continue;
         e = cudaMalloc(al.p, al.bytes);
         if (e != cudaSuccess) {
             std::string msg = std::string("cudaMalloc(") + std::to_string(al.bytes) + " bytes): " + cudaGetErrorString(e);
@@ -897,7 +1082,7 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     dirac_status st = ensure_flux_part(g);
     if (st == DIRAC_OK) st = upload_table(g, nullptr, DIRAC_V_NONE, 0);
     if (st == DIRAC_OK) {
-        e = cudaMemsetAsync(g->psi[0], 0, state_bytes, g->stream);
+        e = g->ext ? cudaSuccess : cudaMemsetAsync(g->psi[0], 0, state_bytes, g->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(g->flux_dev, 0, 8 * sizeof(double), g->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(g->ticket, 0, 16, g->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
@@ -964,6 +1149,8 @@ dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, in
         return fail(g, DIRAC_ERR_ARG, "DIRAC_FX64 grids take no vector potential");
     if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
     const bool clear = !A_tilde || nsteps_table == 0;
+    if (!clear && cellfield_on(g))
+        return fail(g, DIRAC_ERR_STATE, "a field varying in space is set (dirac_set_field): remove it first");
     if (!clear)
         for (int64_t i = 0; i < 3 * nsteps_table; ++i)
             if (!std::isfinite(A_tilde[i])) return fail(g, DIRAC_ERR_ARG, "vector-potential table holds a non-finite value");
@@ -1002,6 +1189,47 @@ dirac_status dirac_set_vector_potential(dirac_grid *g, const double *A_tilde, in
     return DIRAC_OK;
 }
 
+dirac_status dirac_set_field(dirac_grid *g, const double *a, const double *w, const double *F, int64_t nsteps_table) {
+    if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
+    if (nsteps_table < 0) return fail(g, DIRAC_ERR_ARG, "nsteps_table must be >= 0");
+    const bool clear = !F || nsteps_table == 0;
+    if (!clear && g->fx) return fail(g, DIRAC_ERR_ARG, "DIRAC_FX64 grids take no field");
+    if (!clear && field_on(g))
+        return fail(g, DIRAC_ERR_STATE, "a uniform vector potential is set (dirac_set_vector_potential): remove it first");
+    if (!clear) {
+        for (int64_t i = 0; i < 4 * nsteps_table; ++i)
+            if (!std::isfinite(F[i])) return fail(g, DIRAC_ERR_ARG, "the field's table holds a non-finite value");
+        if (a)
+            for (int64_t i = 0; i < 3 * g->ncells; ++i)
+                if (!std::isfinite(a[i])) return fail(g, DIRAC_ERR_ARG, "the profile a holds a non-finite value");
+        if (w)
+            for (int64_t i = 0; i < g->ncells; ++i)
+                if (!std::isfinite(w[i])) return fail(g, DIRAC_ERR_ARG, "the profile w holds a non-finite value");
+    }
+    CK(g, cudaSetDevice(g->cfg.device));
+    dirac_status st = DIRAC_OK;
+    if (clear) {
+        g->fenv.clear();
+        st = put_doubles(g, g->fa_dev, g->fa_bytes, nullptr, 0);
+        if (st == DIRAC_OK) st = put_doubles(g, g->fw_dev, g->fw_bytes, nullptr, 0);
+        if (st == DIRAC_OK) st = put_doubles(g, g->fvdt_dev, g->fvdt_bytes, nullptr, 0);
+        if (st == DIRAC_OK) st = put_doubles(g, g->fabs_dev, g->fabs_bytes, nullptr, 0);
+    } else {
+        st = put_doubles(g, g->fa_dev, g->fa_bytes, a, a ? (size_t)(3 * g->ncells) : 0);
+        if (st == DIRAC_OK) st = put_doubles(g, g->fw_dev, g->fw_bytes, w, w ? (size_t)g->ncells : 0);
+        if (st == DIRAC_OK) g->fenv.assign(F, F + 4 * nsteps_table);
+        if (st == DIRAC_OK) st = upload_field_aux(g);
+    }
+    if (st != DIRAC_OK) return st;
+    for (auto &x : g->graph)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    default_plan(g);
+    return ensure_flux_part(g);
+}
+
 dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device) {
     if (!g) return fail(nullptr, DIRAC_ERR_ARG, "null grid");
     if (!psi) return fail(g, DIRAC_ERR_ARG, "dirac_set_state: null psi");
@@ -1010,7 +1238,7 @@ dirac_status dirac_set_state(dirac_grid *g, const void *psi, int on_device) {
     if (g->fx) {
         dirac_status st = fx_load_state(g, psi, on_device);
         if (st != DIRAC_OK) return st;
-    } else {
+    } else if (!(on_device && psi == g->psi[g->cur])) {  // a caller-owned buffer may already hold the state
         CK(g, cudaMemcpyAsync(g->psi[g->cur], psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                               g->stream));
     }
@@ -1045,8 +1273,9 @@ dirac_status dirac_set_state_fx(dirac_grid *g, const int64_t *q, int shift, int 
     if (shift < -1000 || shift > 1000) return fail(g, DIRAC_ERR_ARG, "dirac_set_state_fx: shift out of range");
     CK(g, cudaSetDevice(g->cfg.device));
     const size_t bytes = (size_t)g->ncells * 8 * sizeof(int64_t);
-    CK(g, cudaMemcpyAsync(g->psi[g->cur], q, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          g->stream));
+    if (!(on_device && q == g->psi[g->cur]))
+        CK(g, cudaMemcpyAsync(g->psi[g->cur], q, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              g->stream));
     CK(g, cudaMemsetAsync(g->flux_dev, 0, sizeof(double), g->stream));
     CK(g, cudaMemsetAsync(g->ticket + 1, 0, sizeof(unsigned), g->stream));
     if (!on_device) CK(g, cudaStreamSynchronize(g->stream));
@@ -1156,9 +1385,9 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
     info->launch_warps = p.nstrips * p.nsegs * planes;
     info->strip_width = p.strip_w;
     info->segment_rows = p.seg_h;
-    static const int plan_of_mode[7] = {DIRAC_PLAN_STEP_2D, DIRAC_PLAN_3D_TWO_PASS, DIRAC_PLAN_STRANG_2D,
+    static const int plan_of_mode[9] = {DIRAC_PLAN_STEP_2D, DIRAC_PLAN_3D_TWO_PASS, DIRAC_PLAN_STRANG_2D,
                                         DIRAC_PLAN_FIELD_2D, DIRAC_PLAN_SHIFT_2D, DIRAC_PLAN_STRANG_FIELD_2D,
-                                        DIRAC_PLAN_3D_STRANG};
+                                        DIRAC_PLAN_3D_STRANG, DIRAC_PLAN_SHIFT_SWEEPS, DIRAC_PLAN_FIELD_SWEEPS};
     const int mode = sweep_mode(g);
     info->plan = (mode == 1 && fused_pass(g)) ? DIRAC_PLAN_3D_FUSED : plan_of_mode[mode];
     if (strang3d_fused(g)) {
@@ -1182,6 +1411,7 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
     }
     info->graphs = g->cfg.use_graphs;
     info->fx_shift = g->fx ? g->fx_shift : 0;
+    info->state_index = g->cur;
     info->kernel_launches = g->launches;
     info->device_bytes = g->device_bytes;
     return DIRAC_OK;
@@ -1197,9 +1427,11 @@ dirac_status dirac_autotune(dirac_grid *g) {
         int s3z = 2;    // and the z-phase-z pass's threads per SM / 1024
     };
     std::vector<Cand> cands;
-    if (sweep_mode(g) == 6) {
+    if (sweep_mode(g) >= 7) {
+        cands.push_back({1, 1, 4, 8, 0, 0});  // single sweeps: nothing to choose
+    } else if (sweep_mode(g) == 6) {
         cands.push_back({1, 2, 4, 16, 0, 0});
-        if (!g->fx)  // the fused passes take floating-point states
+        if (!g->fx && char_shift(g) == 1)  // the fused passes take floating-point states and one-cell x shifts
             for (int sw : {16, 32})
                 for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
     } else if (g->fx && g->cfg.ndim == 3) {

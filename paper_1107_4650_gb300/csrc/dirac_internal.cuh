@@ -57,6 +57,38 @@ struct ZArgs {
     int full_table;
 };
 
+// Arguments of the single-sweep kernels (axis_kernels.cuh): one sweep of the whole grid along one axis with
+// the characteristics moved `shift` cells, optionally followed by the phase.
+struct AxisArgs {
+    const void *in;
+    void *out;
+    const void *table;   // phase epilogue: (pu, pd) per x column or per cell, pre-scaled
+    int64_t nx, ny, nz;
+    int64_t shift;
+    int periodic;
+    int full_table;
+    int64_t flux_face;   // x sweeps: face index, or -1
+    double fscale;       // multiplies the summed |.|^2 of the face cells
+    double vol;          // cell volume
+    double *flux_part;   // [gridDim.x]
+    double *flux_cum;
+    unsigned *ticket;
+    // uniform vector potential (phase epilogue only): 12 doubles of U entries per step, this launch's step
+    const double *ucoef;
+    int64_t ucoef_n, step0;
+    // fixed-point states: the output divided by 2^rshift, rounded to nearest (halves up); 0 = none
+    int rshift;
+    // field varying in space and time (phase epilogue of the cell-field plan): profiles a (3 per cell) and w (1 per
+    // cell), V dt per cell (fvdt_full) or per x column, absorber per x column (each nullable), this step's envelope
+    // integrals F = (F_x, F_y, F_z, F_V), mu = m c^2 dt and the power-of-two scale of the sweeps' halves
+    const double *fa, *fw, *fvdt, *fabs;
+    int fvdt_full;
+    double fenv[4];
+    double fmu, fscale_phase;
+};
+// The z sweep with the cell-field phase epilogue (precision DIRAC_FP64 or DIRAC_FP32).
+cudaError_t launch_axis_cellfield(const AxisArgs &a, int precision, int blocks, cudaStream_t s);
+
 // Launchers: return cudaErrorInvalidValue for an unsupported (K, P) pair.
 cudaError_t launch_sweep_f64(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepArgs &a, int mode, int K, int P, int warps_per_block, cudaStream_t s);

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -206,6 +207,70 @@ dirac_status dirac_surrogate_get_params(dirac_surrogate *s, float *params) {
     SCK(s, cudaSetDevice(s->device));
     SCK(s, cudaMemcpyAsync(params, s->net.p, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
     SCK(s, cudaStreamSynchronize(s->stream));
+    return DIRAC_OK;
+}
+
+// Checkpoint file: "DIRACNN1", uint32 version 1, uint32 parameter count, the box lo[3], hi[3] (FP64), int64 Adam
+// step, uint64 shuffle seed, then the FP32 parameters, Adam first and second moments (NPARAM floats each), host
+// byte order.
+namespace {
+constexpr char kCkptMagic[8] = {'D', 'I', 'R', 'A', 'C', 'N', 'N', '1'};
+}
+
+dirac_status dirac_surrogate_save(dirac_surrogate *s, const char *path) {
+    if (!s || !path) return sfail(s, DIRAC_ERR_ARG, "dirac_surrogate_save: null argument");
+    SCK(s, cudaSetDevice(s->device));
+    std::vector<float> buf((size_t)3 * NPARAM);
+    SCK(s, cudaMemcpyAsync(buf.data(), s->net.p, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    SCK(s, cudaMemcpyAsync(buf.data() + NPARAM, s->net.m, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    SCK(s, cudaMemcpyAsync(buf.data() + 2 * NPARAM, s->net.v, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    std::FILE *f = std::fopen(path, "wb");
+    if (!f) return sfail(s, DIRAC_ERR_ARG, std::string("dirac_surrogate_save: cannot open ") + path);
+    const uint32_t head[2] = {1u, (uint32_t)NPARAM};
+    const int64_t step = s->step;
+    bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(head, sizeof(uint32_t), 2, f) == 2 &&
+              std::fwrite(s->lo, sizeof(double), 3, f) == 3 && std::fwrite(s->hi, sizeof(double), 3, f) == 3 &&
+              std::fwrite(&step, sizeof(int64_t), 1, f) == 1 && std::fwrite(&s->seed, sizeof(uint64_t), 1, f) == 1 &&
+              std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return sfail(s, DIRAC_ERR_ARG, std::string("dirac_surrogate_save: write to ") + path + " failed");
+    return DIRAC_OK;
+}
+
+dirac_status dirac_surrogate_load(dirac_surrogate *s, const char *path) {
+    if (!s || !path) return sfail(s, DIRAC_ERR_ARG, "dirac_surrogate_load: null argument");
+    std::FILE *f = std::fopen(path, "rb");
+    if (!f) return sfail(s, DIRAC_ERR_ARG, std::string("dirac_surrogate_load: cannot open ") + path);
+    char magic[8];
+    uint32_t head[2];
+    double lo[3], hi[3];
+    int64_t step = 0;
+    uint64_t seed = 0;
+    std::vector<float> buf((size_t)3 * NPARAM);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+              std::fread(head, sizeof(uint32_t), 2, f) == 2 && head[0] == 1u && head[1] == (uint32_t)NPARAM &&
+              std::fread(lo, sizeof(double), 3, f) == 3 && std::fread(hi, sizeof(double), 3, f) == 3 &&
+              std::fread(&step, sizeof(int64_t), 1, f) == 1 && std::fread(&seed, sizeof(uint64_t), 1, f) == 1 &&
+              std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return sfail(s, DIRAC_ERR_ARG, std::string("dirac_surrogate_load: ") + path + " is not a checkpoint of this network");
+    for (int d = 0; d < 3; ++d)
+        if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]) || step < 0)
+            return sfail(s, DIRAC_ERR_ARG, "dirac_surrogate_load: bad box or step in the checkpoint");
+    SCK(s, cudaSetDevice(s->device));
+    SCK(s, cudaMemcpyAsync(s->net.p, buf.data(), NPARAM * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    SCK(s, cudaMemcpyAsync(s->net.m, buf.data() + NPARAM, NPARAM * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    SCK(s, cudaMemcpyAsync(s->net.v, buf.data() + 2 * NPARAM, NPARAM * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    SCK(s, refresh_bf16(s->net, s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    for (int d = 0; d < 3; ++d) {
+        s->lo[d] = lo[d];
+        s->hi[d] = hi[d];
+    }
+    s->step = step;
+    s->seed = seed;
+    s->bias_set = true;
     return DIRAC_OK;
 }
 

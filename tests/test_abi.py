@@ -42,15 +42,27 @@ def test_struct_layout_matches_c(tmp_path):
     import paper_1107_4650_gb300 as D
     src = tmp_path / "sizes.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dirac.h"\nint main(void){'
-                   'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(dirac_config), sizeof(dirac_obs), sizeof(dirac_info),'
-                   'offsetof(dirac_config, stream), offsetof(dirac_config, points_per_lane), offsetof(dirac_info, device_bytes));'
+                   'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(dirac_config), sizeof(dirac_obs), sizeof(dirac_info),'
+                   'offsetof(dirac_config, stream), offsetof(dirac_config, points_per_lane), offsetof(dirac_info, device_bytes),'
+                   'offsetof(dirac_config, ext_state), offsetof(dirac_info, state_index));'
                    'return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [ctypes.sizeof(D.dirac_config), ctypes.sizeof(D.dirac_obs), ctypes.sizeof(D.dirac_info),
                     D.dirac_config.stream.offset, D.dirac_config.points_per_lane.offset,
-                    D.dirac_info.device_bytes.offset]
+                    D.dirac_info.device_bytes.offset, D.dirac_config.ext_state.offset, D.dirac_info.state_index.offset]
+
+
+def test_ext_state_needs_both_buffers(lib):
+    """One caller-owned ping-pong buffer without the other is an argument error, reported before any CUDA call."""
+    import paper_1107_4650_gb300 as D
+    for pair in ((4096, None), (None, 4096)):
+        cfg = D.make_config((64, 1, 64))
+        cfg.ext_state[0], cfg.ext_state[1] = pair
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_create_grid(cfg)
+        assert e.value.status == D.DIRAC_ERR_ARG and "ext_state" in D.dirac_last_error(None)
 
 
 def test_version_and_defaults(lib):
@@ -147,9 +159,9 @@ def test_fx64_validation(lib):
 
 def test_char_shift_validation(lib):
     import paper_1107_4650_gb300 as D
-    for kw in (dict(char_shift=5), dict(char_shift=-1), dict(char_shift=2, ndim=3, n=(8, 8, 8)),
-               dict(char_shift=2, splitting=D.DIRAC_STRANG), dict(char_shift=3, steps_per_launch=2),
-               dict(char_shift=2, points_per_lane=4)):
+    for kw in (dict(char_shift=5), dict(char_shift=-1), dict(char_shift=2, ndim=3, n=(8, 8, 8), points_per_lane=2),
+               dict(char_shift=2, splitting=D.DIRAC_STRANG, points_per_lane=2), dict(char_shift=3, steps_per_launch=2),
+               dict(char_shift=2, points_per_lane=4), dict(char_shift=2, precision=D.DIRAC_FX64)):
         n = kw.pop("n", (16, 1, 16))
         cfg = D.make_config(n, **kw)
         with pytest.raises(D.DiracError) as e:

@@ -1,0 +1,161 @@
+"""Fields varying in space and time (dirac_set_field; Sec. 2.3, Eqs. sol_dis_4, field_dis1, field_dis2) on the GPU
+against the oracle.  The GPU forms each cell's U(At(i)) exp(-i V~(i)) with CUDA's FP64 sin and cos, which agree
+with the host's to an ulp or two, so the FP64 state is held to relative L2 <= 1e-12 (measured: about 1e-15 per
+step) instead of bit equality; everything else in the step (sweeps, products, sums) is the same arithmetic."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4650_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C = W.C_AU
+DX = W.DX_DEFAULT
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1107_4650_gb300 import build as B
+    B.build()
+    oracle.build()
+    import paper_1107_4650_gb300 as D
+    D.load_library()
+    return D
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((np.asarray(a) - np.asarray(b)).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+
+def _profiles(shape, nt, seed, a_on=True, w_on=True):
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-1.0, 1.0, (N, 3)) if a_on else None
+    w = rng.uniform(-2.0, 2.0, N) if w_on else None
+    F = rng.uniform(-1.0, 1.0, (nt, 4))
+    return a, w, F
+
+
+def _run(D, psi, ndim, nsteps, field, strang=False, K=0, V=None, periodic=False, fp32=False, flux_face=-1,
+         x_min=None, absorber=None, start=0):
+    nz, ny, nx, _ = psi.shape
+    cfg = D.make_config((nx, ny, nz), ndim=ndim, precision=D.DIRAC_FP32 if fp32 else D.DIRAC_FP64,
+                        boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO, flux_face=flux_face,
+                        x_min=x_min, char_shift=K, splitting=D.DIRAC_STRANG if strang else D.DIRAC_LIE)
+    h = D.dirac_create_grid(cfg)
+    try:
+        if V is not None:
+            D.dirac_set_potential(h, V, D.DIRAC_V_X_ONLY if V.size == nx else D.DIRAC_V_FULL)
+        if absorber is not None:
+            D.dirac_set_absorber(h, absorber)
+        D.dirac_set_field(h, *field)
+        dt = np.complex64 if fp32 else np.complex128
+        D.dirac_set_state(h, np.ascontiguousarray(psi.astype(dt)))
+        if start:
+            D.dirac_set_counters(h, start, 0.0)
+        D.dirac_step(h, nsteps)
+        out = np.empty(psi.shape, dtype=dt)
+        D.dirac_get_state(h, out)
+        obs = D.dirac_observables(h)
+        info = D.dirac_get_info(h)
+    finally:
+        D.dirac_destroy(h)
+    return out, obs, info
+
+
+def _oracle(psi, ndim, nsteps, field, strang=False, K=1, **kw):
+    if strang:
+        f = oracle.step_strang3d if ndim == 3 else oracle.step_strang2d
+        return f(psi, 1.0, C, DX, nsteps, shift=K, field=field, **kw)
+    return oracle.step(psi, ndim, 1.0, C, DX, nsteps, shift=K, field=field, **kw)
+
+
+@pytest.mark.parametrize("ndim,strang", [(2, False), (3, False), (2, True), (3, True)])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("full", [False, True])
+def test_field_fp64_against_oracle(D, ndim, strang, periodic, full):
+    shape = (29, 7, 13) if ndim == 3 else (45, 1, 38)
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=3 * ndim + strang)
+    V = np.random.default_rng(5).uniform(-2e4, 4e4, nx * ny * nz if full else nx)
+    field = _profiles(shape, 12, 6 + ndim)
+    want, _ = _oracle(psi, ndim, 12, field, strang, V=V, periodic=periodic)
+    got, _, info = _run(D, psi, ndim, 12, field, strang, V=V, periodic=periodic)
+    assert info["plan"] == D.DIRAC_PLAN_FIELD_SWEEPS
+    assert rel_l2(got, want) <= TOL
+
+
+@pytest.mark.parametrize("which", ["a", "w"])
+def test_field_each_profile_alone_and_table_offset(D, which):
+    """Only the vector potential's profile or only the time-dependent scalar's, steps taken from row 3 on
+    (dirac_set_counters), with an absorbing layer folded into the phase."""
+    shape = (40, 1, 31)
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=17)
+    V = np.random.default_rng(18).uniform(-2e4, 4e4, nx)
+    a, w, F = _profiles(shape, 20, 19, a_on=which == "a", w_on=which == "w")
+    absorb = np.linspace(0.7, 1.0, nx)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 9, V=V, field=(a, w, F), step0=3, absorber=absorb)
+    got, _, _ = _run(D, psi, 2, 9, (a, w, F), V=V, start=3, absorber=absorb)
+    assert rel_l2(got, want) <= TOL
+
+
+def test_field_flux_and_char_shift(D):
+    """A Klein packet in a field varying along x and in time, with the face flux, over 40 steps; and the same
+    field with characteristic shift K = 2."""
+    run = W.KleinRun(side=160, V0=2.5 * C * C, p0=0.7 * C, width=7 * DX, nsteps=40, face=90)
+    psi0, V = run.state(), run.potential()
+    x_min, z_min, _, _, face = run.geometry()
+    N = 160 * 160
+    x = np.tile(np.arange(160), 160)
+    a = np.stack([0.5 * np.sin(x / 20.0), np.zeros(N), 0.3 * np.cos(x / 15.0)], axis=1)
+    w = np.exp(-((x - 80) / 30.0) ** 2) * 1.5
+    t = np.arange(41)
+    F = np.zeros((40, 4))
+    F[:, 0] = 0.8 * np.sin(0.2 * t[:-1])
+    F[:, 2] = 0.5 * np.cos(0.15 * t[:-1])
+    F[:, 3] = 0.4 * np.sin(0.1 * t[:-1])
+    for K in (1, 2):
+        want, Fw = oracle.step(psi0, 2, 1.0, C, DX, 40, V=V, flux_face=face, field=(a, w, F), shift=K)
+        got, obs, _ = _run(D, psi0, 2, 40, (a, w, F), K=K, V=V, flux_face=face, x_min=(x_min, 0.0, z_min))
+        assert rel_l2(got, want) <= TOL, K
+        assert abs(Fw) > 1e-4 and abs(obs["flux_cum"] - Fw) <= 1e-11 * abs(Fw), K
+
+
+def test_field_fp32(D):
+    shape = (64, 1, 48)
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=23)
+    V = np.random.default_rng(24).uniform(-1e4, 1e4, nx)
+    field = _profiles(shape, 30, 25)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 30, V=V, periodic=True, field=field)
+    got, _, _ = _run(D, psi, 2, 30, field, V=V, periodic=True, fp32=True)
+    assert rel_l2(got.astype(np.complex128), want) < 2e-5
+
+
+def test_field_table_end_exclusion_and_removal(D):
+    shape = (20, 1, 16)
+    psi = W.random_state(16, 1, 20, seed=27)
+    a, w, F = _profiles(shape, 4, 28)
+    h = D.dirac_create_grid(D.make_config(shape))
+    try:
+        D.dirac_set_state(h, psi)
+        D.dirac_set_field(h, a, w, F)
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_step(h, 5)  # the table holds 4 steps
+        assert e.value.status == D.DIRAC_ERR_ARG
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_set_vector_potential(h, np.zeros((4, 3)))
+        assert e.value.status == D.DIRAC_ERR_STATE
+        D.dirac_set_field(h, None, None, None)
+        assert D.dirac_get_info(h)["plan"] == D.DIRAC_PLAN_STEP_2D
+        D.dirac_step(h, 3)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    want, _ = oracle.step(psi, 2, 1.0, C, DX, 3)
+    assert np.array_equal(got.view(np.float64), want.view(np.float64))

@@ -90,8 +90,10 @@ def _solve(D, qs, fp32):
 
 
 def test_klein_surrogate_small_box(D):
-    """1024 batched FP32 solves train the network; 48 held-out points are checked against the FP64 solver; queries
-    outside the box fall back to the solver; the network answers >= 100x faster than per-run FP64 solves."""
+    """Training from scratch inside the test (a smoke test of the training path, not the accuracy claim, which the
+    shipped network's test above holds to |dT| <= 1e-3): 1024 batched FP32 solves train the network for 1500 epochs;
+    48 held-out points are checked against the FP64 solver; queries outside the box fall back to the solver; the
+    network answers >= 100x faster than per-run FP64 solves."""
     rng = np.random.default_rng(11)
     q_train = LO + (HI - LO) * rng.uniform(0, 1, (1024, 3))
     T_train = _solve(D, q_train, fp32=True)
@@ -121,13 +123,15 @@ def test_klein_surrogate_small_box(D):
 
 def test_shipped_checkpoint_against_fp64_solver(D):
     """The shipped network (20000 FP32-labelled runs over V0/mc^2 in [0.5, 3], p0/mc in [0.2, 1], width/dx in
-    [40, 150]) predicts the FP64 batched solver's transmission on fresh points of the box."""
+    [40, 150]) predicts the FP64 batched solver's transmission on 64 fresh points of the box to the scope's bar
+    |dT| <= 1e-3: the mean within it and at most one point (the held-out 1000 had one, 1.1e-3) above it, that
+    one below 2e-3."""
     import os
     path = os.path.join(os.path.dirname(D.__file__), "data", "surrogate_klein_box.npz")
     z = np.load(path)
     lo, hi = z["lo"], z["hi"]
     rng = np.random.default_rng(W.SEED + 5)
-    q = lo + (hi - lo) * rng.uniform(0.0, 1.0, (24, 3))
+    q = lo + (hi - lo) * rng.uniform(0.0, 1.0, (64, 3))
     h = D.dirac_surrogate_create(lo, hi, seed=0, max_batch=64)
     try:
         D.dirac_surrogate_set_params(h, z["params"])
@@ -139,4 +143,36 @@ def test_shipped_checkpoint_against_fp64_solver(D):
     cfg.steps_per_launch = 2
     T64, _ = D.dirac_batch_klein([D.dirac_klein_run_from_reduced(x, DX, C, 1.0) for x in q], cfg)
     dT = np.abs(T_net - T64)
-    assert dT.mean() < 1e-3 and dT.max() < 5e-3, (dT.mean(), dT.max())
+    print("shipped surrogate on 64 fresh points: mean |dT| %.2e, p99 %.2e, max %.2e"
+          % (dT.mean(), np.percentile(dT, 99), dT.max()))
+    assert dT.mean() <= 1e-3 and np.sum(dT > 1e-3) <= 1 and dT.max() < 2e-3, (dT.mean(), dT.max())
+
+
+def test_checkpoint_save_load_resumes_training(D, tmp_path):
+    """A checkpoint restores the box, parameters and Adam state: training on after a reload gives the same
+    parameters as training on without it, and a foreign file is rejected."""
+    rng = np.random.default_rng(21)
+    q = LO + (HI - LO) * rng.uniform(0, 1, (512, 3))
+    t = rng.uniform(0, 0.5, 512)
+    path = str(tmp_path / "net.ckpt")
+    h = D.dirac_surrogate_create(LO, HI, seed=3, max_batch=256)
+    try:
+        D.dirac_surrogate_train(h, q, t, 2, 128, 1e-3)
+        D.dirac_surrogate_save(h, path)
+        D.dirac_surrogate_train(h, q, t, 2, 128, 1e-3)
+        want = D.dirac_surrogate_get_params(h)
+    finally:
+        D.dirac_surrogate_destroy(h)
+    h2 = D.dirac_surrogate_create(np.zeros(3), np.ones(3), seed=99, max_batch=256)
+    try:
+        D.dirac_surrogate_load(h2, path)
+        D.dirac_surrogate_train(h2, q, t, 2, 128, 1e-3)
+        got = D.dirac_surrogate_get_params(h2)
+        bad = tmp_path / "bad.ckpt"
+        bad.write_bytes(b"not a checkpoint")
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_surrogate_load(h2, str(bad))
+        assert e.value.status == D.DIRAC_ERR_ARG
+    finally:
+        D.dirac_surrogate_destroy(h2)
+    assert np.array_equal(got, want)
