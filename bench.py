@@ -774,7 +774,42 @@ def main():
             "workload": "%d independent 2-D Klein runs, sides %s, 2000-6000 steps, one persistent kernel per "
                         "block of steps, graph-replayed; %d drawn sides raised to hold the packet"
                         % (len(runs), sorted(set(r.side for r in runs)), len(deviations)),
-            "T_mean": float(np.mean(bres["T"])), "T_min": float(np.min(bres["T"])), "T_max": float(np.max(bres["T"]))}
+            "T_mean": float(np.mean(bres["T"])), "T_min": float(np.min(bres["T"])), "T_max": float(np.max(bres["T"])),
+            "T_lower_bound": -W.packet_mass_right_of_step(),
+            "T_lower_bound_note": "T is the net flux through the face over the initial norm; the part of the packet "
+                                  "already right of the step (erfc(4/sqrt 2)/2 = 3.2e-5 for a packet 4 widths "
+                                  "left of it) can flow back, so T >= -3.2e-5 in the gap where nothing transmits"}
+
+        # the same persistent kernel on an ensemble that keeps its drawn sides 256..1024 (packets narrowed to fit):
+        # how the task queue balances grids of uneven size and step count
+        runs_u, log_u = W.klein_ensemble_drawn_sides(args.batch_runs, seed=W.SEED + 7 + rank)
+        hu = D.dirac_batch_create([r.as_batch_fields() for r in runs_u], bcfg)
+        D.dirac_batch_autotune(hu)
+        D.dirac_batch_run(hu)
+        stream.synchronize()
+        D.dirac_batch_reset(hu)
+        stream.synchronize()
+        barrier()
+        eu0, eu1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eu0.record(stream)
+        D.dirac_batch_run(hu)
+        eu1.record(stream)
+        stream.synchronize()
+        tu = max_over_ranks(eu0.elapsed_time(eu1))
+        uinfo = D.dirac_batch_get_info(hu)
+        D.dirac_batch_destroy(hu)
+        ups = uinfo["point_steps"] * world / (tu / 1e3)
+        sides_u = [r.side for r in runs_u]
+        variants["batched_fp32_drawn_sides"] = {
+            "value": ups, "unit": "point-steps/s", "ms_per_pass": tu, "runs": len(runs_u),
+            "point_steps_per_pass": uinfo["point_steps"], "steps_per_launch": uinfo["steps_per_launch"],
+            "points_per_lane": uinfo["points_per_lane"], "segment_rows": uinfo["segment_rows"],
+            "effective_hbm_frac": FP32_BYTES_PER_POINT_STEP * ups / world / 1e9 / hbm_peak,
+            "runs_per_side": {str(sd): sides_u.count(sd) for sd in sorted(set(sides_u))},
+            "relative_to_raised_sides_ensemble": ups / bps,
+            "workload": "%d independent 2-D Klein runs keeping their drawn sides 256..1024 (widths capped to fit: %d "
+                        "of them), 16-column layers, 2000-6000 steps: the queue's balance over uneven grids"
+                        % (len(runs_u), len(log_u))}
 
     # ---------------------------------------------------------------- transmission surrogate
     ckpt = os.path.join(ROOT, "paper_1107_4650_gb300", "data", "surrogate_klein_box.npz")

@@ -91,12 +91,12 @@ template <typename T> __device__ __forceinline__ Cx<T> cmulp(Cx<T> z, Cx<T> p) {
 // from three products instead of four (k1 = p.re (z.re + z.im), k2 = z.re (p.im - p.re), k3 = z.im (p.re +
 // p.im); re = k1 - k3, im = k1 + k2): integer arithmetic, so the same bits.  |z| < 2^62 and |p| <= 2^60
 // keep the sums inside int64.
-__device__ __forceinline__ long long fx_round62(__int128 v) { return (long long)((v + ((__int128)1 << 61)) >> 62); }
+// The rounding offset 2^61 is added to k1 once, for both outputs: the same integers as rounding each.
 template <> __device__ __forceinline__ Cx<long long> cmulp<long long>(Cx<long long> z, Cx<long long> p) {
-    const __int128 k1 = (__int128)p.re * (z.re + z.im);
+    const __int128 k1 = (__int128)p.re * (z.re + z.im) + ((__int128)1 << 61);
     const __int128 k2 = (__int128)z.re * (p.im - p.re);
     const __int128 k3 = (__int128)z.im * (p.re + p.im);
-    return {fx_round62(k1 - k3), fx_round62(k1 + k2)};
+    return {(long long)((k1 - k3) >> 62), (long long)((k1 + k2) >> 62)};
 }
 // acc + z p with re = fma(z.re, p.re, fma(-z.im, p.im, acc.re)), im = fma(z.re, p.im, fma(z.im, p.re, acc.im))
 template <typename T> __device__ __forceinline__ Cx<T> cmac(Cx<T> acc, Cx<T> z, Cx<T> p) {
@@ -176,7 +176,10 @@ __device__ __forceinline__ int64_t pmod(int64_t a, int64_t n) {
 
 // Rows per iteration of the row loop (1 or 2; measured per variant: two rows let the history registers
 // alternate instead of moving, which pays where the loop body is short).
-template <typename T, int K, int MODE> struct RowUnroll { static constexpr int value = (sizeof(T) == 4 && K == 1 && MODE == 0) ? 2 : 1; };
+template <typename T, int K, int MODE> struct RowUnroll {
+    static constexpr bool FX = sizeof(T) == 8 && (T)0.5 == (T)0;  // the int64 fixed-point state
+    static constexpr int value = ((sizeof(T) == 4 || FX) && K == 1 && MODE == 0) ? 2 : 1;
+};
 template <typename T, int K, int P, int MODE, int UNR = RowUnroll<T, K, MODE>::value>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem);
 template <int K>
@@ -396,6 +399,8 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     const T *in = static_cast<const T *>(a.in) + plane * nr * nx * 8;
     T *out = static_cast<T *>(a.out) + plane * nr * nx * 8;
 
+    // every lane's cells lie inside the grid (or wrap): output rows inside the grid need no ghost-zero mask
+    const bool strip_in = per || (xa >= 0 && xa + 32 * P <= nx);
     int64_t xl[P];
     bool xin[P];
 #pragma unroll
@@ -676,9 +681,14 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                     push_row<T, UNR>(UH[0][lev][j], UH[1][lev][j], UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j], U14, U23);
                 }
                 if (need_out) {
-                    const bool keep = per || (out_row_ok && xin[j]);
+                    if (strip_in && out_row_ok) {  // warp-uniform: no cell of this row is a ghost cell
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) st[j][c] = keep ? o[c] : Cx<T>{T(0), T(0)};
+                        for (int c = 0; c < 4; ++c) st[j][c] = o[c];
+                    } else {
+                        const bool keep = per || (out_row_ok && xin[j]);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) st[j][c] = keep ? o[c] : Cx<T>{T(0), T(0)};
+                    }
                 } else {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) st[j][c] = Cx<T>{T(0), T(0)};

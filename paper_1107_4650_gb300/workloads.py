@@ -245,3 +245,43 @@ def klein_ensemble(nruns: int = 512, seed: int = SEED + 1, m: float = M_E, c: fl
         runs.append(KleinRun(side=side, V0=V0, p0=p0, width=w_cells * dx, nsteps=nsteps, dx=dx, L=4 * dx,
                              face=face, absorb=ABSORB_CELLS, eta=ABSORB_ETA))
     return runs, log
+
+
+DRAWN_SIDES_ABSORB = 16   # absorbing columns at each x edge in the drawn-sides ensemble
+DRAWN_SIDES_BEYOND = 32   # cells between the step and the right layer in the drawn-sides ensemble
+
+
+def klein_ensemble_drawn_sides(nruns: int = 512, seed: int = SEED + 7, m: float = M_E, c: float = C_AU):
+    """An ensemble whose runs keep their drawn sides U{256, 384, 512, 768, 1024}, for measuring how the persistent
+    kernel's task queue balances truly uneven grids (up to 16x in cells and 3x in steps).  V0, p0 and the width
+    are drawn as in klein_ensemble; the width is then capped so that the packet (4 widths left of the step, 4
+    widths of tail) fits the drawn side with 16-column absorbing layers and 32 cells beyond the step, so the
+    narrow grids carry narrow packets.  The transmissions of these runs are not the configuration's physics (the
+    short region beyond the step lets evanescent waves reach the layer); only their cost and balance matter.
+    Returns (runs, log) with every capped width logged."""
+    rng = np.random.default_rng(seed)
+    dx = DX_DEFAULT
+    runs, log = [], []
+    for r in range(nruns):
+        side = int(rng.choice(ALLOWED_SIDES))
+        V0 = rng.uniform(0.5, 3.0) * m * c * c
+        p0 = rng.uniform(0.2, 1.0) * m * c
+        w_cells = rng.uniform(40, 150)
+        cap = (side - 8 - DRAWN_SIDES_BEYOND - 2 * DRAWN_SIDES_ABSORB) / 8.0
+        if w_cells > cap:
+            log.append((r, "width", w_cells, cap))
+            w_cells = cap
+        E = np.sqrt(p0 * p0 * c * c + m * m * c ** 4)
+        nsteps = int(np.clip(np.ceil(8 * w_cells / (p0 * c / E)) + 200, 2000, 6000))
+        face = min(int(np.ceil(8 * w_cells)) + 8 + DRAWN_SIDES_ABSORB, side - DRAWN_SIDES_BEYOND - DRAWN_SIDES_ABSORB)
+        runs.append(KleinRun(side=side, V0=V0, p0=p0, width=w_cells * dx, nsteps=nsteps, dx=dx, L=4 * dx,
+                             face=face, absorb=DRAWN_SIDES_ABSORB, eta=ABSORB_ETA))
+    return runs, log
+
+
+def packet_mass_right_of_step(width_cells: float = 1.0) -> float:
+    """Fraction of a Gaussian packet |psi|^2 ~ exp(-(x - x0)^2 / (2 width^2)) centred 4 widths left of the step
+    that already lies right of it: erfc(4 / sqrt 2) / 2 (independent of the width).  The net flux through the
+    face, the ensembles' T, can go below zero by at most this much: that part can only flow back."""
+    from math import erfc, sqrt
+    return 0.5 * erfc(4.0 / sqrt(2.0))

@@ -223,3 +223,35 @@ def test_full_512_run_ensemble_sampled_outputs(D):
             want, _ = oracle.step(psi0[sz, :, sx], 2, 1.0, C, r.dx, 40, V=V[sx], absorber=a[sx])
             got = outs[i][z, 0, x]
             assert np.array_equal(got.view(np.float64), want[z - sz.start, 0, x - sx.start].view(np.float64)), (i, z, x)
+
+
+def test_gap_transmission_bounded_below_by_the_initial_tail(D):
+    """Runs whose packet energy lies in the gap |E - V0| < m c^2 of the step transmit nothing; their T, the net
+    flux through the face over the initial norm, is then the part of the packet that started right of the step
+    flowing back: T >= -erfc(4 / sqrt 2) / 2 = -3.2e-5 (the packet starts 4 widths left of the step), FP32 and FP64."""
+    q = [(1.2, 0.2, 40.0), (1.5, 0.25, 60.0), (0.9, 0.3, 45.0), (1.8, 0.2, 80.0)]
+    runs = [D.dirac_klein_run_from_reduced(x, DX, C, 1.0) for x in q]
+    bound = -W.packet_mass_right_of_step()
+    for prec in (D.DIRAC_FP32, D.DIRAC_FP64):
+        cfg = D.dirac_batch_default_config()
+        cfg.precision = prec
+        cfg.steps_per_launch = 2
+        T, _ = D.dirac_batch_klein(runs, cfg)
+        assert np.all(T >= bound * 1.02), (prec, T)
+        assert np.all(T < 1e-3), (prec, T)
+
+
+def test_drawn_sides_ensemble_keeps_its_sides_and_matches_the_oracle(D):
+    """The ensemble that keeps its drawn sides (the queue-balance workload): every allowed side occurs, and two of
+    its runs (the smallest and a large one, steps cut to 31) evolve in the batch as the oracle's single grid."""
+    runs, _ = W.klein_ensemble_drawn_sides(64, seed=W.SEED + 7)
+    assert {r.side for r in runs} == set(W.ALLOWED_SIDES)
+    small = min(runs, key=lambda r: r.side)
+    big = max(runs, key=lambda r: r.side)
+    pick = [W.KleinRun(side=r.side, V0=r.V0, p0=r.p0, width=r.width, nsteps=31, face=r.face, absorb=r.absorb,
+                       eta=r.eta) for r in (small, big)]
+    outs, res, _ = _run_batch(D, pick, fp32=False)
+    for i, r in enumerate(pick):
+        want, F = _oracle(r)
+        assert np.array_equal(outs[i].view(np.float64), want.view(np.float64))
+        assert abs(res["flux"][i] - F) <= 1e-12 * max(abs(F), 1e-30) + 1e-18
