@@ -643,9 +643,15 @@ def main():
                 elif prec == D.DIRAC_FX64:
                     # algorithmic: the state read and written once plus the per-cell int64 table (32 B); first
                     # order moves that in the fused pass and 2 x 128 + 32 B in its two passes, second order
-                    # 8 x 128 + 32 B in its eight single sweeps
-                    moved = (160 if i3["plan"] == D.DIRAC_PLAN_3D_FUSED else 288) if split == D.DIRAC_LIE \
-                        else 8 * 128 + 32
+                    # 8 x 128 + 32 B in its eight single sweeps or about 288 B in its fused passes
+                    if split == D.DIRAC_LIE:
+                        moved = 160 if i3["plan"] == D.DIRAC_PLAN_3D_FUSED else 288
+                    elif i3["plan"] == D.DIRAC_PLAN_3D_STRANG_FUSED:
+                        # per step a z-phase-z pass (128 B + the 32 B table) and an x-y pass (128 B), one more x-y
+                        # pass per run
+                        moved = 160 + 128 * (n_steps3 + 1) / n_steps3
+                    else:
+                        moved = 8 * 128 + 32
                     entry["bytes_per_point_step"] = 160
                     entry["hbm_frac"] = 160 * v3 / world / 1e9 / hbm_peak
                     entry["pass_bytes_per_point_step"] = moved

@@ -74,13 +74,6 @@ __device__ __forceinline__ void cell_field_matrix(const AxisArgs &a, int64_t c, 
     }
 }
 
-// Fixed point: o / 2^r rounded to nearest, halves upward (floating-point states never ask for it).
-template <typename T> __device__ __forceinline__ void round_shift(Cx<T> (&)[4], int) {}
-template <> __device__ __forceinline__ void round_shift<long long>(Cx<long long> (&o)[4], int r) {
-    const long long half = 1ll << (r - 1);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) o[q] = Cx<long long>{(o[q].re + half) >> r, (o[q].im + half) >> r};
-}
 
 template <typename T, int AXIS, bool PHASE, int FLD>
 __global__ void __launch_bounds__(256) axis_kernel(const AxisArgs a) {

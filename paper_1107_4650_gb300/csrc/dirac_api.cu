@@ -575,6 +575,13 @@ dirac_status enqueue_strang3d_run(dirac_grid *g, int parity, int64_t m, cudaStre
     static const double first_half[4] = {0.5, 0.5 / 16.0, 0.0, 0.0};
     static const double second_half[4] = {0.5 * 64.0, 0.5 * 4.0, 0.0, 0.0};
     static const double both_halves[4] = {0.5 * 64.0, 0.5 * 4.0, 0.5, 0.5 / 16.0};
+    // fixed point: the phase carries the first four halves (1/16), so the states entering a step's x sweeps are
+    // 1, 4, 2 and 8 times the true state and the step's last x sweep is followed by the division by 16
+    static const double first_half_fx[4] = {0.5, 0.5 / 16.0, 0.0, 0.0};
+    static const double second_half_fx[4] = {0.5 / 4.0, 0.5 / 64.0, 0.0, 0.0};
+    static const double both_halves_fx[4] = {0.5 / 4.0, 0.5 / 64.0, 0.5, 0.5 / 16.0};
+    const int prec = g->fx ? 2 : g->fp32;
+    const double funit = g->fx ? std::ldexp(1.0, -2 * g->fx_shift) : 1.0;
     SweepArgs a{};
     a.table = g->table;
     a.nx = g->cfg.n[0];
@@ -589,26 +596,31 @@ dirac_status enqueue_strang3d_run(dirac_grid *g, int parity, int64_t m, cudaStre
     const double *ucoef = field_on(g) ? g->ucoef : nullptr;
     const int64_t ucoef_n = (int64_t)(g->avec.size() / 3);
     int par = parity;
-    auto xy = [&](int nh, const double *fs) -> dirac_status {
+    // ends_step: the pass's last sweep ends a step (fixed point: divide by 16 there)
+    auto xy = [&](int nh, const double *fs, bool ends_step) -> dirac_status {
         const Plan::XY &q = p.s3_xy[nh - 1];
         a.in = g->psi[par];
         a.out = g->psi[par ^ 1];
         a.nsegs = q.nzsegs * q.nytiles * p.s3_warps;  // flux parts per x sweep
-        cudaError_t e = launch_strang_xy(a, g->fp32, p.s3_warps, nh, ny, nz, q.nstrips, q.nytiles, q.nzsegs, q.zseg_h,
-                                         fs, s);
+        double fsu[4];
+        for (int i = 0; i < 4; ++i) fsu[i] = fs[i] * funit;
+        const int rmid = (g->fx && nh == 2) ? 4 : 0, rend = (g->fx && ends_step) ? 4 : 0;
+        cudaError_t e = launch_strang_xy(a, prec, p.s3_warps, nh, ny, nz, q.nstrips, q.nytiles, q.nzsegs, q.zseg_h,
+                                         fsu, rmid, rend, s);
         if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order x-y-x pass launch");
         g->launches++;
         par ^= 1;
         return DIRAC_OK;
     };
-    dirac_status st = xy(1, first_half);
+    dirac_status st = xy(1, g->fx ? first_half_fx : first_half, false);
     for (int64_t i = 0; i < m && st == DIRAC_OK; ++i) {
         cudaError_t e = launch_strang_z(g->psi[par], g->psi[par ^ 1], g->table, a.nx, ny, nz, a.periodic, g->table_full,
-                                        ucoef, ucoef_n, step0 + i, p.s3_z_nsegs, p.s3_z_seg_h, g->fp32, s);
+                                        ucoef, ucoef_n, step0 + i, p.s3_z_nsegs, p.s3_z_seg_h, prec, s);
         if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order z-phase-z pass launch");
         g->launches++;
         par ^= 1;
-        st = xy(i + 1 < m ? 2 : 1, i + 1 < m ? both_halves : second_half);
+        const bool last = i + 1 == m;
+        st = xy(last ? 1 : 2, last ? (g->fx ? second_half_fx : second_half) : (g->fx ? both_halves_fx : both_halves), last);
     }
     return st;
 }
@@ -788,10 +800,13 @@ void default_plan(dirac_grid *g) {
     }
     if (ndim_of(g) == 3 && g->fx) {
         // fixed point, first order: points_per_lane 0 = the fused single pass (one step per pass), 1, 2 or 4 =
-        // the x-y pass + z/phase pass with that P; second order: single sweeps
+        // the x-y pass + z/phase pass with that P; second order: points_per_lane 1 = eight single sweeps, 0 or 2 =
+        // the fused passes (bandwidth-bound integer sweeps: the passes move a seventh of the single sweeps' bytes)
         g->plan.fused3d = pp > 0 ? 0 : 1;
         g->plan.f_warps = g->cfg.n[1] <= 12 ? 8 : 16;
-        g->plan.s3_fused = 0;
+        g->plan.s3_fused = (strang(g) && pp != 1) ? 1 : 0;
+        g->plan.s3_warps = 32;  // measured at 384^3: 12.5 G point-steps/s against 10.5 with 16-warp blocks (fewer
+                                // recomputed halo rows outweigh the int64 x-y-x-x-y-x pass's small spill at 64 registers)
         make_plan(g, 1, pp > 0 ? pp : 1, 4, 16);
         return;
     }
@@ -952,9 +967,9 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->precision == DIRAC_FX64) {
         if (cfg->char_shift > 1)
             return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs characteristic shift 1 (char_shift 0 or 1)");
-        if (cfg->ndim == 3 && cfg->splitting == DIRAC_STRANG && cfg->points_per_lane > 1)
+        if (cfg->ndim == 3 && cfg->splitting == DIRAC_STRANG && cfg->points_per_lane > 2)
             return fail(nullptr, DIRAC_ERR_ARG,
-                        "DIRAC_FX64 3-D second-order steps run as single sweeps (points_per_lane 0 or 1)");
+                        "DIRAC_FX64 3-D second-order steps run as single sweeps (points_per_lane 1) or fused passes (0, 2)");
         const int fmode = cfg->ndim == 3 ? 1 : (cfg->splitting == DIRAC_STRANG ? 2 : 0);
         const bool strang3 = cfg->ndim == 3 && cfg->splitting == DIRAC_STRANG;
         if (cfg->steps_per_launch > 2 || ((cfg->ndim == 3 || fmode == 2) && cfg->steps_per_launch > 1) ||
@@ -1431,7 +1446,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
         cands.push_back({1, 1, 4, 8, 0, 0});  // single sweeps: nothing to choose
     } else if (sweep_mode(g) == 6) {
         cands.push_back({1, 2, 4, 16, 0, 0});
-        if (!g->fx && char_shift(g) == 1)  // the fused passes take floating-point states and one-cell x shifts
+        if (char_shift(g) == 1)  // the fused passes take one-cell x shifts
             for (int sw : {16, 32})
                 for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
     } else if (g->fx && g->cfg.ndim == 3) {

@@ -152,11 +152,14 @@ cudaError_t launch_fused3d(const SweepArgs &a, int precision, int warps, int ste
 // (a.nsegs * a.nplanes must equal nzsegs * nytiles * warps).  z-phase-z pass: one thread per column and
 // plane parity over nsegs segments of seg_h planes, the phase from `table` (or, with ucoef, the
 // vector-potential matrix of step step0).
-cudaError_t launch_strang_xy(const SweepArgs &a, int fp32, int warps, int nh, int64_t ny, int64_t nz, int64_t nstrips,
-                             int64_t nytiles, int64_t nzsegs, int64_t zseg_h, const double fscale[4], cudaStream_t s);
+// precision: 0 FP64, 1 FP32, 2 64-bit fixed point (rshift_mid / rshift_end: the step's final division by 2^r,
+// rounded, between the halves of an NH = 2 pass / after the pass's last sweep; 0 for floating-point states).
+cudaError_t launch_strang_xy(const SweepArgs &a, int precision, int warps, int nh, int64_t ny, int64_t nz,
+                             int64_t nstrips, int64_t nytiles, int64_t nzsegs, int64_t zseg_h, const double fscale[4],
+                             int rshift_mid, int rshift_end, cudaStream_t s);
 cudaError_t launch_strang_z(const void *in, void *out, const void *table, int64_t nx, int64_t ny, int64_t nz,
                             int periodic, int full_table, const double *ucoef, int64_t ucoef_n, int64_t step0,
-                            int64_t nsegs, int64_t seg_h, int fp32, cudaStream_t s);
+                            int64_t nsegs, int64_t seg_h, int precision, cudaStream_t s);
 
 // Entries of the U matrix of Sec. 2.3 for mu = m c^2 dt and the field integral At (12 doubles:
 // Dup, Ddn, Ez, -Ez, Ep, Em as (re, im)); A = sqrt(((mu^2 + At_x^2) + At_y^2) + At_z^2), sin(A)/A -> 1 at A = 0.

@@ -98,6 +98,13 @@ template <> __device__ __forceinline__ Cx<long long> cmulp<long long>(Cx<long lo
     const __int128 k3 = (__int128)z.im * (p.re + p.im);
     return {(long long)((k1 - k3) >> 62), (long long)((k1 + k2) >> 62)};
 }
+// Fixed point: o / 2^r rounded to nearest, halves upward (floating-point states never ask for it).
+template <typename T> __device__ __forceinline__ void round_shift(Cx<T> (&)[4], int) {}
+template <> __device__ __forceinline__ void round_shift<long long>(Cx<long long> (&o)[4], int r) {
+    const long long half = 1ll << (r - 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = Cx<long long>{(o[q].re + half) >> r, (o[q].im + half) >> r};
+}
 // acc + z p with re = fma(z.re, p.re, fma(-z.im, p.im, acc.re)), im = fma(z.re, p.im, fma(z.im, p.re, acc.im))
 template <typename T> __device__ __forceinline__ Cx<T> cmac(Cx<T> acc, Cx<T> z, Cx<T> p) {
     return {Ar<T>::fma(z.re, p.re, Ar<T>::fma(-z.im, p.im, acc.re)), Ar<T>::fma(z.re, p.im, Ar<T>::fma(z.im, p.re, acc.im))};

@@ -19,6 +19,10 @@
 // Face flux: every x sweep adds, on the face strip's owned rows, 1/2 (|u14|^2 + |u23|^2) of cell face - 1 and
 // subtracts 1/2 (|w14|^2 + |w23|^2) of cell face, of the state entering it, times 1 / s^2 for the state's
 // scale s (fscale); one part per (sweep, z segment, y tile, warp), folded by the last block.
+// 64-bit fixed-point state (q = psi 2^S): the sweeps are exact integer sums, the face terms are formed in FP64
+// (fscale carries 2^-2S), and the step's final division by 16 (rounded to nearest, halves up: the phase carries
+// only the first four halves) follows the step's last x sweep: at the end of a pass that ends a step and between
+// the halves of an x-y-x-x-y-x pass (rshift_end, rshift_mid; 0 for floating-point states).
 //
 // z-phase-z pass: the two-cell z sweeps couple plane k only with planes k - 2 and k + 2, and the phase is
 // pointwise, so even and odd planes form two independent chains.  One thread per (x, y) column and plane
@@ -40,6 +44,8 @@ struct StrangXYArgs {
     int64_t ny, nz;
     int64_t nstrips, nytiles, nzsegs, zseg_h;
     double fscale[4];     // per x sweep: 1/2 over the square of the scale of the state entering it
+    int rshift_mid;       // fixed point, NH = 2: divide by 2^rshift_mid (rounded) after the first half's last sweep
+    int rshift_end;       // fixed point: divide by 2^rshift_end (rounded) after the pass's last sweep
 };
 
 struct StrangZArgs {
@@ -58,19 +64,29 @@ template <typename T, int W> struct XYMinBlocks { static constexpr int value = (
 // z-phase-z pass: 128-thread blocks per SM the register budget is fitted to
 template <typename T, bool FIELD> struct ZMinBlocks { static constexpr int value = sizeof(T) == 4 ? 4 : 3; };
 
+// type the face terms are summed in: the state's own floating-point type, FP64 for a fixed-point state
+template <typename T> struct FaceAcc { using type = T; };
+template <> struct FaceAcc<long long> { using type = double; };
+
 template <typename T>
-__device__ __forceinline__ T face_term(Cx<T> p14, Cx<T> p23) {
+__device__ __forceinline__ typename FaceAcc<T>::type face_term(Cx<T> p14, Cx<T> p23) {
     return Ar<T>::fma(p14.re, p14.re, Ar<T>::fma(p14.im, p14.im, Ar<T>::fma(p23.re, p23.re, Ar<T>::mul(p23.im, p23.im))));
+}
+template <> __device__ __forceinline__ double face_term<long long>(Cx<long long> p14, Cx<long long> p23) {
+    const double a = (double)p14.re, b = (double)p14.im, c = (double)p23.re, d = (double)p23.im;
+    return __fma_rn(a, a, __fma_rn(b, b, __fma_rn(c, c, __dmul_rn(d, d))));
 }
 
 // A: x sweep, one cell (Eq. sol_dis_1), of a row held one cell per lane; the output (2x the swept state) is
 // valid on lanes whose two neighbours hold valid cells.  The face lanes add their term of the entering state.
 template <typename T>
-__device__ __forceinline__ void xsweep_row(const Cx<T> s[4], Cx<T> o[4], int lane, bool fl_u, bool fl_w, T &fp) {
+__device__ __forceinline__ void xsweep_row(const Cx<T> s[4], Cx<T> o[4], int lane, bool fl_u, bool fl_w,
+                                           typename FaceAcc<T>::type &fp) {
+    using F = typename FaceAcc<T>::type;
     const Cx<T> u14 = cadd(s[0], s[3]), w14 = csub(s[0], s[3]);
     const Cx<T> u23 = cadd(s[1], s[2]), w23 = csub(s[1], s[2]);
-    if (fl_u) fp = Ar<T>::add(fp, face_term(u14, u23));
-    if (fl_w) fp = Ar<T>::sub(fp, face_term(w14, w23));
+    if (fl_u) fp = Ar<F>::add(fp, face_term(u14, u23));
+    if (fl_w) fp = Ar<F>::sub(fp, face_term(w14, w23));
     const Cx<T> lu14 = shfl_c(u14, (lane + 31) & 31), lu23 = shfl_c(u23, (lane + 31) & 31);
     const Cx<T> rw14 = shfl_c(w14, (lane + 1) & 31), rw23 = shfl_c(w23, (lane + 1) & 31);
     o[0] = cadd(lu14, rw14);
@@ -136,14 +152,15 @@ __device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int
     const int64_t face = a.flux_face;
     const bool fw = FLUX && owned_row;  // warp-uniform
     const bool fl_u = fw && x == face - 1, fl_w = fw && x == face;
+    using FA = typename FaceAcc<T>::type;
     double facc[NS];
-    T fp[NS];
+    FA fp[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         facc[q] = 0.0;
-        fp[q] = T(0);
+        fp[q] = FA(0);
     }
-    auto sweep_x = [&](const Cx<T> in4[4], Cx<T> out4[4], T &acc) {
+    auto sweep_x = [&](const Cx<T> in4[4], Cx<T> out4[4], FA &acc) {
         if (FLUX && fw) {
             xsweep_row(in4, out4, lane, fl_u, fl_w, acc);
         } else {
@@ -151,7 +168,7 @@ __device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int
         }
     };
 
-    // planes in flight: two ahead in FP32 (bandwidth-bound), one in FP64
+    // planes in flight: two ahead in FP32 (bandwidth-bound), one in FP64 and fixed point
     constexpr int LA = sizeof(T) == 4 ? 2 : 1;
     Cx<T> ring[LA][4];
 #pragma unroll
@@ -192,6 +209,7 @@ __device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int
                 ysweep_row(buf1, w, lane, q);
                 if (ghost) zero_pt(q);
                 sweep_x(q, t, fp[1]);
+                if (A.rshift_end > 0) round_shift(t, A.rshift_end);
                 if (own_lane) store_pt(dst, t);
             }
         } else {
@@ -200,6 +218,7 @@ __device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int
                 ysweep_row(buf1, w, lane, q);
                 if (ghost) zero_pt(q);
                 sweep_x(q, t, fp[1]);
+                if (A.rshift_mid > 0) round_shift(t, A.rshift_mid);  // fixed point: the end of a step
                 if (ghost) zero_pt(t);  // the state between the two half steps
                 sweep_x(t, q, fp[NS > 2 ? 2 : 0]);
                 ywrite_row(buf2, w, lane, q);
@@ -209,6 +228,7 @@ __device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int
                 ysweep_row(buf2, w, lane, q);
                 if (ghost) zero_pt(q);
                 sweep_x(q, t, fp[NS > 3 ? 3 : 0]);
+                if (A.rshift_end > 0) round_shift(t, A.rshift_end);
                 if (own_lane) store_pt(dst, t);
             }
         }
@@ -216,7 +236,7 @@ __device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int
 #pragma unroll
             for (int s2 = 0; s2 < NS; ++s2) {
                 facc[s2] = __dadd_rn(facc[s2], (double)fp[s2]);
-                fp[s2] = T(0);
+                fp[s2] = FA(0);
             }
         }
     }

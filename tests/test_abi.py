@@ -145,7 +145,7 @@ def test_fx64_validation(lib):
     single sweeps)."""
     import paper_1107_4650_gb300 as D
     for n, kw in (((8, 8, 8), dict(ndim=3, steps_per_launch=2)), ((8, 8, 8), dict(ndim=3, splitting=D.DIRAC_STRANG,
-                                                                                     points_per_lane=2)),
+                                                                                     points_per_lane=4)),
                   ((16, 1, 16), dict(splitting=D.DIRAC_STRANG, steps_per_launch=2)),
                   ((16, 1, 16), dict(splitting=D.DIRAC_STRANG, steps_per_launch=1, points_per_lane=4)),
                   ((16, 1, 16), dict(char_shift=2)), ((16, 1, 16), dict(steps_per_launch=4)),

@@ -277,33 +277,37 @@ def test_fx_strang2d_klein_within_1e12_of_fp64_oracle(D):
     assert np.array_equal(q1, oracle.step_strang2d_fx(q0, 1.0, C, DX, run.nsteps, V=V))
 
 
-@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13)])
+@pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13), (60, 30, 40), (29, 13, 3)])
 @pytest.mark.parametrize("periodic", [False, True])
 @pytest.mark.parametrize("full", [False, True])
-def test_fx_strang3d_bit_exact_against_fixed_point_oracle(D, shape, periodic, full):
-    """3-D second-order steps as eight single sweeps on the int64 state, against oracle_step_strang3d_fx."""
+@pytest.mark.parametrize("pp,nsteps", [(1, 3), (2, 3), (2, 1), (2, 34)])
+def test_fx_strang3d_bit_exact_against_fixed_point_oracle(D, shape, periodic, full, pp, nsteps):
+    """3-D second-order steps on the int64 state, as eight single sweeps (points_per_lane 1) or as the fused
+    x-y-x / z-phase-z / x-y-x-x-y-x passes (2; 34 steps: a captured 32-step run and a 2-step run), against
+    oracle_step_strang3d_fx bit for bit."""
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx * 3 + ny + nz)
     V = np.random.default_rng(ny + nz).uniform(-4e4, 4e4, nx * ny * nz if full else nx)
     S = oracle.fx_shift(psi, 3, strang=True)
     q0 = oracle.fx_encode(psi, S)
-    want = oracle.step_strang3d_fx(q0, 1.0, C, DX, 3, V=V, periodic=periodic)
-    cfg = D.make_config((nx, ny, nz), ndim=3, precision=D.DIRAC_FX64, splitting=D.DIRAC_STRANG,
+    want = oracle.step_strang3d_fx(q0, 1.0, C, DX, nsteps, V=V, periodic=periodic)
+    cfg = D.make_config((nx, ny, nz), ndim=3, precision=D.DIRAC_FX64, splitting=D.DIRAC_STRANG, points_per_lane=pp,
                         boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
     h = D.dirac_create_grid(cfg)
     try:
         D.dirac_set_potential(h, V, D.DIRAC_V_FULL if full else D.DIRAC_V_X_ONLY)
         D.dirac_set_state_fx(h, q0, S)
-        D.dirac_step(h, 3)
+        D.dirac_step(h, nsteps)
         got, _ = _q_of(D, h, (nz, ny, nx))
         info = D.dirac_get_info(h)
     finally:
         D.dirac_destroy(h)
-    assert info["plan"] == D.DIRAC_PLAN_3D_STRANG
+    assert info["plan"] == (D.DIRAC_PLAN_3D_STRANG if pp == 1 else D.DIRAC_PLAN_3D_STRANG_FUSED)
     assert np.array_equal(got, want)
 
 
-def test_fx_strang3d_coulomb_within_1e12_of_fp64_oracle(D):
+@pytest.mark.parametrize("pp", [1, 2])
+def test_fx_strang3d_coulomb_within_1e12_of_fp64_oracle(D, pp):
     """3-D second-order steps in the soft-Coulomb potential (48^3, face flux, 40 steps, autotuned, graphs): the
     decoded state within relative L2 1e-12 of the FP64 oracle, flux within 1e-12 relative, integer state equal
     to the fixed-point oracle's; dirac_set_state picks the second-order shift."""
@@ -311,7 +315,8 @@ def test_fx_strang3d_coulomb_within_1e12_of_fp64_oracle(D):
     psi = W.gaussian_packet(n, n, DX, -n * DX / 2, -n * DX / 2, -6 * DX, 0.0, 4 * DX, 0.4 * C, ny=n, y_min=-n * DX / 2)
     V = W.soft_coulomb_3d(n, DX, 10.0, 2 * DX).reshape(-1)
     want, F = oracle.step_strang3d(psi, 1.0, C, DX, 40, V=V, flux_face=n // 2)
-    cfg = D.make_config((n, n, n), ndim=3, precision=D.DIRAC_FX64, splitting=D.DIRAC_STRANG, flux_face=n // 2)
+    cfg = D.make_config((n, n, n), ndim=3, precision=D.DIRAC_FX64, splitting=D.DIRAC_STRANG, flux_face=n // 2,
+                        points_per_lane=pp)
     h = D.dirac_create_grid(cfg)
     try:
         D.dirac_set_potential(h, V, D.DIRAC_V_FULL)
