@@ -26,6 +26,15 @@
 
 #include "dirac_internal.cuh"
 
+// Compile-time tunables of the fixed-point 2-D step kernel (sweep_kernel<long long, 1, 1, 0>): resident blocks
+// the register budget is fitted to, and rows per loop iteration.
+#ifndef FX_MIN_BLOCKS
+#define FX_MIN_BLOCKS 1
+#endif
+#ifndef FX_ROW_UNROLL
+#define FX_ROW_UNROLL 2
+#endif
+
 namespace dirac {
 
 // Opts `kernel` in to `smem` bytes of dynamic shared memory, once per device (bit `dev` of `done`; devices
@@ -185,7 +194,7 @@ __device__ __forceinline__ int64_t pmod(int64_t a, int64_t n) {
 // alternate instead of moving, which pays where the loop body is short).
 template <typename T, int K, int MODE> struct RowUnroll {
     static constexpr bool FX = sizeof(T) == 8 && (T)0.5 == (T)0;  // the int64 fixed-point state
-    static constexpr int value = ((sizeof(T) == 4 || FX) && K == 1 && MODE == 0) ? 2 : 1;
+    static constexpr int value = (sizeof(T) == 4 && K == 1 && MODE == 0) ? 2 : ((FX && K == 1 && MODE == 0) ? FX_ROW_UNROLL : 1);
 };
 template <typename T, int K, int P, int MODE, int UNR = RowUnroll<T, K, MODE>::value>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem);
@@ -204,8 +213,14 @@ template <int K, int MODE> struct Levels { static constexpr int value = (MODE ==
 //         Eq. sol_dis_4, U(step) exp(-i V dt), with the table holding g = exp(-i V dt) / 4 per column or cell.
 // MODE 5: MODE 2 with a uniform vector potential (the phase of each step's first level is the matrix, the
 //         table holding g = exp(-i V dt) / 16).
+// Resident 4-warp blocks per SM the register budget is fitted to (1: the compiler's choice).
+template <typename T, int K, int P, int MODE> struct SweepMinBlocks {
+    static constexpr bool FX = sizeof(T) == 8 && (T)0.5 == (T)0;
+    static constexpr int value = (FX && K == 1 && P == 1 && MODE == 0) ? FX_MIN_BLOCKS : 1;
+};
+
 template <typename T, int K, int P, int MODE>
-__global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(128, SweepMinBlocks<T, K, P, MODE>::value) sweep_kernel(const SweepArgs a) {
     constexpr int L = Levels<K, MODE>::value;
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
