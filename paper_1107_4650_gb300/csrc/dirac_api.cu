@@ -958,7 +958,8 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     *out = nullptr;
     if (cfg->ndim != 2 && cfg->ndim != 3) return fail(nullptr, DIRAC_ERR_ARG, "ndim must be 2 or 3");
     for (int d = 0; d < 3; ++d)
-        if (cfg->n[d] < 1) return fail(nullptr, DIRAC_ERR_ARG, "grid sizes must be >= 1");
+        if (cfg->n[d] < 1 || cfg->n[d] > 0x7fffffff)
+            return fail(nullptr, DIRAC_ERR_ARG, "grid sizes must be >= 1 and below 2^31");
     if (cfg->ndim == 2 && cfg->n[1] != 1) return fail(nullptr, DIRAC_ERR_ARG, "2-D grids (x-z plane) need n[1] == 1");
     if (!(cfg->dx > 0) || !(cfg->c > 0) || !std::isfinite(cfg->dx) || !std::isfinite(cfg->c) || !std::isfinite(cfg->m))
         return fail(nullptr, DIRAC_ERR_ARG, "dx and c must be finite and > 0, m finite");

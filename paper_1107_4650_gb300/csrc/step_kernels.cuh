@@ -23,13 +23,22 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "dirac_internal.cuh"
 
-// Compile-time tunables of the fixed-point 2-D step kernel (sweep_kernel<long long, 1, 1, 0>): resident blocks
-// the register budget is fitted to, and rows per loop iteration.
+// Compile-time tunables of the 2-D step kernels: resident 4-warp blocks per SM the register budget is fitted to
+// (fixed point k = 1, P = 1; FP32 k = 2, P = 2; FP64 k = 1, P = 2 and 4), and rows per loop iteration of the
+// fixed-point kernel.  Fixed point: 4 blocks with two rows per iteration fit 128 registers without spilling (33.1
+// against 26.7 G point-steps/s at 150 registers and 3 blocks, 2048^2).
 #ifndef FX_MIN_BLOCKS
-#define FX_MIN_BLOCKS 1
+#define FX_MIN_BLOCKS 4
+#endif
+#ifndef F32_MIN_BLOCKS
+#define F32_MIN_BLOCKS 1
+#endif
+#ifndef F64_MIN_BLOCKS
+#define F64_MIN_BLOCKS 1
 #endif
 #ifndef FX_ROW_UNROLL
 #define FX_ROW_UNROLL 2
@@ -216,7 +225,11 @@ template <int K, int MODE> struct Levels { static constexpr int value = (MODE ==
 // Resident 4-warp blocks per SM the register budget is fitted to (1: the compiler's choice).
 template <typename T, int K, int P, int MODE> struct SweepMinBlocks {
     static constexpr bool FX = sizeof(T) == 8 && (T)0.5 == (T)0;
-    static constexpr int value = (FX && K == 1 && P == 1 && MODE == 0) ? FX_MIN_BLOCKS : 1;
+    static constexpr bool F64 = sizeof(T) == 8 && !FX;
+    static constexpr int value = (FX && K == 1 && P == 1 && MODE == 0)                  ? FX_MIN_BLOCKS
+                                 : (sizeof(T) == 4 && K == 2 && P == 2 && MODE == 0)   ? F32_MIN_BLOCKS
+                                 : (F64 && K == 1 && (P == 2 || P == 4) && MODE == 0) ? F64_MIN_BLOCKS
+                                                                                       : 1;
 };
 
 template <typename T, int K, int P, int MODE>
@@ -416,19 +429,25 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     const int64_t x_own0 = strip * a.strip_w;
     const int64_t x_own1 = min(x_own0 + a.strip_w, nx);
     const int64_t xa = x_own0 - L;
-    const int64_t r_begin = seg * a.seg_h;
-    const int64_t r_end = min(r_begin + a.seg_h, nr);
+    // Row indices fit 32 bits (the host limits every grid dimension below 2^31).  The floating-point kernels run
+    // their row loop on 32-bit indices (FP32 k = 2: 105 against 94 G point-steps/s at 2048^2); the fixed-point
+    // kernel keeps 64-bit ones, with which it fits its 128-register budget without spilling (33.2 against 31.5 G).
+    using RI = typename std::conditional<RowUnroll<T, K, MODE>::FX, int64_t, int>::type;
+    const RI nr32 = (RI)nr;
+    const RI r_begin = (RI)(seg * a.seg_h);
+    const RI r_end = (RI)min((int64_t)r_begin + a.seg_h, nr);
     const T *in = static_cast<const T *>(a.in) + plane * nr * nx * 8;
     T *out = static_cast<T *>(a.out) + plane * nr * nx * 8;
 
     // every lane's cells lie inside the grid (or wrap): output rows inside the grid need no ghost-zero mask
     const bool strip_in = per || (xa >= 0 && xa + 32 * P <= nx);
     int64_t xl[P];
-    bool xin[P];
+    bool xin[P], own[P];  // own: the cell is in this warp's strip (it stores it)
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         const int64_t x = xa + 32 * j + lane;
         xin[j] = (x >= 0 && x < nx);
+        own[j] = x >= x_own0 && x < x_own1;
         xl[j] = per ? pmod(x, nx) : min(max(x, (int64_t)0), nx - 1);
     }
     // phase coefficients per x column (mode 0, x-only table)
@@ -492,7 +511,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     const uint32_t bar0 = smem_u32(wsmem);
     const uint32_t slot0 = smem_u32(wsmem + 128);
     const uint32_t dst_off = (uint32_t)((cx0 - xa) * 8 * (int64_t)sizeof(T));
-    const int64_t r_first = r_begin - L, r_last = r_end + L;  // rows [r_first, r_last) are read
+    const RI r_first = r_begin - L, r_last = r_end + L;  // rows [r_first, r_last) are read
     uint32_t phase_bits = 0, pending = 0;
     bool aborted = false;
     if (ring) {
@@ -505,8 +524,8 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
         bool stall = a.inject_stall && wid == 0;
 #pragma unroll
         for (int sl = 0; sl < RG::SLOTS; ++sl) {
-            const int64_t r = r_first + sl;
-            if (r < r_last && r >= 0 && r < nr) {
+            const RI r = r_first + sl;
+            if (r < r_last && r >= 0 && r < nr32) {
                 if (lane == 0) {
                     // failure-detection test hook: the first warp of the launch announces 16 bytes more than
                     // its first row copy delivers, so that slot's phase never completes and its bounded wait
@@ -514,7 +533,8 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                     if (stall)
                         asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], 16;" ::"r"(bar0 + 8 * sl)
                                      : "memory");
-                    bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + (r * nx + cx0) * 8, copy_bytes, bar0 + 8 * sl);
+                    bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + ((int64_t)r * nx + cx0) * 8, copy_bytes,
+                              bar0 + 8 * sl);
                 }
                 stall = false;
                 pending |= 1u << sl;
@@ -523,13 +543,13 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     }
 
     int sl = 0;
-    for (int64_t r0 = r_first; r0 < r_last && !aborted; r0 += UNR) {
+    for (RI r0 = r_first; r0 < r_last && !aborted; r0 += UNR) {
 #pragma unroll
     for (int par = 0; par < UNR; ++par) {
-        const int64_t r = r0 + par;
+        const RI r = r0 + par;
         if (r >= r_last) break;
         Cx<T> st[P][4];
-        const bool row_ok = per || (r >= 0 && r < nr);
+        const bool row_ok = per || (r >= 0 && r < nr32);
         const int64_t rl = per ? pmod(r, nr) : r;
         if (ring) {
             if (row_ok) {
@@ -563,13 +583,13 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
         }
 #pragma unroll
         for (int lev = 0; lev < L; ++lev) {
-            const int64_t q = r - lev;  // row of the level-lev state in st
+            const RI q = r - lev;  // row of the level-lev state in st
             // rows of level lev+1 that later levels (or the store) use: [r_first + lev + 1, r_last - lev - 1)
             const bool need_out = (q - 1 >= r_first + lev + 1) && (q - 1 < r_last - lev - 1);
             if ((MODE == 2 || MODE == 5) && (lev & 1)) {
                 // second half of a Strang step: z sweep of rows q-2 and q into row q-1, then the x sweep of
                 // row q-1.  The input is 1/4 of the state (the phase carried 1/16), the z-swept row 1/2 of it.
-                const bool zrow_ok = per || (q - 1 >= 0 && q - 1 < nr);
+                const bool zrow_ok = per || (q - 1 >= 0 && q - 1 < nr32);
                 Cx<T> zs[P][4];
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
@@ -638,7 +658,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
             if (has_face && q >= r_begin && q < r_end)
                 flux_row<T, P>(lu14, lu23, w14, w23, face_j, face_lane, lane, q - r_begin, q == r_end - 1,
                                gsm + lev * 8 * 32, 0.5 * a.flux_unit, facc[lev]);
-            const bool out_row_ok = per || (q - 1 >= 0 && q - 1 < nr);
+            const bool out_row_ok = per || (q - 1 >= 0 && q - 1 < nr32);
 #pragma unroll
             for (int j = 0; j < P; ++j) {
                 // x sweep (Eq. sol_dis_1), x2
@@ -659,7 +679,7 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                         // phase (Eq. sol_dis_4) with the deferred 1/4
                         Cx<T> qu, qd;
                         if (a.full_table) {
-                            const int64_t rr = per ? pmod(q - 1, nr) : min(max(q - 1, (int64_t)0), nr - 1);
+                            const int64_t rr = per ? pmod(q - 1, nr) : (int64_t)min(max(q - 1, (RI)0), nr32 - 1);
                             load_tab(static_cast<const T *>(a.table) + (plane * nr * nx + rr * nx + xl[j]) * 4, qu, qd);
                         } else {
                             qu = pu[j];
@@ -717,22 +737,30 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 }
             }
         }
-        const int64_t ro = r - L;
+        const RI ro = r - L;
         if (ro >= r_begin && ro < r_end) {
+            if constexpr (sizeof(RI) == 8) {
 #pragma unroll
-            for (int j = 0; j < P; ++j) {
-                const int64_t x = xa + 32 * j + lane;
-                if (x >= x_own0 && x < x_own1) store_pt(out + (ro * nx + x) * 8, st[j]);
+                for (int j = 0; j < P; ++j) {
+                    const int64_t x = xa + 32 * j + lane;
+                    if (x >= x_own0 && x < x_own1) store_pt(out + (ro * nx + x) * 8, st[j]);
+                }
+            } else {
+                T *orow = out + (int64_t)ro * nx * 8;
+#pragma unroll
+                for (int j = 0; j < P; ++j)
+                    if (own[j]) store_pt(orow + (xa + 32 * j + lane) * 8, st[j]);
             }
         }
         if (ring) {
             // refill this slot with row r + SLOTS once every lane has read it
             __syncwarp();
-            const int64_t rn = r + RG::SLOTS;
-            if (rn < r_last && rn >= 0 && rn < nr) {
+            const RI rn = r + RG::SLOTS;
+            if (rn < r_last && rn >= 0 && rn < nr32) {
                 if (lane == 0) {
                     fence_proxy_async();
-                    bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + (rn * nx + cx0) * 8, copy_bytes, bar0 + 8 * sl);
+                    bulk_load(slot0 + sl * RG::ROW_BYTES + dst_off, in + ((int64_t)rn * nx + cx0) * 8, copy_bytes,
+                              bar0 + 8 * sl);
                 }
                 pending |= 1u << sl;
             }
