@@ -34,6 +34,10 @@ struct Fused3DArgs {
 // accumulator type of the face terms: the storage type, FP64 for fixed-point states
 template <typename T> struct FaceAcc { using type = T; };
 template <> struct FaceAcc<long long> { using type = double; };
+// plane index type of the z loop: 32-bit for floating-point states (grid dimensions stay below 2^31), 64-bit for
+// the fixed-point state (register budget)
+template <typename T> struct PlaneIdx { using type = int; };
+template <> struct PlaneIdx<long long> { using type = int64_t; };
 
 // |p14|^2 + |p23|^2 as a fused chain in the accumulator type
 template <typename T>
@@ -59,7 +63,8 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
     const int64_t x = x_own0 - 1 + lane;
     const int64_t y = ytile * H - 1 + w;
     const bool owned_row = w >= 1 && w <= H && y < ny;
-    const int64_t z_begin = zseg * A.zseg_h, z_end = min(z_begin + A.zseg_h, nz);
+    using ZI = typename PlaneIdx<T>::type;
+    const ZI z_begin = (ZI)(zseg * A.zseg_h), z_end = (ZI)min((int64_t)z_begin + A.zseg_h, nz);
     const bool xin = x >= 0 && x < nx, yin = y >= 0 && y < ny;
     const int64_t xl = per ? pmod(x, nx) : min(max(x, (int64_t)0), nx - 1);
     const int64_t yl = per ? pmod(y, ny) : min(max(y, (int64_t)0), ny - 1);
@@ -87,11 +92,11 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
 
     // cell (xl, yl) of a plane: plane k at (k nx ny + cell) (periodic: halo planes wrap)
     const int64_t plane_cells = nx * ny, cell = yl * nx + xl;
-    auto wrap_z = [&](int64_t k) -> int64_t {
-        if (per && (k < 0 || k >= nz)) return pmod(k, nz);
+    auto wrap_z = [&](ZI k) -> int64_t {
+        if (per && (k < 0 || k >= nz)) return pmod((int64_t)k, nz);
         return k;
     };
-    auto load_row = [&](int64_t k, Cx<T> s[4]) {
+    auto load_row = [&](ZI k, Cx<T> s[4]) {
         const bool ok = per || (yin && k >= 0 && k < nz && xin);
         if (ok) {
             load_pt(in + (wrap_z(k) * plane_cells + cell) * 8, s);
@@ -111,11 +116,11 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
     // per-cell table entries of the next output plane, loaded one plane ahead (full table only)
     Cx<T> tu = pu, td = pd, tu_next = pu, td_next = pd;
 
-    for (int64_t k = z_begin - 1; k <= z_end; ++k) {
+    for (ZI k = z_begin - 1; k <= z_end; ++k) {
         if (a.full_table && owned_row) {
             tu = tu_next;
             td = td_next;
-            if (k >= z_begin && k < z_end) load_tab(tab + (k * plane_cells + cell) * 4, tu_next, td_next);
+            if (k >= z_begin && k < z_end) load_tab(tab + ((int64_t)k * plane_cells + cell) * 4, tu_next, td_next);
         }
         Cx<T> st[4];
 #pragma unroll
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
             // z sweep (Eq. sol_dis_3): +z movers (s1+s3, s2-s4) of plane k-2, -z movers (s1-s3, s2+s4) of plane k
             const Cx<T> U13 = cadd(s[0], s[2]), U24 = csub(s[1], s[3]);
             const Cx<T> W13 = csub(s[0], s[2]), W24 = cadd(s[1], s[3]);
-            const int64_t zo = k - 1;
+            const ZI zo = k - 1;
             if (zo >= z_begin && zo < z_end) {
                 Cx<T> o[4];
                 o[0] = cadd(UA[0], W13);
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
                     o[2] = cmulp(o[2], qd);
                     o[3] = cmulp(o[3], qd);
                 }
-                if (x >= x_own0 && x < x_own1) store_pt(out + (zo * plane_cells + cell) * 8, o);
+                if (x >= x_own0 && x < x_own1) store_pt(out + ((int64_t)zo * plane_cells + cell) * 8, o);
             }
             UA[0] = UB[0];
             UA[1] = UB[1];
@@ -234,7 +239,8 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d2_kernel(const Fused3DArgs A
     const bool owned_row = w >= 2 && w < W - 2 && y < ny;
     const bool mid_row = w >= 1 && w < W - 1;
     const bool own_lane = x >= x_own0 && x < x_own1;
-    const int64_t z_begin = zseg * A.zseg_h, z_end = min(z_begin + A.zseg_h, nz);
+    using ZI = typename PlaneIdx<T>::type;
+    const ZI z_begin = (ZI)(zseg * A.zseg_h), z_end = (ZI)min((int64_t)z_begin + A.zseg_h, nz);
     const bool xin = x >= 0 && x < nx, yin = y >= 0 && y < ny;
     const bool ghost_xy = !per && !(xin && yin);
     const int64_t xl = per ? pmod(x, nx) : min(max(x, (int64_t)0), nx - 1);
@@ -267,11 +273,11 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d2_kernel(const Fused3DArgs A
 
     // cell (xl, yl) of a plane: plane k at (k nx ny + cell) (periodic: halo planes wrap)
     const int64_t plane_cells = nx * ny, cell = yl * nx + xl;
-    auto wrap_z = [&](int64_t k) -> int64_t {
-        if (per && (k < 0 || k >= nz)) return pmod(k, nz);
+    auto wrap_z = [&](ZI k) -> int64_t {
+        if (per && (k < 0 || k >= nz)) return pmod((int64_t)k, nz);
         return k;
     };
-    auto load_row = [&](int64_t k, Cx<T> s[4]) {
+    auto load_row = [&](ZI k, Cx<T> s[4]) {
         const bool ok = per || (yin && k >= 0 && k < nz && xin);
         if (ok) {
             load_pt(in + (wrap_z(k) * plane_cells + cell) * 8, s);
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d2_kernel(const Fused3DArgs A
     };
 
     constexpr int LA = sizeof(T) == 4 ? 2 : 1;
-    const int64_t k_first = z_begin - 2, k_last = z_end + 1;
+    const ZI k_first = z_begin - 2, k_last = z_end + 1;
     Cx<T> ring[LA][4];
 #pragma unroll
     for (int j = 0; j < LA; ++j)
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d2_kernel(const Fused3DArgs A
     Cx<T> H1A[2] = {{T(0), T(0)}, {T(0), T(0)}}, H1B[2] = {{T(0), T(0)}, {T(0), T(0)}};
     Cx<T> H2A[2] = {{T(0), T(0)}, {T(0), T(0)}}, H2B[2] = {{T(0), T(0)}, {T(0), T(0)}};
     // per-cell table entries (full table): step 1 at plane k - 1 (rows one inside the halo), step 2 at k - 2
-    auto table_at = [&](int64_t j, Cx<T> &qu, Cx<T> &qd) {
+    auto table_at = [&](ZI j, Cx<T> &qu, Cx<T> &qd) {
         qu = pu;
         qd = pd;
         if (a.full_table && (per || (j >= 0 && j < nz)))
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d2_kernel(const Fused3DArgs A
     table_at(k_first - 1, t1u, t1d);
     table_at(k_first - 2, t2u, t2d);
 
-    for (int64_t k = k_first; k <= k_last; ++k) {
+    for (ZI k = k_first; k <= k_last; ++k) {
         Cx<T> st[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) st[c] = ring[0][c];
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d2_kernel(const Fused3DArgs A
         xsweep(st, b4, fp[0], k >= z_begin && k < z_end);
         ywrite(buf1, b4);
         __syncthreads();
-        const int64_t j1 = k - 1;  // step 1's output plane
+        const ZI j1 = k - 1;  // step 1's output plane
         if (mid_row) {
             Cx<T> o[4];
             yz_phase(buf1, H1A, H1B, q1u, q1d, 0, o);
@@ -393,11 +399,11 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d2_kernel(const Fused3DArgs A
             ywrite(buf2, b4);
         }
         __syncthreads();
-        const int64_t m = k - 2;  // step 2's output plane
+        const ZI m = k - 2;  // step 2's output plane
         if (owned_row) {
             Cx<T> o[4];
             yz_phase(buf2, H2A, H2B, q2u, q2d, 1, o);
-            if (own_lane && m >= z_begin && m < z_end) store_pt(out + (m * plane_cells + cell) * 8, o);
+            if (own_lane && m >= z_begin && m < z_end) store_pt(out + ((int64_t)m * plane_cells + cell) * 8, o);
         }
         if ((fl_u || fl_w) && (((k - k_first) & 31) == 31 || k == k_last)) {
 #pragma unroll

@@ -67,6 +67,10 @@ template <typename T, bool FIELD> struct ZMinBlocks { static constexpr int value
 // type the face terms are summed in: the state's own floating-point type, FP64 for a fixed-point state
 template <typename T> struct FaceAcc { using type = T; };
 template <> struct FaceAcc<long long> { using type = double; };
+// plane index type of the z loops: 32-bit for floating-point states (grid dimensions stay below 2^31), 64-bit for
+// the fixed-point state
+template <typename T> struct PlaneIdx { using type = int; };
+template <> struct PlaneIdx<long long> { using type = int64_t; };
 
 template <typename T>
 __device__ __forceinline__ typename FaceAcc<T>::type face_term(Cx<T> p14, Cx<T> p23) {
@@ -140,7 +144,8 @@ __device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int
     const bool owned_row = w >= HX && w < W - HX && y < ny;
     const bool mid_row = w >= 2 && w < W - 2;  // NH = 2: rows of the first half step's second sweep pair
     const bool own_lane = x >= x_own0 && x < x_own1;
-    const int64_t z_begin = zseg * A.zseg_h, z_end = min(z_begin + A.zseg_h, nz);
+    using ZI = typename PlaneIdx<T>::type;
+    const ZI z_begin = (ZI)(zseg * A.zseg_h), z_end = (ZI)min((int64_t)z_begin + A.zseg_h, nz);
     const bool ghost = EDGE && !(x >= 0 && x < nx && y >= 0 && y < ny);  // outside the grid (zero boundary)
     const int64_t xl = per ? pmod(x, nx) : min(max(x, (int64_t)0), nx - 1);
     const int64_t yl = per ? pmod(y, ny) : min(max(y, (int64_t)0), ny - 1);
@@ -183,7 +188,7 @@ __device__ __forceinline__ void strang_xy_block(const StrangXYArgs &A, const int
     }
     const T *ld = src + LA * plane;
 
-    for (int64_t k = z_begin; k < z_end; ++k, ld += plane, dst += plane) {
+    for (ZI k = z_begin; k < z_end; ++k, ld += plane, dst += plane) {
         Cx<T> st[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) st[c] = ring[0][c];
@@ -290,7 +295,8 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
     if (col >= ncol) return;
     const bool per = a.periodic != 0;
     const int par = (int)(blockIdx.y & 1);
-    const int64_t z_begin = (int64_t)(blockIdx.y >> 1) * a.seg_h, z_end = min(z_begin + a.seg_h, nz);
+    using ZI = typename PlaneIdx<T>::type;
+    const ZI z_begin = (ZI)((int64_t)(blockIdx.y >> 1) * a.seg_h), z_end = (ZI)min((int64_t)z_begin + a.seg_h, nz);
     const T *in = static_cast<const T *>(a.in);
     T *out = static_cast<T *>(a.out);
     const T *tab = static_cast<const T *>(a.table);
@@ -304,9 +310,9 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
         for (int e = 0; e < (FIELD ? 6 : 1); ++e) UM[e] = Cx<T>{(T)__ldg(u + 2 * e), (T)__ldg(u + 2 * e + 1)};
     }
     const int64_t plane = ncol * 8;
-    auto load_plane = [&](int64_t k, Cx<T> s[4]) {
+    auto load_plane = [&](ZI k, Cx<T> s[4]) {
         if (per || (k >= 0 && k < nz)) {
-            const int64_t kl = per ? pmod(k, nz) : k;
+            const int64_t kl = per ? pmod((int64_t)k, nz) : (int64_t)k;
             load_pt(in + kl * plane + col * 8, s);
         } else {
 #pragma unroll
@@ -318,12 +324,12 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
 #pragma unroll
     for (int t = 0; t < 2; ++t) R1[t][0] = R1[t][1] = R2[t][0] = R2[t][1] = Cx<T>{T(0), T(0)};
     // planes of this thread's parity from z_begin - 4 (or - 3) to z_end + 3 (or + 2)
-    const int64_t k_first = z_begin - 4 + ((par - z_begin) & 1);
-    const int64_t k_last = z_end + 3 - (((z_end + 3) - par) & 1);
+    const ZI k_first = z_begin - 4 + ((par - z_begin) & 1);
+    const ZI k_last = z_end + 3 - (((z_end + 3) - par) & 1);
     constexpr int LA = sizeof(T) == 4 ? 2 : 1;
     // the phase at plane j = k - 2 takes the table entry loaded with input plane k
-    auto load_phase = [&](int64_t k, Cx<T> &qu, Cx<T> &qd) {
-        const int64_t j = k - 2;
+    auto load_phase = [&](ZI k, Cx<T> &qu, Cx<T> &qd) {
+        const ZI j = k - 2;
         if (a.full_table && (per || (j >= 0 && j < nz))) load_tab(tab + ((per ? pmod(j, nz) : j) * ncol + col) * 4, qu, qd);
     };
     Cx<T> pre[LA][4], tpu[LA], tpd[LA];
@@ -335,10 +341,10 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
         load_phase(k_first + 2 * j, tpu[j], tpd[j]);
     }
 
-    for (int64_t k0 = k_first; k0 <= k_last; k0 += 4) {
+    for (ZI k0 = k_first; k0 <= k_last; k0 += 4) {
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-            const int64_t k = k0 + 2 * t;
+            const ZI k = k0 + 2 * t;
             if (k > k_last) break;
             Cx<T> s[4];
 #pragma unroll
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
             R1[t][0] = U13;
             R1[t][1] = U24;
             // D: phase of Eq. sol_dis_4 at plane j (zero outside the grid under the zero boundary)
-            const int64_t j = k - 2;
+            const ZI j = k - 2;
             if (per || (j >= 0 && j < nz)) {
                 if (FIELD) {
                     // (U_ab g) psi_b over the non-zero entries, columns in order, g = the table's exp(-i V dt)
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
             r[3] = csub(X24, R2[t][1]);
             R2[t][0] = V13;
             R2[t][1] = V24;
-            const int64_t m = k - 4;
+            const ZI m = k - 4;
             if (m >= z_begin && m < z_end) store_pt(out + m * plane + col * 8, r);
         }
     }
