@@ -52,10 +52,11 @@ FP64_ISSUE_PEAK_NOMINAL = FP64_INSTR_PER_SM_CLOCK * SM_COUNT * 2.07e9 / 1e12  # 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel on the 2048^2 workload, keyed
 # by (steps per launch, points per lane) of the captured variant (profiles/step_kernel_fp64_klein2048.md,
 # profiles/step_kernel_fp32_klein2048.md).  A variant without a capture reports null.
-MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": {(1, 2): 277.515264e6 + 216.816896e6, (1, 4): 287.006976e6 + 216.340992e6},
-                               "fp32": {(2, 2): 147.680256e6 + 85.511168e6}}
+MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": {(1, 2): 277.539584e6 + 216.977408e6, (1, 4): 287.031808e6 + 217.295616e6},
+                               "fp32": {(2, 2): 147.694080e6 + 85.042432e6},
+                               "fx64": {(1, 1): 277.640448e6 + 217.100288e6}}
 # ncu sm__pipe_fp64_cycles_active of the same captures (fraction of active cycles)
-MEASURED_FP64_PIPE = {(1, 2): 0.836, (1, 4): 0.8375}
+MEASURED_FP64_PIPE = {(1, 2): 0.8311, (1, 4): 0.8297}
 
 
 def parse():
@@ -460,6 +461,8 @@ def main():
             "value": vx, "unit": "point-steps/s", "ms_per_step": tx / args.steps,
             "steps_per_launch": ix["steps_per_launch"], "points_per_lane": ix["points_per_lane"],
             "fx_shift": ix["fx_shift"], "bytes_per_point_step": FP64_BYTES_PER_POINT_STEP,
+            "traffic_per_launch": (MEASURED_TRAFFIC_PER_LAUNCH["fx64"].get((ix["steps_per_launch"], ix["points_per_lane"]))
+                                   if args.side == 2048 else None),
             "hbm_frac": FP64_BYTES_PER_POINT_STEP * vx / world / 1e9 / hbm_peak,
             "rel_l2_vs_fp64_after_%d_steps" % args.nsteps: rel,
             "flux_rel_diff_vs_fp64": abs(fx_flux - fp64_flux) / abs(fp64_flux) if fp64_flux else None,

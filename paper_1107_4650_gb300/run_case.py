@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="let dirac_autotune choose the launch plan first")
     ap.add_argument("--field", action="store_true",
                     help="2-D: add a uniform two-cycle laser pulse (vector potential) over the run")
+    ap.add_argument("--cellfield", action="store_true",
+                    help="2-D/3-D: a field varying along x and in time (dirac_set_field) over the run")
     ap.add_argument("--mlp", type=int, default=0,
                     help="instead: train the transmission network this many epochs on seeded random targets")
     args = ap.parse_args()
@@ -109,6 +111,16 @@ def main():
                             splitting=D.DIRAC_STRANG if args.strang else D.DIRAC_LIE)
         layout = D.DIRAC_V_FULL
     h = D.dirac_create_grid(cfg)
+    if args.cellfield:
+        total = args.nsteps * args.repeat
+        ncell = shape[0] * shape[1] * shape[2]
+        xi = np.tile(np.arange(shape[0]), ncell // shape[0])
+        a = np.stack([0.5 * np.sin(xi / 40.0), 0.2 * np.cos(xi / 25.0), 0.3 * np.cos(xi / 30.0)], axis=1)
+        w = 1.5 * np.exp(-((xi - shape[0] / 2) / (shape[0] / 6)) ** 2)
+        t = np.arange(total)
+        F = np.stack([0.8 * np.sin(0.02 * t), 0.1 * np.cos(0.03 * t), 0.5 * np.cos(0.015 * t), 0.4 * np.sin(0.01 * t)],
+                     axis=1)
+        D.dirac_set_field(h, a, w, F)
     if args.field:
         total = args.nsteps * args.repeat
         dt = W.DX_DEFAULT / W.C_AU
@@ -120,7 +132,7 @@ def main():
         D.dirac_autotune(h)
     times = []
     for it in range(args.repeat):
-        if args.field:
+        if args.field or args.cellfield:
             D.dirac_set_counters(h, it * args.nsteps, 0.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
