@@ -148,13 +148,15 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d_kernel(const Fused3DArgs A)
         const Cx<T> b1 = cadd(lu23, rw23), b2 = csub(lu23, rw23);
         // y characteristics (Eq. sol_dis_2): "+y" movers (b1 - i b4, b2 + i b3), "-y" movers (b1 + i b4, b2 - i b3)
         Cx<T> *buf = ych + (size_t)((k - z_begin + 1) & 1) * (W * 4 * 32);
-        ych_put(buf, w, lane, csub_ib(b0, b3), cadd_ib(b1, b2), cadd_ib(b0, b3), csub_ib(b1, b2));
+        buf[(w * 4 + 0) * 32 + lane] = csub_ib(b0, b3);
+        buf[(w * 4 + 1) * 32 + lane] = cadd_ib(b1, b2);
+        buf[(w * 4 + 2) * 32 + lane] = cadd_ib(b0, b3);
+        buf[(w * 4 + 3) * 32 + lane] = csub_ib(b1, b2);
         __syncthreads();
         if (owned_row) {
             // y sweep of row y: "+y" movers of row y-1, "-y" movers of row y+1 (x2 again: 4x the state)
-            Cx<T> U14, U23, W14, W23;
-            ych_plus(buf, w - 1, lane, U14, U23);
-            ych_minus(buf, w + 1, lane, W14, W23);
+            const Cx<T> U14 = buf[((w - 1) * 4 + 0) * 32 + lane], U23 = buf[((w - 1) * 4 + 1) * 32 + lane];
+            const Cx<T> W14 = buf[((w + 1) * 4 + 2) * 32 + lane], W23 = buf[((w + 1) * 4 + 3) * 32 + lane];
             Cx<T> s[4];
             s[0] = cadd(U14, W14);
             s[3] = cmul_i(csub(U14, W14));
@@ -302,13 +304,15 @@ __global__ void __launch_bounds__(32 * W, 1) fused3d2_kernel(const Fused3DArgs A
     };
     // y characteristics (Eq. sol_dis_2): "+y" movers (b1 - i b4, b2 + i b3), "-y" movers (b1 + i b4, b2 - i b3)
     auto ywrite = [&](Cx<T> *buf, const Cx<T> b4[4]) {
-        ych_put(buf, w, lane, csub_ib(b4[0], b4[3]), cadd_ib(b4[1], b4[2]), cadd_ib(b4[0], b4[3]), csub_ib(b4[1], b4[2]));
+        buf[(w * 4 + 0) * 32 + lane] = csub_ib(b4[0], b4[3]);
+        buf[(w * 4 + 1) * 32 + lane] = cadd_ib(b4[1], b4[2]);
+        buf[(w * 4 + 2) * 32 + lane] = cadd_ib(b4[0], b4[3]);
+        buf[(w * 4 + 3) * 32 + lane] = csub_ib(b4[1], b4[2]);
     };
     // y sweep from rows w - 1 and w + 1, z sweep against the history (output plane = input plane - 1), phase
     auto yz_phase = [&](const Cx<T> *buf, Cx<T> (&HA)[2], Cx<T> (&HB)[2], Cx<T> qu, Cx<T> qd, int st, Cx<T> o[4]) {
-        Cx<T> U14, U23, W14, W23;
-        ych_plus(buf, w - 1, lane, U14, U23);
-        ych_minus(buf, w + 1, lane, W14, W23);
+        const Cx<T> U14 = buf[((w - 1) * 4 + 0) * 32 + lane], U23 = buf[((w - 1) * 4 + 1) * 32 + lane];
+        const Cx<T> W14 = buf[((w + 1) * 4 + 2) * 32 + lane], W23 = buf[((w + 1) * 4 + 3) * 32 + lane];
         Cx<T> s[4];
         s[0] = cadd(U14, W14);
         s[3] = cmul_i(csub(U14, W14));

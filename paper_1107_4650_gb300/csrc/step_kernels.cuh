@@ -194,46 +194,6 @@ __device__ __forceinline__ void load_tab(const float *p, Cx<float> &pu, Cx<float
     pd = {a.z, a.w};
 }
 
-// Shared-memory exchange of a row's y characteristics between the warps of a block (the 3-D passes): per row w
-// and lane the "+y" movers (U14, U23) and the "-y" movers (W14, W23).  FP32: each pair is one 16-byte access in a
-// [w][2][32] layout (lanes 16 B apart: no bank conflict); wider components: four 16-byte accesses in a [w][4][32]
-// layout.  Either layout takes W x 4 x 32 components per buffer.
-template <typename T>
-__device__ __forceinline__ void ych_put(Cx<T> *buf, int w, int lane, Cx<T> u14, Cx<T> u23, Cx<T> w14, Cx<T> w23) {
-    if constexpr (sizeof(T) == 4) {
-        float4 *b = reinterpret_cast<float4 *>(buf);
-        b[(w * 2 + 0) * 32 + lane] = make_float4(u14.re, u14.im, u23.re, u23.im);
-        b[(w * 2 + 1) * 32 + lane] = make_float4(w14.re, w14.im, w23.re, w23.im);
-    } else {
-        buf[(w * 4 + 0) * 32 + lane] = u14;
-        buf[(w * 4 + 1) * 32 + lane] = u23;
-        buf[(w * 4 + 2) * 32 + lane] = w14;
-        buf[(w * 4 + 3) * 32 + lane] = w23;
-    }
-}
-// "+y" movers of row w
-template <typename T> __device__ __forceinline__ void ych_plus(const Cx<T> *buf, int w, int lane, Cx<T> &u14, Cx<T> &u23) {
-    if constexpr (sizeof(T) == 4) {
-        const float4 v = reinterpret_cast<const float4 *>(buf)[(w * 2 + 0) * 32 + lane];
-        u14 = Cx<T>{v.x, v.y};
-        u23 = Cx<T>{v.z, v.w};
-    } else {
-        u14 = buf[(w * 4 + 0) * 32 + lane];
-        u23 = buf[(w * 4 + 1) * 32 + lane];
-    }
-}
-// "-y" movers of row w
-template <typename T> __device__ __forceinline__ void ych_minus(const Cx<T> *buf, int w, int lane, Cx<T> &w14, Cx<T> &w23) {
-    if constexpr (sizeof(T) == 4) {
-        const float4 v = reinterpret_cast<const float4 *>(buf)[(w * 2 + 1) * 32 + lane];
-        w14 = Cx<T>{v.x, v.y};
-        w23 = Cx<T>{v.z, v.w};
-    } else {
-        w14 = buf[(w * 4 + 2) * 32 + lane];
-        w23 = buf[(w * 4 + 3) * 32 + lane];
-    }
-}
-
 __device__ __forceinline__ int64_t pmod(int64_t a, int64_t n) {
     int64_t r = a % n;
     return r < 0 ? r + n : r;

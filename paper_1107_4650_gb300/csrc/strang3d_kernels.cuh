@@ -102,15 +102,17 @@ __device__ __forceinline__ void xsweep_row(const Cx<T> s[4], Cx<T> o[4], int lan
 // y characteristics of row w (Eq. sol_dis_2): "+y" movers (a1 - i a4, a2 + i a3), "-y" movers (a1 + i a4, a2 - i a3)
 template <typename T>
 __device__ __forceinline__ void ywrite_row(Cx<T> *buf, int w, int lane, const Cx<T> a[4]) {
-    ych_put(buf, w, lane, csub_ib(a[0], a[3]), cadd_ib(a[1], a[2]), cadd_ib(a[0], a[3]), csub_ib(a[1], a[2]));
+    buf[(w * 4 + 0) * 32 + lane] = csub_ib(a[0], a[3]);
+    buf[(w * 4 + 1) * 32 + lane] = cadd_ib(a[1], a[2]);
+    buf[(w * 4 + 2) * 32 + lane] = cadd_ib(a[0], a[3]);
+    buf[(w * 4 + 3) * 32 + lane] = csub_ib(a[1], a[2]);
 }
 
 // B: y sweep, two cells, of row w: "+y" movers of row w - 2, "-y" movers of row w + 2
 template <typename T>
 __device__ __forceinline__ void ysweep_row(const Cx<T> *buf, int w, int lane, Cx<T> q[4]) {
-    Cx<T> U14, U23, W14, W23;
-    ych_plus(buf, w - 2, lane, U14, U23);
-    ych_minus(buf, w + 2, lane, W14, W23);
+    const Cx<T> U14 = buf[((w - 2) * 4 + 0) * 32 + lane], U23 = buf[((w - 2) * 4 + 1) * 32 + lane];
+    const Cx<T> W14 = buf[((w + 2) * 4 + 2) * 32 + lane], W23 = buf[((w + 2) * 4 + 3) * 32 + lane];
     q[0] = cadd(U14, W14);
     q[3] = cmul_i(csub(U14, W14));
     q[1] = cadd(U23, W23);
