@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--side3d", type=int, default=384)
     ap.add_argument("--batch-runs", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--check-points", type=int, default=16)
+    ap.add_argument("--check-points", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=0.0,
                     help="--impl reference: oracle seconds per step (0: about 60 s over all steps, 2 s at least)")
@@ -860,7 +860,8 @@ def main():
             "queries_per_s_batched_fp32_solver": (1.0 / t32) if t32 else None,
             "gain_network_over_fp64_solve": t64 / t_net,
             "gain_batched_fp32_over_fp64_solve": (t64 / t32) if t32 else None,
-            "checked_points": len(qj), "dT_mean": float(dT.mean()), "dT_max": float(dT.max()),
+            "checked_points": len(qj), "dT_mean": float(dT.mean()), "dT_p99": float(np.percentile(dT, 99)),
+            "dT_max": float(dT.max()),
             "checkpoint": "paper_1107_4650_gb300/data/surrogate_klein_box.npz",
             "box": "V0/mc^2 [%g, %g], p0/mc [%g, %g], width/dx [%g, %g]" % (lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]),
             "training": json.loads(str(z["stats"])) if "stats" in z else None}
