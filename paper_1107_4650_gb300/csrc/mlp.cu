@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *A, 
                                                            int64_t ldc, int M, int N, int K, int accumulate, unsigned *err) {
     extern __shared__ unsigned char gsm_raw[];
     unsigned char *gsm = reinterpret_cast<unsigned char *>(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ float tr[4][32][33];  // epilogue: each warp's 32 x 32 block, rows padded (no bank conflicts)
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -179,7 +180,6 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *A, 
         ok = __syncthreads_and(bar_wait(smem_addr(&mbar[(nchunks - 1) & 1]), (uint32_t)(((nchunks - 1) >> 1) & 1)));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int m = m0 + warp * 32 + lane;
 #pragma unroll 1
         for (int c0 = 0; c0 < GN; c0 += 32) {
             uint32_t r[32];
@@ -199,17 +199,21 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *A, 
 #pragma unroll
                 for (int j = 0; j < 32; ++j) r[j] = 0u;
             }
-            if (m < M) {
+            // lane = row in the accumulator's layout: through shared memory, so that each store instruction writes
+            // 32 consecutive columns of one row (128 bytes) instead of one column of 32 rows
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int n = n0 + c0 + j;
-                    if (n < N) {
-                        float *p = C + (int64_t)m * ldc + n;
-                        const float v = __uint_as_float(r[j]);
-                        *p = accumulate ? (*p + v) : v;
-                    }
+            for (int j = 0; j < 32; ++j) tr[warp][lane][j] = __uint_as_float(r[j]);
+            __syncwarp();
+            const int n = n0 + c0 + lane;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int mr = m0 + warp * 32 + rr;
+                if (mr < M && n < N) {
+                    float *p = C + (int64_t)mr * ldc + n;
+                    const float v = tr[warp][rr][lane];
+                    *p = accumulate ? (*p + v) : v;
                 }
             }
+            __syncwarp();
         }
     } else if (lane == 0) {
         atomicOr(err, 1u);
