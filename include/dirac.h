@@ -69,7 +69,10 @@ typedef struct {
     int boundary;         /* DIRAC_BC_ZERO: cells outside the grid are zero at every sub-step
                              (Dirichlet condition of Sec. 5); DIRAC_BC_PERIODIC: wrap */
     int64_t flux_face;    /* x face index i_s in [1, nx-1] whose crossing probability is accumulated
-                             every step (between cells i_s-1 and i_s), or -1 for none */
+                             every step (between cells i_s-1 and i_s), or -1 for none.  With periodic
+                             boundaries and char_shift K > 1 it must lie in [K, nx-K], so that the K
+                             cells each side of the face whose characteristics cross it are grid cells
+                             (DIRAC_ERR_ARG otherwise) */
     void *stream;         /* cudaStream_t the grid's work is enqueued on (NULL = legacy stream) */
     int device;           /* CUDA device ordinal */
     int steps_per_launch; /* steps fused in one kernel launch (temporal block depth).  2-D: 1 or 2 for FP64,

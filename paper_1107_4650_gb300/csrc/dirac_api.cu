@@ -997,6 +997,11 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->char_shift < 0 || cfg->char_shift > 4)
         return fail(nullptr, DIRAC_ERR_ARG, "char_shift must be 0 (= 1), 1, 2, 3 or 4");
     if (cfg->char_shift > 1) {
+        if (cfg->boundary == DIRAC_BC_PERIODIC && cfg->flux_face >= 0 &&
+            (cfg->flux_face < cfg->char_shift || cfg->flux_face > cfg->n[0] - cfg->char_shift))
+            return fail(nullptr, DIRAC_ERR_ARG,
+                        "periodic grids with char_shift K > 1 take a flux_face in [K, nx-K] (the K cells on each "
+                        "side of the face inside the grid)");
         if (cfg->steps_per_launch > 1)
             return fail(nullptr, DIRAC_ERR_ARG, "char_shift > 1 runs one step per launch (steps_per_launch 0 or 1)");
         if (cfg->ndim == 2 && cfg->splitting == DIRAC_LIE && cfg->points_per_lane == 4)

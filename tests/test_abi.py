@@ -161,7 +161,10 @@ def test_char_shift_validation(lib):
     import paper_1107_4650_gb300 as D
     for kw in (dict(char_shift=5), dict(char_shift=-1), dict(char_shift=2, ndim=3, n=(8, 8, 8), points_per_lane=2),
                dict(char_shift=2, splitting=D.DIRAC_STRANG, points_per_lane=2), dict(char_shift=3, steps_per_launch=2),
-               dict(char_shift=2, points_per_lane=4), dict(char_shift=2, precision=D.DIRAC_FX64)):
+               dict(char_shift=2, points_per_lane=4), dict(char_shift=2, precision=D.DIRAC_FX64),
+               dict(char_shift=3, boundary=D.DIRAC_BC_PERIODIC, flux_face=2),
+               dict(char_shift=2, boundary=D.DIRAC_BC_PERIODIC, flux_face=15),
+               dict(char_shift=4, boundary=D.DIRAC_BC_PERIODIC, flux_face=3, ndim=3, n=(8, 8, 8))):
         n = kw.pop("n", (16, 1, 16))
         cfg = D.make_config(n, **kw)
         with pytest.raises(D.DiracError) as e:

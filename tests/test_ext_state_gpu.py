@@ -121,3 +121,23 @@ def test_ext_state_rejects_host_and_misaligned_buffers(D):
         with pytest.raises(D.DiracError) as e:
             D.dirac_create_grid(cfg)
         assert e.value.status == D.DIRAC_ERR_ARG
+
+
+@pytest.mark.parametrize("shape,ndim", [((1, 1, 1), 2), ((1, 1, 1), 3), ((5, 1, 3), 2), ((3, 4, 2), 3)])
+def test_ext_state_tiny_grids(D, shape, ndim):
+    """Caller-owned buffers of one-cell and small grids: the same bits as the oracle after 9 steps."""
+    torch = pytest.importorskip("torch")
+    nx, ny, nz = shape
+    psi = W.random_state(nz, ny, nx, seed=nx + 3 * ny + 7 * nz + ndim)
+    want, _ = oracle.step(psi, ndim, 1.0, C, DX, 9)
+    bufs = [torch.from_numpy(psi.view(np.float64).copy()).cuda(), torch.zeros(psi.size * 2, dtype=torch.float64,
+                                                                              device="cuda")]
+    torch.cuda.synchronize()
+    h = D.dirac_create_grid(D.make_config((nx, ny, nz), ndim=ndim, ext_state=bufs))
+    try:
+        D.dirac_step(h, 9)
+        got = np.empty_like(psi)
+        D.dirac_get_state(h, got)
+    finally:
+        D.dirac_destroy(h)
+    assert np.array_equal(got.view(np.float64), want.view(np.float64))

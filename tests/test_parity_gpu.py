@@ -661,7 +661,7 @@ def _run_shift(D, psi, nsteps, S, V=None, periodic=False, fp32=False, P=0, flux_
 
 @pytest.mark.parametrize("S", [2, 3, 4])
 @pytest.mark.parametrize("P", [1, 2])
-@pytest.mark.parametrize("shape", [(70, 45), (9, 6), (131, 37)])
+@pytest.mark.parametrize("shape", [(70, 45), (9, 6), (131, 37), (1, 1), (3, 2)])
 @pytest.mark.parametrize("periodic", [False, True])
 def test_shift_fp64_bit_exact(D, S, P, shape, periodic):
     nx, nz = shape

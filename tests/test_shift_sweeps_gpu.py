@@ -130,3 +130,39 @@ def test_shift_sweeps_with_vector_potential(D, ndim, strang):
     want, _ = _oracle(psi, ndim, 6, 2, strang, V=V, A_tilde=At)
     got, _, _ = _run(D, psi, ndim, 6, 2, strang, V=V, A_tilde=At)
     assert _bits_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("ndim,strang", CASES)
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 2), (2, 5, 3), (5, 1, 4)])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_shift_sweeps_degenerate_grids(D, ndim, strang, shape, periodic):
+    """Grids smaller than the shift K = 4 (periodic: the characteristics wrap more than once; zero boundary:
+    everything leaves), one-cell grids, and 2-D shapes: bit-exact with the oracle."""
+    nx, ny, nz = shape
+    if ndim == 2:
+        ny = 1
+    psi = W.random_state(nz, ny, nx, seed=nx * 7 + ny * 3 + nz)
+    V = np.random.default_rng(nx + nz).uniform(-2e4, 2e4, nx)
+    want, _ = _oracle(psi, ndim, 3, 4, strang, V=V, periodic=periodic)
+    got, _, _ = _run(D, psi, ndim, 3, 4, strang, V=V, periodic=periodic)
+    assert _bits_equal(got, want)
+
+
+@pytest.mark.parametrize("ndim,strang", [(2, False)] + CASES)
+@pytest.mark.parametrize("periodic,where", [(True, "K"), (True, "nx-K"), (False, "1"), (False, "nx-1")])
+def test_shift_flux_face_near_the_edges(D, ndim, strang, periodic, where):
+    """The face flux with K = 3 and the face at the edges allowed: periodic grids take faces in [K, nx-K] (the
+    window of K cells each side inside the grid); zero-boundary grids any face, the cells outside being zero.
+    The flux of a random state is a difference of terms of the order of its probability P = dx^d sum |psi|^2
+    (periodic: about 1e-3 P after cancellation), so it is held to 1e-12 P per step."""
+    K = 3
+    shape = (19, 5, 11) if ndim == 3 else (23, 1, 17)
+    nx, ny, nz = shape
+    face = {"K": K, "nx-K": nx - K, "1": 1, "nx-1": nx - 1}[where]
+    psi = W.random_state(nz, ny, nx, seed=7 * face + ndim)
+    V = np.random.default_rng(face).uniform(-2e4, 2e4, nx)
+    want, F = _oracle(psi, ndim, 4, K, strang, V=V, periodic=periodic, flux_face=face)
+    got, obs, _ = _run(D, psi, ndim, 4, K, strang, V=V, periodic=periodic, flux_face=face)
+    assert _bits_equal(got, want)
+    P = float(np.sum(np.abs(psi) ** 2)) * DX ** ndim
+    assert abs(F) > 1e-6 * P and abs(obs["flux_cum"] - F) <= 4e-12 * P
