@@ -636,6 +636,8 @@ def main():
                          "plan": {D.DIRAC_PLAN_3D_FUSED: "fused pass, %d step(s) per launch" % i3["steps_per_launch"],
                                   D.DIRAC_PLAN_3D_TWO_PASS: "x-y pass + z/phase pass, P=%d" % i3["points_per_lane"],
                                   D.DIRAC_PLAN_3D_STRANG: "eight single-sweep launches",
+                                  D.DIRAC_PLAN_3D_STRANG_ZPASS: "x, y, x single sweeps, one z-phase-z pass, x, y, x "
+                                                                "single sweeps",
                                   D.DIRAC_PLAN_3D_STRANG_FUSED: "fused passes: x-y-x, then per step z-phase-z and "
                                                                 "x-y-x-x-y-x (the last x-y-x)"}
                                  .get(i3["plan"], str(i3["plan"])),

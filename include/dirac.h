@@ -87,11 +87,13 @@ typedef struct {
                              dt = 2 dx / c, so each half-step sweep is the one-cell shift; steps_per_launch
                              1 (FP64) or 1, 2 (FP32).  3-D: A B A C D C A B A with dt = 4 dx / c, x sweeps
                              moving one cell and y, z sweeps two (c dt/2 = 2 dx), run as eight single-sweep
-                             launches per step (points_per_lane 1) or as fused passes (points_per_lane 2): a
-                             run of m steps (one dirac_step call, or a captured graph of 32 steps) is x-y-x,
-                             m z-phase-z passes separated by m - 1 x-y-x-x-y-x passes, then x-y-x, so the
-                             state in memory is at a step boundary only between runs; 0 = library choice
-                             (fused passes for FP32 storage, single sweeps for FP64) */
+                             launches per step (points_per_lane 1), as six single sweeps with C D C in one
+                             z-phase-z pass (points_per_lane 4: the same bits) or as fused passes
+                             (points_per_lane 2): a run of m steps (one dirac_step call, or a captured graph
+                             of 32 steps) is x-y-x, m z-phase-z passes separated by m - 1 x-y-x-x-y-x
+                             passes, then x-y-x, so the state in memory is at a step boundary only between
+                             runs; 0 = library choice (fused passes for FP32 and fixed-point storage, the
+                             z-phase-z plan for FP64; char_shift > 1: eight single sweeps) */
     int char_shift;       /* characteristic shift K of Sec. 2.3: c dt = K dx, each sweep moves the
                              characteristics by K cells.  0 or 1: the paper's K = 1; 2, 3 or 4 (FP64 or FP32
                              storage, one step per launch): 2-D first order (dt = K dx / c, the fused
@@ -257,7 +259,8 @@ enum {
     DIRAC_PLAN_3D_STRANG_FUSED = 8, /* 3-D second-order steps: x-y-x, z-phase-z, x-y-x-x-y-x, ... passes */
     DIRAC_PLAN_SHIFT_SWEEPS = 9,    /* char_shift > 1 as single-sweep launches: 3-D first order x y z+phase,
                                        2-D second order x z+phase z x */
-    DIRAC_PLAN_FIELD_SWEEPS = 10    /* a field varying in space and time (dirac_set_field): single-sweep launches */
+    DIRAC_PLAN_FIELD_SWEEPS = 10,   /* a field varying in space and time (dirac_set_field): single-sweep launches */
+    DIRAC_PLAN_3D_STRANG_ZPASS = 11 /* 3-D second-order step: x y x single sweeps, one z-phase-z pass, x y x */
 };
 
 dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info);

@@ -25,6 +25,7 @@ DIRAC_LIE, DIRAC_STRANG = 0, 1
 DIRAC_PLAN_STEP_2D, DIRAC_PLAN_STRANG_2D, DIRAC_PLAN_FIELD_2D, DIRAC_PLAN_SHIFT_2D = 0, 1, 2, 3
 DIRAC_PLAN_3D_TWO_PASS, DIRAC_PLAN_3D_FUSED, DIRAC_PLAN_3D_STRANG, DIRAC_PLAN_STRANG_FIELD_2D = 4, 5, 6, 7
 DIRAC_PLAN_3D_STRANG_FUSED, DIRAC_PLAN_SHIFT_SWEEPS, DIRAC_PLAN_FIELD_SWEEPS = 8, 9, 10
+DIRAC_PLAN_3D_STRANG_ZPASS = 11
 
 STATUS_NAMES = {0: "DIRAC_OK", 1: "DIRAC_ERR_ARG", 2: "DIRAC_ERR_OOM", 3: "DIRAC_ERR_CUDA",
                 4: "DIRAC_ERR_NONFINITE", 5: "DIRAC_ERR_TIMEOUT", 6: "DIRAC_ERR_STATE"}

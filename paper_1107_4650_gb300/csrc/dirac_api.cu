@@ -35,6 +35,8 @@ struct Plan {
     int64_t f2_nstrips = 0, f2_nytiles = 0, f2_nzsegs = 0, f2_zseg_h = 0;
     // 3-D second-order step: three fused passes (strang3d_kernels.cuh) instead of eight single sweeps
     int s3_fused = 0, s3_warps = 16, s3_zfactor = 2;
+    // 3-D second order as single sweeps with one-cell x shifts: C D C as one z-phase-z pass (seven launches a step)
+    int s3_zpass = 0;
     struct XY {
         int64_t nstrips = 0, nytiles = 0, nzsegs = 0, zseg_h = 0;
     } s3_xy[2];  // x-y-x pass (half step) and x-y-x-x-y-x pass (two half steps)
@@ -145,6 +147,9 @@ bool fused_pass(const dirac_grid *g) {
 }
 // 3-D second-order step as the x-y-x, z-phase-z, x-y-x passes
 bool strang3d_fused(const dirac_grid *g) { return sweep_mode(g) == 6 && g->plan.s3_fused && char_shift(g) == 1; }
+bool strang3d_zpass(const dirac_grid *g) {
+    return sweep_mode(g) == 6 && !g->plan.s3_fused && g->plan.s3_zpass && char_shift(g) == 1;
+}
 // x halo cells of a strip (each side) for K steps per launch
 int halo_of(const dirac_grid *g, int K) { return sweep_mode(g) == 4 ? char_shift(g) : levels(g, K); }
 double cell_volume(const dirac_grid *g) {
@@ -419,9 +424,22 @@ dirac_status enqueue_block(dirac_grid *g, int parity, int K, cudaStream_t s, int
         static const double fscale_fx[8] = {0.5, 0, 0.5 / 16.0, 0, 0, 0.5 / 4.0, 0, 0.5 / 64.0};
         const int blocks = axis_blocks(g);
         const int64_t K = char_shift(g);  // c dt / 4 = K dx: x sweeps move K cells, y and z sweeps 2 K
+        const bool zpass = strang3d_zpass(g);
         int par = parity;
         for (int q = 0; q < 8; ++q) {
             const int ax = axes[q];
+            if (zpass && q == 3) {
+                // C D C in one pass: the same sums in the same order as sweeps 3 and 4, so the same bits
+                cudaError_t e = launch_strang_z(g->psi[par], g->psi[par ^ 1], g->table, g->cfg.n[0], g->cfg.n[1],
+                                                g->cfg.n[2], a.periodic, g->table_full, field_on(g) ? g->ucoef : nullptr,
+                                                a.ucoef_n, step0, g->plan.s3_z_nsegs, g->plan.s3_z_seg_h,
+                                                g->fx ? 2 : (g->fp32 ? 1 : 0), s);
+                if (e != cudaSuccess) return cuda_fail(g, e, "3-D second-order z-phase-z pass launch");
+                g->launches++;
+                par ^= 1;
+                ++q;  // sweep 4 is done too
+                continue;
+            }
             cudaError_t e = launch_axis(g->psi[par], g->psi[par ^ 1], g->table, g->cfg.n[0], g->cfg.n[1], g->cfg.n[2], ax,
                                         ax == 0 ? K : 2 * K, a.periodic, g->table_full, q == 3 ? 1 : 0,
                                         ax == 0 ? a.flux_face : -1, (g->fx ? fscale_fx[q] : fscale[q]) * a.flux_unit,
@@ -626,7 +644,8 @@ dirac_status enqueue_strang3d_run(dirac_grid *g, int parity, int64_t m, cudaStre
 }
 
 int block_flips(const dirac_grid *g) {
-    if (sweep_mode(g) == 6) return 0;  // eight sweeps per step: parity returns (fused runs: enqueue_strang3d_run)
+    if (sweep_mode(g) == 6)  // eight sweeps per step: parity returns; seven with the z-phase-z pass: it flips
+        return strang3d_zpass(g) ? 1 : 0;  // (fused runs: enqueue_strang3d_run)
     if (sweep_mode(g) == 7) return ndim_of(g) == 3 ? 1 : 0;  // three or four single sweeps
     if (sweep_mode(g) == 8) return (ndim_of(g) == 3 && !strang(g)) ? 1 : 0;  // two, three, four or eight sweeps
     return (ndim_of(g) == 3 && !fused_pass(g)) ? 0 : 1;
@@ -667,7 +686,7 @@ dirac_status get_graph(dirac_grid *g, int parity, cudaGraphExec_t *out) {
 }
 
 int64_t launches_per_block(const dirac_grid *g) {
-    if (sweep_mode(g) == 6) return 8;
+    if (sweep_mode(g) == 6) return strang3d_zpass(g) ? 7 : 8;
     if (sweep_mode(g) == 7) return ndim_of(g) == 3 ? 3 : 4;
     if (sweep_mode(g) == 8) return strang(g) ? (ndim_of(g) == 3 ? 8 : 4) : (ndim_of(g) == 3 ? 3 : 2);
     return 1 + ((ndim_of(g) == 3 && !fused_pass(g)) ? 1 : 0);
@@ -795,16 +814,19 @@ void default_plan(dirac_grid *g) {
     if (sweep_mode(g) >= 7) {  // single-sweep launches, one step per block
         g->plan.fused3d = 0;
         g->plan.s3_fused = 0;
+        g->plan.s3_zpass = 0;
         make_plan(g, 1, 1, 4, 8);
         return;
     }
     if (ndim_of(g) == 3 && g->fx) {
         // fixed point, first order: points_per_lane 0 = the fused single pass (one step per pass), 1, 2 or 4 =
         // the x-y pass + z/phase pass with that P; second order: points_per_lane 1 = eight single sweeps, 0 or 2 =
-        // the fused passes (bandwidth-bound integer sweeps: the passes move a seventh of the single sweeps' bytes)
+        // the fused passes (bandwidth-bound integer sweeps: the passes move a seventh of the single sweeps' bytes),
+        // 4 = single x and y sweeps with one z-phase-z pass
         g->plan.fused3d = pp > 0 ? 0 : 1;
         g->plan.f_warps = g->cfg.n[1] <= 12 ? 8 : 16;
-        g->plan.s3_fused = (strang(g) && pp != 1) ? 1 : 0;
+        g->plan.s3_fused = (strang(g) && pp != 1 && pp != 4) ? 1 : 0;
+        g->plan.s3_zpass = (strang(g) && pp == 4) ? 1 : 0;
         g->plan.s3_warps = 32;  // measured at 384^3: 12.5 G point-steps/s against 10.5 with 16-warp blocks (fewer
                                 // recomputed halo rows outweigh the int64 x-y-x-x-y-x pass's small spill at 64 registers)
         make_plan(g, 1, pp > 0 ? pp : 1, 4, 16);
@@ -814,10 +836,12 @@ void default_plan(dirac_grid *g) {
         // points_per_lane 0: the fused single-pass step; 1, 2 or 4: the x-y pass + z/phase pass with that P
         g->plan.fused3d = pp > 0 ? 0 : 1;
         g->plan.f_warps = g->cfg.n[1] <= 12 ? 8 : 16;  // short y extents: 6-row tiles waste fewer halo rows
-        // second-order step: points_per_lane 1 = eight single-sweep launches, 2 = the three fused passes,
-        // 0 = library choice (fused passes for FP32 storage, which is bandwidth-bound; single sweeps for
-        // FP64, which is bound by the FP64 pipe and would recompute the x-y-x pass's halo cells)
-        g->plan.s3_fused = pp == 1 ? 0 : (pp == 2 ? 1 : (g->fp32 ? 1 : 0));
+        // second-order step: points_per_lane 1 = eight single-sweep launches, 2 = the three fused passes, 4 = x and
+        // y single sweeps with one z-phase-z pass, 0 = library choice (fused passes for FP32 storage, which is
+        // bandwidth-bound; for FP64, which is bound by the FP64 pipe and would recompute the x-y-x pass's halo
+        // cells, single x and y sweeps with the z-phase-z pass: 3.06 against 2.95 G point-steps/s at 384^3)
+        g->plan.s3_fused = (pp == 1 || pp == 4) ? 0 : (pp == 2 ? 1 : (g->fp32 ? 1 : 0));
+        g->plan.s3_zpass = (pp == 4 || (pp == 0 && !g->fp32)) ? 1 : 0;
         g->plan.s3_warps = 32;  // measured at 384^3: 24 owned rows of 32 beat 8 of 16 (more recomputed halo rows)
         // first-order fused pass: steps_per_launch 1 or 2 (temporal block); library choice two in FP32
         // storage (bandwidth-bound), one in FP64 (bound by the FP64 pipe: the second step's halo would cost)
@@ -968,9 +992,10 @@ dirac_status dirac_create_grid(const dirac_config *cfg, dirac_grid **out) {
     if (cfg->precision == DIRAC_FX64) {
         if (cfg->char_shift > 1)
             return fail(nullptr, DIRAC_ERR_ARG, "DIRAC_FX64 runs characteristic shift 1 (char_shift 0 or 1)");
-        if (cfg->ndim == 3 && cfg->splitting == DIRAC_STRANG && cfg->points_per_lane > 2)
+        if (cfg->ndim == 3 && cfg->splitting == DIRAC_STRANG && (cfg->points_per_lane == 3 || cfg->points_per_lane > 4))
             return fail(nullptr, DIRAC_ERR_ARG,
-                        "DIRAC_FX64 3-D second-order steps run as single sweeps (points_per_lane 1) or fused passes (0, 2)");
+                        "DIRAC_FX64 3-D second-order steps run as single sweeps (points_per_lane 1), single sweeps with "
+                        "a z-phase-z pass (4) or fused passes (0, 2)");
         const int fmode = cfg->ndim == 3 ? 1 : (cfg->splitting == DIRAC_STRANG ? 2 : 0);
         const bool strang3 = cfg->ndim == 3 && cfg->splitting == DIRAC_STRANG;
         if (cfg->steps_per_launch > 2 || ((cfg->ndim == 3 || fmode == 2) && cfg->steps_per_launch > 1) ||
@@ -1411,6 +1436,7 @@ dirac_status dirac_get_info(const dirac_grid *g, dirac_info *info) {
                                         DIRAC_PLAN_3D_STRANG, DIRAC_PLAN_SHIFT_SWEEPS, DIRAC_PLAN_FIELD_SWEEPS};
     const int mode = sweep_mode(g);
     info->plan = (mode == 1 && fused_pass(g)) ? DIRAC_PLAN_3D_FUSED : plan_of_mode[mode];
+    if (strang3d_zpass(g)) info->plan = DIRAC_PLAN_3D_STRANG_ZPASS;
     if (strang3d_fused(g)) {
         info->plan = DIRAC_PLAN_3D_STRANG_FUSED;
         info->points_per_lane = 1;
@@ -1446,15 +1472,18 @@ dirac_status dirac_autotune(dirac_grid *g) {
         int fused = 0;  // 3-D: warps per block of the fused pass (0: two-pass path)
         int s3 = 0;     // 3-D second order: 0 = eight single sweeps, else warps per block of the x-y-x pass
         int s3z = 2;    // and the z-phase-z pass's threads per SM / 1024
+        int s3zp = 0;   // 3-D second order, single sweeps: C D C as one z-phase-z pass
     };
     std::vector<Cand> cands;
     if (sweep_mode(g) >= 7) {
         cands.push_back({1, 1, 4, 8, 0, 0});  // single sweeps: nothing to choose
     } else if (sweep_mode(g) == 6) {
         cands.push_back({1, 2, 4, 16, 0, 0});
-        if (char_shift(g) == 1)  // the fused passes take one-cell x shifts
+        if (char_shift(g) == 1) {  // the fused passes take one-cell x shifts
             for (int sw : {16, 32})
                 for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, sw, zf});
+            for (int zf : {1, 2, 4}) cands.push_back({1, 2, 4, 16, 0, 0, zf, 1});
+        }
     } else if (g->fx && g->cfg.ndim == 3) {
         for (int P : {1, 2, 4})
             for (int wsm : {8, 16, 32}) cands.push_back({1, P, 4, wsm, 0});
@@ -1507,7 +1536,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     Cand best = {g->plan.K, g->plan.P, g->plan.wpb, 0, g->plan.fused3d ? g->plan.f_warps : 0,
-                 g->plan.s3_fused ? g->plan.s3_warps : 0, g->plan.s3_zfactor};
+                 g->plan.s3_fused ? g->plan.s3_warps : 0, g->plan.s3_zfactor, g->plan.s3_zpass};
     double best_t = 1e300;
     const int use_graphs = g->cfg.use_graphs;
     g->cfg.use_graphs = 0;
@@ -1519,6 +1548,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
         g->plan.s3_fused = c.s3 ? 1 : 0;
         if (c.s3) g->plan.s3_warps = c.s3;
         g->plan.s3_zfactor = c.s3z;
+        g->plan.s3_zpass = c.s3zp;
         make_plan(g, c.K, c.P, c.wpb, c.wsm);
         st = ensure_flux_part(g);
         if (st != DIRAC_OK) break;
@@ -1548,6 +1578,7 @@ dirac_status dirac_autotune(dirac_grid *g) {
         g->plan.s3_fused = best.s3 ? 1 : 0;
         if (best.s3) g->plan.s3_warps = best.s3;
         g->plan.s3_zfactor = best.s3z;
+        g->plan.s3_zpass = best.s3zp;
         make_plan(g, best.K, best.P, best.wpb, best.wsm ? best.wsm : 8);
         st = ensure_flux_part(g);
     }

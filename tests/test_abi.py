@@ -33,6 +33,16 @@ def test_header_declares_the_boundary():
         assert want in names
 
 
+def test_binding_constants_match_the_header():
+    """Every DIRAC_* enumerator of the header has the same value in the Python binding."""
+    import paper_1107_4650_gb300 as D
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(DIRAC_[A-Z0-9_]+)\s*=\s*(-?\d+)\s*[,}\n]", text))
+    assert "DIRAC_PLAN_3D_STRANG_ZPASS" in consts and len(consts) > 20
+    wrong = {k: (v, getattr(D, k, None)) for k, v in consts.items() if getattr(D, k, None) != v}
+    assert not wrong, wrong
+
+
 def test_every_declared_symbol_is_exported(lib):
     missing = [n for n in _declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
@@ -141,11 +151,11 @@ def test_3d_steps_per_launch_validation(lib):
 
 
 def test_fx64_validation(lib):
-    """DIRAC_FX64 runs first-order steps (one or, in 2-D, two per launch) and second-order steps (one; 3-D as
-    single sweeps)."""
+    """DIRAC_FX64 runs first-order steps (one or, in 2-D, two per launch) and second-order steps (one per launch
+    block; 3-D as single sweeps, single sweeps with a z-phase-z pass, or fused passes)."""
     import paper_1107_4650_gb300 as D
     for n, kw in (((8, 8, 8), dict(ndim=3, steps_per_launch=2)), ((8, 8, 8), dict(ndim=3, splitting=D.DIRAC_STRANG,
-                                                                                     points_per_lane=4)),
+                                                                                     steps_per_launch=2)),
                   ((16, 1, 16), dict(splitting=D.DIRAC_STRANG, steps_per_launch=2)),
                   ((16, 1, 16), dict(splitting=D.DIRAC_STRANG, steps_per_launch=1, points_per_lane=4)),
                   ((16, 1, 16), dict(char_shift=2)), ((16, 1, 16), dict(steps_per_launch=4)),

@@ -280,11 +280,11 @@ def test_fx_strang2d_klein_within_1e12_of_fp64_oracle(D):
 @pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13), (60, 30, 40), (29, 13, 3)])
 @pytest.mark.parametrize("periodic", [False, True])
 @pytest.mark.parametrize("full", [False, True])
-@pytest.mark.parametrize("pp,nsteps", [(1, 3), (2, 3), (2, 1), (2, 34)])
+@pytest.mark.parametrize("pp,nsteps", [(1, 3), (2, 3), (2, 1), (2, 34), (4, 3), (4, 34)])
 def test_fx_strang3d_bit_exact_against_fixed_point_oracle(D, shape, periodic, full, pp, nsteps):
-    """3-D second-order steps on the int64 state, as eight single sweeps (points_per_lane 1) or as the fused
-    x-y-x / z-phase-z / x-y-x-x-y-x passes (2; 34 steps: a captured 32-step run and a 2-step run), against
-    oracle_step_strang3d_fx bit for bit."""
+    """3-D second-order steps on the int64 state, as eight single sweeps (points_per_lane 1), as single x and y
+    sweeps with one z-phase-z pass (4) or as the fused x-y-x / z-phase-z / x-y-x-x-y-x passes (2; 34 steps: a
+    captured 32-step run and a 2-step run), against oracle_step_strang3d_fx bit for bit."""
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx * 3 + ny + nz)
     V = np.random.default_rng(ny + nz).uniform(-4e4, 4e4, nx * ny * nz if full else nx)
@@ -302,7 +302,8 @@ def test_fx_strang3d_bit_exact_against_fixed_point_oracle(D, shape, periodic, fu
         info = D.dirac_get_info(h)
     finally:
         D.dirac_destroy(h)
-    assert info["plan"] == (D.DIRAC_PLAN_3D_STRANG if pp == 1 else D.DIRAC_PLAN_3D_STRANG_FUSED)
+    assert info["plan"] == {1: D.DIRAC_PLAN_3D_STRANG, 2: D.DIRAC_PLAN_3D_STRANG_FUSED,
+                            4: D.DIRAC_PLAN_3D_STRANG_ZPASS}[pp]
     assert np.array_equal(got, want)
 
 

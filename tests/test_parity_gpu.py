@@ -700,14 +700,16 @@ def test_shift_fp32_against_oracle(D):
 
 # ------------------------------------------------------------------ 3-D second-order (Strang) splitting
 
-# points_per_lane 1: eight single-sweep launches per step; 2: the x-y-x, z-phase-z, x-y-x passes
-S3_PLANS = {1: "DIRAC_PLAN_3D_STRANG", 2: "DIRAC_PLAN_3D_STRANG_FUSED"}
+# points_per_lane 1: eight single-sweep launches per step; 2: the x-y-x, z-phase-z, x-y-x passes; 4: x, y, x
+# single sweeps, one z-phase-z pass, x, y, x single sweeps
+S3_PLANS = {1: "DIRAC_PLAN_3D_STRANG", 2: "DIRAC_PLAN_3D_STRANG_FUSED", 4: "DIRAC_PLAN_3D_STRANG_ZPASS"}
+S3_LAUNCHES = {1: lambda m: 8 * m, 2: lambda m: 2 * m + 1, 4: lambda m: 7 * m}
 
 
 @pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6), (41, 9, 13), (60, 30, 40), (29, 13, 3)])
 @pytest.mark.parametrize("periodic", [False, True])
 @pytest.mark.parametrize("full", [False, True])
-@pytest.mark.parametrize("pp", [1, 2])
+@pytest.mark.parametrize("pp", [1, 2, 4])
 def test_strang3d_fp64_bit_exact(D, shape, periodic, full, pp):
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx * ny + nz)
@@ -727,7 +729,7 @@ def test_strang3d_fp64_bit_exact(D, shape, periodic, full, pp):
     finally:
         D.dirac_destroy(h)
     assert info["plan"] == getattr(D, S3_PLANS[pp])
-    assert info["kernel_launches"] == (5 * 8 if pp == 1 else 2 * 5 + 1)
+    assert info["kernel_launches"] == S3_LAUNCHES[pp](5)
     assert _bits_equal(got, want), rel_l2(got, want)
 
 
@@ -775,7 +777,7 @@ def test_strang3d_fused_passes_fp32_same_bits_as_single_sweeps(D, periodic):
     psi = W.random_state(nz, ny, nx, seed=77).astype(np.complex64)
     V = np.random.default_rng(78).uniform(-4e4, 4e4, nx * ny * nz)
     out = {}
-    for pp in (1, 2):
+    for pp in (1, 2, 4):
         cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=pp, precision=D.DIRAC_FP32,
                             boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
         h = D.dirac_create_grid(cfg)
@@ -789,11 +791,12 @@ def test_strang3d_fused_passes_fp32_same_bits_as_single_sweeps(D, periodic):
         finally:
             D.dirac_destroy(h)
     assert np.array_equal(out[1].view(np.uint32), out[2].view(np.uint32))
+    assert np.array_equal(out[1].view(np.uint32), out[4].view(np.uint32))
     want, _ = oracle.step_strang3d(psi.astype(np.complex128), 1.0, C, DX, 6, V=V, periodic=periodic)
     assert rel_l2(out[2].astype(np.complex128), want) < 5e-6
 
 
-@pytest.mark.parametrize("pp", [1, 2])
+@pytest.mark.parametrize("pp", [1, 2, 4])
 def test_strang3d_interior_blocks_and_face_bit_exact(D, pp):
     """A grid wide enough that the fused passes have interior blocks (no boundary masks) next to edge blocks,
     with the face in an interior strip: state bit-exact and the face flux within rounding of the oracle."""
@@ -824,7 +827,7 @@ def test_strang3d_fused_field_fp32_same_bits_as_single_sweeps(D, periodic):
     V = np.random.default_rng(94).uniform(-4e4, 4e4, nx)
     At = _field_table(10, ny, scale=0.9)
     out = {}
-    for pp in (1, 2):
+    for pp in (1, 2, 4):
         cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, points_per_lane=pp, precision=D.DIRAC_FP32,
                             boundary=D.DIRAC_BC_PERIODIC if periodic else D.DIRAC_BC_ZERO)
         h = D.dirac_create_grid(cfg)
@@ -839,18 +842,20 @@ def test_strang3d_fused_field_fp32_same_bits_as_single_sweeps(D, periodic):
         finally:
             D.dirac_destroy(h)
     assert np.array_equal(out[1].view(np.uint32), out[2].view(np.uint32))
+    assert np.array_equal(out[1].view(np.uint32), out[4].view(np.uint32))
     want, _ = oracle.step_strang3d(psi.astype(np.complex128), 1.0, C, DX, 7, V=V, periodic=periodic, A_tilde=At)
     assert rel_l2(out[2].astype(np.complex128), want) < 5e-6
 
 
 def test_strang3d_default_plans_and_autotune(D):
-    """Library choice: FP32 storage runs the fused passes, FP64 the single sweeps; dirac_autotune picks among
-    both (and the fused pass's block and segment shapes) without changing the result."""
+    """Library choice: FP32 storage runs the fused passes, FP64 single x and y sweeps with the z-phase-z pass;
+    dirac_autotune picks among the three plans (and the passes' block and segment shapes) without changing the
+    result."""
     nx, ny, nz = 48, 40, 36
     psi = W.random_state(nz, ny, nx, seed=5)
     V = np.random.default_rng(6).uniform(-4e4, 4e4, nx)
     want, _ = oracle.step_strang3d(psi, 1.0, C, DX, 7, V=V, periodic=False)
-    for prec, plan in ((D.DIRAC_FP32, D.DIRAC_PLAN_3D_STRANG_FUSED), (D.DIRAC_FP64, D.DIRAC_PLAN_3D_STRANG)):
+    for prec, plan in ((D.DIRAC_FP32, D.DIRAC_PLAN_3D_STRANG_FUSED), (D.DIRAC_FP64, D.DIRAC_PLAN_3D_STRANG_ZPASS)):
         cfg = D.make_config((nx, ny, nz), ndim=3, splitting=D.DIRAC_STRANG, precision=prec)
         h = D.dirac_create_grid(cfg)
         try:
@@ -859,7 +864,8 @@ def test_strang3d_default_plans_and_autotune(D):
             st = psi.astype(np.complex64) if prec == D.DIRAC_FP32 else psi
             D.dirac_set_state(h, st)
             D.dirac_autotune(h)
-            assert D.dirac_get_info(h)["plan"] in (D.DIRAC_PLAN_3D_STRANG, D.DIRAC_PLAN_3D_STRANG_FUSED)
+            assert D.dirac_get_info(h)["plan"] in (D.DIRAC_PLAN_3D_STRANG, D.DIRAC_PLAN_3D_STRANG_FUSED,
+                                                   D.DIRAC_PLAN_3D_STRANG_ZPASS)
             D.dirac_step(h, 7)
             got = np.empty_like(st)
             D.dirac_get_state(h, got)
@@ -989,11 +995,12 @@ def coulomb384():
     return psi0, W.soft_coulomb_3d(n3, DX, 10.0, 2 * DX)
 
 
-@pytest.mark.parametrize("prec,pp", [("fp64", 0), ("fp64", 2), ("fp32", 0)])
+@pytest.mark.parametrize("prec,pp", [("fp64", 0), ("fp64", 1), ("fp64", 2), ("fp32", 0)])
 def test_full_size_384_cubed_strang_sampled_outputs(D, coulomb384, prec, pp):
-    """The 384^3 soft-Coulomb grid with second-order steps in the benchmark's plans (FP64: eight single sweeps;
-    FP32: the fused passes, a 3-step run) and the fused passes in FP64: 8 sampled cells recomputed by the oracle
-    on their light-cone crops (4 cells per step along each axis), FP64 bit for bit, FP32 within its rounding."""
+    """The 384^3 soft-Coulomb grid with second-order steps in the benchmark's plans (FP64: single x and y sweeps
+    with the z-phase-z pass; FP32: the fused passes, a 3-step run), and in FP64 eight single sweeps and the
+    fused passes: 8 sampled cells recomputed by the oracle on their light-cone crops (4 cells per step along
+    each axis), FP64 bit for bit, FP32 within its rounding."""
     psi0, V = coulomb384
     n3, nsteps = 384, 3
     fp32 = prec == "fp32"
@@ -1010,7 +1017,8 @@ def test_full_size_384_cubed_strang_sampled_outputs(D, coulomb384, prec, pp):
         plan = D.dirac_get_info(h)["plan"]
     finally:
         D.dirac_destroy(h)
-    assert plan == (D.DIRAC_PLAN_3D_STRANG_FUSED if (fp32 or pp == 2) else D.DIRAC_PLAN_3D_STRANG)
+    assert plan == (D.DIRAC_PLAN_3D_STRANG_FUSED if (fp32 or pp == 2) else
+                    (D.DIRAC_PLAN_3D_STRANG if pp == 1 else D.DIRAC_PLAN_3D_STRANG_ZPASS))
     scale = np.abs(psi0).max()
     for cell in [(192, 192, 192), (192, 192, 224), (0, 0, 0), (383, 200, 17), (100, 383, 383), (191, 5, 300),
                  (250, 250, 150), (7, 380, 192)]:
@@ -1270,7 +1278,7 @@ def test_strang_with_vector_potential_bit_exact(D, shape, periodic, P):
 
 @pytest.mark.parametrize("shape", [(24, 20, 18), (7, 5, 6)])
 @pytest.mark.parametrize("periodic", [False, True])
-@pytest.mark.parametrize("pp", [1, 2])
+@pytest.mark.parametrize("pp", [1, 2, 4])
 def test_strang3d_with_vector_potential_bit_exact(D, shape, periodic, pp):
     nx, ny, nz = shape
     psi = W.random_state(nz, ny, nx, seed=nx * ny + nz + 1)
