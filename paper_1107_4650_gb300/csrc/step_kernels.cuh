@@ -116,6 +116,17 @@ template <> __device__ __forceinline__ Cx<long long> cmulp<long long>(Cx<long lo
     const __int128 k3 = (__int128)z.im * (p.re + p.im);
     return {(long long)((k1 - k3) >> 62), (long long)((k1 + k2) >> 62)};
 }
+// The same product with four multiplies for the fixed-point state: each output from two independent 128-bit
+// products (re = z.re p.re - z.im p.im, im = z.re p.im + z.im p.re, each rounded as in cmulp, so the same
+// integers).  More instructions but no shared sum ahead of the products: measured faster in the 3-D
+// second-order z-phase-z pass (12.40 against 12.10 G point-steps/s at 256^3), slower in the 2-D step (31.0
+// against 33.2).  Floating-point states take cmulp.
+template <typename T> __device__ __forceinline__ Cx<T> cmulp4(Cx<T> z, Cx<T> p) { return cmulp(z, p); }
+template <> __device__ __forceinline__ Cx<long long> cmulp4<long long>(Cx<long long> z, Cx<long long> p) {
+    const __int128 a = (__int128)z.re * p.re + ((__int128)1 << 61), b = (__int128)z.im * p.im;
+    const __int128 c = (__int128)z.re * p.im + ((__int128)1 << 61), d = (__int128)z.im * p.re;
+    return {(long long)((a - b) >> 62), (long long)((c + d) >> 62)};
+}
 // Fixed point: o / 2^r rounded to nearest, halves upward (floating-point states never ask for it).
 template <typename T> __device__ __forceinline__ void round_shift(Cx<T> (&)[4], int) {}
 template <> __device__ __forceinline__ void round_shift<long long>(Cx<long long> (&o)[4], int r) {

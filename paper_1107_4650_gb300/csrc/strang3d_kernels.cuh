@@ -389,10 +389,10 @@ __global__ void __launch_bounds__(128, ZMinBlocks<T, FIELD>::value) strang_z_ker
                     o[2] = n2;
                     o[3] = n3;
                 } else {
-                    o[0] = cmulp(o[0], qu);
-                    o[1] = cmulp(o[1], qu);
-                    o[2] = cmulp(o[2], qd);
-                    o[3] = cmulp(o[3], qd);
+                    o[0] = cmulp4(o[0], qu);
+                    o[1] = cmulp4(o[1], qu);
+                    o[2] = cmulp4(o[2], qd);
+                    o[3] = cmulp4(o[3], qd);
                 }
             } else {
 #pragma unroll
