@@ -47,9 +47,9 @@ typedef enum {
 
 /* storage precision.  DIRAC_FX64: 64-bit fixed point, q = round(psi 2^S) per real component in int64, for
  * first-order steps (2-D: the fused step kernel, k = 1 or 2; 3-D: the fused single pass, points_per_lane 0,
- * or the x-y pass + z/phase pass) and second-order steps (2-D: one per launch; 3-D: eight single sweeps, the
- * phase carrying the first four
- * halves and the last sweep dividing by 16 with rounding): the sweeps' additions are exact and each step
+ * or the x-y pass + z/phase pass) and second-order steps (2-D: one per launch; 3-D: the fused passes, eight
+ * single sweeps, or single sweeps with one z-phase-z pass, the phase carrying the first four halves and the
+ * step's last x sweep dividing by 16 with rounding): the sweeps' additions are exact and each step
  * rounds once (twice in 3-D second order), in the phase (a 128-bit product with the coefficients held as
  * round(p 2^62)).  dirac_set_state picks S from the state's discrete norm (dirac_info.fx_shift); states go
  * in and out as complex128.  No vector potential or char_shift > 1. */
