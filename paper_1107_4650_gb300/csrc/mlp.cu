@@ -356,6 +356,208 @@ __global__ void to_bf16_kernel(const float *p, __nv_bfloat16 *pb, int64_t n) {
 
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
+// ---- Inference: the whole network for 128 queries per CTA in one launch.
+//
+// The weights of layers 2-4 are first packed into the canonical no-swizzle K-major layout the MMA reads
+// (the layout `stage` builds: B(k, n) = W[n][k], 256 rows n), so each layer's 128 KB operand reaches shared
+// memory as bulk copies (cp.async.bulk, completion counted on an mbarrier), issued as soon as the previous
+// layer's MMAs have read the buffer and overlapping that layer's epilogue.  Layer 1 (K = 3) runs on the CUDA
+// cores and writes bf16(h1) straight into the A operand (128 queries x 256); each hidden layer is 16
+// tcgen05.mma (M = 128, N = 256, K = 16, BF16 -> FP32) into 256 TMEM columns.  The epilogue runs on 8 warps:
+// warps w and w + 4 read the same 32 TMEM lanes (queries 32 (w % 4)..), columns 0-127 and 128-255; they add
+// the bias, take tanh and write bf16(h) over the A operand.  The output layer then sums bf16(h4) bf16(w5)
+// per query in out_fwd_kernel's order (32 strided partial sums, then its shuffle tree), so every rounding
+// point is forward's.  Every wait is bounded; a timeout sets *err.
+constexpr int IQ = 128;                          // queries per CTA (the MMA's M)
+constexpr int IW_SLAB = HID * 16 * 2;            // one 16-deep K slab of a 256-row weight operand (8 KB)
+constexpr int IH_SLAB = IQ * 16 * 2;             // one 16-deep K slab of the activations (4 KB)
+constexpr int IW_BYTES = (HID / 16) * IW_SLAB;   // 128 KB per layer
+constexpr int IH_BYTES = (HID / 16) * IH_SLAB;   // 64 KB
+constexpr int INFER_SMEM = IH_BYTES + IW_BYTES + 1024;
+static_assert(3 * (int64_t)IW_BYTES == WPACK_BYTES, "packed weight size");
+
+// pack[l][tile_off(n, k)] = W_{l+2}[n][k]: one thread per 8 consecutive k of one row.
+__global__ void pack_weights_kernel(const __nv_bfloat16 *wb, int64_t off2, int64_t off3, int64_t off4,
+                                    unsigned char *pack) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * HID * (HID / 8)) return;
+    const int l = (int)(e / (HID * (HID / 8))), n = (int)((e / (HID / 8)) % HID), k8 = (int)(e % (HID / 8)) * 8;
+    const int64_t off = l == 0 ? off2 : (l == 1 ? off3 : off4);
+    *reinterpret_cast<uint4 *>(pack + (int64_t)l * IW_BYTES + tile_off(n, k8, IW_SLAB)) =
+        *reinterpret_cast<const uint4 *>(wb + off + (int64_t)n * HID + k8);
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// One layer's packed weights into the B buffer: four 32 KB copies counted on `bar`.
+__device__ __forceinline__ void load_layer_weights(uint32_t ws, const unsigned char *src, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)IW_BYTES) : "memory");
+#pragma unroll
+    for (int c = 0; c < 4; ++c) bulk_copy(ws + c * (IW_BYTES / 4), src + c * (IW_BYTES / 4), IW_BYTES / 4, bar);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat16 lo = __float2bfloat16(a), hi = __float2bfloat16(b);
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__global__ void __launch_bounds__(256, 1) mlp_infer_kernel(const float *x, const __nv_bfloat16 *W1, const float *b1,
+                                                           const unsigned char *pack, const float *b2, const float *b3,
+                                                           const float *b4, const __nv_bfloat16 *w5, const float *b5,
+                                                           float *y, int Bn, unsigned *err) {
+    extern __shared__ unsigned char ism_raw[];
+    unsigned char *hs = reinterpret_cast<unsigned char *>(((uintptr_t)ism_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *wsm = hs + IH_BYTES;
+    __shared__ __align__(8) uint64_t bars[2];  // [0]: a layer's weights have landed, [1]: its MMAs are done
+    __shared__ uint32_t tmem_slot;
+    __shared__ int issued;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = (warp & 3) * 32 + lane;  // query within the tile = TMEM lane
+    const int cbase = (warp >> 2) * (HID / 2);  // this thread's 128 columns
+    const int q = blockIdx.x * IQ + row;
+    const uint32_t wbar = smem_addr(&bars[0]), mbar = smem_addr(&bars[1]), ws = smem_addr(wsm);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(wbar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        load_layer_weights(ws, pack, wbar);
+    }
+    // layer 1 on the CUDA cores (layer1_fwd_kernel's arithmetic): this thread's 128 columns of its query
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    if (q < Bn) {
+        x0 = x[(int64_t)q * 3 + 0];
+        x1 = x[(int64_t)q * 3 + 1];
+        x2 = x[(int64_t)q * 3 + 2];
+    }
+    for (int j0 = cbase; j0 < cbase + HID / 2; j0 += 8) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            float h[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int j = j0 + i + u;
+                float z = b1[j];
+                z = fmaf(x0, __bfloat162float(W1[j * 3 + 0]), z);
+                z = fmaf(x1, __bfloat162float(W1[j * 3 + 1]), z);
+                z = fmaf(x2, __bfloat162float(W1[j * 3 + 2]), z);
+                h[u] = tanhf(z);
+            }
+            pk[i / 2] = pack_bf16x2(h[0], h[1]);
+        }
+        *reinterpret_cast<uint4 *>(hs + tile_off(row, j0, IH_SLAB)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // activations -> the tensor core's view
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = 256, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(HID >> 3) << 17) | ((uint32_t)(IQ >> 4) << 24);
+    bool ok = true;
+    int copies = 1;  // weight copies issued (each completes one phase of wbar)
+    for (int L = 0; L < 3 && ok; ++L) {
+        if (tid == 0) {
+            issued = 0;
+            if (bar_wait(wbar, (uint32_t)(L & 1))) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < HID / 16; ++j) {
+                    const uint64_t ad = umma_desc(smem_addr(hs + j * IH_SLAB));
+                    const uint64_t bd = umma_desc(ws + j * IW_SLAB);
+                    const uint32_t acc = j > 0 ? 1u : 0u;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                 : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                             : "memory");
+                issued = 1;
+            }
+        }
+        __syncthreads();
+        ok = __syncthreads_and(issued && bar_wait(mbar, (uint32_t)(L & 1)));
+        if (!ok) break;
+        // the MMAs have read both operands: the next layer's weights can land while this epilogue runs
+        if (tid == 0 && L < 2) {
+            load_layer_weights(ws, pack + (int64_t)(L + 1) * IW_BYTES, wbar);
+            ++copies;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float *bias = L == 0 ? b2 : (L == 1 ? b3 : b4);
+#pragma unroll 1
+        for (int c0 = cbase; c0 < cbase + HID / 2; c0 += 32) {
+            uint32_t r[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 32; i += 8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int u = 0; u < 8; u += 2)
+                    pk[u / 2] = pack_bf16x2(tanhf(__uint_as_float(r[i + u]) + bias[c0 + i + u]),
+                                            tanhf(__uint_as_float(r[i + u + 1]) + bias[c0 + i + u + 1]));
+                *reinterpret_cast<uint4 *>(hs + tile_off(row, c0 + i, IH_SLAB)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (ok && warp < 4 && q < Bn) {
+        // output layer in out_fwd_kernel's order: partial sum l takes columns l, l + 32, ..., then the xor tree
+        float s[32];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) s[l] = 0.f;
+#pragma unroll
+        for (int t = 0; t < HID / 32; ++t)
+#pragma unroll
+            for (int l8 = 0; l8 < 32; l8 += 8) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(hs + tile_off(row, 32 * t + l8, IH_SLAB));
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const __nv_bfloat16 h = __ushort_as_bfloat16((unsigned short)(w[u / 2] >> (16 * (u & 1))));
+                    s[l8 + u] = fmaf(__bfloat162float(h), __bfloat162float(w5[32 * t + l8 + u]), s[l8 + u]);
+                }
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int l = 0; l < o; ++l) s[l] = s[l] + s[l + o];
+        y[q] = 1.f / (1.f + expf(-(s[0] + b5[0])));
+    }
+    if (!ok && tid == 0) {
+        atomicOr(err, 1u);
+        // let this CTA's last weight copy finish (bounded) before its shared memory is released; the earlier
+        // ones completed before their layer's MMAs were issued
+        bar_wait(wbar, (uint32_t)((copies - 1) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
 }  // namespace
 
 cudaError_t gemm_bf16(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B, int64_t sbk, int64_t sbn,
@@ -373,6 +575,27 @@ cudaError_t gemm_bf16(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __
     }
     dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
     gemm_bf16_kernel<<<grid, 128, GEMM_SMEM, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, accumulate, err);
+    return cudaGetLastError();
+}
+
+cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s) {
+    if (Bn <= 0) return cudaSuccess;
+    if ((n.off_w[1] | n.off_w[2] | n.off_w[3]) & 7) return cudaErrorInvalidValue;  // 16-byte rows for the packing
+    pack_weights_kernel<<<nblk(3 * HID * (HID / 8), 256), 256, 0, s>>>(n.wb, n.off_w[1], n.off_w[2], n.off_w[3], n.wpack);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (!bit || !(attr_set.load(std::memory_order_relaxed) & bit)) {
+        e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, INFER_SMEM);
+        if (e != cudaSuccess) return e;
+        if (bit) attr_set.fetch_or(bit, std::memory_order_relaxed);
+    }
+    mlp_infer_kernel<<<nblk(Bn, IQ), 256, INFER_SMEM, s>>>(x, n.wb + n.off_w[0], n.p + n.off_b[0], n.wpack,
+                                                           n.p + n.off_b[1], n.p + n.off_b[2], n.p + n.off_b[3],
+                                                           n.wb + n.off_w[4], n.p + n.off_b[4], y, Bn, n.err);
     return cudaGetLastError();
 }
 

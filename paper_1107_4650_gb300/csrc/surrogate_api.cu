@@ -146,6 +146,7 @@ dirac_status dirac_surrogate_create(const double lo[3], const double hi[3], uint
     if (e == cudaSuccess) e = salloc(s, &s->net.m, NPARAM * sizeof(float));
     if (e == cudaSuccess) e = salloc(s, &s->net.v, NPARAM * sizeof(float));
     if (e == cudaSuccess) e = salloc(s, &s->net.wb, NPARAM * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = salloc(s, &s->net.wpack, WPACK_BYTES);
     if (e == cudaSuccess) e = salloc(s, &s->grad, NPARAM * sizeof(float));
     for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
         e = salloc(s, &s->acts.h[l], B * HID * sizeof(float));
@@ -381,7 +382,7 @@ dirac_status dirac_surrogate_predict(dirac_surrogate *s, const double *X, int64_
         const int nb = (int)std::min<int64_t>(s->max_batch, n - i0);
         dirac_status st = stage(s, X, nullptr, i0, nb);
         if (st != DIRAC_OK) return st;
-        SCK(s, forward(s->net, s->acts, s->xb, nb, s->stream));
+        SCK(s, infer(s->net, s->xb, s->acts.y, nb, s->stream));
         SCK(s, cudaMemcpyAsync(y.data(), s->acts.y, nb * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
         SCK(s, cudaStreamSynchronize(s->stream));
         for (int b = 0; b < nb; ++b) T_out[i0 + b] = y[b];
