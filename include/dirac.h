@@ -386,7 +386,10 @@ dirac_status dirac_surrogate_destroy(dirac_surrogate *s);
 dirac_status dirac_surrogate_train(dirac_surrogate *s, const double *X, const double *T, int64_t n, int epochs,
                                    int batch, double lr, double *loss_out);
 
-/* Network prediction for n points (host buffers), no range check. */
+/* Network prediction for n points (host buffers), no range check: one fused kernel launch per max_batch
+ * points (128 points per CTA: tensor-core layers, weights staged by bulk copies), the same rounding points
+ * and results as the training forward pass.  Synchronises; DIRAC_ERR_TIMEOUT if a bounded tensor-core wait
+ * ran out. */
 dirac_status dirac_surrogate_predict(dirac_surrogate *s, const double *X, int64_t n, double *T_out);
 
 /* Gradient of mean((y - T)^2) over the n <= max_batch samples with respect to every parameter (FP32, the

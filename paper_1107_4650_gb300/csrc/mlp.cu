@@ -365,7 +365,8 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 // cores and writes bf16(h1) straight into the A operand (128 queries x 256); each hidden layer is 16
 // tcgen05.mma (M = 128, N = 256, K = 16, BF16 -> FP32) into 256 TMEM columns.  The epilogue runs on 8 warps:
 // warps w and w + 4 read the same 32 TMEM lanes (queries 32 (w % 4)..), columns 0-127 and 128-255; they add
-// the bias, take tanh and write bf16(h) over the A operand.  The output layer then sums bf16(h4) bf16(w5)
+// the bias, take tanh and write bf16(h) over the A operand.  (16 warps: four per lane group, 64 columns each,
+// the epilogue's tanh spread over twice the threads.)  The output layer then sums bf16(h4) bf16(w5)
 // per query in out_fwd_kernel's order (32 strided partial sums, then its shuffle tree), so every rounding
 // point is forward's.  Every wait is bounded; a timeout sets *err.
 constexpr int IQ = 128;                          // queries per CTA (the MMA's M)
@@ -405,7 +406,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__global__ void __launch_bounds__(256, 1) mlp_infer_kernel(const float *x, const __nv_bfloat16 *W1, const float *b1,
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 1) mlp_infer_kernel(const float *x, const __nv_bfloat16 *W1, const float *b1,
                                                            const unsigned char *pack, const float *b2, const float *b3,
                                                            const float *b4, const __nv_bfloat16 *w5, const float *b5,
                                                            float *y, int Bn, unsigned *err) {
@@ -417,7 +419,8 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_kernel(const float *x, const
     __shared__ int issued;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = (warp & 3) * 32 + lane;  // query within the tile = TMEM lane
-    const int cbase = (warp >> 2) * (HID / 2);  // this thread's 128 columns
+    constexpr int NCOL = HID / (NW / 4);  // columns per thread: the NW / 4 warps of a lane group split them
+    const int cbase = (warp >> 2) * NCOL;
     const int q = blockIdx.x * IQ + row;
     const uint32_t wbar = smem_addr(&bars[0]), mbar = smem_addr(&bars[1]), ws = smem_addr(wsm);
     if (warp == 0) {
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_kernel(const float *x, const
         x1 = x[(int64_t)q * 3 + 1];
         x2 = x[(int64_t)q * 3 + 2];
     }
-    for (int j0 = cbase; j0 < cbase + HID / 2; j0 += 8) {
+    for (int j0 = cbase; j0 < cbase + NCOL; j0 += 8) {
         uint32_t pk[4];
 #pragma unroll
         for (int i = 0; i < 8; i += 2) {
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_kernel(const float *x, const
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const float *bias = L == 0 ? b2 : (L == 1 ? b3 : b4);
 #pragma unroll 1
-        for (int c0 = cbase; c0 < cbase + HID / 2; c0 += 32) {
+        for (int c0 = cbase; c0 < cbase + NCOL; c0 += 32) {
             uint32_t r[32];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -578,24 +581,31 @@ cudaError_t gemm_bf16(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __
     return cudaGetLastError();
 }
 
-cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s) {
-    if (Bn <= 0) return cudaSuccess;
+cudaError_t pack_weights(const Net &n, cudaStream_t s) {
     if ((n.off_w[1] | n.off_w[2] | n.off_w[3]) & 7) return cudaErrorInvalidValue;  // 16-byte rows for the packing
     pack_weights_kernel<<<nblk(3 * HID * (HID / 8), 256), 256, 0, s>>>(n.wb, n.off_w[1], n.off_w[2], n.off_w[3], n.wpack);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+#ifndef MLP_INFER_WARPS
+#define MLP_INFER_WARPS 16
+#endif
+
+cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s) {
+    if (Bn <= 0) return cudaSuccess;
+    constexpr int NW = MLP_INFER_WARPS;
     static std::atomic<unsigned long long> attr_set{0};
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
     if (!bit || !(attr_set.load(std::memory_order_relaxed) & bit)) {
-        e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, INFER_SMEM);
+        cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, INFER_SMEM);
         if (e != cudaSuccess) return e;
         if (bit) attr_set.fetch_or(bit, std::memory_order_relaxed);
     }
-    mlp_infer_kernel<<<nblk(Bn, IQ), 256, INFER_SMEM, s>>>(x, n.wb + n.off_w[0], n.p + n.off_b[0], n.wpack,
-                                                           n.p + n.off_b[1], n.p + n.off_b[2], n.p + n.off_b[3],
-                                                           n.wb + n.off_w[4], n.p + n.off_b[4], y, Bn, n.err);
+    mlp_infer_kernel<NW><<<nblk(Bn, IQ), 32 * NW, INFER_SMEM, s>>>(x, n.wb + n.off_w[0], n.p + n.off_b[0], n.wpack,
+                                                                   n.p + n.off_b[1], n.p + n.off_b[2], n.p + n.off_b[3],
+                                                                   n.wb + n.off_w[4], n.p + n.off_b[4], y, Bn, n.err);
     return cudaGetLastError();
 }
 

@@ -46,9 +46,10 @@ inline void layout(Net &n) {
 cudaError_t gemm_bf16(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B, int64_t sbk, int64_t sbn,
                       float *C, int64_t ldc, int M, int N, int K, int accumulate, unsigned *err, cudaStream_t s);
 cudaError_t forward(const Net &n, const Acts &a, const float *x, int Bn, cudaStream_t s);
-// Inference only: y = network(x) for Bn queries in one fused launch (after packing W2-W4); the same rounding
-// points as forward.  Bytes of n.wpack it needs:
+// Inference only: y = network(x) for Bn queries in one fused launch, with the same rounding points as forward.
+// It reads W2-W4 from n.wpack, which pack_weights fills from n.wb (again after every change of the weights).
 constexpr int64_t WPACK_BYTES = 3 * (int64_t)HID * HID * 2;
+cudaError_t pack_weights(const Net &n, cudaStream_t s);
 cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s);
 cudaError_t backward(const Net &n, const Acts &a, const float *x, const float *t, float *g, int Bn, cudaStream_t s);
 cudaError_t adam(const Net &n, const float *g, float lr, int64_t step, cudaStream_t s);

@@ -50,6 +50,8 @@ struct dirac_surrogate {
     float *xb = nullptr, *tb = nullptr;
     int *idx = nullptr;
     float *host_pinned = nullptr;  // staging: max_batch * 4 floats
+    unsigned *flag_pinned = nullptr;  // the tensor-wait flag, read back with a prediction's outputs
+    bool packed = false;  // net.wpack holds the current W2-W4 (cleared whenever the weights change)
     int64_t step = 0;
     bool bias_set = false;  // output bias already chosen (trained or loaded parameters)
     std::vector<void *> owned;
@@ -164,6 +166,7 @@ dirac_status dirac_surrogate_create(const double lo[3], const double hi[3], uint
     if (e == cudaSuccess) e = salloc(s, &s->net.err, 16);
     if (e == cudaSuccess) e = cudaMemset(s->net.err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost(&s->host_pinned, B * 4 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->flag_pinned, 16);
     if (e != cudaSuccess) return bail(scuda(s, e, "surrogate allocation"));
     // Xavier-uniform weights, zero biases
     std::vector<float> p(NPARAM, 0.f);
@@ -186,6 +189,7 @@ dirac_status dirac_surrogate_destroy(dirac_surrogate *s) {
     cudaStreamSynchronize(s->stream);
     for (void *p : s->owned) cudaFree(p);
     if (s->host_pinned) cudaFreeHost(s->host_pinned);
+    if (s->flag_pinned) cudaFreeHost(s->flag_pinned);
     delete s;
     return DIRAC_OK;
 }
@@ -196,6 +200,7 @@ dirac_status dirac_surrogate_set_params(dirac_surrogate *s, const float *params)
     SCK(s, cudaMemcpyAsync(s->net.p, params, NPARAM * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     SCK(s, cudaMemsetAsync(s->net.m, 0, NPARAM * sizeof(float), s->stream));
     SCK(s, cudaMemsetAsync(s->net.v, 0, NPARAM * sizeof(float), s->stream));
+    s->packed = false;
     SCK(s, refresh_bf16(s->net, s->stream));
     SCK(s, cudaStreamSynchronize(s->stream));
     s->step = 0;
@@ -263,6 +268,7 @@ dirac_status dirac_surrogate_load(dirac_surrogate *s, const char *path) {
     SCK(s, cudaMemcpyAsync(s->net.p, buf.data(), NPARAM * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     SCK(s, cudaMemcpyAsync(s->net.m, buf.data() + NPARAM, NPARAM * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     SCK(s, cudaMemcpyAsync(s->net.v, buf.data() + 2 * NPARAM, NPARAM * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    s->packed = false;
     SCK(s, refresh_bf16(s->net, s->stream));
     SCK(s, cudaStreamSynchronize(s->stream));
     for (int d = 0; d < 3; ++d) {
@@ -302,6 +308,7 @@ dirac_status dirac_surrogate_train(dirac_surrogate *s, const double *X, const do
     if (!s || !X || !T || n < 1 || epochs < 0 || batch < 1 || batch > s->max_batch || !(lr > 0))
         return sfail(s, DIRAC_ERR_ARG, "dirac_surrogate_train: bad arguments");
     SCK(s, cudaSetDevice(s->device));
+    s->packed = false;  // the Adam steps change the weights
     float *dX = nullptr, *dT = nullptr;
     int *dIdx = nullptr;
     std::vector<float> hx((size_t)n * 3), ht(n);
@@ -377,17 +384,28 @@ dirac_status dirac_surrogate_train(dirac_surrogate *s, const double *X, const do
 dirac_status dirac_surrogate_predict(dirac_surrogate *s, const double *X, int64_t n, double *T_out) {
     if (!s || !X || !T_out || n < 0) return sfail(s, DIRAC_ERR_ARG, "bad arguments");
     SCK(s, cudaSetDevice(s->device));
+    if (!s->packed) {
+        SCK(s, pack_weights(s->net, s->stream));
+        s->packed = true;
+    }
     std::vector<float> y(s->max_batch);
+    *s->flag_pinned = 0;
     for (int64_t i0 = 0; i0 < n; i0 += s->max_batch) {
         const int nb = (int)std::min<int64_t>(s->max_batch, n - i0);
         dirac_status st = stage(s, X, nullptr, i0, nb);
         if (st != DIRAC_OK) return st;
         SCK(s, infer(s->net, s->xb, s->acts.y, nb, s->stream));
         SCK(s, cudaMemcpyAsync(y.data(), s->acts.y, nb * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+        if (i0 + nb >= n)  // the flag a timed-out tensor-core wait sets, read with the last outputs
+            SCK(s, cudaMemcpyAsync(s->flag_pinned, s->net.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
         SCK(s, cudaStreamSynchronize(s->stream));
         for (int b = 0; b < nb; ++b) T_out[i0 + b] = y[b];
     }
-    return check_tensor_waits(s);
+    if (*s->flag_pinned) {
+        SCK(s, cudaMemset(s->net.err, 0, sizeof(unsigned)));
+        return sfail(s, DIRAC_ERR_TIMEOUT, "a tensor-core wait of the inference kernel ran out; results are invalid");
+    }
+    return DIRAC_OK;
 }
 
 dirac_status dirac_klein_run_from_reduced(const double q[3], double dx, double c, double m, dirac_klein_run *run) {
