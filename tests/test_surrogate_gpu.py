@@ -95,6 +95,37 @@ def test_fused_inference_matches_training_forward_and_oracle(D, n, max_batch):
     assert d.max() < 1e-3 and d.mean() < 2e-5, (d.max(), d.mean())
 
 
+def test_inference_follows_every_change_of_the_weights(D):
+    """The inference kernel reads packed copies of W2-W4: after dirac_surrogate_set_params and after training,
+    predictions equal those of a fresh handle holding the same parameters."""
+    rng = np.random.default_rng(5)
+    q = LO + (HI - LO) * rng.uniform(0, 1, (200, 3))
+    t = rng.uniform(0.1, 0.9, 200)
+
+    def fresh(params):
+        h2 = D.dirac_surrogate_create(LO, HI, seed=1, max_batch=256)
+        try:
+            D.dirac_surrogate_set_params(h2, params)
+            return D.dirac_surrogate_predict(h2, q)
+        finally:
+            D.dirac_surrogate_destroy(h2)
+
+    h = D.dirac_surrogate_create(LO, HI, seed=3, max_batch=256)
+    try:
+        y0 = D.dirac_surrogate_predict(h, q)
+        pb = rng.normal(0.0, 0.05, D.dirac_surrogate_get_params(h).size)
+        D.dirac_surrogate_set_params(h, pb)
+        y1 = D.dirac_surrogate_predict(h, q)
+        D.dirac_surrogate_train(h, q, t, 2, 64, 1e-3)
+        y2 = D.dirac_surrogate_predict(h, q)
+        p2 = D.dirac_surrogate_get_params(h)
+    finally:
+        D.dirac_surrogate_destroy(h)
+    assert not np.array_equal(y0, y1) and not np.array_equal(y1, y2)
+    assert np.array_equal(y1, fresh(pb.astype(np.float32)))
+    assert np.array_equal(y2, fresh(p2))
+
+
 def test_training_fits_a_smooth_function(D):
     rng = np.random.default_rng(5)
     q = LO + (HI - LO) * rng.uniform(0, 1, (4096, 3))
