@@ -94,6 +94,8 @@ bool in_box(const dirac_surrogate *s, const double *q) {
 // Uploads normalised inputs (and targets) of points [i0, i0 + nb) into the batch buffers.
 dirac_status stage(dirac_surrogate *s, const double *X, const double *T, int64_t i0, int nb) {
     float *h = s->host_pinned;
+    // large batches: the per-query divisions on all host cores (each query's arithmetic unchanged)
+#pragma omp parallel for schedule(static) if (nb >= 32768)
     for (int b = 0; b < nb; ++b) normalise(s, X + (i0 + b) * 3, h + b * 3);
     SCK(s, cudaMemcpyAsync(s->xb, h, (size_t)nb * 3 * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     if (T) {
@@ -399,6 +401,7 @@ dirac_status dirac_surrogate_predict(dirac_surrogate *s, const double *X, int64_
         if (i0 + nb >= n)  // the flag a timed-out tensor-core wait sets, read with the last outputs
             SCK(s, cudaMemcpyAsync(s->flag_pinned, s->net.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
         SCK(s, cudaStreamSynchronize(s->stream));
+#pragma omp parallel for schedule(static) if (nb >= 32768)
         for (int b = 0; b < nb; ++b) T_out[i0 + b] = y[b];
     }
     if (*s->flag_pinned) {
