@@ -388,8 +388,10 @@ dirac_status dirac_surrogate_train(dirac_surrogate *s, const double *X, const do
 
 /* Network prediction for n points (host buffers), no range check: one fused kernel launch per max_batch
  * points (128 points per CTA: tensor-core layers, weights staged by bulk copies), the same rounding points
- * and results as the training forward pass.  Synchronises; DIRAC_ERR_TIMEOUT if a bounded tensor-core wait
- * ran out. */
+ * and results as the training forward pass.  Synchronises; DIRAC_ERR_TIMEOUT if a bounded wait (weights
+ * copied in, tensor-core products done; about one second each) ran out, the outputs then invalid.  Setting
+ * DIRAC_INJECT_STALL before dirac_surrogate_create makes every prediction launch of that network stall one
+ * weight wait on purpose, to test this path. */
 dirac_status dirac_surrogate_predict(dirac_surrogate *s, const double *X, int64_t n, double *T_out);
 
 /* Gradient of mean((y - T)^2) over the n <= max_batch samples with respect to every parameter (FP32, the

@@ -394,9 +394,11 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
                  : "memory");
 }
 
-// One layer's packed weights into the B buffer: four 32 KB copies counted on `bar`.
-__device__ __forceinline__ void load_layer_weights(uint32_t ws, const unsigned char *src, uint32_t bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)IW_BYTES) : "memory");
+// One layer's packed weights into the B buffer: four 32 KB copies counted on `bar`.  `extra` bytes more are
+// announced than the copies deliver when a test asks for a stalled wait (the phase then never completes).
+__device__ __forceinline__ void load_layer_weights(uint32_t ws, const unsigned char *src, uint32_t bar, uint32_t extra) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)IW_BYTES + extra)
+                 : "memory");
 #pragma unroll
     for (int c = 0; c < 4; ++c) bulk_copy(ws + c * (IW_BYTES / 4), src + c * (IW_BYTES / 4), IW_BYTES / 4, bar);
 }
@@ -410,7 +412,7 @@ template <int NW>
 __global__ void __launch_bounds__(32 * NW, 1) mlp_infer_kernel(const float *x, const __nv_bfloat16 *W1, const float *b1,
                                                            const unsigned char *pack, const float *b2, const float *b3,
                                                            const float *b4, const __nv_bfloat16 *w5, const float *b5,
-                                                           float *y, int Bn, unsigned *err) {
+                                                           float *y, int Bn, unsigned *err, int inject_stall) {
     extern __shared__ unsigned char ism_raw[];
     unsigned char *hs = reinterpret_cast<unsigned char *>(((uintptr_t)ism_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *wsm = hs + IH_BYTES;
@@ -432,7 +434,8 @@ __global__ void __launch_bounds__(32 * NW, 1) mlp_infer_kernel(const float *x, c
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(wbar) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        load_layer_weights(ws, pack, wbar);
+        // failure-detection test hook: the first CTA's first weight wait runs out
+        load_layer_weights(ws, pack, wbar, (inject_stall && blockIdx.x == 0) ? 16u : 0u);
     }
     // layer 1 on the CUDA cores (layer1_fwd_kernel's arithmetic): this thread's 128 columns of its query
     float x0 = 0.f, x1 = 0.f, x2 = 0.f;
@@ -466,8 +469,9 @@ __global__ void __launch_bounds__(32 * NW, 1) mlp_infer_kernel(const float *x, c
     const uint32_t tmem = tmem_slot;
     // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = 256, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(HID >> 3) << 17) | ((uint32_t)(IQ >> 4) << 24);
+    // Every weight copy is waited for (bounded) before the MMAs that read it, and the next one is issued only
+    // after those MMAs completed, so no copy is in flight wherever the loop stops early.
     bool ok = true;
-    int copies = 1;  // weight copies issued (each completes one phase of wbar)
     for (int L = 0; L < 3 && ok; ++L) {
         if (tid == 0) {
             issued = 0;
@@ -493,8 +497,7 @@ __global__ void __launch_bounds__(32 * NW, 1) mlp_infer_kernel(const float *x, c
         if (!ok) break;
         // the MMAs have read both operands: the next layer's weights can land while this epilogue runs
         if (tid == 0 && L < 2) {
-            load_layer_weights(ws, pack + (int64_t)(L + 1) * IW_BYTES, wbar);
-            ++copies;
+            load_layer_weights(ws, pack + (int64_t)(L + 1) * IW_BYTES, wbar, 0u);
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const float *bias = L == 0 ? b2 : (L == 1 ? b3 : b4);
@@ -550,12 +553,7 @@ __global__ void __launch_bounds__(32 * NW, 1) mlp_infer_kernel(const float *x, c
             for (int l = 0; l < o; ++l) s[l] = s[l] + s[l + o];
         y[q] = 1.f / (1.f + expf(-(s[0] + b5[0])));
     }
-    if (!ok && tid == 0) {
-        atomicOr(err, 1u);
-        // let this CTA's last weight copy finish (bounded) before its shared memory is released; the earlier
-        // ones completed before their layer's MMAs were issued
-        bar_wait(wbar, (uint32_t)((copies - 1) & 1));
-    }
+    if (!ok && tid == 0) atomicOr(err, 1u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
@@ -591,7 +589,7 @@ cudaError_t pack_weights(const Net &n, cudaStream_t s) {
 #define MLP_INFER_WARPS 16
 #endif
 
-cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s) {
+cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s, int inject_stall) {
     if (Bn <= 0) return cudaSuccess;
     constexpr int NW = MLP_INFER_WARPS;
     static std::atomic<unsigned long long> attr_set{0};
@@ -605,7 +603,8 @@ cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s
     }
     mlp_infer_kernel<NW><<<nblk(Bn, IQ), 32 * NW, INFER_SMEM, s>>>(x, n.wb + n.off_w[0], n.p + n.off_b[0], n.wpack,
                                                                    n.p + n.off_b[1], n.p + n.off_b[2], n.p + n.off_b[3],
-                                                                   n.wb + n.off_w[4], n.p + n.off_b[4], y, Bn, n.err);
+                                                                   n.wb + n.off_w[4], n.p + n.off_b[4], y, Bn, n.err,
+                                                                   inject_stall);
     return cudaGetLastError();
 }
 

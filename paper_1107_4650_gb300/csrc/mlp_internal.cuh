@@ -50,7 +50,8 @@ cudaError_t forward(const Net &n, const Acts &a, const float *x, int Bn, cudaStr
 // It reads W2-W4 from n.wpack, which pack_weights fills from n.wb (again after every change of the weights).
 constexpr int64_t WPACK_BYTES = 3 * (int64_t)HID * HID * 2;
 cudaError_t pack_weights(const Net &n, cudaStream_t s);
-cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s);
+// inject_stall (tests): the first CTA's first weight wait runs out, as a stuck copy would make it.
+cudaError_t infer(const Net &n, const float *x, float *y, int Bn, cudaStream_t s, int inject_stall);
 cudaError_t backward(const Net &n, const Acts &a, const float *x, const float *t, float *g, int Bn, cudaStream_t s);
 cudaError_t adam(const Net &n, const float *g, float lr, int64_t step, cudaStream_t s);
 cudaError_t refresh_bf16(const Net &n, cudaStream_t s);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -52,6 +53,7 @@ struct dirac_surrogate {
     float *host_pinned = nullptr;  // staging: max_batch * 4 floats
     unsigned *flag_pinned = nullptr;  // the tensor-wait flag, read back with a prediction's outputs
     bool packed = false;  // net.wpack holds the current W2-W4 (cleared whenever the weights change)
+    int inject_stall = 0;  // DIRAC_INJECT_STALL set at creation: every prediction launch stalls one wait
     int64_t step = 0;
     bool bias_set = false;  // output bias already chosen (trained or loaded parameters)
     std::vector<void *> owned;
@@ -135,6 +137,7 @@ dirac_status dirac_surrogate_create(const double lo[3], const double hi[3], uint
     std::memcpy(s->hi, hi, sizeof(s->hi));
     s->seed = seed;
     s->max_batch = max_batch;
+    s->inject_stall = std::getenv("DIRAC_INJECT_STALL") ? 1 : 0;
     s->stream = static_cast<cudaStream_t>(stream);
     s->device = device;
     auto bail = [&](dirac_status st) {
@@ -396,7 +399,7 @@ dirac_status dirac_surrogate_predict(dirac_surrogate *s, const double *X, int64_
         const int nb = (int)std::min<int64_t>(s->max_batch, n - i0);
         dirac_status st = stage(s, X, nullptr, i0, nb);
         if (st != DIRAC_OK) return st;
-        SCK(s, infer(s->net, s->xb, s->acts.y, nb, s->stream));
+        SCK(s, infer(s->net, s->xb, s->acts.y, nb, s->stream, s->inject_stall));
         SCK(s, cudaMemcpyAsync(y.data(), s->acts.y, nb * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
         if (i0 + nb >= n)  // the flag a timed-out tensor-core wait sets, read with the last outputs
             SCK(s, cudaMemcpyAsync(s->flag_pinned, s->net.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));

@@ -126,6 +126,36 @@ def test_inference_follows_every_change_of_the_weights(D):
     assert np.array_equal(y2, fresh(p2))
 
 
+def test_stalled_weight_copy_is_reported_and_the_context_survives(D, monkeypatch):
+    """DIRAC_INJECT_STALL makes the inference kernel's first weight wait run out (its barrier expects 16 bytes
+    more than the copies deliver; the copies complete): the CTA gives up after its bounded wait, predict returns
+    DIRAC_ERR_TIMEOUT, and the same process then predicts correctly with a network created without the hook."""
+    import time
+    rng = np.random.default_rng(9)
+    q = LO + (HI - LO) * rng.uniform(0, 1, (100, 3))
+    monkeypatch.setenv("DIRAC_INJECT_STALL", "1")
+    h = D.dirac_surrogate_create(LO, HI, seed=2, max_batch=128)
+    monkeypatch.delenv("DIRAC_INJECT_STALL")
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_surrogate_predict(h, q)
+        waited = time.perf_counter() - t0
+        assert e.value.status == D.DIRAC_ERR_TIMEOUT
+        assert 0.5 < waited < 20.0, waited
+        p = D.dirac_surrogate_get_params(h)
+    finally:
+        D.dirac_surrogate_destroy(h)
+    h2 = D.dirac_surrogate_create(LO, HI, seed=2, max_batch=128)
+    try:
+        D.dirac_surrogate_set_params(h2, p)
+        y = D.dirac_surrogate_predict(h2, q)
+    finally:
+        D.dirac_surrogate_destroy(h2)
+    want = M.predict(p.astype(np.float64), _norm(q))
+    assert np.all(np.isfinite(y)) and np.max(np.abs(y - want)) < 1e-3
+
+
 def test_training_fits_a_smooth_function(D):
     rng = np.random.default_rng(5)
     q = LO + (HI - LO) * rng.uniform(0, 1, (4096, 3))
