@@ -507,6 +507,31 @@ def main():
                                 "norm_fp32": o32["norm"], "norm_fp64": fp64_norm,
                                 "dT": (o32["flux_cum"] - fp64_flux) / n0}}
         D.dirac_destroy(h32)
+        # the same FP32 step at one step per launch (k = 1, P = 2): it moves the full 64 B per point-step, so
+        # its HBM fraction is on its own traffic (the k = 2 plan above moves half of that and runs faster)
+        c1 = D.make_config((args.side, 1, args.side), x_min=(x_min, 0.0, z_min), flux_face=face,
+                           stream=stream.cuda_stream, device=local, precision=D.DIRAC_FP32, steps_per_launch=1,
+                           points_per_lane=2)
+        h1 = D.dirac_create_grid(c1)
+        D.dirac_set_potential(h1, V, D.DIRAC_V_X_ONLY)
+        D.dirac_set_state(h1, dev32)
+        n1 = 400
+        D.dirac_step(h1, 64)  # warm-up
+        e10, e11 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e10.record(stream)
+        D.dirac_step(h1, n1)
+        e11.record(stream)
+        stream.synchronize()
+        t1 = max_over_ranks(e10.elapsed_time(e11))
+        D.dirac_destroy(h1)
+        v1 = ncell * n1 * world / (t1 / 1e3)
+        variants["fp32_k1"] = {
+            "value": v1, "unit": "point-steps/s", "steps": n1, "ms_per_step": t1 / n1, "steps_per_launch": 1,
+            "points_per_lane": 2, "bytes_per_point_step": FP32_BYTES_PER_POINT_STEP,
+            "hbm_frac": FP32_BYTES_PER_POINT_STEP * v1 / world / 1e9 / hbm_peak,
+            "workload": "the 2048^2 Klein grid, FP32 storage, one step per launch (the state read and written "
+                        "once per step: 64 B per point-step)"}
     del fp64_final
 
     # ---------------------------------------------------------------- FP64 with a laser field
