@@ -864,6 +864,17 @@ def main():
         qj = qq[:args.check_points]
         T_net = D.dirac_surrogate_predict(hs, qj)
         D.dirac_surrogate_destroy(hs)
+        # the same network on 65,536 queries per call (one fused launch of 512 CTAs per call)
+        big = 65536
+        hb_ = D.dirac_surrogate_create(lo, hi, seed=0, max_batch=big, stream=stream.cuda_stream, device=local)
+        D.dirac_surrogate_set_params(hb_, z["params"])
+        qb = lo + (hi - lo) * rng.uniform(0, 1, (big, 3))
+        D.dirac_surrogate_predict(hb_, qb)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            D.dirac_surrogate_predict(hb_, qb)
+        t_big = (time.perf_counter() - t0) / (5 * big)
+        D.dirac_surrogate_destroy(hb_)
 
         def solve(qs, prec):
             cfg_b = D.dirac_batch_default_config()
@@ -883,7 +894,8 @@ def main():
         bq = variants.get("batched_fp32", {})
         t32 = bq["ms_per_pass"] / 1e3 / bq["runs"] if bq else None
         variants["surrogate"] = {
-            "queries_per_s_network": 1.0 / t_net, "queries_per_s_fp64_solver": 1.0 / t64,
+            "queries_per_s_network": 1.0 / t_net, "queries_per_s_network_65536_per_call": 1.0 / t_big,
+            "queries_per_call": len(qq), "queries_per_s_fp64_solver": 1.0 / t64,
             "queries_per_s_batched_fp32_solver": (1.0 / t32) if t32 else None,
             "gain_network_over_fp64_solve": t64 / t_net,
             "gain_batched_fp32_over_fp64_solve": (t64 / t32) if t32 else None,
