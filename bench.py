@@ -53,7 +53,7 @@ FP64_ISSUE_PEAK_NOMINAL = FP64_INSTR_PER_SM_CLOCK * SM_COUNT * 2.07e9 / 1e12  # 
 # by (steps per launch, points per lane) of the captured variant (profiles/step_kernel_fp64_klein2048.md,
 # profiles/step_kernel_fp32_klein2048.md).  A variant without a capture reports null.
 MEASURED_TRAFFIC_PER_LAUNCH = {"fp64": {(1, 2): 277.539584e6 + 216.977408e6, (1, 4): 287.031808e6 + 217.295616e6},
-                               "fp32": {(2, 2): 147.694080e6 + 85.042432e6},
+                               "fp32": {(2, 2): 152.147456e6 + 83.809024e6},
                                "fx64": {(1, 1): 277.640448e6 + 217.100288e6}}
 # ncu sm__pipe_fp64_cycles_active of the same captures (fraction of active cycles)
 MEASURED_FP64_PIPE = {(1, 2): 0.8311, (1, 4): 0.8297}

@@ -877,7 +877,8 @@ void default_plan(dirac_grid *g) {
         K = 1;
         P = 2;
     }
-    make_plan(g, K, P, 4, g->fp32 ? 12 : 8);
+    // FP32 two steps per pass, P = 2: four blocks per SM fit (the sweep history in shared memory)
+    make_plan(g, K, P, 4, g->fp32 ? ((mode == 0 && K == 2 && P == 2) ? 16 : 12) : 8);
 }
 
 }  // namespace

@@ -30,12 +30,13 @@
 // Compile-time tunables of the 2-D step kernels: resident 4-warp blocks per SM the register budget is fitted to
 // (fixed point k = 1, P = 1; FP32 k = 2, P = 2; FP64 k = 1, P = 2 and 4), and rows per loop iteration of the
 // fixed-point kernel.  Fixed point: 4 blocks with two rows per iteration fit 128 registers without spilling (33.1
-// against 26.7 G point-steps/s at 150 registers and 3 blocks, 2048^2).
+// against 26.7 G point-steps/s at 150 registers and 3 blocks, 2048^2).  FP32 k = 2, P = 2: 4 blocks fit once
+// the z sweep's history lives in shared memory (HistSmem below).
 #ifndef FX_MIN_BLOCKS
 #define FX_MIN_BLOCKS 4
 #endif
 #ifndef F32_MIN_BLOCKS
-#define F32_MIN_BLOCKS 1
+#define F32_MIN_BLOCKS 4
 #endif
 #ifndef F64_MIN_BLOCKS
 #define F64_MIN_BLOCKS 1
@@ -216,11 +217,19 @@ template <typename T, int K, int MODE> struct RowUnroll {
     static constexpr bool FX = sizeof(T) == 8 && (T)0.5 == (T)0;  // the int64 fixed-point state
     static constexpr int value = (sizeof(T) == 4 && K == 1 && MODE == 0) ? 2 : ((FX && K == 1 && MODE == 0) ? FX_ROW_UNROLL : 1);
 };
-template <typename T, int K, int P, int MODE, int UNR = RowUnroll<T, K, MODE>::value>
+// Whether the z sweep's history (the "+" sums of the two previous rows per level) lives in the warp's shared
+// memory instead of registers, one slot per row parity so that nothing moves.  Measured for the single-grid
+// FP32 two-step kernel (k = 2, P = 2): the registers it frees let four blocks (16 warps) per SM run without
+// spilling, 114.5 against 105.0 G point-steps/s at 2048^2 with the same bits.  The batched kernel, which runs
+// the same warp routine, keeps the history in registers (107.5 against 116.0 G with it in shared memory).
+template <typename T, int K, int P, int MODE> struct HistSmem {
+    static constexpr bool value = sizeof(T) == 4 && K == 2 && P == 2 && MODE == 0;
+};
+template <typename T, int K, int P, int MODE, int UNR = RowUnroll<T, K, MODE>::value, bool HS = false>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem);
 template <int K>
 __device__ __forceinline__ void finish_flux(const SweepArgs &a);
-template <typename T, int K, int P> struct Ring;
+template <typename T, int K, int P, bool HS = false> struct Ring;
 
 // Pipelined levels of one launch: K steps, or 2K levels for the second-order splitting (mode 2).
 template <int K, int MODE> struct Levels { static constexpr int value = (MODE == 2 || MODE == 5) ? 2 * K : K; };
@@ -246,13 +255,14 @@ template <typename T, int K, int P, int MODE> struct SweepMinBlocks {
 template <typename T, int K, int P, int MODE>
 __global__ void __launch_bounds__(128, SweepMinBlocks<T, K, P, MODE>::value) sweep_kernel(const SweepArgs a) {
     constexpr int L = Levels<K, MODE>::value;
+    constexpr bool HS = HistSmem<T, K, P, MODE>::value;
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t per_plane = a.nstrips * a.nsegs;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    unsigned char *wsmem = dyn_smem + (threadIdx.x >> 5) * Ring<T, L, P>::WARP_BYTES;
+    unsigned char *wsmem = dyn_smem + (threadIdx.x >> 5) * Ring<T, L, P, HS>::WARP_BYTES;
     // Warps past the end skip the work but still reach the block-completion ticket below.
-    if (wid < per_plane * a.nplanes) sweep_warp<T, K, P, MODE>(a, wid, lane, wsmem);
+    if (wid < per_plane * a.nplanes) sweep_warp<T, K, P, MODE, RowUnroll<T, K, MODE>::value, HS>(a, wid, lane, wsmem);
     if (a.flux_face >= 0) finish_flux<L>(a);
 }
 
@@ -333,17 +343,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// Per-warp shared memory: 128 B of mbarriers, the row ring, then the flux hand-off area
-// (K levels x 8 values x 32 lanes).
-template <typename T, int K, int P> struct Ring {
+// Per-warp shared memory: 128 B of mbarriers, the row ring, the flux hand-off area (K levels x 8 values x 32
+// lanes), then with HS the sweep history ([row parity 2][level K][lane 32][point P][2] complex values; the ring
+// keeps three rows so that four blocks fit).
+template <typename T, int K, int P, bool HS> struct Ring {
     static constexpr int ROW_BYTES = 32 * P * 8 * (int)sizeof(T);  // one warp row: 32P cells
-    static constexpr int SLOTS = ROW_BYTES >= 8192 ? 3 : 4;
+    static constexpr int SLOTS = (HS || ROW_BYTES >= 8192) ? 3 : 4;
     static constexpr int FLUX_BYTES = K * 8 * 32 * (int)sizeof(T);
-    static constexpr int WARP_BYTES = 128 + SLOTS * ROW_BYTES + FLUX_BYTES;
+    static constexpr int HIST_BYTES = HS ? 2 * K * 32 * P * 2 * 2 * (int)sizeof(T) : 0;
+    static constexpr int WARP_BYTES = 128 + SLOTS * ROW_BYTES + FLUX_BYTES + HIST_BYTES;
 };
 
 // Dynamic shared memory a block of `wpb` warps needs.
-template <typename T, int K, int P> constexpr int ring_smem_bytes(int wpb) { return wpb * Ring<T, K, P>::WARP_BYTES; }
+template <typename T, int K, int P, bool HS = false> constexpr int ring_smem_bytes(int wpb) {
+    return wpb * Ring<T, K, P, HS>::WARP_BYTES;
+}
 
 // Records row q's "+" sums in the two-slot history: with two rows per iteration into the slot that held row
 // q - 2 (`older`); with one, slot 0 takes slot 1 (row q - 1) and slot 1 takes row q.
@@ -426,7 +440,7 @@ __device__ __forceinline__ void flux_row(const Cx<T> *lu14, const Cx<T> *lu23, c
     }
 }
 
-template <typename T, int K, int P, int MODE, int UNR>
+template <typename T, int K, int P, int MODE, int UNR, bool HS>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem) {
     constexpr int L = Levels<K, MODE>::value;  // pipelined levels (one row and one x cell of halo each)
     const int64_t per_plane = a.nstrips * a.nsegs;
@@ -515,7 +529,14 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
     const int src_prev = (lane + 31) & 31, src_next = (lane + 1) & 31;
 
     // Row ring: the copied span of a row is the strip's cells clipped to the grid.
-    using RG = Ring<T, L, P>;
+    using RG = Ring<T, L, P, HS>;
+    // HS: the sweep history in shared memory, slot = parity of the row it holds, zero at the task's start
+    Cx<T> *hist = reinterpret_cast<Cx<T> *>(wsmem + 128 + RG::SLOTS * RG::ROW_BYTES + RG::FLUX_BYTES);
+    if (HS) {
+#pragma unroll
+        for (int t = 0; t < 2 * L * P * 2; ++t)
+            hist[((t / (L * P * 2) * L + (t / (P * 2)) % L) * 32 + lane) * P * 2 + t % (P * 2)] = Cx<T>{T(0), T(0)};
+    }
     T *gsm = reinterpret_cast<T *>(wsmem + 128 + RG::SLOTS * RG::ROW_BYTES);  // flux hand-off [K][8][32]
     const int64_t cx0 = max(xa, (int64_t)0), cx1 = min(xa + 32 * P, nx);
     const uint32_t copy_bytes = (uint32_t)((cx1 - cx0) * 8 * (int64_t)sizeof(T));
@@ -681,12 +702,22 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                 if (MODE != 1) {
                     // z sweep (Eq. sol_dis_3): +z movers (b1+b3, b2-b4), -z movers (b1-b3, b2+b4)
                     const Cx<T> U13 = cadd(b0, b2), U24 = csub(b1, b3);
+                    // row q - 2's sums: the slot of q's parity (HS) or the register slot
+                    Cx<T> *hp = hist + ((((int)(q & 1) * L + lev) * 32 + lane) * P + j) * 2;
+                    Cx<T> h0, h1;
+                    if (HS) {
+                        h0 = hp[0];
+                        h1 = hp[1];
+                    } else {
+                        h0 = UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][0];
+                        h1 = UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][1];
+                    }
                     if (need_out) {
                         const Cx<T> W13 = csub(b0, b2), W24 = cadd(b1, b3);
-                        o[0] = cadd(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][0], W13);
-                        o[2] = csub(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][0], W13);
-                        o[1] = cadd(UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][1], W24);
-                        o[3] = csub(W24, UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j][1]);
+                        o[0] = cadd(h0, W13);
+                        o[2] = csub(h0, W13);
+                        o[1] = cadd(h1, W24);
+                        o[3] = csub(W24, h1);
                         // phase (Eq. sol_dis_4) with the deferred 1/4
                         Cx<T> qu, qd;
                         if (a.full_table) {
@@ -720,7 +751,12 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                             o[3] = cmulp(o[3], qd);
                         }
                     }
-                    push_row<T, UNR>(UH[0][lev][j], UH[1][lev][j], UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j], U13, U24);
+                    if (HS) {  // row q's sums replace row q - 2's
+                        hp[0] = U13;
+                        hp[1] = U24;
+                    } else {
+                        push_row<T, UNR>(UH[0][lev][j], UH[1][lev][j], UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j], U13, U24);
+                    }
                 } else {
                     // y sweep (Eq. sol_dis_2): +y movers (b1 - i b4, b2 + i b3), -y movers (b1 + i b4, b2 - i b3)
                     const Cx<T> U14 = csub_ib(b0, b3), U23 = cadd_ib(b1, b2);

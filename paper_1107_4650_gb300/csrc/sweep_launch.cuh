@@ -9,7 +9,7 @@ static cudaError_t launch_one(const SweepArgs &a, int wpb, cudaStream_t s) {
     const int64_t warps = a.nstrips * a.nsegs * a.nplanes;
     const int64_t blocks = (warps + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
-    const int smem = ring_smem_bytes<T, Levels<K, MODE>::value, P>(wpb);
+    const int smem = ring_smem_bytes<T, Levels<K, MODE>::value, P, HistSmem<T, K, P, MODE>::value>(wpb);
     // opt in to > 48 KB of dynamic shared memory, once per device and block size
     static std::atomic<unsigned long long> done[4];
     const int slot = (wpb == 4) ? 0 : (wpb == 2) ? 1 : (wpb == 8) ? 2 : 3;
