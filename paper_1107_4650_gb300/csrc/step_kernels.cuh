@@ -219,11 +219,12 @@ template <typename T, int K, int MODE> struct RowUnroll {
 };
 // Whether the z sweep's history (the "+" sums of the two previous rows per level) lives in the warp's shared
 // memory instead of registers, one slot per row parity so that nothing moves.  Measured for the single-grid
-// FP32 two-step kernel (k = 2, P = 2): the registers it frees let four blocks (16 warps) per SM run without
-// spilling, 114.5 against 105.0 G point-steps/s at 2048^2 with the same bits.  The batched kernel, which runs
-// the same warp routine, keeps the history in registers (107.5 against 116.0 G with it in shared memory).
+// FP32 kernels with P = 2: at k = 2 the registers it frees let four blocks (16 warps) per SM run without
+// spilling, 114.5 against 105.0 G point-steps/s at 2048^2; at k = 4 it takes the kernel from 208 to 128
+// registers, 105.3 against 67.1 G; the same bits either way.  The batched kernel, which runs the same warp
+// routine, keeps the history in registers (107.5 against 116.0 G with it in shared memory).
 template <typename T, int K, int P, int MODE> struct HistSmem {
-    static constexpr bool value = sizeof(T) == 4 && K == 2 && P == 2 && MODE == 0;
+    static constexpr bool value = sizeof(T) == 4 && (K == 2 || K == 4) && P == 2 && MODE == 0;
 };
 template <typename T, int K, int P, int MODE, int UNR = RowUnroll<T, K, MODE>::value, bool HS = false>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem);
