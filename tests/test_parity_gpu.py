@@ -296,6 +296,25 @@ def test_2d_fp32_error_against_fp64_oracle(D):
         assert abs(obs["norm"] - o["norm"]) < 1e-5
 
 
+@pytest.mark.parametrize("shape", [(70, 45), (131, 37), (9, 6), (200, 3)])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_2d_fp32_plans_give_the_same_bits(D, shape, periodic):
+    """FP32 storage: every launch plan does each step's arithmetic in the same order, so the states agree bit for
+    bit whether the sweep history sits in registers (k = 1; P = 4) or in shared memory (k = 2 and 4 with P = 2),
+    and however many steps one launch fuses."""
+    nx, nz = shape
+    psi = W.random_state(nz, 1, nx, seed=nx + 3 * nz + periodic)
+    V = np.random.default_rng(nx).uniform(-2e4, 5e4, nx)
+    ref = None
+    for K, P in ((1, 1), (1, 2), (2, 2), (2, 4), (4, 2), (4, 4)):
+        got, _, info = run_gpu(D, psi, 2, 13, V=V, periodic=periodic, fp32=True, K=K, P=P)
+        assert info["steps_per_launch"] == K and info["points_per_lane"] == P
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (K, P)
+
+
 def test_2d_fp32_klein_flux(D):
     run = W.KleinRun(side=384, V0=2.5 * C * C, p0=0.6 * C, width=20 * DX, nsteps=300, face=240)
     psi0 = run.state()
