@@ -868,7 +868,8 @@ void default_plan(dirac_grid *g) {
         return;
     }
     int K = g->fp32 ? 2 : 1, P = (g->fp32 || mode >= 2) ? 2 : 4;
-    if (mode == 2 || mode == 3 || mode == 5) K = 1;  // measured: the field's phase matrix makes k = 2 register-bound
+    if (mode == 3 || mode == 5) K = 1;  // measured: the field's phase matrix makes k = 2 register-bound
+    if (mode == 2) K = g->fp32 ? 2 : 1;  // FP32 second order: two steps per pass with the history in shared memory
     if (mode == 5 && !g->fp32) P = 1;  // the FP64 two-level matrix step spills at P = 2
     if (k > 0) K = k;
     if (pp > 0) P = pp;
@@ -877,8 +878,10 @@ void default_plan(dirac_grid *g) {
         K = 1;
         P = 2;
     }
-    // FP32 two steps per pass, P = 2: four blocks per SM fit (the sweep history in shared memory)
-    make_plan(g, K, P, 4, g->fp32 ? ((mode == 0 && K == 2 && P == 2) ? 16 : 12) : 8);
+    // FP32 P = 2 with the sweep history in shared memory: four blocks per SM fit (first order two steps per
+    // pass, second order one)
+    const bool four = g->fp32 && P == 2 && ((mode == 0 && K == 2) || (mode == 2 && K == 1));
+    make_plan(g, K, P, 4, g->fp32 ? (four ? 16 : 12) : 8);
 }
 
 }  // namespace

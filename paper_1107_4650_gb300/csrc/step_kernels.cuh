@@ -30,8 +30,8 @@
 // Compile-time tunables of the 2-D step kernels: resident 4-warp blocks per SM the register budget is fitted to
 // (fixed point k = 1, P = 1; FP32 k = 2, P = 2; FP64 k = 1, P = 2 and 4), and rows per loop iteration of the
 // fixed-point kernel.  Fixed point: 4 blocks with two rows per iteration fit 128 registers without spilling (33.1
-// against 26.7 G point-steps/s at 150 registers and 3 blocks, 2048^2).  FP32 k = 2, P = 2: 4 blocks fit once
-// the z sweep's history lives in shared memory (HistSmem below).
+// against 26.7 G point-steps/s at 150 registers and 3 blocks, 2048^2).  FP32 k = 2, P = 2 (and the second-order
+// step at k = 1, P = 2): 4 blocks fit once the z sweep's history lives in shared memory (HistSmem below).
 #ifndef FX_MIN_BLOCKS
 #define FX_MIN_BLOCKS 4
 #endif
@@ -221,10 +221,12 @@ template <typename T, int K, int MODE> struct RowUnroll {
 // memory instead of registers, one slot per row parity so that nothing moves.  Measured for the single-grid
 // FP32 kernels with P = 2: at k = 2 the registers it frees let four blocks (16 warps) per SM run without
 // spilling, 114.5 against 105.0 G point-steps/s at 2048^2; at k = 4 it takes the kernel from 208 to 128
-// registers, 105.3 against 67.1 G; the same bits either way.  The batched kernel, which runs the same warp
-// routine, keeps the history in registers (107.5 against 116.0 G with it in shared memory).
+// registers, 105.3 against 67.1 G; in the second-order step (mode 2) 150 -> 114 registers at k = 1 and
+// 197 -> 126 at k = 2, the best plan 60.8 against 56.8 G; the same bits every time.  The batched kernel, which
+// runs the same warp routine, keeps the history in registers (107.5 against 116.0 G with it in shared memory).
 template <typename T, int K, int P, int MODE> struct HistSmem {
-    static constexpr bool value = sizeof(T) == 4 && (K == 2 || K == 4) && P == 2 && MODE == 0;
+    static constexpr bool value =
+        sizeof(T) == 4 && P == 2 && ((MODE == 0 && (K == 2 || K == 4)) || (MODE == 2 && (K == 1 || K == 2)));
 };
 template <typename T, int K, int P, int MODE, int UNR = RowUnroll<T, K, MODE>::value, bool HS = false>
 __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid, const int lane, unsigned char *wsmem);
@@ -249,6 +251,7 @@ template <typename T, int K, int P, int MODE> struct SweepMinBlocks {
     static constexpr bool F64 = sizeof(T) == 8 && !FX;
     static constexpr int value = (FX && K == 1 && P == 1 && MODE == 0)                  ? FX_MIN_BLOCKS
                                  : (sizeof(T) == 4 && K == 2 && P == 2 && MODE == 0)   ? F32_MIN_BLOCKS
+                                 : (sizeof(T) == 4 && K == 1 && P == 2 && MODE == 2)   ? F32_MIN_BLOCKS
                                  : (F64 && K == 1 && (P == 2 || P == 4) && MODE == 0) ? F64_MIN_BLOCKS
                                                                                        : 1;
 };
@@ -629,11 +632,18 @@ __device__ __forceinline__ void sweep_warp(const SweepArgs &a, const int64_t wid
                     const Cx<T> U13 = cadd(st[j][0], st[j][2]), U24 = csub(st[j][1], st[j][3]);
                     const Cx<T> W13 = csub(st[j][0], st[j][2]), W24 = cadd(st[j][1], st[j][3]);
                     Cx<T>(&UO)[2] = UH[UNR == 2 ? (par + lev) & 1 : 0][lev][j];  // row q - 2
-                    zs[j][0] = cadd(UO[0], W13);
-                    zs[j][2] = csub(UO[0], W13);
-                    zs[j][1] = cadd(UO[1], W24);
-                    zs[j][3] = csub(W24, UO[1]);
-                    push_row<T, UNR>(UH[0][lev][j], UH[1][lev][j], UO, U13, U24);
+                    Cx<T> *hq = hist + ((((int)(q & 1) * L + lev) * 32 + lane) * P + j) * 2;  // HS: its slot
+                    const Cx<T> o0 = HS ? hq[0] : UO[0], o1 = HS ? hq[1] : UO[1];
+                    zs[j][0] = cadd(o0, W13);
+                    zs[j][2] = csub(o0, W13);
+                    zs[j][1] = cadd(o1, W24);
+                    zs[j][3] = csub(W24, o1);
+                    if (HS) {
+                        hq[0] = U13;
+                        hq[1] = U24;
+                    } else {
+                        push_row<T, UNR>(UH[0][lev][j], UH[1][lev][j], UO, U13, U24);
+                    }
                     if (!zrow_ok)
 #pragma unroll
                         for (int c = 0; c < 4; ++c) zs[j][c] = Cx<T>{T(0), T(0)};
